@@ -1,0 +1,273 @@
+"""Python access to the plain FP64 CPU oracle (relsim_oracle.c).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package. The CUDA library and its
+binding never do. The oracle is compiled from C with gcc on first use (or by
+``oracle.build.build()``), with no fast-math and no FMA contraction.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import build, lib_path
+
+__all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "curl_c",
+           "curl_n", "rhs", "gmres", "field_update", "push", "energies", "cell_keys",
+           "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
+           "to_full_offsets", "make_config"]
+
+
+class OracleConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dt", ctypes.c_double), ("theta", ctypes.c_double),
+                ("nspecies", ctypes.c_int),
+                ("q", ctypes.c_double * 4), ("m", ctypes.c_double * 4),
+                ("gmres_tol", ctypes.c_double),
+                ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int)]
+
+
+class Ledger(ctypes.Structure):
+    _fields_ = [("W_E0", ctypes.c_double), ("W_B0", ctypes.c_double), ("K0", ctypes.c_double),
+                ("W_E1", ctypes.c_double), ("W_B1", ctypes.c_double), ("K1", ctypes.c_double),
+                ("work_grid", ctypes.c_double), ("work_particles", ctypes.c_double),
+                ("mismatch", ctypes.c_double), ("dissipation", ctypes.c_double),
+                ("residual", ctypes.c_double), ("gmres_iters", ctypes.c_int),
+                ("gmres_relres", ctypes.c_double)]
+
+    def asdict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_I64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_C = ctypes.POINTER(OracleConfig)
+
+
+def load():
+    """Load (building if needed) the oracle shared library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        build()
+    lib = ctypes.CDLL(path)
+    sig = {
+        "orc_version": (ctypes.c_int, []),
+        "orc_node_weights": (None, [_C, ctypes.c_double, ctypes.c_double, _I64, _D]),
+        "orc_gather_E": (None, [_C, _D, ctypes.c_double, ctypes.c_double, _D]),
+        "orc_gather_B": (None, [_C, _D, ctypes.c_double, ctypes.c_double, _D]),
+        "orc_alpha": (None, [ctypes.c_double, ctypes.c_double, _D, _D]),
+        "orc_deposit": (None, [_C, _I64, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
+        "orc_curl_c": (None, [_C, _D, _D]),
+        "orc_curl_n": (None, [_C, _D, _D]),
+        "orc_apply_M": (None, [_C, _D, _D, _D]),
+        "orc_apply_A": (None, [_C, _D, _D, _D]),
+        "orc_rhs": (None, [_C, _D, _D, _D, _D]),
+        "orc_gmres": (ctypes.c_int, [_C, _D, _D, _D, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double)]),
+        "orc_field_update": (None, [_C, _D, _D, _D]),
+        "orc_push": (None, [_C, _I64, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
+        "orc_energies": (None, [_C, _I64, _D, _D, _D, _D, _D, _D, _D]),
+        "orc_cell_keys": (None, [_C, ctypes.c_int64, _D, _D, _I32]),
+        "orc_stable_sort": (None, [ctypes.c_int64, _I32, ctypes.c_int32, _I64, _I64]),
+        "orc_step": (ctypes.c_int, [_C, _I64, _D, _D, _D, _D, _D, _D, _D, _D,
+                                    ctypes.POINTER(Ledger), ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta=0.5, q=(1.0, -1.0), m=(1.0, 1.0),
+                gmres_tol=1e-12, gmres_restart=50, gmres_maxit=2000) -> OracleConfig:
+    c = OracleConfig()
+    c.nx, c.ny, c.dx, c.dy, c.dt, c.theta = nx, ny, dx, dy, dt, theta
+    c.nspecies = len(q)
+    for s in range(len(q)):
+        c.q[s] = q[s]
+        c.m[s] = m[s]
+    c.gmres_tol, c.gmres_restart, c.gmres_maxit = gmres_tol, gmres_restart, gmres_maxit
+    return c
+
+
+def _f(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Particles:
+    """Concatenated FP64 particle arrays of all species (oracle layout)."""
+
+    def __init__(self, species):
+        self.off = np.zeros(len(species) + 1, dtype=np.int64)
+        for s, sp in enumerate(species):
+            self.off[s + 1] = self.off[s] + len(sp["x"])
+        cat = lambda k: _f(np.concatenate([np.asarray(sp[k], dtype=np.float64) for sp in species]))
+        self.x, self.y = cat("x"), cat("y")
+        self.ux, self.uy, self.uz = cat("ux"), cat("uy"), cat("uz")
+        self.w = cat("w")
+
+    def species(self, s):
+        a, b = self.off[s], self.off[s + 1]
+        return {k: getattr(self, k)[a:b].copy() for k in ("x", "y", "ux", "uy", "uz", "w")}
+
+    def copy(self):
+        p = Particles.__new__(Particles)
+        p.off = self.off.copy()
+        for k in ("x", "y", "ux", "uy", "uz", "w"):
+            setattr(p, k, getattr(self, k).copy())
+        return p
+
+
+def node_weights(c, x, y):
+    g = np.zeros(4, dtype=np.int64)
+    W = np.zeros(4)
+    load().orc_node_weights(ctypes.byref(c), x, y, g, W)
+    return g, W
+
+
+def gather_E(c, E, x, y):
+    out = np.zeros(3)
+    load().orc_gather_E(ctypes.byref(c), _f(E).ravel(), x, y, out)
+    return out
+
+
+def gather_B(c, B, x, y):
+    out = np.zeros(3)
+    load().orc_gather_B(ctypes.byref(c), _f(B).ravel(), x, y, out)
+    return out
+
+
+def alpha(beta, gbar, Bp):
+    out = np.zeros(9)
+    load().orc_alpha(beta, gbar, _f(Bp), out)
+    return out.reshape(3, 3)
+
+
+def deposit(c, P: Particles, B):
+    nn = c.nx * c.ny
+    J = np.zeros(3 * nn)
+    M = np.zeros(81 * nn)
+    load().orc_deposit(ctypes.byref(c), P.off, P.x, P.y, P.ux, P.uy, P.uz, P.w,
+                       _f(B).ravel(), J, M)
+    return J.reshape(3, nn), M.reshape(nn, 9, 3, 3)
+
+
+def curl_c(c, E):
+    out = np.zeros(3 * c.nx * c.ny)
+    load().orc_curl_c(ctypes.byref(c), _f(E).ravel(), out)
+    return out.reshape(3, -1)
+
+
+def curl_n(c, B):
+    out = np.zeros(3 * c.nx * c.ny)
+    load().orc_curl_n(ctypes.byref(c), _f(B).ravel(), out)
+    return out.reshape(3, -1)
+
+
+def apply_M(c, M, v):
+    out = np.zeros(3 * c.nx * c.ny)
+    load().orc_apply_M(ctypes.byref(c), _f(M).ravel(), _f(v).ravel(), out)
+    return out.reshape(3, -1)
+
+
+def apply_A(c, M, v):
+    out = np.zeros(3 * c.nx * c.ny)
+    load().orc_apply_A(ctypes.byref(c), _f(M).ravel(), _f(v).ravel(), out)
+    return out.reshape(3, -1)
+
+
+def rhs(c, E, B, J):
+    out = np.zeros(3 * c.nx * c.ny)
+    load().orc_rhs(ctypes.byref(c), _f(E).ravel(), _f(B).ravel(), _f(J).ravel(), out)
+    return out.reshape(3, -1)
+
+
+def gmres(c, M, b, x0):
+    x = _f(x0).ravel().copy()
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().orc_gmres(ctypes.byref(c), _f(M).ravel(), _f(b).ravel(), x,
+                          ctypes.byref(it), ctypes.byref(rr))
+    return x.reshape(3, -1), st, it.value, rr.value
+
+
+def field_update(c, Etheta, E, B):
+    E = _f(E).ravel().copy()
+    B = _f(B).ravel().copy()
+    load().orc_field_update(ctypes.byref(c), _f(Etheta).ravel(), E, B)
+    return E.reshape(3, -1), B.reshape(3, -1)
+
+
+def push(c, P: Particles, Etheta, B):
+    """Push in place; returns sums (K0, K1, work_particles, mismatch)."""
+    sums = np.zeros(4)
+    load().orc_push(ctypes.byref(c), P.off, P.x, P.y, P.ux, P.uy, P.uz, P.w,
+                    _f(Etheta).ravel(), _f(B).ravel(), sums)
+    return sums
+
+
+def energies(c, P: Particles, E, B):
+    out = np.zeros(3)
+    load().orc_energies(ctypes.byref(c), P.off, P.ux, P.uy, P.uz, P.w, _f(E).ravel(),
+                        _f(B).ravel(), out)
+    return out
+
+
+def cell_keys(c, x, y):
+    x, y = _f(x), _f(y)
+    keys = np.zeros(x.size, dtype=np.int32)
+    load().orc_cell_keys(ctypes.byref(c), x.size, x, y, keys)
+    return keys
+
+
+def stable_sort(keys, nkeys):
+    keys = np.ascontiguousarray(keys, dtype=np.int32)
+    perm = np.zeros(keys.size, dtype=np.int64)
+    start = np.zeros(nkeys + 1, dtype=np.int64)
+    load().orc_stable_sort(keys.size, keys, nkeys, perm, start)
+    return perm, start
+
+
+def step(c, P: Particles, E, B, want_matrices=False):
+    """One full step in place on P; returns (E, B, ledger dict, extras)."""
+    nn = c.nx * c.ny
+    E = _f(E).ravel().copy()
+    B = _f(B).ravel().copy()
+    led = Ledger()
+    extras = {}
+    if want_matrices:
+        J = np.zeros(3 * nn)
+        M = np.zeros(81 * nn)
+        Et = np.zeros(3 * nn)
+        ptrs = [J.ctypes.data, M.ctypes.data, Et.ctypes.data]
+    else:
+        ptrs = [None, None, None]
+    st = load().orc_step(ctypes.byref(c), P.off, P.x, P.y, P.ux, P.uy, P.uz, P.w, E, B,
+                         ctypes.byref(led), *ptrs)
+    if want_matrices:
+        extras = {"J": J.reshape(3, nn), "M": M.reshape(nn, 9, 3, 3),
+                  "Etheta": Et.reshape(3, nn)}
+    d = led.asdict()
+    d["status"] = st
+    return E.reshape(3, nn), B.reshape(3, nn), d, extras
+
+
+# the five neighbour offsets (di, dj) a half-stored mass matrix keeps: the
+# other four follow from M_{g,g+o} = M_{g+o,g}
+HALF_OFFSETS = ((0, 0), (1, 0), (-1, 1), (0, 1), (1, 1))
+
+
+def to_full_offsets(o):
+    di, dj = o
+    return (dj + 1) * 3 + (di + 1)

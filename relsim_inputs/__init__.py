@@ -1,0 +1,7 @@
+"""Seeded synthetic input generators shared by the oracle tests, the CUDA
+parity tests and the benchmark. Holds no arithmetic of the method itself."""
+from .harris import (HarrisConfig, harris_derived, make_harris, random_state,
+                     sample_maxwell_juettner, boost_flip)
+
+__all__ = ["HarrisConfig", "harris_derived", "make_harris", "random_state",
+           "sample_maxwell_juettner", "boost_flip"]

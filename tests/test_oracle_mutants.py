@@ -1,0 +1,72 @@
+"""The oracle pins catch plausible mistakes.
+
+Each case copies oracle/ to a temporary directory, plants one mistake in the
+C source (a dropped term, a flipped sign, a wrong index or a transposed
+operand), rebuilds it there and runs the pin suite against the copy, which
+must then fail. The committed oracle is never modified.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "alpha_rotation_sign": ("- ax[r * 3 + s] + a[r] * a[s]", "+ ax[r * 3 + s] + a[r] * a[s]"),
+    "alpha_drops_aaT": ("- ax[r * 3 + s] + a[r] * a[s])", "- ax[r * 3 + s])"),
+    "jhat_drops_1_over_gamma": ("vJ[r] /= gbar;", ";"),
+    "jhat_skips_alpha": ("vJ[r] += alpha[r * 3 + k] * u[k];", "vJ[r] += (r == k) * u[k];"),
+    "mass_matrix_wrong_weight": ("cM * W[a] * W[b] * alpha[rs]", "cM * W[a] * W[a] * alpha[rs]"),
+    "mass_matrix_drops_gamma": ("double cM = w[p] * q * beta / (gbar * dV);",
+                                "double cM = w[p] * q * beta / dV;"),
+    "pair_slot_no_unwrap": ("if (di > 1) di -= c->nx;", ";"),
+    "curl_c_sign": ("out[nn + n00] = -DX(Ez);", "out[nn + n00] = DX(Ez);"),
+    "curl_n_sign": ("out[2 * nn + c11] = DX(By) - DY(Bx);", "out[2 * nn + c11] = DX(By) + DY(Bx);"),
+    "operator_drops_square": ("out[k] = v[k] + td * td * cn[k] + td * mv[k];",
+                              "out[k] = v[k] + td * cn[k] + td * mv[k];"),
+    "apply_M_wrong_node": ("acc[r] += blk[r * 3 + s] * v[s * nn + h];",
+                           "acc[r] += blk[r * 3 + s] * v[s * nn + g];"),
+    "rhs_current_sign": ("b[k] = E[k] + td * cn[k] - td * J[k];", "b[k] = E[k] + td * cn[k] + td * J[k];"),
+    "faraday_sign": ("B[k] = B[k] - c->dt * cc[k];", "B[k] = B[k] + c->dt * cc[k];"),
+    "E_update_drops_extrapolation": ("E[k] = (Etheta[k] - (1.0 - th) * E[k]) / th;", "E[k] = Etheta[k];"),
+    "push_no_leapfrog": ("u1[k] = 2.0 * ub[k] - u0[k];", "u1[k] = ub[k];"),
+    "push_alpha_transposed": ("ub[r] += alpha[r * 3 + k] * wv[k];", "ub[r] += alpha[k * 3 + r] * wv[k];"),
+    "push_double_kick": ("wv[k] = u0[k] + beta * Ep[k];", "wv[k] = u0[k] + 2.0 * beta * Ep[k];"),
+    "push_position_uses_u": ("x[p] = wrap_pos(x[p] + c->dt * u1[0] / g1, Lx);",
+                             "x[p] = wrap_pos(x[p] + c->dt * u1[0], Lx);"),
+    "gather_B_on_nodes": ("    centre_weights(c, x, y, g, W);\n", "    orc_node_weights(c, x, y, g, W);\n"),
+    "node_offsets_transposed": ("locate(x, c->dx, c->nx, &i, &fx);\n    locate(y, c->dy, c->ny, &j, &fy);",
+                                "locate(x, c->dx, c->nx, &i, &fy);\n    locate(y, c->dy, c->ny, &j, &fx);"),
+    "gmres_update_half": ("x[k] += y[i] * V[(int64_t)i * n + k];", "x[k] += 0.5 * y[i] * V[(int64_t)i * n + k];"),
+    "gmres_givens_sign": ("H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];",
+                          "H[(i + 1) * m + j] = sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];"),
+    "sort_unstable": ("perm[start[k] + cursor[k]++] = p;", "perm[start[k + 1] - 1 - cursor[k]++] = p;"),
+    "field_energy_factor": ("out[0] = 0.5 * dV * dot(3 * nn, E, E);", "out[0] = dV * dot(3 * nn, E, E);"),
+    "push_uses_new_E": ("orc_push(c, off, x, y, ux, uy, uz, w, Et, B0, sums);",
+                        "orc_push(c, off, x, y, ux, uy, uz, w, E, B0, sums);"),
+    "push_uses_new_B": ("orc_push(c, off, x, y, ux, uy, uz, w, Et, B0, sums);",
+                        "orc_push(c, off, x, y, ux, uy, uz, w, Et, B, sums);"),
+    "dissipation_sign": ("led->dissipation = (c->theta - 0.5) * dV * (dE2 + dB2);",
+                         "led->dissipation = (0.5 - c->theta) * dV * (dE2 + dB2);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    orig, repl = MUTANTS[name]
+    src_dir = os.path.join(ROOT, "oracle")
+    src = open(os.path.join(src_dir, "relsim_oracle.c")).read()
+    assert src.count(orig) == 1, f"mutation site for {name} is not unique"
+    dst = tmp_path / "oracle"
+    shutil.copytree(src_dir, dst, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    (dst / "relsim_oracle.c").write_text(src.replace(orig, repl))
+    env = dict(os.environ, RELSIM_ORACLE_MUTANT_DIR=str(tmp_path))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    # the copy really was the one under test
+    assert (dst / "liboracle.so").exists()
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
