@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Particle-pushes/s of the RelSIM step on the 2D relativistic double Harris
+sheet, 1024 x 512 cells, 64 particles per cell per species (67.1M particles),
+FP32 form; with the HBM roofline of the dominant kernel, the FP64 form on the
+same GPU, an end-to-end figure through host buffers, and the FP64 CPU oracle
+timed on a bounded sample as a reported baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one pass of the whole hot path: deposit of the predicted current
+and mass matrices, the GMRES field solve with the field update, the push
+with the cell re-sort, and the energy ledger. Inputs stay resident in HBM
+for the headline value; they are far larger than L2 (1.6 GB of particles),
+so no L2 flush is needed between steps. With N > 1 (torchrun) every rank runs
+an independent replica (the workload is one periodic domain; the path is
+not sharded), and the value is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import ctypes
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-pushes/s incl. mass-matrix build, % HBM roofline, FP32 vs FP64 form"
+UNIT = "particle-pushes/s"
+
+WORKLOAD = {
+    "workload": "2D relativistic double Harris sheet, pair plasma, 1024x512 cells (dx=dy=1 d_e), "
+                "64 ppc per species (67,108,864 particles), sigma=10, theta_T=0.3, delta=1 d_e, "
+                "dt=1/omega_pe, theta=0.5, 1% B_y perturbation, seed 0",
+    "nx": 1024, "ny": 512, "ppc_per_species": 64, "particles": 67108864,
+    "form": "FP32 particles/fields/mass matrix, FP64 GMRES basis and ledger",
+    "gmres_tol": 1e-6, "gmres_restart": 30,
+    "l2": "inputs larger than L2 (1.6 GB of particle data per step), no flush",
+}
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def harris_config(seed=0):
+    from relsim_inputs import HarrisConfig
+    return HarrisConfig(nx=1024, ny=512, ppc=64, theta_T=0.3, delta=1.0, sigma=10.0, pert=0.01,
+                        dt=1.0, theta=0.5, seed=seed)
+
+
+def subsample(state, every):
+    """Every `every`-th particle of each species, weights scaled to keep the
+    charge and current densities (the bounded CPU-baseline sample)."""
+    import numpy as np
+    out = dict(state)
+    sp = []
+    for s in state["species"]:
+        d = {k: (v[::every] if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+        d["w"] = d["w"] * every
+        sp.append(d)
+    out["species"] = sp
+    return out
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    rec = d.get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2509_11100_gb300", "csrc", rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != rec.get("source_sha256_16"):
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
+def algorithmic_bytes(slot, n_particles, n_per_species, ncell, esz):
+    """Bytes a launch of the slot must move (what the method reads/writes)."""
+    if slot == "deposit":       # read x-offsets, u, w; write M (45) + Jhat (3) per node
+        return n_particles * 6 * esz + ncell * 48 * esz
+    if slot == "push_count":    # per species: read offsets, u, w; write moves per cell
+        return n_per_species * 6 * esz + ncell * 9 * 4
+    if slot == "push_scatter":  # per species: read + write the particle record
+        return n_per_species * 12 * esz + ncell * 18 * 4
+    if slot == "gmres_apply":   # M, v (FP64 in), Av (FP64 out)
+        return ncell * (45 * esz + 24 + 24)
+    if slot == "field_update":
+        return ncell * (24 + 45 * esz + 3 * esz * 6)
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2509_11100_gb300 as rs
+    from relsim_inputs import make_harris
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    hc = harris_config(seed=rank)
+    t0 = time.time()
+    state = make_harris(hc)
+    t_gen = time.time() - t0
+    n_per = [len(s["w"]) for s in state["species"]]
+    N = sum(n_per)
+    ncell = hc.nx * hc.ny
+
+    cfg = rs.make_config(hc.nx, hc.ny, dt=hc.dt, theta_implicit=hc.theta, precision=32,
+                         gmres_tol=WORKLOAD["gmres_tol"], gmres_restart=WORKLOAD["gmres_restart"])
+    sim = rs.Simulation(cfg)
+    sim.load_state(state)
+    for _ in range(args.warmup):
+        sim.step(ledger=True)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sim.profile(True)
+    sim.profile_read(reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = rs.relsim_kernel_launches()
+    ev0.record(stream)
+    ledgers = []
+    iters = []
+    for _ in range(args.steps):
+        led, status = sim.step(ledger=True)
+        ledgers.append(led)
+        iters.append(led["gmres_iters"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = rs.relsim_kernel_launches() - launches0
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = sim.profile_read(reset=True)
+    sim.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N / (ms / 1e3)
+
+    # per-kernel times, dominant kernel roofline
+    esz = 4
+    per_kernel = {k: {"ms_per_step": v[0] / args.steps, "groups": v[1], "kernels": v[2]}
+                  for k, v in prof.items() if v[1] > 0}
+    step_kernel_ms = sum(v["ms_per_step"] for v in per_kernel.values())
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
+    peak, peak_kind = measured_peaks()
+    groups_per_step = per_kernel[dom]["groups"] / args.steps
+    launch_ms = per_kernel[dom]["ms_per_step"] / groups_per_step
+    ab = algorithmic_bytes(dom, N, n_per[0], ncell, esz)
+    achieved = ab / (launch_ms / 1e3) / 1e9 if ab else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                "traffic": traffic_record(dom), "algorithmic_bytes_per_launch": ab,
+                "launch_ms": launch_ms}
+    # the mover + mass-matrix kernels together (deposit, push passes, sort tables)
+    mover = ("deposit", "push_count", "sort_tables", "push_scatter")
+    mover_ms = sum(per_kernel[k]["ms_per_step"] for k in mover if k in per_kernel)
+    mover_bytes = (algorithmic_bytes("deposit", N, 0, ncell, esz)
+                   + sum(algorithmic_bytes("push_count", n, 0, ncell, esz)
+                         + algorithmic_bytes("push_scatter", n, 0, ncell, esz) for n in n_per))
+    mover_gbs = mover_bytes / (mover_ms / 1e3) / 1e9
+    last = ledgers[-1]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism=f"replicas{world}" if world > 1 else "single"),
+        "roofline": roofline,
+        "mover_mass_matrix": {"value": N / (mover_ms / 1e3), "unit": UNIT, "ms_per_step": mover_ms,
+                              "achieved_gbs": mover_gbs, "frac": mover_gbs / peak,
+                              "kernels": list(mover)},
+        "per_kernel": per_kernel,
+        "kernel_ms_per_step": step_kernel_ms,
+        "gpu_launches": int(launches),
+        "gmres_iters_per_step": statistics.mean(iters),
+        "ledger": {"residual_rel": abs(last["residual"]) / last["total"],
+                   "mismatch_rel": abs(last["mismatch"]) / last["total"],
+                   "gmres_relres": last["gmres_relres"]},
+        "clocks": clk,
+        "input_generation_s": t_gen,
+    }
+
+    # end to end through the C ABI with host buffers: every step loads the
+    # state from pinned host memory, steps, and reads the ledger back
+    if not args.no_e2e:
+        pinned = []
+        for s in state["species"]:
+            x = torch.from_numpy(np.stack([s["x"], s["y"]], axis=1)).pin_memory()
+            u = torch.from_numpy(np.stack([s["ux"], s["uy"], s["uz"]], axis=1)).pin_memory()
+            w = torch.from_numpy(np.ascontiguousarray(s["w"])).pin_memory()
+            pinned.append((x, u, w))
+        E = torch.from_numpy(np.ascontiguousarray(state["E"])).pin_memory()
+        B = torch.from_numpy(np.ascontiguousarray(state["B"])).pin_memory()
+        h2d = sum(x.numel() * 8 + u.numel() * 8 + w.numel() * 8 for x, u, w in pinned)
+        h2d += (E.numel() + B.numel()) * 8
+        d2h = ctypes.sizeof(rs.relsim_energy)
+
+        def e2e_step():
+            for s, (x, u, w) in enumerate(pinned):
+                sim.load_species(s, x, u, w)
+            sim.set_fields(E, B)
+            led, _ = sim.step(ledger=True)
+            return led
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        ke = max(1, min(args.steps, 5))
+        t1 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t1) / ke
+        if dist is not None:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        out["e2e"] = {"value": world * N / te, "unit": UNIT, "ms_per_step": te * 1e3,
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "steps": ke}
+        del pinned
+    sim.close()
+    del sim
+
+    # the FP64 form on the same GPU and workload
+    if not args.no_fp64:
+        cfg64 = rs.make_config(hc.nx, hc.ny, dt=hc.dt, theta_implicit=hc.theta, precision=64,
+                               gmres_tol=1e-10, gmres_restart=WORKLOAD["gmres_restart"])
+        s64 = rs.Simulation(cfg64)
+        s64.load_state(state)
+        s64.step()
+        torch.cuda.synchronize()
+        k64 = max(1, min(args.steps, 3))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k64):
+            led64, _ = s64.step(ledger=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b) / k64
+        out["fp64_form"] = {"value": N / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                            "steps": k64, "gmres_tol": 1e-10,
+                            "ledger_residual_rel": abs(led64["residual"]) / led64["total"],
+                            "speedup_fp32_over_fp64": ms64 / ms}
+        s64.close()
+
+    # the FP64 CPU oracle, as it stands, on a bounded sample of the workload
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_baseline(state, hc, steps=2)
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def oracle_baseline(state, hc, steps=2, every=8):
+    """Time the FP64 CPU oracle on the workload's grid with every 8th particle
+    of each cell (8 ppc per species, 8.4M particles, weights x8)."""
+    import oracle
+    sample = subsample(state, every)
+    c = oracle.make_config(hc.nx, hc.ny, dt=hc.dt, theta=hc.theta, gmres_tol=1e-12, gmres_restart=50)
+    P = oracle.Particles(sample["species"])
+    n = int(P.off[-1])
+    E, B = sample["E"], sample["B"]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        E, B, led, _ = oracle.step(c, P, E, B)
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"same 1024x512 grid and fields, every {every}th particle of each cell "
+                      f"({n} particles, weights x{every}), {steps} full oracle steps "
+                      f"(deposit, GMRES tol 1e-12, push), single thread, FP64",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, local = rank_info()
+    if rank != 0:
+        return
+    from relsim_inputs import make_harris
+    import oracle
+    hc = harris_config(seed=0)
+    state = make_harris(hc)
+    every = 8
+    sample = subsample(state, every)
+    c = oracle.make_config(hc.nx, hc.ny, dt=hc.dt, theta=hc.theta, gmres_tol=1e-12, gmres_restart=50)
+    P = oracle.Particles(sample["species"])
+    n = int(P.off[-1])
+    E, B = sample["E"], sample["B"]
+    for _ in range(args.warmup):
+        E, B, led, _ = oracle.step(c, P, E, B)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        E, B, led, _ = oracle.step(c, P, E, B)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n / dt
+    sample_desc = (f"same 1024x512 grid and fields, every {every}th particle of each cell "
+                   f"({n} particles, weights x{every}); one full oracle step per timed step")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(WORKLOAD, parallelism="host cores (oracle)"),
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample_desc, "value": value,
+                         "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

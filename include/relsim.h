@@ -1,0 +1,260 @@
+/*
+ * relsim.h -- C ABI of the GB300 (sm_103a) RelSIM hot-path library.
+ *
+ * One time step of the relativistic semi-implicit particle-in-cell method
+ * used in the paper (Sec. 2, "Methods and Simulation Setup": the particle
+ * pusher is explicit, only the field solver is implicit, and the field
+ * solver uses a mass-matrix formulation). A step is three calls, in order:
+ *
+ *   relsim_build_mass_matrix   gather B^n at x^{n+1/2}, build each
+ *                              particle's rotation matrix alpha, deposit the
+ *                              predicted current Jhat and the 3x3 mass
+ *                              matrix blocks M_{g,g'} on the grid nodes
+ *   relsim_field_solve         solve the implicit field equation for
+ *                              E^{n+theta} (matrix-free GMRES), then advance
+ *                              E^{n+1} and B^{n+1}
+ *   relsim_push                push u^{n+1}, x^{n+3/2} with E^{n+theta} and
+ *                              B^n, and re-sort the particles by cell
+ *
+ * followed, when wanted, by relsim_energy_ledger. relsim_step does all
+ * four. The discrete equations (the paper cites them and does not print
+ * them; these are the readings this library implements, rationalised
+ * units with c = 1):
+ *
+ *   gbar  = sqrt(1 + |u^n|^2),  beta = q dt / (2 m),  a = beta B^n(x)/gbar
+ *   alpha = (I - [a]x + a a^T)/(1 + |a|^2)
+ *   Jhat_g = sum_p w q W_g(x) alpha u^n / gbar / dV
+ *   M_gg'  = sum_p w q beta / gbar W_g(x) W_g'(x) alpha / dV
+ *   (I + (theta dt)^2 curl_n curl_c + theta dt M) E^{n+theta}
+ *        = E^n + theta dt curl_n B^n - theta dt Jhat
+ *   E^{n+1} = (E^{n+theta} - (1 - theta) E^n)/theta
+ *   B^{n+1} = B^n - dt curl_c E^{n+theta}
+ *   ubar = alpha (u^n + beta E^{n+theta}(x)),  u^{n+1} = 2 ubar - u^n
+ *   x^{n+3/2} = x^{n+1/2} + dt u^{n+1}/sqrt(1 + |u^{n+1}|^2)   (periodic)
+ *
+ * Grid: 2D, periodic, nx x ny. Node (i,j) sits at (i dx, j dy) and carries
+ * E, Jhat and M; the cell centre (i+1/2, j+1/2) carries B. Node and cell
+ * (i,j) both have the linear index j*nx + i. W is the linear (cloud-in-cell)
+ * shape function. Requires nx, ny >= 3.
+ *
+ * Conventions for every entry point:
+ * - Return value: RELSIM_OK (0) or a negative RELSIM_ERR_* code. Nothing
+ *   aborts; relsim_last_error() returns a message owned by the context
+ *   (valid until the next call on it).
+ * - All work is enqueued on the CUDA stream given to relsim_init (0 means
+ *   the legacy default stream). Calls that return data to the host
+ *   (RELSIM_HOST outputs, relsim_field_solve's residual, the ledger)
+ *   synchronise that stream; the others return without waiting.
+ * - Buffers are owned by the caller. The library copies inputs (it never
+ *   keeps a caller pointer) and owns its device buffers until
+ *   relsim_destroy. "where" says whether a caller pointer is host memory
+ *   (RELSIM_HOST) or device memory of the context's GPU (RELSIM_DEVICE).
+ * - Field arrays are FP64, component-major: F[k*ncell + idx], k = x, y, z,
+ *   ncell = nx*ny. Particle arrays are FP64: positions x[2n] interleaved
+ *   (x_p, y_p) absolute in [0, nx dx) x [0, ny dy), momenta u[3n]
+ *   interleaved (ux, uy, uz) with u = gamma v, weights w[n].
+ * - Internally the FP32 form stores a position as cell index + FP32 offset
+ *   and computes particles, fields and mass matrices in FP32, keeping FP64
+ *   for the GMRES Krylov basis, its orthogonalisation and residual, and for
+ *   the energy-ledger reductions. The FP64 form computes everything in FP64.
+ */
+#ifndef RELSIM_H
+#define RELSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RELSIM_OK 0
+#define RELSIM_ERR_INVALID_ARG (-1)   /* bad pointer, size, species or config   */
+#define RELSIM_ERR_BAD_STATE (-2)     /* calls out of order (build/solve/push)  */
+#define RELSIM_ERR_CUDA (-3)          /* a CUDA runtime error; see the message  */
+#define RELSIM_ERR_OOM (-4)           /* device allocation failed               */
+#define RELSIM_ERR_NOT_CONVERGED (-5) /* GMRES hit gmres_maxit; state advanced  */
+#define RELSIM_ERR_NONFINITE (-6)     /* NaN/Inf found in inputs or results     */
+#define RELSIM_ERR_TIMEOUT (-7)       /* a bounded device wait gave up          */
+#define RELSIM_ERR_INTERNAL (-8)      /* an internal consistency check failed   */
+
+#define RELSIM_HOST 0
+#define RELSIM_DEVICE 1
+
+typedef struct relsim_ctx relsim_ctx;  /* opaque, owned by the library */
+
+typedef struct {
+    int dim;               /* must be 2                                        */
+    int nx, ny, nz;        /* cells per direction (nz ignored in 2D)           */
+    double dx, dy, dz;     /* cell sizes                                       */
+    double dt;             /* time step                                        */
+    double theta_implicit; /* theta in (0, 1]; 0.5 conserves energy            */
+    int precision;         /* 32 (FP32 form) or 64 (FP64 form)                 */
+    int nspecies;          /* 1..4                                             */
+    double q[4], m[4];     /* charge and mass per species (m > 0)              */
+    double gmres_tol;      /* relative residual target; 0 -> 1e-6 (FP32 form)
+                              or 1e-10 (FP64 form)                             */
+    int gmres_restart;     /* Krylov dimension per cycle; 0 -> 30 (max 100)    */
+    int gmres_maxit;       /* total Arnoldi steps per solve; 0 -> 500          */
+    int track_ids;         /* nonzero: carry an int32 id per particle (its load
+                              index) through every sort, for tracking           */
+    uint64_t seed;         /* reserved                                         */
+} relsim_config;
+
+typedef struct {
+    /* energies of the current state (after the last push or load) */
+    double W_E, W_B, K, total;   /* 1/2 dV sum|E|^2, 1/2 dV sum|B|^2,
+                                    sum w m (gamma - 1), their sum            */
+    double K_species[4];
+    /* terms of the last completed step (zero before the first step) */
+    double W_E0, W_B0, K0;       /* energies at the start of that step          */
+    double dW_E, dW_B, dK;       /* changes over the step, summed per element   */
+    double work_grid;            /* dt dV sum_g (Jhat + M E^{n+theta}).E^{n+theta} */
+    double work_particles;       /* dt sum_p w q (ubar/gbar).E^{n+theta}(x_p)    */
+    double mismatch;             /* dt sum_p w q ubar.E [2/(g0+g1) - 1/gbar]     */
+    double dissipation;          /* (theta - 1/2) dV (sum|dE|^2 + sum|dB|^2)     */
+    double residual;             /* dW_E + dW_B + dK - mismatch + dissipation:
+                                    zero up to the solve tolerance and round-off */
+    int gmres_iters;
+    int gmres_restarts;
+    double gmres_relres;         /* true ||b - A E^{n+theta}|| / ||b||           */
+    int64_t step;                /* completed steps since the last load          */
+    int64_t n_particles;
+} relsim_energy;
+
+/* Create a context for one simulation on the current CUDA device.
+   cfg: see relsim_config. cuda_stream: a cudaStream_t (or 0). On success
+   *out receives the context. Errors: INVALID_ARG (bad config), CUDA, OOM.
+   Allocates the grid arrays (fields, Jhat, M, GMRES basis) up front. */
+int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out);
+
+/* Free every device buffer of the context and the context itself. Safe on
+   NULL. Synchronises the context's stream first. */
+void relsim_destroy(relsim_ctx* ctx);
+
+/* Message of the last error on this context ("" if none). Owned by ctx. */
+const char* relsim_last_error(const relsim_ctx* ctx);
+
+/* Load (replace) the particles of one species: n particles, positions x[2n],
+   momenta u[3n], weights w[n], all FP64 (layout above). Positions outside
+   the box are wrapped periodically. The library converts to its internal
+   form and sorts the particles by cell (stable: equal cells keep the input
+   order). Ids (if tracked) are the input indices 0..n-1. n = 0 empties the
+   species. Errors: INVALID_ARG (species out of range, n < 0 or > 2^31-1,
+   NULL arrays with n > 0), NONFINITE (NaN/Inf in the input), OOM, CUDA.
+   Resets the step state: the next call must be relsim_build_mass_matrix. */
+int relsim_load_particles(relsim_ctx* ctx, int species, int64_t n, const double* x,
+                          const double* u, const double* w, int where);
+
+/* Set E^n on nodes and B^n on cell centres (each 3*ncell FP64, layout above).
+   Either pointer may be NULL to keep that field. Resets the step state.
+   Errors: INVALID_ARG, NONFINITE, CUDA. */
+int relsim_set_fields(relsim_ctx* ctx, const double* E, const double* B, int where);
+
+/* Copy the current E and B (after a solve: E^{n+1}, B^{n+1}) out as FP64.
+   Either pointer may be NULL. Errors: INVALID_ARG, CUDA. */
+int relsim_get_fields(relsim_ctx* ctx, double* E, double* B, int where);
+
+/* Number of particles of a species. */
+int relsim_num_particles(relsim_ctx* ctx, int species, int64_t* n);
+
+/* Copy the particles of a species out, in the library's current order
+   (sorted by cell, stable), as FP64 x[2n], u[3n], w[n] and, if ids are
+   tracked, id[n] (each pointer may be NULL to skip it). Positions are
+   absolute. Errors: INVALID_ARG (species out of range, id requested but not
+   tracked), CUDA. */
+int relsim_get_particles(relsim_ctx* ctx, int species, double* x, double* u, double* w,
+                         int32_t* id, int where);
+
+/* Start index of each cell's particles of a species in the current order:
+   start[ncell+1], start[ncell] = n. Errors: INVALID_ARG, CUDA. */
+int relsim_get_cell_start(relsim_ctx* ctx, int species, int64_t* start, int where);
+
+/* Step part 1: gather B^n, form alpha per particle, deposit Jhat and M.
+   Allowed after load/set_fields or a push. Errors: BAD_STATE, CUDA. */
+int relsim_build_mass_matrix(relsim_ctx* ctx);
+
+/* The deposited Jhat (3*ncell, component-major) and M, stored for the five
+   neighbour offsets o in {(0,0), (1,0), (-1,1), (0,1), (1,1)} as
+   M[(g*5 + k)*9 + r*3 + s] = block (r,s) of M_{g, g+o_k}; the other four
+   offsets follow from M_{g+o,g} = M_{g,g+o}. FP64 out. Either pointer may
+   be NULL. Errors: BAD_STATE (nothing built), INVALID_ARG, CUDA. */
+int relsim_get_mass_matrix(relsim_ctx* ctx, double* M, double* J, int where);
+
+/* Replace the built Jhat and M by caller values (same layouts as
+   relsim_get_mass_matrix), e.g. to drive the field solve on its own.
+   Leaves the context in the built state. Errors: INVALID_ARG, CUDA. */
+int relsim_set_mass_matrix(relsim_ctx* ctx, const double* M, const double* J, int where);
+
+/* Step part 2: GMRES solve for E^{n+theta}, then E^{n+1}, B^{n+1}.
+   *iters (may be NULL) receives the Arnoldi steps, *rel_residual (may be
+   NULL) the true relative residual. Synchronises the stream (the restart
+   loop checks convergence on the host). Errors: BAD_STATE (not built),
+   NOT_CONVERGED (gmres_maxit reached; the fields are still advanced with
+   the best iterate), NONFINITE, CUDA. */
+int relsim_field_solve(relsim_ctx* ctx, int* iters, double* rel_residual);
+
+/* E^{n+theta} of the last solve (3*ncell FP64). Errors: BAD_STATE, CUDA. */
+int relsim_get_E_theta(relsim_ctx* ctx, double* E, int where);
+
+/* Apply the implicit operator A = I + (theta dt)^2 curl_n curl_c + theta dt M
+   of the built mass matrix to v (3*ncell FP64, device or host per where),
+   writing out (same layout). Errors: BAD_STATE, INVALID_ARG, CUDA. */
+int relsim_apply_operator(relsim_ctx* ctx, const double* v, double* out, int where);
+
+/* Step part 3: push velocities and positions of every species with
+   E^{n+theta} and B^n, then sort each species by its new cells. Also
+   accumulates the particle terms of the energy ledger. Allowed after a
+   solve. Errors: BAD_STATE, CUDA. */
+int relsim_push(relsim_ctx* ctx);
+
+/* Energy ledger of the current state and of the last step (FP64 struct,
+   caller-owned). Synchronises the stream. Errors: INVALID_ARG, NONFINITE
+   (NaN/Inf in an energy), CUDA. */
+int relsim_energy_ledger(relsim_ctx* ctx, relsim_energy* out);
+
+/* One full step: build, solve, push; fills *ledger if it is non-NULL.
+   Returns the first error of its parts (NOT_CONVERGED still completes the
+   step). */
+int relsim_step(relsim_ctx* ctx, relsim_energy* ledger);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int relsim_version(void);
+
+/* ---- profiling (the paper has no counterpart; a measurement aid) ----
+   When enabled, the library records a CUDA event pair on its stream around
+   each group of kernel launches below and accumulates the elapsed device
+   time per group. Slots: */
+#define RELSIM_PROF_DEPOSIT 0      /* zero M/Jhat + the deposit kernel          */
+#define RELSIM_PROF_PUSH_COUNT 1   /* push pass 1: moves per cell + ledger sums */
+#define RELSIM_PROF_SORT_TABLES 2  /* new-cell counts, scan, move offsets      */
+#define RELSIM_PROF_PUSH_SCATTER 3 /* push pass 2: write to sorted slots       */
+#define RELSIM_PROF_GMRES_APPLY 4  /* operator applications in GMRES           */
+#define RELSIM_PROF_GMRES_ORTHO 5  /* Gram-Schmidt, norms, basis updates       */
+#define RELSIM_PROF_FIELD_UPDATE 6 /* E^{n+1}, B^{n+1}, field ledger terms     */
+#define RELSIM_PROF_RHS 7          /* right-hand side of the field equation    */
+#define RELSIM_PROF_LOAD 8         /* load conversion + radix sort + gather    */
+#define RELSIM_PROF_GENERAL_SORT 9 /* long-move push path (radix sort)         */
+#define RELSIM_PROF_NSLOTS 10
+
+typedef struct {
+    double ms[16];           /* accumulated device time per slot            */
+    int64_t groups[16];      /* timed launch groups per slot                */
+    int64_t kernels[16];     /* kernel launches per slot                    */
+} relsim_profile;
+
+/* Turn event timing on (nonzero) or off. Errors: INVALID_ARG, CUDA. */
+int relsim_profile_enable(relsim_ctx* ctx, int on);
+
+/* Read the accumulated times (synchronises the stream); reset != 0 clears
+   them afterwards. Errors: INVALID_ARG, CUDA. */
+int relsim_profile_read(relsim_ctx* ctx, relsim_profile* out, int reset);
+
+/* Total kernel launches made by this library in this process (all
+   contexts), for counting the kernels of a timed region. */
+int64_t relsim_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RELSIM_H */

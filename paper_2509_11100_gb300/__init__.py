@@ -1,0 +1,446 @@
+"""Python binding of the GB300 RelSIM hot-path library (librelsim.so).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels behind the C ABI declared in include/relsim.h. The functions keep the
+C names (relsim_init, relsim_load_particles, relsim_build_mass_matrix,
+relsim_field_solve, relsim_push, relsim_energy_ledger, ...). Arrays may be
+numpy arrays (host memory) or CUDA torch tensors (device memory); torch
+supplies device memory and the CUDA stream, nothing else.
+
+If the shared library has not been built, importing works but the first call
+raises RelsimUnavailable: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+__all__ = [
+    "RelsimError", "RelsimUnavailable", "relsim_config", "relsim_energy", "lib", "lib_path",
+    "make_config", "relsim_init", "relsim_destroy", "relsim_last_error", "relsim_load_particles",
+    "relsim_set_fields", "relsim_get_fields", "relsim_num_particles", "relsim_get_particles",
+    "relsim_get_cell_start", "relsim_build_mass_matrix", "relsim_get_mass_matrix",
+    "relsim_set_mass_matrix", "relsim_field_solve", "relsim_get_E_theta", "relsim_apply_operator",
+    "relsim_push", "relsim_energy_ledger", "relsim_step", "relsim_version", "Simulation",
+    "relsim_profile_enable", "relsim_profile_read", "relsim_kernel_launches", "PROFILE_SLOTS",
+    "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+RELSIM_OK = 0
+RELSIM_ERR_INVALID_ARG = -1
+RELSIM_ERR_BAD_STATE = -2
+RELSIM_ERR_CUDA = -3
+RELSIM_ERR_OOM = -4
+RELSIM_ERR_NOT_CONVERGED = -5
+RELSIM_ERR_NONFINITE = -6
+RELSIM_ERR_TIMEOUT = -7
+RELSIM_ERR_INTERNAL = -8
+RELSIM_HOST = 0
+RELSIM_DEVICE = 1
+
+_ERRNAMES = {-1: "INVALID_ARG", -2: "BAD_STATE", -3: "CUDA", -4: "OOM", -5: "NOT_CONVERGED",
+             -6: "NONFINITE", -7: "TIMEOUT", -8: "INTERNAL"}
+
+
+class RelsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"relsim error {code} ({_ERRNAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class RelsimUnavailable(RuntimeError):
+    pass
+
+
+class relsim_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("theta_implicit", ctypes.c_double),
+                ("precision", ctypes.c_int), ("nspecies", ctypes.c_int),
+                ("q", ctypes.c_double * 4), ("m", ctypes.c_double * 4),
+                ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
+                ("gmres_maxit", ctypes.c_int), ("track_ids", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class relsim_energy(ctypes.Structure):
+    _fields_ = [("W_E", ctypes.c_double), ("W_B", ctypes.c_double), ("K", ctypes.c_double),
+                ("total", ctypes.c_double), ("K_species", ctypes.c_double * 4),
+                ("W_E0", ctypes.c_double), ("W_B0", ctypes.c_double), ("K0", ctypes.c_double),
+                ("dW_E", ctypes.c_double), ("dW_B", ctypes.c_double), ("dK", ctypes.c_double),
+                ("work_grid", ctypes.c_double), ("work_particles", ctypes.c_double),
+                ("mismatch", ctypes.c_double), ("dissipation", ctypes.c_double),
+                ("residual", ctypes.c_double), ("gmres_iters", ctypes.c_int),
+                ("gmres_restarts", ctypes.c_int), ("gmres_relres", ctypes.c_double),
+                ("step", ctypes.c_int64), ("n_particles", ctypes.c_int64)]
+
+    def asdict(self) -> dict:
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if k == "K_species" else v
+        return d
+
+
+_P = ctypes.c_void_p
+_CTX = ctypes.c_void_p
+_SIGS = {
+    "relsim_version": (ctypes.c_int, []),
+    "relsim_init": (ctypes.c_int, [ctypes.POINTER(relsim_config), _P, ctypes.POINTER(_CTX)]),
+    "relsim_destroy": (None, [_CTX]),
+    "relsim_last_error": (ctypes.c_char_p, [_CTX]),
+    "relsim_load_particles": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int64, _P, _P, _P, ctypes.c_int]),
+    "relsim_set_fields": (ctypes.c_int, [_CTX, _P, _P, ctypes.c_int]),
+    "relsim_get_fields": (ctypes.c_int, [_CTX, _P, _P, ctypes.c_int]),
+    "relsim_num_particles": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "relsim_get_particles": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int]),
+    "relsim_get_cell_start": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
+    "relsim_build_mass_matrix": (ctypes.c_int, [_CTX]),
+    "relsim_get_mass_matrix": (ctypes.c_int, [_CTX, _P, _P, ctypes.c_int]),
+    "relsim_set_mass_matrix": (ctypes.c_int, [_CTX, _P, _P, ctypes.c_int]),
+    "relsim_field_solve": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "relsim_get_E_theta": (ctypes.c_int, [_CTX, _P, ctypes.c_int]),
+    "relsim_apply_operator": (ctypes.c_int, [_CTX, _P, _P, ctypes.c_int]),
+    "relsim_push": (ctypes.c_int, [_CTX]),
+    "relsim_energy_ledger": (ctypes.c_int, [_CTX, ctypes.POINTER(relsim_energy)]),
+    "relsim_step": (ctypes.c_int, [_CTX, ctypes.POINTER(relsim_energy)]),
+    "relsim_profile_enable": (ctypes.c_int, [_CTX, ctypes.c_int]),
+    "relsim_profile_read": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_int]),
+    "relsim_kernel_launches": (ctypes.c_int64, []),
+}
+
+PROFILE_SLOTS = ("deposit", "push_count", "sort_tables", "push_scatter", "gmres_apply",
+                 "gmres_ortho", "field_update", "rhs", "load", "general_sort")
+
+
+class relsim_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 16), ("groups", ctypes.c_int64 * 16),
+                ("kernels", ctypes.c_int64 * 16)]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return os.path.join(HERE, "librelsim.so")
+
+
+def lib():
+    """The loaded librelsim.so; raises RelsimUnavailable if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RelsimUnavailable(
+            f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(the RelSIM path has no CPU fallback)")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype=np.float64, writable=False):
+    """(pointer, where, keepalive) of a numpy array or torch tensor."""
+    if a is None:
+        return None, RELSIM_HOST, None
+    if _is_torch(a):
+        import torch
+        want = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return a.data_ptr(), (RELSIM_DEVICE if a.is_cuda else RELSIM_HOST), a
+    arr = np.asarray(a)
+    if arr.dtype != dtype or not arr.flags["C_CONTIGUOUS"] or (writable and not arr.flags["WRITEABLE"]):
+        if writable:
+            raise TypeError(f"output array must be a writable C-contiguous {np.dtype(dtype)} array")
+        arr = np.ascontiguousarray(arr, dtype=dtype)
+    return arr.ctypes.data, RELSIM_HOST, arr
+
+
+def _where(*items):
+    ws = {w for (p, w, k) in items if p is not None}
+    if len(ws) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return ws.pop() if ws else RELSIM_HOST
+
+
+def _check(ctx, code, allow=()):
+    if code != RELSIM_OK and code not in allow:
+        msg = lib().relsim_last_error(ctx)
+        raise RelsimError(code, msg.decode() if msg else "")
+    return code
+
+
+def _stream(stream=None) -> int:
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, one Python function each
+
+def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta_implicit=0.5, precision=32,
+                q=(1.0, -1.0), m=(1.0, 1.0), gmres_tol=0.0, gmres_restart=0, gmres_maxit=0,
+                track_ids=False) -> relsim_config:
+    c = relsim_config()
+    c.dim, c.nx, c.ny, c.nz = 2, nx, ny, 1
+    c.dx, c.dy, c.dz, c.dt, c.theta_implicit = dx, dy, 1.0, dt, theta_implicit
+    c.precision, c.nspecies = precision, len(q)
+    for s in range(len(q)):
+        c.q[s] = q[s]
+        c.m[s] = m[s]
+    c.gmres_tol, c.gmres_restart, c.gmres_maxit = gmres_tol, gmres_restart, gmres_maxit
+    c.track_ids = 1 if track_ids else 0
+    return c
+
+
+def relsim_version() -> int:
+    return lib().relsim_version()
+
+
+def relsim_init(cfg: relsim_config, stream=None):
+    ctx = _CTX()
+    code = lib().relsim_init(ctypes.byref(cfg), _P(_stream(stream)), ctypes.byref(ctx))
+    if code != RELSIM_OK:
+        raise RelsimError(code, "relsim_init failed (check the config)")
+    return ctx
+
+
+def relsim_destroy(ctx):
+    if ctx:
+        lib().relsim_destroy(ctx)
+
+
+def relsim_last_error(ctx) -> str:
+    m = lib().relsim_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def relsim_load_particles(ctx, species, x, u, w):
+    n = int(len(w))
+    px, pu, pw = _ptr(x), _ptr(u), _ptr(w)
+    return _check(ctx, lib().relsim_load_particles(ctx, species, n, px[0], pu[0], pw[0],
+                                                   _where(px, pu, pw)))
+
+
+def relsim_set_fields(ctx, E=None, B=None):
+    pE, pB = _ptr(E), _ptr(B)
+    return _check(ctx, lib().relsim_set_fields(ctx, pE[0], pB[0], _where(pE, pB)))
+
+
+def _out(shape, dtype, device):
+    if device:
+        import torch
+        td = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        return torch.empty(shape, dtype=td, device="cuda")
+    return np.empty(shape, dtype=dtype)
+
+
+def _ncell(ctx_cfg):
+    return ctx_cfg.nx * ctx_cfg.ny
+
+
+def relsim_get_fields(ctx, ncell, device=False):
+    E, B = _out((3, ncell), np.float64, device), _out((3, ncell), np.float64, device)
+    pE, pB = _ptr(E, writable=True), _ptr(B, writable=True)
+    _check(ctx, lib().relsim_get_fields(ctx, pE[0], pB[0], _where(pE, pB)))
+    return E, B
+
+
+def relsim_num_particles(ctx, species) -> int:
+    n = ctypes.c_int64(0)
+    _check(ctx, lib().relsim_num_particles(ctx, species, ctypes.byref(n)))
+    return n.value
+
+
+def relsim_get_particles(ctx, species, ids=False, device=False):
+    n = relsim_num_particles(ctx, species)
+    x = _out((n, 2), np.float64, device)
+    u = _out((n, 3), np.float64, device)
+    w = _out((n,), np.float64, device)
+    i = _out((n,), np.int32, device) if ids else None
+    px, pu, pw = _ptr(x, writable=True), _ptr(u, writable=True), _ptr(w, writable=True)
+    pi = _ptr(i, np.int32, writable=True) if ids else (None, RELSIM_HOST, None)
+    _check(ctx, lib().relsim_get_particles(ctx, species, px[0], pu[0], pw[0], pi[0], _where(px, pu, pw)))
+    return (x, u, w, i) if ids else (x, u, w)
+
+
+def relsim_get_cell_start(ctx, species, ncell, device=False):
+    s = _out((ncell + 1,), np.int64, device)
+    ps = _ptr(s, np.int64, writable=True)
+    _check(ctx, lib().relsim_get_cell_start(ctx, species, ps[0], ps[1]))
+    return s
+
+
+def relsim_build_mass_matrix(ctx):
+    return _check(ctx, lib().relsim_build_mass_matrix(ctx))
+
+
+def relsim_get_mass_matrix(ctx, ncell, device=False):
+    M = _out((ncell, 5, 3, 3), np.float64, device)
+    J = _out((3, ncell), np.float64, device)
+    pM, pJ = _ptr(M, writable=True), _ptr(J, writable=True)
+    _check(ctx, lib().relsim_get_mass_matrix(ctx, pM[0], pJ[0], _where(pM, pJ)))
+    return M, J
+
+
+def relsim_set_mass_matrix(ctx, M, J):
+    pM, pJ = _ptr(M), _ptr(J)
+    return _check(ctx, lib().relsim_set_mass_matrix(ctx, pM[0], pJ[0], _where(pM, pJ)))
+
+
+def relsim_field_solve(ctx):
+    """Returns (iters, rel_residual, status); status may be NOT_CONVERGED."""
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    code = _check(ctx, lib().relsim_field_solve(ctx, ctypes.byref(it), ctypes.byref(rr)),
+                  allow=(RELSIM_ERR_NOT_CONVERGED,))
+    return it.value, rr.value, code
+
+
+def relsim_get_E_theta(ctx, ncell, device=False):
+    E = _out((3, ncell), np.float64, device)
+    pE = _ptr(E, writable=True)
+    _check(ctx, lib().relsim_get_E_theta(ctx, pE[0], pE[1]))
+    return E
+
+
+def relsim_apply_operator(ctx, v, device=False):
+    pv = _ptr(v)
+    out = _out(tuple(np.shape(v)) if not _is_torch(v) else tuple(v.shape), np.float64,
+               pv[1] == RELSIM_DEVICE)
+    po = _ptr(out, writable=True)
+    _check(ctx, lib().relsim_apply_operator(ctx, pv[0], po[0], _where(pv, po)))
+    return out
+
+
+def relsim_push(ctx):
+    return _check(ctx, lib().relsim_push(ctx))
+
+
+def relsim_energy_ledger(ctx) -> dict:
+    e = relsim_energy()
+    _check(ctx, lib().relsim_energy_ledger(ctx, ctypes.byref(e)))
+    return e.asdict()
+
+
+def relsim_step(ctx, ledger=True):
+    """One full step; returns (ledger dict or None, status)."""
+    e = relsim_energy()
+    code = _check(ctx, lib().relsim_step(ctx, ctypes.byref(e) if ledger else None),
+                  allow=(RELSIM_ERR_NOT_CONVERGED,))
+    return (e.asdict() if ledger else None), code
+
+
+def relsim_profile_enable(ctx, on=True):
+    return _check(ctx, lib().relsim_profile_enable(ctx, 1 if on else 0))
+
+
+def relsim_profile_read(ctx, reset=True) -> dict:
+    """{slot name: (ms, timed groups, kernel launches)} since the last reset."""
+    p = relsim_profile()
+    _check(ctx, lib().relsim_profile_read(ctx, ctypes.byref(p), 1 if reset else 0))
+    return {name: (p.ms[k], p.groups[k], p.kernels[k]) for k, name in enumerate(PROFILE_SLOTS)}
+
+
+def relsim_kernel_launches() -> int:
+    return int(lib().relsim_kernel_launches())
+
+
+class Simulation:
+    """Owns one relsim context; methods forward to the C entry points."""
+
+    def __init__(self, cfg: relsim_config, stream=None):
+        self.cfg = cfg
+        self.ncell = cfg.nx * cfg.ny
+        self.ctx = relsim_init(cfg, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            relsim_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_species(self, s, x, u, w):
+        return relsim_load_particles(self.ctx, s, x, u, w)
+
+    def load_state(self, state: dict):
+        """Load a state dict as produced by relsim_inputs (species + E + B)."""
+        for s, sp in enumerate(state["species"]):
+            x = np.stack([np.asarray(sp["x"], np.float64), np.asarray(sp["y"], np.float64)], axis=1)
+            u = np.stack([np.asarray(sp[k], np.float64) for k in ("ux", "uy", "uz")], axis=1)
+            self.load_species(s, x, u, np.asarray(sp["w"], np.float64))
+        relsim_set_fields(self.ctx, np.asarray(state["E"], np.float64), np.asarray(state["B"], np.float64))
+
+    def set_fields(self, E=None, B=None):
+        return relsim_set_fields(self.ctx, E, B)
+
+    def fields(self, device=False):
+        return relsim_get_fields(self.ctx, self.ncell, device)
+
+    def particles(self, s, ids=False, device=False):
+        return relsim_get_particles(self.ctx, s, ids, device)
+
+    def cell_start(self, s, device=False):
+        return relsim_get_cell_start(self.ctx, s, self.ncell, device)
+
+    def build(self):
+        return relsim_build_mass_matrix(self.ctx)
+
+    def mass_matrix(self, device=False):
+        return relsim_get_mass_matrix(self.ctx, self.ncell, device)
+
+    def set_mass_matrix(self, M, J):
+        return relsim_set_mass_matrix(self.ctx, M, J)
+
+    def solve(self):
+        return relsim_field_solve(self.ctx)
+
+    def E_theta(self, device=False):
+        return relsim_get_E_theta(self.ctx, self.ncell, device)
+
+    def apply_operator(self, v):
+        return relsim_apply_operator(self.ctx, v)
+
+    def push(self):
+        return relsim_push(self.ctx)
+
+    def ledger(self):
+        return relsim_energy_ledger(self.ctx)
+
+    def step(self, ledger=True):
+        return relsim_step(self.ctx, ledger)
+
+    def profile(self, on=True):
+        return relsim_profile_enable(self.ctx, on)
+
+    def profile_read(self, reset=True):
+        return relsim_profile_read(self.ctx, reset)

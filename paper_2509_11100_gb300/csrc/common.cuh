@@ -1,0 +1,97 @@
+// common.cuh -- device-side helpers shared by the RelSIM kernels.
+//
+// Grid conventions (2D, periodic): node (i,j) at (i dx, j dy), cell (i,j)
+// spanning [i dx,(i+1) dx) x [j dy,(j+1) dy) with its centre at
+// ((i+1/2) dx, (j+1/2) dy); both have linear index j*nx + i. E, Jhat and the
+// mass matrix live on nodes, B on cell centres. Field arrays are
+// component-major: F[k*ncell + idx].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace relsim {
+
+// Number of neighbour offsets kept per node in the half-stored mass matrix:
+// o_0 = (0,0), o_1 = (1,0), o_2 = (-1,1), o_3 = (0,1), o_4 = (1,1). The other
+// four offsets follow from M_{g+o,g} = M_{g,g+o} (alpha is shared by both
+// node orderings of a pair).
+constexpr int kHalf = 5;
+constexpr int kMBlock = kHalf * 9;   // values per node
+constexpr int kNDir = 9;             // cell-to-cell moves of one step
+constexpr int kMaxSpecies = 4;
+constexpr int kMaxRestart = 100;
+
+struct GridP {
+    int nx, ny, ncell;
+    double dx, dy, dt, theta, dV;
+};
+
+__host__ __device__ __forceinline__ int wrap1(int i, int n)
+{
+    // wrap an index known to lie in [-n, 2n)
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of NS doubles; thread 0 of the block gets the totals in
+// out[]. Needs blockDim.x a multiple of 32 and <= 1024. smem: 32*NS doubles.
+template <int NS>
+__device__ __forceinline__ void block_sum(double (&v)[NS], double* smem, double (&out)[NS])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        double t = warp_sum(v[s]);
+        if (lane == 0) smem[wid * NS + s] = t;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            double t = lane < nw ? smem[lane * NS + s] : 0.0;
+            t = warp_sum(t);
+            out[s] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// round-toward-zero conversion keeps an offset in [0,1) below 1 in FP32
+template <typename T> __device__ __forceinline__ T from_double_rz(double v);
+template <> __device__ __forceinline__ float from_double_rz<float>(double v) { return __double2float_rz(v); }
+template <> __device__ __forceinline__ double from_double_rz<double>(double v) { return v; }
+
+template <typename T> struct Consts;
+template <> struct Consts<float> {
+    static __device__ __forceinline__ float one_below() { return 0.99999994f; }  // 1 - 2^-24
+};
+template <> struct Consts<double> {
+    static __device__ __forceinline__ double one_below() { return 0.99999999999999989; }  // 1 - 2^-53
+};
+
+}  // namespace relsim

@@ -1,0 +1,527 @@
+// fields.cu -- grid kernels: right-hand side and matrix-free operator of
+// the implicit field equation, the field update with the field terms of the
+// energy ledger, FP64 GMRES vector kernels, and format conversions.
+//
+// Discrete curls (2D, all three components kept, z ignorable):
+//   curl_c (node -> centre (i+1/2, j+1/2)): differences across the cell,
+//     averaged over its two edges, e.g. (d_x f) = [(f_{i+1,j} - f_{i,j}) +
+//     (f_{i+1,j+1} - f_{i,j+1})]/(2 dx);
+//   curl_n (centre -> node (i,j)): the same over the four centres around
+//     the node. curl_n is the transpose of curl_c on the periodic grid, which
+//     makes the discrete Poynting balance exact.
+#include "launch.cuh"
+
+namespace relsim {
+
+namespace {
+
+constexpr int kFieldThreads = 256;
+constexpr int kFieldLedger = 6;   // dW_E, dW_B, dissipation, W_E1, W_B1, work_grid
+
+template <typename T>
+__global__ void k_from_double(const double* __restrict__ in, T* out, int64_t n, int* bad)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        double v = in[k];
+        if (!isfinite(v)) atomicOr(bad, 1);
+        out[k] = (T)v;
+    }
+}
+
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ in, double* out, int64_t n)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = (double)in[k];
+}
+
+// b = E^n + theta dt curl_n B^n - theta dt Jhat
+template <typename T>
+__global__ void k_rhs(const T* __restrict__ E, const T* __restrict__ B, const T* __restrict__ J,
+                      double* __restrict__ b, GridP g)
+{
+    const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gidx >= g.ncell) return;
+    const int nc = g.ncell, nx = g.nx;
+    const int i = gidx % nx, j = gidx / nx;
+    const int im = wrap1(i - 1, nx), jm = wrap1(j - 1, g.ny);
+    const int c11 = j * nx + i, c01 = j * nx + im, c10 = jm * nx + i, c00 = jm * nx + im;
+    const T idx2 = T(0.5 / g.dx), idy2 = T(0.5 / g.dy);
+    const T* Bx = B;
+    const T* By = B + nc;
+    const T* Bz = B + 2 * nc;
+    const T dxBy = (By[c11] - By[c01] + By[c10] - By[c00]) * idx2;
+    const T dyBx = (Bx[c11] - Bx[c10] + Bx[c01] - Bx[c00]) * idy2;
+    const T dxBz = (Bz[c11] - Bz[c01] + Bz[c10] - Bz[c00]) * idx2;
+    const T dyBz = (Bz[c11] - Bz[c10] + Bz[c01] - Bz[c00]) * idy2;
+    const T td = T(g.theta * g.dt);
+    b[gidx] = (double)(E[gidx] + td * dyBz - td * J[gidx]);
+    b[nc + gidx] = (double)(E[nc + gidx] - td * dxBz - td * J[nc + gidx]);
+    b[2 * nc + gidx] = (double)(E[2 * nc + gidx] + td * (dxBy - dyBx) - td * J[2 * nc + gidx]);
+}
+
+// Node-local loads of a vector given in FP64 as T
+template <typename T>
+__device__ __forceinline__ T vld(const double* v, int64_t k) { return (T)__ldg(v + k); }
+
+// (curl_n curl_c v) and (M v) at node (i,j); v FP64 component-major.
+template <typename T>
+__device__ __forceinline__ void op_parts(const T* __restrict__ M, const double* __restrict__ v, int i,
+                                         int j, const GridP& g, T cc[3], T mv[3])
+{
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int xs[3] = {wrap1(i - 1, nx), i, wrap1(i + 1, nx)};
+    const int ys[3] = {wrap1(j - 1, ny) * nx, j * nx, wrap1(j + 1, ny) * nx};
+    T f[3][3][3];   // f[k][a][b]: component k at node (i-1+a, j-1+b)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) f[k][a][b] = vld<T>(v, (int64_t)k * nc + ys[b] + xs[a]);
+    const T idx2 = T(0.5 / g.dx), idy2 = T(0.5 / g.dy);
+    // curl_c at the four centres (i-1+ca+1/2, j-1+cb+1/2)
+    T C[3][2][2];
+#pragma unroll
+    for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
+            T dx[3], dy[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                dx[k] = (f[k][ca + 1][cb] - f[k][ca][cb] + f[k][ca + 1][cb + 1] - f[k][ca][cb + 1]) * idx2;
+                dy[k] = (f[k][ca][cb + 1] - f[k][ca][cb] + f[k][ca + 1][cb + 1] - f[k][ca + 1][cb]) * idy2;
+            }
+            C[0][ca][cb] = dy[2];
+            C[1][ca][cb] = -dx[2];
+            C[2][ca][cb] = dx[1] - dy[0];
+        }
+    // curl_n at the node from the four centres
+    T dx[3], dy[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dx[k] = (C[k][1][1] - C[k][0][1] + C[k][1][0] - C[k][0][0]) * idx2;
+        dy[k] = (C[k][1][1] - C[k][1][0] + C[k][0][1] - C[k][0][0]) * idy2;
+    }
+    cc[0] = dy[2];
+    cc[1] = -dx[2];
+    cc[2] = dx[1] - dy[0];
+    // M v: own blocks M[g][o] times v(g+o), neighbours' blocks M[g-o][o] times v(g-o)
+    const int64_t gi = (int64_t)ys[1] + xs[1];
+    // half offsets o_1..o_4 = (1,0), (-1,1), (0,1), (1,1): (a,b) stencil indices
+    constexpr int pa[4] = {2, 0, 1, 2}, pb[4] = {1, 2, 2, 2};   // g + o
+    constexpr int ma[4] = {0, 2, 1, 0}, mb[4] = {1, 0, 0, 0};   // g - o
+    T r[3] = {T(0), T(0), T(0)};
+    const T* Mg = M + gi * kMBlock;
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int s = 0; s < 3; ++s) r[rr] += ld(Mg + rr * 3 + s) * f[s][1][1];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const T* Mo = Mg + (o + 1) * 9;
+        const T* Mn = M + ((int64_t)ys[mb[o]] + xs[ma[o]]) * kMBlock + (o + 1) * 9;
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+                r[rr] += ld(Mo + rr * 3 + s) * f[s][pa[o]][pb[o]] + ld(Mn + rr * 3 + s) * f[s][ma[o]][mb[o]];
+    }
+    mv[0] = r[0];
+    mv[1] = r[1];
+    mv[2] = r[2];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFieldThreads)
+k_apply_A(const T* __restrict__ M, const double* __restrict__ v, double* __restrict__ out, GridP g)
+{
+    const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gidx >= g.ncell) return;
+    const int i = gidx % g.nx, j = gidx / g.nx;
+    T cc[3], mv[3];
+    op_parts<T>(M, v, i, j, g, cc, mv);
+    const T td = T(g.theta * g.dt);
+    const int nc = g.ncell;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T vk = vld<T>(v, (int64_t)k * nc + gidx);
+        out[(int64_t)k * nc + gidx] = (double)(vk + td * td * cc[k] + td * mv[k]);
+    }
+}
+
+// E^{n+theta} from the solve, E^{n+1}, B^{n+1}, and the field ledger terms.
+template <typename T>
+__global__ void __launch_bounds__(kFieldThreads)
+k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* __restrict__ J,
+               T* __restrict__ Eth, T* __restrict__ E, const T* __restrict__ B0, T* __restrict__ B1,
+               GridP g, double* __restrict__ partial)
+{
+    __shared__ double red[32 * kFieldLedger];
+    const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+    T acc[kFieldLedger] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    if (gidx < g.ncell) {
+        const int nc = g.ncell, nx = g.nx, ny = g.ny;
+        const int i = gidx % nx, j = gidx / nx;
+        const T th = T(g.theta), hdV = T(0.5 * g.dV);
+        T et[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) et[k] = vld<T>(x, (int64_t)k * nc + gidx);
+        // E update
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T e0 = E[(int64_t)k * nc + gidx];
+            const T e1 = (et[k] - (T(1) - th) * e0) / th;
+            Eth[(int64_t)k * nc + gidx] = et[k];
+            E[(int64_t)k * nc + gidx] = e1;
+            acc[0] += hdV * (e1 - e0) * (e1 + e0);
+            acc[2] += (e1 - e0) * (e1 - e0);
+            acc[3] += hdV * e1 * e1;
+        }
+        // B update of cell (i,j) from E^{n+theta} at its four nodes
+        const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+        const int64_t n00 = (int64_t)j * nx + i, n10 = (int64_t)j * nx + i1;
+        const int64_t n01 = (int64_t)j1 * nx + i, n11 = (int64_t)j1 * nx + i1;
+        const T idx2 = T(0.5 / g.dx), idy2 = T(0.5 / g.dy);
+        T dxE[3], dyE[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T a = vld<T>(x, k * nc + n00), b = vld<T>(x, k * nc + n10);
+            const T c = vld<T>(x, k * nc + n01), d = vld<T>(x, k * nc + n11);
+            dxE[k] = (b - a + d - c) * idx2;
+            dyE[k] = (c - a + d - b) * idy2;
+        }
+        const T curl[3] = {dyE[2], -dxE[2], dxE[1] - dyE[0]};
+        const T dt = T(g.dt);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T b0 = B0[(int64_t)k * nc + gidx];
+            const T b1 = b0 - dt * curl[k];
+            B1[(int64_t)k * nc + gidx] = b1;
+            acc[1] += hdV * (b1 - b0) * (b1 + b0);
+            acc[2] += (b1 - b0) * (b1 - b0);
+            acc[4] += hdV * b1 * b1;
+        }
+        acc[2] *= T((g.theta - 0.5) * g.dV);
+        // work: dt dV (Jhat + M E^{n+theta}) . E^{n+theta}
+        T cc[3], mv[3];
+        op_parts<T>(M, x, i, j, g, cc, mv);
+        T wk = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) wk += (J[(int64_t)k * nc + gidx] + mv[k]) * et[k];
+        acc[5] = T(g.dt * g.dV) * wk;
+    }
+    double v[kFieldLedger], out[kFieldLedger];
+#pragma unroll
+    for (int s = 0; s < kFieldLedger; ++s) v[s] = (double)acc[s];
+    block_sum<kFieldLedger>(v, red, out);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int s = 0; s < kFieldLedger; ++s) partial[(int64_t)blockIdx.x * kFieldLedger + s] = out[s];
+}
+
+template <typename T>
+__global__ void k_field_energy(const T* __restrict__ E, const T* __restrict__ B, GridP g,
+                               double* __restrict__ partial)
+{
+    __shared__ double red[32 * 2];
+    T we = T(0), wb = T(0);
+    const int64_t n = 3 * (int64_t)g.ncell;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        we += E[k] * E[k];
+        wb += B[k] * B[k];
+    }
+    double v[2] = {0.5 * g.dV * (double)we, 0.5 * g.dV * (double)wb}, out[2];
+    block_sum<2>(v, red, out);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x * 2] = out[0];
+        partial[blockIdx.x * 2 + 1] = out[1];
+    }
+}
+
+template <typename T>
+__global__ void k_mass_to_double(const T* __restrict__ M, const T* __restrict__ J, double* Md,
+                                 double* Jd, GridP g)
+{
+    const int64_t nm = (int64_t)g.ncell * kMBlock, nj = 3 * (int64_t)g.ncell;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nm;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (Md) Md[k] = (double)M[k];
+        if (Jd && k < nj) Jd[k] = (double)J[k];
+    }
+}
+
+template <typename T>
+__global__ void k_mass_from_double(const double* __restrict__ Md, const double* __restrict__ Jd, T* M,
+                                   T* J, GridP g, int* bad)
+{
+    const int64_t nm = (int64_t)g.ncell * kMBlock, nj = 3 * (int64_t)g.ncell;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nm;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        double a = Md[k];
+        if (!isfinite(a)) atomicOr(bad, 1);
+        M[k] = (T)a;
+        if (k < nj) {
+            double b = Jd[k];
+            if (!isfinite(b)) atomicOr(bad, 1);
+            J[k] = (T)b;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GMRES vectors (FP64)
+
+constexpr int kGmThreads = 256;
+constexpr int kDotChunk = 8;
+
+__global__ void __launch_bounds__(kGmThreads)
+k_gm_dots(const double* __restrict__ V, int64_t ldv, int k0, int kc, const double* __restrict__ w,
+          int64_t n, double* __restrict__ partial, int stride, bool with_ww)
+{
+    __shared__ double red[32 * (kDotChunk + 1)];
+    double acc[kDotChunk + 1];
+#pragma unroll
+    for (int c = 0; c <= kDotChunk; ++c) acc[c] = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double we = w[e];
+#pragma unroll
+        for (int c = 0; c < kDotChunk; ++c)
+            if (c < kc) acc[c] += V[(int64_t)(k0 + c) * ldv + e] * we;
+        if (with_ww) acc[kDotChunk] += we * we;
+    }
+    double out[kDotChunk + 1];
+    block_sum<kDotChunk + 1>(acc, red, out);
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < kc; ++c) partial[(int64_t)blockIdx.x * stride + k0 + c] = out[c];
+        if (with_ww) partial[(int64_t)blockIdx.x * stride + stride - 1] = out[kDotChunk];
+    }
+}
+
+__global__ void __launch_bounds__(kGmThreads)
+k_gm_update(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int k,
+            const double* __restrict__ h, int64_t n, double* __restrict__ partial)
+{
+    __shared__ double hs[kMaxRestart + 1];
+    __shared__ double red[32];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) hs[c] = h[c];
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = w[e];
+        for (int c = 0; c < k; ++c) s -= hs[c] * V[(int64_t)c * ldv + e];
+        w[e] = s;
+        acc += s * s;
+    }
+    double v[1] = {acc}, out[1];
+    block_sum<1>(v, red, out);
+    if (threadIdx.x == 0) partial[blockIdx.x] = out[0];
+}
+
+__global__ void k_gm_scale(double* dst, const double* __restrict__ src, double s, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[e] * s;
+}
+
+__global__ void __launch_bounds__(kGmThreads)
+k_gm_sub(double* r, const double* __restrict__ b, const double* __restrict__ Ax, int64_t n,
+         double* partial)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = b[e] - Ax[e];
+        r[e] = s;
+        acc += s * s;
+    }
+    double v[1] = {acc}, out[1];
+    block_sum<1>(v, red, out);
+    if (threadIdx.x == 0) partial[blockIdx.x] = out[0];
+}
+
+__global__ void k_gm_combine(double* x, const double* __restrict__ V, int64_t ldv, int k,
+                             const double* __restrict__ y, int64_t n)
+{
+    __shared__ double ys[kMaxRestart + 1];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = y[c];
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = x[e];
+        for (int c = 0; c < k; ++c) s += ys[c] * V[(int64_t)c * ldv + e];
+        x[e] = s;
+    }
+}
+
+// out[s] = sum_b partial[b*nsums + s], fixed order (deterministic)
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblocks, int nsums,
+                                  double* out)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += partial[(int64_t)b * nsums + s];
+    double v[1] = {acc}, o[1];
+    block_sum<1>(v, red, o);
+    if (threadIdx.x == 0) out[s] = o[0];
+}
+
+int grid_for(int64_t n, int threads, int cap)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+}  // namespace
+
+int field_grid_blocks(GridP g) { return grid_for(g.ncell, kFieldThreads, 1 << 30); }
+int gm_blocks(int64_t n) { return grid_for(n, kGmThreads, 152 * 4); }
+
+template <typename T>
+cudaError_t fields_from_double(const double* in, T* out, int64_t n, int* bad, cudaStream_t st)
+{
+    count_launches(1);
+    k_from_double<T><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(in, out, n, bad);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t fields_to_double(const T* in, double* out, int64_t n, cudaStream_t st)
+{
+    count_launches(1);
+    k_to_double<T><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStream_t st)
+{
+    count_launches(1);
+    k_rhs<T><<<grid_for(g.ncell, 256, 1 << 30), 256, 0, st>>>(E, B, J, b, g);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, cudaStream_t st)
+{
+    count_launches(1);
+    k_apply_A<T><<<grid_for(g.ncell, kFieldThreads, 1 << 30), kFieldThreads, 0, st>>>(M, v, out, g);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t field_update(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0,
+                         T* B1, GridP g, double* partial, int nblocks, cudaStream_t st)
+{
+    count_launches(1);
+    k_field_update<T><<<nblocks, kFieldThreads, 0, st>>>(x, M, J, Eth, E, B0, B1, g, partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t field_energy(const T* E, const T* B, GridP g, double* partial, int nblocks,
+                         cudaStream_t st)
+{
+    count_launches(1);
+    k_field_energy<T><<<nblocks, 256, 0, st>>>(E, B, g, partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mass_to_double(const T* M, const T* J, double* Md, double* Jd, GridP g,
+                           cudaStream_t st)
+{
+    count_launches(1);
+    k_mass_to_double<T><<<grid_for((int64_t)g.ncell * kMBlock, 256, 152 * 16), 256, 0, st>>>(M, J, Md, Jd, g);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mass_from_double(const double* Md, const double* Jd, T* M, T* J, GridP g, int* bad,
+                             cudaStream_t st)
+{
+    count_launches(1);
+    k_mass_from_double<T><<<grid_for((int64_t)g.ncell * kMBlock, 256, 152 * 16), 256, 0, st>>>(Md, Jd, M, J, g, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t gm_dots(const double* V, int64_t ldv, int k, const double* w, int64_t n,
+                    double* partial, int nblocks, cudaStream_t st)
+{
+    // partial row stride k+1: k dots then w.w
+    for (int k0 = 0; k0 < k || k0 == 0; k0 += kDotChunk) {
+        int kc = k - k0 < kDotChunk ? k - k0 : kDotChunk;
+        if (kc < 0) kc = 0;
+        count_launches(1);
+        k_gm_dots<<<nblocks, kGmThreads, 0, st>>>(V, ldv, k0, kc, w, n, partial, k + 1, k0 == 0);
+        if (k0 + kDotChunk >= k) break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t gm_update(double* w, const double* V, int64_t ldv, int k, const double* h, int64_t n,
+                      double* partial, int nblocks, cudaStream_t st)
+{
+    count_launches(1);
+    k_gm_update<<<nblocks, kGmThreads, 0, st>>>(w, V, ldv, k, h, n, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t gm_scale(double* dst, const double* src, double s, int64_t n, cudaStream_t st)
+{
+    count_launches(1);
+    k_gm_scale<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(dst, src, s, n);
+    return cudaGetLastError();
+}
+
+cudaError_t gm_sub(double* r, const double* b, const double* Ax, int64_t n, double* partial,
+                   int nblocks, cudaStream_t st)
+{
+    count_launches(1);
+    k_gm_sub<<<nblocks, kGmThreads, 0, st>>>(r, b, Ax, n, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t gm_combine(double* x, const double* V, int64_t ldv, int k, const double* y, int64_t n,
+                       cudaStream_t st)
+{
+    count_launches(1);
+    k_gm_combine<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, k, y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, double* out,
+                            cudaStream_t st)
+{
+    count_launches(1);
+    k_reduce_partials<<<nsums, 256, 0, st>>>(partial, nblocks, nsums, out);
+    return cudaGetLastError();
+}
+
+#define RELSIM_FIELDS_INSTANTIATE(T)                                                               \
+    template cudaError_t fields_from_double<T>(const double*, T*, int64_t, int*, cudaStream_t);   \
+    template cudaError_t fields_to_double<T>(const T*, double*, int64_t, cudaStream_t);           \
+    template cudaError_t rhs<T>(const T*, const T*, const T*, double*, GridP, cudaStream_t);      \
+    template cudaError_t apply_A<T>(const T*, const double*, double*, GridP, cudaStream_t);       \
+    template cudaError_t field_update<T>(const double*, const T*, const T*, T*, T*, const T*, T*, \
+                                         GridP, double*, int, cudaStream_t);                      \
+    template cudaError_t field_energy<T>(const T*, const T*, GridP, double*, int, cudaStream_t);  \
+    template cudaError_t mass_to_double<T>(const T*, const T*, double*, double*, GridP,           \
+                                           cudaStream_t);                                         \
+    template cudaError_t mass_from_double<T>(const double*, const double*, T*, T*, GridP, int*,   \
+                                             cudaStream_t);
+
+RELSIM_FIELDS_INSTANTIATE(float)
+RELSIM_FIELDS_INSTANTIATE(double)
+
+}  // namespace relsim

@@ -1,0 +1,133 @@
+// launch.cuh -- host-side launchers of the RelSIM kernels (internal).
+//
+// Every launcher enqueues on the given stream and returns the launch status
+// (cudaGetLastError); none synchronises.
+#pragma once
+
+#include "common.cuh"
+
+namespace relsim {
+
+// process-wide count of kernel launches made by this library
+void count_launches(int n);
+
+// One buffer of a species' particles in the internal form: position as cell
+// (implicit: the particles are stored sorted by cell, cell c owning
+// [start[c], start[c+1])) plus offsets fx, fy in [0,1); momenta u = gamma v;
+// weight w; optional int32 id.
+template <typename T>
+struct PArrays {
+    T* fx;
+    T* fy;
+    T* ux;
+    T* uy;
+    T* uz;
+    T* w;
+    int32_t* id;   // may be null
+};
+
+// Per-species constants of the deposit and the push.
+struct SpeciesConst {
+    double q, m;
+};
+
+template <typename T>
+struct DepositSpecies {
+    int nsp;
+    const T* fx[kMaxSpecies];
+    const T* fy[kMaxSpecies];
+    const T* ux[kMaxSpecies];
+    const T* uy[kMaxSpecies];
+    const T* uz[kMaxSpecies];
+    const T* w[kMaxSpecies];
+    const int32_t* start[kMaxSpecies];
+    T beta[kMaxSpecies];   // q dt / (2 m)
+    T cJ[kMaxSpecies];     // q / dV
+    T cM[kMaxSpecies];     // q beta / dV
+};
+
+// ----- sort.cu -----
+// exclusive scan of n int32 values (n <= 4096*16384); out may alias in;
+// *total (device) receives the sum if non-null. tmp: scan_tmp_size(n) ints.
+size_t scan_tmp_ints(int64_t n);
+cudaError_t scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total,
+                               int32_t* tmp, cudaStream_t st);
+// stable LSD radix sort of (key, val) pairs, keys in [0, 2^key_bits).
+// Ping-pongs between (k0,v0) and (k1,v1); *result_in_1 tells where it ended.
+size_t radix_tmp_ints(int64_t n);
+cudaError_t radix_sort_pairs(int32_t* k0, int32_t* v0, int32_t* k1, int32_t* v1, int64_t n,
+                             int key_bits, int32_t* tmp, bool* result_in_1, cudaStream_t st);
+// counts[k] = #keys equal to k (counts zeroed inside)
+cudaError_t histogram_keys(const int32_t* keys, int64_t n, int32_t* counts, int nkeys,
+                           cudaStream_t st);
+// new-cell counts and destination offsets of the neighbour-move sort
+cudaError_t move_counts(const int32_t* n9, int32_t* count_new, GridP g, cudaStream_t st);
+cudaError_t move_offsets(const int32_t* n9, const int32_t* start_new, int32_t* off9, GridP g,
+                         cudaStream_t st);
+cudaError_t iota_i32(int32_t* a, int64_t n, cudaStream_t st);
+
+// ----- particles.cu -----
+template <typename T>
+cudaError_t load_convert(const double* x, const double* u, const double* w, int64_t n, GridP g,
+                         PArrays<T> out, int32_t* key, int32_t* val, int* bad, cudaStream_t st);
+template <typename T>
+cudaError_t gather_particles(const int32_t* perm, PArrays<T> src, PArrays<T> dst, int64_t n,
+                             bool ids_from_perm, cudaStream_t st);
+template <typename T>
+cudaError_t export_particles(PArrays<T> p, const int32_t* start, GridP g, double* x, double* u,
+                             double* w, int32_t* id, cudaStream_t st);
+template <typename T>
+cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g, cudaStream_t st);
+// phase 0: count moves per (old cell, direction) into n9 and accumulate the
+//          particle ledger sums (K0, dK, work, mismatch, K1) into lsum;
+// phase 1: write each pushed particle to its sorted slot off9[new][dir] + rank;
+// phase 2: write pushed particles in place order to dst plus their new cell
+//          key (general sort path for moves longer than one cell).
+template <typename T>
+cudaError_t push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* n9,
+                 const int32_t* off9, int32_t* key, const T* Eth, const T* B, GridP g,
+                 SpeciesConst sc, double* lsum_partial, int lsum_blocks, int64_t npart, int* err,
+                 cudaStream_t st);
+int push_grid_blocks();
+template <typename T>
+cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, int nblocks,
+                           cudaStream_t st);
+
+// ----- fields.cu -----
+template <typename T>
+cudaError_t fields_from_double(const double* in, T* out, int64_t n, int* bad, cudaStream_t st);
+template <typename T>
+cudaError_t fields_to_double(const T* in, double* out, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStream_t st);
+template <typename T>
+cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, cudaStream_t st);
+template <typename T>
+cudaError_t field_update(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0,
+                         T* B1, GridP g, double* partial, int nblocks, cudaStream_t st);
+template <typename T>
+cudaError_t field_energy(const T* E, const T* B, GridP g, double* partial, int nblocks,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t mass_to_double(const T* M, const T* J, double* Md, double* Jd, GridP g,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t mass_from_double(const double* Md, const double* Jd, T* M, T* J, GridP g, int* bad,
+                             cudaStream_t st);
+int field_grid_blocks(GridP g);
+
+// GMRES vector kernels (FP64)
+cudaError_t gm_dots(const double* V, int64_t ldv, int k, const double* w, int64_t n,
+                    double* partial, int nblocks, cudaStream_t st);     // k dots + w.w
+cudaError_t gm_update(double* w, const double* V, int64_t ldv, int k, const double* h,
+                      int64_t n, double* partial, int nblocks, cudaStream_t st);  // w -= V h; |w|^2
+cudaError_t gm_scale(double* dst, const double* src, double s, int64_t n, cudaStream_t st);
+cudaError_t gm_sub(double* r, const double* b, const double* Ax, int64_t n, double* partial,
+                   int nblocks, cudaStream_t st);                      // r = b - Ax; |r|^2
+cudaError_t gm_combine(double* x, const double* V, int64_t ldv, int k, const double* y,
+                       int64_t n, cudaStream_t st);                    // x += V y
+cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, double* out,
+                            cudaStream_t st);
+int gm_blocks(int64_t n);
+
+}  // namespace relsim

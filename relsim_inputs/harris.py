@@ -214,8 +214,8 @@ def make_harris(cfg: HarrisConfig, dtype=np.float64) -> dict:
     x = np.minimum(x, np.nextafter((ci + 1) * cfg.dx, -np.inf))
     y = np.minimum(y, np.nextafter((cj + 1) * cfg.dy, -np.inf))
 
-    n1 = 1.0 / np.cosh((y - 0.25 * Ly) / a) ** 2
-    n2 = 1.0 / np.cosh((y - 0.75 * Ly) / a) ** 2
+    n1 = (1.0 / np.cosh((y - 0.25 * Ly) / a)) ** 2   # sech^2, no overflow far out
+    n2 = (1.0 / np.cosh((y - 0.75 * Ly) / a)) ** 2
     ntot = n1 + n2 + d["n_b"]
     w = ntot * cfg.dx * cfg.dy / ppc
     rmem = _rng(cfg.seed, 0xFF, 2).random(n)
