@@ -52,10 +52,23 @@ def rank_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def harris_config(seed=0):
+SMALL = {"nx": 512, "ny": 256, "ppc_per_species": 64, "particles": 16777216}
+
+
+def harris_config(seed=0, small=False):
     from relsim_inputs import HarrisConfig
-    return HarrisConfig(nx=1024, ny=512, ppc=64, theta_T=0.3, delta=1.0, sigma=10.0, pert=0.01,
+    nx, ny = (SMALL["nx"], SMALL["ny"]) if small else (1024, 512)
+    return HarrisConfig(nx=nx, ny=ny, ppc=64, theta_T=0.3, delta=1.0, sigma=10.0, pert=0.01,
                         dt=1.0, theta=0.5, seed=seed)
+
+
+def workload_config(small):
+    w = dict(WORKLOAD)
+    if small:
+        w.update(SMALL)
+        w["workload"] = w["workload"].replace("1024x512", "512x256").replace("67,108,864", "16,777,216")
+        w["profiling_case"] = "reduced grid for profiler captures (not the headline workload)"
+    return w
 
 
 def subsample(state, every):
@@ -176,7 +189,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    hc = harris_config(seed=rank)
+    hc = harris_config(seed=rank, small=args.workload == "small")
     t0 = time.time()
     state = make_harris(hc)
     t_gen = time.time() - t0
@@ -250,7 +263,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, parallelism=f"replicas{world}" if world > 1 else "single"),
+        "config": dict(workload_config(args.workload == "small"),
+                       parallelism=f"replicas{world}" if world > 1 else "single"),
         "roofline": roofline,
         "mover_mass_matrix": {"value": N / (mover_ms / 1e3), "unit": UNIT, "ms_per_step": mover_ms,
                               "achieved_gbs": mover_gbs, "frac": mover_gbs / peak,
@@ -404,6 +418,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["c1", "small"], default="c1",
+                    help="small: 512x256 cells for profiler captures")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
