@@ -253,6 +253,37 @@ int relsim_profile_read(relsim_ctx* ctx, relsim_profile* out, int reset);
    contexts), for counting the kernels of a timed region. */
 int64_t relsim_kernel_launches(void);
 
+/* ---- allocation-free kinetic energy (the paper has no counterpart) ----
+   For callers that cannot allocate device memory where they need this
+   number: a diagnostics hook inside a time loop whose device memory is all
+   reserved up front by its own pool, or code running where cudaMalloc /
+   cudaFree would synchronise the device or is not allowed.
+
+   *out (one device double) = sum_p w[p] m (gamma_p - 1) over n particles,
+   gamma_p = sqrt(1 + |u_p|^2), u[3n] interleaved (ux, uy, uz) and w[n] FP64
+   in device memory; the same sum the energy ledger reports per species. No
+   context is needed and nothing is allocated: the per-block partial sums
+   go to one fixed 32 KB device array inside the library, which every GPU
+   that loads the library holds until the process exits. The work is
+   enqueued on cuda_stream (0: the legacy default stream) and the call
+   returns without waiting.
+
+   The first call on a device looks up that array's device address
+   (cudaGetSymbolAddress) with the device current; make that first call
+   before any stream capture. All calls share the array and each overwrites
+   the partials it uses, so nothing needs clearing, but calls that overlap
+   on the GPU (on different streams, or from several threads) race on it and
+   must be serialised by the caller. The result is written by the second of
+   two kernels, in a fixed order, so repeated calls give identical sums.
+
+   Errors: INVALID_ARG (n < 0, NULL out, or NULL arrays with n > 0),
+   TOO_LARGE (n > RELSIM_NOALLOC_MAX_PARTICLES: split the particles and add
+   the results), CUDA (launch failure or no current device). */
+#define RELSIM_ERR_TOO_LARGE (-9)
+#define RELSIM_NOALLOC_MAX_PARTICLES 33554432   /* 4096 blocks x 8192 particles */
+int relsim_kinetic_energy_noalloc(const double* u, const double* w, int64_t n, double m,
+                                  double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,7 @@ __all__ = [
     "relsim_set_mass_matrix", "relsim_field_solve", "relsim_get_E_theta", "relsim_apply_operator",
     "relsim_push", "relsim_energy_ledger", "relsim_step", "relsim_version", "Simulation",
     "relsim_profile_enable", "relsim_profile_read", "relsim_kernel_launches", "PROFILE_SLOTS",
+    "relsim_kinetic_energy_noalloc", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
 ]
 
@@ -40,11 +41,14 @@ RELSIM_ERR_NOT_CONVERGED = -5
 RELSIM_ERR_NONFINITE = -6
 RELSIM_ERR_TIMEOUT = -7
 RELSIM_ERR_INTERNAL = -8
+RELSIM_ERR_TOO_LARGE = -9
+RELSIM_NOALLOC_MAX_PARTICLES = 33554432
 RELSIM_HOST = 0
 RELSIM_DEVICE = 1
 
 _ERRNAMES = {-1: "INVALID_ARG", -2: "BAD_STATE", -3: "CUDA", -4: "OOM", -5: "NOT_CONVERGED",
-             -6: "NONFINITE", -7: "TIMEOUT", -8: "INTERNAL"}
+             -6: "NONFINITE", -7: "TIMEOUT", -8: "INTERNAL",
+             -9: "TOO_LARGE"}
 
 
 class RelsimError(RuntimeError):
@@ -112,6 +116,7 @@ _SIGS = {
     "relsim_profile_enable": (ctypes.c_int, [_CTX, ctypes.c_int]),
     "relsim_profile_read": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_int]),
     "relsim_kernel_launches": (ctypes.c_int64, []),
+    "relsim_kinetic_energy_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
 }
 
 PROFILE_SLOTS = ("deposit", "push_count", "sort_tables", "push_scatter", "gmres_apply",
@@ -368,6 +373,18 @@ def relsim_profile_read(ctx, reset=True) -> dict:
 
 def relsim_kernel_launches() -> int:
     return int(lib().relsim_kernel_launches())
+
+
+def relsim_kinetic_energy_noalloc(u, w, m, out, stream=None) -> int:
+    """Allocation-free kinetic energy sum w m (gamma - 1) of device arrays
+    u (n, 3) and w (n,) (CUDA float64 tensors) into out (a one-element CUDA
+    float64 tensor). Returns the C status code unchanged (0 on success) so a
+    caller can see TOO_LARGE; asynchronous on the stream."""
+    pu, pw, po = _ptr(u), _ptr(w), _ptr(out, writable=True)
+    if _where(pu, pw, po) != RELSIM_DEVICE:
+        raise ValueError("relsim_kinetic_energy_noalloc takes device arrays only")
+    n = int(w.shape[0]) if _is_torch(w) else int(np.shape(w)[0])
+    return lib().relsim_kinetic_energy_noalloc(pu[0], pw[0], n, float(m), po[0], _P(_stream(stream)))
 
 
 class Simulation:
