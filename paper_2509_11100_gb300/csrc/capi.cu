@@ -277,7 +277,7 @@ int ensure_species(relsim_ctx* c, int s, int64_t n)
     }
     sp.cap = 0;
     for (int b = 0; b < 2; ++b) {
-        for (int k = 0; k < 6; ++k) TRY(dalloc(c, &sp.a[b][k], c->esz * (size_t)n));
+        for (int k = 0; k < 6; ++k) TRY(dalloc(c, &sp.a[b][k], c->esz * (size_t)(n + 8)));
         if (c->cfg.track_ids) TRY(dalloc(c, &sp.id[b], sizeof(int32_t) * (size_t)n));
     }
     sp.cap = n;
@@ -463,7 +463,7 @@ int build_impl(relsim_ctx* c)
         ds.cJ[s] = (T)(c->cfg.q[s] / c->g.dV);
         ds.cM[s] = (T)(c->cfg.q[s] * beta / c->g.dV);
     }
-    CK(deposit<T>(ds, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->st));
+    CK(deposit<T>(ds, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->dpush, c->st));
     PROF_END();
     return RELSIM_OK;
 }
@@ -620,7 +620,7 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
 template <typename T>
 int push_impl(relsim_ctx* c)
 {
-    const int nbp = push_grid_blocks();
+    const int nbp = push_grid_blocks(c->g);
     TRY(ensure_partial(c, (int64_t)nbp * 5));
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         Species& sp = c->sp[s];
@@ -680,6 +680,8 @@ int push_impl(relsim_ctx* c)
 
 int check_push(relsim_ctx* c)
 {
+    if (*c->hpush & 2)
+        return fail(c, RELSIM_ERR_TIMEOUT, "deposit: a shared-memory staging wait gave up");
     if (*c->hpush)
         return fail(c, RELSIM_ERR_INTERNAL, "particle sort: count and scatter passes disagreed");
     return RELSIM_OK;

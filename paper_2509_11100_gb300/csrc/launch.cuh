@@ -77,7 +77,8 @@ template <typename T>
 cudaError_t export_particles(PArrays<T> p, const int32_t* start, GridP g, double* x, double* u,
                              double* w, int32_t* id, cudaStream_t st);
 template <typename T>
-cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g, cudaStream_t st);
+cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g, int* err,
+                    cudaStream_t st);
 // phase 0: count moves per (old cell, direction) into n9 and accumulate the
 //          particle ledger sums (K0, dK, work, mismatch, K1) into lsum;
 // phase 1: write each pushed particle to its sorted slot off9[new][dir] + rank;
@@ -88,7 +89,7 @@ cudaError_t push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* start
                  const int32_t* off9, int32_t* key, const T* Eth, const T* B, GridP g,
                  SpeciesConst sc, double* lsum_partial, int lsum_blocks, int64_t npart, int* err,
                  cudaStream_t st);
-int push_grid_blocks();
+int push_grid_blocks(GridP g);
 template <typename T>
 cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, int nblocks,
                            cudaStream_t st);

@@ -97,27 +97,109 @@ __global__ void k_export(PArrays<T> pa, const int32_t* __restrict__ start, GridP
 // ---------------------------------------------------------------------------
 // shared per-particle arithmetic
 
-// B^n at the particle from the cell-centre lattice. The centre lattice
-// coordinate is i + fx - 1/2: the two centres are (i-1, i) when fx < 1/2 and
-// (i, i+1) otherwise.
-template <typename T>
-__device__ __forceinline__ void gather_B(const T* __restrict__ B, int nc, int nx, int i, int im,
-                                         int ip, int jr, int jmr, int jpr, T fx, T fy, T& Bx, T& By,
-                                         T& Bz)
+// Work units of both particle passes: row segments of up to kUnitW
+// consecutive cells (same row j, columns i0 .. i0+cn-1), so a unit's
+// particles are one contiguous range of the sorted arrays and its fields fit
+// a small shared-memory tile.
+constexpr int kUnitW = 32;
+constexpr int kTB = kUnitW + 2;   // centre columns i0-1 .. i0+cn
+constexpr int kTE = kUnitW + 1;   // node columns i0 .. i0+cn
+
+struct Unit {
+    int j, i0, cn, c0;
+};
+
+__device__ __forceinline__ Unit unit_of(int u, int nx)
 {
-    // jr, jmr, jpr are row offsets j*nx, (j-1)*nx, (j+1)*nx (wrapped)
+    const int nseg = (nx + kUnitW - 1) / kUnitW;
+    Unit r;
+    r.j = u / nseg;
+    r.i0 = (u - r.j * nseg) * kUnitW;
+    r.cn = min(kUnitW, nx - r.i0);
+    r.c0 = r.j * nx + r.i0;
+    return r;
+}
+
+__host__ __device__ __forceinline__ int units_of(int nx, int ny) { return ny * ((nx + kUnitW - 1) / kUnitW); }
+
+// B^n on the centres around a unit: [comp][row j-1, j, j+1][col i0-1 .. i0+cn]
+template <typename T>
+__device__ __forceinline__ void load_tile_B(T (*sB)[3][kTB], const T* __restrict__ B, const Unit& un, int nx,
+                                            int ny, int nc, int tid, int nthr)
+{
+    for (int idx = tid; idx < 9 * kTB; idx += nthr) {
+        const int comp = idx / (3 * kTB), r = (idx / kTB) % 3, col = idx % kTB;
+        if (col > un.cn + 1) continue;
+        const int gi = wrap1(un.i0 - 1 + col, nx), gj = wrap1(un.j - 1 + r, ny);
+        sB[comp][r][col] = ld(B + comp * nc + gj * nx + gi);
+    }
+}
+
+// E^{n+theta} on the nodes of a unit: [comp][row j, j+1][col i0 .. i0+cn]
+template <typename T>
+__device__ __forceinline__ void load_tile_E(T (*sE)[2][kTE], const T* __restrict__ E, const Unit& un, int nx,
+                                            int ny, int nc, int tid, int nthr)
+{
+    for (int idx = tid; idx < 6 * kTE; idx += nthr) {
+        const int comp = idx / (2 * kTE), r = (idx / kTE) % 2, col = idx % kTE;
+        if (col > un.cn) continue;
+        const int gi = wrap1(un.i0 + col, nx), gj = wrap1(un.j + r, ny);
+        sE[comp][r][col] = ld(E + comp * nc + gj * nx + gi);
+    }
+}
+
+// B at a particle of local cell l: the centre lattice coordinate is
+// i + fx - 1/2, so the two centres are (i-1, i) when fx < 1/2, else (i, i+1)
+template <typename T>
+__device__ __forceinline__ void tile_B(const T (*sB)[3][kTB], int l, T fx, T fy, T& Bx, T& By, T& Bz)
+{
     const bool lx = fx < T(0.5), ly = fy < T(0.5);
     const T tx = lx ? fx + T(0.5) : fx - T(0.5);
     const T ty = ly ? fy + T(0.5) : fy - T(0.5);
-    const int c0x = lx ? im : i, c1x = lx ? i : ip;
-    const int r0 = ly ? jmr : jr, r1 = ly ? jr : jpr;
+    const int c0 = lx ? l : l + 1;
+    const int r0 = ly ? 0 : 1;
     const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
     const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
-    const int a = r0 + c0x, b = r0 + c1x, c = r1 + c0x, d = r1 + c1x;
-    Bx = w00 * ld(B + a) + w10 * ld(B + b) + w01 * ld(B + c) + w11 * ld(B + d);
-    By = w00 * ld(B + nc + a) + w10 * ld(B + nc + b) + w01 * ld(B + nc + c) + w11 * ld(B + nc + d);
-    Bz = w00 * ld(B + 2 * nc + a) + w10 * ld(B + 2 * nc + b) + w01 * ld(B + 2 * nc + c) +
-         w11 * ld(B + 2 * nc + d);
+    Bx = w00 * sB[0][r0][c0] + w10 * sB[0][r0][c0 + 1] + w01 * sB[0][r0 + 1][c0] + w11 * sB[0][r0 + 1][c0 + 1];
+    By = w00 * sB[1][r0][c0] + w10 * sB[1][r0][c0 + 1] + w01 * sB[1][r0 + 1][c0] + w11 * sB[1][r0 + 1][c0 + 1];
+    Bz = w00 * sB[2][r0][c0] + w10 * sB[2][r0][c0 + 1] + w01 * sB[2][r0 + 1][c0] + w11 * sB[2][r0 + 1][c0 + 1];
+}
+
+// E at a particle of local cell l from the four nodes of the cell
+template <typename T>
+__device__ __forceinline__ void tile_E(const T (*sE)[2][kTE], int l, T W0, T W1, T W2, T W3, T& Ex, T& Ey,
+                                       T& Ez)
+{
+    Ex = W0 * sE[0][0][l] + W1 * sE[0][0][l + 1] + W2 * sE[0][1][l] + W3 * sE[0][1][l + 1];
+    Ey = W0 * sE[1][0][l] + W1 * sE[1][0][l + 1] + W2 * sE[1][1][l] + W3 * sE[1][1][l + 1];
+    Ez = W0 * sE[2][0][l] + W1 * sE[2][0][l + 1] + W2 * sE[2][1][l] + W3 * sE[2][1][l + 1];
+}
+
+// reciprocal square root and reciprocal: the hardware approximations in the
+// FP32 form (a few ulp), exact operations in the FP64 form
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+
+// The rotation of one particle, shared by the deposit and the push so both
+// see the same alpha: 1/gbar, a = beta B/gbar and 1/(1 + |a|^2).
+template <typename T>
+struct Rot {
+    T ig, ax, ay, az, sa;
+};
+
+template <typename T>
+__device__ __forceinline__ Rot<T> rotation(T u2, T Bx, T By, T Bz, T beta)
+{
+    Rot<T> r;
+    r.ig = rsqrt_t(T(1) + u2);
+    const T bg = beta * r.ig;
+    r.ax = bg * Bx;
+    r.ay = bg * By;
+    r.az = bg * Bz;
+    r.sa = rcp_t(T(1) + r.ax * r.ax + r.ay * r.ay + r.az * r.az);
+    return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -128,289 +210,508 @@ __device__ __forceinline__ void gather_B(const T* __restrict__ B, int nc, int nx
 // XX = ((1-fx)^2, (1-fx) fx, fx^2), YY likewise in y, alpha' = alpha (1+|a|^2)
 // and c_p = w q beta /(gbar dV (1+|a|^2)). The ten node pairs of a cell take
 // nine distinct weight products; (n00,n11) and (n10,n01) share k = 4.
+//
+// A CTA handles units (row segments of up to 32 cells, one contiguous
+// particle range per species). Each (unit, species) stage is copied into
+// shared memory by TMA bulk copies (cp.async.bulk, completion on an
+// mbarrier), two stages in flight, so two CTAs fit on an SM; the groups read
+// their cell's particles and the unit's B tile from shared memory. A stage
+// larger than the buffer is read from global memory instead.
 
-template <typename T, int G>
-__global__ void __launch_bounds__(256)
-k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* __restrict__ J,
-          GridP g)
+constexpr int kDepThreads = 256;
+constexpr int kDepG = 8;                               // lanes per cell
+constexpr int kDepCells = kDepThreads / kDepG;         // = kUnitW cells per unit
+constexpr int kDepCap = 2176;                          // particles per staged array
+constexpr int kDepBuf = 2;                             // stages in flight
+constexpr long long kDepMaxPolls = 1ll << 26;          // bounded mbarrier wait
+static_assert(kDepCells == kUnitW, "one group of lanes per cell of a unit");
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
 {
-    constexpr int GPW = 32 / G;   // groups per warp
-    const int lane = threadIdx.x & 31;
-    const int gl = lane % G;      // lane within group
-    const int gw = lane / G;      // group within warp
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    return (unsigned)__cvta_generic_to_shared(p);
+}
 
-    for (int cb = warp * GPW; cb < nc; cb += nwarps * GPW) {
-        const int c = cb + gw;
-        const bool valid = c < nc;
-        T S[81];
-        T Jm[12];
+__device__ __forceinline__ void mbar_init(uint64_t* mb, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx_arrive(uint64_t* mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* mb)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mb))
+        : "memory");
+}
+
+// bounded wait on the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity)
+{
+    const unsigned a = smem_u32(mb);
+    for (long long it = 0; it < kDepMaxPolls; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Register accumulators of one lane: 81 moments S[k][e] and 12 currents.
+// The FP32 form packs pairs of alpha' entries so the moment update is 45
+// paired FMAs (__ffma2_rn) instead of 81.
+template <typename T>
+struct Moments {
+    T S[81];
+    T Jm[12];
+    __device__ __forceinline__ void zero()
+    {
 #pragma unroll
-        for (int k = 0; k < 81; ++k) S[k] = T(0);
+        for (int q = 0; q < 81; ++q) S[q] = T(0);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) Jm[k] = T(0);
-        int i = 0, j = 0;
+        for (int q = 0; q < 12; ++q) Jm[q] = T(0);
+    }
+    __device__ __forceinline__ void add(const T (&t)[9], const T (&e)[9])
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) S[k * 9 + q] += t[k] * e[q];
+    }
+    __device__ __forceinline__ T get(int k, int q) const { return S[k * 9 + q]; }
+    template <int G>
+    __device__ __forceinline__ void group_reduce()
+    {
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 81; ++q) S[q] += __shfl_xor_sync(0xffffffffu, S[q], o);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) Jm[q] += __shfl_xor_sync(0xffffffffu, Jm[q], o);
+        }
+    }
+};
+
+template <>
+struct Moments<float> {
+    float2 S2[45];   // S2[k*5 + h] = (S[k][2h], S[k][2h+1]); S[k][9] is padding
+    float Jm[12];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int q = 0; q < 45; ++q) S2[q] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) Jm[q] = 0.f;
+    }
+    __device__ __forceinline__ void add(const float (&t)[9], const float (&e)[9])
+    {
+        const float2 e2[5] = {make_float2(e[0], e[1]), make_float2(e[2], e[3]), make_float2(e[4], e[5]),
+                              make_float2(e[6], e[7]), make_float2(e[8], 0.f)};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float2 tk = make_float2(t[k], t[k]);
+#pragma unroll
+            for (int h = 0; h < 5; ++h) S2[k * 5 + h] = __ffma2_rn(tk, e2[h], S2[k * 5 + h]);
+        }
+    }
+    __device__ __forceinline__ float get(int k, int q) const
+    {
+        return (q & 1) ? S2[k * 5 + q / 2].y : S2[k * 5 + q / 2].x;
+    }
+    template <int G>
+    __device__ __forceinline__ void group_reduce()
+    {
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 45; ++q) {
+                S2[q].x += __shfl_xor_sync(0xffffffffu, S2[q].x, o);
+                if (q % 5 != 4) S2[q].y += __shfl_xor_sync(0xffffffffu, S2[q].y, o);
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) Jm[q] += __shfl_xor_sync(0xffffffffu, Jm[q], o);
+        }
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void deposit_particle(const T fx, const T fy, const T ux, const T uy, const T uz,
+                                                 const T w, const T (*sB)[3][kTB], int l, T beta, T cJ, T cM,
+                                                 Moments<T>& acc)
+{
+    T Bx, By, Bz;
+    tile_B(sB, l, fx, fy, Bx, By, Bz);
+    const Rot<T> r = rotation<T>(ux * ux + uy * uy + uz * uz, Bx, By, Bz, beta);
+    const T ax = r.ax, ay = r.ay, az = r.az;
+    T e[9];
+    e[0] = T(1) + ax * ax; e[1] = ax * ay + az;   e[2] = ax * az - ay;
+    e[3] = ax * ay - az;   e[4] = T(1) + ay * ay; e[5] = ay * az + ax;
+    e[6] = ax * az + ay;   e[7] = ay * az - ax;   e[8] = T(1) + az * az;
+    // predicted current: w q alpha u / gbar / dV at the 4 nodes
+    const T cj = w * cJ * r.sa * r.ig;
+    const T vx = cj * (e[0] * ux + e[1] * uy + e[2] * uz);
+    const T vy = cj * (e[3] * ux + e[4] * uy + e[5] * uz);
+    const T vz = cj * (e[6] * ux + e[7] * uy + e[8] * uz);
+    const T X0 = T(1) - fx, X1 = fx, Y0 = T(1) - fy, Y1 = fy;
+    const T W[4] = {X0 * Y0, X1 * Y0, X0 * Y1, X1 * Y1};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        acc.Jm[a * 3 + 0] += W[a] * vx;
+        acc.Jm[a * 3 + 1] += W[a] * vy;
+        acc.Jm[a * 3 + 2] += W[a] * vz;
+    }
+    const T cm = w * cM * r.sa * r.ig;
+    const T xx[3] = {cm * X0 * X0, cm * X0 * X1, cm * X1 * X1};
+    const T yy[3] = {Y0 * Y0, Y0 * Y1, Y1 * Y1};
+    T t[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) t[a * 3 + b] = xx[a] * yy[b];
+    acc.add(t, e);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDepThreads, sizeof(T) == 4 ? 2 : 1)
+k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* __restrict__ J, GridP g,
+          int* __restrict__ err)
+{
+    constexpr int G = kDepG;
+    constexpr int NB = kDepBuf;
+    constexpr int A = 16 / sizeof(T);   // elements per 16 bytes (TMA granule)
+    extern __shared__ __align__(128) unsigned char dsmem[];
+    __shared__ uint64_t mbar[NB];
+    __shared__ int sp0a[NB];      // aligned first particle of the staged range
+    __shared__ int sstaged[NB];   // 1 if staged in shared memory, 0 if read from global
+    __shared__ T sB[3][3][kTB];
+    T* buf = reinterpret_cast<T*>(dsmem);
+    const int tid = threadIdx.x;
+    const int gl = tid % G, grp = tid / G;
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int nsp = sp.nsp;
+    const int nunits = units_of(nx, ny);
+    const int myunits = blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int nstages = myunits * nsp;
+
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) mbar_init(&mbar[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // thread 0: start the copies of stage k into buffer k % NB
+    auto issue = [&](int k) {
+        if (k >= nstages) return;
+        const int b = k % NB;
+        const Unit un = unit_of(blockIdx.x + (k / nsp) * gridDim.x, nx);
+        const int s = k % nsp;
+        const int p0 = sp.start[s][un.c0], p1 = sp.start[s][un.c0 + un.cn];
+        const int p0a = p0 & ~(A - 1);
+        const int p1a = (p1 + A - 1) & ~(A - 1);
+        const int cnt = p1a - p0a;
+        sp0a[b] = p0a;
+        if (p1 > p0 && cnt <= kDepCap) {
+            sstaged[b] = 1;
+            const unsigned bytes = (unsigned)(cnt * sizeof(T));
+            mbar_expect_tx_arrive(&mbar[b], 6 * bytes);
+            T* dst = buf + (size_t)b * 6 * kDepCap;
+            const T* srcs[6] = {sp.fx[s], sp.fy[s], sp.ux[s], sp.uy[s], sp.uz[s], sp.w[s]};
+#pragma unroll
+            for (int a = 0; a < 6; ++a) bulk_g2s(dst + a * kDepCap, srcs[a] + p0a, bytes, &mbar[b]);
+        } else {
+            sstaged[b] = 0;
+            mbar_expect_tx_arrive(&mbar[b], 0);
+        }
+    };
+
+    if (tid == 0)
+        for (int k = 0; k < NB - 1; ++k) issue(k);
+
+    Moments<T> acc;
+    int kfail = -1;
+    for (int k = 0; k < nstages; ++k) {
+        if (tid == 0) issue(k + NB - 1);
+        const int b = k % NB;
+        const Unit un = unit_of(blockIdx.x + (k / nsp) * gridDim.x, nx);
+        const int s = k % nsp;
+        if (s == 0) {
+            acc.zero();
+            load_tile_B<T>(sB, B, un, nx, ny, nc, tid, kDepThreads);
+        }
+        const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1));
+        // leave together if any thread gave up (never diverge at a barrier);
+        // the barrier also publishes the B tile
+        if (__syncthreads_or(!ok)) {
+            kfail = k;
+            break;
+        }
+        const bool valid = grp < un.cn;
+        const int c = un.c0 + grp;
         if (valid) {
-            i = c % nx;
-            j = c / nx;
-            const int im = wrap1(i - 1, nx), ip = wrap1(i + 1, nx);
-            const int jr = j * nx, jmr = wrap1(j - 1, ny) * nx, jpr = wrap1(j + 1, ny) * nx;
-            for (int s = 0; s < sp.nsp; ++s) {
-                const int p0 = sp.start[s][c], p1 = sp.start[s][c + 1];
-                const T beta = sp.beta[s], cJ = sp.cJ[s], cM = sp.cM[s];
-                const T* __restrict__ pfx = sp.fx[s];
-                const T* __restrict__ pfy = sp.fy[s];
-                const T* __restrict__ pux = sp.ux[s];
-                const T* __restrict__ puy = sp.uy[s];
-                const T* __restrict__ puz = sp.uz[s];
-                const T* __restrict__ pw = sp.w[s];
-                for (int p = p0 + gl; p < p1; p += G) {
-                    const T fx = ld(pfx + p), fy = ld(pfy + p);
-                    const T ux = ld(pux + p), uy = ld(puy + p), uz = ld(puz + p);
-                    const T w = ld(pw + p);
-                    T Bx, By, Bz;
-                    gather_B(B, nc, nx, i, im, ip, jr, jmr, jpr, fx, fy, Bx, By, Bz);
-                    const T u2 = ux * ux + uy * uy + uz * uz;
-                    const T ig = T(1) / sqrt(T(1) + u2);
-                    const T bg = beta * ig;
-                    const T ax = bg * Bx, ay = bg * By, az = bg * Bz;
-                    const T sa = T(1) / (T(1) + ax * ax + ay * ay + az * az);
-                    T e[9];
-                    e[0] = T(1) + ax * ax; e[1] = ax * ay + az;   e[2] = ax * az - ay;
-                    e[3] = ax * ay - az;   e[4] = T(1) + ay * ay; e[5] = ay * az + ax;
-                    e[6] = ax * az + ay;   e[7] = ay * az - ax;   e[8] = T(1) + az * az;
-                    // predicted current: w q alpha u / gbar / dV at the 4 nodes
-                    const T cj = w * cJ * sa * ig;
-                    const T vx = cj * (e[0] * ux + e[1] * uy + e[2] * uz);
-                    const T vy = cj * (e[3] * ux + e[4] * uy + e[5] * uz);
-                    const T vz = cj * (e[6] * ux + e[7] * uy + e[8] * uz);
-                    const T X0 = T(1) - fx, X1 = fx, Y0 = T(1) - fy, Y1 = fy;
-                    const T W[4] = {X0 * Y0, X1 * Y0, X0 * Y1, X1 * Y1};
+            const int p0 = sp.start[s][c], p1 = sp.start[s][c + 1];
+            const T beta = sp.beta[s], cJ = sp.cJ[s], cM = sp.cM[s];
+            if (sstaged[b]) {
+                const T* sb = buf + (size_t)b * 6 * kDepCap - sp0a[b];
+                for (int p = p0 + gl; p < p1; p += G)
+                    deposit_particle<T>(sb[p], sb[kDepCap + p], sb[2 * kDepCap + p], sb[3 * kDepCap + p],
+                                        sb[4 * kDepCap + p], sb[5 * kDepCap + p], sB, grp, beta, cJ, cM, acc);
+            } else {
+                for (int p = p0 + gl; p < p1; p += G)
+                    deposit_particle<T>(ld(sp.fx[s] + p), ld(sp.fy[s] + p), ld(sp.ux[s] + p),
+                                        ld(sp.uy[s] + p), ld(sp.uz[s] + p), ld(sp.w[s] + p), sB, grp, beta,
+                                        cJ, cM, acc);
+            }
+        }
+        if (s == nsp - 1) {
+            acc.template group_reduce<G>();
+            if (valid) {
+                const int i = un.i0 + grp, j = un.j;
+                const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+                const int n00 = j * nx + i, n10 = j * nx + i1, n01 = j1 * nx + i, n11 = j1 * nx + i1;
+                // (destination node, half offset, moment k) of the ten node pairs
+                const int pn[10] = {n00, n00, n00, n00, n10, n10, n10, n01, n01, n11};
+                constexpr int po[10] = {0, 1, 3, 4, 0, 2, 3, 0, 1, 0};
+                constexpr int pk[10] = {0, 3, 1, 4, 6, 4, 7, 2, 5, 8};
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        Jm[a * 3 + 0] += W[a] * vx;
-                        Jm[a * 3 + 1] += W[a] * vy;
-                        Jm[a * 3 + 2] += W[a] * vz;
+                for (int it = 0; it < 90; ++it) {
+                    if (it % G == gl) {
+                        const int pr = it / 9, q = it % 9;
+                        atomicAdd(M + (int64_t)pn[pr] * kMBlock + po[pr] * 9 + q, acc.get(pk[pr], q));
                     }
-                    const T cm = w * cM * sa * ig;
-                    const T xx[3] = {cm * X0 * X0, cm * X0 * X1, cm * X1 * X1};
-                    const T yy[3] = {Y0 * Y0, Y0 * Y1, Y1 * Y1};
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) {
-                            const T t = xx[a] * yy[b];
-#pragma unroll
-                            for (int q = 0; q < 9; ++q) S[(a * 3 + b) * 9 + q] += t * e[q];
-                        }
                 }
+                const int jn[4] = {n00, n10, n01, n11};
+#pragma unroll
+                for (int it = 0; it < 12; ++it)
+                    if ((90 + it) % G == gl) atomicAdd(J + (int64_t)(it % 3) * nc + jn[it / 3], acc.Jm[it]);
             }
         }
-        // reduce across the G lanes of the group
-        if (G > 1) {
-#pragma unroll
-            for (int o = G / 2; o >= 1; o >>= 1) {
-#pragma unroll
-                for (int k = 0; k < 81; ++k) S[k] += __shfl_xor_sync(0xffffffffu, S[k], o);
-#pragma unroll
-                for (int k = 0; k < 12; ++k) Jm[k] += __shfl_xor_sync(0xffffffffu, Jm[k], o);
-            }
-        }
-        if (!valid) continue;
-        const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
-        const int n00 = j * nx + i, n10 = j * nx + i1, n01 = j1 * nx + i, n11 = j1 * nx + i1;
-        // (destination node, half offset, moment k) of the ten node pairs
-        const int pn[10] = {n00, n00, n00, n00, n10, n10, n10, n01, n01, n11};
-        constexpr int po[10] = {0, 1, 3, 4, 0, 2, 3, 0, 1, 0};
-        constexpr int pk[10] = {0, 3, 1, 4, 6, 4, 7, 2, 5, 8};
-#pragma unroll
-        for (int it = 0; it < 90; ++it) {
-            if (it % G == gl) {
-                const int pr = it / 9, q = it % 9;
-                atomicAdd(M + (int64_t)pn[pr] * kMBlock + po[pr] * 9 + q, S[pk[pr] * 9 + q]);
-            }
-        }
-        const int jn[4] = {n00, n10, n01, n11};
-#pragma unroll
-        for (int it = 0; it < 12; ++it) {
-            if ((90 + it) % G == gl) atomicAdd(J + (int64_t)(it % 3) * nc + jn[it / 3], Jm[it]);
-        }
+        __syncthreads();   // buffer b and the B tile are free for the next stage
+    }
+    if (kfail >= 0 && tid == 0) {
+        atomicOr(err, 2);
+        // let the copies already issued land before the CTA leaves (bounded)
+        for (int kk = kfail; kk < nstages && kk < kfail + NB; ++kk) mbar_wait(&mbar[kk % NB], (kk / NB) & 1);
     }
 }
 
 // ---------------------------------------------------------------------------
-// push. One warp per (cell, species); the lanes walk the cell's particles in
-// order, so ranks within a (cell, direction) group follow the old order.
+// push. A warp owns a unit (a row segment of up to 32 cells), whose particles
+// are one contiguous range of the sorted arrays; its lanes stream that range
+// in order, kPushUnroll batches of 32 at a time (coalesced, independent
+// loads), follow the cell of each particle from a shared copy of the unit's
+// cell starts, and gather E^{n+theta} and B^n from the unit's shared field
+// tile. Counts and ranks per (old cell, direction) are warp-aggregated in
+// shared memory in particle order, so ranks follow the old order (the stable
+// sort).
 
 constexpr int kPushThreads = 256;
+constexpr int kPushWarps = kPushThreads / 32;
+constexpr int kPushUnroll = 2;
 constexpr int kLedger = 5;   // K0, dK, work, mismatch, K1
+
+template <typename T>
+struct Pushed {
+    T fxn, fyn, u1x, u1y, u1z, w;
+    int sx, sy, dir;
+};
+
+// the explicit push of one particle: E^{n+theta}, B^n gathered at x^{n+1/2},
+// ubar = alpha (u + beta E), u1 = 2 ubar - u, x += dt u1/gamma1; ledger sums
+template <typename T>
+__device__ __forceinline__ void push_particle(const T fx, const T fy, const T ux, const T uy, const T uz,
+                                              const T w, int l, const T (*sE)[2][kTE],
+                                              const T (*sB)[3][kTB], T beta, T dt_dx, T dt_dy, T qdt, T m,
+                                              bool clamp, bool ledger, T (&acc)[kLedger], Pushed<T>& o)
+{
+    T Bx, By, Bz, Ex, Ey, Ez;
+    tile_B(sB, l, fx, fy, Bx, By, Bz);
+    const T X0 = T(1) - fx, Y0 = T(1) - fy;
+    tile_E(sE, l, X0 * Y0, fx * Y0, X0 * fy, fx * fy, Ex, Ey, Ez);
+    const T u02 = ux * ux + uy * uy + uz * uz;
+    const Rot<T> r = rotation<T>(u02, Bx, By, Bz, beta);
+    const T ax = r.ax, ay = r.ay, az = r.az, sa = r.sa;
+    // ubar = alpha w = (w + w x a + (w.a) a)/(1 + |a|^2), w = u + beta E
+    const T wx = ux + beta * Ex, wy = uy + beta * Ey, wz = uz + beta * Ez;
+    const T wa = wx * ax + wy * ay + wz * az;
+    const T ubx = sa * (wx + (wy * az - wz * ay) + wa * ax);
+    const T uby = sa * (wy + (wz * ax - wx * az) + wa * ay);
+    const T ubz = sa * (wz + (wx * ay - wy * ax) + wa * az);
+    o.u1x = T(2) * ubx - ux;
+    o.u1y = T(2) * uby - uy;
+    o.u1z = T(2) * ubz - uz;
+    o.w = w;
+    const T u12 = o.u1x * o.u1x + o.u1y * o.u1y + o.u1z * o.u1z;
+    const T ig1 = rsqrt_t(T(1) + u12);
+    // x^{n+3/2} = x^{n+1/2} + dt u^{n+1}/gamma^{n+1}, as cell shift + offset
+    const T tx = fx + dt_dx * (o.u1x * ig1);
+    const T ty = fy + dt_dy * (o.u1y * ig1);
+    const T flx = floor(tx), fly = floor(ty);
+    int sx = (int)flx, sy = (int)fly;
+    T fxn = tx - flx, fyn = ty - fly;
+    if (fxn >= T(1)) { fxn -= T(1); sx += 1; }
+    if (fyn >= T(1)) { fyn -= T(1); sy += 1; }
+    if (clamp) {
+        // with c dt <= dx a move of more than one cell can only come from
+        // rounding at |v| = c; keep the particle on the last representable
+        // point of the neighbour cell
+        if (sx > 1) { sx = 1; fxn = Consts<T>::one_below(); }
+        if (sx < -1) { sx = -1; fxn = T(0); }
+        if (sy > 1) { sy = 1; fyn = Consts<T>::one_below(); }
+        if (sy < -1) { sy = -1; fyn = T(0); }
+    }
+    o.fxn = fxn;
+    o.fyn = fyn;
+    o.sx = sx;
+    o.sy = sy;
+    o.dir = (sy + 1) * 3 + (sx + 1);
+    if (ledger) {
+        const T g0 = (T(1) + u02) * r.ig, g1 = (T(1) + u12) * ig1;
+        const T ue = ubx * Ex + uby * Ey + ubz * Ez;
+        // g0 - g1 = (u0 - u1).(u0 + u1)/(g0 + g1)
+        const T du = (ux - o.u1x) * (ux + o.u1x) + (uy - o.u1y) * (uy + o.u1y) +
+                     (uz - o.u1z) * (uz + o.u1z);
+        const T igs = rcp_t(g0 + g1);
+        acc[0] += w * m * u02 * rcp_t(g0 + T(1));            // K0
+        acc[1] -= w * m * du * igs;                          // dK
+        acc[2] += qdt * w * ue * r.ig;                       // work
+        acc[3] += qdt * w * ue * du * igs * igs * r.ig;      // mismatch
+        acc[4] += w * m * u12 * rcp_t(g1 + T(1));            // K1
+    }
+}
+
+template <typename T>
+struct PushTile {
+    T B[3][3][kTB];
+    T E[3][2][kTE];
+};
 
 template <typename T>
 __global__ void __launch_bounds__(kPushThreads)
 k_push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start,
        int32_t* __restrict__ n9, const int32_t* __restrict__ off9, int32_t* __restrict__ key,
        const T* __restrict__ Eth, const T* __restrict__ B, GridP g, T beta, T dt_dx, T dt_dy,
-       T qw_dt, T m, double* __restrict__ lsum, int npart, int* __restrict__ err)
+       T qdt, T m, double* __restrict__ lsum, int npart, int* __restrict__ err)
 {
-    __shared__ int rankbase[kPushThreads / 32][kNDir];
+    __shared__ int sstart[kPushWarps][kUnitW + 1];
+    __shared__ int scnt[kPushWarps][kUnitW * kNDir];
+    __shared__ PushTile<T> stile[kPushWarps];
     __shared__ double red[32 * kLedger];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int nunits = units_of(nx, ny);
     const unsigned lt = (1u << lane) - 1u;
+    int* ss = sstart[wib];
+    int* sc = scnt[wib];
+    PushTile<T>& tl = stile[wib];
     T acc[kLedger] = {T(0), T(0), T(0), T(0), T(0)};
 
-    for (int c = warp; c < nc; c += nwarps) {
-        const int i = c % nx, j = c / nx;
-        const int im = wrap1(i - 1, nx), ip = wrap1(i + 1, nx);
-        const int jr = j * nx, jmr = wrap1(j - 1, ny) * nx, jpr = wrap1(j + 1, ny) * nx;
-        // E^{n+theta} at the four nodes of the cell
-        const int n00 = jr + i, n10 = jr + ip, n01 = jpr + i, n11 = jpr + ip;
-        T En[3][4];
+    for (int u = warp; u < nunits; u += nwarps) {
+        const Unit un = unit_of(u, nx);
+        const int cn = un.cn, c0 = un.c0;
+        for (int k = lane; k <= cn; k += 32) ss[k] = start[c0 + k];
+        for (int k = lane; k < cn * kNDir; k += 32) sc[k] = 0;
+        load_tile_B<T>(tl.B, B, un, nx, ny, nc, lane, 32);
+        load_tile_E<T>(tl.E, Eth, un, nx, ny, nc, lane, 32);
+        __syncwarp();
+        const int P0 = ss[0], P1 = ss[cn];
+        int cl = 0;   // the lane's current local cell (particles ascend)
+        for (int base = P0; base < P1; base += 32 * kPushUnroll) {
+            Pushed<T> o[kPushUnroll];
+            int cls[kPushUnroll], pp[kPushUnroll];
+            bool act[kPushUnroll];
+            T fx[kPushUnroll], fy[kPushUnroll], ux[kPushUnroll], uy[kPushUnroll], uz[kPushUnroll],
+                w[kPushUnroll];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            En[k][0] = ld(Eth + k * nc + n00);
-            En[k][1] = ld(Eth + k * nc + n10);
-            En[k][2] = ld(Eth + k * nc + n01);
-            En[k][3] = ld(Eth + k * nc + n11);
-        }
-        const int p0 = start[c], p1 = start[c + 1];
-        int cnt[kNDir];
+            for (int v = 0; v < kPushUnroll; ++v) {
+                pp[v] = base + 32 * v + lane;
+                act[v] = pp[v] < P1;
+                const int q = act[v] ? pp[v] : P0;
+                fx[v] = ld(src.fx + q);
+                fy[v] = ld(src.fy + q);
+                ux[v] = ld(src.ux + q);
+                uy[v] = ld(src.uy + q);
+                uz[v] = ld(src.uz + q);
+                w[v] = ld(src.w + q);
+            }
 #pragma unroll
-        for (int d = 0; d < kNDir; ++d) cnt[d] = 0;
-        if (phase != 0) {
-            if (lane < kNDir) rankbase[wib][lane] = 0;
-            __syncwarp();
-        }
-        for (int base = p0; base < p1; base += 32) {
-            const int p = base + lane;
-            const bool act = p < p1;
-            int dir = kNDir;   // inactive lanes use a direction no active lane has
-            T fxn = T(0), fyn = T(0), u1x = T(0), u1y = T(0), u1z = T(0), w = T(0);
-            int sx = 0, sy = 0;
-            if (act) {
-                const T fx = src.fx[p], fy = src.fy[p];
-                const T ux = src.ux[p], uy = src.uy[p], uz = src.uz[p];
-                w = src.w[p];
-                T Bx, By, Bz;
-                gather_B(B, nc, nx, i, im, ip, jr, jmr, jpr, fx, fy, Bx, By, Bz);
-                const T X0 = T(1) - fx, Y0 = T(1) - fy;
-                const T W0 = X0 * Y0, W1 = fx * Y0, W2 = X0 * fy, W3 = fx * fy;
-                const T Ex = W0 * En[0][0] + W1 * En[0][1] + W2 * En[0][2] + W3 * En[0][3];
-                const T Ey = W0 * En[1][0] + W1 * En[1][1] + W2 * En[1][2] + W3 * En[1][3];
-                const T Ez = W0 * En[2][0] + W1 * En[2][1] + W2 * En[2][2] + W3 * En[2][3];
-                const T u02 = ux * ux + uy * uy + uz * uz;
-                const T g0 = sqrt(T(1) + u02);
-                const T bg = beta / g0;
-                const T ax = bg * Bx, ay = bg * By, az = bg * Bz;
-                const T sa = T(1) / (T(1) + ax * ax + ay * ay + az * az);
-                // ubar = alpha w = (w + w x a + (w.a) a)/(1 + |a|^2), w = u + beta E
-                const T wx = ux + beta * Ex, wy = uy + beta * Ey, wz = uz + beta * Ez;
-                const T wa = wx * ax + wy * ay + wz * az;
-                const T ubx = sa * (wx + (wy * az - wz * ay) + wa * ax);
-                const T uby = sa * (wy + (wz * ax - wx * az) + wa * ay);
-                const T ubz = sa * (wz + (wx * ay - wy * ax) + wa * az);
-                u1x = T(2) * ubx - ux;
-                u1y = T(2) * uby - uy;
-                u1z = T(2) * ubz - uz;
-                const T u12 = u1x * u1x + u1y * u1y + u1z * u1z;
-                const T g1 = sqrt(T(1) + u12);
-                const T ig1 = T(1) / g1;
-                // position: x^{n+3/2} = x^{n+1/2} + dt u^{n+1}/gamma^{n+1}
-                T tx = fx + dt_dx * (u1x * ig1);
-                T ty = fy + dt_dy * (u1y * ig1);
-                T flx = floor(tx), fly = floor(ty);
-                sx = (int)flx;
-                sy = (int)fly;
-                fxn = tx - flx;
-                fyn = ty - fly;
-                if (fxn >= T(1)) { fxn -= T(1); sx += 1; }
-                if (fyn >= T(1)) { fyn -= T(1); sy += 1; }
-                if (phase != 2) {
-                    // with c dt <= dx a move of more than one cell can only come
-                    // from rounding at |v| = c; keep the particle on the last
-                    // representable point of the neighbour cell
-                    if (sx > 1) { sx = 1; fxn = Consts<T>::one_below(); }
-                    if (sx < -1) { sx = -1; fxn = T(0); }
-                    if (sy > 1) { sy = 1; fyn = Consts<T>::one_below(); }
-                    if (sy < -1) { sy = -1; fyn = T(0); }
-                    dir = (sy + 1) * 3 + (sx + 1);
-                } else {
-                    dir = 0;
-                }
-                if (phase == 0) {
-                    const T ue = ubx * Ex + uby * Ey + ubz * Ez;
-                    // g0 - g1 = (u0 - u1).(u0 + u1)/(g0 + g1)
-                    const T du = (ux - u1x) * (ux + u1x) + (uy - u1y) * (uy + u1y) +
-                                 (uz - u1z) * (uz + u1z);
-                    const T gs = g0 + g1;
-                    acc[0] += w * m * (u02 / (g0 + T(1)));      // K0
-                    acc[1] += -w * m * (du / gs);               // dK
-                    acc[2] += qw_dt * w * ue / g0;              // work (qw_dt = q dt)
-                    acc[3] += qw_dt * w * ue * (du / gs) / (g0 * gs);   // mismatch
-                    acc[4] += w * m * (u12 / (g1 + T(1)));      // K1
+            for (int v = 0; v < kPushUnroll; ++v) {
+                cls[v] = 0;
+                o[v].dir = kNDir;
+                if (act[v]) {
+                    while (ss[cl + 1] <= pp[v]) ++cl;
+                    cls[v] = cl;
+                    push_particle<T>(fx[v], fy[v], ux[v], uy[v], uz[v], w[v], cl, tl.E, tl.B, beta, dt_dx,
+                                     dt_dy, qdt, m, phase != 2, phase == 0, acc, o[v]);
+                    if (phase == 2) o[v].dir = 0;
                 }
             }
-            if (phase == 0) {
 #pragma unroll
-                for (int d = 0; d < kNDir; ++d) cnt[d] += __popc(__ballot_sync(0xffffffffu, dir == d));
-            } else {
-                const unsigned peers = __match_any_sync(0xffffffffu, dir);
+            for (int v = 0; v < kPushUnroll; ++v) {
+                // (local cell, direction) key; inactive lanes get a key of their own
+                const int kk = act[v] ? cls[v] * kNDir + o[v].dir : (1 << 20) + lane;
+                const unsigned peers = __match_any_sync(0xffffffffu, kk);
                 const int rk = __popc(peers & lt);
-                int rb = 0;
-                if (act) rb = rankbase[wib][dir];
-                __syncwarp();
-                if (act && rk == 0) rankbase[wib][dir] = rb + __popc(peers);
-                __syncwarp();
-                if (act) {
-                    int ni, nj;
-                    if (phase == 1) {
-                        ni = wrap1(i + sx, nx);
-                        nj = wrap1(j + sy, ny);
-                    } else {
-                        ni = (i + sx) % nx;
-                        nj = (j + sy) % ny;
-                        if (ni < 0) ni += nx;
-                        if (nj < 0) nj += ny;
-                    }
-                    const int k = nj * nx + ni;
-                    if (phase == 1) {
-                        const int dpos = off9[(int64_t)k * kNDir + dir] + rb + rk;
+                if (phase == 0) {
+                    if (act[v] && rk == 0) sc[kk] += __popc(peers);
+                    __syncwarp();
+                } else if (phase == 1) {
+                    const int rb = act[v] ? sc[kk] : 0;
+                    __syncwarp();
+                    if (act[v] && rk == 0) sc[kk] = rb + __popc(peers);
+                    __syncwarp();
+                    if (act[v]) {
+                        const int c = c0 + cls[v];
+                        const int ci = un.i0 + cls[v], cj = un.j;
+                        const int k = wrap1(cj + o[v].sy, ny) * nx + wrap1(ci + o[v].sx, nx);
+                        const int dpos = off9[(int64_t)k * kNDir + o[v].dir] + rb + rk;
                         // the count pass and this pass must agree move by move;
                         // if they ever did not, flag it instead of writing
-                        if (rb + rk >= n9[(int64_t)c * kNDir + dir] || dpos < 0 || dpos >= npart) {
+                        if (rb + rk >= n9[(int64_t)c * kNDir + o[v].dir] || dpos < 0 || dpos >= npart) {
                             atomicOr(err, 1);
-                            continue;
+                        } else {
+                            dst.fx[dpos] = o[v].fxn;
+                            dst.fy[dpos] = o[v].fyn;
+                            dst.ux[dpos] = o[v].u1x;
+                            dst.uy[dpos] = o[v].u1y;
+                            dst.uz[dpos] = o[v].u1z;
+                            dst.w[dpos] = o[v].w;
+                            if (dst.id) dst.id[dpos] = src.id[pp[v]];
                         }
-                        dst.fx[dpos] = fxn;
-                        dst.fy[dpos] = fyn;
-                        dst.ux[dpos] = u1x;
-                        dst.uy[dpos] = u1y;
-                        dst.uz[dpos] = u1z;
-                        dst.w[dpos] = w;
-                        if (dst.id) dst.id[dpos] = src.id[p];
-                    } else {
-                        dst.fx[p] = fxn;
-                        dst.fy[p] = fyn;
-                        dst.ux[p] = u1x;
-                        dst.uy[p] = u1y;
-                        dst.uz[p] = u1z;
-                        dst.w[p] = w;
-                        if (dst.id) dst.id[p] = src.id[p];
-                        key[p] = k;
                     }
+                } else if (act[v]) {
+                    // general path: in place, with the new cell as sort key
+                    const int ci = un.i0 + cls[v], cj = un.j;
+                    int ni = (ci + o[v].sx) % nx, nj = (cj + o[v].sy) % ny;
+                    if (ni < 0) ni += nx;
+                    if (nj < 0) nj += ny;
+                    const int p = pp[v];
+                    dst.fx[p] = o[v].fxn;
+                    dst.fy[p] = o[v].fyn;
+                    dst.ux[p] = o[v].u1x;
+                    dst.uy[p] = o[v].u1y;
+                    dst.uz[p] = o[v].u1z;
+                    dst.w[p] = o[v].w;
+                    if (dst.id) dst.id[p] = src.id[p];
+                    key[p] = nj * nx + ni;
                 }
             }
         }
-        if (phase == 0 && lane < kNDir) {
-            int v = 0;
-#pragma unroll
-            for (int d = 0; d < kNDir; ++d) v = lane == d ? cnt[d] : v;
-            n9[(int64_t)c * kNDir + lane] = v;
-        }
+        if (phase == 0)
+            for (int k = lane; k < cn * kNDir; k += 32) n9[(int64_t)c0 * kNDir + k] = sc[k];
+        __syncwarp();
     }
     if (phase == 0) {
         double v[kLedger], out[kLedger];
@@ -449,7 +750,10 @@ int blocks_for(int64_t n, int threads, int cap)
 
 }  // namespace
 
-int push_grid_blocks() { return 152 * 8; }
+int push_grid_blocks(GridP g)
+{
+    return blocks_for(units_of(g.nx, g.ny), kPushWarps, 152 * 16);
+}
 
 template <typename T>
 cudaError_t load_convert(const double* x, const double* u, const double* w, int64_t n, GridP g,
@@ -481,14 +785,19 @@ cudaError_t export_particles(PArrays<T> p, const int32_t* start, GridP g, double
 }
 
 template <typename T>
-cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g, cudaStream_t st)
+cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g, int* err, cudaStream_t st)
 {
-    constexpr int G = 8;
-    const int threads = 256;
-    int64_t groups = g.ncell;
-    int blocks = blocks_for(groups * G, threads, 152 * 16);
+    const int nunits = units_of(g.nx, g.ny);
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm *= 2;   // two CTAs per SM
+    const size_t smem = (size_t)kDepBuf * 6 * kDepCap * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_deposit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = nunits < nsm ? nunits : nsm;
     count_launches(1);
-    k_deposit<T, G><<<blocks, threads, 0, st>>>(sp, B, M, J, g);
+    k_deposit<T><<<blocks, kDepThreads, smem, st>>>(sp, B, M, J, g, err);
     return cudaGetLastError();
 }
 
@@ -523,7 +832,7 @@ cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, i
                                              cudaStream_t);                                        \
     template cudaError_t export_particles<T>(PArrays<T>, const int32_t*, GridP, double*, double*,  \
                                              double*, int32_t*, cudaStream_t);                     \
-    template cudaError_t deposit<T>(const DepositSpecies<T>&, const T*, T*, T*, GridP, cudaStream_t); \
+    template cudaError_t deposit<T>(const DepositSpecies<T>&, const T*, T*, T*, GridP, int*, cudaStream_t); \
     template cudaError_t push<T>(int, PArrays<T>, PArrays<T>, const int32_t*, int32_t*,            \
                                  const int32_t*, int32_t*, const T*, const T*, GridP, SpeciesConst, \
                                  double*, int, int64_t, int*, cudaStream_t);                       \
