@@ -255,8 +255,8 @@ def run_ours(args):
     mover = ("deposit", "push_count", "sort_tables", "push_scatter")
     mover_ms = sum(per_kernel[k]["ms_per_step"] for k in mover if k in per_kernel)
     mover_bytes = (algorithmic_bytes("deposit", N, 0, ncell, esz)
-                   + sum(algorithmic_bytes("push_count", n, 0, ncell, esz)
-                         + algorithmic_bytes("push_scatter", n, 0, ncell, esz) for n in n_per))
+                   + sum(algorithmic_bytes("push_count", 0, n, ncell, esz)
+                         + algorithmic_bytes("push_scatter", 0, n, ncell, esz) for n in n_per))
     mover_gbs = mover_bytes / (mover_ms / 1e3) / 1e9
     last = ledgers[-1]
     out = {

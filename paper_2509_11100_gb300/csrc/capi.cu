@@ -620,7 +620,7 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
 template <typename T>
 int push_impl(relsim_ctx* c)
 {
-    const int nbp = push_grid_blocks(c->g);
+    const int nbp = push_grid_blocks(c->g, c->prec);
     TRY(ensure_partial(c, (int64_t)nbp * 5));
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         Species& sp = c->sp[s];

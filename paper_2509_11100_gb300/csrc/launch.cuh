@@ -89,7 +89,7 @@ cudaError_t push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* start
                  const int32_t* off9, int32_t* key, const T* Eth, const T* B, GridP g,
                  SpeciesConst sc, double* lsum_partial, int lsum_blocks, int64_t npart, int* err,
                  cudaStream_t st);
-int push_grid_blocks(GridP g);
+int push_grid_blocks(GridP g, int precision);
 template <typename T>
 cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, int nblocks,
                            cudaStream_t st);

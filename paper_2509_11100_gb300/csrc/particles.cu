@@ -515,8 +515,10 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
 // shared memory in particle order, so ranks follow the old order (the stable
 // sort).
 
-constexpr int kPushThreads = 256;
-constexpr int kPushWarps = kPushThreads / 32;
+template <typename T> struct PushCfg {
+    static constexpr int warps = sizeof(T) == 4 ? 8 : 4;   // static shared memory < 48 KB
+    static constexpr int threads = 32 * warps;
+};
 constexpr int kPushUnroll = 2;
 constexpr int kLedger = 5;   // K0, dK, work, mismatch, K1
 
@@ -597,15 +599,18 @@ struct PushTile {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kPushThreads)
+__global__ void __launch_bounds__(PushCfg<T>::threads)
 k_push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start,
        int32_t* __restrict__ n9, const int32_t* __restrict__ off9, int32_t* __restrict__ key,
        const T* __restrict__ Eth, const T* __restrict__ B, GridP g, T beta, T dt_dx, T dt_dy,
        T qdt, T m, double* __restrict__ lsum, int npart, int* __restrict__ err)
 {
-    __shared__ int sstart[kPushWarps][kUnitW + 1];
-    __shared__ int scnt[kPushWarps][kUnitW * kNDir];
-    __shared__ PushTile<T> stile[kPushWarps];
+    constexpr int W = PushCfg<T>::warps;
+    __shared__ int sstart[W][kUnitW + 1];
+    __shared__ int scnt[W][kUnitW * kNDir];
+    // destinations of the unit's moves: [dest row j-1..j+1][dest col i0-1..i0+cn][sx+1]
+    __shared__ int soff[W][3][kTB][3];
+    __shared__ PushTile<T> stile[W];
     __shared__ double red[32 * kLedger];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -625,6 +630,15 @@ k_push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ st
         for (int k = lane; k < cn * kNDir; k += 32) sc[k] = 0;
         load_tile_B<T>(tl.B, B, un, nx, ny, nc, lane, 32);
         load_tile_E<T>(tl.E, Eth, un, nx, ny, nc, lane, 32);
+        if (phase == 1) {
+            int* so = &soff[wib][0][0][0];
+            for (int idx = lane; idx < 9 * kTB; idx += 32) {
+                const int r = idx / (3 * kTB), col = (idx / 3) % kTB, sxi = idx % 3;
+                if (col > cn + 1) continue;
+                const int k = wrap1(un.j - 1 + r, ny) * nx + wrap1(un.i0 - 1 + col, nx);
+                so[idx] = off9[(int64_t)k * kNDir + r * 3 + sxi];
+            }
+        }
         __syncwarp();
         const int P0 = ss[0], P1 = ss[cn];
         int cl = 0;   // the lane's current local cell (particles ascend)
@@ -673,13 +687,9 @@ k_push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ st
                     if (act[v] && rk == 0) sc[kk] = rb + __popc(peers);
                     __syncwarp();
                     if (act[v]) {
-                        const int c = c0 + cls[v];
-                        const int ci = un.i0 + cls[v], cj = un.j;
-                        const int k = wrap1(cj + o[v].sy, ny) * nx + wrap1(ci + o[v].sx, nx);
-                        const int dpos = off9[(int64_t)k * kNDir + o[v].dir] + rb + rk;
-                        // the count pass and this pass must agree move by move;
-                        // if they ever did not, flag it instead of writing
-                        if (rb + rk >= n9[(int64_t)c * kNDir + o[v].dir] || dpos < 0 || dpos >= npart) {
+                        const int dpos =
+                            soff[wib][o[v].sy + 1][cls[v] + 1 + o[v].sx][o[v].sx + 1] + rb + rk;
+                        if (dpos < 0 || dpos >= npart) {
                             atomicOr(err, 1);
                         } else {
                             dst.fx[dpos] = o[v].fxn;
@@ -711,6 +721,11 @@ k_push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ st
         }
         if (phase == 0)
             for (int k = lane; k < cn * kNDir; k += 32) n9[(int64_t)c0 * kNDir + k] = sc[k];
+        if (phase == 1)
+            // the count pass and this pass must agree move by move; if they
+            // ever did not, say so (the writes stayed in bounds)
+            for (int k = lane; k < cn * kNDir; k += 32)
+                if (sc[k] != n9[(int64_t)c0 * kNDir + k]) atomicOr(err, 1);
         __syncwarp();
     }
     if (phase == 0) {
@@ -750,9 +765,10 @@ int blocks_for(int64_t n, int threads, int cap)
 
 }  // namespace
 
-int push_grid_blocks(GridP g)
+int push_grid_blocks(GridP g, int precision)
 {
-    return blocks_for(units_of(g.nx, g.ny), kPushWarps, 152 * 16);
+    return blocks_for(units_of(g.nx, g.ny), precision == 32 ? PushCfg<float>::warps : PushCfg<double>::warps,
+                      152 * 16);
 }
 
 template <typename T>
@@ -809,7 +825,7 @@ cudaError_t push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* start
 {
     const T beta = (T)(sc.q * g.dt / (2.0 * sc.m));
     count_launches(1);
-    k_push<T><<<lsum_blocks, kPushThreads, 0, st>>>(phase, src, dst, start, n9, off9, key, Eth, B, g,
+    k_push<T><<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(phase, src, dst, start, n9, off9, key, Eth, B, g,
                                                     beta, (T)(g.dt / g.dx), (T)(g.dt / g.dy),
                                                     (T)(sc.q * g.dt), (T)sc.m, lsum_partial,
                                                     (int)npart, err);
