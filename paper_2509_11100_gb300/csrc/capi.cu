@@ -88,6 +88,7 @@ struct relsim_ctx {
     int64_t nvec = 0;
     double* V = nullptr;
     double* gw = nullptr;
+    double* gw2 = nullptr;
     double* gx = nullptr;
     double* gb = nullptr;
     double* partial = nullptr;
@@ -468,10 +469,11 @@ int build_impl(relsim_ctx* c)
     return RELSIM_OK;
 }
 
-// sum of the first k+1 reduced values: read back after a sync
+// read back count reduced values (and the kernels' error flags) after a sync
 int readback(relsim_ctx* c, const double* dev, int count, double* host)
 {
     CK(cudaMemcpyAsync(host, dev, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c->hpush, c->dpush, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     return RELSIM_OK;
 }
@@ -479,11 +481,16 @@ int readback(relsim_ctx* c, const double* dev, int count, double* host)
 template <typename T>
 int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
 {
+    // Restarted GMRES on A = I + B. The Arnoldi process runs on B (the same
+    // Krylov space: A V_k = V_k + B V_k, so the Hessenberg matrix of A is that
+    // of B plus the identity). Working on B avoids the cancellation of
+    // orthogonalising A v ~ v against v, and keeps the identity exact in FP64.
     const int64_t n = c->nvec;
     const int64_t ldv = n;
     const int m = c->mrest;
     const int nb = gm_blocks(n);
-    TRY(ensure_partial(c, (int64_t)nb * (m + 2)));
+    const int nbo = op_blocks(c->g, c->prec);
+    TRY(ensure_partial(c, (int64_t)(nb > nbo ? nb : nbo) * (m + 2)));
     const double tol = c->cfg.gmres_tol;
     const int maxit = c->cfg.gmres_maxit;
     double* hp = c->hpin;                      // readback area
@@ -491,6 +498,7 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
     double* dy = c->dsum + 2 * (kMaxRestart + 2);
     double H[(kMaxRestart + 1) * kMaxRestart];
     double cs[kMaxRestart], sn[kMaxRestart], gv[kMaxRestart + 1], y[kMaxRestart];
+    double* gw[2] = {c->gw, c->gw2};
 
     PROF_BEGIN(RELSIM_PROF_RHS);
     CK(rhs<T>((const T*)c->E, (const T*)c->B[c->bcur], (const T*)c->J, c->gb, c->g, c->st));
@@ -508,15 +516,13 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
         CK(cudaMemsetAsync(c->gx, 0, sizeof(double) * (size_t)n, c->st));
     } else {
         for (;;) {
-            // r = b - A x into V_0
+            // r = b - A x (unnormalised first Krylov vector) and |r|^2
             PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
-            CK(apply_A<T>((const T*)c->M, c->gx, c->gw, c->g, c->st));
-            PROF_END();
-            PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-            CK(gm_sub(c->V, c->gb, c->gw, n, c->partial, nb, c->st));
-            CK(reduce_partials(c->partial, nb, 1, c->dsum, c->st));
+            CK(op_residual<T>((const T*)c->M, c->gx, c->gb, gw[0], c->g, c->partial, c->dpush, c->st));
+            CK(reduce_partials(c->partial, nbo, 1, c->dsum, c->st));
             PROF_END();
             TRY(readback(c, c->dsum, 1, hp));
+            TRY(check_push(c));
             const double beta = std::sqrt(hp[0]);
             if (!std::isfinite(beta)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite residual");
             relres = beta / bnorm;
@@ -526,49 +532,58 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
                               "GMRES reached %d iterations at relative residual %.3e", total, relres);
                 break;
             }
-            PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-            CK(gm_scale(c->V, c->V, 1.0 / beta, n, c->st));
-            PROF_END();
             for (int k = 0; k <= m; ++k) gv[k] = 0.0;
             gv[0] = beta;
             int kdim = 0;
             for (int j = 0; j < m; ++j) {
-                double* vj = c->V + (int64_t)j * ldv;
-                double* vn = c->V + (int64_t)(j + 1) * ldv;
+                // w = B v_j (v_0 = r/|r| is written to V_0 on the way) and the
+                // dot products <w, V_i> (i <= j), <w, w>
                 PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
-                CK(apply_A<T>((const T*)c->M, vj, c->gw, c->g, c->st));
+                if (j == 0)
+                    CK(op_arnoldi<T>((const T*)c->M, gw[0], 1.0 / beta, c->V, gw[1], c->V, ldv, 0, c->g,
+                                     c->partial, c->dpush, c->st));
+                else
+                    CK(op_arnoldi<T>((const T*)c->M, c->V + (int64_t)j * ldv, 1.0, nullptr, gw[1], c->V, ldv,
+                                     j, c->g, c->partial, c->dpush, c->st));
                 PROF_END();
-                // classical Gram-Schmidt: h = V^T w (plus w.w), w -= V h, |w|^2
+                // classical Gram-Schmidt with the normalisation fused:
+                // V_{j+1} = (w - V h)/hn, hn^2 = <w,w> - |h|^2
                 PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                CK(gm_dots(c->V, ldv, j + 1, c->gw, n, c->partial, nb, c->st));
-                CK(reduce_partials(c->partial, nb, j + 2, c->dsum, c->st));
-                CK(gm_update(c->gw, c->V, ldv, j + 1, c->dsum, n, c->partial, nb, c->st));
-                CK(reduce_partials(c->partial, nb, 1, c->dsum + kMaxRestart + 1, c->st));
+                CK(reduce_partials(c->partial, nbo, j + 2, c->dsum, c->st));
+                CK(gm_update_scale(gw[1], c->V, ldv, j + 1, c->dsum, c->V + (int64_t)(j + 1) * ldv, n, c->st));
                 PROF_END();
-                TRY(readback(c, c->dsum, kMaxRestart + 2, hp));
-                double ww = hp[j + 1];
-                double hn2 = hp[kMaxRestart + 1];
-                for (int i = 0; i <= j; ++i) H[i * m + j] = hp[i];
-                if (hn2 < 0.25 * ww) {
-                    // heavy cancellation: orthogonalise once more (CGS2)
+                TRY(readback(c, c->dsum, j + 2, hp));
+                TRY(check_push(c));
+                const double ww = hp[j + 1];
+                double hn2 = ww;
+                for (int i = 0; i <= j; ++i) {
+                    H[i * m + j] = hp[i];
+                    hn2 -= hp[i] * hp[i];
+                }
+                if (!std::isfinite(hn2)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite Arnoldi norm");
+                if (hn2 < 1e-4 * ww) {
+                    // |w - V h| < |w|/100: the norm above has lost digits;
+                    // orthogonalise w twice explicitly (CGS2) and normalise
                     PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                    CK(gm_dots(c->V, ldv, j + 1, c->gw, n, c->partial, nb, c->st));
+                    CK(gm_update(gw[1], c->V, ldv, j + 1, c->dsum, n, c->partial, nb, c->st));
+                    CK(gm_dots(c->V, ldv, j + 1, gw[1], n, c->partial, nb, c->st));
                     CK(reduce_partials(c->partial, nb, j + 2, c->dsum, c->st));
-                    CK(gm_update(c->gw, c->V, ldv, j + 1, c->dsum, n, c->partial, nb, c->st));
+                    CK(gm_update(gw[1], c->V, ldv, j + 1, c->dsum, n, c->partial, nb, c->st));
                     CK(reduce_partials(c->partial, nb, 1, c->dsum + kMaxRestart + 1, c->st));
                     PROF_END();
                     TRY(readback(c, c->dsum, kMaxRestart + 2, hp));
                     for (int i = 0; i <= j; ++i) H[i * m + j] += hp[i];
                     hn2 = hp[kMaxRestart + 1];
+                    if (!std::isfinite(hn2)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite Arnoldi norm");
+                    if (hn2 > 0.0) {
+                        PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
+                        CK(gm_scale(c->V + (int64_t)(j + 1) * ldv, gw[1], 1.0 / std::sqrt(hn2), n, c->st));
+                        PROF_END();
+                    }
                 }
                 const double hn = std::sqrt(hn2 > 0.0 ? hn2 : 0.0);
-                if (!std::isfinite(hn)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite Arnoldi norm");
+                H[j * m + j] += 1.0;   // A = I + B
                 H[(j + 1) * m + j] = hn;
-                if (hn > 0.0) {
-                    PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                    CK(gm_scale(vn, c->gw, 1.0 / hn, n, c->st));
-                    PROF_END();
-                }
                 for (int i = 0; i < j; ++i) {
                     const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
                     H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
@@ -681,7 +696,7 @@ int push_impl(relsim_ctx* c)
 int check_push(relsim_ctx* c)
 {
     if (*c->hpush & 2)
-        return fail(c, RELSIM_ERR_TIMEOUT, "deposit: a shared-memory staging wait gave up");
+        return fail(c, RELSIM_ERR_TIMEOUT, "a shared-memory staging wait gave up (deposit or operator)");
     if (*c->hpush)
         return fail(c, RELSIM_ERR_INTERNAL, "particle sort: count and scatter passes disagreed");
     return RELSIM_OK;
@@ -812,6 +827,7 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     A(dalloc(c, &c->scan_tmp, sizeof(int32_t) * c->scan_tmp_n));
     A(dalloc(c, &c->V, sizeof(double) * (size_t)(c->mrest + 1) * c->nvec));
     A(dalloc(c, &c->gw, sizeof(double) * c->nvec));
+    A(dalloc(c, &c->gw2, sizeof(double) * c->nvec));
     A(dalloc(c, &c->gx, sizeof(double) * c->nvec));
     A(dalloc(c, &c->gb, sizeof(double) * c->nvec));
     A(dalloc(c, &c->dsum, sizeof(double) * 4 * (kMaxRestart + 2)));
@@ -875,7 +891,7 @@ void relsim_destroy(relsim_ctx* c)
         dfree(c->rv[b]);
     }
     dfree(c->rtmp);
-    dfree(c->V); dfree(c->gw); dfree(c->gx); dfree(c->gb); dfree(c->partial);
+    dfree(c->V); dfree(c->gw); dfree(c->gw2); dfree(c->gx); dfree(c->gb); dfree(c->partial);
     dfree(c->dsum); dfree(c->dled); dfree(c->dflag); dfree(c->dpush); dfree(c->stage);
     if (c->hpin) cudaFreeHost(c->hpin);
     if (c->hflag) cudaFreeHost(c->hflag);
@@ -1055,9 +1071,12 @@ int relsim_apply_operator(relsim_ctx* c, const double* v, double* out, int where
     if (where == RELSIM_HOST) TRY(ensure_stage(c, n));
     TRY(stage_in(c, v, n, where, &dv, 0));
     // the GMRES work vector is free outside a solve
-    if (c->prec == 32) CK(apply_A<float>((const float*)c->M, dv, c->gw, c->g, c->st));
-    else CK(apply_A<double>((const double*)c->M, dv, c->gw, c->g, c->st));
-    return copy_out(c, out, c->gw, n, where);
+    if (c->prec == 32) CK(apply_A<float>((const float*)c->M, dv, c->gw, c->g, c->dpush, c->st));
+    else CK(apply_A<double>((const double*)c->M, dv, c->gw, c->g, c->dpush, c->st));
+    if (where == RELSIM_DEVICE) return copy_out(c, out, c->gw, n, where);
+    CK(cudaMemcpyAsync(c->hpush, c->dpush, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    TRY(copy_out(c, out, c->gw, n, where));
+    return check_push(c);
 }
 
 int relsim_push(relsim_ctx* c)

@@ -94,4 +94,51 @@ template <> struct Consts<double> {
     static __device__ __forceinline__ double one_below() { return 0.99999999999999989; }  // 1 - 2^-53
 };
 
+// ---- TMA bulk copies (cp.async.bulk) completing on an mbarrier ----
+// A bulk copy needs 16-byte aligned source and destination addresses and a
+// size that is a multiple of 16 bytes.
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mb, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx_arrive(uint64_t* mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* mb)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mb))
+        : "memory");
+}
+
+// bounded wait on the mbarrier phase with the given parity: at most
+// max_polls polls; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity, long long max_polls)
+{
+    const unsigned a = smem_u32(mb);
+    for (long long it = 0; it < max_polls; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 }  // namespace relsim

@@ -9,6 +9,8 @@
 //   curl_n (centre -> node (i,j)): the same over the four centres around
 //     the node. curl_n is the transpose of curl_c on the periodic grid, which
 //     makes the discrete Poynting balance exact.
+#include <atomic>
+
 #include "launch.cuh"
 
 namespace relsim {
@@ -66,22 +68,15 @@ __global__ void k_rhs(const T* __restrict__ E, const T* __restrict__ B, const T*
 template <typename T>
 __device__ __forceinline__ T vld(const double* v, int64_t k) { return (T)__ldg(v + k); }
 
-// (curl_n curl_c v) and (M v) at node (i,j); v FP64 component-major.
-template <typename T>
-__device__ __forceinline__ void op_parts(const T* __restrict__ M, const double* __restrict__ v, int i,
-                                         int j, const GridP& g, T cc[3], T mv[3])
+// (curl_n curl_c v) and (M v) at a node from its 3x3 stencil of v,
+// f[k][a][b] = component k at node (i-1+a, j-1+b), and its mass-matrix
+// blocks: Mg = the node's own five blocks M[g][0..4], Mn[o] = the block
+// M[g-o][o+1] of the neighbour g - o for the half offsets o = (1,0), (-1,1),
+// (0,1), (1,1) (M_{g,g-o} = M_{g-o,g}).
+template <typename T, typename P>
+__device__ __forceinline__ void op_stencil(const T (&f)[3][3][3], P Mg, const P (&Mn)[4], T idx2, T idy2,
+                                           T cc[3], T mv[3])
 {
-    const int nx = g.nx, ny = g.ny, nc = g.ncell;
-    const int xs[3] = {wrap1(i - 1, nx), i, wrap1(i + 1, nx)};
-    const int ys[3] = {wrap1(j - 1, ny) * nx, j * nx, wrap1(j + 1, ny) * nx};
-    T f[3][3][3];   // f[k][a][b]: component k at node (i-1+a, j-1+b)
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) f[k][a][b] = vld<T>(v, (int64_t)k * nc + ys[b] + xs[a]);
-    const T idx2 = T(0.5 / g.dx), idy2 = T(0.5 / g.dy);
     // curl_c at the four centres (i-1+ca+1/2, j-1+cb+1/2)
     T C[3][2][2];
 #pragma unroll
@@ -109,46 +104,232 @@ __device__ __forceinline__ void op_parts(const T* __restrict__ M, const double* 
     cc[1] = -dx[2];
     cc[2] = dx[1] - dy[0];
     // M v: own blocks M[g][o] times v(g+o), neighbours' blocks M[g-o][o] times v(g-o)
-    const int64_t gi = (int64_t)ys[1] + xs[1];
-    // half offsets o_1..o_4 = (1,0), (-1,1), (0,1), (1,1): (a,b) stencil indices
-    constexpr int pa[4] = {2, 0, 1, 2}, pb[4] = {1, 2, 2, 2};   // g + o
+    constexpr int pa[4] = {2, 0, 1, 2}, pb[4] = {1, 2, 2, 2};   // g + o in the stencil
     constexpr int ma[4] = {0, 2, 1, 0}, mb[4] = {1, 0, 0, 0};   // g - o
     T r[3] = {T(0), T(0), T(0)};
-    const T* Mg = M + gi * kMBlock;
 #pragma unroll
     for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
-        for (int s = 0; s < 3; ++s) r[rr] += ld(Mg + rr * 3 + s) * f[s][1][1];
+        for (int s = 0; s < 3; ++s) r[rr] += T(Mg[rr * 3 + s]) * f[s][1][1];
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-        const T* Mo = Mg + (o + 1) * 9;
-        const T* Mn = M + ((int64_t)ys[mb[o]] + xs[ma[o]]) * kMBlock + (o + 1) * 9;
+        P Mo = Mg + (o + 1) * 9;
 #pragma unroll
         for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
             for (int s = 0; s < 3; ++s)
-                r[rr] += ld(Mo + rr * 3 + s) * f[s][pa[o]][pb[o]] + ld(Mn + rr * 3 + s) * f[s][ma[o]][mb[o]];
+                r[rr] += T(Mo[rr * 3 + s]) * f[s][pa[o]][pb[o]] + T(Mn[o][rr * 3 + s]) * f[s][ma[o]][mb[o]];
     }
     mv[0] = r[0];
     mv[1] = r[1];
     mv[2] = r[2];
 }
 
+// the same at node (i,j) straight from global memory (v FP64, component-major)
 template <typename T>
-__global__ void __launch_bounds__(kFieldThreads)
-k_apply_A(const T* __restrict__ M, const double* __restrict__ v, double* __restrict__ out, GridP g)
+__device__ __forceinline__ void op_parts(const T* __restrict__ M, const double* __restrict__ v, int i,
+                                         int j, const GridP& g, T cc[3], T mv[3])
 {
-    const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gidx >= g.ncell) return;
-    const int i = gidx % g.nx, j = gidx / g.nx;
-    T cc[3], mv[3];
-    op_parts<T>(M, v, i, j, g, cc, mv);
-    const T td = T(g.theta * g.dt);
-    const int nc = g.ncell;
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int xs[3] = {wrap1(i - 1, nx), i, wrap1(i + 1, nx)};
+    const int ys[3] = {wrap1(j - 1, ny) * nx, j * nx, wrap1(j + 1, ny) * nx};
+    T f[3][3][3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const T vk = vld<T>(v, (int64_t)k * nc + gidx);
-        out[(int64_t)k * nc + gidx] = (double)(vk + td * td * cc[k] + td * mv[k]);
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) f[k][a][b] = vld<T>(v, (int64_t)k * nc + ys[b] + xs[a]);
+    const T* Mg = M + ((int64_t)ys[1] + xs[1]) * kMBlock;
+    const T* Mn[4] = {M + ((int64_t)ys[1] + xs[0]) * kMBlock + 9, M + ((int64_t)ys[0] + xs[2]) * kMBlock + 18,
+                      M + ((int64_t)ys[0] + xs[1]) * kMBlock + 27, M + ((int64_t)ys[0] + xs[0]) * kMBlock + 36};
+    op_stencil<T, const T*>(f, Mg, Mn, T(0.5 / g.dx), T(0.5 / g.dy), cc, mv);
+}
+
+// ---------------------------------------------------------------------------
+// The implicit operator A = I + B, B = (theta dt)^2 curl_n curl_c + theta dt M,
+// on tiles of X x Y nodes (one thread per node, one warp per tile row). The
+// tile's mass-matrix rows j0-1 .. j0+Y-1 (its own blocks and those of the
+// row below it that reach into the tile) are staged in shared memory, the
+// main columns by TMA bulk copies (one per row) when the rows are 16-byte
+// aligned, the two halo columns and the input vector on its 1-node halo by
+// plain loads; the input is staged in T, converted once per staged value
+// (on GB300 every FP64 operation, conversions included, runs on a pipe about
+// 64 times slower than FP32, so the kernels keep their FP64 work to the
+// node's own values, the dot products and their reduction). Three modes:
+//   kOpA:        out = A in
+//   kOpResidual: out = b - A in, per-tile partial of |out|^2
+//   kOpArnoldi:  v = s in (written to vj for the tile's nodes when vj is not
+//                null), out = B v, per-tile partials of <out, V_q> (q < nv),
+//                <out, v> and <out, out> (nv + 2 sums).
+// B v is computed in T (the FP32 form's operator precision); the identity,
+// the residual and the dot products are formed in FP64.
+
+enum { kOpA = 0, kOpResidual = 1, kOpArnoldi = 2 };
+constexpr long long kOpMaxPolls = 1ll << 26;   // bounded mbarrier wait
+constexpr int kOpChunk = 8;                    // dot products reduced per shared-memory pass
+
+template <typename T>
+struct OpTile {
+    static constexpr int X = 32;
+    static constexpr int Y = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int threads = X * Y;
+};
+
+template <typename T>
+struct OpShared {
+    // rows j0-1 .., columns i0 .. i0+X-1; reused for the dot-product
+    // reduction once the operator is applied
+    T Mm[OpTile<T>::Y + 1][OpTile<T>::X * kMBlock];
+    T Mh[OpTile<T>::Y + 1][2][kMBlock];          // columns i0-1 and i0+tw
+    T v[3][OpTile<T>::Y + 2][OpTile<T>::X + 2];  // rows j0-1 .. j0+Y, columns i0-1 .. i0+tw
+    uint64_t mbar;
+};
+static_assert(sizeof(float) * (OpTile<float>::Y + 1) * OpTile<float>::X * kMBlock >=
+                  sizeof(double) * kOpChunk * OpTile<float>::threads,
+              "the reduction buffer fits in the mass-matrix tile");
+static_assert(sizeof(double) * (OpTile<double>::Y + 1) * OpTile<double>::X * kMBlock >=
+                  sizeof(double) * kOpChunk * OpTile<double>::threads,
+              "the reduction buffer fits in the mass-matrix tile");
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(OpTile<T>::threads, sizeof(T) == 4 ? 3 : 2)
+k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const double* __restrict__ b,
+     double* __restrict__ out, double* __restrict__ vj, const double* __restrict__ V, int64_t ldv, int nv,
+     GridP g, int tma, double* __restrict__ partial, int* __restrict__ err)
+{
+    constexpr int X = OpTile<T>::X, Y = OpTile<T>::Y, NT = OpTile<T>::threads;
+    extern __shared__ __align__(128) unsigned char op_smem[];
+    OpShared<T>& S = *reinterpret_cast<OpShared<T>*>(op_smem);
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int tilesx = (nx + X - 1) / X;
+    const int i0 = (blockIdx.x % tilesx) * X, j0 = (blockIdx.x / tilesx) * Y;
+    const int tw = min(X, nx - i0), th = min(Y, ny - j0);
+    const int tid = threadIdx.x, tx = tid % X, ty = tid / X;
+    const bool active = tx < tw && ty < th;
+    const int64_t gidx = (int64_t)(j0 + ty) * nx + i0 + tx;
+
+    if (tma) {
+        if (tid == 0) {
+            mbar_init(&S.mbar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned bytes = (unsigned)(tw * kMBlock * sizeof(T));
+            mbar_expect_tx_arrive(&S.mbar, bytes * (unsigned)(th + 1));
+            for (int r = 0; r <= th; ++r) {
+                const int jr = wrap1(j0 - 1 + r, ny);
+                bulk_g2s(&S.Mm[r][0], M + ((int64_t)jr * nx + i0) * kMBlock, bytes, &S.mbar);
+            }
+        }
+    } else {
+        for (int r = 0; r <= th; ++r) {
+            const T* src = M + ((int64_t)wrap1(j0 - 1 + r, ny) * nx + i0) * kMBlock;
+            for (int q = tid; q < tw * kMBlock; q += NT) S.Mm[r][q] = ld(src + q);
+        }
+    }
+    // the node's own input value in FP64
+    double own[3] = {0.0, 0.0, 0.0};
+    if (active)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            own[k] = __ldg(in + (int64_t)k * nc + gidx);
+            if (MODE == kOpArnoldi && s != 1.0) own[k] *= s;
+        }
+    for (int q = tid; q < (th + 1) * 2 * kMBlock; q += NT) {
+        const int r = q / (2 * kMBlock), side = (q / kMBlock) % 2, e = q % kMBlock;
+        const int ic = side == 0 ? wrap1(i0 - 1, nx) : wrap1(i0 + tw, nx);
+        S.Mh[r][side][e] = ld(M + ((int64_t)wrap1(j0 - 1 + r, ny) * nx + ic) * kMBlock + e);
+    }
+    const int vw = tw + 2, vh = th + 2;
+    const T sT = (T)s;
+    for (int q = tid; q < 3 * vh * vw; q += NT) {
+        const int k = q / (vh * vw), rem = q % (vh * vw), r = rem / vw, cc = rem % vw;
+        T val = (T)__ldg(in + (int64_t)k * nc + (int64_t)wrap1(j0 - 1 + r, ny) * nx + wrap1(i0 - 1 + cc, nx));
+        if (MODE == kOpArnoldi) val *= sT;
+        S.v[k][r][cc] = val;
+    }
+    bool ok = true;
+    if (tma) ok = mbar_wait(&S.mbar, 0, kOpMaxPolls);
+    if (__syncthreads_or(!ok)) {   // publishes the plain stores too
+        if (tid == 0) {
+            atomicOr(err, 2);
+            mbar_wait(&S.mbar, 0, kOpMaxPolls);   // let copies in flight land (bounded)
+        }
+        return;
+    }
+
+    double wv[3] = {0.0, 0.0, 0.0};
+    if (active) {
+        T f[3][3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb) f[k][a][bb] = S.v[k][ty + bb][tx + a];
+        // mass-matrix block row of the node at local column c, local row r
+        auto blk = [&](int c, int r) -> const T* {
+            return c < 0 ? S.Mh[r + 1][0] : (c >= tw ? S.Mh[r + 1][1] : &S.Mm[r + 1][c * kMBlock]);
+        };
+        const T* Mn[4] = {blk(tx - 1, ty) + 9, blk(tx + 1, ty - 1) + 18, blk(tx, ty - 1) + 27,
+                          blk(tx - 1, ty - 1) + 36};
+        T cc[3], mv[3];
+        op_stencil<T, const T*>(f, blk(tx, ty), Mn, T(0.5 / g.dx), T(0.5 / g.dy), cc, mv);
+        const T td = T(g.theta * g.dt);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double bv = (double)(td * td * cc[k] + td * mv[k]);
+            if (MODE == kOpA) wv[k] = own[k] + bv;
+            else if (MODE == kOpResidual) wv[k] = b[(int64_t)k * nc + gidx] - (own[k] + bv);
+            else wv[k] = bv;
+            out[(int64_t)k * nc + gidx] = wv[k];
+            if (MODE == kOpArnoldi && vj) vj[(int64_t)k * nc + gidx] = own[k];
+        }
+    }
+    if (MODE == kOpA) return;
+
+    // per-tile dot products, kOpChunk at a time: every thread writes its
+    // products to shared memory, then each warp sums some of them
+    const int nq = MODE == kOpResidual ? 1 : nv + 2;
+    const int lane = tid & 31, wid = tid >> 5;
+    double* buf = reinterpret_cast<double*>(&S.Mm[0][0]);   // [kOpChunk][NT]
+    __syncthreads();   // the mass-matrix tile is no longer read
+    for (int q0 = 0; q0 < nq; q0 += kOpChunk) {
+        const int kc = min(kOpChunk, nq - q0);   // live sums in this pass (warp-uniform)
+        double vq[kOpChunk][3];
+#pragma unroll
+        for (int c = 0; c < kOpChunk; ++c) {
+            const int q = q0 + c;
+            const bool gl = MODE == kOpArnoldi && active && q < nv;
+            const double* Vq = V + (int64_t)(gl ? q : 0) * ldv + gidx;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) vq[c][k] = gl ? __ldg(Vq + (int64_t)k * nc) : 0.0;
+        }
+        // FP64 work only for the live sums: a branch, not predication (a
+        // predicated-off FP64 instruction still takes its slot on the pipe)
+#pragma unroll
+        for (int c = 0; c < kOpChunk; ++c) {
+            if (c >= kc) break;
+            const int q = q0 + c;
+            double d = 0.0;
+            if (active) {
+                if (MODE == kOpResidual || q == nv + 1) d = wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2];
+                else if (q == nv) d = wv[0] * own[0] + wv[1] * own[1] + wv[2] * own[2];
+                else d = wv[0] * vq[c][0] + wv[1] * vq[c][1] + wv[2] * vq[c][2];
+            }
+            buf[c * NT + tid] = d;
+        }
+        __syncthreads();
+        for (int c = wid; c < kc; c += NT / 32) {
+            double t = 0.0;
+#pragma unroll
+            for (int m = 0; m < NT / 32; ++m) t += buf[c * NT + m * 32 + lane];
+            t = warp_sum(t);
+            if (lane == 0) partial[(int64_t)blockIdx.x * nq + q0 + c] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -290,8 +471,10 @@ k_gm_dots(const double* __restrict__ V, int64_t ldv, int k0, int kc, const doubl
          e += (int64_t)gridDim.x * blockDim.x) {
         const double we = w[e];
 #pragma unroll
-        for (int c = 0; c < kDotChunk; ++c)
-            if (c < kc) acc[c] += V[(int64_t)(k0 + c) * ldv + e] * we;
+        for (int c = 0; c < kDotChunk; ++c) {
+            if (c >= kc) break;   // a branch: no predicated-off FP64 work
+            acc[c] += V[(int64_t)(k0 + c) * ldv + e] * we;
+        }
         if (with_ww) acc[kDotChunk] += we * we;
     }
     double out[kDotChunk + 1];
@@ -301,6 +484,8 @@ k_gm_dots(const double* __restrict__ V, int64_t ldv, int k0, int kc, const doubl
         if (with_ww) partial[(int64_t)blockIdx.x * stride + stride - 1] = out[kDotChunk];
     }
 }
+
+constexpr int kGmChunk = 8;   // basis vectors per group of independent loads
 
 __global__ void __launch_bounds__(kGmThreads)
 k_gm_update(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int k,
@@ -314,13 +499,58 @@ k_gm_update(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, i
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         double s = w[e];
-        for (int c = 0; c < k; ++c) s -= hs[c] * V[(int64_t)c * ldv + e];
+        for (int c0 = 0; c0 < k; c0 += kGmChunk) {
+            const int kc = min(kGmChunk, k - c0);
+            double vv[kGmChunk];
+#pragma unroll
+            for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
+#pragma unroll
+            for (int c = 0; c < kGmChunk; ++c) {
+                if (c >= kc) break;   // a branch: no predicated-off FP64 work
+                s -= hs[c0 + c] * vv[c];
+            }
+        }
         w[e] = s;
         acc += s * s;
     }
     double v[1] = {acc}, out[1];
     block_sum<1>(v, red, out);
     if (threadIdx.x == 0) partial[blockIdx.x] = out[0];
+}
+
+// Arnoldi update with the normalisation fused: v_{k} = (w - sum_{c<k} h_c V_c)/hn
+// with hn^2 = <w,w> - sum h_c^2 (h and <w,w> from the dot-product sums hw =
+// [h_0 .. h_{k-1}, <w,w>]; every block forms hn itself).
+__global__ void __launch_bounds__(kGmThreads)
+k_gm_update_scale(const double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int k,
+                  const double* __restrict__ hw, double* __restrict__ vout, int64_t n)
+{
+    __shared__ double hs[kMaxRestart + 1];
+    __shared__ double inv;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) hs[c] = hw[c];
+    if (threadIdx.x == 0) {
+        double h2 = hw[k];
+        for (int c = 0; c < k; ++c) h2 -= hw[c] * hw[c];
+        inv = h2 > 0.0 ? 1.0 / sqrt(h2) : 0.0;
+    }
+    __syncthreads();
+    const double sc = inv;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = w[e];
+        for (int c0 = 0; c0 < k; c0 += kGmChunk) {
+            const int kc = min(kGmChunk, k - c0);
+            double vv[kGmChunk];
+#pragma unroll
+            for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
+#pragma unroll
+            for (int c = 0; c < kGmChunk; ++c) {
+                if (c >= kc) break;   // a branch: no predicated-off FP64 work
+                s -= hs[c0 + c] * vv[c];
+            }
+        }
+        vout[e] = s * sc;
+    }
 }
 
 __global__ void k_gm_scale(double* dst, const double* __restrict__ src, double s, int64_t n)
@@ -356,7 +586,17 @@ __global__ void k_gm_combine(double* x, const double* __restrict__ V, int64_t ld
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         double s = x[e];
-        for (int c = 0; c < k; ++c) s += ys[c] * V[(int64_t)c * ldv + e];
+        for (int c0 = 0; c0 < k; c0 += kGmChunk) {
+            const int kc = min(kGmChunk, k - c0);
+            double vv[kGmChunk];
+#pragma unroll
+            for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
+#pragma unroll
+            for (int c = 0; c < kGmChunk; ++c) {
+                if (c >= kc) break;   // a branch: no predicated-off FP64 work
+                s += ys[c0 + c] * vv[c];
+            }
+        }
         x[e] = s;
     }
 }
@@ -385,6 +625,11 @@ int grid_for(int64_t n, int threads, int cap)
 }  // namespace
 
 int field_grid_blocks(GridP g) { return grid_for(g.ncell, kFieldThreads, 1 << 30); }
+int op_blocks(GridP g, int precision)
+{
+    const int X = 32, Y = precision == 32 ? OpTile<float>::Y : OpTile<double>::Y;
+    return ((g.nx + X - 1) / X) * ((g.ny + Y - 1) / Y);
+}
 int gm_blocks(int64_t n) { return grid_for(n, kGmThreads, 152 * 4); }
 
 template <typename T>
@@ -411,12 +656,48 @@ cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStre
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, cudaStream_t st)
+template <typename T, int MODE>
+cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
+                      const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st)
 {
+    // the dynamic shared-memory limit, set once per kernel and device
+    static std::atomic<unsigned> attr_set{0};
+    const int smem = (int)sizeof(OpShared<T>);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned bit = 1u << (dev & 31);
+    if (!(attr_set.load() & bit)) {
+        e = cudaFuncSetAttribute(k_op<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set.fetch_or(bit);
+    }
+    // bulk copies need every staged mass-matrix row to start on 16 bytes
+    const int tma = ((int64_t)g.nx * kMBlock * sizeof(T)) % 16 == 0 ? 1 : 0;
     count_launches(1);
-    k_apply_A<T><<<grid_for(g.ncell, kFieldThreads, 1 << 30), kFieldThreads, 0, st>>>(M, v, out, g);
+    k_op<T, MODE><<<op_blocks(g, sizeof(T) == 4 ? 32 : 64), OpTile<T>::threads, smem, st>>>(
+        M, in, sc, b, out, vj, V, ldv, nv, g, tma, partial, err);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, int* err, cudaStream_t st)
+{
+    return launch_op<T, kOpA>(M, v, 1.0, nullptr, out, nullptr, nullptr, 0, 0, g, nullptr, err, st);
+}
+
+template <typename T>
+cudaError_t op_residual(const T* M, const double* x, const double* b, double* r, GridP g, double* partial,
+                        int* err, cudaStream_t st)
+{
+    return launch_op<T, kOpResidual>(M, x, 1.0, b, r, nullptr, nullptr, 0, 0, g, partial, err, st);
+}
+
+template <typename T>
+cudaError_t op_arnoldi(const T* M, const double* u, double sc, double* vj, double* w, const double* V,
+                       int64_t ldv, int j, GridP g, double* partial, int* err, cudaStream_t st)
+{
+    return launch_op<T, kOpArnoldi>(M, u, sc, nullptr, w, vj, V, ldv, j, g, partial, err, st);
 }
 
 template <typename T>
@@ -477,6 +758,14 @@ cudaError_t gm_update(double* w, const double* V, int64_t ldv, int k, const doub
     return cudaGetLastError();
 }
 
+cudaError_t gm_update_scale(const double* w, const double* V, int64_t ldv, int k, const double* hw,
+                            double* vout, int64_t n, cudaStream_t st)
+{
+    count_launches(1);
+    k_gm_update_scale<<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(w, V, ldv, k, hw, vout, n);
+    return cudaGetLastError();
+}
+
 cudaError_t gm_scale(double* dst, const double* src, double s, int64_t n, cudaStream_t st)
 {
     count_launches(1);
@@ -512,7 +801,12 @@ cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, doubl
     template cudaError_t fields_from_double<T>(const double*, T*, int64_t, int*, cudaStream_t);   \
     template cudaError_t fields_to_double<T>(const T*, double*, int64_t, cudaStream_t);           \
     template cudaError_t rhs<T>(const T*, const T*, const T*, double*, GridP, cudaStream_t);      \
-    template cudaError_t apply_A<T>(const T*, const double*, double*, GridP, cudaStream_t);       \
+    template cudaError_t apply_A<T>(const T*, const double*, double*, GridP, int*, cudaStream_t); \
+    template cudaError_t op_residual<T>(const T*, const double*, const double*, double*, GridP,    \
+                                        double*, int*, cudaStream_t);                             \
+    template cudaError_t op_arnoldi<T>(const T*, const double*, double, double*, double*,         \
+                                       const double*, int64_t, int, GridP, double*, int*,          \
+                                       cudaStream_t);                                             \
     template cudaError_t field_update<T>(const double*, const T*, const T*, T*, T*, const T*, T*, \
                                          GridP, double*, int, cudaStream_t);                      \
     template cudaError_t field_energy<T>(const T*, const T*, GridP, double*, int, cudaStream_t);  \

@@ -101,8 +101,22 @@ template <typename T>
 cudaError_t fields_to_double(const T* in, double* out, int64_t n, cudaStream_t st);
 template <typename T>
 cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStream_t st);
+// The implicit operator A = I + B, B = (theta dt)^2 curl_n curl_c + theta dt M,
+// on shared-memory tiles; err gets bit 2 if a staging wait gave up.
+// out = A v:
 template <typename T>
-cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, cudaStream_t st);
+cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, int* err, cudaStream_t st);
+// r = b - A x and per-tile partials of |r|^2 (op_blocks(g) of them):
+template <typename T>
+cudaError_t op_residual(const T* M, const double* x, const double* b, double* r, GridP g, double* partial,
+                        int* err, cudaStream_t st);
+// one Arnoldi step on B: v_j = sc u is written to vj (if not null), w = B v_j,
+// and per tile the j+2 partials <w, V_q> (q < j), <w, v_j>, <w, w> (row
+// stride j+2):
+template <typename T>
+cudaError_t op_arnoldi(const T* M, const double* u, double sc, double* vj, double* w, const double* V,
+                       int64_t ldv, int j, GridP g, double* partial, int* err, cudaStream_t st);
+int op_blocks(GridP g, int precision);
 template <typename T>
 cudaError_t field_update(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0,
                          T* B1, GridP g, double* partial, int nblocks, cudaStream_t st);
@@ -123,6 +137,9 @@ cudaError_t gm_dots(const double* V, int64_t ldv, int k, const double* w, int64_
 cudaError_t gm_update(double* w, const double* V, int64_t ldv, int k, const double* h,
                       int64_t n, double* partial, int nblocks, cudaStream_t st);  // w -= V h; |w|^2
 cudaError_t gm_scale(double* dst, const double* src, double s, int64_t n, cudaStream_t st);
+// vout = (w - V h)/hn with hn^2 = hw[k] - |h|^2, h = hw[0..k-1]
+cudaError_t gm_update_scale(const double* w, const double* V, int64_t ldv, int k, const double* hw,
+                            double* vout, int64_t n, cudaStream_t st);
 cudaError_t gm_sub(double* r, const double* b, const double* Ax, int64_t n, double* partial,
                    int nblocks, cudaStream_t st);                      // r = b - Ax; |r|^2
 cudaError_t gm_combine(double* x, const double* V, int64_t ldv, int k, const double* y,

@@ -226,48 +226,6 @@ constexpr int kDepBuf = 2;                             // stages in flight
 constexpr long long kDepMaxPolls = 1ll << 26;          // bounded mbarrier wait
 static_assert(kDepCells == kUnitW, "one group of lanes per cell of a unit");
 
-__device__ __forceinline__ unsigned smem_u32(const void* p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* mb, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx_arrive(uint64_t* mb, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* mb)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(mb))
-        : "memory");
-}
-
-// bounded wait on the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity)
-{
-    const unsigned a = smem_u32(mb);
-    for (long long it = 0; it < kDepMaxPolls; ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 // Register accumulators of one lane: 81 moments S[k][e] and 12 currents.
 // The FP32 form packs pairs of alpha' entries so the moment update is 45
 // paired FMAs (__ffma2_rn) instead of 81.
@@ -449,7 +407,7 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
             acc.zero();
             load_tile_B<T>(sB, B, un, nx, ny, nc, tid, kDepThreads);
         }
-        const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1));
+        const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1), kDepMaxPolls);
         // leave together if any thread gave up (never diverge at a barrier);
         // the barrier also publishes the B tile
         if (__syncthreads_or(!ok)) {
@@ -501,7 +459,7 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
     if (kfail >= 0 && tid == 0) {
         atomicOr(err, 2);
         // let the copies already issued land before the CTA leaves (bounded)
-        for (int kk = kfail; kk < nstages && kk < kfail + NB; ++kk) mbar_wait(&mbar[kk % NB], (kk / NB) & 1);
+        for (int kk = kfail; kk < nstages && kk < kfail + NB; ++kk) mbar_wait(&mbar[kk % NB], (kk / NB) & 1, kDepMaxPolls);
     }
 }
 
