@@ -158,13 +158,13 @@ def traffic_record(kernel):
 
 
 def algorithmic_bytes(slot, n_particles, n_per_species, ncell, esz):
-    """Bytes a launch of the slot must move (what the method reads/writes)."""
-    if slot == "deposit":       # read x-offsets, u, w; write M (45) + Jhat (3) per node
+    """Bytes a launch of the slot must move (what its job reads and writes)."""
+    if slot == "deposit":       # read offsets, u, w; write M (45) + Jhat (3) per node
         return n_particles * 6 * esz + ncell * 48 * esz
-    if slot == "push_count":    # per species: read offsets, u, w; write moves per cell
-        return n_per_species * 6 * esz + ncell * 9 * 4
-    if slot == "push_scatter":  # per species: read + write the particle record
+    if slot == "push":          # per species: read + write the particle record; runs per cell
         return n_per_species * 12 * esz + ncell * 18 * 4
+    if slot == "permute":       # per species: read + write the particle record; run tables
+        return n_per_species * 12 * esz + ncell * 19 * 4
     if slot == "gmres_apply":   # M, v (FP64 in), Av (FP64 out)
         return ncell * (45 * esz + 24 + 24)
     if slot == "field_update":
@@ -252,11 +252,11 @@ def run_ours(args):
                 "traffic": traffic_record(dom), "algorithmic_bytes_per_launch": ab,
                 "launch_ms": launch_ms}
     # the mover + mass-matrix kernels together (deposit, push passes, sort tables)
-    mover = ("deposit", "push_count", "sort_tables", "push_scatter")
+    mover = ("deposit", "push", "sort_tables", "permute")
     mover_ms = sum(per_kernel[k]["ms_per_step"] for k in mover if k in per_kernel)
     mover_bytes = (algorithmic_bytes("deposit", N, 0, ncell, esz)
-                   + sum(algorithmic_bytes("push_count", 0, n, ncell, esz)
-                         + algorithmic_bytes("push_scatter", 0, n, ncell, esz) for n in n_per))
+                   + sum(algorithmic_bytes("push", 0, n, ncell, esz)
+                         + algorithmic_bytes("permute", 0, n, ncell, esz) for n in n_per))
     mover_gbs = mover_bytes / (mover_ms / 1e3) / 1e9
     last = ledgers[-1]
     out = {

@@ -63,6 +63,13 @@
 
 #include <stdint.h>
 
+/* the library exports these entry points and nothing else */
+#if defined(__GNUC__)
+#define RELSIM_API __attribute__((visibility("default")))
+#else
+#define RELSIM_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -125,14 +132,14 @@ typedef struct {
    cfg: see relsim_config. cuda_stream: a cudaStream_t (or 0). On success
    *out receives the context. Errors: INVALID_ARG (bad config), CUDA, OOM.
    Allocates the grid arrays (fields, Jhat, M, GMRES basis) up front. */
-int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out);
+RELSIM_API int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out);
 
 /* Free every device buffer of the context and the context itself. Safe on
    NULL. Synchronises the context's stream first. */
-void relsim_destroy(relsim_ctx* ctx);
+RELSIM_API void relsim_destroy(relsim_ctx* ctx);
 
 /* Message of the last error on this context ("" if none). Owned by ctx. */
-const char* relsim_last_error(const relsim_ctx* ctx);
+RELSIM_API const char* relsim_last_error(const relsim_ctx* ctx);
 
 /* Load (replace) the particles of one species: n particles, positions x[2n],
    momenta u[3n], weights w[n], all FP64 (layout above). Positions outside
@@ -142,48 +149,48 @@ const char* relsim_last_error(const relsim_ctx* ctx);
    species. Errors: INVALID_ARG (species out of range, n < 0 or > 2^31-1,
    NULL arrays with n > 0), NONFINITE (NaN/Inf in the input), OOM, CUDA.
    Resets the step state: the next call must be relsim_build_mass_matrix. */
-int relsim_load_particles(relsim_ctx* ctx, int species, int64_t n, const double* x,
+RELSIM_API int relsim_load_particles(relsim_ctx* ctx, int species, int64_t n, const double* x,
                           const double* u, const double* w, int where);
 
 /* Set E^n on nodes and B^n on cell centres (each 3*ncell FP64, layout above).
    Either pointer may be NULL to keep that field. Resets the step state.
    Errors: INVALID_ARG, NONFINITE, CUDA. */
-int relsim_set_fields(relsim_ctx* ctx, const double* E, const double* B, int where);
+RELSIM_API int relsim_set_fields(relsim_ctx* ctx, const double* E, const double* B, int where);
 
 /* Copy the current E and B (after a solve: E^{n+1}, B^{n+1}) out as FP64.
    Either pointer may be NULL. Errors: INVALID_ARG, CUDA. */
-int relsim_get_fields(relsim_ctx* ctx, double* E, double* B, int where);
+RELSIM_API int relsim_get_fields(relsim_ctx* ctx, double* E, double* B, int where);
 
 /* Number of particles of a species. */
-int relsim_num_particles(relsim_ctx* ctx, int species, int64_t* n);
+RELSIM_API int relsim_num_particles(relsim_ctx* ctx, int species, int64_t* n);
 
 /* Copy the particles of a species out, in the library's current order
    (sorted by cell, stable), as FP64 x[2n], u[3n], w[n] and, if ids are
    tracked, id[n] (each pointer may be NULL to skip it). Positions are
    absolute. Errors: INVALID_ARG (species out of range, id requested but not
    tracked), CUDA. */
-int relsim_get_particles(relsim_ctx* ctx, int species, double* x, double* u, double* w,
+RELSIM_API int relsim_get_particles(relsim_ctx* ctx, int species, double* x, double* u, double* w,
                          int32_t* id, int where);
 
 /* Start index of each cell's particles of a species in the current order:
    start[ncell+1], start[ncell] = n. Errors: INVALID_ARG, CUDA. */
-int relsim_get_cell_start(relsim_ctx* ctx, int species, int64_t* start, int where);
+RELSIM_API int relsim_get_cell_start(relsim_ctx* ctx, int species, int64_t* start, int where);
 
 /* Step part 1: gather B^n, form alpha per particle, deposit Jhat and M.
    Allowed after load/set_fields or a push. Errors: BAD_STATE, CUDA. */
-int relsim_build_mass_matrix(relsim_ctx* ctx);
+RELSIM_API int relsim_build_mass_matrix(relsim_ctx* ctx);
 
 /* The deposited Jhat (3*ncell, component-major) and M, stored for the five
    neighbour offsets o in {(0,0), (1,0), (-1,1), (0,1), (1,1)} as
    M[(g*5 + k)*9 + r*3 + s] = block (r,s) of M_{g, g+o_k}; the other four
    offsets follow from M_{g+o,g} = M_{g,g+o}. FP64 out. Either pointer may
    be NULL. Errors: BAD_STATE (nothing built), INVALID_ARG, CUDA. */
-int relsim_get_mass_matrix(relsim_ctx* ctx, double* M, double* J, int where);
+RELSIM_API int relsim_get_mass_matrix(relsim_ctx* ctx, double* M, double* J, int where);
 
 /* Replace the built Jhat and M by caller values (same layouts as
    relsim_get_mass_matrix), e.g. to drive the field solve on its own.
    Leaves the context in the built state. Errors: INVALID_ARG, CUDA. */
-int relsim_set_mass_matrix(relsim_ctx* ctx, const double* M, const double* J, int where);
+RELSIM_API int relsim_set_mass_matrix(relsim_ctx* ctx, const double* M, const double* J, int where);
 
 /* Step part 2: GMRES solve for E^{n+theta}, then E^{n+1}, B^{n+1}.
    *iters (may be NULL) receives the Arnoldi steps, *rel_residual (may be
@@ -191,43 +198,44 @@ int relsim_set_mass_matrix(relsim_ctx* ctx, const double* M, const double* J, in
    loop checks convergence on the host). Errors: BAD_STATE (not built),
    NOT_CONVERGED (gmres_maxit reached; the fields are still advanced with
    the best iterate), NONFINITE, CUDA. */
-int relsim_field_solve(relsim_ctx* ctx, int* iters, double* rel_residual);
+RELSIM_API int relsim_field_solve(relsim_ctx* ctx, int* iters, double* rel_residual);
 
 /* E^{n+theta} of the last solve (3*ncell FP64). Errors: BAD_STATE, CUDA. */
-int relsim_get_E_theta(relsim_ctx* ctx, double* E, int where);
+RELSIM_API int relsim_get_E_theta(relsim_ctx* ctx, double* E, int where);
 
 /* Apply the implicit operator A = I + (theta dt)^2 curl_n curl_c + theta dt M
    of the built mass matrix to v (3*ncell FP64, device or host per where),
    writing out (same layout). Errors: BAD_STATE, INVALID_ARG, CUDA. */
-int relsim_apply_operator(relsim_ctx* ctx, const double* v, double* out, int where);
+RELSIM_API int relsim_apply_operator(relsim_ctx* ctx, const double* v, double* out, int where);
 
 /* Step part 3: push velocities and positions of every species with
    E^{n+theta} and B^n, then sort each species by its new cells. Also
    accumulates the particle terms of the energy ledger. Allowed after a
    solve. Errors: BAD_STATE, CUDA. */
-int relsim_push(relsim_ctx* ctx);
+RELSIM_API int relsim_push(relsim_ctx* ctx);
 
 /* Energy ledger of the current state and of the last step (FP64 struct,
    caller-owned). Synchronises the stream. Errors: INVALID_ARG, NONFINITE
    (NaN/Inf in an energy), CUDA. */
-int relsim_energy_ledger(relsim_ctx* ctx, relsim_energy* out);
+RELSIM_API int relsim_energy_ledger(relsim_ctx* ctx, relsim_energy* out);
 
 /* One full step: build, solve, push; fills *ledger if it is non-NULL.
    Returns the first error of its parts (NOT_CONVERGED still completes the
    step). */
-int relsim_step(relsim_ctx* ctx, relsim_energy* ledger);
+RELSIM_API int relsim_step(relsim_ctx* ctx, relsim_energy* ledger);
 
 /* Library version (major*10000 + minor*100 + patch). */
-int relsim_version(void);
+RELSIM_API int relsim_version(void);
 
 /* ---- profiling (the paper has no counterpart; a measurement aid) ----
    When enabled, the library records a CUDA event pair on its stream around
    each group of kernel launches below and accumulates the elapsed device
    time per group. Slots: */
 #define RELSIM_PROF_DEPOSIT 0      /* zero M/Jhat + the deposit kernel          */
-#define RELSIM_PROF_PUSH_COUNT 1   /* push pass 1: moves per cell + ledger sums */
-#define RELSIM_PROF_SORT_TABLES 2  /* new-cell counts, scan, move offsets      */
-#define RELSIM_PROF_PUSH_SCATTER 3 /* push pass 2: write to sorted slots       */
+#define RELSIM_PROF_PUSH 1         /* push; each old cell written back grouped
+                                      by move direction; ledger sums          */
+#define RELSIM_PROF_SORT_TABLES 2  /* new-cell counts and their scan           */
+#define RELSIM_PROF_PERMUTE 3      /* the pushed particles into new-cell order */
 #define RELSIM_PROF_GMRES_APPLY 4  /* operator applications in GMRES           */
 #define RELSIM_PROF_GMRES_ORTHO 5  /* Gram-Schmidt, norms, basis updates       */
 #define RELSIM_PROF_FIELD_UPDATE 6 /* E^{n+1}, B^{n+1}, field ledger terms     */
@@ -243,15 +251,15 @@ typedef struct {
 } relsim_profile;
 
 /* Turn event timing on (nonzero) or off. Errors: INVALID_ARG, CUDA. */
-int relsim_profile_enable(relsim_ctx* ctx, int on);
+RELSIM_API int relsim_profile_enable(relsim_ctx* ctx, int on);
 
 /* Read the accumulated times (synchronises the stream); reset != 0 clears
    them afterwards. Errors: INVALID_ARG, CUDA. */
-int relsim_profile_read(relsim_ctx* ctx, relsim_profile* out, int reset);
+RELSIM_API int relsim_profile_read(relsim_ctx* ctx, relsim_profile* out, int reset);
 
 /* Total kernel launches made by this library in this process (all
    contexts), for counting the kernels of a timed region. */
-int64_t relsim_kernel_launches(void);
+RELSIM_API int64_t relsim_kernel_launches(void);
 
 /* ---- allocation-free kinetic energy (the paper has no counterpart) ----
    For callers that cannot allocate device memory where they need this
@@ -281,7 +289,7 @@ int64_t relsim_kernel_launches(void);
    the results), CUDA (launch failure or no current device). */
 #define RELSIM_ERR_TOO_LARGE (-9)
 #define RELSIM_NOALLOC_MAX_PARTICLES 33554432   /* 4096 blocks x 8192 particles */
-int relsim_kinetic_energy_noalloc(const double* u, const double* w, int64_t n, double m,
+RELSIM_API int relsim_kinetic_energy_noalloc(const double* u, const double* w, int64_t n, double m,
                                   double* out, void* cuda_stream);
 
 #ifdef __cplusplus

@@ -119,7 +119,7 @@ _SIGS = {
     "relsim_kinetic_energy_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
 }
 
-PROFILE_SLOTS = ("deposit", "push_count", "sort_tables", "push_scatter", "gmres_apply",
+PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
                  "gmres_ortho", "field_update", "rhs", "load", "general_sort")
 
 

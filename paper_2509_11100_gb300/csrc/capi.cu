@@ -648,23 +648,22 @@ int push_impl(relsim_ctx* c)
         PArrays<T> src = arrays<T>(sp, sp.cur), dst = arrays<T>(sp, 1 - sp.cur);
         const T* Eth = (const T*)c->Eth;
         const T* B = (const T*)c->B[c->bcur];
-        PROF_BEGIN(RELSIM_PROF_PUSH_COUNT);
-        CK(push<T>(0, src, dst, sp.start, c->n9, nullptr, nullptr, Eth, B, c->g, sc, c->partial, nbp,
-                   sp.n, c->dpush, c->st));
-        CK(reduce_partials(c->partial, nbp, kLedgerSpecies, led, c->st));
-        PROF_END();
         if (c->fast_sort) {
+            // push, each old cell written back grouped by move direction
+            // into the other buffer; then the stable new-cell order back into
+            // the current buffer
+            PROF_BEGIN(RELSIM_PROF_PUSH);
+            CK(push_sort<T>(src, dst, sp.start, c->n9, c->off9, Eth, B, c->g, sc, c->partial, nbp, c->st));
+            CK(reduce_partials(c->partial, nbp, kLedgerSpecies, led, c->st));
+            PROF_END();
             PROF_BEGIN(RELSIM_PROF_SORT_TABLES);
             CK(move_counts(c->n9, c->count_new, c->g, c->st));
             CK(scan_exclusive_i32(c->count_new, sp.start_alt, c->g.ncell, sp.start_alt + c->g.ncell,
                                   c->scan_tmp, c->st));
-            CK(move_offsets(c->n9, sp.start_alt, c->off9, c->g, c->st));
             PROF_END();
-            PROF_BEGIN(RELSIM_PROF_PUSH_SCATTER);
-            CK(push<T>(1, src, dst, sp.start, c->n9, c->off9, nullptr, Eth, B, c->g, sc, c->partial,
-                       nbp, sp.n, c->dpush, c->st));
+            PROF_BEGIN(RELSIM_PROF_PERMUTE);
+            CK(permute<T>(dst, src, sp.start_alt, c->n9, c->off9, c->g, c->dpush, c->st));
             PROF_END();
-            sp.cur = 1 - sp.cur;
             int32_t* t = sp.start;
             sp.start = sp.start_alt;
             sp.start_alt = t;
@@ -672,8 +671,8 @@ int push_impl(relsim_ctx* c)
             // general path: push in place order with keys, radix sort, gather
             TRY(ensure_radix(c, sp.n));
             PROF_BEGIN(RELSIM_PROF_GENERAL_SORT);
-            CK(push<T>(2, src, dst, sp.start, c->n9, nullptr, c->rk[0], Eth, B, c->g, sc, c->partial,
-                       nbp, sp.n, c->dpush, c->st));
+            CK(push_general<T>(src, dst, sp.start, c->rk[0], Eth, B, c->g, sc, c->partial, nbp, c->st));
+            CK(reduce_partials(c->partial, nbp, kLedgerSpecies, led, c->st));
             CK(iota_i32(c->rv[0], sp.n, c->st));
             bool in1 = false;
             CK(radix_sort_pairs(c->rk[0], c->rv[0], c->rk[1], c->rv[1], sp.n, c->key_bits, c->rtmp,
@@ -698,7 +697,7 @@ int check_push(relsim_ctx* c)
     if (*c->hpush & 2)
         return fail(c, RELSIM_ERR_TIMEOUT, "a shared-memory staging wait gave up (deposit or operator)");
     if (*c->hpush)
-        return fail(c, RELSIM_ERR_INTERNAL, "particle sort: count and scatter passes disagreed");
+        return fail(c, RELSIM_ERR_INTERNAL, "particle sort: the moves counted and the new cell starts disagreed");
     return RELSIM_OK;
 }
 

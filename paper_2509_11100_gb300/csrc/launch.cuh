@@ -60,10 +60,8 @@ cudaError_t radix_sort_pairs(int32_t* k0, int32_t* v0, int32_t* k1, int32_t* v1,
 // counts[k] = #keys equal to k (counts zeroed inside)
 cudaError_t histogram_keys(const int32_t* keys, int64_t n, int32_t* counts, int nkeys,
                            cudaStream_t st);
-// new-cell counts and destination offsets of the neighbour-move sort
+// new-cell counts of the neighbour-move sort
 cudaError_t move_counts(const int32_t* n9, int32_t* count_new, GridP g, cudaStream_t st);
-cudaError_t move_offsets(const int32_t* n9, const int32_t* start_new, int32_t* off9, GridP g,
-                         cudaStream_t st);
 cudaError_t iota_i32(int32_t* a, int64_t n, cudaStream_t st);
 
 // ----- particles.cu -----
@@ -79,16 +77,25 @@ cudaError_t export_particles(PArrays<T> p, const int32_t* start, GridP g, double
 template <typename T>
 cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g, int* err,
                     cudaStream_t st);
-// phase 0: count moves per (old cell, direction) into n9 and accumulate the
-//          particle ledger sums (K0, dK, work, mismatch, K1) into lsum;
-// phase 1: write each pushed particle to its sorted slot off9[new][dir] + rank;
-// phase 2: write pushed particles in place order to dst plus their new cell
-//          key (general sort path for moves longer than one cell).
+// push with the cell-local sort: each old cell's pushed particles are written
+// back over the cell's own index range in dst grouped by move direction d;
+// n9[c][d] and off9[c][d] receive the count and the start of each run; the
+// particle ledger sums (K0, dK, work, mismatch, K1) go to lsum (per block).
 template <typename T>
-cudaError_t push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* n9,
-                 const int32_t* off9, int32_t* key, const T* Eth, const T* B, GridP g,
-                 SpeciesConst sc, double* lsum_partial, int lsum_blocks, int64_t npart, int* err,
-                 cudaStream_t st);
+cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* n9, int32_t* off9,
+                      const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
+                      cudaStream_t st);
+// general path (moves longer than one cell): pushed particles to the same
+// index of dst, their new cell to key; ledger sums as above
+template <typename T>
+cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, const T* Eth,
+                         const T* B, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
+                         cudaStream_t st);
+// the stable new-cell order from the runs of push_sort (err bit 1 if the
+// runs and the new cell starts disagree)
+template <typename T>
+cudaError_t permute(PArrays<T> src, PArrays<T> dst, const int32_t* start_new, const int32_t* n9,
+                    const int32_t* off9, GridP g, int* err, cudaStream_t st);
 int push_grid_blocks(GridP g, int precision);
 template <typename T>
 cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, int nblocks,

@@ -122,29 +122,37 @@ __device__ __forceinline__ Unit unit_of(int u, int nx)
 
 __host__ __device__ __forceinline__ int units_of(int nx, int ny) { return ny * ((nx + kUnitW - 1) / kUnitW); }
 
-// B^n on the centres around a unit: [comp][row j-1, j, j+1][col i0-1 .. i0+cn]
-template <typename T>
+// B^n on the centres around a unit: [comp][row j-1, j, j+1][col i0-1 .. i0+cn].
+// NTHR threads (tid < NTHR) share the loads; for a warp the loop unrolls so
+// its loads issue together.
+template <typename T, int NTHR>
 __device__ __forceinline__ void load_tile_B(T (*sB)[3][kTB], const T* __restrict__ B, const Unit& un, int nx,
-                                            int ny, int nc, int tid, int nthr)
+                                            int ny, int nc, int tid)
 {
-    for (int idx = tid; idx < 9 * kTB; idx += nthr) {
+#pragma unroll(NTHR < 128 ? 16 : 1)
+    for (int idx0 = 0; idx0 < 9 * kTB; idx0 += NTHR) {
+        const int idx = idx0 + tid;
         const int comp = idx / (3 * kTB), r = (idx / kTB) % 3, col = idx % kTB;
-        if (col > un.cn + 1) continue;
-        const int gi = wrap1(un.i0 - 1 + col, nx), gj = wrap1(un.j - 1 + r, ny);
-        sB[comp][r][col] = ld(B + comp * nc + gj * nx + gi);
+        if (idx < 9 * kTB && col <= un.cn + 1) {
+            const int gi = wrap1(un.i0 - 1 + col, nx), gj = wrap1(un.j - 1 + r, ny);
+            sB[comp][r][col] = ld(B + comp * nc + gj * nx + gi);
+        }
     }
 }
 
 // E^{n+theta} on the nodes of a unit: [comp][row j, j+1][col i0 .. i0+cn]
-template <typename T>
+template <typename T, int NTHR>
 __device__ __forceinline__ void load_tile_E(T (*sE)[2][kTE], const T* __restrict__ E, const Unit& un, int nx,
-                                            int ny, int nc, int tid, int nthr)
+                                            int ny, int nc, int tid)
 {
-    for (int idx = tid; idx < 6 * kTE; idx += nthr) {
+#pragma unroll(NTHR < 128 ? 16 : 1)
+    for (int idx0 = 0; idx0 < 6 * kTE; idx0 += NTHR) {
+        const int idx = idx0 + tid;
         const int comp = idx / (2 * kTE), r = (idx / kTE) % 2, col = idx % kTE;
-        if (col > un.cn) continue;
-        const int gi = wrap1(un.i0 + col, nx), gj = wrap1(un.j + r, ny);
-        sE[comp][r][col] = ld(E + comp * nc + gj * nx + gi);
+        if (idx < 6 * kTE && col <= un.cn) {
+            const int gi = wrap1(un.i0 + col, nx), gj = wrap1(un.j + r, ny);
+            sE[comp][r][col] = ld(E + comp * nc + gj * nx + gi);
+        }
     }
 }
 
@@ -405,7 +413,7 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
         const int s = k % nsp;
         if (s == 0) {
             acc.zero();
-            load_tile_B<T>(sB, B, un, nx, ny, nc, tid, kDepThreads);
+            load_tile_B<T, kDepThreads>(sB, B, un, nx, ny, nc, tid);
         }
         const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1), kDepMaxPolls);
         // leave together if any thread gave up (never diverge at a barrier);
@@ -465,20 +473,28 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
 
 // ---------------------------------------------------------------------------
 // push. A warp owns a unit (a row segment of up to 32 cells), whose particles
-// are one contiguous range of the sorted arrays; its lanes stream that range
-// in order, kPushUnroll batches of 32 at a time (coalesced, independent
-// loads), follow the cell of each particle from a shared copy of the unit's
-// cell starts, and gather E^{n+theta} and B^n from the unit's shared field
-// tile. Counts and ranks per (old cell, direction) are warp-aggregated in
-// shared memory in particle order, so ranks follow the old order (the stable
-// sort).
+// are one contiguous range of the sorted arrays, and gathers E^{n+theta} and
+// B^n from the unit's shared field tile.
+//
+// The re-sort by the new cell takes two kernels. k_push_sort pushes each
+// cell's particles once (batches of 32 lanes), ranks them per move
+// direction d = (sy+1)*3 + (sx+1) with ballots (in particle order), keeps the
+// pushed records in shared memory and writes the cell back over its own
+// index range grouped by direction (coalesced stores). Runs (old cell c,
+// direction d) are then contiguous: n9[c][d] particles starting at
+// off9[c][d]. k_permute builds the new order: the particles of new cell k
+// are the nine runs that end in k, in ascending order of their old cell
+// (the stable counting sort), copied with coalesced stores. A particle moves
+// at most one cell per step when c dt <= min(dx, dy); otherwise the library
+// takes the general path (k_push_general + radix sort).
 
 template <typename T> struct PushCfg {
-    static constexpr int warps = sizeof(T) == 4 ? 8 : 4;   // static shared memory < 48 KB
+    static constexpr int warps = 4;                        // static shared memory < 48 KB
     static constexpr int threads = 32 * warps;
+    static constexpr int min_blocks = sizeof(T) == 4 ? 6 : 2;
 };
-constexpr int kPushUnroll = 2;
-constexpr int kLedger = 5;   // K0, dK, work, mismatch, K1
+constexpr int kPushCap = 128;   // particles of one cell staged per warp
+constexpr int kLedger = 5;      // K0, dK, work, mismatch, K1
 
 template <typename T>
 struct Pushed {
@@ -556,19 +572,75 @@ struct PushTile {
     T E[3][2][kTE];
 };
 
+// a cell's pushed particles, staged for the write back in direction order
 template <typename T>
-__global__ void __launch_bounds__(PushCfg<T>::threads)
-k_push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start,
-       int32_t* __restrict__ n9, const int32_t* __restrict__ off9, int32_t* __restrict__ key,
-       const T* __restrict__ Eth, const T* __restrict__ B, GridP g, T beta, T dt_dx, T dt_dy,
-       T qdt, T m, double* __restrict__ lsum, int npart, int* __restrict__ err)
+struct PushStage {
+    T fx[kPushCap], fy[kPushCap], ux[kPushCap], uy[kPushCap], uz[kPushCap], w[kPushCap];
+    int32_t id[kPushCap];
+    uint8_t dir[kPushCap], rank[kPushCap], inv[kPushCap];
+    int doff[kNDir + 1];
+    int run[kNDir];
+};
+
+template <typename T>
+__device__ __forceinline__ void block_ledger(const T (&acc)[kLedger], double* red, double* __restrict__ lsum)
+{
+    double v[kLedger], out[kLedger];
+#pragma unroll
+    for (int s = 0; s < kLedger; ++s) v[s] = (double)acc[s];
+    block_sum<kLedger>(v, red, out);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int s = 0; s < kLedger; ++s) lsum[(int64_t)blockIdx.x * kLedger + s] = out[s];
+}
+
+// load a unit's cell starts (ss[0..cn]) and field tiles
+template <typename T>
+__device__ __forceinline__ void unit_setup(const Unit& un, const int32_t* __restrict__ start, int* ss,
+                                           PushTile<T>& tl, const T* __restrict__ Eth, const T* __restrict__ B,
+                                           int nx, int ny, int nc, int lane)
+{
+#pragma unroll
+    for (int k0 = 0; k0 <= kUnitW; k0 += 32)
+        if (k0 + lane <= un.cn) ss[k0 + lane] = start[un.c0 + k0 + lane];
+    load_tile_B<T, 32>(tl.B, B, un, nx, ny, nc, lane);
+    load_tile_E<T, 32>(tl.E, Eth, un, nx, ny, nc, lane);
+    __syncwarp();
+}
+
+// lanes 0..9 store the exclusive prefix of the per-direction counts run[]:
+// doff[d] = run[0] + .. + run[d-1], doff[9] = the total
+__device__ __forceinline__ void store_doff(const int* run, int* doff, int lane)
+{
+    int v = 0;
+#pragma unroll
+    for (int d = 0; d < kNDir; ++d) v += d < lane ? run[d] : 0;
+    if (lane <= kNDir) doff[lane] = v;
+}
+
+// the lanes (of those active) whose move direction equals this lane's: one
+// ballot per bit of the direction code
+__device__ __forceinline__ unsigned dir_peers(bool act, int dir)
+{
+    unsigned m = __ballot_sync(0xffffffffu, act);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (dir >> b) & 1);
+        m &= ((dir >> b) & 1) ? bal : ~bal;
+    }
+    return m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PushCfg<T>::threads, PushCfg<T>::min_blocks)
+k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int32_t* __restrict__ n9,
+            int32_t* __restrict__ off9, const T* __restrict__ Eth, const T* __restrict__ B, GridP g, T beta,
+            T dt_dx, T dt_dy, T qdt, T m, double* __restrict__ lsum)
 {
     constexpr int W = PushCfg<T>::warps;
     __shared__ int sstart[W][kUnitW + 1];
-    __shared__ int scnt[W][kUnitW * kNDir];
-    // destinations of the unit's moves: [dest row j-1..j+1][dest col i0-1..i0+cn][sx+1]
-    __shared__ int soff[W][3][kTB][3];
     __shared__ PushTile<T> stile[W];
+    __shared__ PushStage<T> sstage[W];
     __shared__ double red[32 * kLedger];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -577,123 +649,264 @@ k_push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ st
     const int nunits = units_of(nx, ny);
     const unsigned lt = (1u << lane) - 1u;
     int* ss = sstart[wib];
-    int* sc = scnt[wib];
     PushTile<T>& tl = stile[wib];
+    PushStage<T>& st = sstage[wib];
+    const bool ids = dst.id != nullptr;
     T acc[kLedger] = {T(0), T(0), T(0), T(0), T(0)};
 
     for (int u = warp; u < nunits; u += nwarps) {
         const Unit un = unit_of(u, nx);
-        const int cn = un.cn, c0 = un.c0;
-        for (int k = lane; k <= cn; k += 32) ss[k] = start[c0 + k];
-        for (int k = lane; k < cn * kNDir; k += 32) sc[k] = 0;
-        load_tile_B<T>(tl.B, B, un, nx, ny, nc, lane, 32);
-        load_tile_E<T>(tl.E, Eth, un, nx, ny, nc, lane, 32);
-        if (phase == 1) {
-            int* so = &soff[wib][0][0][0];
-            for (int idx = lane; idx < 9 * kTB; idx += 32) {
-                const int r = idx / (3 * kTB), col = (idx / 3) % kTB, sxi = idx % 3;
-                if (col > cn + 1) continue;
-                const int k = wrap1(un.j - 1 + r, ny) * nx + wrap1(un.i0 - 1 + col, nx);
-                so[idx] = off9[(int64_t)k * kNDir + r * 3 + sxi];
+        unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
+        for (int l = 0; l < un.cn; ++l) {
+            const int s0 = ss[l], s1 = ss[l + 1], np = s1 - s0;
+            int* run = st.run;   // particles of this cell per direction so far
+            if (lane < kNDir) run[lane] = 0;
+            __syncwarp();
+            const bool staged = np <= kPushCap;
+            // big cells take a counting pass first (no ledger, nothing written)
+            for (int b0 = s0; !staged && b0 < s1; b0 += 32) {
+                const int p = b0 + lane;
+                const bool act = p < s1;
+                const int q = act ? p : s0;
+                Pushed<T> o;
+                push_particle<T>(ld(src.fx + q), ld(src.fy + q), ld(src.ux + q), ld(src.uy + q), ld(src.uz + q),
+                                 ld(src.w + q), l, tl.E, tl.B, beta, dt_dx, dt_dy, qdt, m, true, false, acc, o);
+                const unsigned peers = dir_peers(act, o.dir);
+                if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
+                __syncwarp();
             }
-        }
-        __syncwarp();
-        const int P0 = ss[0], P1 = ss[cn];
-        int cl = 0;   // the lane's current local cell (particles ascend)
-        for (int base = P0; base < P1; base += 32 * kPushUnroll) {
-            Pushed<T> o[kPushUnroll];
-            int cls[kPushUnroll], pp[kPushUnroll];
-            bool act[kPushUnroll];
-            T fx[kPushUnroll], fy[kPushUnroll], ux[kPushUnroll], uy[kPushUnroll], uz[kPushUnroll],
-                w[kPushUnroll];
-#pragma unroll
-            for (int v = 0; v < kPushUnroll; ++v) {
-                pp[v] = base + 32 * v + lane;
-                act[v] = pp[v] < P1;
-                const int q = act[v] ? pp[v] : P0;
-                fx[v] = ld(src.fx + q);
-                fy[v] = ld(src.fy + q);
-                ux[v] = ld(src.ux + q);
-                uy[v] = ld(src.uy + q);
-                uz[v] = ld(src.uz + q);
-                w[v] = ld(src.w + q);
+            if (!staged) {
+                store_doff(run, st.doff, lane);
+                __syncwarp();
+                if (lane < kNDir) run[lane] = 0;
+                __syncwarp();
             }
+            // the pass that ranks (and stages or writes) every particle
+            for (int b0 = s0; b0 < s1; b0 += 32) {
+                const int p = b0 + lane;
+                const bool act = p < s1;
+                const int q = act ? p : s0;
+                const T fx = ld(src.fx + q), fy = ld(src.fy + q), ux = ld(src.ux + q), uy = ld(src.uy + q),
+                        uz = ld(src.uz + q), w = ld(src.w + q);
+                Pushed<T> o;
+                T lacc[kLedger] = {T(0), T(0), T(0), T(0), T(0)};
+                push_particle<T>(fx, fy, ux, uy, uz, w, l, tl.E, tl.B, beta, dt_dx, dt_dy, qdt, m, true, true, lacc,
+                                 o);
+                if (act)
 #pragma unroll
-            for (int v = 0; v < kPushUnroll; ++v) {
-                cls[v] = 0;
-                o[v].dir = kNDir;
-                if (act[v]) {
-                    while (ss[cl + 1] <= pp[v]) ++cl;
-                    cls[v] = cl;
-                    push_particle<T>(fx[v], fy[v], ux[v], uy[v], uz[v], w[v], cl, tl.E, tl.B, beta, dt_dx,
-                                     dt_dy, qdt, m, phase != 2, phase == 0, acc, o[v]);
-                    if (phase == 2) o[v].dir = 0;
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < kPushUnroll; ++v) {
-                // (local cell, direction) key; inactive lanes get a key of their own
-                const int kk = act[v] ? cls[v] * kNDir + o[v].dir : (1 << 20) + lane;
-                const unsigned peers = __match_any_sync(0xffffffffu, kk);
-                const int rk = __popc(peers & lt);
-                if (phase == 0) {
-                    if (act[v] && rk == 0) sc[kk] += __popc(peers);
-                    __syncwarp();
-                } else if (phase == 1) {
-                    const int rb = act[v] ? sc[kk] : 0;
-                    __syncwarp();
-                    if (act[v] && rk == 0) sc[kk] = rb + __popc(peers);
-                    __syncwarp();
-                    if (act[v]) {
-                        const int dpos =
-                            soff[wib][o[v].sy + 1][cls[v] + 1 + o[v].sx][o[v].sx + 1] + rb + rk;
-                        if (dpos < 0 || dpos >= npart) {
-                            atomicOr(err, 1);
-                        } else {
-                            dst.fx[dpos] = o[v].fxn;
-                            dst.fy[dpos] = o[v].fyn;
-                            dst.ux[dpos] = o[v].u1x;
-                            dst.uy[dpos] = o[v].u1y;
-                            dst.uz[dpos] = o[v].u1z;
-                            dst.w[dpos] = o[v].w;
-                            if (dst.id) dst.id[dpos] = src.id[pp[v]];
-                        }
+                    for (int s = 0; s < kLedger; ++s) acc[s] += lacc[s];
+                // rank among the cell's particles of the same direction, in order
+                const unsigned peers = dir_peers(act, o.dir);
+                const int rank = (act ? run[o.dir] : 0) + __popc(peers & lt);
+                __syncwarp();
+                if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
+                __syncwarp();
+                if (act) {
+                    if (staged) {
+                        const int e = p - s0;
+                        st.fx[e] = o.fxn;
+                        st.fy[e] = o.fyn;
+                        st.ux[e] = o.u1x;
+                        st.uy[e] = o.u1y;
+                        st.uz[e] = o.u1z;
+                        st.w[e] = o.w;
+                        if (ids) st.id[e] = src.id[p];
+                        st.dir[e] = (uint8_t)o.dir;
+                        st.rank[e] = (uint8_t)rank;
+                    } else {
+                        const int pos = s0 + st.doff[o.dir] + rank;
+                        dst.fx[pos] = o.fxn;
+                        dst.fy[pos] = o.fyn;
+                        dst.ux[pos] = o.u1x;
+                        dst.uy[pos] = o.u1y;
+                        dst.uz[pos] = o.u1z;
+                        dst.w[pos] = o.w;
+                        if (ids) dst.id[pos] = src.id[p];
                     }
-                } else if (act[v]) {
-                    // general path: in place, with the new cell as sort key
-                    const int ci = un.i0 + cls[v], cj = un.j;
-                    int ni = (ci + o[v].sx) % nx, nj = (cj + o[v].sy) % ny;
-                    if (ni < 0) ni += nx;
-                    if (nj < 0) nj += ny;
-                    const int p = pp[v];
-                    dst.fx[p] = o[v].fxn;
-                    dst.fy[p] = o[v].fyn;
-                    dst.ux[p] = o[v].u1x;
-                    dst.uy[p] = o[v].u1y;
-                    dst.uz[p] = o[v].u1z;
-                    dst.w[p] = o[v].w;
-                    if (dst.id) dst.id[p] = src.id[p];
-                    key[p] = nj * nx + ni;
                 }
             }
+            if (staged) {
+                // direction offsets, the inverse permutation, then the
+                // coalesced write of the cell in direction order
+                store_doff(run, st.doff, lane);
+                __syncwarp();
+                for (int e = lane; e < np; e += 32) st.inv[st.doff[st.dir[e]] + st.rank[e]] = (uint8_t)e;
+                __syncwarp();
+                for (int qq = lane; qq < np; qq += 32) {
+                    const int e = st.inv[qq];
+                    dst.fx[s0 + qq] = st.fx[e];
+                    dst.fy[s0 + qq] = st.fy[e];
+                    dst.ux[s0 + qq] = st.ux[e];
+                    dst.uy[s0 + qq] = st.uy[e];
+                    dst.uz[s0 + qq] = st.uz[e];
+                    dst.w[s0 + qq] = st.w[e];
+                    if (ids) dst.id[s0 + qq] = st.id[e];
+                }
+            }
+            // the runs of this cell: counts and starts per direction
+            const int c = un.c0 + l;
+            if (lane < kNDir) {
+                n9[(int64_t)c * kNDir + lane] = st.doff[lane + 1] - st.doff[lane];
+                off9[(int64_t)c * kNDir + lane] = s0 + st.doff[lane];
+            }
+            __syncwarp();
         }
-        if (phase == 0)
-            for (int k = lane; k < cn * kNDir; k += 32) n9[(int64_t)c0 * kNDir + k] = sc[k];
-        if (phase == 1)
-            // the count pass and this pass must agree move by move; if they
-            // ever did not, say so (the writes stayed in bounds)
-            for (int k = lane; k < cn * kNDir; k += 32)
-                if (sc[k] != n9[(int64_t)c0 * kNDir + k]) atomicOr(err, 1);
+    }
+    block_ledger<T>(acc, red, lsum);
+}
+
+// General path (moves of more than one cell): push in place order, write the
+// pushed particle to the same index of dst and its new cell to key.
+template <typename T>
+__global__ void __launch_bounds__(PushCfg<T>::threads, PushCfg<T>::min_blocks)
+k_push_general(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int32_t* __restrict__ key,
+               const T* __restrict__ Eth, const T* __restrict__ B, GridP g, T beta, T dt_dx, T dt_dy, T qdt, T m,
+               double* __restrict__ lsum)
+{
+    constexpr int W = PushCfg<T>::warps;
+    __shared__ int sstart[W][kUnitW + 1];
+    __shared__ PushTile<T> stile[W];
+    __shared__ double red[32 * kLedger];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int nunits = units_of(nx, ny);
+    int* ss = sstart[wib];
+    PushTile<T>& tl = stile[wib];
+    T acc[kLedger] = {T(0), T(0), T(0), T(0), T(0)};
+    for (int u = warp; u < nunits; u += nwarps) {
+        const Unit un = unit_of(u, nx);
+        unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
+        const int P0 = ss[0], P1 = ss[un.cn];
+        int cl = 0;   // the lane's current local cell (particles ascend)
+        for (int p = P0 + lane; p < P1; p += 32) {
+            while (ss[cl + 1] <= p) ++cl;
+            Pushed<T> o;
+            push_particle<T>(ld(src.fx + p), ld(src.fy + p), ld(src.ux + p), ld(src.uy + p), ld(src.uz + p),
+                             ld(src.w + p), cl, tl.E, tl.B, beta, dt_dx, dt_dy, qdt, m, false, true, acc, o);
+            int ni = (un.i0 + cl + o.sx) % nx, nj = (un.j + o.sy) % ny;
+            if (ni < 0) ni += nx;
+            if (nj < 0) nj += ny;
+            dst.fx[p] = o.fxn;
+            dst.fy[p] = o.fyn;
+            dst.ux[p] = o.u1x;
+            dst.uy[p] = o.u1y;
+            dst.uz[p] = o.u1z;
+            dst.w[p] = o.w;
+            if (dst.id) dst.id[p] = src.id[p];
+            key[p] = nj * nx + ni;
+        }
         __syncwarp();
     }
-    if (phase == 0) {
-        double v[kLedger], out[kLedger];
+    block_ledger<T>(acc, red, lsum);
+}
+
+// The new cell order: warp per unit of new cells. New cell k (its particles at
+// [start_new[k], start_new[k+1])) is the concatenation of the nine runs
+// (old cell k - o_d, direction d) in ascending order of the old cell index.
+// Lane l sets up the runs of the unit's cell l (sorted, with prefix sums);
+// then the lanes walk the unit's whole new range, 32 consecutive particles at
+// a time, each finding its cell and run. A cell whose runs do not add up to
+// its new count flags err.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_permute(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start_new, const int32_t* __restrict__ n9,
+          const int32_t* __restrict__ off9, GridP g, int* __restrict__ err)
+{
+    __shared__ int scs[8][kUnitW + 1];          // new cell starts of the unit
+    __shared__ int srs[8][kUnitW][kNDir];       // run start in src, in run order
+    __shared__ int srp[8][kUnitW][kNDir + 1];   // run prefix within the cell
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nx = g.nx, ny = g.ny;
+    const int nunits = units_of(nx, ny);
+    const bool ids = dst.id != nullptr;
+    int* cs = scs[wib];
+    for (int u = warp; u < nunits; u += nwarps) {
+        const Unit un = unit_of(u, nx);
+        const int cn = un.cn;
 #pragma unroll
-        for (int s = 0; s < kLedger; ++s) v[s] = (double)acc[s];
-        block_sum<kLedger>(v, red, out);
-        if (threadIdx.x == 0)
+        for (int k0 = 0; k0 <= kUnitW; k0 += 32)
+            if (k0 + lane <= cn) cs[k0 + lane] = start_new[un.c0 + k0 + lane];
+        if (lane < cn) {
+            const int i = un.i0 + lane, j = un.j;
+            int sc[kNDir], cnt[kNDir], st0[kNDir];
 #pragma unroll
-            for (int s = 0; s < kLedger; ++s) lsum[(int64_t)blockIdx.x * kLedger + s] = out[s];
+            for (int d = 0; d < kNDir; ++d) {
+                const int sx = d % 3 - 1, sy = d / 3 - 1;
+                sc[d] = wrap1(j - sy, ny) * nx + wrap1(i - sx, nx);
+                cnt[d] = n9[(int64_t)sc[d] * kNDir + d];
+                st0[d] = off9[(int64_t)sc[d] * kNDir + d];
+            }
+            int* rp = srp[wib][lane];
+            int tot = 0;
+#pragma unroll
+            for (int d = 0; d < kNDir; ++d) {
+                int r = 0;   // rank of the run among the nine (old cells are distinct)
+#pragma unroll
+                for (int e = 0; e < kNDir; ++e) r += sc[e] < sc[d] ? 1 : 0;
+                srs[wib][lane][r] = st0[d];
+                rp[r + 1] = cnt[d];
+                tot += cnt[d];
+            }
+            rp[0] = 0;
+#pragma unroll
+            for (int r = 0; r < kNDir; ++r) rp[r + 1] += rp[r];
+            if (tot != start_new[un.c0 + lane + 1] - start_new[un.c0 + lane]) atomicOr(err, 1);
+        }
+        __syncwarp();
+        const int q0 = cs[0], q1 = cs[cn];
+        constexpr int U = 4;   // positions per lane in flight
+        int l = 0;             // the lane's current cell (positions ascend)
+        for (int qb = q0 + lane; qb < q1; qb += 32 * U) {
+            int sp[U], qd[U];
+#pragma unroll
+            for (int v = 0; v < U; ++v) {
+                const int q = qb + 32 * v;
+                qd[v] = -1;
+                sp[v] = 0;
+                if (q < q1) {
+                    while (l + 1 < cn && cs[l + 1] <= q) ++l;
+                    const int e = q - cs[l];
+                    const int* rp = srp[wib][l];
+                    int r = 0;
+#pragma unroll
+                    for (int t = 1; t < kNDir; ++t) r += rp[t] <= e ? 1 : 0;
+                    if (e < rp[kNDir]) {   // else inconsistent counts (flagged above)
+                        sp[v] = srs[wib][l][r] + (e - rp[r]);
+                        qd[v] = q;
+                    }
+                }
+            }
+            T a[U][6];
+            int32_t idv[U];
+#pragma unroll
+            for (int v = 0; v < U; ++v) {
+                const int p = sp[v];
+                a[v][0] = ld(src.fx + p);
+                a[v][1] = ld(src.fy + p);
+                a[v][2] = ld(src.ux + p);
+                a[v][3] = ld(src.uy + p);
+                a[v][4] = ld(src.uz + p);
+                a[v][5] = ld(src.w + p);
+                idv[v] = ids ? src.id[p] : 0;
+            }
+#pragma unroll
+            for (int v = 0; v < U; ++v) {
+                const int q = qd[v];
+                if (q < 0) continue;
+                dst.fx[q] = a[v][0];
+                dst.fy[q] = a[v][1];
+                dst.ux[q] = a[v][2];
+                dst.uy[q] = a[v][3];
+                dst.uz[q] = a[v][4];
+                dst.w[q] = a[v][5];
+                if (ids) dst.id[q] = idv[v];
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -776,17 +989,38 @@ cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g
 }
 
 template <typename T>
-cudaError_t push(int phase, PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* n9,
-                 const int32_t* off9, int32_t* key, const T* Eth, const T* B, GridP g,
-                 SpeciesConst sc, double* lsum_partial, int lsum_blocks, int64_t npart, int* err,
-                 cudaStream_t st)
+cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* n9, int32_t* off9,
+                      const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
+                      cudaStream_t st)
 {
     const T beta = (T)(sc.q * g.dt / (2.0 * sc.m));
     count_launches(1);
-    k_push<T><<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(phase, src, dst, start, n9, off9, key, Eth, B, g,
-                                                    beta, (T)(g.dt / g.dx), (T)(g.dt / g.dy),
-                                                    (T)(sc.q * g.dt), (T)sc.m, lsum_partial,
-                                                    (int)npart, err);
+    k_push_sort<T><<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(src, dst, start, n9, off9, Eth, B, g, beta,
+                                                                (T)(g.dt / g.dx), (T)(g.dt / g.dy),
+                                                                (T)(sc.q * g.dt), (T)sc.m, lsum_partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, const T* Eth,
+                         const T* B, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
+                         cudaStream_t st)
+{
+    const T beta = (T)(sc.q * g.dt / (2.0 * sc.m));
+    count_launches(1);
+    k_push_general<T><<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(src, dst, start, key, Eth, B, g, beta,
+                                                                   (T)(g.dt / g.dx), (T)(g.dt / g.dy),
+                                                                   (T)(sc.q * g.dt), (T)sc.m, lsum_partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t permute(PArrays<T> src, PArrays<T> dst, const int32_t* start_new, const int32_t* n9,
+                    const int32_t* off9, GridP g, int* err, cudaStream_t st)
+{
+    count_launches(1);
+    k_permute<T><<<blocks_for(units_of(g.nx, g.ny), 8, 152 * 16), 256, 0, st>>>(src, dst, start_new, n9, off9,
+                                                                             g, err);
     return cudaGetLastError();
 }
 
@@ -807,9 +1041,13 @@ cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, i
     template cudaError_t export_particles<T>(PArrays<T>, const int32_t*, GridP, double*, double*,  \
                                              double*, int32_t*, cudaStream_t);                     \
     template cudaError_t deposit<T>(const DepositSpecies<T>&, const T*, T*, T*, GridP, int*, cudaStream_t); \
-    template cudaError_t push<T>(int, PArrays<T>, PArrays<T>, const int32_t*, int32_t*,            \
-                                 const int32_t*, int32_t*, const T*, const T*, GridP, SpeciesConst, \
-                                 double*, int, int64_t, int*, cudaStream_t);                       \
+    template cudaError_t push_sort<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, int32_t*,   \
+                                      const T*, const T*, GridP, SpeciesConst, double*, int,        \
+                                      cudaStream_t);                                                \
+    template cudaError_t push_general<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, const T*, \
+                                         const T*, GridP, SpeciesConst, double*, int, cudaStream_t); \
+    template cudaError_t permute<T>(PArrays<T>, PArrays<T>, const int32_t*, const int32_t*,         \
+                                    const int32_t*, GridP, int*, cudaStream_t);                     \
     template cudaError_t kinetic_energy<T>(PArrays<T>, int64_t, double, double*, int, cudaStream_t);
 
 RELSIM_INSTANTIATE(float)

@@ -216,28 +216,6 @@ __global__ void k_move_counts(const int32_t* __restrict__ n9, int32_t* count_new
     count_new[k] = c;
 }
 
-__global__ void k_move_offsets(const int32_t* __restrict__ n9, const int32_t* __restrict__ start_new,
-                               int32_t* off9, GridP g)
-{
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.ncell) return;
-    int i = k % g.nx, j = k / g.nx;
-    int src[kNDir], cnt[kNDir];
-#pragma unroll
-    for (int d = 0; d < kNDir; ++d) {
-        src[d] = src_cell(i, j, d, g);
-        cnt[d] = n9[(int64_t)src[d] * kNDir + d];
-    }
-    int s0 = start_new[k];
-#pragma unroll
-    for (int d = 0; d < kNDir; ++d) {
-        int o = s0;
-#pragma unroll
-        for (int e = 0; e < kNDir; ++e) o += src[e] < src[d] ? cnt[e] : 0;
-        off9[(int64_t)k * kNDir + d] = o;
-    }
-}
-
 }  // namespace
 
 size_t scan_tmp_ints(int64_t n)
@@ -310,14 +288,6 @@ cudaError_t move_counts(const int32_t* n9, int32_t* count_new, GridP g, cudaStre
 {
     count_launches(1);
     k_move_counts<<<(g.ncell + 255) / 256, 256, 0, st>>>(n9, count_new, g);
-    return cudaGetLastError();
-}
-
-cudaError_t move_offsets(const int32_t* n9, const int32_t* start_new, int32_t* off9, GridP g,
-                         cudaStream_t st)
-{
-    count_launches(1);
-    k_move_offsets<<<(g.ncell + 255) / 256, 256, 0, st>>>(n9, start_new, off9, g);
     return cudaGetLastError();
 }
 
