@@ -362,6 +362,40 @@ def test_per_step_sort_is_stable(rs, orc):
     sim.close()
 
 
+def test_crowded_cell_sort_is_stable(rs, orc):
+    # one cell holds far more particles than a warp stages at once (the
+    # two-pass big-cell path of the push) and they leave in every direction
+    nx, ny, dt = 8, 8, 0.9
+    rng = np.random.default_rng(11)
+    nbig, nrest = 400, 300
+    x = np.concatenate([3.0 + rng.random((nbig, 2)), rng.random((nrest, 2)) * [nx, ny]])
+    u = rng.normal(scale=1.5, size=(nbig + nrest, 3))
+    w = rng.random(nbig + nrest) + 0.5
+    st = {"species": [dict(x=x[:, 0], y=x[:, 1], ux=u[:, 0], uy=u[:, 1], uz=u[:, 2], w=w)] * 2,
+          "E": rng.normal(scale=0.1, size=(3, nx * ny)), "B": rng.normal(scale=0.5, size=(3, nx * ny))}
+    st = fp32_state(st, nx, ny)
+    sim = make_sim(rs, nx, ny, 32, dt=dt)
+    sim.load_state(st)
+    assert np.diff(sim.cell_start(0)).max() >= nbig
+    _, _, _, ids0 = sim.particles(0, ids=True)
+    led, status = sim.step()
+    assert status == 0
+    x1, u1, _, ids1 = sim.particles(0, ids=True)
+    keys_new = (np.floor(x1[:, 1]).astype(np.int64) * nx + np.floor(x1[:, 0]).astype(np.int64))
+    pos_of = np.empty(len(ids1), dtype=np.int64)
+    pos_of[ids1] = np.arange(len(ids1))
+    perm, start = orc.stable_sort(keys_new[pos_of[ids0]].astype(np.int32), nx * ny)
+    np.testing.assert_array_equal(ids0[perm], ids1)
+    np.testing.assert_array_equal(sim.cell_start(0), start)
+    # and the pushed momenta are the oracle's
+    c = ocfg(orc, nx, ny, dt=dt)
+    P = orc.Particles(st["species"])
+    orc.step(c, P, st["E"], st["B"])
+    o = P.species(0)
+    assert rel(u1, np.stack([o["ux"], o["uy"], o["uz"]], axis=1)[ids1]) < 2e-5
+    sim.close()
+
+
 def test_ledger_identity_on_gpu(rs):
     nx, ny = 64, 32
     st = harris_small(nx, ny, 16)
