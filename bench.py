@@ -280,6 +280,20 @@ def run_ours(args):
         "input_generation_s": t_gen,
     }
 
+    # the particle spectrum of the final state (a diagnostic, not part of the
+    # step): 256 log bins of gamma - 1 over [1e-2, 1e4], both species
+    edges = np.geomspace(1e-2, 1e4, 257)
+    sim.spectrum(0, edges, 0)
+    sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sa.record(stream)
+    spec = [sim.spectrum(s, edges, 0, device=True) for s in range(len(n_per))]
+    sb.record(stream)
+    torch.cuda.synchronize()
+    cnt = sum(c.cpu().numpy() for _, c in spec)
+    out["spectrum"] = {"bins": 256, "variable": "gamma-1", "range": [1e-2, 1e4], "ms": sa.elapsed_time(sb),
+                       "particles_binned": int(cnt.sum()),
+                       "peak_bin_gamma_minus_1": float(np.sqrt(edges[:-1] * edges[1:])[int(np.argmax(cnt[1:-1]))])}
+
     # end to end through the C ABI with host buffers: every step loads the
     # state from pinned host memory, steps, and reads the ledger back
     if not args.no_e2e:

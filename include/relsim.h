@@ -224,6 +224,24 @@ RELSIM_API int relsim_energy_ledger(relsim_ctx* ctx, relsim_energy* out);
    step). */
 RELSIM_API int relsim_step(relsim_ctx* ctx, relsim_energy* ledger);
 
+/* Particle energy spectrum of a species (diagnostic; the paper's spectra,
+   Sec. 3.2 "Nonlinear reconnection and spectra" and its spectrum figures,
+   are weighted particle distributions over the Lorentz factor or the proper
+   speed u/c). variable 0 bins x = gamma - 1 = |u|^2/(gamma + 1), variable 1
+   bins x = |u|. edges: nbins + 1 strictly ascending finite FP64 bin edges in
+   HOST memory (1 <= nbins <= 4096), e.g. logarithmic. Outputs (each may be
+   NULL, host or device per where) have nbins + 2 entries: [0] below
+   edges[0], [b] for edges[b-1] <= x < edges[b] (b = 1..nbins), [nbins+1] at
+   or above edges[nbins]; weight = sum of the particles' weights (FP64),
+   count = number of particles. x is computed in the form's precision (FP32
+   or FP64) with correctly rounded operations and no fused multiply-add, and
+   the bin decision is exact against the FP64 edges, so counts are
+   reproducible bit for bit. Synchronises the stream for host outputs.
+   Errors: INVALID_ARG (species, variable, nbins, edges not ascending or not
+   finite), OOM, CUDA. */
+RELSIM_API int relsim_energy_spectrum(relsim_ctx* ctx, int species, int variable, int nbins,
+                                      const double* edges, double* weight, int64_t* count, int where);
+
 /* Library version (major*10000 + minor*100 + patch). */
 RELSIM_API int relsim_version(void);
 

@@ -17,7 +17,7 @@ from .build import build, lib_path
 __all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "curl_c",
            "curl_n", "rhs", "gmres", "field_update", "push", "energies", "cell_keys",
            "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
-           "to_full_offsets", "make_config"]
+           "to_full_offsets", "make_config", "spectrum"]
 
 
 class OracleConfig(ctypes.Structure):
@@ -271,3 +271,27 @@ HALF_OFFSETS = ((0, 0), (1, 0), (-1, 1), (0, 1), (1, 1))
 def to_full_offsets(o):
     di, dj = o
     return (dj + 1) * 3 + (di + 1)
+
+
+def spectrum(ux, uy, uz, w, edges, variable=0, precision=64):
+    """Weighted and counted particle spectrum: the paper's spectra (Sec. 3.2,
+    "Nonlinear reconnection and spectra") are weighted particle distributions
+    over the Lorentz factor or the proper speed u/c.
+
+    x = gamma - 1 = |u|^2/(gamma + 1) (variable 0) or x = |u| (variable 1),
+    formed in the given precision (32 or 64: the bin is an integer decided in
+    floating point, so it is decided in the precision of the form being
+    compared), with |u|^2 summed x, y, z in that order. Bins: [0] below
+    edges[0], [b] for edges[b-1] <= x < edges[b], [nbins+1] at or above
+    edges[nbins]. Returns (weights, counts), each of length nbins + 2.
+    """
+    t = np.float32 if precision == 32 else np.float64
+    ux, uy, uz = (np.asarray(a, dtype=np.float64).astype(t) for a in (ux, uy, uz))
+    u2 = ux * ux + uy * uy + uz * uz
+    one = t(1)
+    x = u2 / (np.sqrt(one + u2) + one) if variable == 0 else np.sqrt(u2)
+    e = np.asarray(edges, dtype=np.float64)
+    idx = np.searchsorted(e, x.astype(np.float64), side="right")
+    nb = e.size + 1
+    return (np.bincount(idx, weights=np.asarray(w, dtype=np.float64), minlength=nb),
+            np.bincount(idx, minlength=nb).astype(np.int64))

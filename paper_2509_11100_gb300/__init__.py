@@ -26,7 +26,7 @@ __all__ = [
     "relsim_set_mass_matrix", "relsim_field_solve", "relsim_get_E_theta", "relsim_apply_operator",
     "relsim_push", "relsim_energy_ledger", "relsim_step", "relsim_version", "Simulation",
     "relsim_profile_enable", "relsim_profile_read", "relsim_kernel_launches", "PROFILE_SLOTS",
-    "relsim_kinetic_energy_noalloc", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
+    "relsim_kinetic_energy_noalloc", "relsim_energy_spectrum", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
 ]
 
@@ -117,6 +117,8 @@ _SIGS = {
     "relsim_profile_read": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_int]),
     "relsim_kernel_launches": (ctypes.c_int64, []),
     "relsim_kinetic_energy_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
+    "relsim_energy_spectrum": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                              ctypes.c_int]),
 }
 
 PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
@@ -342,6 +344,20 @@ def relsim_apply_operator(ctx, v, device=False):
     return out
 
 
+def relsim_energy_spectrum(ctx, species, edges, variable=0, device=False):
+    """Weighted and counted histogram of gamma - 1 (variable 0) or |u|
+    (variable 1) over the bins between the FP64 edges (host array), plus the
+    bins below and above them. Returns (weight[nbins + 2], count[nbins + 2])."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = e.size - 1
+    wgt = _out((nb + 2,), np.float64, device)
+    cnt = _out((nb + 2,), np.int64, device)
+    pw, pc = _ptr(wgt, writable=True), _ptr(cnt, np.int64, writable=True)
+    _check(ctx, lib().relsim_energy_spectrum(ctx, species, variable, nb, e.ctypes.data, pw[0], pc[0],
+                                             _where(pw, pc)))
+    return wgt, cnt
+
+
 def relsim_push(ctx):
     return _check(ctx, lib().relsim_push(ctx))
 
@@ -446,6 +462,9 @@ class Simulation:
 
     def apply_operator(self, v):
         return relsim_apply_operator(self.ctx, v)
+
+    def spectrum(self, s, edges, variable=0, device=False):
+        return relsim_energy_spectrum(self.ctx, s, edges, variable, device)
 
     def push(self):
         return relsim_push(self.ctx)

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <string>
 #include <vector>
@@ -100,6 +101,11 @@ struct relsim_ctx {
     int* hflag = nullptr;
     int* dpush = nullptr;     // set by the push if its two passes ever disagree
     int* hpush = nullptr;
+    // spectrum diagnostic (grown on demand)
+    double* spec_w = nullptr;
+    unsigned long long* spec_c = nullptr;
+    void* spec_e = nullptr;
+    int spec_cap = 0;   // bins
     // staging for host <-> device copies
     double* stage = nullptr;
     int64_t stage_cap = 0;   // doubles
@@ -692,6 +698,40 @@ int push_impl(relsim_ctx* c)
     return RELSIM_OK;
 }
 
+template <typename T>
+int spectrum_impl(relsim_ctx* c, int s, int variable, int nbins, const double* edges, double* weight,
+                  int64_t* count, int where)
+{
+    if (nbins > c->spec_cap) {
+        dfree(c->spec_w);
+        dfree(c->spec_c);
+        dfree(c->spec_e);
+        c->spec_cap = 0;
+        TRY(dalloc(c, &c->spec_w, sizeof(double) * (size_t)(nbins + 2)));
+        TRY(dalloc(c, &c->spec_c, sizeof(unsigned long long) * (size_t)(nbins + 2)));
+        TRY(dalloc(c, &c->spec_e, sizeof(double) * (size_t)(nbins + 1)));
+        c->spec_cap = nbins;
+    }
+    // the edges in T, rounded up: for x in T, x >= e holds exactly when x >= edge
+    std::vector<T> et((size_t)nbins + 1);
+    for (int b = 0; b <= nbins; ++b) {
+        T v = (T)edges[b];
+        if ((double)v < edges[b]) v = std::nextafter(v, std::numeric_limits<T>::infinity());
+        et[(size_t)b] = v;
+    }
+    CK(cudaMemcpyAsync(c->spec_e, et.data(), sizeof(T) * et.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemsetAsync(c->spec_w, 0, sizeof(double) * (size_t)(nbins + 2), c->st));
+    CK(cudaMemsetAsync(c->spec_c, 0, sizeof(unsigned long long) * (size_t)(nbins + 2), c->st));
+    Species& sp = c->sp[s];
+    CK(spectrum<T>(arrays<T>(sp, sp.cur), sp.n, variable, (const T*)c->spec_e, nbins, c->spec_w, c->spec_c, c->st));
+    const cudaMemcpyKind kind = where == RELSIM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (weight) CK(cudaMemcpyAsync(weight, c->spec_w, sizeof(double) * (size_t)(nbins + 2), kind, c->st));
+    if (count) CK(cudaMemcpyAsync(count, c->spec_c, sizeof(int64_t) * (size_t)(nbins + 2), kind, c->st));
+    // the host copy of the edges must outlive the copy above
+    CK(cudaStreamSynchronize(c->st));
+    return RELSIM_OK;
+}
+
 int check_push(relsim_ctx* c)
 {
     if (*c->hpush & 2)
@@ -892,6 +932,7 @@ void relsim_destroy(relsim_ctx* c)
     dfree(c->rtmp);
     dfree(c->V); dfree(c->gw); dfree(c->gw2); dfree(c->gx); dfree(c->gb); dfree(c->partial);
     dfree(c->dsum); dfree(c->dled); dfree(c->dflag); dfree(c->dpush); dfree(c->stage);
+    dfree(c->spec_w); dfree(c->spec_c); dfree(c->spec_e);
     if (c->hpin) cudaFreeHost(c->hpin);
     if (c->hflag) cudaFreeHost(c->hflag);
     if (c->hpush) cudaFreeHost(c->hpush);
@@ -1125,6 +1166,22 @@ int relsim_profile_read(relsim_ctx* c, relsim_profile* out, int reset)
         memset(c->prof.kernels, 0, sizeof(c->prof.kernels));
     }
     return RELSIM_OK;
+}
+
+int relsim_energy_spectrum(relsim_ctx* c, int species, int variable, int nbins, const double* edges,
+                           double* weight, int64_t* count, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (species < 0 || species >= c->cfg.nspecies)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
+    if (variable != 0 && variable != 1) return fail(c, RELSIM_ERR_INVALID_ARG, "variable must be 0 or 1");
+    if (nbins < 1 || nbins > 4096) return fail(c, RELSIM_ERR_INVALID_ARG, "nbins must be 1..4096");
+    if (!edges) return fail(c, RELSIM_ERR_INVALID_ARG, "null edges");
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    for (int b = 0; b <= nbins; ++b)
+        if (!std::isfinite(edges[b]) || (b > 0 && !(edges[b] > edges[b - 1])))
+            return fail(c, RELSIM_ERR_INVALID_ARG, "edges must be finite and strictly ascending");
+    return DISPATCH(spectrum_impl, c, species, variable, nbins, edges, weight, count, where);
 }
 
 int64_t relsim_kernel_launches(void) { return (int64_t)g_launches.load(); }

@@ -97,6 +97,12 @@ template <typename T>
 cudaError_t permute(PArrays<T> src, PArrays<T> dst, const int32_t* start_new, const int32_t* n9,
                     const int32_t* off9, GridP g, int* err, cudaStream_t st);
 int push_grid_blocks(GridP g, int precision);
+// weighted and counted histogram of gamma - 1 (variable 0) or |u| (1) over
+// nbins bins between ascending edges (nbins + 1, rounded up to T), plus the
+// bins below and above them: wsum/cnt[nbins + 2], accumulated (zero them)
+template <typename T>
+cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int nbins, double* wsum,
+                     unsigned long long* cnt, cudaStream_t st);
 template <typename T>
 cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, int nblocks,
                            cudaStream_t st);

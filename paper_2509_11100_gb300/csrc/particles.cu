@@ -926,6 +926,59 @@ __global__ void k_kinetic(PArrays<T> pa, int64_t n, T m, double* partial)
     if (threadIdx.x == 0) partial[blockIdx.x] = out[0];
 }
 
+// The particle spectrum: every particle adds its weight (and 1 to the count)
+// to the bin of x = gamma - 1 (variable 0) or x = |u| (variable 1) among the
+// ascending edges e_0 < .. < e_nbins: bin 0 below e_0, bin b for
+// e_{b-1} <= x < e_b, bin nbins+1 at or above e_nbins. x is formed with
+// round-to-nearest operations and no contraction, in T; the edges arrive
+// rounded up to T, so the comparisons equal those against the FP64 edges.
+// Per block the bins live in shared memory; one atomic flush per bin.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_spectrum(PArrays<T> pa, int64_t n, int variable, const T* __restrict__ edges, int nbins,
+           double* __restrict__ wsum, unsigned long long* __restrict__ cnt)
+{
+    extern __shared__ __align__(16) unsigned char ssm[];
+    const int nb = nbins + 2;
+    double* sw = reinterpret_cast<double*>(ssm);
+    unsigned* sc = reinterpret_cast<unsigned*>(sw + nb);
+    T* se = reinterpret_cast<T*>(sw + 2 * nb);   // past both bin arrays, 8-byte aligned
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        sw[b] = 0.0;
+        sc[b] = 0u;
+    }
+    for (int b = threadIdx.x; b <= nbins; b += blockDim.x) se[b] = edges[b];
+    __syncthreads();
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const T ux = pa.ux[p], uy = pa.uy[p], uz = pa.uz[p];
+        const T u2 = add_rn(add_rn(mul_rn(ux, ux), mul_rn(uy, uy)), mul_rn(uz, uz));
+        const T x = variable == 0 ? div_rn(u2, add_rn(sqrt_rn(add_rn(T(1), u2)), T(1))) : sqrt_rn(u2);
+        int a = 0, b = nbins + 1;   // the number of edges <= x
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (se[mid] <= x) a = mid + 1;
+            else b = mid;
+        }
+        atomicAdd(&sw[a], (double)pa.w[p]);
+        atomicAdd(&sc[a], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (sc[b]) {
+            atomicAdd(&wsum[b], sw[b]);
+            atomicAdd(&cnt[b], (unsigned long long)sc[b]);
+        }
+}
+
 int blocks_for(int64_t n, int threads, int cap)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -1033,6 +1086,19 @@ cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, i
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int nbins, double* wsum,
+                     unsigned long long* cnt, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = (size_t)(nbins + 2) * (sizeof(double) + sizeof(double)) + (size_t)(nbins + 1) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_spectrum<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_spectrum<T><<<blocks_for(n, 256, 152 * 4), 256, smem, st>>>(p, n, variable, edges, nbins, wsum, cnt);
+    return cudaGetLastError();
+}
+
 #define RELSIM_INSTANTIATE(T)                                                                      \
     template cudaError_t load_convert<T>(const double*, const double*, const double*, int64_t,     \
                                          GridP, PArrays<T>, int32_t*, int32_t*, int*, cudaStream_t); \
@@ -1048,7 +1114,9 @@ cudaError_t kinetic_energy(PArrays<T> p, int64_t n, double m, double* partial, i
                                          const T*, GridP, SpeciesConst, double*, int, cudaStream_t); \
     template cudaError_t permute<T>(PArrays<T>, PArrays<T>, const int32_t*, const int32_t*,         \
                                     const int32_t*, GridP, int*, cudaStream_t);                     \
-    template cudaError_t kinetic_energy<T>(PArrays<T>, int64_t, double, double*, int, cudaStream_t);
+    template cudaError_t kinetic_energy<T>(PArrays<T>, int64_t, double, double*, int, cudaStream_t); \
+    template cudaError_t spectrum<T>(PArrays<T>, int64_t, int, const T*, int, double*, unsigned long long*, \
+                                     cudaStream_t);
 
 RELSIM_INSTANTIATE(float)
 RELSIM_INSTANTIATE(double)

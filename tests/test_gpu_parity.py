@@ -362,13 +362,18 @@ def test_per_step_sort_is_stable(rs, orc):
     sim.close()
 
 
-def test_crowded_cell_sort_is_stable(rs, orc):
-    # one cell holds far more particles than a warp stages at once (the
-    # two-pass big-cell path of the push) and they leave in every direction
+@pytest.mark.parametrize("case", ["cell", "row"])
+def test_crowded_cell_sort_is_stable(rs, orc, case):
+    # "cell": one cell holds far more particles than a warp stages at once
+    # (the two-pass big-cell path of the push); "row": one row of cells holds
+    # more particles than the deposit's staging buffer (the permutation goes
+    # through global memory). Particles leave in every direction; a second
+    # step runs the deposit that completes the first step's sort.
     nx, ny, dt = 8, 8, 0.9
     rng = np.random.default_rng(11)
-    nbig, nrest = 400, 300
-    x = np.concatenate([3.0 + rng.random((nbig, 2)), rng.random((nrest, 2)) * [nx, ny]])
+    nbig, nrest = (400, 300) if case == "cell" else (4000, 300)
+    lo, span = ((3.0, 3.0), (1.0, 1.0)) if case == "cell" else ((0.0, 3.0), (nx, 1.0))
+    x = np.concatenate([np.array(lo) + rng.random((nbig, 2)) * span, rng.random((nrest, 2)) * [nx, ny]])
     u = rng.normal(scale=1.5, size=(nbig + nrest, 3))
     w = rng.random(nbig + nrest) + 0.5
     st = {"species": [dict(x=x[:, 0], y=x[:, 1], ux=u[:, 0], uy=u[:, 1], uz=u[:, 2], w=w)] * 2,
@@ -376,10 +381,15 @@ def test_crowded_cell_sort_is_stable(rs, orc):
     st = fp32_state(st, nx, ny)
     sim = make_sim(rs, nx, ny, 32, dt=dt)
     sim.load_state(st)
-    assert np.diff(sim.cell_start(0)).max() >= nbig
+    counts = np.diff(sim.cell_start(0))
+    assert (counts.max() if case == "cell" else counts.reshape(ny, nx).sum(axis=1).max()) >= nbig
     _, _, _, ids0 = sim.particles(0, ids=True)
     led, status = sim.step()
     assert status == 0
+    # the next deposit completes this step's sort (fused) before anything reads
+    # the particles
+    sim.build()
+    M, J = sim.mass_matrix()
     x1, u1, _, ids1 = sim.particles(0, ids=True)
     keys_new = (np.floor(x1[:, 1]).astype(np.int64) * nx + np.floor(x1[:, 0]).astype(np.int64))
     pos_of = np.empty(len(ids1), dtype=np.int64)
@@ -387,12 +397,44 @@ def test_crowded_cell_sort_is_stable(rs, orc):
     perm, start = orc.stable_sort(keys_new[pos_of[ids0]].astype(np.int32), nx * ny)
     np.testing.assert_array_equal(ids0[perm], ids1)
     np.testing.assert_array_equal(sim.cell_start(0), start)
-    # and the pushed momenta are the oracle's
+    # the pushed momenta and the next deposit are the oracle's
     c = ocfg(orc, nx, ny, dt=dt)
     P = orc.Particles(st["species"])
-    orc.step(c, P, st["E"], st["B"])
+    E1o, B1o, _, _ = orc.step(c, P, st["E"], st["B"])
     o = P.species(0)
     assert rel(u1, np.stack([o["ux"], o["uy"], o["uz"]], axis=1)[ids1]) < 2e-5
+    Jo, Mo = orc.deposit(c, P, B1o)
+    assert rel(M, half_from_full(Mo, nx, ny)) < 1e-4
+    assert rel(J, Jo) < 1e-4
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_spectrum_matches_oracle(rs, orc, prec):
+    nx, ny, dt = 64, 32, 0.5
+    st = harris_small(nx, ny, 16)
+    sim = make_sim(rs, nx, ny, prec, dt=dt)
+    sim.load_state(st)
+    for _ in range(2):
+        sim.step(ledger=False)
+    edges0 = np.geomspace(1e-2, 1e4, 257)    # 256 log bins of gamma - 1
+    edges1 = np.geomspace(1e-3, 1e3, 97)     # 96 log bins of |u|
+    for s in range(2):
+        x, u, w, ids = sim.particles(s, ids=True)
+        for var, edges in ((0, edges0), (1, edges1)):
+            wt, ct = sim.spectrum(s, edges, var)
+            wo, co = orc.spectrum(u[:, 0], u[:, 1], u[:, 2], w, edges, var, prec)
+            # the bin of every particle is decided exactly as the oracle does
+            np.testing.assert_array_equal(ct, co)
+            np.testing.assert_allclose(wt, wo, rtol=1e-12, atol=1e-12 * w.sum())
+            assert ct.sum() == len(w)
+    wd, cd = sim.spectrum(0, edges0, 0, device=True)
+    np.testing.assert_array_equal(cd.cpu().numpy(), sim.spectrum(0, edges0, 0)[1])
+    for bad in (np.array([1.0]), np.array([1.0, 1.0]), np.array([2.0, 1.0]), np.array([1.0, np.nan])):
+        with pytest.raises(rs.RelsimError):
+            sim.spectrum(0, bad, 0)
+    with pytest.raises(rs.RelsimError):
+        sim.spectrum(0, edges0, 2)
     sim.close()
 
 

@@ -501,3 +501,58 @@ def test_oracle_golden_trajectory():
         for k in ("W_E1", "W_B1", "K1", "work_grid", "mismatch", "E_l2", "B_l2", "ux_sum", "x_sum"):
             assert abs(a[k] - b[k]) <= 1e-9 * max(1.0, abs(b[k])), k
         assert abs(a["gmres_iters"] - b["gmres_iters"]) <= 1
+
+
+# ---------------------------------------------------------------------------
+# particle spectrum (diagnostic of Sec. 3.2's spectra)
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_spectrum_places_known_energies_in_their_bins(orc, precision):
+    # particles built at the geometric centre of each log bin of gamma - 1
+    # (far from either edge) land in that bin, whatever the direction of u
+    rng = np.random.default_rng(5)
+    edges = np.geomspace(1e-2, 1e4, 257)
+    centres = np.sqrt(edges[:-1] * edges[1:])
+    x = np.repeat(centres, 3)
+    umag = np.sqrt((1.0 + x) ** 2 - 1.0)
+    d = rng.normal(size=(x.size, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    u = d * umag[:, None]
+    w = rng.random(x.size) + 0.5
+    wt, ct = orc.spectrum(u[:, 0], u[:, 1], u[:, 2], w, edges, 0, precision)
+    expect = np.zeros(258, dtype=np.int64)
+    expect[1:257] = 3
+    np.testing.assert_array_equal(ct, expect)
+    np.testing.assert_allclose(wt[1:257], w.reshape(256, 3).sum(axis=1), rtol=1e-15)
+
+
+def test_spectrum_bins_are_closed_below_open_above(orc):
+    # |u| = 5 exactly (u = (3, 4, 0)) sits on the edge 5 and belongs to the
+    # bin above it; values outside the edges go to the two end bins
+    edges = np.array([1.0, 2.0, 5.0, 7.0])
+    u = np.array([[3.0, 4.0, 0.0], [0.0, 0.5, 0.0], [0.0, 0.0, 9.0], [0.0, 7.0, 0.0], [1.5, 0.0, 0.0]])
+    for precision in (32, 64):
+        _, ct = orc.spectrum(u[:, 0], u[:, 1], u[:, 2], np.ones(5), edges, 1, precision)
+        np.testing.assert_array_equal(ct, [1, 1, 0, 1, 2])
+
+
+def test_spectrum_of_maxwell_juttner_matches_the_analytic_distribution(orc):
+    # the gamma - 1 histogram of a Maxwell-Juttner sample against the bin
+    # probabilities of f(gamma) ~ gamma sqrt(gamma^2 - 1) exp(-gamma/theta),
+    # integrated numerically, within the sample's counting error
+    from scipy import integrate
+    from relsim_inputs.harris import sample_maxwell_juettner
+    theta = 0.3
+    rng = np.random.default_rng(17)
+    n = 200_000
+    u = sample_maxwell_juettner(rng, theta, n).T
+    edges = np.geomspace(1e-2, 1e2, 41)
+    _, ct = orc.spectrum(u[:, 0], u[:, 1], u[:, 2], np.ones(n), edges, 0, 64)
+    f = lambda g: g * np.sqrt(g * g - 1.0) * np.exp(-(g - 1.0) / theta)
+    norm = integrate.quad(f, 1.0, np.inf, limit=200)[0]
+    p = np.array([integrate.quad(f, 1.0 + a, 1.0 + b, limit=200)[0] for a, b in zip(edges[:-1], edges[1:])]) / norm
+    p_below = integrate.quad(f, 1.0, 1.0 + edges[0])[0] / norm
+    expect = n * np.concatenate([[p_below], p, [1.0 - p_below - p.sum()]])
+    sd = np.sqrt(np.maximum(expect, 1.0))
+    assert np.max(np.abs(ct - expect) / sd) < 5.0
+    assert ct.sum() == n
