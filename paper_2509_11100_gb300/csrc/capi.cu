@@ -642,7 +642,7 @@ template <typename T>
 int push_impl(relsim_ctx* c)
 {
     const int nbp = push_grid_blocks(c->g, c->prec);
-    TRY(ensure_partial(c, (int64_t)nbp * 5));
+    TRY(ensure_partial(c, (int64_t)nbp * (kLedgerSpecies - 1)));
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         Species& sp = c->sp[s];
         double* led = c->dled + kLedgerField + kLedgerSpecies * s;
@@ -659,8 +659,10 @@ int push_impl(relsim_ctx* c)
             // into the other buffer; then the stable new-cell order back into
             // the current buffer
             PROF_BEGIN(RELSIM_PROF_PUSH);
+            // K0 of this step is the kinetic energy the last push (or load) left
+            CK(cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
             CK(push_sort<T>(src, dst, sp.start, c->n9, c->off9, Eth, B, c->g, sc, c->partial, nbp, c->st));
-            CK(reduce_partials(c->partial, nbp, kLedgerSpecies, led, c->st));
+            CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
             PROF_END();
             PROF_BEGIN(RELSIM_PROF_SORT_TABLES);
             CK(move_counts(c->n9, c->count_new, c->g, c->st));
@@ -677,8 +679,9 @@ int push_impl(relsim_ctx* c)
             // general path: push in place order with keys, radix sort, gather
             TRY(ensure_radix(c, sp.n));
             PROF_BEGIN(RELSIM_PROF_GENERAL_SORT);
+            CK(cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
             CK(push_general<T>(src, dst, sp.start, c->rk[0], Eth, B, c->g, sc, c->partial, nbp, c->st));
-            CK(reduce_partials(c->partial, nbp, kLedgerSpecies, led, c->st));
+            CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
             CK(iota_i32(c->rv[0], sp.n, c->st));
             bool in1 = false;
             CK(radix_sort_pairs(c->rk[0], c->rv[0], c->rk[1], c->rv[1], sp.n, c->key_bits, c->rtmp,

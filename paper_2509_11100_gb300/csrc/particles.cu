@@ -491,10 +491,10 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
 template <typename T> struct PushCfg {
     static constexpr int warps = 4;                        // static shared memory < 48 KB
     static constexpr int threads = 32 * warps;
-    static constexpr int min_blocks = sizeof(T) == 4 ? 6 : 2;
+    static constexpr int min_blocks = sizeof(T) == 4 ? 5 : 2;
 };
 constexpr int kPushCap = 128;   // particles of one cell staged per warp
-constexpr int kLedger = 5;      // K0, dK, work, mismatch, K1
+constexpr int kLedger = 4;      // dK, work, mismatch, K1 (K0 is the previous K1)
 
 template <typename T>
 struct Pushed {
@@ -558,11 +558,10 @@ __device__ __forceinline__ void push_particle(const T fx, const T fy, const T ux
         const T du = (ux - o.u1x) * (ux + o.u1x) + (uy - o.u1y) * (uy + o.u1y) +
                      (uz - o.u1z) * (uz + o.u1z);
         const T igs = rcp_t(g0 + g1);
-        acc[0] += w * m * u02 * rcp_t(g0 + T(1));            // K0
-        acc[1] -= w * m * du * igs;                          // dK
-        acc[2] += qdt * w * ue * r.ig;                       // work
-        acc[3] += qdt * w * ue * du * igs * igs * r.ig;      // mismatch
-        acc[4] += w * m * u12 * rcp_t(g1 + T(1));            // K1
+        acc[0] -= w * m * du * igs;                          // dK
+        acc[1] += qdt * w * ue * r.ig;                       // work
+        acc[2] += qdt * w * ue * du * igs * igs * r.ig;      // mismatch
+        acc[3] += w * m * u12 * rcp_t(g1 + T(1));            // K1
     }
 }
 
@@ -652,11 +651,14 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
     PushTile<T>& tl = stile[wib];
     PushStage<T>& st = sstage[wib];
     const bool ids = dst.id != nullptr;
-    T acc[kLedger] = {T(0), T(0), T(0), T(0), T(0)};
+    T acc[kLedger] = {T(0), T(0), T(0), T(0)};
 
     for (int u = warp; u < nunits; u += nwarps) {
         const Unit un = unit_of(u, nx);
         unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
+        const int P1 = ss[un.cn];
+        int pf_pos = -1;   // the first particle of the prefetched batch
+        T pfx = T(0), pfy = T(0), pux = T(0), puy = T(0), puz = T(0), pw = T(0);
         for (int l = 0; l < un.cn; ++l) {
             const int s0 = ss[l], s1 = ss[l + 1], np = s1 - s0;
             int* run = st.run;   // particles of this cell per direction so far
@@ -681,20 +683,44 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
                 if (lane < kNDir) run[lane] = 0;
                 __syncwarp();
             }
-            // the pass that ranks (and stages or writes) every particle
+            // the pass that ranks (and stages or writes) every particle; the
+            // next batch of the unit (this cell's or the next one's) is loaded
+            // while this one is pushed
             for (int b0 = s0; b0 < s1; b0 += 32) {
                 const int p = b0 + lane;
                 const bool act = p < s1;
                 const int q = act ? p : s0;
-                const T fx = ld(src.fx + q), fy = ld(src.fy + q), ux = ld(src.ux + q), uy = ld(src.uy + q),
-                        uz = ld(src.uz + q), w = ld(src.w + q);
+                T fx, fy, ux, uy, uz, w;
+                if (pf_pos == b0) {
+                    fx = pfx;
+                    fy = pfy;
+                    ux = pux;
+                    uy = puy;
+                    uz = puz;
+                    w = pw;
+                } else {
+                    fx = ld(src.fx + q);
+                    fy = ld(src.fy + q);
+                    ux = ld(src.ux + q);
+                    uy = ld(src.uy + q);
+                    uz = ld(src.uz + q);
+                    w = ld(src.w + q);
+                }
+                // the next batch starts here in this cell, or at the next cell
+                pf_pos = b0 + 32 < s1 ? b0 + 32 : s1;
+                if (pf_pos < P1) {
+                    const int pq = pf_pos + lane < P1 ? pf_pos + lane : P1 - 1;
+                    pfx = ld(src.fx + pq);
+                    pfy = ld(src.fy + pq);
+                    pux = ld(src.ux + pq);
+                    puy = ld(src.uy + pq);
+                    puz = ld(src.uz + pq);
+                    pw = ld(src.w + pq);
+                }
                 Pushed<T> o;
-                T lacc[kLedger] = {T(0), T(0), T(0), T(0), T(0)};
-                push_particle<T>(fx, fy, ux, uy, uz, w, l, tl.E, tl.B, beta, dt_dx, dt_dy, qdt, m, true, true, lacc,
-                                 o);
-                if (act)
-#pragma unroll
-                    for (int s = 0; s < kLedger; ++s) acc[s] += lacc[s];
+                // idle lanes carry weight 0: no ledger contribution (and nothing is stored)
+                push_particle<T>(fx, fy, ux, uy, uz, act ? w : T(0), l, tl.E, tl.B, beta, dt_dx, dt_dy, qdt, m, true,
+                                 true, acc, o);
                 // rank among the cell's particles of the same direction, in order
                 const unsigned peers = dir_peers(act, o.dir);
                 const int rank = (act ? run[o.dir] : 0) + __popc(peers & lt);
@@ -774,7 +800,7 @@ k_push_general(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start
     const int nunits = units_of(nx, ny);
     int* ss = sstart[wib];
     PushTile<T>& tl = stile[wib];
-    T acc[kLedger] = {T(0), T(0), T(0), T(0), T(0)};
+    T acc[kLedger] = {T(0), T(0), T(0), T(0)};
     for (int u = warp; u < nunits; u += nwarps) {
         const Unit un = unit_of(u, nx);
         unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
