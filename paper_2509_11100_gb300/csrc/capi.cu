@@ -99,6 +99,7 @@ struct relsim_ctx {
     double* hpin = nullptr;    // pinned host, 4*(kMaxRestart+2)
     int* dflag = nullptr;
     int* hflag = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};   // read-back events of the pipelined Arnoldi loop
     int* dpush = nullptr;     // set by the push if its two passes ever disagree
     int* hpush = nullptr;
     // spectrum diagnostic (grown on demand)
@@ -334,17 +335,32 @@ int load_impl(relsim_ctx* c, int s, int64_t n, const double* x, const double* u,
         PROF_BEGIN(RELSIM_PROF_LOAD);
         PArrays<T> tmp = arrays<T>(sp, 1), dst = arrays<T>(sp, 0);
         CK(load_convert<T>(dx, du, dw, n, c->g, tmp, c->rk[0], c->rv[0], c->dflag, c->st));
-        bool in1 = false;
-        CK(radix_sort_pairs(c->rk[0], c->rv[0], c->rk[1], c->rv[1], n, c->key_bits, c->rtmp, &in1,
-                            c->st));
-        const int32_t* keys = c->rk[in1 ? 1 : 0];
-        const int32_t* perm = c->rv[in1 ? 1 : 0];
-        CK(gather_particles<T>(perm, tmp, dst, n, true, c->st));
+        CK(keys_unsorted(c->rk[0], n, c->dflag, c->st));
+        PROF_END();
+        CK(cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (*c->hflag & 1) return fail(c, RELSIM_ERR_NONFINITE, "non-finite value in particles");
+        PROF_BEGIN(RELSIM_PROF_LOAD);
+        const int32_t* keys = c->rk[0];
+        if (*c->hflag & 2) {
+            // the stable sort by cell, then the particles gathered in that order
+            bool in1 = false;
+            CK(radix_sort_pairs(c->rk[0], c->rv[0], c->rk[1], c->rv[1], n, c->key_bits, c->rtmp, &in1,
+                                c->st));
+            keys = c->rk[in1 ? 1 : 0];
+            const int32_t* perm = c->rv[in1 ? 1 : 0];
+            CK(gather_particles<T>(perm, tmp, dst, n, true, c->st));
+        } else {
+            // already in cell order (e.g. state read back from this library):
+            // the identity is the stable sort, and the converted buffer stays
+            sp.cur = 1;
+            if (tmp.id)
+                CK(cudaMemcpyAsync(tmp.id, c->rv[0], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, c->st));
+        }
         CK(histogram_keys(keys, n, c->count_new, c->g.ncell, c->st));
         CK(scan_exclusive_i32(c->count_new, sp.start, c->g.ncell, sp.start + c->g.ncell, c->scan_tmp,
                               c->st));
         PROF_END();
-        TRY(check_flag(c, "particles"));
     }
     // kinetic energy of the loaded species -> ledger slot K1
     const int nb = 152 * 4;
@@ -541,51 +557,80 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
             for (int k = 0; k <= m; ++k) gv[k] = 0.0;
             gv[0] = beta;
             int kdim = 0;
-            for (int j = 0; j < m; ++j) {
-                // w = B v_j (v_0 = r/|r| is written to V_0 on the way) and the
-                // dot products <w, V_i> (i <= j), <w, w>
+            // Iteration j: w_j = B v_j (v_0 = r/|r|, written to V_0 on the
+            // way) with the dot products <w_j, V_i> (i <= j) and <w_j, w_j>,
+            // then V_{j+1} = (w_j - V h)/hn, hn^2 = <w,w> - |h|^2 formed on
+            // the device (classical Gram-Schmidt with the normalisation
+            // fused). Nothing of it waits for the host, so iteration j+1 is
+            // launched before the host reads iteration j's sums back; w, the
+            // device sums and the host read-back alternate between two slots.
+            double* ws[2] = {gw[1], gw[0]};   // gw[0] holds r until iteration 0 has read it
+            double* dss[2] = {c->dsum, c->dsum + 3 * (kMaxRestart + 2)};
+            double* hps[2] = {c->hpin, c->hpin + (kMaxRestart + 2)};
+            auto launch_iter = [&](int j) -> int {
+                double* w = ws[j % 2];
+                double* ds = dss[j % 2];
                 PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
                 if (j == 0)
-                    CK(op_arnoldi<T>((const T*)c->M, gw[0], 1.0 / beta, c->V, gw[1], c->V, ldv, 0, c->g,
-                                     c->partial, c->dpush, c->st));
+                    CK(op_arnoldi<T>((const T*)c->M, gw[0], 1.0 / beta, c->V, w, c->V, ldv, 0, c->g, c->partial,
+                                     c->dpush, c->st));
                 else
-                    CK(op_arnoldi<T>((const T*)c->M, c->V + (int64_t)j * ldv, 1.0, nullptr, gw[1], c->V, ldv,
-                                     j, c->g, c->partial, c->dpush, c->st));
+                    CK(op_arnoldi<T>((const T*)c->M, c->V + (int64_t)j * ldv, 1.0, nullptr, w, c->V, ldv, j, c->g,
+                                     c->partial, c->dpush, c->st));
                 PROF_END();
-                // classical Gram-Schmidt with the normalisation fused:
-                // V_{j+1} = (w - V h)/hn, hn^2 = <w,w> - |h|^2
                 PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                CK(reduce_partials(c->partial, nbo, j + 2, c->dsum, c->st));
-                CK(gm_update_scale(gw[1], c->V, ldv, j + 1, c->dsum, c->V + (int64_t)(j + 1) * ldv, n, c->st));
+                CK(reduce_partials(c->partial, nbo, j + 2, ds, c->st));
+                CK(gm_update_scale(w, c->V, ldv, j + 1, ds, c->V + (int64_t)(j + 1) * ldv, n, c->st));
                 PROF_END();
-                TRY(readback(c, c->dsum, j + 2, hp));
+                CK(cudaMemcpyAsync(hps[j % 2], ds, sizeof(double) * (size_t)(j + 2), cudaMemcpyDeviceToHost, c->st));
+                CK(cudaMemcpyAsync(c->hpush, c->dpush, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+                CK(cudaEventRecord(c->gev[j % 2], c->st));
+                return RELSIM_OK;
+            };
+            TRY(launch_iter(0));
+            for (int j = 0; j < m; ++j) {
+                const bool more = j + 1 < m && total + 1 < maxit;   // could iteration j+1 run?
+                // launch it ahead unless the residual's geometric trend says
+                // iteration j converges (a launch ahead is then wasted work)
+                // (|sin| of the previous rotation is the last reduction factor)
+                const bool last = j >= 1 && std::fabs(gv[j]) * std::fabs(sn[j - 1]) <= tol * bnorm;
+                const bool ahead = more && !last;
+                if (ahead) TRY(launch_iter(j + 1));
+                CK(cudaEventSynchronize(c->gev[j % 2]));
                 TRY(check_push(c));
-                const double ww = hp[j + 1];
+                const double* hj = hps[j % 2];
+                const double ww = hj[j + 1];
                 double hn2 = ww;
                 for (int i = 0; i <= j; ++i) {
-                    H[i * m + j] = hp[i];
-                    hn2 -= hp[i] * hp[i];
+                    H[i * m + j] = hj[i];
+                    hn2 -= hj[i] * hj[i];
                 }
                 if (!std::isfinite(hn2)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite Arnoldi norm");
                 if (hn2 < 1e-4 * ww) {
-                    // |w - V h| < |w|/100: the norm above has lost digits;
-                    // orthogonalise w twice explicitly (CGS2) and normalise
+                    // |w - V h| < |w|/100: the norm above has lost digits.
+                    // Drain the speculative iteration, orthogonalise w_j twice
+                    // explicitly (CGS2), normalise it into V_{j+1}, and launch
+                    // iteration j+1 again.
+                    CK(cudaStreamSynchronize(c->st));
+                    double* w = ws[j % 2];
+                    double* scratch = dss[(j + 1) % 2];
                     PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                    CK(gm_update(gw[1], c->V, ldv, j + 1, c->dsum, n, c->partial, nb, c->st));
-                    CK(gm_dots(c->V, ldv, j + 1, gw[1], n, c->partial, nb, c->st));
-                    CK(reduce_partials(c->partial, nb, j + 2, c->dsum, c->st));
-                    CK(gm_update(gw[1], c->V, ldv, j + 1, c->dsum, n, c->partial, nb, c->st));
-                    CK(reduce_partials(c->partial, nb, 1, c->dsum + kMaxRestart + 1, c->st));
+                    CK(gm_update(w, c->V, ldv, j + 1, dss[j % 2], n, c->partial, nb, c->st));
+                    CK(gm_dots(c->V, ldv, j + 1, w, n, c->partial, nb, c->st));
+                    CK(reduce_partials(c->partial, nb, j + 2, scratch, c->st));
+                    CK(gm_update(w, c->V, ldv, j + 1, scratch, n, c->partial, nb, c->st));
+                    CK(reduce_partials(c->partial, nb, 1, scratch + kMaxRestart + 1, c->st));
                     PROF_END();
-                    TRY(readback(c, c->dsum, kMaxRestart + 2, hp));
+                    TRY(readback(c, scratch, kMaxRestart + 2, hp));
                     for (int i = 0; i <= j; ++i) H[i * m + j] += hp[i];
                     hn2 = hp[kMaxRestart + 1];
                     if (!std::isfinite(hn2)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite Arnoldi norm");
                     if (hn2 > 0.0) {
                         PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                        CK(gm_scale(c->V + (int64_t)(j + 1) * ldv, gw[1], 1.0 / std::sqrt(hn2), n, c->st));
+                        CK(gm_scale(c->V + (int64_t)(j + 1) * ldv, w, 1.0 / std::sqrt(hn2), n, c->st));
                         PROF_END();
                     }
+                    if (ahead) TRY(launch_iter(j + 1));
                 }
                 const double hn = std::sqrt(hn2 > 0.0 ? hn2 : 0.0);
                 H[j * m + j] += 1.0;   // A = I + B
@@ -605,7 +650,10 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
                 gv[j] = cs[j] * gv[j];
                 ++total;
                 kdim = j + 1;
+                // a speculative iteration j+1 still in flight only writes
+                // V_{j+2}, its w and its sums: nothing the solution reads
                 if (std::fabs(gv[j + 1]) <= tol * bnorm || total >= maxit || hn == 0.0) break;
+                if (more && !ahead) TRY(launch_iter(j + 1));
             }
             for (int i = kdim - 1; i >= 0; --i) {
                 double s = gv[i];
@@ -876,6 +924,12 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     A(dalloc(c, &c->dled, sizeof(double) * kLedgerLen));
     A(dalloc(c, &c->dflag, sizeof(int)));
     A(dalloc(c, &c->dpush, sizeof(int)));
+    if (cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        r = fail(c, RELSIM_ERR_CUDA, "cudaEventCreate failed");
+        goto fail_init;
+    }
     if (cudaMallocHost((void**)&c->hpin, sizeof(double) * 4 * (kMaxRestart + 2)) != cudaSuccess ||
         cudaMallocHost((void**)&c->hflag, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&c->hpush, sizeof(int)) != cudaSuccess) {
@@ -940,6 +994,8 @@ void relsim_destroy(relsim_ctx* c)
     if (c->hflag) cudaFreeHost(c->hflag);
     if (c->hpush) cudaFreeHost(c->hpush);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->gev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 

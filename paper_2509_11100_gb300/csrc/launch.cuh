@@ -65,6 +65,8 @@ cudaError_t move_counts(const int32_t* n9, int32_t* count_new, GridP g, cudaStre
 cudaError_t iota_i32(int32_t* a, int64_t n, cudaStream_t st);
 
 // ----- particles.cu -----
+// bit 2 of *flag if keys[0..n) is not non-decreasing (flag accumulates)
+cudaError_t keys_unsorted(const int32_t* keys, int64_t n, int* flag, cudaStream_t st);
 template <typename T>
 cudaError_t load_convert(const double* x, const double* u, const double* w, int64_t n, GridP g,
                          PArrays<T> out, int32_t* key, int32_t* val, int* bad, cudaStream_t st);

@@ -14,6 +14,13 @@ namespace {
 // ---------------------------------------------------------------------------
 // load: absolute FP64 positions -> (cell key, offsets), FP64 -> T
 
+// true when v (> 0, finite) is a power of two
+__device__ __forceinline__ bool is_pow2(double v)
+{
+    int e;
+    return frexp(v, &e) == 0.5;
+}
+
 template <typename T>
 __global__ void k_load_convert(const double* __restrict__ x, const double* __restrict__ u,
                                const double* __restrict__ w, int64_t n, GridP g, PArrays<T> out,
@@ -21,17 +28,23 @@ __global__ void k_load_convert(const double* __restrict__ x, const double* __res
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // a power-of-two cell size scales exactly by its reciprocal (FP64
+    // division is costly on this GPU); any other size divides
+    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+    const bool exact = is_pow2(g.dx) && is_pow2(g.dy);
     for (; p < n; p += stride) {
-        double xs = x[2 * p] / g.dx, ys = x[2 * p + 1] / g.dy;
+        double xs = exact ? x[2 * p] * rdx : x[2 * p] / g.dx;
+        double ys = exact ? x[2 * p + 1] * rdy : x[2 * p + 1] / g.dy;
         double ux = u[3 * p], uy = u[3 * p + 1], uz = u[3 * p + 2], ww = w[p];
         if (!isfinite(xs) || !isfinite(ys) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz) ||
             !isfinite(ww)) {
             atomicOr(bad, 1);
             xs = ys = 0.0;
         }
-        // periodic wrap into [0, n) then split into cell + offset
-        xs -= g.nx * floor(xs / g.nx);
-        ys -= g.ny * floor(ys / g.ny);
+        // periodic wrap into [0, n) (only for positions outside the box),
+        // then split into cell + offset
+        if (xs < 0.0 || xs >= (double)g.nx) xs -= g.nx * floor(xs / g.nx);
+        if (ys < 0.0 || ys >= (double)g.ny) ys -= g.ny * floor(ys / g.ny);
         double fi = floor(xs), fj = floor(ys);
         int i = (int)fi, j = (int)fj;
         if (i >= g.nx) i -= g.nx;
@@ -47,6 +60,15 @@ __global__ void k_load_convert(const double* __restrict__ x, const double* __res
         key[p] = j * g.nx + i;
         val[p] = (int32_t)p;
     }
+}
+
+// sets bit 2 of flag if keys[] is not non-decreasing
+__global__ void k_keys_unsorted(const int32_t* __restrict__ keys, int64_t n, int* flag)
+{
+    bool bad = false;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p + 1 < n; p += (int64_t)gridDim.x * blockDim.x)
+        bad = bad || keys[p] > keys[p + 1];
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 2);
 }
 
 template <typename T>
@@ -1028,6 +1050,14 @@ cudaError_t load_convert(const double* x, const double* u, const double* w, int6
     if (n <= 0) return cudaSuccess;
     count_launches(1);
     k_load_convert<T><<<blocks_for(n, 256, 152 * 32), 256, 0, st>>>(x, u, w, n, g, out, key, val, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t keys_unsorted(const int32_t* keys, int64_t n, int* flag, cudaStream_t st)
+{
+    if (n <= 1) return cudaSuccess;
+    count_launches(1);
+    k_keys_unsorted<<<blocks_for(n, 256, 152 * 8), 256, 0, st>>>(keys, n, flag);
     return cudaGetLastError();
 }
 
