@@ -242,6 +242,64 @@ RELSIM_API int relsim_step(relsim_ctx* ctx, relsim_energy* ledger);
 RELSIM_API int relsim_energy_spectrum(relsim_ctx* ctx, int species, int variable, int nbins,
                                       const double* edges, double* weight, int64_t* count, int where);
 
+/* Energy in the Fourier modes along x of one component of B (diagnostic;
+   the linear-tearing measurement of Sec. 3.1 and Fig. 1 follows the B_y
+   energy, its low-pass part and single modes, whose exponential growth gives
+   the tearing rate). For m = 0 .. nmodes-1, with F_{m,j} the DFT along x of
+   row j of the cell-centre component B_c,
+     F_{m,j} = sum_i B_c(i, j) exp(-2 pi sqrt(-1) m i / nx),
+     energy[m] = (1/2) dV (c_m / nx) sum_j |F_{m,j}|^2,
+   c_m = 1 for m = 0 and m = nx/2, else 2, so that the energies of
+   m = 0 .. nx/2 add up to (1/2) sum B_c^2 dV (Parseval). Mode m has the
+   wavenumber k = 2 pi m / L_x, L_x = nx dx. B is the current B (B^{n+1}
+   after a push). component: 0, 1, 2 (x, y, z); 1 <= nmodes <= nx/2 + 1.
+   energy: nmodes FP64 values, host or device per where. With where =
+   RELSIM_DEVICE nothing waits (the result is enqueued on the stream);
+   with RELSIM_HOST the stream is synchronised. The sums along x run in the
+   form's precision from exact integer phases, the rest in FP64 in a fixed
+   order: repeated calls give identical results. Errors: INVALID_ARG, OOM,
+   CUDA. */
+RELSIM_API int relsim_field_modes(relsim_ctx* ctx, int component, int nmodes, double* energy, int where);
+
+/* Exponential growth rate of a positive series s[k] sampled at equal
+   steps dt (host code, no context): the least-squares slope of log s[k]
+   against k dt over every run of `window` consecutive samples
+   (2 <= window <= n), and the largest of them with the index of its first
+   sample. Runs containing a non-positive or non-finite sample are skipped.
+   For a mode energy the field amplitude grows at half this rate. Errors:
+   INVALID_ARG (bad sizes, NULL, dt <= 0, or no admissible run). */
+RELSIM_API int relsim_growth_fit(const double* s, int n, double dt, int window, double* rate, int* first);
+
+/* ---- batched independent instances (the paper has no counterpart: a
+   parameter scan of independent tearing runs, e.g. over L_x, the sheet
+   half-thickness and sigma, each instance a context of its own) ----
+   relsim_batch_create takes `count` contexts that hold a loaded state
+   (particles and fields) and `nworkers` host threads (1 <= nworkers <= 256).
+   The batch does not own the contexts: destroy them after the batch. Give
+   each context its own CUDA stream so instances overlap on the GPU.
+   Errors: INVALID_ARG, OOM. */
+typedef struct relsim_batch relsim_batch;
+RELSIM_API int relsim_batch_create(relsim_ctx* const* ctxs, int count, int nworkers, relsim_batch** out);
+
+/* Advance every instance nsteps full steps (relsim_step without the
+   ledger). The workers take instances largest first (by particle count) and
+   each runs its instance through all steps before taking the next; no two
+   threads touch one context. After every step of instance b the energies of
+   modes 0 .. nmodes-1 of B's component `component` (as relsim_field_modes)
+   go to modes[(b nsteps + s) nmodes + m] (host; pass NULL or nmodes = 0
+   to skip) and the step's GMRES iteration count to iters[b nsteps + s]
+   (host, may be NULL). status[b] (host, required) receives RELSIM_OK, the
+   first error of instance b (its later steps are skipped), or
+   RELSIM_ERR_NOT_CONVERGED if a solve hit gmres_maxit (the steps go on).
+   Returns RELSIM_OK when every status is OK, otherwise the first non-OK
+   status in instance order. Errors of the call itself: INVALID_ARG, OOM,
+   CUDA. */
+RELSIM_API int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, double* modes,
+                                int* status, int* iters);
+
+/* Free the batch (not its contexts). NULL is a no-op. */
+RELSIM_API void relsim_batch_destroy(relsim_batch* b);
+
 /* Library version (major*10000 + minor*100 + patch). */
 RELSIM_API int relsim_version(void);
 

@@ -17,7 +17,7 @@ from .build import build, lib_path
 __all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "curl_c",
            "curl_n", "rhs", "gmres", "field_update", "push", "energies", "cell_keys",
            "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
-           "to_full_offsets", "make_config", "spectrum"]
+           "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit"]
 
 
 class OracleConfig(ctypes.Structure):
@@ -295,3 +295,48 @@ def spectrum(ux, uy, uz, w, edges, variable=0, precision=64):
     nb = e.size + 1
     return (np.bincount(idx, weights=np.asarray(w, dtype=np.float64), minlength=nb),
             np.bincount(idx, minlength=nb).astype(np.int64))
+
+
+def field_modes(c, B, component=1, nmodes=8):
+    """Energy in the Fourier modes along x of one B component, the
+    linear-tearing diagnostic of Sec. 3.1 (Fig. 1: the B_y energy, its
+    low-pass part and single modes, whose growth gives the tearing rate).
+
+    B is the (3, ny*nx) cell-centre field. With F_{m,j} the DFT along x of
+    row j (numpy's FFT, FP64), the energy of mode m = 0 .. nmodes-1 is
+    (1/2) dV (c_m / nx) sum_j |F_{m,j}|^2, c_m = 1 for m = 0 and m = nx/2,
+    else 2 (mode m and its mirror nx - m), so that modes 0 .. nx/2 add up to
+    (1/2) sum B_c^2 dV by Parseval. Mode m has k = 2 pi m / L_x.
+    """
+    nx, ny = c.nx, c.ny
+    Bc = np.asarray(B, dtype=np.float64).reshape(3, ny, nx)[component]
+    F = np.fft.rfft(Bc, axis=1)
+    e = (np.abs(F) ** 2).sum(axis=0)
+    cm = np.full(e.size, 2.0)
+    cm[0] = 1.0
+    if nx % 2 == 0:
+        cm[-1] = 1.0
+    dV = c.dx * c.dy
+    return (0.5 * dV * cm * e / nx)[:nmodes]
+
+
+def growth_fit(s, dt, window):
+    """Exponential growth rate of a positive series (Sec. 3.1 measures the
+    tearing rate as a best fit over the linear phase): for every run of
+    `window` consecutive samples spaced dt, the least-squares slope of log s
+    against time (numpy's polyfit, degree 1); returns the largest slope and
+    the index of its run's first sample. Runs with a non-positive sample are
+    skipped."""
+    s = np.asarray(s, dtype=np.float64)
+    t = np.arange(window) * dt
+    best = None
+    for a in range(s.size - window + 1):
+        seg = s[a:a + window]
+        if np.any(~(seg > 0)) or not np.all(np.isfinite(seg)):
+            continue
+        slope = np.polyfit(t, np.log(seg), 1)[0]
+        if best is None or slope > best[0]:
+            best = (slope, a)
+    if best is None:
+        raise ValueError("no admissible window")
+    return best

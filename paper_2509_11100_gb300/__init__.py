@@ -28,6 +28,8 @@ __all__ = [
     "relsim_profile_enable", "relsim_profile_read", "relsim_kernel_launches", "PROFILE_SLOTS",
     "relsim_kinetic_energy_noalloc", "relsim_energy_spectrum", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
+    "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
+    "relsim_batch_destroy", "Batch",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -119,6 +121,11 @@ _SIGS = {
     "relsim_kinetic_energy_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     "relsim_energy_spectrum": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                               ctypes.c_int]),
+    "relsim_field_modes": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int]),
+    "relsim_growth_fit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P]),
+    "relsim_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "relsim_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "relsim_batch_destroy": (None, [_P]),
 }
 
 PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
@@ -358,6 +365,53 @@ def relsim_energy_spectrum(ctx, species, edges, variable=0, device=False):
     return wgt, cnt
 
 
+def relsim_field_modes(ctx, component, nmodes, device=False):
+    """Energy in the Fourier modes m = 0 .. nmodes-1 (along x) of one
+    component of B: (1/2) dV (c_m / nx) sum_j |DFT_x(B_c)(m, j)|^2."""
+    out = _out((nmodes,), np.float64, device)
+    po = _ptr(out, writable=True)
+    _check(ctx, lib().relsim_field_modes(ctx, component, nmodes, po[0], po[1]))
+    return out
+
+
+def relsim_growth_fit(s, dt, window):
+    """(rate, first): the largest least-squares slope of log s over runs of
+    `window` consecutive samples spaced dt, and the run's first index."""
+    a = np.ascontiguousarray(s, dtype=np.float64)
+    rate = ctypes.c_double()
+    first = ctypes.c_int()
+    code = lib().relsim_growth_fit(a.ctypes.data, a.size, float(dt), int(window), ctypes.byref(rate),
+                                   ctypes.byref(first))
+    if code != RELSIM_OK:
+        raise RelsimError(code, "growth fit: bad arguments or no admissible window")
+    return rate.value, first.value
+
+
+def relsim_batch_create(ctxs, nworkers):
+    arr = (_CTX * len(ctxs))(*ctxs)
+    b = _P()
+    code = lib().relsim_batch_create(arr, len(ctxs), int(nworkers), ctypes.byref(b))
+    if code != RELSIM_OK:
+        raise RelsimError(code, "batch create: bad arguments")
+    return b
+
+
+def relsim_batch_run(b, count, nsteps, component=1, nmodes=0):
+    """Advance every instance nsteps steps. Returns (modes[count, nsteps,
+    nmodes] or None, status[count], iters[count, nsteps], code)."""
+    modes = np.zeros((count, nsteps, nmodes)) if nmodes > 0 else None
+    status = np.zeros(count, dtype=np.int32)
+    iters = np.zeros((count, nsteps), dtype=np.int32)
+    code = lib().relsim_batch_run(b, int(nsteps), int(component), int(nmodes),
+                                  modes.ctypes.data if modes is not None else None, status.ctypes.data,
+                                  iters.ctypes.data)
+    return modes, status, iters, code
+
+
+def relsim_batch_destroy(b):
+    lib().relsim_batch_destroy(b)
+
+
 def relsim_push(ctx):
     return _check(ctx, lib().relsim_push(ctx))
 
@@ -480,3 +534,40 @@ class Simulation:
 
     def profile_read(self, reset=True):
         return relsim_profile_read(self.ctx, reset)
+
+    def field_modes(self, component=1, nmodes=8, device=False):
+        return relsim_field_modes(self.ctx, component, nmodes, device)
+
+
+class Batch:
+    """Independent Simulations advanced concurrently by `nworkers` host
+    threads (each Simulation should have a CUDA stream of its own). The
+    batch does not own the simulations."""
+
+    def __init__(self, sims, nworkers=8):
+        self.sims = list(sims)
+        self.b = relsim_batch_create([s.ctx for s in self.sims], nworkers)
+
+    def run(self, nsteps, component=1, nmodes=0):
+        """Returns (modes[count, nsteps, nmodes] or None, status[count],
+        iters[count, nsteps]); raises if an instance failed with anything
+        but NOT_CONVERGED."""
+        modes, status, iters, code = relsim_batch_run(self.b, len(self.sims), nsteps, component, nmodes)
+        bad = [i for i, s in enumerate(status) if s not in (RELSIM_OK, RELSIM_ERR_NOT_CONVERGED)]
+        if bad:
+            i = bad[0]
+            raise RelsimError(int(status[i]), f"instance {i}: " + relsim_last_error(self.sims[i].ctx))
+        if code not in (RELSIM_OK, RELSIM_ERR_NOT_CONVERGED):
+            raise RelsimError(code, "batch run failed")
+        return modes, status, iters
+
+    def close(self):
+        if getattr(self, "b", None):
+            relsim_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,201 @@
+// batch.cu -- independent instances advanced concurrently (a parameter scan
+// of tearing runs: uneven grid sizes, sheet thicknesses and magnetisations,
+// each instance a context on a stream of its own), and the exponential
+// growth-rate fit of a diagnostic series (Sec. 3.1: the tearing rate is the
+// best-fit slope of a mode's energy over its linear phase).
+//
+// Host threads drive the instances: each step of an instance waits on the
+// host a few times (GMRES read-backs), so one thread per in-flight instance
+// keeps several instances' kernels on the GPU at once while each thread
+// waits. Workers take instances largest first and run each one through all
+// steps, which balances uneven sizes without any barrier between steps.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <exception>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "launch.cuh"
+#include "relsim.h"
+
+struct relsim_batch {
+    std::vector<relsim_ctx*> ctx;
+    int nworkers = 1;
+    int device = 0;
+};
+
+using namespace relsim;
+
+extern "C" {
+
+int relsim_growth_fit(const double* s, int n, double dt, int window, double* rate, int* first)
+{
+    if (!s || !rate || n < 2 || window < 2 || window > n || !(dt > 0.0) || !std::isfinite(dt))
+        return RELSIM_ERR_INVALID_ARG;
+    // centred abscissae k - (window-1)/2 make the slope sum(k' y) / sum(k'^2)
+    const double kc = 0.5 * (double)(window - 1);
+    double sxx = 0.0;
+    for (int k = 0; k < window; ++k) sxx += ((double)k - kc) * ((double)k - kc);
+    bool found = false;
+    double best = 0.0;
+    int best_at = 0;
+    for (int a = 0; a + window <= n; ++a) {
+        double sxy = 0.0;
+        bool ok = true;
+        for (int k = 0; k < window && ok; ++k) {
+            const double v = s[a + k];
+            if (!(v > 0.0) || !std::isfinite(v)) ok = false;
+            else sxy += ((double)k - kc) * std::log(v);
+        }
+        if (!ok) continue;
+        const double slope = sxy / sxx / dt;
+        if (!found || slope > best) {
+            best = slope;
+            best_at = a;
+            found = true;
+        }
+    }
+    if (!found) return RELSIM_ERR_INVALID_ARG;
+    *rate = best;
+    if (first) *first = best_at;
+    return RELSIM_OK;
+}
+
+int relsim_batch_create(relsim_ctx* const* ctxs, int count, int nworkers, relsim_batch** out)
+{
+    if (!out) return RELSIM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!ctxs || count < 1 || nworkers < 1 || nworkers > 256) return RELSIM_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i]) return RELSIM_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return RELSIM_ERR_INVALID_ARG;   // one thread per context
+    }
+    relsim_batch* b = new (std::nothrow) relsim_batch;
+    if (!b) return RELSIM_ERR_OOM;
+    try {
+        b->ctx.assign(ctxs, ctxs + count);
+    } catch (...) {
+        delete b;
+        return RELSIM_ERR_OOM;
+    }
+    b->nworkers = std::min(nworkers, count);
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return RELSIM_ERR_CUDA;
+    }
+    *out = b;
+    return RELSIM_OK;
+}
+
+int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, double* modes, int* status,
+                     int* iters)
+{
+    if (!b || !status || nsteps < 0 || component < 0 || component > 2 || nmodes < 0)
+        return RELSIM_ERR_INVALID_ARG;
+    const int count = (int)b->ctx.size();
+    if (!modes) nmodes = 0;
+    for (int i = 0; i < count; ++i) status[i] = RELSIM_OK;
+    if (nsteps == 0) return RELSIM_OK;
+    if (cudaSetDevice(b->device) != cudaSuccess) return RELSIM_ERR_CUDA;
+
+    // device slots for the mode energies: (instance, step, mode); one
+    // call per context first, on the loaded state, sizes the context's
+    // diagnostic buffers before the workers start (no allocation while
+    // other instances run)
+    double* dmodes = nullptr;
+    const size_t per = (size_t)(nsteps + 1) * (size_t)nmodes;
+    if (nmodes > 0) {
+        if (cudaMalloc((void**)&dmodes, sizeof(double) * per * (size_t)count) != cudaSuccess)
+            return RELSIM_ERR_OOM;
+        for (int i = 0; i < count; ++i) {
+            const int r = relsim_field_modes(b->ctx[i], component, nmodes, dmodes + per * (size_t)i, RELSIM_DEVICE);
+            if (r != RELSIM_OK) {
+                cudaDeviceSynchronize();
+                cudaFree(dmodes);
+                return r;
+            }
+        }
+    }
+
+    // largest instances first
+    std::vector<int> order(count);
+    std::vector<int64_t> size(count);
+    for (int i = 0; i < count; ++i) {
+        order[i] = i;
+        size[i] = ctx_particles(b->ctx[i]);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return size[a] > size[c]; });
+
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        if (cudaSetDevice(b->device) != cudaSuccess) {
+            for (int k = next.fetch_add(count); k < count; ++k) status[order[k]] = RELSIM_ERR_CUDA;
+            return;
+        }
+        for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) {
+            const int i = order[k];
+            relsim_ctx* c = b->ctx[i];
+            int st = RELSIM_OK;
+            for (int s = 0; s < nsteps; ++s) {
+                const int r = relsim_step(c, nullptr);
+                if (r != RELSIM_OK && r != RELSIM_ERR_NOT_CONVERGED) {
+                    st = r;
+                    break;
+                }
+                if (r == RELSIM_ERR_NOT_CONVERGED && st == RELSIM_OK) st = r;
+                if (iters) iters[(size_t)i * nsteps + s] = ctx_last_iters(c);
+                if (nmodes > 0) {
+                    const int q = relsim_field_modes(c, component, nmodes,
+                                                     dmodes + per * (size_t)i + (size_t)(s + 1) * nmodes,
+                                                     RELSIM_DEVICE);
+                    if (q != RELSIM_OK) {
+                        st = q;
+                        break;
+                    }
+                }
+            }
+            if (cudaStreamSynchronize(ctx_stream(c)) != cudaSuccess && st == RELSIM_OK) st = RELSIM_ERR_CUDA;
+            status[i] = st;
+        }
+    };
+
+    int rc = RELSIM_OK;
+    std::vector<std::thread> pool;
+    try {
+        pool.reserve((size_t)b->nworkers);
+        for (int t = 0; t < b->nworkers; ++t) pool.emplace_back(worker);
+    } catch (...) {
+        rc = RELSIM_ERR_OOM;   // fewer threads started: the ones running finish the queue
+        if (pool.empty()) worker();
+    }
+    for (std::thread& t : pool) t.join();
+
+    if (nmodes > 0) {
+        cudaError_t e = cudaDeviceSynchronize();
+        std::vector<double> h;
+        try {
+            h.resize(per * (size_t)count);
+        } catch (...) {
+            cudaFree(dmodes);
+            return RELSIM_ERR_OOM;
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(h.data(), dmodes, sizeof(double) * h.size(), cudaMemcpyDeviceToHost);
+        cudaFree(dmodes);
+        if (e != cudaSuccess) return RELSIM_ERR_CUDA;
+        for (int i = 0; i < count; ++i)
+            std::copy(h.begin() + (ptrdiff_t)(per * (size_t)i + (size_t)nmodes),
+                      h.begin() + (ptrdiff_t)(per * (size_t)(i + 1)),
+                      modes + (size_t)i * nsteps * nmodes);
+    }
+    if (rc != RELSIM_OK) return rc;
+    for (int i = 0; i < count; ++i)
+        if (status[i] != RELSIM_OK) return status[i];
+    return RELSIM_OK;
+}
+
+void relsim_batch_destroy(relsim_batch* b) { delete b; }
+
+}  // extern "C"

@@ -107,6 +107,11 @@ struct relsim_ctx {
     unsigned long long* spec_c = nullptr;
     void* spec_e = nullptr;
     int spec_cap = 0;   // bins
+    // field-mode diagnostic: twiddles for modes < mode_tw_m, row sums
+    void* mode_tw = nullptr;
+    int mode_tw_m = 0;
+    double* mode_rows = nullptr;
+    int64_t mode_rows_cap = 0;   // doubles
     // staging for host <-> device copies
     double* stage = nullptr;
     int64_t stage_cap = 0;   // doubles
@@ -783,6 +788,35 @@ int spectrum_impl(relsim_ctx* c, int s, int variable, int nbins, const double* e
     return RELSIM_OK;
 }
 
+template <typename T>
+int modes_impl(relsim_ctx* c, int comp, int nmodes, double* energy, int where)
+{
+    const int nx = c->g.nx, ny = c->g.ny;
+    if (nmodes > c->mode_tw_m) {
+        dfree(c->mode_tw);
+        c->mode_tw_m = 0;
+        TRY(dalloc(c, &c->mode_tw, sizeof(T) * 2 * (size_t)nx * (size_t)nmodes));
+        CK(mode_twiddles<T>((T*)c->mode_tw, nx, nmodes, c->st));
+        c->mode_tw_m = nmodes;
+    }
+    const int64_t need = (int64_t)nmodes * (ny + 1);
+    if (need > c->mode_rows_cap) {
+        dfree(c->mode_rows);
+        c->mode_rows_cap = 0;
+        TRY(dalloc(c, &c->mode_rows, sizeof(double) * (size_t)need));
+        c->mode_rows_cap = need;
+    }
+    const int bnow = c->state == kSolved ? 1 - c->bcur : c->bcur;
+    const T* Bc = (const T*)c->B[bnow] + (int64_t)comp * c->g.ncell;
+    double* out = where == RELSIM_DEVICE ? energy : c->mode_rows + (int64_t)nmodes * ny;
+    CK(field_modes<T>(Bc, (const T*)c->mode_tw, nx, ny, nmodes, c->g.dV, c->mode_rows, out, c->st));
+    if (where == RELSIM_HOST) {
+        CK(cudaMemcpyAsync(energy, out, sizeof(double) * (size_t)nmodes, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    return RELSIM_OK;
+}
+
 int check_push(relsim_ctx* c)
 {
     if (*c->hpush & 2)
@@ -859,6 +893,17 @@ int validate(const relsim_config* cfg, std::string* why)
 }
 
 }  // namespace
+
+namespace relsim {
+cudaStream_t ctx_stream(const relsim_ctx* c) { return c->st; }
+int ctx_last_iters(const relsim_ctx* c) { return c->last_iters; }
+int64_t ctx_particles(const relsim_ctx* c)
+{
+    int64_t n = 0;
+    for (int s = 0; s < c->cfg.nspecies; ++s) n += c->sp[s].n;
+    return n;
+}
+}  // namespace relsim
 
 #define DISPATCH(fn, ...) (c->prec == 32 ? fn<float>(__VA_ARGS__) : fn<double>(__VA_ARGS__))
 
@@ -990,6 +1035,7 @@ void relsim_destroy(relsim_ctx* c)
     dfree(c->V); dfree(c->gw); dfree(c->gw2); dfree(c->gx); dfree(c->gb); dfree(c->partial);
     dfree(c->dsum); dfree(c->dled); dfree(c->dflag); dfree(c->dpush); dfree(c->stage);
     dfree(c->spec_w); dfree(c->spec_c); dfree(c->spec_e);
+    dfree(c->mode_tw); dfree(c->mode_rows);
     if (c->hpin) cudaFreeHost(c->hpin);
     if (c->hflag) cudaFreeHost(c->hflag);
     if (c->hpush) cudaFreeHost(c->hpush);
@@ -1244,6 +1290,17 @@ int relsim_energy_spectrum(relsim_ctx* c, int species, int variable, int nbins, 
 }
 
 int64_t relsim_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int relsim_field_modes(relsim_ctx* c, int component, int nmodes, double* energy, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (component < 0 || component > 2) return fail(c, RELSIM_ERR_INVALID_ARG, "component %d out of range", component);
+    if (nmodes < 1 || nmodes > c->g.nx / 2 + 1)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "nmodes %d outside [1, nx/2 + 1]", nmodes);
+    if (!energy) return fail(c, RELSIM_ERR_INVALID_ARG, "null output");
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    return DISPATCH(modes_impl, c, component, nmodes, energy, where);
+}
 
 int relsim_step(relsim_ctx* c, relsim_energy* ledger)
 {

@@ -163,4 +163,22 @@ cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, doubl
                             cudaStream_t st);
 int gm_blocks(int64_t n);
 
+// ----- diag.cu -----
+// tw[2 (m nx + i) + {0, 1}] = cos, sin of 2 pi ((m i) mod nx) / nx, m < nmodes
+template <typename T>
+cudaError_t mode_twiddles(T* tw, int nx, int nmodes, cudaStream_t st);
+// out[m] = (1/2) dV (c_m / nx) sum_j |sum_i Bc(i,j) e^{-2 pi i m i/nx}|^2 for
+// m < nmodes (Bc: one component, ny rows of nx); rows: nmodes * ny doubles
+template <typename T>
+cudaError_t field_modes(const T* Bc, const T* tw, int nx, int ny, int nmodes, double dV, double* rows,
+                        double* out, cudaStream_t st);
+
+}  // namespace relsim
+
+// ----- capi.cu: what the batch runner needs of a context -----
+struct relsim_ctx;
+namespace relsim {
+cudaStream_t ctx_stream(const relsim_ctx* c);
+int ctx_last_iters(const relsim_ctx* c);
+int64_t ctx_particles(const relsim_ctx* c);
 }  // namespace relsim

@@ -6,6 +6,8 @@ import os
 import re
 import shutil
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -90,3 +92,42 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(rs, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(rs.RelsimUnavailable):
         rs.lib()
+
+
+def test_growth_fit_host_code_matches_oracle(librelsim):
+    # relsim_growth_fit is host code: it runs without a GPU
+    import oracle
+    rng = np.random.default_rng(5)
+    for n, window, dt in [(40, 8, 0.5), (200, 50, 0.25), (7, 7, 1.0), (12, 2, 2.0)]:
+        t = np.arange(n) * dt
+        s = np.exp(0.3 * t - 0.002 * t * t + 0.05 * rng.normal(size=n))
+        rate, first = librelsim.relsim_growth_fit(s, dt, window)
+        orate, ofirst = oracle.growth_fit(s, dt, window)
+        assert first == ofirst
+        assert abs(rate - orate) < 1e-10 * max(1.0, abs(orate))
+    s = np.exp(np.arange(10.0))
+    s[4] = -1.0
+    rate, first = librelsim.relsim_growth_fit(s, 1.0, 3)
+    assert not (first <= 4 < first + 3) and abs(rate - 1.0) < 1e-12
+    L = librelsim.lib()
+    r, f = ctypes.c_double(), ctypes.c_int()
+    for args in [(None, 5, 1.0, 2), (s.ctypes.data, 1, 1.0, 2), (s.ctypes.data, 10, 1.0, 11),
+                 (s.ctypes.data, 10, 0.0, 3), (s.ctypes.data, 10, 1.0, 1)]:
+        assert L.relsim_growth_fit(*args, ctypes.byref(r), ctypes.byref(f)) == librelsim.RELSIM_ERR_INVALID_ARG
+    neg = -np.ones(6)
+    assert L.relsim_growth_fit(neg.ctypes.data, 6, 1.0, 3, ctypes.byref(r), None) == librelsim.RELSIM_ERR_INVALID_ARG
+
+
+def test_batch_rejects_bad_arguments(librelsim):
+    L = librelsim.lib()
+    out = ctypes.c_void_p()
+    assert L.relsim_batch_create(None, 1, 1, ctypes.byref(out)) == librelsim.RELSIM_ERR_INVALID_ARG
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.relsim_batch_create(arr, 2, 1, ctypes.byref(out)) == librelsim.RELSIM_ERR_INVALID_ARG
+    assert L.relsim_batch_create(arr, 0, 1, ctypes.byref(out)) == librelsim.RELSIM_ERR_INVALID_ARG
+    assert L.relsim_batch_create(arr, 2, 1, None) == librelsim.RELSIM_ERR_INVALID_ARG
+    assert not out.value
+    st = np.zeros(1, dtype=np.int32)
+    assert L.relsim_batch_run(None, 1, 1, 0, None, st.ctypes.data, None) == librelsim.RELSIM_ERR_INVALID_ARG
+    L.relsim_batch_destroy(None)
+    assert L.relsim_field_modes(None, 1, 1, None, 0) == librelsim.RELSIM_ERR_INVALID_ARG

@@ -1,8 +1,8 @@
 """The oracle pins catch plausible mistakes.
 
 Each case copies oracle/ to a temporary directory, plants one mistake in the
-C source (a dropped term, a flipped sign, a wrong index or a transposed
-operand), rebuilds it there and runs the pin suite against the copy, which
+C source or the Python diagnostics (a dropped term, a flipped sign, a wrong
+index or a transposed operand), rebuilds it there and runs the pin suite against the copy, which
 must then fail. The committed oracle is never modified.
 """
 import os
@@ -54,15 +54,28 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+# mistakes planted in the Python part of the oracle (diagnostics)
+PY_MUTANTS = {
+    "modes_no_mirror_factor": ("cm = np.full(e.size, 2.0)", "cm = np.full(e.size, 1.0)"),
+    "modes_nyquist_counted_twice": ("        cm[-1] = 1.0", "        cm[-1] = 2.0"),
+    "modes_drops_cell_volume": ("return (0.5 * dV * cm * e / nx)[:nmodes]", "return (0.5 * cm * e / nx)[:nmodes]"),
+    "modes_wrong_axis": ("F = np.fft.rfft(Bc, axis=1)", "F = np.fft.rfft(Bc.T, axis=1)"),
+    "growth_fit_no_log": ("np.polyfit(t, np.log(seg), 1)[0]", "np.polyfit(t, seg, 1)[0]"),
+    "growth_fit_smallest": ("if best is None or slope > best[0]:", "if best is None or slope < best[0]:"),
+}
+CASES = {**{k: ("relsim_oracle.c",) + v for k, v in MUTANTS.items()},
+         **{k: ("__init__.py",) + v for k, v in PY_MUTANTS.items()}}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    orig, repl = MUTANTS[name]
+    fname, orig, repl = CASES[name]
     src_dir = os.path.join(ROOT, "oracle")
-    src = open(os.path.join(src_dir, "relsim_oracle.c")).read()
+    src = open(os.path.join(src_dir, fname)).read()
     assert src.count(orig) == 1, f"mutation site for {name} is not unique"
     dst = tmp_path / "oracle"
     shutil.copytree(src_dir, dst, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
-    (dst / "relsim_oracle.c").write_text(src.replace(orig, repl))
+    (dst / fname).write_text(src.replace(orig, repl))
     env = dict(os.environ, RELSIM_ORACLE_MUTANT_DIR=str(tmp_path))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],

@@ -556,3 +556,95 @@ def test_spectrum_of_maxwell_juttner_matches_the_analytic_distribution(orc):
     sd = np.sqrt(np.maximum(expect, 1.0))
     assert np.max(np.abs(ct - expect) / sd) < 5.0
     assert ct.sum() == n
+
+
+# ---------------------------------------------------------------------------
+# field-mode energies and the growth fit (linear-tearing diagnostic, Sec. 3.1)
+
+@pytest.mark.parametrize("nx,ny", [(16, 6), (15, 7)])
+def test_field_modes_parseval(orc, nx, ny):
+    # the energies of modes 0 .. nx/2 add up to the component's field energy
+    c = orc.make_config(nx, ny, dx=0.7, dy=1.3)
+    B = np.random.default_rng(11).normal(size=(3, nx * ny))
+    for comp in range(3):
+        W = orc.field_modes(c, B, comp, nx // 2 + 1)
+        assert W.size == nx // 2 + 1
+        assert np.all(W >= 0)
+        direct = 0.5 * c.dx * c.dy * np.sum(B[comp] ** 2)
+        assert abs(W.sum() - direct) < 1e-12 * direct
+
+
+def test_field_modes_of_a_single_cosine(orc):
+    # B_y = C + A cos(2 pi m0 i / nx + phase): all the oscillating energy,
+    # (1/4) A^2 nx ny dV, sits in mode m0, and (1/2) C^2 nx ny dV in mode 0
+    nx, ny, m0, A, C = 24, 5, 3, 0.7, -0.2
+    c = orc.make_config(nx, ny, dx=0.5, dy=2.0)
+    dV = c.dx * c.dy
+    for phase in (0.0, 0.9, -np.pi / 2):
+        B = np.zeros((3, ny, nx))
+        B[1] = C + A * np.cos(2 * np.pi * m0 * np.arange(nx) / nx + phase)[None, :]
+        W = orc.field_modes(c, B.reshape(3, -1), 1, nx // 2 + 1)
+        expect = np.zeros(nx // 2 + 1)
+        expect[0] = 0.5 * C * C * nx * ny * dV
+        expect[m0] = 0.25 * A * A * nx * ny * dV
+        assert np.allclose(W, expect, rtol=1e-12, atol=1e-12)
+
+
+def test_field_modes_nyquist_and_row_independence(orc):
+    # the alternating pattern (-1)^i is the Nyquist mode (counted once), and
+    # rows with different amplitudes add their energies
+    nx, ny = 8, 3
+    c = orc.make_config(nx, ny)
+    amp = np.array([1.0, 2.0, -3.0])
+    B = np.zeros((3, ny, nx))
+    B[2] = amp[:, None] * (-1.0) ** np.arange(nx)[None, :]
+    W = orc.field_modes(c, B.reshape(3, -1), 2, nx // 2 + 1)
+    assert np.allclose(W[:-1], 0.0, atol=1e-12)
+    assert abs(W[-1] - 0.5 * nx * np.sum(amp ** 2)) < 1e-12
+
+
+def test_growth_fit_recovers_an_exponential(orc):
+    t = np.arange(50) * 0.25
+    rate, first = orc.growth_fit(3.0 * np.exp(0.37 * t), 0.25, 10)
+    assert abs(rate - 0.37) < 1e-12
+    # growth, then saturation: the best window lies in the growth phase
+    s = np.concatenate([np.exp(0.5 * t[:30]), np.full(20, np.exp(0.5 * t[29]))])
+    rate, first = orc.growth_fit(s, 0.25, 10)
+    assert abs(rate - 0.5) < 1e-12 and first + 10 <= 30
+    # decay: the largest slope is still the (negative) decay rate
+    rate, _ = orc.growth_fit(np.exp(-0.2 * t), 0.25, 7)
+    assert abs(rate + 0.2) < 1e-12
+
+
+def test_growth_fit_skips_nonpositive_samples(orc):
+    s = np.exp(0.1 * np.arange(20))
+    s[3] = 0.0
+    rate, first = orc.growth_fit(s, 1.0, 5)
+    assert first >= 4 and abs(rate - 0.1) < 1e-12
+    with pytest.raises(ValueError):
+        orc.growth_fit(-np.ones(6), 1.0, 3)
+
+
+def test_splitmix64_reference_outputs():
+    # published SplitMix64 outputs from state 0
+    from relsim_inputs import splitmix64
+    s, out = 0, []
+    for _ in range(3):
+        s, o = splitmix64(s)
+        out.append(o)
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_tearing_scan_instances():
+    from relsim_inputs import SCAN_DELTA, SCAN_LX, SCAN_SIGMA, tearing_scan
+    L = tearing_scan(48, seed=0)
+    assert len(L) == 48
+    assert all(c.nx in SCAN_LX and c.ny == c.nx // 2 and c.ppc == 32 for c in L)
+    assert all(c.delta in SCAN_DELTA and c.sigma in SCAN_SIGMA for c in L)
+    assert [c.seed for c in L] == list(range(48))
+    # every box length, thickness and magnetisation occurs
+    assert {c.nx for c in L} == set(SCAN_LX)
+    assert {c.delta for c in L} == set(SCAN_DELTA) and {c.sigma for c in L} == set(SCAN_SIGMA)
+    total = sum(2 * c.nx * c.ny * c.ppc for c in L)
+    assert 200e6 < total < 400e6
+    assert tearing_scan(48, seed=0) == L and tearing_scan(48, seed=1) != L
