@@ -139,6 +139,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def max_over_ranks(x, dist):
+    """The largest x over all ranks (NCCL reduces a CUDA tensor, gloo a CPU one)."""
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def traffic_record(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
@@ -231,9 +240,7 @@ def run_ours(args):
     prof = sim.profile_read(reset=True)
     sim.profile(False)
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist)
     value = world * N / (ms / 1e3)
 
     # per-kernel times, dominant kernel roofline
@@ -326,9 +333,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         te = (time.perf_counter() - t1) / ke
         if dist is not None:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+            te = max_over_ranks(te, dist)
         out["e2e"] = {"value": world * N / te, "unit": UNIT, "ms_per_step": te * 1e3,
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                       "steps": ke}
@@ -429,6 +434,155 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+SCAN = {
+    "workload": "batched linear tearing scan: 48 independent 2D pair-plasma double Harris sheets, "
+                "L_x from {128,192,256,384,512,768} cells (L_y = L_x/2), delta from {0.5,1,2} d_e, "
+                "sigma from {1,10,40} (SplitMix64 draws from seed 0), theta_T=0.3, 32 ppc per species, "
+                "0.1% B_y perturbation, dt=0.5/omega_pe, theta=0.5",
+    "form": "FP32 particles/fields/mass matrix, FP64 GMRES basis and ledger",
+    "gmres_tol": 1e-6, "gmres_restart": 30,
+    "l2": "inputs larger than L2 (about 8 GB of particle data per step), no flush",
+}
+
+
+def lpt_shard(sizes, world):
+    """Instances per rank: largest first onto the least-loaded rank."""
+    load = [0] * world
+    owner = [0] * len(sizes)
+    for i in sorted(range(len(sizes)), key=lambda k: -sizes[k]):
+        r = min(range(world), key=lambda q: load[q])
+        owner[i] = r
+        load[r] += sizes[i]
+    return owner
+
+
+def run_scan(args):
+    """The 48-instance tearing scan, advanced by the library's batch runner
+    (one context and stream per instance, host worker threads); instances
+    are sharded whole across ranks (no exchange)."""
+    import numpy as np
+    import torch
+    import paper_2509_11100_gb300 as rs
+    from relsim_inputs import make_harris, tearing_scan
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    insts = tearing_scan(48, seed=0)
+    sizes = [2 * hc.nx * hc.ny * hc.ppc for hc in insts]
+    owner = lpt_shard(sizes, world)
+    mine = [i for i in range(len(insts)) if owner[i] == rank]
+    t0 = time.time()
+    streams, sims = [], []
+    for i in mine:
+        hc = insts[i]
+        st = make_harris(hc)
+        stream = torch.cuda.Stream()
+        sim = rs.Simulation(rs.make_config(hc.nx, hc.ny, dt=hc.dt, theta_implicit=hc.theta, precision=32,
+                                           gmres_tol=SCAN["gmres_tol"], gmres_restart=SCAN["gmres_restart"]),
+                            stream=stream.cuda_stream)
+        sim.load_state(st)
+        del st
+        streams.append(stream)
+        sims.append(sim)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t0
+    N = sum(sizes[i] for i in mine)
+    batch = rs.Batch(sims, nworkers=args.workers)
+    batch.run(args.warmup)
+    torch.cuda.synchronize()
+
+    # device span: every instance stream waits on ev0; the default stream
+    # waits on every instance stream before ev1
+    clocks = ClockSampler(local)
+    dflt = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = rs.relsim_kernel_launches()
+    ev0.record(dflt)
+    for st in streams:
+        st.wait_event(ev0)
+    t1 = time.perf_counter()
+    modes, status, iters = batch.run(args.steps, component=1, nmodes=2)
+    wall = time.perf_counter() - t1
+    for st in streams:
+        e = torch.cuda.Event()
+        e.record(st)
+        dflt.wait_event(e)
+    ev1.record(dflt)
+    torch.cuda.synchronize()
+    launches = rs.relsim_kernel_launches() - launches0
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        ms = max_over_ranks(ms, dist)
+    total = sum(sizes)
+    value = total / (ms / 1e3) if world > 1 else N / (ms / 1e3)
+    batch.close()
+    for sim in sims:
+        sim.close()
+
+    # per instance: the m = 1 B_y mode's energy growth rate over its best
+    # 40-step window (the field amplitude grows at half of it)
+    rows = []
+    win = min(40, args.steps)
+    for k, i in enumerate(mine):
+        hc = insts[i]
+        try:
+            rate, first = rs.relsim_growth_fit(modes[k, :, 1], hc.dt, win) if win >= 2 else (None, None)
+        except rs.RelsimError:
+            rate, first = None, None
+        rows.append({"index": i, "nx": hc.nx, "ny": hc.ny, "delta": hc.delta, "sigma": hc.sigma,
+                     "particles": sizes[i], "status": int(status[k]),
+                     "gmres_iters_mean": float(np.mean(iters[k])) if args.steps else None,
+                     "m1_energy_growth_rate": rate, "fit_window_first_step": first})
+    # algorithmic bytes of the particle passes and mass-matrix flush per step
+    esz = 4
+    mover = 0
+    for i in mine:
+        hc = insts[i]
+        n, ncell = sizes[i], hc.nx * hc.ny
+        mover += algorithmic_bytes("deposit", n, 0, ncell, esz)
+        mover += 2 * (algorithmic_bytes("push", 0, n // 2, ncell, esz)
+                      + algorithmic_bytes("permute", 0, n // 2, ncell, esz))
+    peak, peak_kind = measured_peaks()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(SCAN, instances=len(insts), instances_here=len(mine), particles_total=total,
+                       particles_here=N, workers=args.workers,
+                       parallelism=f"instances sharded over {world} ranks" if world > 1 else "single"),
+        "step_effective": {"mover_bytes_per_step": mover, "gbs": mover / (ms / 1e3) / 1e9,
+                           "frac_of_peak": mover / (ms / 1e3) / 1e9 / peak, "peak": peak,
+                           "peak_source": peak_kind,
+                           "note": "particle passes + mass-matrix flush bytes over the whole step's span "
+                                   "(GMRES and host waits included)"},
+        "host_wall_ms_per_step": wall * 1e3 / max(1, args.steps),
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "setup_s": t_setup,
+        "instances": rows,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,13 +592,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["c1", "small"], default="c1",
-                    help="small: 512x256 cells for profiler captures")
+    ap.add_argument("--workload", choices=["c1", "small", "scan"], default="c1",
+                    help="small: 512x256 cells for profiler captures; scan: the 48-instance batched "
+                         "tearing scan (run with --steps 400 for its full length)")
+    ap.add_argument("--workers", type=int, default=8, help="host worker threads of the scan's batch runner")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "scan":
+        run_scan(args)
     else:
         run_ours(args)
 
