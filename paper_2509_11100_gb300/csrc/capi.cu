@@ -297,7 +297,10 @@ int ensure_species(relsim_ctx* c, int s, int64_t n)
     return RELSIM_OK;
 }
 
-// copy a caller array to the device (or use it in place)
+// copy a caller array to the device (or use it in place). Page-locked host
+// memory that is mapped into the device's address space is read in place by
+// the consuming kernel, over the host link, with no staging copy; the caller
+// synchronises before returning, so no caller pointer outlives the call.
 int stage_in(relsim_ctx* c, const double* src, int64_t count, int where, const double** dev,
              int64_t stage_off)
 {
@@ -305,6 +308,12 @@ int stage_in(relsim_ctx* c, const double* src, int64_t count, int where, const d
         *dev = src;
         return RELSIM_OK;
     }
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+        *dev = (const double*)at.devicePointer;
+        return RELSIM_OK;
+    }
+    (void)cudaGetLastError();   // an unregistered pointer is not an error here
     CK(cudaMemcpyAsync(c->stage + stage_off, src, sizeof(double) * (size_t)count,
                        cudaMemcpyHostToDevice, c->st));
     *dev = c->stage + stage_off;
