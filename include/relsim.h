@@ -194,8 +194,12 @@ RELSIM_API int relsim_set_mass_matrix(relsim_ctx* ctx, const double* M, const do
 
 /* Step part 2: GMRES solve for E^{n+theta}, then E^{n+1}, B^{n+1}.
    *iters (may be NULL) receives the Arnoldi steps, *rel_residual (may be
-   NULL) the true relative residual. Synchronises the stream (the restart
-   loop checks convergence on the host). Errors: BAD_STATE (not built),
+   NULL) the true relative residual. Synchronises the stream. The restart
+   and Arnoldi decisions (Givens rotations, stop tests, the triangular
+   solve) are taken on the device; here the host only reads them to know
+   when to stop enqueueing iterations. A cycle whose new basis vector loses
+   orthogonality (|w - V h|^2 < 1e-4 |w|^2) ends without it and restarts
+   from the true residual. Errors: BAD_STATE (not built),
    NOT_CONVERGED (gmres_maxit reached; the fields are still advanced with
    the best iterate), NONFINITE, CUDA. */
 RELSIM_API int relsim_field_solve(relsim_ctx* ctx, int* iters, double* rel_residual);
@@ -221,8 +225,21 @@ RELSIM_API int relsim_energy_ledger(relsim_ctx* ctx, relsim_energy* out);
 
 /* One full step: build, solve, push; fills *ledger if it is non-NULL.
    Returns the first error of its parts (NOT_CONVERGED still completes the
-   step). */
+   step). The first step after a load runs its parts from the host; later
+   steps (when profiling is off and no particle can cross more than one cell
+   per step) run as one CUDA graph captured on first use for the current
+   buffer layout: the solve's restart and Arnoldi loops are conditional while
+   nodes whose conditions the device sets, so the step needs one launch and
+   one synchronisation. Both routes run the same kernels in the same order.
+   If capturing fails the context keeps stepping from the host (see
+   relsim_graph_info). A NONFINITE solve in a graph step is reported after
+   the whole step ran (the state is then invalid, as on the host route). */
 RELSIM_API int relsim_step(relsim_ctx* ctx, relsim_energy* ledger);
+
+/* Whether steps run as graphs: *graph_steps (may be NULL) = steps run as a
+   graph so far; *disabled = 1 if a capture failed and *why (owned by the
+   context) says why. Errors: INVALID_ARG. */
+RELSIM_API int relsim_graph_info(const relsim_ctx* ctx, int64_t* graph_steps, int* disabled, const char** why);
 
 /* Particle energy spectrum of a species (diagnostic; the paper's spectra,
    Sec. 3.2 "Nonlinear reconnection and spectra" and its spectrum figures,

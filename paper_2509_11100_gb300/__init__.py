@@ -29,7 +29,7 @@ __all__ = [
     "relsim_kinetic_energy_noalloc", "relsim_energy_spectrum", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
     "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
-    "relsim_batch_destroy", "Batch",
+    "relsim_batch_destroy", "Batch", "relsim_graph_info",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -126,6 +126,7 @@ _SIGS = {
     "relsim_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "relsim_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "relsim_batch_destroy": (None, [_P]),
+    "relsim_graph_info": (ctypes.c_int, [_CTX, _P, _P, _P]),
 }
 
 PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
@@ -387,6 +388,16 @@ def relsim_growth_fit(s, dt, window):
     return rate.value, first.value
 
 
+def relsim_graph_info(ctx) -> dict:
+    """{"graph_steps": steps run as a CUDA graph, "disabled": capture failed,
+    "why": the failure}."""
+    n = ctypes.c_int64()
+    d = ctypes.c_int()
+    why = ctypes.c_char_p()
+    _check(ctx, lib().relsim_graph_info(ctx, ctypes.byref(n), ctypes.byref(d), ctypes.byref(why)))
+    return {"graph_steps": n.value, "disabled": bool(d.value), "why": (why.value or b"").decode()}
+
+
 def relsim_batch_create(ctxs, nworkers):
     arr = (_CTX * len(ctxs))(*ctxs)
     b = _P()
@@ -534,6 +545,9 @@ class Simulation:
 
     def profile_read(self, reset=True):
         return relsim_profile_read(self.ctx, reset)
+
+    def graph_info(self):
+        return relsim_graph_info(self.ctx)
 
     def field_modes(self, component=1, nmodes=8, device=False):
         return relsim_field_modes(self.ctx, component, nmodes, device)

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <limits>
@@ -16,7 +17,13 @@
 
 namespace relsim {
 static std::atomic<long long> g_launches{0};
-void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// while a step graph is captured, launches count into the graph's tally
+static thread_local long long* t_capture_count = nullptr;
+void count_launches(int n)
+{
+    if (t_capture_count) *t_capture_count += n;
+    else g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 }  // namespace relsim
 
 using namespace relsim;
@@ -55,6 +62,17 @@ struct Prof {
     int open_slot = -1;
     size_t open_ev = 0;
     long long open_k = 0;
+};
+
+// One step captured as a CUDA graph (deposit, the solve with its loops as
+// conditional while nodes, field update, push and re-sort), valid for the
+// buffer layout it was captured on.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t gen = 0;
+    int bcur = -1;
+    int32_t* start[kMaxSpecies] = {};
+    long long k_static = 0, k_cycle = 0, k_iter = 0;   // kernels outside the loops, per cycle, per iteration
 };
 
 }  // namespace
@@ -99,7 +117,19 @@ struct relsim_ctx {
     double* hpin = nullptr;    // pinned host, 4*(kMaxRestart+2)
     int* dflag = nullptr;
     int* hflag = nullptr;
-    cudaEvent_t gev[2] = {nullptr, nullptr};   // read-back events of the pipelined Arnoldi loop
+    cudaEvent_t gev[2] = {nullptr, nullptr};   // read-back events of the host-driven Arnoldi loop
+    GmState* gms = nullptr;    // device-side GMRES control state
+    GmState* ghead = nullptr;  // pinned host, two read-back slots (heads only)
+    // step graphs (two layouts alternate from step to step)
+    StepGraph sg[2];
+    uint64_t gen = 1;          // bumped whenever a buffer or the loaded state changes
+    bool graph_off = false;    // a capture failed: host-driven steps from then on
+    std::string graph_why;     // why
+    int64_t graph_steps = 0;   // steps run as a graph
+    bool capturing = false;
+    cudaStream_t gst = nullptr;        // graph stream, joined to st by events
+    cudaStream_t aux[2] = {nullptr, nullptr};   // capture streams of the loop bodies
+    cudaEvent_t gjoin[2] = {nullptr, nullptr};
     int* dpush = nullptr;     // set by the push if its two passes ever disagree
     int* hpush = nullptr;
     // spectrum diagnostic (grown on demand)
@@ -138,6 +168,7 @@ int fail(relsim_ctx* c, int code, const char* fmt, ...)
 }
 
 int check_push(relsim_ctx* c);
+int ledger_fill(relsim_ctx* c, const double* h, relsim_energy* out);
 
 #define CK(call)                                                                             \
     do {                                                                                     \
@@ -198,6 +229,8 @@ template <class P>
 int dalloc(relsim_ctx* c, P** p, size_t bytes)
 {
     *p = nullptr;
+    if (c->capturing) return fail(c, RELSIM_ERR_INTERNAL, "device allocation while a step graph is captured");
+    ++c->gen;   // captured step graphs may hold the buffer this replaces
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc((void**)p, bytes);
     if (e != cudaSuccess) {
@@ -514,194 +547,194 @@ int readback(relsim_ctx* c, const double* dev, int count, double* host)
     return RELSIM_OK;
 }
 
+// Restarted GMRES on A = I + B, controlled on the device (gmres.cu). The
+// Arnoldi process runs on B (the same Krylov space: A V_k = V_k + B V_k, so
+// the Hessenberg matrix of A is that of B plus the identity). Working on B
+// avoids the cancellation of orthogonalising A v ~ v against v, and keeps the
+// identity exact in FP64. The pieces below enqueue on a given stream; each
+// takes the graph condition it sets (0 when driven from the host).
+struct GmSetup {
+    int64_t n, ldv;
+    int m, nb, nbo;
+    GmPtrs p;
+    GmParams q;
+};
+
+GmSetup gm_setup(relsim_ctx* c)
+{
+    GmSetup s;
+    s.n = c->nvec;
+    s.ldv = s.n;
+    s.m = c->mrest;
+    s.nb = gm_blocks(s.n);
+    s.nbo = op_blocks(c->g, c->prec);
+    s.p.r = c->gw;
+    s.p.w0 = c->gw2;
+    s.p.V = c->V;
+    s.p.ds0 = c->dsum;
+    s.p.ds1 = c->dsum + 3 * (kMaxRestart + 2);
+    s.p.ldv = s.ldv;
+    s.q.tol = c->cfg.gmres_tol;
+    s.q.m = s.m;
+    s.q.maxit = c->cfg.gmres_maxit;
+    return s;
+}
+
+// b, x = E^n, |b|, r = b - A x, |r|, start of the first cycle
+template <typename T>
+int solve_prologue(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond outer)
+{
+    PROF_BEGIN(RELSIM_PROF_RHS);
+    CK(rhs<T>((const T*)c->E, (const T*)c->B[c->bcur], (const T*)c->J, c->gb, c->g, s));
+    CK(fields_to_double<T>((const T*)c->E, c->gx, S.n, s));
+    PROF_END();
+    PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
+    CK(gm_dots(c->V, S.ldv, 0, c->gb, S.n, c->partial, S.nb, s));
+    CK(reduce_partials(c->partial, S.nb, 1, c->dsum, s));
+    CK(gm_begin(c->gms, c->dsum, s));
+    CK(gm_zero_x(c->gms, c->gx, S.n, s));
+    PROF_END();
+    PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
+    CK(op_residual<T>((const T*)c->M, c->gx, c->gb, S.p.r, c->g, c->partial, c->dpush, s));
+    CK(reduce_partials(c->partial, S.nbo, 1, c->dsum, s));
+    CK(gm_cycle(c->gms, c->dsum, S.p, S.q, outer, s));
+    PROF_END();
+    return RELSIM_OK;
+}
+
+// one Arnoldi iteration with the arguments the device left in gms->dyn
+template <typename T>
+int arnoldi_body(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond inner)
+{
+    PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
+    CK(op_arnoldi_dyn<T>((const T*)c->M, &c->gms->dyn, c->V, S.ldv, c->g, c->partial, c->dpush, s));
+    PROF_END();
+    PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
+    CK(reduce_partials_dyn(c->partial, S.nbo, &c->gms->dyn, S.m + 2, s));
+    CK(gm_update_scale_dyn(&c->gms->dyn, c->V, S.ldv, S.n, s));
+    CK(gm_tail(c->gms, S.p, S.q, inner, s));
+    PROF_END();
+    return RELSIM_OK;
+}
+
+// x += V y of the finished cycle, the true residual, next cycle or stop
+template <typename T>
+int cycle_end(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond outer)
+{
+    PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
+    CK(gm_finish_cycle(c->gms, c->gx, c->V, S.ldv, S.n, S.m, s));
+    PROF_END();
+    PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
+    CK(op_residual<T>((const T*)c->M, c->gx, c->gb, S.p.r, c->g, c->partial, c->dpush, s));
+    CK(reduce_partials(c->partial, S.nbo, 1, c->dsum, s));
+    CK(gm_cycle(c->gms, c->dsum, S.p, S.q, outer, s));
+    PROF_END();
+    return RELSIM_OK;
+}
+
+// E^{n+1}, B^{n+1} and the field side of the ledger
+template <typename T>
+int solve_epilogue(relsim_ctx* c, cudaStream_t s)
+{
+    CK(cudaMemcpyAsync(c->dled + kLedgerLen - 2, c->dled + 3, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int nbf = field_grid_blocks(c->g);
+    PROF_BEGIN(RELSIM_PROF_FIELD_UPDATE);
+    CK(field_update<T>(c->gx, (const T*)c->M, (const T*)c->J, (T*)c->Eth, (T*)c->E, (const T*)c->B[c->bcur],
+                       (T*)c->B[1 - c->bcur], c->g, c->partial, nbf, s));
+    CK(reduce_partials(c->partial, nbf, 6, c->dled, s));
+    PROF_END();
+    return RELSIM_OK;
+}
+
+// buffers the solve needs, sized before anything is enqueued (a graph
+// capture must not allocate)
+int solve_reserve(relsim_ctx* c, const GmSetup& S)
+{
+    const int nbf = field_grid_blocks(c->g);
+    int64_t need = (int64_t)(S.nb > S.nbo ? S.nb : S.nbo) * (S.m + 2);
+    if ((int64_t)nbf * 6 > need) need = (int64_t)nbf * 6;
+    return ensure_partial(c, need);
+}
+
+// the solve's outcome from the device state read back after it
+int solve_outcome(relsim_ctx* c, const GmState* h, int* iters_out, double* relres_out)
+{
+    c->last_iters = h->total;
+    c->last_restarts = h->restarts;
+    c->last_relres = h->relres;
+    if (iters_out) *iters_out = h->total;
+    if (relres_out) *relres_out = h->relres;
+    if (h->status == kGmNonfinite) return fail(c, RELSIM_ERR_NONFINITE, "non-finite value in the field solve");
+    if (h->status == kGmNotConverged)
+        return fail(c, RELSIM_ERR_NOT_CONVERGED, "GMRES reached %d iterations at relative residual %.3e", h->total,
+                    h->relres);
+    return RELSIM_OK;
+}
+
+constexpr size_t kGmHead = offsetof(GmState, cs);
+
+// the control state's head into host slot k (and the kernels' error flags)
+int head_async(relsim_ctx* c, int k)
+{
+    CK(cudaMemcpyAsync(c->ghead + k, c->gms, kGmHead, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c->hpush, c->dpush, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    return RELSIM_OK;
+}
+
+// The solve driven from the host: the same kernels as the graph, with the
+// host reading the device's decisions. Iteration j+1 is enqueued before
+// iteration j's decision is read (it returns at once if j was the last).
 template <typename T>
 int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
 {
-    // Restarted GMRES on A = I + B. The Arnoldi process runs on B (the same
-    // Krylov space: A V_k = V_k + B V_k, so the Hessenberg matrix of A is that
-    // of B plus the identity). Working on B avoids the cancellation of
-    // orthogonalising A v ~ v against v, and keeps the identity exact in FP64.
-    const int64_t n = c->nvec;
-    const int64_t ldv = n;
-    const int m = c->mrest;
-    const int nb = gm_blocks(n);
-    const int nbo = op_blocks(c->g, c->prec);
-    TRY(ensure_partial(c, (int64_t)(nb > nbo ? nb : nbo) * (m + 2)));
-    const double tol = c->cfg.gmres_tol;
-    const int maxit = c->cfg.gmres_maxit;
-    double* hp = c->hpin;                      // readback area
-    double* yp = c->hpin + 2 * (kMaxRestart + 2);   // y upload area
-    double* dy = c->dsum + 2 * (kMaxRestart + 2);
-    double H[(kMaxRestart + 1) * kMaxRestart];
-    double cs[kMaxRestart], sn[kMaxRestart], gv[kMaxRestart + 1], y[kMaxRestart];
-    double* gw[2] = {c->gw, c->gw2};
-
-    PROF_BEGIN(RELSIM_PROF_RHS);
-    CK(rhs<T>((const T*)c->E, (const T*)c->B[c->bcur], (const T*)c->J, c->gb, c->g, c->st));
-    CK(fields_to_double<T>((const T*)c->E, c->gx, n, c->st));
-    PROF_END();
-    CK(gm_dots(c->V, ldv, 0, c->gb, n, c->partial, nb, c->st));
-    CK(reduce_partials(c->partial, nb, 1, c->dsum, c->st));
-    TRY(readback(c, c->dsum, 1, hp));
+    const GmSetup S = gm_setup(c);
+    TRY(solve_reserve(c, S));
+    TRY(solve_prologue<T>(c, S, c->st, GmCond{0, 0}));
+    TRY(head_async(c, 0));
+    CK(cudaStreamSynchronize(c->st));
     TRY(check_push(c));
-    const double bnorm = std::sqrt(hp[0]);
-    if (!std::isfinite(bnorm)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite right-hand side");
-    int total = 0, restarts = 0, status = RELSIM_OK;
-    double relres = 0.0;
-    if (bnorm == 0.0) {
-        CK(cudaMemsetAsync(c->gx, 0, sizeof(double) * (size_t)n, c->st));
-    } else {
-        for (;;) {
-            // r = b - A x (unnormalised first Krylov vector) and |r|^2
-            PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
-            CK(op_residual<T>((const T*)c->M, c->gx, c->gb, gw[0], c->g, c->partial, c->dpush, c->st));
-            CK(reduce_partials(c->partial, nbo, 1, c->dsum, c->st));
-            PROF_END();
-            TRY(readback(c, c->dsum, 1, hp));
+    while (c->ghead[0].run) {
+        int cur = 0;
+        TRY(arnoldi_body<T>(c, S, c->st, GmCond{0, 0}));
+        TRY(head_async(c, cur));
+        CK(cudaEventRecord(c->gev[cur], c->st));
+        for (int guard = 0; guard <= S.m; ++guard) {
+            TRY(arnoldi_body<T>(c, S, c->st, GmCond{0, 0}));
+            TRY(head_async(c, 1 - cur));
+            CK(cudaEventRecord(c->gev[1 - cur], c->st));
+            CK(cudaEventSynchronize(c->gev[cur]));
             TRY(check_push(c));
-            const double beta = std::sqrt(hp[0]);
-            if (!std::isfinite(beta)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite residual");
-            relres = beta / bnorm;
-            if (relres <= tol) break;
-            if (total >= maxit) {
-                status = fail(c, RELSIM_ERR_NOT_CONVERGED,
-                              "GMRES reached %d iterations at relative residual %.3e", total, relres);
-                break;
-            }
-            for (int k = 0; k <= m; ++k) gv[k] = 0.0;
-            gv[0] = beta;
-            int kdim = 0;
-            // Iteration j: w_j = B v_j (v_0 = r/|r|, written to V_0 on the
-            // way) with the dot products <w_j, V_i> (i <= j) and <w_j, w_j>,
-            // then V_{j+1} = (w_j - V h)/hn, hn^2 = <w,w> - |h|^2 formed on
-            // the device (classical Gram-Schmidt with the normalisation
-            // fused). Nothing of it waits for the host, so iteration j+1 is
-            // launched before the host reads iteration j's sums back; w, the
-            // device sums and the host read-back alternate between two slots.
-            double* ws[2] = {gw[1], gw[0]};   // gw[0] holds r until iteration 0 has read it
-            double* dss[2] = {c->dsum, c->dsum + 3 * (kMaxRestart + 2)};
-            double* hps[2] = {c->hpin, c->hpin + (kMaxRestart + 2)};
-            auto launch_iter = [&](int j) -> int {
-                double* w = ws[j % 2];
-                double* ds = dss[j % 2];
-                PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
-                if (j == 0)
-                    CK(op_arnoldi<T>((const T*)c->M, gw[0], 1.0 / beta, c->V, w, c->V, ldv, 0, c->g, c->partial,
-                                     c->dpush, c->st));
-                else
-                    CK(op_arnoldi<T>((const T*)c->M, c->V + (int64_t)j * ldv, 1.0, nullptr, w, c->V, ldv, j, c->g,
-                                     c->partial, c->dpush, c->st));
-                PROF_END();
-                PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                CK(reduce_partials(c->partial, nbo, j + 2, ds, c->st));
-                CK(gm_update_scale(w, c->V, ldv, j + 1, ds, c->V + (int64_t)(j + 1) * ldv, n, c->st));
-                PROF_END();
-                CK(cudaMemcpyAsync(hps[j % 2], ds, sizeof(double) * (size_t)(j + 2), cudaMemcpyDeviceToHost, c->st));
-                CK(cudaMemcpyAsync(c->hpush, c->dpush, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-                CK(cudaEventRecord(c->gev[j % 2], c->st));
-                return RELSIM_OK;
-            };
-            TRY(launch_iter(0));
-            for (int j = 0; j < m; ++j) {
-                const bool more = j + 1 < m && total + 1 < maxit;   // could iteration j+1 run?
-                // launch it ahead unless the residual's geometric trend says
-                // iteration j converges (a launch ahead is then wasted work)
-                // (|sin| of the previous rotation is the last reduction factor)
-                const bool last = j >= 1 && std::fabs(gv[j]) * std::fabs(sn[j - 1]) <= tol * bnorm;
-                const bool ahead = more && !last;
-                if (ahead) TRY(launch_iter(j + 1));
-                CK(cudaEventSynchronize(c->gev[j % 2]));
-                TRY(check_push(c));
-                const double* hj = hps[j % 2];
-                const double ww = hj[j + 1];
-                double hn2 = ww;
-                for (int i = 0; i <= j; ++i) {
-                    H[i * m + j] = hj[i];
-                    hn2 -= hj[i] * hj[i];
-                }
-                if (!std::isfinite(hn2)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite Arnoldi norm");
-                if (hn2 < 1e-4 * ww) {
-                    // |w - V h| < |w|/100: the norm above has lost digits.
-                    // Drain the speculative iteration, orthogonalise w_j twice
-                    // explicitly (CGS2), normalise it into V_{j+1}, and launch
-                    // iteration j+1 again.
-                    CK(cudaStreamSynchronize(c->st));
-                    double* w = ws[j % 2];
-                    double* scratch = dss[(j + 1) % 2];
-                    PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                    CK(gm_update(w, c->V, ldv, j + 1, dss[j % 2], n, c->partial, nb, c->st));
-                    CK(gm_dots(c->V, ldv, j + 1, w, n, c->partial, nb, c->st));
-                    CK(reduce_partials(c->partial, nb, j + 2, scratch, c->st));
-                    CK(gm_update(w, c->V, ldv, j + 1, scratch, n, c->partial, nb, c->st));
-                    CK(reduce_partials(c->partial, nb, 1, scratch + kMaxRestart + 1, c->st));
-                    PROF_END();
-                    TRY(readback(c, scratch, kMaxRestart + 2, hp));
-                    for (int i = 0; i <= j; ++i) H[i * m + j] += hp[i];
-                    hn2 = hp[kMaxRestart + 1];
-                    if (!std::isfinite(hn2)) return fail(c, RELSIM_ERR_NONFINITE, "non-finite Arnoldi norm");
-                    if (hn2 > 0.0) {
-                        PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-                        CK(gm_scale(c->V + (int64_t)(j + 1) * ldv, w, 1.0 / std::sqrt(hn2), n, c->st));
-                        PROF_END();
-                    }
-                    if (ahead) TRY(launch_iter(j + 1));
-                }
-                const double hn = std::sqrt(hn2 > 0.0 ? hn2 : 0.0);
-                H[j * m + j] += 1.0;   // A = I + B
-                H[(j + 1) * m + j] = hn;
-                for (int i = 0; i < j; ++i) {
-                    const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-                    H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-                    H[i * m + j] = t;
-                }
-                const double a = H[j * m + j], b = H[(j + 1) * m + j];
-                const double r = std::hypot(a, b);
-                cs[j] = r == 0.0 ? 1.0 : a / r;
-                sn[j] = r == 0.0 ? 0.0 : b / r;
-                H[j * m + j] = r;
-                H[(j + 1) * m + j] = 0.0;
-                gv[j + 1] = -sn[j] * gv[j];
-                gv[j] = cs[j] * gv[j];
-                ++total;
-                kdim = j + 1;
-                // a speculative iteration j+1 still in flight only writes
-                // V_{j+2}, its w and its sums: nothing the solution reads
-                if (std::fabs(gv[j + 1]) <= tol * bnorm || total >= maxit || hn == 0.0) break;
-                if (more && !ahead) TRY(launch_iter(j + 1));
-            }
-            for (int i = kdim - 1; i >= 0; --i) {
-                double s = gv[i];
-                for (int k = i + 1; k < kdim; ++k) s -= H[i * m + k] * y[k];
-                y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
-            }
-            for (int i = 0; i < kdim; ++i) yp[i] = y[i];
-            CK(cudaMemcpyAsync(dy, yp, sizeof(double) * (size_t)kdim, cudaMemcpyHostToDevice, c->st));
-            PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-            CK(gm_combine(c->gx, c->V, ldv, kdim, dy, n, c->st));
-            PROF_END();
-            ++restarts;
+            if (!c->ghead[cur].inner) break;
+            cur = 1 - cur;
         }
+        TRY(cycle_end<T>(c, S, c->st, GmCond{0, 0}));
+        TRY(head_async(c, 0));
+        CK(cudaStreamSynchronize(c->st));
+        TRY(check_push(c));
     }
-    // field update and the field side of the ledger
-    CK(cudaMemcpyAsync(c->dled + kLedgerLen - 2, c->dled + 3, 2 * sizeof(double),
-                       cudaMemcpyDeviceToDevice, c->st));
-    const int nbf = field_grid_blocks(c->g);
-    TRY(ensure_partial(c, (int64_t)nbf * 6));
-    PROF_BEGIN(RELSIM_PROF_FIELD_UPDATE);
-    CK(field_update<T>(c->gx, (const T*)c->M, (const T*)c->J, (T*)c->Eth, (T*)c->E,
-                       (const T*)c->B[c->bcur], (T*)c->B[1 - c->bcur], c->g, c->partial, nbf, c->st));
-    CK(reduce_partials(c->partial, nbf, 6, c->dled, c->st));
-    PROF_END();
-    c->last_iters = total;
-    c->last_restarts = restarts;
-    c->last_relres = relres;
-    if (iters_out) *iters_out = total;
-    if (relres_out) *relres_out = relres;
-    return status;
+    const GmState h = c->ghead[0];
+    if (h.status == kGmNonfinite) return solve_outcome(c, &h, iters_out, relres_out);
+    TRY(solve_epilogue<T>(c, c->st));
+    return solve_outcome(c, &h, iters_out, relres_out);
 }
 
+// the host side of a push: the new cell starts and the new B become current
+void push_commit(relsim_ctx* c)
+{
+    if (c->fast_sort)
+        for (int s = 0; s < c->cfg.nspecies; ++s) {
+            Species& sp = c->sp[s];
+            if (sp.n == 0) continue;
+            int32_t* t = sp.start;
+            sp.start = sp.start_alt;
+            sp.start_alt = t;
+        }
+    c->bcur = 1 - c->bcur;
+}
+
+// enqueue the push and the re-sort of every species (push_commit follows)
 template <typename T>
-int push_impl(relsim_ctx* c)
+int push_enqueue(relsim_ctx* c)
 {
     const int nbp = push_grid_blocks(c->g, c->prec);
     TRY(ensure_partial(c, (int64_t)nbp * (kLedgerSpecies - 1)));
@@ -734,9 +767,6 @@ int push_impl(relsim_ctx* c)
             PROF_BEGIN(RELSIM_PROF_PERMUTE);
             CK(permute<T>(dst, src, sp.start_alt, c->n9, c->off9, c->g, c->dpush, c->st));
             PROF_END();
-            int32_t* t = sp.start;
-            sp.start = sp.start_alt;
-            sp.start_alt = t;
         } else {
             // general path: push in place order with keys, radix sort, gather
             TRY(ensure_radix(c, sp.n));
@@ -757,9 +787,200 @@ int push_impl(relsim_ctx* c)
             PROF_END();
         }
     }
-    c->bcur = 1 - c->bcur;
     // read back lazily: checked after the next synchronising call
     CK(cudaMemcpyAsync(c->hpush, c->dpush, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    return RELSIM_OK;
+}
+
+template <typename T>
+int push_impl(relsim_ctx* c)
+{
+    TRY(push_enqueue<T>(c));
+    push_commit(c);
+    return RELSIM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// A whole step as one CUDA graph. The solve's restart loop and Arnoldi loop
+// become conditional while nodes whose conditions the control kernels set,
+// so a step needs no host decision: one graph launch, then one read-back.
+
+// the graph being captured on stream s
+int capture_graph(relsim_ctx* c, cudaStream_t s, cudaGraph_t* g)
+{
+    cudaStreamCaptureStatus cs;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return fail(c, RELSIM_ERR_INTERNAL, "stream not capturing");
+    return RELSIM_OK;
+}
+
+// append a while node with condition h to the capture on stream s; the
+// capture continues after it; *body receives the loop body to capture into
+int add_while(relsim_ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &ed, &nd));
+    // the parameter struct holds a union: zeroed raw storage stands in for
+    // its (deleted) default constructor
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, ed, nd, &np));
+    *body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return RELSIM_OK;
+}
+
+// capture the enqueue function f into the body graph on stream s
+template <class F>
+int capture_into(relsim_ctx* c, cudaStream_t s, cudaGraph_t body, long long* tally, F f)
+{
+    long long* saved = t_capture_count;
+    t_capture_count = tally;
+    CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int r = f();
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &out);
+    t_capture_count = saved;
+    if (r == RELSIM_OK && e != cudaSuccess) r = fail(c, RELSIM_ERR_CUDA, "body capture: %s", cudaGetErrorString(e));
+    return r;
+}
+
+// The solve: prologue, then while (cycle) { arm; while (iteration) { Arnoldi
+// step }; finish the cycle }, then the field update. Each condition handle
+// is created on the graph that holds its while node, before the kernels that
+// set it are captured.
+template <typename T>
+int capture_solve(relsim_ctx* c, const GmSetup& S, StepGraph& G)
+{
+    cudaGraph_t top = nullptr;
+    TRY(capture_graph(c, c->st, &top));
+    cudaGraphConditionalHandle ho;
+    CK(cudaGraphConditionalHandleCreate(&ho, top, 0, cudaGraphCondAssignDefault));
+    TRY(solve_prologue<T>(c, S, c->st, GmCond{(unsigned long long)ho, 1}));
+    cudaGraph_t outer = nullptr;
+    TRY(add_while(c, c->st, ho, &outer));
+    cudaGraphConditionalHandle hi;
+    CK(cudaGraphConditionalHandleCreate(&hi, outer, 0, cudaGraphCondAssignDefault));
+    TRY(capture_into(c, c->aux[0], outer, &G.k_cycle, [&]() -> int {
+        CK(gm_arm(c->gms, GmCond{(unsigned long long)hi, 1}, c->aux[0]));
+        cudaGraph_t inner = nullptr;
+        TRY(add_while(c, c->aux[0], hi, &inner));
+        TRY(capture_into(c, c->aux[1], inner, &G.k_iter,
+                         [&]() -> int { return arnoldi_body<T>(c, S, c->aux[1], GmCond{(unsigned long long)hi, 1}); }));
+        return cycle_end<T>(c, S, c->aux[0], GmCond{(unsigned long long)ho, 1});
+    }));
+    return solve_epilogue<T>(c, c->st);
+}
+
+// capture the step on the graph stream for the current buffer layout
+template <typename T>
+int capture_step(relsim_ctx* c, StepGraph& G)
+{
+    const GmSetup S = gm_setup(c);
+    TRY(solve_reserve(c, S));
+    TRY(ensure_partial(c, (int64_t)push_grid_blocks(c->g, c->prec) * (kLedgerSpecies - 1)));
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    G.k_static = G.k_cycle = G.k_iter = 0;
+    cudaStream_t user = c->st;
+    c->st = c->gst;
+    c->capturing = true;
+    t_capture_count = &G.k_static;
+    int r = RELSIM_OK;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        r = fail(c, RELSIM_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    } else {
+        r = build_impl<T>(c);
+        if (r == RELSIM_OK) r = capture_solve<T>(c, S, G);
+        if (r == RELSIM_OK) r = push_enqueue<T>(c);
+        e = cudaStreamEndCapture(c->st, &graph);
+        if (r == RELSIM_OK && e != cudaSuccess) r = fail(c, RELSIM_ERR_CUDA, "step capture: %s", cudaGetErrorString(e));
+    }
+    t_capture_count = nullptr;
+    c->capturing = false;
+    c->st = user;
+    if (r == RELSIM_OK) {
+        e = cudaGraphInstantiate(&G.exec, graph, 0);
+        if (e != cudaSuccess) {
+            G.exec = nullptr;
+            r = fail(c, RELSIM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();
+    if (r != RELSIM_OK) return r;
+    G.gen = c->gen;
+    G.bcur = c->bcur;
+    for (int s = 0; s < kMaxSpecies; ++s) G.start[s] = c->sp[s].start;
+    return RELSIM_OK;
+}
+
+bool graph_matches(const relsim_ctx* c, const StepGraph& G)
+{
+    if (!G.exec || G.gen != c->gen || G.bcur != c->bcur) return false;
+    for (int s = 0; s < kMaxSpecies; ++s)
+        if (G.start[s] != c->sp[s].start) return false;
+    return true;
+}
+
+// one step through the graph of the current layout (captured on first use);
+// returns 1 when the graph path is unavailable (the caller steps eagerly)
+template <typename T>
+int step_graph(relsim_ctx* c, relsim_energy* ledger, int* status)
+{
+    StepGraph* G = nullptr;
+    for (StepGraph& g : c->sg)
+        if (graph_matches(c, g)) G = &g;
+    if (!G) {
+        // replace the slot not matching the other parity's layout
+        G = &c->sg[c->sg[0].exec && c->sg[0].gen == c->gen && c->sg[0].bcur != c->bcur ? 1 : 0];
+        if (capture_step<T>(c, *G) != RELSIM_OK) {
+            c->graph_off = true;
+            c->graph_why = c->err;
+            c->err.clear();
+            return 1;
+        }
+    }
+    CK(cudaEventRecord(c->gjoin[0], c->st));
+    CK(cudaStreamWaitEvent(c->gst, c->gjoin[0], 0));
+    CK(cudaGraphLaunch(G->exec, c->gst));
+    CK(cudaEventRecord(c->gjoin[1], c->gst));
+    CK(cudaStreamWaitEvent(c->st, c->gjoin[1], 0));
+    push_commit(c);
+    c->state = kReady;
+    c->have_step = true;
+    ++c->step;
+    ++c->graph_steps;
+    TRY(head_async(c, 0));
+    double* h = c->hpin;
+    if (ledger) CK(cudaMemcpyAsync(h, c->dled, sizeof(double) * kLedgerLen, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const GmState hd = c->ghead[0];
+    count_launches((int)(G->k_static + G->k_cycle * hd.restarts + G->k_iter * hd.total));
+    TRY(check_push(c));
+    *status = solve_outcome(c, &hd, nullptr, nullptr);
+    if (*status != RELSIM_OK && *status != RELSIM_ERR_NOT_CONVERGED) return RELSIM_OK;
+    if (ledger) {
+        double hl[kLedgerLen];
+        memcpy(hl, h, sizeof(hl));
+        const int r = ledger_fill(c, hl, ledger);
+        if (r != RELSIM_OK) *status = r;
+    }
     return RELSIM_OK;
 }
 
@@ -840,6 +1061,12 @@ int ledger_impl(relsim_ctx* c, relsim_energy* out)
     double h[kLedgerLen];
     TRY(readback(c, c->dled, kLedgerLen, h));
     TRY(check_push(c));
+    return ledger_fill(c, h, out);
+}
+
+// the ledger from the device sums h (kLedgerLen values)
+int ledger_fill(relsim_ctx* c, const double* h, relsim_energy* out)
+{
     memset(out, 0, sizeof(*out));
     out->W_E = h[3];
     out->W_B = h[4];
@@ -975,6 +1202,23 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     A(dalloc(c, &c->gx, sizeof(double) * c->nvec));
     A(dalloc(c, &c->gb, sizeof(double) * c->nvec));
     A(dalloc(c, &c->dsum, sizeof(double) * 4 * (kMaxRestart + 2)));
+    A(dalloc(c, &c->gms, sizeof(GmState)));
+    if (cudaMemsetAsync(c->gms, 0, sizeof(GmState), c->st) != cudaSuccess) {
+        r = fail(c, RELSIM_ERR_CUDA, "cudaMemsetAsync failed");
+        goto fail_init;
+    }
+    if (cudaMallocHost((void**)&c->ghead, 2 * sizeof(GmState)) != cudaSuccess) {
+        r = fail(c, RELSIM_ERR_OOM, "cudaMallocHost failed");
+        goto fail_init;
+    }
+    if (cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->aux[1], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gjoin[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gjoin[1], cudaEventDisableTiming) != cudaSuccess) {
+        r = fail(c, RELSIM_ERR_CUDA, "stream or event creation failed");
+        goto fail_init;
+    }
     A(dalloc(c, &c->dled, sizeof(double) * kLedgerLen));
     A(dalloc(c, &c->dflag, sizeof(int)));
     A(dalloc(c, &c->dpush, sizeof(int)));
@@ -1045,6 +1289,14 @@ void relsim_destroy(relsim_ctx* c)
     dfree(c->dsum); dfree(c->dled); dfree(c->dflag); dfree(c->dpush); dfree(c->stage);
     dfree(c->spec_w); dfree(c->spec_c); dfree(c->spec_e);
     dfree(c->mode_tw); dfree(c->mode_rows);
+    dfree(c->gms);
+    if (c->ghead) cudaFreeHost(c->ghead);
+    for (StepGraph& G : c->sg)
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+    for (cudaStream_t t : {c->gst, c->aux[0], c->aux[1]})
+        if (t) cudaStreamDestroy(t);
+    for (cudaEvent_t e : c->gjoin)
+        if (e) cudaEventDestroy(e);
     if (c->hpin) cudaFreeHost(c->hpin);
     if (c->hflag) cudaFreeHost(c->hflag);
     if (c->hpush) cudaFreeHost(c->hpush);
@@ -1058,6 +1310,7 @@ int relsim_load_particles(relsim_ctx* c, int species, int64_t n, const double* x
                           const double* w, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
+    ++c->gen;
     if (species < 0 || species >= c->cfg.nspecies)
         return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
     if (n < 0 || n > 2147483647LL) return fail(c, RELSIM_ERR_INVALID_ARG, "bad particle count %lld", (long long)n);
@@ -1075,6 +1328,7 @@ int relsim_load_particles(relsim_ctx* c, int species, int64_t n, const double* x
 int relsim_set_fields(relsim_ctx* c, const double* E, const double* B, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
+    ++c->gen;
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     if (c->state == kSolved) c->bcur = 1 - c->bcur;   // the solved fields become current
     int r = DISPATCH(set_fields_impl, c, E, B, where);
@@ -1176,6 +1430,7 @@ int relsim_set_mass_matrix(relsim_ctx* c, const double* M, const double* J, int 
 {
     if (!c || !M || !J) return RELSIM_ERR_INVALID_ARG;
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    ++c->gen;
     if (c->state == kEmpty) return fail(c, RELSIM_ERR_BAD_STATE, "context not initialised");
     if (c->state == kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "push the solved step first");
     const int64_t nm = (int64_t)c->g.ncell * kMBlock, nj = 3 * (int64_t)c->g.ncell;
@@ -1311,9 +1566,26 @@ int relsim_field_modes(relsim_ctx* c, int component, int nmodes, double* energy,
     return DISPATCH(modes_impl, c, component, nmodes, energy, where);
 }
 
+int relsim_graph_info(const relsim_ctx* c, int64_t* graph_steps, int* disabled, const char** why)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (graph_steps) *graph_steps = c->graph_steps;
+    if (disabled) *disabled = c->graph_off ? 1 : 0;
+    if (why) *why = c->graph_why.c_str();
+    return RELSIM_OK;
+}
+
 int relsim_step(relsim_ctx* c, relsim_energy* ledger)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
+    // after one host-driven step has sized every buffer, steps run as a
+    // captured graph (not while profiling: event timing needs host launches)
+    if (c->state == kReady && c->have_step && c->fast_sort && !c->prof.on && !c->graph_off) {
+        int status = RELSIM_OK;
+        const int r = DISPATCH(step_graph, c, ledger, &status);
+        if (r == RELSIM_OK) return status;
+        if (r != 1) return r;
+    }
     int r = relsim_build_mass_matrix(c);
     if (r != RELSIM_OK) return r;
     int first = RELSIM_OK;

@@ -196,9 +196,18 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(OpTile<T>::threads, sizeof(T) == 4 ? 3 : 2)
 k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const double* __restrict__ b,
      double* __restrict__ out, double* __restrict__ vj, const double* __restrict__ V, int64_t ldv, int nv,
-     GridP g, int tma, double* __restrict__ partial, int* __restrict__ err)
+     GridP g, int tma, double* __restrict__ partial, int* __restrict__ err, const GmDyn* __restrict__ dyn)
 {
     constexpr int X = OpTile<T>::X, Y = OpTile<T>::Y, NT = OpTile<T>::threads;
+    if (MODE == kOpArnoldi && dyn) {
+        // arguments of a device-decided Arnoldi iteration
+        if (!dyn->live) return;
+        in = dyn->in;
+        s = dyn->s;
+        vj = dyn->vj;
+        out = dyn->out;
+        nv = dyn->nv;
+    }
     extern __shared__ __align__(128) unsigned char op_smem[];
     OpShared<T>& S = *reinterpret_cast<OpShared<T>*>(op_smem);
     const int nx = g.nx, ny = g.ny, nc = g.ncell;
@@ -523,10 +532,18 @@ k_gm_update(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, i
 // [h_0 .. h_{k-1}, <w,w>]; every block forms hn itself).
 __global__ void __launch_bounds__(kGmThreads)
 k_gm_update_scale(const double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int k,
-                  const double* __restrict__ hw, double* __restrict__ vout, int64_t n)
+                  const double* __restrict__ hw, double* __restrict__ vout, int64_t n,
+                  const GmDyn* __restrict__ dyn)
 {
     __shared__ double hs[kMaxRestart + 1];
     __shared__ double inv;
+    if (dyn) {
+        if (!dyn->live) return;
+        w = dyn->out;
+        k = dyn->nv + 1;
+        hw = dyn->ds;
+        vout = const_cast<double*>(V) + (int64_t)k * ldv;
+    }
     for (int c = threadIdx.x; c < k; c += blockDim.x) hs[c] = hw[c];
     if (threadIdx.x == 0) {
         double h2 = hw[k];
@@ -578,9 +595,10 @@ k_gm_sub(double* r, const double* __restrict__ b, const double* __restrict__ Ax,
 }
 
 __global__ void k_gm_combine(double* x, const double* __restrict__ V, int64_t ldv, int k,
-                             const double* __restrict__ y, int64_t n)
+                             const double* __restrict__ y, int64_t n, const int* __restrict__ kdev)
 {
     __shared__ double ys[kMaxRestart + 1];
+    if (kdev) k = *kdev;   // the dimension decided on the device
     for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = y[c];
     __syncthreads();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -603,10 +621,16 @@ __global__ void k_gm_combine(double* x, const double* __restrict__ V, int64_t ld
 
 // out[s] = sum_b partial[b*nsums + s], fixed order (deterministic)
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nblocks, int nsums,
-                                  double* out)
+                                  double* out, const GmDyn* __restrict__ dyn)
 {
     __shared__ double red[32];
     const int s = blockIdx.x;
+    if (dyn) {
+        if (!dyn->live) return;
+        nsums = dyn->nv + 2;
+        out = dyn->ds;
+        if (s >= nsums) return;
+    }
     double acc = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += partial[(int64_t)b * nsums + s];
     double v[1] = {acc}, o[1];
@@ -658,7 +682,8 @@ cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStre
 
 template <typename T, int MODE>
 cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
-                      const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st)
+                      const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st,
+                      const GmDyn* dyn = nullptr)
 {
     // the dynamic shared-memory limit, set once per kernel and device
     static std::atomic<unsigned> attr_set{0};
@@ -676,7 +701,7 @@ cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, 
     const int tma = ((int64_t)g.nx * kMBlock * sizeof(T)) % 16 == 0 ? 1 : 0;
     count_launches(1);
     k_op<T, MODE><<<op_blocks(g, sizeof(T) == 4 ? 32 : 64), OpTile<T>::threads, smem, st>>>(
-        M, in, sc, b, out, vj, V, ldv, nv, g, tma, partial, err);
+        M, in, sc, b, out, vj, V, ldv, nv, g, tma, partial, err, dyn);
     return cudaGetLastError();
 }
 
@@ -698,6 +723,14 @@ cudaError_t op_arnoldi(const T* M, const double* u, double sc, double* vj, doubl
                        int64_t ldv, int j, GridP g, double* partial, int* err, cudaStream_t st)
 {
     return launch_op<T, kOpArnoldi>(M, u, sc, nullptr, w, vj, V, ldv, j, g, partial, err, st);
+}
+
+template <typename T>
+cudaError_t op_arnoldi_dyn(const T* M, const GmDyn* dyn, const double* V, int64_t ldv, GridP g, double* partial,
+                           int* err, cudaStream_t st)
+{
+    return launch_op<T, kOpArnoldi>(M, nullptr, 1.0, nullptr, nullptr, nullptr, V, ldv, 0, g, partial, err, st,
+                                    dyn);
 }
 
 template <typename T>
@@ -762,7 +795,16 @@ cudaError_t gm_update_scale(const double* w, const double* V, int64_t ldv, int k
                             double* vout, int64_t n, cudaStream_t st)
 {
     count_launches(1);
-    k_gm_update_scale<<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(w, V, ldv, k, hw, vout, n);
+    k_gm_update_scale<<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(w, V, ldv, k, hw, vout, n,
+                                                                                  nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t gm_update_scale_dyn(const GmDyn* dyn, const double* V, int64_t ldv, int64_t n, cudaStream_t st)
+{
+    count_launches(1);
+    k_gm_update_scale<<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(nullptr, V, ldv, 0, nullptr,
+                                                                                  nullptr, n, dyn);
     return cudaGetLastError();
 }
 
@@ -785,7 +827,15 @@ cudaError_t gm_combine(double* x, const double* V, int64_t ldv, int k, const dou
                        cudaStream_t st)
 {
     count_launches(1);
-    k_gm_combine<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, k, y, n);
+    k_gm_combine<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, k, y, n, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t gm_combine_dev(double* x, const double* V, int64_t ldv, const int* k, const double* y, int64_t n,
+                           cudaStream_t st)
+{
+    count_launches(1);
+    k_gm_combine<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, 0, y, n, k);
     return cudaGetLastError();
 }
 
@@ -793,7 +843,15 @@ cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, doubl
                             cudaStream_t st)
 {
     count_launches(1);
-    k_reduce_partials<<<nsums, 256, 0, st>>>(partial, nblocks, nsums, out);
+    k_reduce_partials<<<nsums, 256, 0, st>>>(partial, nblocks, nsums, out, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_partials_dyn(const double* partial, int nblocks, const GmDyn* dyn, int maxsums,
+                                cudaStream_t st)
+{
+    count_launches(1);
+    k_reduce_partials<<<maxsums, 256, 0, st>>>(partial, nblocks, 0, nullptr, dyn);
     return cudaGetLastError();
 }
 
@@ -807,6 +865,8 @@ cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, doubl
     template cudaError_t op_arnoldi<T>(const T*, const double*, double, double*, double*,         \
                                        const double*, int64_t, int, GridP, double*, int*,          \
                                        cudaStream_t);                                             \
+    template cudaError_t op_arnoldi_dyn<T>(const T*, const GmDyn*, const double*, int64_t, GridP, \
+                                           double*, int*, cudaStream_t);                          \
     template cudaError_t field_update<T>(const double*, const T*, const T*, T*, T*, const T*, T*, \
                                          GridP, double*, int, cudaStream_t);                      \
     template cudaError_t field_energy<T>(const T*, const T*, GridP, double*, int, cudaStream_t);  \

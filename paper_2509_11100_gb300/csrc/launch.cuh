@@ -159,9 +159,76 @@ cudaError_t gm_sub(double* r, const double* b, const double* Ax, int64_t n, doub
                    int nblocks, cudaStream_t st);                      // r = b - Ax; |r|^2
 cudaError_t gm_combine(double* x, const double* V, int64_t ldv, int k, const double* y,
                        int64_t n, cudaStream_t st);                    // x += V y
+cudaError_t gm_combine_dev(double* x, const double* V, int64_t ldv, const int* k, const double* y,
+                           int64_t n, cudaStream_t st);                // x += V y, k read on the device
 cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, double* out,
                             cudaStream_t st);
 int gm_blocks(int64_t n);
+
+// ----- device-side GMRES control (gmres.cu) -----
+// Launch arguments of the next Arnoldi iteration, written by the device (the
+// cycle start or the previous iteration's tail) and read by the iteration's
+// kernels, so that no host decision sits between two iterations.
+struct GmDyn {
+    const double* in;   // v_j unscaled: r for j = 0, V_j after
+    double* vj;         // where v_j = s in is written (V_0 for j = 0), or null
+    double* out;        // w_j = B v_j
+    double* ds;         // the j + 2 sums <w,V_0..V_{j-1}>, <w,v_j>, <w,w>
+    double s;           // 1/beta for j = 0, else 1
+    int nv;             // j
+    int live;           // 0: the iteration is not to run (its kernels return)
+};
+// The solve's control state on the device. The head (up to H) is what the
+// host reads back after a solve.
+struct GmState {
+    GmDyn dyn;
+    double bnorm, beta, relres;
+    int total, restarts, kdim, run, inner, status, zero, pad;
+    double cs[kMaxRestart], sn[kMaxRestart], gv[kMaxRestart + 1], y[kMaxRestart];
+    double H[(kMaxRestart + 1) * kMaxRestart];
+};
+enum { kGmOk = 0, kGmNotConverged = 1, kGmNonfinite = 2 };
+// The fixed pointers the control kernels build launch arguments from.
+struct GmPtrs {
+    double* r;       // residual / first Krylov vector (also w of odd j)
+    double* w0;      // w of even j
+    double* V;       // Krylov basis, ldv apart
+    double* ds0;     // sums of even j
+    double* ds1;     // sums of odd j
+    int64_t ldv;
+};
+struct GmParams {
+    double tol;
+    int m, maxit;
+};
+// a graph loop condition the control kernels set (has = 0: host-driven)
+struct GmCond {
+    unsigned long long h;
+    int has;
+};
+// bnorm from |b|^2 = sums[0]; resets the counters
+cudaError_t gm_begin(GmState* st, const double* sums, cudaStream_t s);
+// x = 0 when b = 0 (the exact solution); no-op otherwise
+cudaError_t gm_zero_x(const GmState* st, double* x, int64_t n, cudaStream_t s);
+// after r = b - A x, |r|^2 = sums[0]: converged / out of iterations / start
+// a cycle (launch arguments of iteration 0); sets the cycle condition
+cudaError_t gm_cycle(GmState* st, const double* sums, GmPtrs p, GmParams q, GmCond cond, cudaStream_t s);
+// sets the Arnoldi-loop condition to the state's "run"
+cudaError_t gm_arm(const GmState* st, GmCond cond, cudaStream_t s);
+// after iteration j's sums: Hessenberg column, Givens rotation, residual
+// estimate, stop test, launch arguments of iteration j + 1; sets the
+// Arnoldi-loop condition
+cudaError_t gm_tail(GmState* st, GmPtrs p, GmParams q, GmCond cond, cudaStream_t s);
+// y from the triangular system of the finished cycle; x += V y
+cudaError_t gm_finish_cycle(GmState* st, double* x, const double* V, int64_t ldv, int64_t n, int m,
+                            cudaStream_t s);
+// Arnoldi iteration kernels reading their arguments from dyn
+template <typename T>
+cudaError_t op_arnoldi_dyn(const T* M, const GmDyn* dyn, const double* V, int64_t ldv, GridP g,
+                           double* partial, int* err, cudaStream_t st);
+cudaError_t reduce_partials_dyn(const double* partial, int nblocks, const GmDyn* dyn, int maxsums,
+                                cudaStream_t st);
+cudaError_t gm_update_scale_dyn(const GmDyn* dyn, const double* V, int64_t ldv, int64_t n, cudaStream_t st);
 
 // ----- diag.cu -----
 // tw[2 (m nx + i) + {0, 1}] = cos, sin of 2 pi ((m i) mod nx) / nx, m < nmodes

@@ -505,3 +505,69 @@ def test_device_pointers_roundtrip(rs):
     np.testing.assert_array_equal(xd.cpu().numpy(), xh)
     np.testing.assert_array_equal(ud.cpu().numpy(), uh)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_graph_steps_match_host_driven_steps(rs, precision):
+    """After the first step, relsim_step runs each step as one CUDA graph
+    (the solve's loops as conditional while nodes). With event profiling on,
+    the same steps are driven from the host. Both routes run the same
+    kernels; the deposit's float atomics make their sums differ in the last
+    bits, so the fields agree to rounding (FP64 1e-11, FP32 2e-5 of the
+    largest entry after 3 steps) and the GMRES iteration counts match."""
+    nx, ny = 24, 16
+    st = harris_small(nx, ny, 4)
+    sims = [make_sim(rs, nx, ny, precision) for _ in range(2)]
+    for s in sims:
+        s.load_state(st)
+    sims[1].profile(True)   # host-driven route
+    its = [[], []]
+    for _ in range(4):
+        for k, s in enumerate(sims):
+            led, code = s.step(ledger=True)
+            assert code == 0
+            its[k].append(led["gmres_iters"])
+    info = sims[0].graph_info()
+    assert not info["disabled"], info["why"]
+    assert info["graph_steps"] == 3
+    assert sims[1].graph_info()["graph_steps"] == 0
+    # FP32: a residual estimate within rounding of the tolerance may stop
+    # one iteration apart
+    assert all(abs(a - b) <= (0 if precision == 64 else 1) for a, b in zip(*its)), its
+    tol = 1e-11 if precision == 64 else 2e-5
+    for a, b in zip(sims[0].fields(), sims[1].fields()):
+        assert np.max(np.abs(a - b)) <= tol * np.abs(b).max()
+    for s in range(2):
+        xa, ua, wa = sims[0].particles(s)
+        xb, ub, wb = sims[1].particles(s)
+        assert np.max(np.abs(ua - ub)) <= tol * np.abs(ub).max()
+    for s in sims:
+        s.close()
+
+
+def test_graph_step_after_reload_and_not_converged(rs):
+    """A reload invalidates the captured graphs (new buffers and layout);
+    NOT_CONVERGED is reported from a graph step as from a host-driven one."""
+    nx, ny = 16, 8
+    sim = make_sim(rs, nx, ny, 32)
+    st = harris_small(nx, ny, 4)
+    sim.load_state(st)
+    for _ in range(3):
+        _, code = sim.step()
+        assert code == 0
+    assert sim.graph_info()["graph_steps"] == 2
+    sim.load_state(st)
+    for _ in range(3):
+        _, code = sim.step()
+        assert code == 0
+    assert sim.graph_info()["graph_steps"] == 4
+    sim.close()
+    cfg = rs.make_config(nx, ny, precision=32, gmres_tol=1e-14)
+    cfg.gmres_maxit = 1
+    sim = rs.Simulation(cfg)
+    sim.load_state(st)
+    for _ in range(3):
+        led, code = sim.step()
+        assert code == rs.RELSIM_ERR_NOT_CONVERGED and led["gmres_iters"] == 1
+    assert sim.graph_info()["graph_steps"] == 2
+    sim.close()
