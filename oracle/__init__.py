@@ -27,7 +27,8 @@ class OracleConfig(ctypes.Structure):
                 ("nspecies", ctypes.c_int),
                 ("q", ctypes.c_double * 4), ("m", ctypes.c_double * 4),
                 ("gmres_tol", ctypes.c_double),
-                ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int)]
+                ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+                ("gamma_pred", ctypes.c_int)]
 
 
 class Ledger(ctypes.Structure):
@@ -64,7 +65,7 @@ def load():
         "orc_gather_E": (None, [_C, _D, ctypes.c_double, ctypes.c_double, _D]),
         "orc_gather_B": (None, [_C, _D, ctypes.c_double, ctypes.c_double, _D]),
         "orc_alpha": (None, [ctypes.c_double, ctypes.c_double, _D, _D]),
-        "orc_deposit": (None, [_C, _I64, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
+        "orc_deposit": (None, [_C, _I64, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
         "orc_curl_c": (None, [_C, _D, _D]),
         "orc_curl_n": (None, [_C, _D, _D]),
         "orc_apply_M": (None, [_C, _D, _D, _D]),
@@ -73,7 +74,7 @@ def load():
         "orc_gmres": (ctypes.c_int, [_C, _D, _D, _D, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double)]),
         "orc_field_update": (None, [_C, _D, _D, _D]),
-        "orc_push": (None, [_C, _I64, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
+        "orc_push": (None, [_C, _I64, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
         "orc_energies": (None, [_C, _I64, _D, _D, _D, _D, _D, _D, _D]),
         "orc_cell_keys": (None, [_C, ctypes.c_int64, _D, _D, _I32]),
         "orc_stable_sort": (None, [ctypes.c_int64, _I32, ctypes.c_int32, _I64, _I64]),
@@ -90,8 +91,11 @@ def load():
 
 
 def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta=0.5, q=(1.0, -1.0), m=(1.0, 1.0),
-                gmres_tol=1e-12, gmres_restart=50, gmres_maxit=2000) -> OracleConfig:
+                gmres_tol=1e-12, gmres_restart=50, gmres_maxit=2000, gamma_pred=0) -> OracleConfig:
+    """gamma_pred = 1: the Lorentz factor in alpha and M is that of the
+    predicted half-step momentum u^n + beta E^n(x) instead of u^n."""
     c = OracleConfig()
+    c.gamma_pred = int(gamma_pred)
     c.nx, c.ny, c.dx, c.dy, c.dt, c.theta = nx, ny, dx, dy, dt, theta
     c.nspecies = len(q)
     for s in range(len(q)):
@@ -154,12 +158,14 @@ def alpha(beta, gbar, Bp):
     return out.reshape(3, 3)
 
 
-def deposit(c, P: Particles, B):
+def deposit(c, P: Particles, B, E=None):
+    """Jhat and M; E (E^n) is used by the predicted-gamma variant only."""
     nn = c.nx * c.ny
     J = np.zeros(3 * nn)
     M = np.zeros(81 * nn)
+    E = np.zeros(3 * nn) if E is None else _f(E).ravel()
     load().orc_deposit(ctypes.byref(c), P.off, P.x, P.y, P.ux, P.uy, P.uz, P.w,
-                       _f(B).ravel(), J, M)
+                       _f(B).ravel(), E, J, M)
     return J.reshape(3, nn), M.reshape(nn, 9, 3, 3)
 
 
@@ -209,11 +215,13 @@ def field_update(c, Etheta, E, B):
     return E.reshape(3, -1), B.reshape(3, -1)
 
 
-def push(c, P: Particles, Etheta, B):
-    """Push in place; returns sums (K0, K1, work_particles, mismatch)."""
+def push(c, P: Particles, Etheta, B, E=None):
+    """Push in place; returns sums (K0, K1, work_particles, mismatch). E
+    (E^n) is used by the predicted-gamma variant only."""
     sums = np.zeros(4)
+    E = np.zeros(3 * c.nx * c.ny) if E is None else _f(E).ravel()
     load().orc_push(ctypes.byref(c), P.off, P.x, P.y, P.ux, P.uy, P.uz, P.w,
-                    _f(Etheta).ravel(), _f(B).ravel(), sums)
+                    _f(Etheta).ravel(), _f(B).ravel(), E, sums)
     return sums
 
 

@@ -15,7 +15,9 @@
  * paper is silent are listed in the repository's design notes):
  *
  *   state: x^{n+1/2}, u^n (u = gamma v), E^n on nodes, B^n on cell centres
- *   1. gbar = sqrt(1 + |u^n|^2)
+ *   1. gbar = sqrt(1 + |u^n|^2)  (or, with gamma_pred, the Lorentz factor of
+ *      the predicted half-step momentum u^n + beta E^n(x): the magnetic
+ *      rotation keeps |u| and E^n stands in for E^{n+theta})
  *   2. a = beta B^n(x)/gbar, beta = q dt/(2m)
  *   3. alpha = (I - [a]x + a a^T)/(1 + |a|^2), the solution operator of
  *      ubar - ubar x a = w (the implicit-midpoint rotation)
@@ -135,6 +137,16 @@ static double gamma_m1(double ux, double uy, double uz)
 }
 
 /* Offset slot of node b relative to node a, both nodes of one cell. */
+/* the Lorentz factor in alpha and M (step 1) */
+static double gbar_of(const orc_config* c, double beta, const double* E, double x, double y,
+                      const double u[3])
+{
+    if (!c->gamma_pred) return gamma_of(u[0], u[1], u[2]);
+    double Ep[3];
+    orc_gather_E(c, E, x, y, Ep);
+    return gamma_of(u[0] + beta * Ep[0], u[1] + beta * Ep[1], u[2] + beta * Ep[2]);
+}
+
 static int pair_slot(const orc_config* c, int64_t ga, int64_t gb)
 {
     int64_t ia = ga % c->nx, ja = ga / c->nx, ib = gb % c->nx, jb = gb / c->nx;
@@ -151,7 +163,7 @@ static int pair_slot(const orc_config* c, int64_t ga, int64_t gb)
 void orc_deposit(const orc_config* c, const int64_t* off,
                  const double* x, const double* y,
                  const double* ux, const double* uy, const double* uz,
-                 const double* w, const double* B, double* J, double* M)
+                 const double* w, const double* B, const double* E, double* J, double* M)
 {
     int64_t nn = (int64_t)c->nx * c->ny;
     double dV = c->dx * c->dy;
@@ -163,7 +175,7 @@ void orc_deposit(const orc_config* c, const int64_t* off,
         for (int64_t p = off[s]; p < off[s + 1]; ++p) {
             double Bp[3], alpha[9], u[3] = {ux[p], uy[p], uz[p]};
             orc_gather_B(c, B, x[p], y[p], Bp);
-            double gbar = gamma_of(u[0], u[1], u[2]);
+            double gbar = gbar_of(c, beta, E, x[p], y[p], u);
             orc_alpha(beta, gbar, Bp, alpha);
             double vJ[3];
             for (int r = 0; r < 3; ++r) {
@@ -399,7 +411,8 @@ static double wrap_pos(double s, double L)
 /* Steps 9 and 10, plus the per-particle energy sums of the ledger. */
 void orc_push(const orc_config* c, const int64_t* off,
               double* x, double* y, double* ux, double* uy, double* uz,
-              const double* w, const double* Etheta, const double* B, double sums[4])
+              const double* w, const double* Etheta, const double* B, const double* E,
+              double sums[4])
 {
     double Lx = c->nx * c->dx, Ly = c->ny * c->dy;
     for (int k = 0; k < 4; ++k) sums[k] = 0.0;
@@ -409,9 +422,11 @@ void orc_push(const orc_config* c, const int64_t* off,
         for (int64_t p = off[s]; p < off[s + 1]; ++p) {
             double Ep[3], Bp[3], alpha[9];
             double u0[3] = {ux[p], uy[p], uz[p]};
+            double Ep0[3] = {0.0, 0.0, 0.0};
             orc_gather_E(c, Etheta, x[p], y[p], Ep);
             orc_gather_B(c, B, x[p], y[p], Bp);
-            double gbar = gamma_of(u0[0], u0[1], u0[2]);
+            if (c->gamma_pred) orc_gather_E(c, E, x[p], y[p], Ep0);
+            double gbar = gbar_of(c, beta, E, x[p], y[p], u0);
             orc_alpha(beta, gbar, Bp, alpha);
             double wv[3], ub[3], u1[3];
             for (int k = 0; k < 3; ++k) wv[k] = u0[k] + beta * Ep[k];
@@ -430,7 +445,21 @@ void orc_push(const orc_config* c, const int64_t* off,
             sums[0] += w[p] * m * gamma_m1(u0[0], u0[1], u0[2]);
             sums[1] += w[p] * m * gamma_m1(u1[0], u1[1], u1[2]);
             sums[2] += c->dt * w[p] * q * ue / gbar;
-            sums[3] += c->dt * w[p] * q * ue * g01 / (gbar * (gbar + g1));
+            if (!c->gamma_pred) {
+                sums[3] += c->dt * w[p] * q * ue * g01 / (gbar * (gbar + g1));
+            } else {
+                /* 2/(g0+g1) - 1/gbar = ((gbar-g0) + (gbar-g1))/(gbar (g0+g1)),
+                   each difference from squares: gbar^2 - g^2 = |u*|^2 - |u|^2 */
+                double g0 = gamma_of(u0[0], u0[1], u0[2]);
+                double d0 = 0.0, d1 = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    double us = u0[k] + beta * (Ep0[k]);
+                    d0 += (us - u0[k]) * (us + u0[k]);
+                    d1 += (us - u1[k]) * (us + u1[k]);
+                }
+                double diff = d0 / (gbar + g0) + d1 / (gbar + g1);
+                sums[3] += c->dt * w[p] * q * ue * diff / (gbar * (g0 + g1));
+            }
             ux[p] = u1[0];
             uy[p] = u1[1];
             uz[p] = u1[2];
@@ -500,14 +529,14 @@ int orc_step(const orc_config* c, const int64_t* off,
     memcpy(E0, E, sizeof(double) * 3 * nn);
     memcpy(B0, B, sizeof(double) * 3 * nn);
 
-    orc_deposit(c, off, x, y, ux, uy, uz, w, B, J, M);          /* steps 1-5 */
+    orc_deposit(c, off, x, y, ux, uy, uz, w, B, E, J, M);       /* steps 1-5 */
     orc_rhs(c, E, B, J, b);                                      /* step 6 */
     memcpy(Et, E, sizeof(double) * 3 * nn);
     int iters = 0;
     double relres = 0.0;
     int st = orc_gmres(c, M, b, Et, &iters, &relres);
     orc_field_update(c, Et, E, B);                               /* steps 7-8 */
-    orc_push(c, off, x, y, ux, uy, uz, w, Et, B0, sums);         /* steps 9-10 */
+    orc_push(c, off, x, y, ux, uy, uz, w, Et, B0, E0, sums);     /* steps 9-10 */
     orc_energies(c, off, ux, uy, uz, w, E, B, en1);
 
     if (led) {

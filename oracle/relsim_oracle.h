@@ -33,6 +33,7 @@ typedef struct {
     double q[4], m[4];
     double gmres_tol;
     int gmres_restart, gmres_maxit;
+    int gamma_pred;   /* 0: gbar = gamma(u^n); 1: gbar = gamma(u^n + beta E^n(x)) */
 } orc_config;
 
 typedef struct {
@@ -61,11 +62,12 @@ void   orc_gather_E(const orc_config* c, const double* E, double x, double y, do
 void   orc_gather_B(const orc_config* c, const double* B, double x, double y, double out[3]);
 void   orc_alpha(double beta, double gbar, const double Bp[3], double alpha[9]);
 
-/* deposit of predicted current Jhat[3*ncell] and mass matrix M[ncell*81] */
+/* deposit of predicted current Jhat[3*ncell] and mass matrix M[ncell*81];
+   E (E^n) is read only with gamma_pred */
 void   orc_deposit(const orc_config* c, const int64_t* off,
                    const double* x, const double* y,
                    const double* ux, const double* uy, const double* uz,
-                   const double* w, const double* B, double* J, double* M);
+                   const double* w, const double* B, const double* E, double* J, double* M);
 
 /* discrete curls and the implicit operator */
 void   orc_curl_c(const orc_config* c, const double* E, double* out);
@@ -77,10 +79,12 @@ int    orc_gmres(const orc_config* c, const double* M, const double* b, double* 
                  int* iters, double* relres);
 void   orc_field_update(const orc_config* c, const double* Etheta, double* E, double* B);
 
-/* explicit push; sums[4] = {K0, K1, work_particles, mismatch} */
+/* explicit push; sums[4] = {K0, K1, work_particles, mismatch}; E (E^n) is
+   read only with gamma_pred */
 void   orc_push(const orc_config* c, const int64_t* off,
                 double* x, double* y, double* ux, double* uy, double* uz,
-                const double* w, const double* Etheta, const double* B, double sums[4]);
+                const double* w, const double* Etheta, const double* B, const double* E,
+                double sums[4]);
 
 /* energies of a state: out[0] = W_E, out[1] = W_B, out[2] = K */
 void   orc_energies(const orc_config* c, const int64_t* off, const double* ux,

@@ -45,10 +45,15 @@ MUTANTS = {
                           "H[(i + 1) * m + j] = sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];"),
     "sort_unstable": ("perm[start[k] + cursor[k]++] = p;", "perm[start[k + 1] - 1 - cursor[k]++] = p;"),
     "field_energy_factor": ("out[0] = 0.5 * dV * dot(3 * nn, E, E);", "out[0] = dV * dot(3 * nn, E, E);"),
-    "push_uses_new_E": ("orc_push(c, off, x, y, ux, uy, uz, w, Et, B0, sums);",
-                        "orc_push(c, off, x, y, ux, uy, uz, w, E, B0, sums);"),
-    "push_uses_new_B": ("orc_push(c, off, x, y, ux, uy, uz, w, Et, B0, sums);",
-                        "orc_push(c, off, x, y, ux, uy, uz, w, Et, B, sums);"),
+    "push_uses_new_E": ("orc_push(c, off, x, y, ux, uy, uz, w, Et, B0, E0, sums);",
+                        "orc_push(c, off, x, y, ux, uy, uz, w, E, B0, E0, sums);"),
+    "push_uses_new_B": ("orc_push(c, off, x, y, ux, uy, uz, w, Et, B0, E0, sums);",
+                        "orc_push(c, off, x, y, ux, uy, uz, w, Et, B, E0, sums);"),
+    "pred_gbar_ignores_E": ("return gamma_of(u[0] + beta * Ep[0], u[1] + beta * Ep[1], u[2] + beta * Ep[2]);",
+                            "return gamma_of(u[0], u[1] + beta * Ep[1], u[2] + beta * Ep[2]);"),
+    "pred_mismatch_uses_Etheta": ("if (c->gamma_pred) orc_gather_E(c, E, x[p], y[p], Ep0);",
+                                  "if (c->gamma_pred) orc_gather_E(c, Etheta, x[p], y[p], Ep0);"),
+    "pred_mismatch_sign": ("d1 += (us - u1[k]) * (us + u1[k]);", "d1 -= (us - u1[k]) * (us + u1[k]);"),
     "dissipation_sign": ("led->dissipation = (c->theta - 0.5) * dV * (dE2 + dB2);",
                          "led->dissipation = (0.5 - c->theta) * dV * (dE2 + dB2);"),
 }
