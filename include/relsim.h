@@ -105,6 +105,11 @@ typedef struct {
     int track_ids;         /* nonzero: carry an int32 id per particle (its load
                               index) through every sort, for tracking           */
     uint64_t seed;         /* reserved                                         */
+    int gamma_pred;        /* 0: gbar = gamma(u^n) in alpha and M; 1: gbar =
+                              gamma(u^n + beta E^n(x)), the Lorentz factor of
+                              the predicted half-step momentum (E^n standing
+                              in for E^{n+theta}), which shrinks the
+                              relativistic energy error of a step          */
 } relsim_config;
 
 typedef struct {

@@ -71,7 +71,7 @@ class relsim_config(ctypes.Structure):
                 ("q", ctypes.c_double * 4), ("m", ctypes.c_double * 4),
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_maxit", ctypes.c_int), ("track_ids", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("gamma_pred", ctypes.c_int)]
 
 
 class relsim_energy(ctypes.Structure):
@@ -219,7 +219,9 @@ def _stream(stream=None) -> int:
 
 def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta_implicit=0.5, precision=32,
                 q=(1.0, -1.0), m=(1.0, 1.0), gmres_tol=0.0, gmres_restart=0, gmres_maxit=0,
-                track_ids=False) -> relsim_config:
+                track_ids=False, gamma_pred=False) -> relsim_config:
+    """gamma_pred: the Lorentz factor in alpha and M is that of the
+    predicted half-step momentum u^n + beta E^n(x) instead of u^n."""
     c = relsim_config()
     c.dim, c.nx, c.ny, c.nz = 2, nx, ny, 1
     c.dx, c.dy, c.dz, c.dt, c.theta_implicit = dx, dy, 1.0, dt, theta_implicit
@@ -229,6 +231,7 @@ def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta_implicit=0.5, precision=32
         c.m[s] = m[s]
     c.gmres_tol, c.gmres_restart, c.gmres_maxit = gmres_tol, gmres_restart, gmres_maxit
     c.track_ids = 1 if track_ids else 0
+    c.gamma_pred = 1 if gamma_pred else 0
     return c
 
 

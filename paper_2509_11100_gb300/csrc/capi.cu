@@ -88,6 +88,7 @@ struct relsim_ctx {
     Species sp[kMaxSpecies];
     void* E = nullptr;
     void* Eth = nullptr;
+    void* En = nullptr;        // E^n kept for the push of the predicted-gamma variant
     void* B[2] = {nullptr, nullptr};
     int bcur = 0;
     void* J = nullptr;
@@ -533,7 +534,8 @@ int build_impl(relsim_ctx* c)
         ds.cJ[s] = (T)(c->cfg.q[s] / c->g.dV);
         ds.cM[s] = (T)(c->cfg.q[s] * beta / c->g.dV);
     }
-    CK(deposit<T>(ds, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->dpush, c->st));
+    CK(deposit<T>(ds, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J, c->g,
+                  c->dpush, c->st));
     PROF_END();
     return RELSIM_OK;
 }
@@ -637,6 +639,8 @@ template <typename T>
 int solve_epilogue(relsim_ctx* c, cudaStream_t s)
 {
     CK(cudaMemcpyAsync(c->dled + kLedgerLen - 2, c->dled + 3, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // the predicted-gamma push needs E^n after E^{n+1} has replaced it
+    if (c->En) CK(cudaMemcpyAsync(c->En, c->E, c->esz * 3 * (size_t)c->g.ncell, cudaMemcpyDeviceToDevice, s));
     const int nbf = field_grid_blocks(c->g);
     PROF_BEGIN(RELSIM_PROF_FIELD_UPDATE);
     CK(field_update<T>(c->gx, (const T*)c->M, (const T*)c->J, (T*)c->Eth, (T*)c->E, (const T*)c->B[c->bcur],
@@ -756,7 +760,8 @@ int push_enqueue(relsim_ctx* c)
             PROF_BEGIN(RELSIM_PROF_PUSH);
             // K0 of this step is the kinetic energy the last push (or load) left
             CK(cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-            CK(push_sort<T>(src, dst, sp.start, c->n9, c->off9, Eth, B, c->g, sc, c->partial, nbp, c->st));
+            CK(push_sort<T>(src, dst, sp.start, c->n9, c->off9, Eth, B, (const T*)c->En, c->g, sc, c->partial,
+                            nbp, c->st));
             CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
             PROF_END();
             PROF_BEGIN(RELSIM_PROF_SORT_TABLES);
@@ -772,7 +777,8 @@ int push_enqueue(relsim_ctx* c)
             TRY(ensure_radix(c, sp.n));
             PROF_BEGIN(RELSIM_PROF_GENERAL_SORT);
             CK(cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-            CK(push_general<T>(src, dst, sp.start, c->rk[0], Eth, B, c->g, sc, c->partial, nbp, c->st));
+            CK(push_general<T>(src, dst, sp.start, c->rk[0], Eth, B, (const T*)c->En, c->g, sc, c->partial, nbp,
+                               c->st));
             CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
             CK(iota_i32(c->rv[0], sp.n, c->st));
             bool in1 = false;
@@ -1187,6 +1193,7 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     } while (0)
     A(dalloc(c, &c->E, c->esz * 3 * nc));
     A(dalloc(c, &c->Eth, c->esz * 3 * nc));
+    if (cfg->gamma_pred) A(dalloc(c, &c->En, c->esz * 3 * nc));
     A(dalloc(c, &c->B[0], c->esz * 3 * nc));
     A(dalloc(c, &c->B[1], c->esz * 3 * nc));
     A(dalloc(c, &c->J, c->esz * 3 * nc));
@@ -1278,7 +1285,7 @@ void relsim_destroy(relsim_ctx* c)
         dfree(sp.start);
         dfree(sp.start_alt);
     }
-    dfree(c->E); dfree(c->Eth); dfree(c->B[0]); dfree(c->B[1]); dfree(c->J); dfree(c->M);
+    dfree(c->E); dfree(c->Eth); dfree(c->En); dfree(c->B[0]); dfree(c->B[1]); dfree(c->J); dfree(c->M);
     dfree(c->n9); dfree(c->off9); dfree(c->count_new); dfree(c->scan_tmp);
     for (int b = 0; b < 2; ++b) {
         dfree(c->rk[b]);

@@ -77,21 +77,21 @@ template <typename T>
 cudaError_t export_particles(PArrays<T> p, const int32_t* start, GridP g, double* x, double* u,
                              double* w, int32_t* id, cudaStream_t st);
 template <typename T>
-cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g, int* err,
-                    cudaStream_t st);
+cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, const T* En, T* M, T* J, GridP g, int* err,
+                    cudaStream_t st);   // En = E^n for the predicted-gamma variant, else null
 // push with the cell-local sort: each old cell's pushed particles are written
 // back over the cell's own index range in dst grouped by move direction d;
 // n9[c][d] and off9[c][d] receive the count and the start of each run; the
 // particle ledger sums (K0, dK, work, mismatch, K1) go to lsum (per block).
 template <typename T>
 cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* n9, int32_t* off9,
-                      const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
-                      cudaStream_t st);
+                      const T* Eth, const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial,
+                      int lsum_blocks, cudaStream_t st);
 // general path (moves longer than one cell): pushed particles to the same
 // index of dst, their new cell to key; ledger sums as above
 template <typename T>
 cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, const T* Eth,
-                         const T* B, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
+                         const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
                          cudaStream_t st);
 // the stable new-cell order from the runs of push_sort (err bit 1 if the
 // runs and the new cell starts disagree)

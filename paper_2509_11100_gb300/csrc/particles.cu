@@ -205,6 +205,38 @@ __device__ __forceinline__ void tile_E(const T (*sE)[2][kTE], int l, T W0, T W1,
     Ez = W0 * sE[2][0][l] + W1 * sE[2][0][l + 1] + W2 * sE[2][1][l] + W3 * sE[2][1][l + 1];
 }
 
+// E^n on a unit's nodes, held only by the predicted-gamma variant (gbar =
+// gamma(u^n + beta E^n(x))); empty otherwise
+template <typename T, bool PRED>
+struct PredTile {
+    __device__ const T (*en() const)[2][kTE] { return nullptr; }
+};
+template <typename T>
+struct PredTile<T, true> {
+    T En[3][2][kTE];
+    __device__ const T (*en() const)[2][kTE] { return En; }
+};
+
+// |u|^2 of the momentum whose Lorentz factor enters alpha: u^n, or with
+// PRED the predicted u^n + beta E^n(x) (node weights W0..W3 of cell l)
+template <typename T, bool PRED>
+__device__ __forceinline__ T gbar_u2(T ux, T uy, T uz, T beta, const T (*sEn)[2][kTE], int l, T W0, T W1, T W2,
+                                     T W3, T& sx, T& sy, T& sz)
+{
+    if (!PRED) {
+        sx = ux;
+        sy = uy;
+        sz = uz;
+        return ux * ux + uy * uy + uz * uz;
+    }
+    T Ex, Ey, Ez;
+    tile_E(sEn, l, W0, W1, W2, W3, Ex, Ey, Ez);
+    sx = ux + beta * Ex;
+    sy = uy + beta * Ey;
+    sz = uz + beta * Ez;
+    return sx * sx + sy * sy + sz * sz;
+}
+
 // reciprocal square root and reciprocal: the hardware approximations in the
 // FP32 form (a few ulp), exact operations in the FP64 form
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
@@ -333,14 +365,17 @@ struct Moments<float> {
     }
 };
 
-template <typename T>
+template <typename T, bool PRED>
 __device__ __forceinline__ void deposit_particle(const T fx, const T fy, const T ux, const T uy, const T uz,
-                                                 const T w, const T (*sB)[3][kTB], int l, T beta, T cJ, T cM,
-                                                 Moments<T>& acc)
+                                                 const T w, const T (*sB)[3][kTB], const T (*sEn)[2][kTE], int l,
+                                                 T beta, T cJ, T cM, Moments<T>& acc)
 {
     T Bx, By, Bz;
     tile_B(sB, l, fx, fy, Bx, By, Bz);
-    const Rot<T> r = rotation<T>(ux * ux + uy * uy + uz * uz, Bx, By, Bz, beta);
+    T sx, sy, sz;
+    const T u2 = gbar_u2<T, PRED>(ux, uy, uz, beta, sEn, l, (T(1) - fx) * (T(1) - fy), fx * (T(1) - fy),
+                                  (T(1) - fx) * fy, fx * fy, sx, sy, sz);
+    const Rot<T> r = rotation<T>(u2, Bx, By, Bz, beta);
     const T ax = r.ax, ay = r.ay, az = r.az;
     T e[9];
     e[0] = T(1) + ax * ax; e[1] = ax * ay + az;   e[2] = ax * az - ay;
@@ -370,10 +405,10 @@ __device__ __forceinline__ void deposit_particle(const T fx, const T fy, const T
     acc.add(t, e);
 }
 
-template <typename T>
+template <typename T, bool PRED>
 __global__ void __launch_bounds__(kDepThreads, sizeof(T) == 4 ? 2 : 1)
-k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* __restrict__ J, GridP g,
-          int* __restrict__ err)
+k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ En, T* __restrict__ M,
+          T* __restrict__ J, GridP g, int* __restrict__ err)
 {
     constexpr int G = kDepG;
     constexpr int NB = kDepBuf;
@@ -383,6 +418,7 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
     __shared__ int sp0a[NB];      // aligned first particle of the staged range
     __shared__ int sstaged[NB];   // 1 if staged in shared memory, 0 if read from global
     __shared__ T sB[3][3][kTB];
+    __shared__ PredTile<T, PRED> sEn;
     T* buf = reinterpret_cast<T*>(dsmem);
     const int tid = threadIdx.x;
     const int gl = tid % G, grp = tid / G;
@@ -436,6 +472,7 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
         if (s == 0) {
             acc.zero();
             load_tile_B<T, kDepThreads>(sB, B, un, nx, ny, nc, tid);
+            if constexpr (PRED) load_tile_E<T, kDepThreads>(sEn.En, En, un, nx, ny, nc, tid);
         }
         const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1), kDepMaxPolls);
         // leave together if any thread gave up (never diverge at a barrier);
@@ -452,13 +489,14 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, T* __restrict__ M, T* _
             if (sstaged[b]) {
                 const T* sb = buf + (size_t)b * 6 * kDepCap - sp0a[b];
                 for (int p = p0 + gl; p < p1; p += G)
-                    deposit_particle<T>(sb[p], sb[kDepCap + p], sb[2 * kDepCap + p], sb[3 * kDepCap + p],
-                                        sb[4 * kDepCap + p], sb[5 * kDepCap + p], sB, grp, beta, cJ, cM, acc);
+                    deposit_particle<T, PRED>(sb[p], sb[kDepCap + p], sb[2 * kDepCap + p], sb[3 * kDepCap + p],
+                                              sb[4 * kDepCap + p], sb[5 * kDepCap + p], sB, sEn.en(), grp, beta,
+                                              cJ, cM, acc);
             } else {
                 for (int p = p0 + gl; p < p1; p += G)
-                    deposit_particle<T>(ld(sp.fx[s] + p), ld(sp.fy[s] + p), ld(sp.ux[s] + p),
-                                        ld(sp.uy[s] + p), ld(sp.uz[s] + p), ld(sp.w[s] + p), sB, grp, beta,
-                                        cJ, cM, acc);
+                    deposit_particle<T, PRED>(ld(sp.fx[s] + p), ld(sp.fy[s] + p), ld(sp.ux[s] + p),
+                                              ld(sp.uy[s] + p), ld(sp.uz[s] + p), ld(sp.w[s] + p), sB, sEn.en(),
+                                              grp, beta, cJ, cM, acc);
             }
         }
         if (s == nsp - 1) {
@@ -526,18 +564,21 @@ struct Pushed {
 
 // the explicit push of one particle: E^{n+theta}, B^n gathered at x^{n+1/2},
 // ubar = alpha (u + beta E), u1 = 2 ubar - u, x += dt u1/gamma1; ledger sums
-template <typename T>
+template <typename T, bool PRED>
 __device__ __forceinline__ void push_particle(const T fx, const T fy, const T ux, const T uy, const T uz,
                                               const T w, int l, const T (*sE)[2][kTE],
-                                              const T (*sB)[3][kTB], T beta, T dt_dx, T dt_dy, T qdt, T m,
-                                              bool clamp, bool ledger, T (&acc)[kLedger], Pushed<T>& o)
+                                              const T (*sB)[3][kTB], const T (*sEn)[2][kTE], T beta, T dt_dx,
+                                              T dt_dy, T qdt, T m, bool clamp, bool ledger, T (&acc)[kLedger],
+                                              Pushed<T>& o)
 {
     T Bx, By, Bz, Ex, Ey, Ez;
     tile_B(sB, l, fx, fy, Bx, By, Bz);
     const T X0 = T(1) - fx, Y0 = T(1) - fy;
     tile_E(sE, l, X0 * Y0, fx * Y0, X0 * fy, fx * fy, Ex, Ey, Ez);
     const T u02 = ux * ux + uy * uy + uz * uz;
-    const Rot<T> r = rotation<T>(u02, Bx, By, Bz, beta);
+    T psx, psy, psz;   // the momentum whose Lorentz factor is gbar
+    const T us2 = gbar_u2<T, PRED>(ux, uy, uz, beta, sEn, l, X0 * Y0, fx * Y0, X0 * fy, fx * fy, psx, psy, psz);
+    const Rot<T> r = rotation<T>(us2, Bx, By, Bz, beta);
     const T ax = r.ax, ay = r.ay, az = r.az, sa = r.sa;
     // ubar = alpha w = (w + w x a + (w.a) a)/(1 + |a|^2), w = u + beta E
     const T wx = ux + beta * Ex, wy = uy + beta * Ey, wz = uz + beta * Ez;
@@ -574,15 +615,31 @@ __device__ __forceinline__ void push_particle(const T fx, const T fy, const T ux
     o.sy = sy;
     o.dir = (sy + 1) * 3 + (sx + 1);
     if (ledger) {
-        const T g0 = (T(1) + u02) * r.ig, g1 = (T(1) + u12) * ig1;
+        const T g1 = (T(1) + u12) * ig1;
         const T ue = ubx * Ex + uby * Ey + ubz * Ez;
         // g0 - g1 = (u0 - u1).(u0 + u1)/(g0 + g1)
         const T du = (ux - o.u1x) * (ux + o.u1x) + (uy - o.u1y) * (uy + o.u1y) +
                      (uz - o.u1z) * (uz + o.u1z);
-        const T igs = rcp_t(g0 + g1);
-        acc[0] -= w * m * du * igs;                          // dK
-        acc[1] += qdt * w * ue * r.ig;                       // work
-        acc[2] += qdt * w * ue * du * igs * igs * r.ig;      // mismatch
+        if (!PRED) {
+            const T g0 = (T(1) + u02) * r.ig;   // gbar = g0
+            const T igs = rcp_t(g0 + g1);
+            acc[0] -= w * m * du * igs;                          // dK
+            acc[1] += qdt * w * ue * r.ig;                       // work
+            acc[2] += qdt * w * ue * du * igs * igs * r.ig;      // mismatch
+        } else {
+            // 2/(g0+g1) - 1/gbar = ((gbar-g0) + (gbar-g1))/(gbar (g0+g1)),
+            // gbar^2 - g^2 = |u*|^2 - |u|^2
+            const T g0 = (T(1) + u02) * rsqrt_t(T(1) + u02);
+            const T gb = (T(1) + us2) * r.ig;
+            const T igs = rcp_t(g0 + g1);
+            const T d0 = (psx - ux) * (psx + ux) + (psy - uy) * (psy + uy) + (psz - uz) * (psz + uz);
+            const T d1 = (psx - o.u1x) * (psx + o.u1x) + (psy - o.u1y) * (psy + o.u1y) +
+                         (psz - o.u1z) * (psz + o.u1z);
+            const T dif = d0 * rcp_t(gb + g0) + d1 * rcp_t(gb + g1);
+            acc[0] -= w * m * du * igs;                          // dK
+            acc[1] += qdt * w * ue * r.ig;                       // work
+            acc[2] += qdt * w * ue * dif * igs * r.ig;           // mismatch
+        }
         acc[3] += w * m * u12 * rcp_t(g1 + T(1));            // K1
     }
 }
@@ -652,15 +709,16 @@ __device__ __forceinline__ unsigned dir_peers(bool act, int dir)
     return m;
 }
 
-template <typename T>
+template <typename T, bool PRED>
 __global__ void __launch_bounds__(PushCfg<T>::threads, PushCfg<T>::min_blocks)
 k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int32_t* __restrict__ n9,
-            int32_t* __restrict__ off9, const T* __restrict__ Eth, const T* __restrict__ B, GridP g, T beta,
-            T dt_dx, T dt_dy, T qdt, T m, double* __restrict__ lsum)
+            int32_t* __restrict__ off9, const T* __restrict__ Eth, const T* __restrict__ B,
+            const T* __restrict__ En, GridP g, T beta, T dt_dx, T dt_dy, T qdt, T m, double* __restrict__ lsum)
 {
     constexpr int W = PushCfg<T>::warps;
     __shared__ int sstart[W][kUnitW + 1];
     __shared__ PushTile<T> stile[W];
+    __shared__ PredTile<T, PRED> sen[W];
     __shared__ PushStage<T> sstage[W];
     __shared__ double red[32 * kLedger];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -678,6 +736,10 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
     for (int u = warp; u < nunits; u += nwarps) {
         const Unit un = unit_of(u, nx);
         unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
+        if constexpr (PRED) {
+            load_tile_E<T, 32>(sen[wib].En, En, un, nx, ny, nc, lane);
+            __syncwarp();
+        }
         const int P1 = ss[un.cn];
         int pf_pos = -1;   // the first particle of the prefetched batch
         T pfx = T(0), pfy = T(0), pux = T(0), puy = T(0), puz = T(0), pw = T(0);
@@ -693,8 +755,9 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
                 const bool act = p < s1;
                 const int q = act ? p : s0;
                 Pushed<T> o;
-                push_particle<T>(ld(src.fx + q), ld(src.fy + q), ld(src.ux + q), ld(src.uy + q), ld(src.uz + q),
-                                 ld(src.w + q), l, tl.E, tl.B, beta, dt_dx, dt_dy, qdt, m, true, false, acc, o);
+                push_particle<T, PRED>(ld(src.fx + q), ld(src.fy + q), ld(src.ux + q), ld(src.uy + q),
+                                       ld(src.uz + q), ld(src.w + q), l, tl.E, tl.B, sen[wib].en(), beta, dt_dx,
+                                       dt_dy, qdt, m, true, false, acc, o);
                 const unsigned peers = dir_peers(act, o.dir);
                 if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
                 __syncwarp();
@@ -741,8 +804,8 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
                 }
                 Pushed<T> o;
                 // idle lanes carry weight 0: no ledger contribution (and nothing is stored)
-                push_particle<T>(fx, fy, ux, uy, uz, act ? w : T(0), l, tl.E, tl.B, beta, dt_dx, dt_dy, qdt, m, true,
-                                 true, acc, o);
+                push_particle<T, PRED>(fx, fy, ux, uy, uz, act ? w : T(0), l, tl.E, tl.B, sen[wib].en(), beta,
+                                       dt_dx, dt_dy, qdt, m, true, true, acc, o);
                 // rank among the cell's particles of the same direction, in order
                 const unsigned peers = dir_peers(act, o.dir);
                 const int rank = (act ? run[o.dir] : 0) + __popc(peers & lt);
@@ -805,15 +868,16 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
 
 // General path (moves of more than one cell): push in place order, write the
 // pushed particle to the same index of dst and its new cell to key.
-template <typename T>
+template <typename T, bool PRED>
 __global__ void __launch_bounds__(PushCfg<T>::threads, PushCfg<T>::min_blocks)
 k_push_general(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int32_t* __restrict__ key,
-               const T* __restrict__ Eth, const T* __restrict__ B, GridP g, T beta, T dt_dx, T dt_dy, T qdt, T m,
-               double* __restrict__ lsum)
+               const T* __restrict__ Eth, const T* __restrict__ B, const T* __restrict__ En, GridP g, T beta,
+               T dt_dx, T dt_dy, T qdt, T m, double* __restrict__ lsum)
 {
     constexpr int W = PushCfg<T>::warps;
     __shared__ int sstart[W][kUnitW + 1];
     __shared__ PushTile<T> stile[W];
+    __shared__ PredTile<T, PRED> sen[W];
     __shared__ double red[32 * kLedger];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -826,13 +890,18 @@ k_push_general(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start
     for (int u = warp; u < nunits; u += nwarps) {
         const Unit un = unit_of(u, nx);
         unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
+        if constexpr (PRED) {
+            load_tile_E<T, 32>(sen[wib].En, En, un, nx, ny, nc, lane);
+            __syncwarp();
+        }
         const int P0 = ss[0], P1 = ss[un.cn];
         int cl = 0;   // the lane's current local cell (particles ascend)
         for (int p = P0 + lane; p < P1; p += 32) {
             while (ss[cl + 1] <= p) ++cl;
             Pushed<T> o;
-            push_particle<T>(ld(src.fx + p), ld(src.fy + p), ld(src.ux + p), ld(src.uy + p), ld(src.uz + p),
-                             ld(src.w + p), cl, tl.E, tl.B, beta, dt_dx, dt_dy, qdt, m, false, true, acc, o);
+            push_particle<T, PRED>(ld(src.fx + p), ld(src.fy + p), ld(src.ux + p), ld(src.uy + p),
+                                   ld(src.uz + p), ld(src.w + p), cl, tl.E, tl.B, sen[wib].en(), beta, dt_dx, dt_dy,
+                                   qdt, m, false, true, acc, o);
             int ni = (un.i0 + cl + o.sx) % nx, nj = (un.j + o.sy) % ny;
             if (ni < 0) ni += nx;
             if (nj < 0) nj += ny;
@@ -1081,7 +1150,8 @@ cudaError_t export_particles(PArrays<T> p, const int32_t* start, GridP g, double
 }
 
 template <typename T>
-cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g, int* err, cudaStream_t st)
+cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, const T* En, T* M, T* J, GridP g, int* err,
+                    cudaStream_t st)
 {
     const int nunits = units_of(g.nx, g.ny);
     int dev = 0, nsm = 152;
@@ -1089,37 +1159,40 @@ cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, T* M, T* J, GridP g
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     nsm *= 2;   // two CTAs per SM
     const size_t smem = (size_t)kDepBuf * 6 * kDepCap * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(k_deposit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = En ? k_deposit<T, true> : k_deposit<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = nunits < nsm ? nunits : nsm;
     count_launches(1);
-    k_deposit<T><<<blocks, kDepThreads, smem, st>>>(sp, B, M, J, g, err);
+    kern<<<blocks, kDepThreads, smem, st>>>(sp, B, En, M, J, g, err);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* n9, int32_t* off9,
-                      const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
-                      cudaStream_t st)
+                      const T* Eth, const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial,
+                      int lsum_blocks, cudaStream_t st)
 {
     const T beta = (T)(sc.q * g.dt / (2.0 * sc.m));
+    auto kern = En ? k_push_sort<T, true> : k_push_sort<T, false>;
     count_launches(1);
-    k_push_sort<T><<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(src, dst, start, n9, off9, Eth, B, g, beta,
-                                                                (T)(g.dt / g.dx), (T)(g.dt / g.dy),
-                                                                (T)(sc.q * g.dt), (T)sc.m, lsum_partial);
+    kern<<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(src, dst, start, n9, off9, Eth, B, En, g, beta,
+                                                      (T)(g.dt / g.dx), (T)(g.dt / g.dy), (T)(sc.q * g.dt),
+                                                      (T)sc.m, lsum_partial);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, const T* Eth,
-                         const T* B, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
+                         const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
                          cudaStream_t st)
 {
     const T beta = (T)(sc.q * g.dt / (2.0 * sc.m));
+    auto kern = En ? k_push_general<T, true> : k_push_general<T, false>;
     count_launches(1);
-    k_push_general<T><<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(src, dst, start, key, Eth, B, g, beta,
-                                                                   (T)(g.dt / g.dx), (T)(g.dt / g.dy),
-                                                                   (T)(sc.q * g.dt), (T)sc.m, lsum_partial);
+    kern<<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(src, dst, start, key, Eth, B, En, g, beta,
+                                                      (T)(g.dt / g.dx), (T)(g.dt / g.dy), (T)(sc.q * g.dt),
+                                                      (T)sc.m, lsum_partial);
     return cudaGetLastError();
 }
 
@@ -1162,12 +1235,14 @@ cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int 
                                              cudaStream_t);                                        \
     template cudaError_t export_particles<T>(PArrays<T>, const int32_t*, GridP, double*, double*,  \
                                              double*, int32_t*, cudaStream_t);                     \
-    template cudaError_t deposit<T>(const DepositSpecies<T>&, const T*, T*, T*, GridP, int*, cudaStream_t); \
+    template cudaError_t deposit<T>(const DepositSpecies<T>&, const T*, const T*, T*, T*, GridP, int*,  \
+                                    cudaStream_t);                                                  \
     template cudaError_t push_sort<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, int32_t*,   \
-                                      const T*, const T*, GridP, SpeciesConst, double*, int,        \
-                                      cudaStream_t);                                                \
+                                      const T*, const T*, const T*, GridP, SpeciesConst, double*,   \
+                                      int, cudaStream_t);                                           \
     template cudaError_t push_general<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, const T*, \
-                                         const T*, GridP, SpeciesConst, double*, int, cudaStream_t); \
+                                         const T*, const T*, GridP, SpeciesConst, double*, int,      \
+                                         cudaStream_t);                                              \
     template cudaError_t permute<T>(PArrays<T>, PArrays<T>, const int32_t*, const int32_t*,         \
                                     const int32_t*, GridP, int*, cudaStream_t);                     \
     template cudaError_t kinetic_energy<T>(PArrays<T>, int64_t, double, double*, int, cudaStream_t); \
