@@ -4,11 +4,18 @@
 // growth-rate fit of a diagnostic series (Sec. 3.1: the tearing rate is the
 // best-fit slope of a mode's energy over its linear phase).
 //
-// Host threads drive the instances: each step of an instance waits on the
-// host a few times (GMRES read-backs), so one thread per in-flight instance
-// keeps several instances' kernels on the GPU at once while each thread
-// waits. Workers take instances largest first and run each one through all
-// steps, which balances uneven sizes without any barrier between steps.
+// Once every instance has taken one host-driven step (which sizes its
+// buffers), each instance's step is a captured CUDA graph (deposit, solve
+// with its loops as conditional nodes, field update, push, re-sort): the
+// runner then enqueues all steps of all instances, step by step across the
+// instances, each on its instance's stream with an asynchronous copy of the
+// solve's outcome, and waits once at the end. No host decision sits between
+// two steps, so the GPU holds work of every instance at once.
+//
+// Instances that cannot step as graphs (event profiling on, or moves of more
+// than one cell per step) are driven by host threads instead: workers take
+// instances largest first and run each one through all its steps, so one
+// instance's host waits are filled by the others' kernels.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -120,7 +127,69 @@ int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, dou
         }
     }
 
-    // largest instances first
+    // the first host-driven step of fresh instances, then the graphs
+    std::vector<int> done(count, 0);
+    bool graphs = true;
+    for (int i = 0; i < count; ++i) {
+        relsim_ctx* c = b->ctx[i];
+        if (cudaStreamSynchronize(ctx_stream(c)) != cudaSuccess) graphs = false;
+        if (!ctx_graph_prepare(c)) {
+            const int r = relsim_step(c, nullptr);
+            if (r != RELSIM_OK && r != RELSIM_ERR_NOT_CONVERGED) {
+                status[i] = r;
+                done[i] = nsteps;   // failed: no further steps
+                continue;
+            }
+            if (r == RELSIM_ERR_NOT_CONVERGED) status[i] = r;
+            if (iters) iters[(size_t)i * nsteps] = ctx_last_iters(c);
+            if (nmodes > 0 &&
+                relsim_field_modes(c, component, nmodes, dmodes + per * (size_t)i + (size_t)nmodes, RELSIM_DEVICE) !=
+                    RELSIM_OK)
+                graphs = false;
+            done[i] = 1;
+            if (nsteps > 1 && !ctx_graph_prepare(c)) graphs = false;
+        }
+    }
+    if (graphs) {
+        const size_t hb = ctx_graph_head_bytes();
+        unsigned char* heads = nullptr;
+        if (cudaMallocHost((void**)&heads, hb * (size_t)count * (size_t)nsteps) != cudaSuccess) {
+            cudaGetLastError();
+            graphs = false;
+        } else {
+            int rc = RELSIM_OK;
+            for (int s = 0; s < nsteps && rc == RELSIM_OK; ++s)
+                for (int i = 0; i < count && rc == RELSIM_OK; ++i) {
+                    if (s < done[i]) continue;
+                    relsim_ctx* c = b->ctx[i];
+                    rc = ctx_graph_enqueue(c, heads + hb * ((size_t)i * nsteps + s));
+                    if (rc == RELSIM_OK && nmodes > 0)
+                        rc = relsim_field_modes(c, component, nmodes,
+                                                dmodes + per * (size_t)i + (size_t)(s + 1) * nmodes, RELSIM_DEVICE);
+                }
+            for (int i = 0; i < count; ++i)
+                if (cudaStreamSynchronize(ctx_stream(b->ctx[i])) != cudaSuccess && rc == RELSIM_OK) rc = RELSIM_ERR_CUDA;
+            if (rc == RELSIM_OK)
+                for (int i = 0; i < count; ++i)
+                    for (int s = done[i]; s < nsteps; ++s) {
+                        int it = 0;
+                        const int r = ctx_graph_outcome(b->ctx[i], heads + hb * ((size_t)i * nsteps + s), &it);
+                        if (iters) iters[(size_t)i * nsteps + s] = it;
+                        if (r != RELSIM_OK && (status[i] == RELSIM_OK || status[i] == RELSIM_ERR_NOT_CONVERGED) &&
+                            !(r == RELSIM_ERR_NOT_CONVERGED && status[i] == RELSIM_ERR_NOT_CONVERGED))
+                            status[i] = r;
+                    }
+            cudaFreeHost(heads);
+            if (rc != RELSIM_OK) {
+                cudaDeviceSynchronize();
+                cudaFree(dmodes);
+                return rc;
+            }
+            for (int i = 0; i < count; ++i) done[i] = nsteps;
+        }
+    }
+
+    // the rest host-driven: largest instances first
     std::vector<int> order(count);
     std::vector<int64_t> size(count);
     for (int i = 0; i < count; ++i) {
@@ -138,8 +207,9 @@ int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, dou
         for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) {
             const int i = order[k];
             relsim_ctx* c = b->ctx[i];
-            int st = RELSIM_OK;
-            for (int s = 0; s < nsteps; ++s) {
+            if (done[i] >= nsteps) continue;
+            int st = status[i];
+            for (int s = done[i]; s < nsteps; ++s) {
                 const int r = relsim_step(c, nullptr);
                 if (r != RELSIM_OK && r != RELSIM_ERR_NOT_CONVERGED) {
                     st = r;

@@ -990,6 +990,80 @@ int step_graph(relsim_ctx* c, relsim_energy* ledger, int* status)
     return RELSIM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// graph steps enqueued back to back (the batch runner): both layouts are
+// captured up front, each step is one graph launch on the context's stream
+// plus an asynchronous copy of its solve outcome, and nothing waits until
+// the caller synchronises the stream.
+
+bool graph_eligible(const relsim_ctx* c)
+{
+    return c->state == kReady && c->have_step && c->fast_sort && !c->prof.on && !c->graph_off;
+}
+
+StepGraph* graph_for_layout(relsim_ctx* c)
+{
+    for (StepGraph& g : c->sg)
+        if (graph_matches(c, g)) return &g;
+    return nullptr;
+}
+
+}  // namespace
+
+namespace relsim {
+
+size_t ctx_graph_head_bytes() { return kGmHead; }
+
+int ctx_graph_prepare(relsim_ctx* c)
+{
+    if (!graph_eligible(c)) return 0;
+    bool have_a = graph_for_layout(c) != nullptr;
+    push_commit(c);
+    bool have_b = graph_for_layout(c) != nullptr;
+    push_commit(c);
+    if (have_a && have_b) return 1;
+    for (int k = 0; k < 2; ++k) {
+        const int r = c->prec == 32 ? capture_step<float>(c, c->sg[k]) : capture_step<double>(c, c->sg[k]);
+        if (r != RELSIM_OK) {
+            if (k == 1) push_commit(c);
+            c->graph_off = true;
+            c->graph_why = c->err;
+            c->err.clear();
+            return 0;
+        }
+        push_commit(c);   // the next layout; after both captures, the first again
+    }
+    return 1;
+}
+
+int ctx_graph_enqueue(relsim_ctx* c, void* head)
+{
+    StepGraph* G = graph_for_layout(c);
+    if (!G) return fail(c, RELSIM_ERR_INTERNAL, "no step graph for the current layout");
+    CK(cudaGraphLaunch(G->exec, c->st));
+    CK(cudaMemcpyAsync(head, c->gms, kGmHead, cudaMemcpyDeviceToHost, c->st));
+    push_commit(c);
+    c->state = kReady;
+    c->have_step = true;
+    ++c->step;
+    ++c->graph_steps;
+    return RELSIM_OK;
+}
+
+int ctx_graph_outcome(relsim_ctx* c, const void* head, int* iters)
+{
+    GmState h;
+    memcpy(&h, head, kGmHead);
+    const StepGraph& G = c->sg[0];
+    count_launches((int)(G.k_static + G.k_cycle * h.restarts + G.k_iter * h.total));
+    TRY(check_push(c));
+    return solve_outcome(c, &h, iters, nullptr);
+}
+
+}  // namespace relsim
+
+namespace {
+
 template <typename T>
 int spectrum_impl(relsim_ctx* c, int s, int variable, int nbins, const double* edges, double* weight,
                   int64_t* count, int where)

@@ -248,4 +248,12 @@ namespace relsim {
 cudaStream_t ctx_stream(const relsim_ctx* c);
 int ctx_last_iters(const relsim_ctx* c);
 int64_t ctx_particles(const relsim_ctx* c);
+// graph steps enqueued without waiting: prepare captures both buffer layouts
+// (1: ready; 0: this context steps from the host); enqueue launches one
+// step and copies its solve outcome (head_bytes) to the pinned host buffer
+// head; outcome reads one such head after the stream was synchronised
+size_t ctx_graph_head_bytes();
+int ctx_graph_prepare(relsim_ctx* c);
+int ctx_graph_enqueue(relsim_ctx* c, void* head);
+int ctx_graph_outcome(relsim_ctx* c, const void* head, int* iters);
 }  // namespace relsim

@@ -98,6 +98,8 @@ def test_batch_equals_instances_stepped_one_by_one(rs):
     assert list(status) == [0] * len(SIZES)
     assert np.all(iters > 0)
     after = [s.fields()[1] for s in sims]
+    # after one host-driven step each instance stepped as enqueued graphs
+    assert all(s.graph_info()["graph_steps"] == steps - 1 for s in sims)
     batch.close()
     # the batch's last mode energies are those of the final fields
     for k, s in enumerate(sims):
