@@ -552,8 +552,9 @@ template <typename T> struct PushCfg {
     static constexpr int warps = 4;                        // static shared memory < 48 KB
     static constexpr int threads = 32 * warps;
     static constexpr int min_blocks = sizeof(T) == 4 ? 5 : 2;
+    static constexpr int cap = sizeof(T) == 4 ? 192 : 128;   // particles of a cell group staged per warp
 };
-constexpr int kPushCap = 128;   // particles of one cell staged per warp
+constexpr int kGroupMax = 8;    // cells staged together at most
 constexpr int kLedger = 4;      // dK, work, mismatch, K1 (K0 is the previous K1)
 
 template <typename T>
@@ -651,14 +652,18 @@ struct PushTile {
 };
 
 // a cell's pushed particles, staged for the write back in direction order
+// a group of cells' pushed particles, staged for the write back in cell and
+// direction order
 template <typename T>
 struct PushStage {
-    T fx[kPushCap], fy[kPushCap], ux[kPushCap], uy[kPushCap], uz[kPushCap], w[kPushCap];
-    int32_t id[kPushCap];
-    uint8_t dir[kPushCap], rank[kPushCap], inv[kPushCap];
-    int doff[kNDir + 1];
-    int run[kNDir];
+    static constexpr int C = PushCfg<T>::cap;
+    T fx[C], fy[C], ux[C], uy[C], uz[C], w[C];
+    int32_t id[C];
+    uint8_t dir[C], rank[C], inv[C], cell[C];
+    int doff[kGroupMax * (kNDir + 1)];
+    int run[kGroupMax * kNDir];
 };
+static_assert(PushCfg<float>::cap <= 256 && PushCfg<double>::cap <= 256, "uint8 staging indices");
 
 template <typename T>
 __device__ __forceinline__ void block_ledger(const T (&acc)[kLedger], double* red, double* __restrict__ lsum)
@@ -743,55 +748,99 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
         const int P1 = ss[un.cn];
         int pf_pos = -1;   // the first particle of the prefetched batch
         T pfx = T(0), pfy = T(0), pux = T(0), puy = T(0), puz = T(0), pw = T(0);
-        for (int l = 0; l < un.cn; ++l) {
-            const int s0 = ss[l], s1 = ss[l + 1], np = s1 - s0;
-            int* run = st.run;   // particles of this cell per direction so far
-            if (lane < kNDir) run[lane] = 0;
-            __syncwarp();
-            const bool staged = np <= kPushCap;
-            // big cells take a counting pass first (no ledger, nothing written)
-            for (int b0 = s0; !staged && b0 < s1; b0 += 32) {
-                const int p = b0 + lane;
-                const bool act = p < s1;
-                const int q = act ? p : s0;
-                Pushed<T> o;
-                push_particle<T, PRED>(ld(src.fx + q), ld(src.fy + q), ld(src.ux + q), ld(src.uy + q),
-                                       ld(src.uz + q), ld(src.w + q), l, tl.E, tl.B, sen[wib].en(), beta, dt_dx,
-                                       dt_dy, qdt, m, true, false, acc, o);
-                const unsigned peers = dir_peers(act, o.dir);
-                if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
+        for (int l = 0; l < un.cn;) {
+            const int s0 = ss[l];
+            if (ss[l + 1] - s0 > PushCfg<T>::cap) {
+                // a big cell alone: a counting pass (no ledger, nothing
+                // written), then every particle written to its slot directly
+                const int s1 = ss[l + 1];
+                int* run = st.run;
+                if (lane < kNDir) run[lane] = 0;
                 __syncwarp();
-            }
-            if (!staged) {
+                for (int b0 = s0; b0 < s1; b0 += 32) {
+                    const int p = b0 + lane;
+                    const bool act = p < s1;
+                    const int q = act ? p : s0;
+                    Pushed<T> o;
+                    push_particle<T, PRED>(ld(src.fx + q), ld(src.fy + q), ld(src.ux + q), ld(src.uy + q),
+                                           ld(src.uz + q), ld(src.w + q), l, tl.E, tl.B, sen[wib].en(), beta,
+                                           dt_dx, dt_dy, qdt, m, true, false, acc, o);
+                    const unsigned peers = __match_any_sync(0xffffffffu, act ? o.dir : 1024 + lane);
+                    if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
+                    __syncwarp();
+                }
                 store_doff(run, st.doff, lane);
                 __syncwarp();
                 if (lane < kNDir) run[lane] = 0;
                 __syncwarp();
+                for (int b0 = s0; b0 < s1; b0 += 32) {
+                    const int p = b0 + lane;
+                    const bool act = p < s1;
+                    const int q = act ? p : s0;
+                    T fx, fy, ux, uy, uz, w;
+                    if (pf_pos == b0) {
+                        fx = pfx; fy = pfy; ux = pux; uy = puy; uz = puz; w = pw;
+                    } else {
+                        fx = ld(src.fx + q); fy = ld(src.fy + q); ux = ld(src.ux + q);
+                        uy = ld(src.uy + q); uz = ld(src.uz + q); w = ld(src.w + q);
+                    }
+                    pf_pos = -1;
+                    Pushed<T> o;
+                    push_particle<T, PRED>(fx, fy, ux, uy, uz, act ? w : T(0), l, tl.E, tl.B, sen[wib].en(), beta,
+                                           dt_dx, dt_dy, qdt, m, true, true, acc, o);
+                    const unsigned peers = __match_any_sync(0xffffffffu, act ? o.dir : 1024 + lane);
+                    const int rank = (act ? run[o.dir] : 0) + __popc(peers & lt);
+                    __syncwarp();
+                    if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
+                    __syncwarp();
+                    if (act) {
+                        const int pos = s0 + st.doff[o.dir] + rank;
+                        dst.fx[pos] = o.fxn;
+                        dst.fy[pos] = o.fyn;
+                        dst.ux[pos] = o.u1x;
+                        dst.uy[pos] = o.u1y;
+                        dst.uz[pos] = o.u1z;
+                        dst.w[pos] = o.w;
+                        if (ids) dst.id[pos] = src.id[p];
+                    }
+                }
+                const int c = un.c0 + l;
+                if (lane < kNDir) {
+                    n9[(int64_t)c * kNDir + lane] = st.doff[lane + 1] - st.doff[lane];
+                    off9[(int64_t)c * kNDir + lane] = s0 + st.doff[lane];
+                }
+                __syncwarp();
+                ++l;
+                continue;
             }
-            // the pass that ranks (and stages or writes) every particle; the
-            // next batch of the unit (this cell's or the next one's) is loaded
-            // while this one is pushed
+            // a group of consecutive cells staged together: the warp's lanes
+            // run over the group's particles in batches of 32 whatever cell
+            // they belong to, so short cells do not leave lanes idle
+            int gsz = 1, tot = ss[l + 1] - s0;
+            while (gsz < kGroupMax && l + gsz < un.cn) {
+                const int nn = ss[l + gsz + 1] - ss[l + gsz];
+                if (tot + nn > PushCfg<T>::cap) break;
+                tot += nn;
+                ++gsz;
+            }
+            const int s1 = s0 + tot;
+            for (int i = lane; i < gsz * kNDir; i += 32) st.run[i] = 0;
+            __syncwarp();
+            int ci = 0;   // this lane's cell within the group
+            // the next batch of the unit (this group's or the next cell's) is
+            // loaded while this one is pushed
             for (int b0 = s0; b0 < s1; b0 += 32) {
                 const int p = b0 + lane;
                 const bool act = p < s1;
                 const int q = act ? p : s0;
+                while (ci + 1 < gsz && ss[l + ci + 1] <= p) ++ci;
                 T fx, fy, ux, uy, uz, w;
                 if (pf_pos == b0) {
-                    fx = pfx;
-                    fy = pfy;
-                    ux = pux;
-                    uy = puy;
-                    uz = puz;
-                    w = pw;
+                    fx = pfx; fy = pfy; ux = pux; uy = puy; uz = puz; w = pw;
                 } else {
-                    fx = ld(src.fx + q);
-                    fy = ld(src.fy + q);
-                    ux = ld(src.ux + q);
-                    uy = ld(src.uy + q);
-                    uz = ld(src.uz + q);
-                    w = ld(src.w + q);
+                    fx = ld(src.fx + q); fy = ld(src.fy + q); ux = ld(src.ux + q);
+                    uy = ld(src.uy + q); uz = ld(src.uz + q); w = ld(src.w + q);
                 }
-                // the next batch starts here in this cell, or at the next cell
                 pf_pos = b0 + 32 < s1 ? b0 + 32 : s1;
                 if (pf_pos < P1) {
                     const int pq = pf_pos + lane < P1 ? pf_pos + lane : P1 - 1;
@@ -804,63 +853,64 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
                 }
                 Pushed<T> o;
                 // idle lanes carry weight 0: no ledger contribution (and nothing is stored)
-                push_particle<T, PRED>(fx, fy, ux, uy, uz, act ? w : T(0), l, tl.E, tl.B, sen[wib].en(), beta,
-                                       dt_dx, dt_dy, qdt, m, true, true, acc, o);
-                // rank among the cell's particles of the same direction, in order
-                const unsigned peers = dir_peers(act, o.dir);
-                const int rank = (act ? run[o.dir] : 0) + __popc(peers & lt);
+                push_particle<T, PRED>(fx, fy, ux, uy, uz, act ? w : T(0), l + ci, tl.E, tl.B, sen[wib].en(),
+                                       beta, dt_dx, dt_dy, qdt, m, true, true, acc, o);
+                // rank among the group's particles of the same cell and direction, in order
+                const unsigned peers = __match_any_sync(0xffffffffu, act ? ci * 16 + o.dir : 1024 + lane);
+                const int ridx = ci * kNDir + o.dir;
+                const int rank = (act ? st.run[ridx] : 0) + __popc(peers & lt);
                 __syncwarp();
-                if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
+                if (act && (peers & lt) == 0) st.run[ridx] += __popc(peers);
                 __syncwarp();
                 if (act) {
-                    if (staged) {
-                        const int e = p - s0;
-                        st.fx[e] = o.fxn;
-                        st.fy[e] = o.fyn;
-                        st.ux[e] = o.u1x;
-                        st.uy[e] = o.u1y;
-                        st.uz[e] = o.u1z;
-                        st.w[e] = o.w;
-                        if (ids) st.id[e] = src.id[p];
-                        st.dir[e] = (uint8_t)o.dir;
-                        st.rank[e] = (uint8_t)rank;
-                    } else {
-                        const int pos = s0 + st.doff[o.dir] + rank;
-                        dst.fx[pos] = o.fxn;
-                        dst.fy[pos] = o.fyn;
-                        dst.ux[pos] = o.u1x;
-                        dst.uy[pos] = o.u1y;
-                        dst.uz[pos] = o.u1z;
-                        dst.w[pos] = o.w;
-                        if (ids) dst.id[pos] = src.id[p];
-                    }
+                    const int e = p - s0;
+                    st.fx[e] = o.fxn;
+                    st.fy[e] = o.fyn;
+                    st.ux[e] = o.u1x;
+                    st.uy[e] = o.u1y;
+                    st.uz[e] = o.u1z;
+                    st.w[e] = o.w;
+                    if (ids) st.id[e] = src.id[p];
+                    st.dir[e] = (uint8_t)o.dir;
+                    st.rank[e] = (uint8_t)rank;
+                    st.cell[e] = (uint8_t)ci;
                 }
             }
-            if (staged) {
-                // direction offsets, the inverse permutation, then the
-                // coalesced write of the cell in direction order
-                store_doff(run, st.doff, lane);
-                __syncwarp();
-                for (int e = lane; e < np; e += 32) st.inv[st.doff[st.dir[e]] + st.rank[e]] = (uint8_t)e;
-                __syncwarp();
-                for (int qq = lane; qq < np; qq += 32) {
-                    const int e = st.inv[qq];
-                    dst.fx[s0 + qq] = st.fx[e];
-                    dst.fy[s0 + qq] = st.fy[e];
-                    dst.ux[s0 + qq] = st.ux[e];
-                    dst.uy[s0 + qq] = st.uy[e];
-                    dst.uz[s0 + qq] = st.uz[e];
-                    dst.w[s0 + qq] = st.w[e];
-                    if (ids) dst.id[s0 + qq] = st.id[e];
+            // offsets per (cell, direction) within the group, the inverse
+            // permutation, then one coalesced write of the group in cell and
+            // direction order
+            for (int i = lane; i < gsz; i += 32) {
+                int v = ss[l + i] - s0;
+#pragma unroll
+                for (int d = 0; d < kNDir; ++d) {
+                    st.doff[i * (kNDir + 1) + d] = v;
+                    v += st.run[i * kNDir + d];
                 }
-            }
-            // the runs of this cell: counts and starts per direction
-            const int c = un.c0 + l;
-            if (lane < kNDir) {
-                n9[(int64_t)c * kNDir + lane] = st.doff[lane + 1] - st.doff[lane];
-                off9[(int64_t)c * kNDir + lane] = s0 + st.doff[lane];
+                st.doff[i * (kNDir + 1) + kNDir] = v;
             }
             __syncwarp();
+            for (int e = lane; e < tot; e += 32)
+                st.inv[st.doff[st.cell[e] * (kNDir + 1) + st.dir[e]] + st.rank[e]] = (uint8_t)e;
+            __syncwarp();
+            for (int qq = lane; qq < tot; qq += 32) {
+                const int e = st.inv[qq];
+                dst.fx[s0 + qq] = st.fx[e];
+                dst.fy[s0 + qq] = st.fy[e];
+                dst.ux[s0 + qq] = st.ux[e];
+                dst.uy[s0 + qq] = st.uy[e];
+                dst.uz[s0 + qq] = st.uz[e];
+                dst.w[s0 + qq] = st.w[e];
+                if (ids) dst.id[s0 + qq] = st.id[e];
+            }
+            // the runs of the group's cells: counts and starts per direction
+            for (int i = lane; i < gsz * kNDir; i += 32) {
+                const int gi = i / kNDir, d = i - gi * kNDir;
+                const int64_t c = un.c0 + l + gi;
+                n9[c * kNDir + d] = st.run[i];
+                off9[c * kNDir + d] = s0 + st.doff[gi * (kNDir + 1) + d];
+            }
+            __syncwarp();
+            l += gsz;
         }
     }
     block_ledger<T>(acc, red, lsum);
