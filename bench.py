@@ -586,10 +586,40 @@ def run_scan(args):
         "setup_s": t_setup,
         "instances": rows,
     }
+    if args.scan_reference and rank == 0:
+        out["single_instance_reference"] = scan_single_reference(rs, torch)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def scan_single_reference(rs, torch, sizes=((1024, 512), (768, 384), (128, 64)), steps=20):
+    """Single instances with the scan's parameters (32 ppc per species,
+    dt = 0.5, delta 1, sigma 10, 0.1% perturbation), graph steps, for scale."""
+    from relsim_inputs import HarrisConfig, make_harris
+    res = []
+    for nx, ny in sizes:
+        hc = HarrisConfig(nx=nx, ny=ny, ppc=32, dt=0.5, delta=1.0, sigma=10.0, pert=1e-3, theta_T=0.3)
+        st = make_harris(hc)
+        n = sum(len(s["w"]) for s in st["species"])
+        sim = rs.Simulation(rs.make_config(nx, ny, dt=hc.dt, theta_implicit=hc.theta, precision=32,
+                                           gmres_tol=SCAN["gmres_tol"], gmres_restart=SCAN["gmres_restart"]))
+        sim.load_state(st)
+        for _ in range(3):
+            sim.step(ledger=False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            sim.step(ledger=True)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        res.append({"nx": nx, "ny": ny, "particles": n, "ms_per_step": ms, "value": n / (ms / 1e3),
+                    "unit": UNIT, "steps": steps})
+        sim.close()
+    return res
 
 
 def main():
@@ -605,6 +635,8 @@ def main():
                     help="small: 512x256 cells for profiler captures; scan: the 48-instance batched "
                          "tearing scan (run with --steps 400 for its full length)")
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the scan's batch runner")
+    ap.add_argument("--scan-reference", action="store_true",
+                    help="scan: also time single 1024x512, 768x384 and 128x64 instances with its parameters")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
