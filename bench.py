@@ -253,6 +253,19 @@ def run_ours(args):
     esz = 4
     per_kernel = {k: {"ms_per_step": v[0] / kp, "groups": v[1], "kernels": v[2]}
                   for k, v in prof.items() if v[1] > 0}
+    # each kernel group's algorithmic bytes per step over its time: the HBM
+    # roofline fraction of every slot that has a byte count
+    peak_gbs, _ = measured_peaks()
+    for k, v in per_kernel.items():
+        if k in ("push", "permute"):
+            ab = sum(algorithmic_bytes(k, 0, n, ncell, 4) for n in n_per)
+        elif k == "gmres_apply":
+            ab = algorithmic_bytes(k, 0, 0, ncell, 4) * v["kernels"] / kp
+        else:
+            ab = algorithmic_bytes(k, N, 0, ncell, 4)
+        if ab:
+            gbs = ab / (v["ms_per_step"] / 1e3) / 1e9
+            v.update({"algorithmic_bytes_per_step": ab, "achieved_gbs": gbs, "frac": gbs / peak_gbs})
     step_kernel_ms = sum(v["ms_per_step"] for v in per_kernel.values())
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
     peak, peak_kind = measured_peaks()

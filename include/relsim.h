@@ -209,6 +209,31 @@ RELSIM_API int relsim_set_mass_matrix(relsim_ctx* ctx, const double* M, const do
    the best iterate), NONFINITE, CUDA. */
 RELSIM_API int relsim_field_solve(relsim_ctx* ctx, int* iters, double* rel_residual);
 
+/* Adjoint of the field part of the solved step, with the particles held
+   fixed (the implicit field solve of Sec. 2 is the step's only global
+   coupling; this is the piece a differentiable window chains with the
+   adjoints of the push and the deposit). The forward map is linear in
+   (E^n, B^n, Jhat):
+     b = E^n + theta dt curl_n B^n - theta dt Jhat,  A E^{n+theta} = b,
+     E^{n+1} = (E^{n+theta} - (1-theta) E^n)/theta,
+     B^{n+1} = B^n - dt curl_c E^{n+theta}.
+   Given gE1 = dL/dE^{n+1} and gB1 = dL/dB^{n+1} (3*ncell FP64 each, field
+   layout), it solves A^T lambda = gE1/theta - dt curl_c^T gB1 by GMRES
+   (the same device-controlled loop, transposed operator; gmres_tol and
+   gmres_maxit of the context) and returns dL/dE^n = lambda - (1-theta)/theta
+   gE1, dL/dB^n = gB1 + theta dt curl_n^T lambda, dL/dJhat = -theta dt lambda
+   (3*ncell each) and dL/dM for the stored mass-matrix blocks (ncell x 45 in
+   relsim_get_mass_matrix's layout; a block serves both node pairs (g, g+o)
+   and (g+o, g)): -theta dt (lambda_g E_{g+o}^T + [o != 0] lambda_{g+o}
+   E_g^T), E = E^{n+theta}. Any output may be NULL. Call it between
+   relsim_field_solve and relsim_push (BAD_STATE otherwise). *iters and
+   *rel_residual (may be NULL) report the adjoint solve. Synchronises the
+   stream. Errors: INVALID_ARG, BAD_STATE, NOT_CONVERGED (outputs still
+   written), NONFINITE, OOM, CUDA. */
+RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const double* gB1, double* gE0,
+                                    double* gB0, double* gJ, double* gM, int* iters, double* rel_residual,
+                                    int where);
+
 /* E^{n+theta} of the last solve (3*ncell FP64). Errors: BAD_STATE, CUDA. */
 RELSIM_API int relsim_get_E_theta(relsim_ctx* ctx, double* E, int where);
 

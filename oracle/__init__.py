@@ -17,7 +17,7 @@ from .build import build, lib_path
 __all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "curl_c",
            "curl_n", "rhs", "gmres", "field_update", "push", "energies", "cell_keys",
            "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
-           "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit"]
+           "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit", "field_adjoint"]
 
 
 class OracleConfig(ctypes.Structure):
@@ -348,3 +348,54 @@ def growth_fit(s, dt, window):
     if best is None:
         raise ValueError("no admissible window")
     return best
+
+
+def field_adjoint(c, M, Etheta, gE1, gB1):
+    """Adjoint of the field part of one step with the particles (hence M and
+    Jhat) held fixed. The forward map (Sec. 2: the implicit field solve) is
+      b = E0 + theta dt curl_n B0 - theta dt J,   A Et = b,
+      E1 = (Et - (1 - theta) E0)/theta,           B1 = B0 - dt curl_c Et,
+    with A = I + (theta dt)^2 curl_n curl_c + theta dt M (M in the oracle's
+    full layout, (nn, 9, 3, 3)). For L with dL/dE1 = gE1, dL/dB1 = gB1 this
+    returns dL/dE0, dL/dB0, dL/dJ and dL/dM (full layout), by the chain rule
+    written out with dense matrices: A, curl_c and curl_n are assembled
+    column by column from the oracle's own operators and transposed with
+    numpy, and A^T lambda = dL/dEt is solved densely. For small grids only.
+    """
+    nn = c.nx * c.ny
+    N = 3 * nn
+    M = np.asarray(M, dtype=np.float64)
+
+    def dense(f):
+        out = np.empty((N, N))
+        e = np.zeros(N)
+        for k in range(N):
+            e[k] = 1.0
+            out[:, k] = np.asarray(f(e)).ravel()
+            e[k] = 0.0
+        return out
+
+    A = dense(lambda v: apply_A(c, M, v))
+    Cc = dense(lambda v: curl_c(c, v))
+    Cn = dense(lambda v: curl_n(c, v))
+    th, dt = c.theta, c.dt
+    gE1 = np.asarray(gE1, dtype=np.float64).ravel()
+    gB1 = np.asarray(gB1, dtype=np.float64).ravel()
+    gEt = gE1 / th - dt * (Cc.T @ gB1)
+    lam = np.linalg.solve(A.T, gEt)
+    gE0 = lam - (1.0 - th) / th * gE1
+    gB0 = gB1 + th * dt * (Cn.T @ lam)
+    gJ = -th * dt * lam
+    # dL/dA = -lambda Et^T; A holds theta dt M_{g g'} in the 3x3 block of
+    # rows g, columns g'
+    Et = np.asarray(Etheta, dtype=np.float64).reshape(3, nn)
+    L3 = lam.reshape(3, nn)
+    gM = np.zeros((nn, 9, 3, 3))
+    for g in range(nn):
+        i, j = g % c.nx, g // c.nx
+        for slot in range(9):
+            di, dj = slot % 3 - 1, slot // 3 - 1
+            h = ((j + dj) % c.ny) * c.nx + (i + di) % c.nx
+            gM[g, slot] = -th * dt * np.outer(L3[:, g], Et[:, h])
+    return {"E0": gE0.reshape(3, nn), "B0": gB0.reshape(3, nn), "J": gJ.reshape(3, nn), "M": gM,
+            "lambda": lam.reshape(3, nn)}

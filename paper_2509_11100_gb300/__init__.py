@@ -29,7 +29,7 @@ __all__ = [
     "relsim_kinetic_energy_noalloc", "relsim_energy_spectrum", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
     "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
-    "relsim_batch_destroy", "Batch", "relsim_graph_info",
+    "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -127,6 +127,7 @@ _SIGS = {
     "relsim_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "relsim_batch_destroy": (None, [_P]),
     "relsim_graph_info": (ctypes.c_int, [_CTX, _P, _P, _P]),
+    "relsim_field_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
 }
 
 PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
@@ -391,6 +392,25 @@ def relsim_growth_fit(s, dt, window):
     return rate.value, first.value
 
 
+def relsim_field_adjoint(ctx, ncell, gE1, gB1, mass=True, device=False):
+    """Adjoint of the solved step's field part (particles fixed): returns
+    {"E0", "B0", "J": (3, ncell), "M": (ncell, 5, 3, 3) or None, "iters",
+    "relres", "status"} for upstream gradients gE1, gB1 of E^{n+1}, B^{n+1}."""
+    p1, p2 = _ptr(gE1), _ptr(gB1)
+    dev = _where(p1, p2) == RELSIM_DEVICE
+    outs = {k: _out((3, ncell), np.float64, dev) for k in ("E0", "B0", "J")}
+    outs["M"] = _out((ncell, 5, 3, 3), np.float64, dev) if mass else None
+    ptrs = {k: _ptr(v, writable=True) for k, v in outs.items() if v is not None}
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    code = _check(ctx, lib().relsim_field_adjoint(
+        ctx, p1[0], p2[0], ptrs["E0"][0], ptrs["B0"][0], ptrs["J"][0], ptrs["M"][0] if mass else None,
+        ctypes.byref(it), ctypes.byref(rr), RELSIM_DEVICE if dev else RELSIM_HOST),
+        allow=(RELSIM_ERR_NOT_CONVERGED,))
+    outs.update(iters=it.value, relres=rr.value, status=code)
+    return outs
+
+
 def relsim_graph_info(ctx) -> dict:
     """{"graph_steps": steps run as a CUDA graph, "disabled": capture failed,
     "why": the failure}."""
@@ -551,6 +571,9 @@ class Simulation:
 
     def graph_info(self):
         return relsim_graph_info(self.ctx)
+
+    def field_adjoint(self, gE1, gB1, mass=True, device=False):
+        return relsim_field_adjoint(self.ctx, self.ncell, gE1, gB1, mass, device)
 
     def field_modes(self, component=1, nmodes=8, device=False):
         return relsim_field_modes(self.ctx, component, nmodes, device)

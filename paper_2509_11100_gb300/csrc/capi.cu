@@ -606,10 +606,10 @@ int solve_prologue(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond outer
 
 // one Arnoldi iteration with the arguments the device left in gms->dyn
 template <typename T>
-int arnoldi_body(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond inner)
+int arnoldi_body(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond inner, bool tr = false)
 {
     PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
-    CK(op_arnoldi_dyn<T>((const T*)c->M, &c->gms->dyn, c->V, S.ldv, c->g, c->partial, c->dpush, s));
+    CK(op_arnoldi_dyn<T>((const T*)c->M, &c->gms->dyn, c->V, S.ldv, c->g, c->partial, c->dpush, s, tr));
     PROF_END();
     PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
     CK(reduce_partials_dyn(c->partial, S.nbo, &c->gms->dyn, S.m + 2, s));
@@ -621,13 +621,13 @@ int arnoldi_body(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond inner)
 
 // x += V y of the finished cycle, the true residual, next cycle or stop
 template <typename T>
-int cycle_end(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond outer)
+int cycle_end(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond outer, bool tr = false)
 {
     PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
     CK(gm_finish_cycle(c->gms, c->gx, c->V, S.ldv, S.n, S.m, s));
     PROF_END();
     PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
-    CK(op_residual<T>((const T*)c->M, c->gx, c->gb, S.p.r, c->g, c->partial, c->dpush, s));
+    CK(op_residual<T>((const T*)c->M, c->gx, c->gb, S.p.r, c->g, c->partial, c->dpush, s, tr));
     CK(reduce_partials(c->partial, S.nbo, 1, c->dsum, s));
     CK(gm_cycle(c->gms, c->dsum, S.p, S.q, outer, s));
     PROF_END();
@@ -688,22 +688,21 @@ int head_async(relsim_ctx* c, int k)
 // The solve driven from the host: the same kernels as the graph, with the
 // host reading the device's decisions. Iteration j+1 is enqueued before
 // iteration j's decision is read (it returns at once if j was the last).
+// the restart and Arnoldi loops from the host, after a prologue enqueued
+// the first cycle start (tr: the operator is A^T)
 template <typename T>
-int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
+int gm_drive(relsim_ctx* c, const GmSetup& S, bool tr)
 {
-    const GmSetup S = gm_setup(c);
-    TRY(solve_reserve(c, S));
-    TRY(solve_prologue<T>(c, S, c->st, GmCond{0, 0}));
     TRY(head_async(c, 0));
     CK(cudaStreamSynchronize(c->st));
     TRY(check_push(c));
     while (c->ghead[0].run) {
         int cur = 0;
-        TRY(arnoldi_body<T>(c, S, c->st, GmCond{0, 0}));
+        TRY(arnoldi_body<T>(c, S, c->st, GmCond{0, 0}, tr));
         TRY(head_async(c, cur));
         CK(cudaEventRecord(c->gev[cur], c->st));
         for (int guard = 0; guard <= S.m; ++guard) {
-            TRY(arnoldi_body<T>(c, S, c->st, GmCond{0, 0}));
+            TRY(arnoldi_body<T>(c, S, c->st, GmCond{0, 0}, tr));
             TRY(head_async(c, 1 - cur));
             CK(cudaEventRecord(c->gev[1 - cur], c->st));
             CK(cudaEventSynchronize(c->gev[cur]));
@@ -711,11 +710,21 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
             if (!c->ghead[cur].inner) break;
             cur = 1 - cur;
         }
-        TRY(cycle_end<T>(c, S, c->st, GmCond{0, 0}));
+        TRY(cycle_end<T>(c, S, c->st, GmCond{0, 0}, tr));
         TRY(head_async(c, 0));
         CK(cudaStreamSynchronize(c->st));
         TRY(check_push(c));
     }
+    return RELSIM_OK;
+}
+
+template <typename T>
+int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
+{
+    const GmSetup S = gm_setup(c);
+    TRY(solve_reserve(c, S));
+    TRY(solve_prologue<T>(c, S, c->st, GmCond{0, 0}));
+    TRY(gm_drive<T>(c, S, false));
     const GmState h = c->ghead[0];
     if (h.status == kGmNonfinite) return solve_outcome(c, &h, iters_out, relres_out);
     TRY(solve_epilogue<T>(c, c->st));
@@ -987,6 +996,54 @@ int step_graph(relsim_ctx* c, relsim_energy* ledger, int* status)
         const int r = ledger_fill(c, hl, ledger);
         if (r != RELSIM_OK) *status = r;
     }
+    return RELSIM_OK;
+}
+
+// The adjoint of the field part of the solved step (particles held fixed):
+// A^T lambda = gE1/theta - dt curl_c^T gB1 by the same device-controlled
+// GMRES on the transposed operator, then the gradients of E^n, B^n, Jhat and
+// the stored mass-matrix blocks (see fields.cu).
+template <typename T>
+int adjoint_impl(relsim_ctx* c, const double* gE1, const double* gB1, double* gE0, double* gB0, double* gJ,
+                 double* gM, int* iters, double* relres, int where)
+{
+    const int64_t n = c->nvec, nm = (int64_t)c->g.ncell * kMBlock;
+    if (where == RELSIM_HOST) TRY(ensure_stage(c, 5 * n + nm));
+    const double *d1, *d2;
+    TRY(stage_in(c, gE1, n, where, &d1, 0));
+    TRY(stage_in(c, gB1, n, where, &d2, n));
+    const GmSetup S = gm_setup(c);
+    TRY(solve_reserve(c, S));
+    CK(adjoint_pre(d1, d2, c->gb, c->g, c->st));
+    CK(gm_dots(c->V, S.ldv, 0, c->gb, S.n, c->partial, S.nb, c->st));
+    CK(reduce_partials(c->partial, S.nb, 1, c->dsum, c->st));
+    CK(gm_begin(c->gms, c->dsum, c->st));
+    CK(cudaMemsetAsync(c->gx, 0, sizeof(double) * (size_t)n, c->st));
+    CK(op_residual<T>((const T*)c->M, c->gx, c->gb, S.p.r, c->g, c->partial, c->dpush, c->st, true));
+    CK(reduce_partials(c->partial, S.nbo, 1, c->dsum, c->st));
+    CK(gm_cycle(c->gms, c->dsum, S.p, S.q, GmCond{0, 0}, c->st));
+    TRY(gm_drive<T>(c, S, true));
+    const GmState h = c->ghead[0];
+    if (iters) *iters = h.total;
+    if (relres) *relres = h.relres;
+    if (h.status == kGmNonfinite) return fail(c, RELSIM_ERR_NONFINITE, "non-finite value in the adjoint solve");
+    const bool host = where == RELSIM_HOST;
+    double* oE = gE0 ? (host ? c->stage + 2 * n : gE0) : nullptr;
+    double* oB = gB0 ? (host ? c->stage + 3 * n : gB0) : nullptr;
+    double* oJ = gJ ? (host ? c->stage + 4 * n : gJ) : nullptr;
+    double* oM = gM ? (host ? c->stage + 5 * n : gM) : nullptr;
+    CK(adjoint_post(d1, d2, c->gx, oE, oB, oJ, c->g, c->st));
+    if (oM) CK(adjoint_mass<T>(c->gx, (const T*)c->Eth, oM, c->g, c->st));
+    if (host) {
+        if (gE0) CK(cudaMemcpyAsync(gE0, oE, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->st));
+        if (gB0) CK(cudaMemcpyAsync(gB0, oB, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->st));
+        if (gJ) CK(cudaMemcpyAsync(gJ, oJ, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->st));
+        if (gM) CK(cudaMemcpyAsync(gM, oM, sizeof(double) * (size_t)nm, cudaMemcpyDeviceToHost, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    if (h.status == kGmNotConverged)
+        return fail(c, RELSIM_ERR_NOT_CONVERGED, "adjoint GMRES reached %d iterations at relative residual %.3e",
+                    h.total, h.relres);
     return RELSIM_OK;
 }
 
@@ -1534,6 +1591,16 @@ int relsim_field_solve(relsim_ctx* c, int* iters, double* rel_residual)
     int r = DISPATCH(solve_impl, c, iters, rel_residual);
     if (r == RELSIM_OK || r == RELSIM_ERR_NOT_CONVERGED) c->state = kSolved;
     return r;
+}
+
+int relsim_field_adjoint(relsim_ctx* c, const double* gE1, const double* gB1, double* gE0, double* gB0,
+                         double* gJ, double* gM, int* iters, double* rel_residual, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (!gE1 || !gB1) return fail(c, RELSIM_ERR_INVALID_ARG, "null upstream gradient");
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    if (c->state != kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "the adjoint needs a solved step (before the push)");
+    return DISPATCH(adjoint_impl, c, gE1, gB1, gE0, gB0, gJ, gM, iters, rel_residual, where);
 }
 
 int relsim_get_E_theta(relsim_ctx* c, double* E, int where)

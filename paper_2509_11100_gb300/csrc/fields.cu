@@ -73,8 +73,8 @@ __device__ __forceinline__ T vld(const double* v, int64_t k) { return (T)__ldg(v
 // blocks: Mg = the node's own five blocks M[g][0..4], Mn[o] = the block
 // M[g-o][o+1] of the neighbour g - o for the half offsets o = (1,0), (-1,1),
 // (0,1), (1,1) (M_{g,g-o} = M_{g-o,g}).
-template <typename T, typename P>
-__device__ __forceinline__ void op_stencil(const T (&f)[3][3][3], P Mg, const P (&Mn)[4], T idx2, T idy2,
+template <typename T, typename P, bool TR>
+__device__ __forceinline__ void op_stencil_t(const T (&f)[3][3][3], P Mg, const P (&Mn)[4], T idx2, T idy2,
                                            T cc[3], T mv[3])
 {
     // curl_c at the four centres (i-1+ca+1/2, j-1+cb+1/2)
@@ -103,14 +103,16 @@ __device__ __forceinline__ void op_stencil(const T (&f)[3][3][3], P Mg, const P 
     cc[0] = dy[2];
     cc[1] = -dx[2];
     cc[2] = dx[1] - dy[0];
-    // M v: own blocks M[g][o] times v(g+o), neighbours' blocks M[g-o][o] times v(g-o)
+    // M v: own blocks M[g][o] times v(g+o), neighbours' blocks M[g-o][o] times v(g-o);
+    // with TR every 3x3 block is applied transposed (M^T v: the stored block
+    // of the pair (g, g') serves both orders, M_{g'g} = M_{gg'})
     constexpr int pa[4] = {2, 0, 1, 2}, pb[4] = {1, 2, 2, 2};   // g + o in the stencil
     constexpr int ma[4] = {0, 2, 1, 0}, mb[4] = {1, 0, 0, 0};   // g - o
     T r[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
-        for (int s = 0; s < 3; ++s) r[rr] += T(Mg[rr * 3 + s]) * f[s][1][1];
+        for (int s = 0; s < 3; ++s) r[rr] += T(Mg[TR ? s * 3 + rr : rr * 3 + s]) * f[s][1][1];
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         P Mo = Mg + (o + 1) * 9;
@@ -118,11 +120,19 @@ __device__ __forceinline__ void op_stencil(const T (&f)[3][3][3], P Mg, const P 
         for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
             for (int s = 0; s < 3; ++s)
-                r[rr] += T(Mo[rr * 3 + s]) * f[s][pa[o]][pb[o]] + T(Mn[o][rr * 3 + s]) * f[s][ma[o]][mb[o]];
+                r[rr] += T(Mo[TR ? s * 3 + rr : rr * 3 + s]) * f[s][pa[o]][pb[o]] +
+                         T(Mn[o][TR ? s * 3 + rr : rr * 3 + s]) * f[s][ma[o]][mb[o]];
     }
     mv[0] = r[0];
     mv[1] = r[1];
     mv[2] = r[2];
+}
+
+template <typename T, typename P>
+__device__ __forceinline__ void op_stencil(const T (&f)[3][3][3], P Mg, const P (&Mn)[4], T idx2, T idy2,
+                                           T cc[3], T mv[3])
+{
+    op_stencil_t<T, P, false>(f, Mg, Mn, idx2, idy2, cc, mv);
 }
 
 // the same at node (i,j) straight from global memory (v FP64, component-major)
@@ -192,7 +202,7 @@ static_assert(sizeof(double) * (OpTile<double>::Y + 1) * OpTile<double>::X * kMB
                   sizeof(double) * kOpChunk * OpTile<double>::threads,
               "the reduction buffer fits in the mass-matrix tile");
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool TR>
 __global__ void __launch_bounds__(OpTile<T>::threads, sizeof(T) == 4 ? 3 : 2)
 k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const double* __restrict__ b,
      double* __restrict__ out, double* __restrict__ vj, const double* __restrict__ V, int64_t ldv, int nv,
@@ -285,7 +295,7 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
         const T* Mn[4] = {blk(tx - 1, ty) + 9, blk(tx + 1, ty - 1) + 18, blk(tx, ty - 1) + 27,
                           blk(tx - 1, ty - 1) + 36};
         T cc[3], mv[3];
-        op_stencil<T, const T*>(f, blk(tx, ty), Mn, T(0.5 / g.dx), T(0.5 / g.dy), cc, mv);
+        op_stencil_t<T, const T*, TR>(f, blk(tx, ty), Mn, T(0.5 / g.dx), T(0.5 / g.dy), cc, mv);
         const T td = T(g.theta * g.dt);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -680,7 +690,7 @@ cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStre
     return cudaGetLastError();
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool TR = false>
 cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
                       const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st,
                       const GmDyn* dyn = nullptr)
@@ -693,29 +703,31 @@ cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, 
     if (e != cudaSuccess) return e;
     const unsigned bit = 1u << (dev & 31);
     if (!(attr_set.load() & bit)) {
-        e = cudaFuncSetAttribute(k_op<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(k_op<T, MODE, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(bit);
     }
     // bulk copies need every staged mass-matrix row to start on 16 bytes
     const int tma = ((int64_t)g.nx * kMBlock * sizeof(T)) % 16 == 0 ? 1 : 0;
     count_launches(1);
-    k_op<T, MODE><<<op_blocks(g, sizeof(T) == 4 ? 32 : 64), OpTile<T>::threads, smem, st>>>(
+    k_op<T, MODE, TR><<<op_blocks(g, sizeof(T) == 4 ? 32 : 64), OpTile<T>::threads, smem, st>>>(
         M, in, sc, b, out, vj, V, ldv, nv, g, tma, partial, err, dyn);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, int* err, cudaStream_t st)
+cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, int* err, cudaStream_t st, bool tr)
 {
-    return launch_op<T, kOpA>(M, v, 1.0, nullptr, out, nullptr, nullptr, 0, 0, g, nullptr, err, st);
+    return tr ? launch_op<T, kOpA, true>(M, v, 1.0, nullptr, out, nullptr, nullptr, 0, 0, g, nullptr, err, st)
+              : launch_op<T, kOpA>(M, v, 1.0, nullptr, out, nullptr, nullptr, 0, 0, g, nullptr, err, st);
 }
 
 template <typename T>
 cudaError_t op_residual(const T* M, const double* x, const double* b, double* r, GridP g, double* partial,
-                        int* err, cudaStream_t st)
+                        int* err, cudaStream_t st, bool tr)
 {
-    return launch_op<T, kOpResidual>(M, x, 1.0, b, r, nullptr, nullptr, 0, 0, g, partial, err, st);
+    return tr ? launch_op<T, kOpResidual, true>(M, x, 1.0, b, r, nullptr, nullptr, 0, 0, g, partial, err, st)
+              : launch_op<T, kOpResidual>(M, x, 1.0, b, r, nullptr, nullptr, 0, 0, g, partial, err, st);
 }
 
 template <typename T>
@@ -727,10 +739,12 @@ cudaError_t op_arnoldi(const T* M, const double* u, double sc, double* vj, doubl
 
 template <typename T>
 cudaError_t op_arnoldi_dyn(const T* M, const GmDyn* dyn, const double* V, int64_t ldv, GridP g, double* partial,
-                           int* err, cudaStream_t st)
+                           int* err, cudaStream_t st, bool tr)
 {
-    return launch_op<T, kOpArnoldi>(M, nullptr, 1.0, nullptr, nullptr, nullptr, V, ldv, 0, g, partial, err, st,
-                                    dyn);
+    return tr ? launch_op<T, kOpArnoldi, true>(M, nullptr, 1.0, nullptr, nullptr, nullptr, V, ldv, 0, g, partial,
+                                               err, st, dyn)
+              : launch_op<T, kOpArnoldi>(M, nullptr, 1.0, nullptr, nullptr, nullptr, V, ldv, 0, g, partial, err,
+                                         st, dyn);
 }
 
 template <typename T>
@@ -855,18 +869,160 @@ cudaError_t reduce_partials_dyn(const double* partial, int nblocks, const GmDyn*
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the field part of a step (particles held fixed). The forward map
+//   b = E0 + theta dt curl_n B0 - theta dt J,   A E_theta = b,
+//   E1 = (E_theta - (1 - theta) E0)/theta,     B1 = B0 - dt curl_c E_theta
+// is linear in (E0, B0, J); with upstream gradients (gE1, gB1):
+//   gE_theta = gE1/theta - dt curl_c^T gB1,    A^T lambda = gE_theta,
+//   gE0 = lambda - (1 - theta)/theta gE1,      gB0 = gB1 + theta dt curl_n^T lambda,
+//   gJ = -theta dt lambda,  and for the stored block of the node pair (g, g+o)
+//   gM = -theta dt (lambda_g E_theta,{g+o}^T + [o != 0] lambda_{g+o} E_theta,g^T).
+// On the periodic grid curl_c^T = curl_n exactly, so the transposed curls
+// are the curls themselves. FP64 throughout.
+
+// curl_c at centre (i, j) = (i+1/2, j+1/2) from the FP64 node field v
+__device__ __forceinline__ void curl_c_at(const double* __restrict__ v, int i, int j, const GridP& g, double out[3])
+{
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+    const int64_t n00 = (int64_t)j * nx + i, n10 = (int64_t)j * nx + i1, n01 = (int64_t)j1 * nx + i,
+                  n11 = (int64_t)j1 * nx + i1;
+    double dx[3], dy[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double* f = v + (int64_t)k * nc;
+        dx[k] = (f[n10] - f[n00] + f[n11] - f[n01]) * (0.5 / g.dx);
+        dy[k] = (f[n01] - f[n00] + f[n11] - f[n10]) * (0.5 / g.dy);
+    }
+    out[0] = dy[2];
+    out[1] = -dx[2];
+    out[2] = dx[1] - dy[0];
+}
+
+// curl_n at node (i, j) from the FP64 centre field v (centres i-1, i and j-1, j)
+__device__ __forceinline__ void curl_n_at(const double* __restrict__ v, int i, int j, const GridP& g, double out[3])
+{
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int im = wrap1(i - 1, nx), jm = wrap1(j - 1, ny);
+    const int64_t c11 = (int64_t)j * nx + i, c01 = (int64_t)j * nx + im, c10 = (int64_t)jm * nx + i,
+                  c00 = (int64_t)jm * nx + im;
+    double dx[3], dy[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double* f = v + (int64_t)k * nc;
+        dx[k] = (f[c11] - f[c01] + f[c10] - f[c00]) * (0.5 / g.dx);
+        dy[k] = (f[c11] - f[c10] + f[c01] - f[c00]) * (0.5 / g.dy);
+    }
+    out[0] = dy[2];
+    out[1] = -dx[2];
+    out[2] = dx[1] - dy[0];
+}
+
+__global__ void k_adj_pre(const double* __restrict__ gE1, const double* __restrict__ gB1, double* __restrict__ gEt,
+                          GridP g)
+{
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.ncell; n += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(n % g.nx), j = (int)(n / g.nx);
+        double cn[3];
+        curl_n_at(gB1, i, j, g, cn);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gEt[k * g.ncell + n] = gE1[k * g.ncell + n] / g.theta - g.dt * cn[k];
+    }
+}
+
+__global__ void k_adj_post(const double* __restrict__ gE1, const double* __restrict__ gB1,
+                           const double* __restrict__ lam, double* __restrict__ gE0, double* __restrict__ gB0,
+                           double* __restrict__ gJ, GridP g)
+{
+    const double td = g.theta * g.dt, e1 = (1.0 - g.theta) / g.theta;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.ncell; n += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(n % g.nx), j = (int)(n / g.nx);
+        double cc[3];
+        curl_c_at(lam, i, j, g, cc);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int64_t q = k * g.ncell + n;
+            if (gE0) gE0[q] = lam[q] - e1 * gE1[q];
+            if (gB0) gB0[q] = gB1[q] + td * cc[k];
+            if (gJ) gJ[q] = -td * lam[q];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_adj_mass(const double* __restrict__ lam, const T* __restrict__ Et, double* __restrict__ gM,
+                           GridP g)
+{
+    constexpr int hdi[5] = {0, 1, -1, 0, 1}, hdj[5] = {0, 0, 1, 1, 1};
+    const double td = g.theta * g.dt;
+    const int nc = g.ncell;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nc; n += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(n % g.nx), j = (int)(n / g.nx);
+        double lg[3], eg[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lg[k] = lam[k * nc + n];
+            eg[k] = (double)Et[k * nc + n];
+        }
+#pragma unroll
+        for (int o = 0; o < 5; ++o) {
+            const int64_t h = (int64_t)wrap1(j + hdj[o], g.ny) * g.nx + wrap1(i + hdi[o], g.nx);
+            double lh[3], eh[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                lh[k] = lam[k * nc + h];
+                eh[k] = (double)Et[k * nc + h];
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double v = lg[r] * eh[c];
+                    if (o) v += lh[r] * eg[c];
+                    gM[n * kMBlock + o * 9 + r * 3 + c] = -td * v;
+                }
+        }
+    }
+}
+
+cudaError_t adjoint_pre(const double* gE1, const double* gB1, double* gEt, GridP g, cudaStream_t st)
+{
+    count_launches(1);
+    k_adj_pre<<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, gEt, g);
+    return cudaGetLastError();
+}
+
+cudaError_t adjoint_post(const double* gE1, const double* gB1, const double* lam, double* gE0, double* gB0,
+                         double* gJ, GridP g, cudaStream_t st)
+{
+    count_launches(1);
+    k_adj_post<<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, lam, gE0, gB0, gJ, g);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t adjoint_mass(const double* lam, const T* Et, double* gM, GridP g, cudaStream_t st)
+{
+    count_launches(1);
+    k_adj_mass<T><<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(lam, Et, gM, g);
+    return cudaGetLastError();
+}
+template cudaError_t adjoint_mass<float>(const double*, const float*, double*, GridP, cudaStream_t);
+template cudaError_t adjoint_mass<double>(const double*, const double*, double*, GridP, cudaStream_t);
+
 #define RELSIM_FIELDS_INSTANTIATE(T)                                                               \
     template cudaError_t fields_from_double<T>(const double*, T*, int64_t, int*, cudaStream_t);   \
     template cudaError_t fields_to_double<T>(const T*, double*, int64_t, cudaStream_t);           \
     template cudaError_t rhs<T>(const T*, const T*, const T*, double*, GridP, cudaStream_t);      \
-    template cudaError_t apply_A<T>(const T*, const double*, double*, GridP, int*, cudaStream_t); \
+    template cudaError_t apply_A<T>(const T*, const double*, double*, GridP, int*, cudaStream_t, bool); \
     template cudaError_t op_residual<T>(const T*, const double*, const double*, double*, GridP,    \
-                                        double*, int*, cudaStream_t);                             \
+                                        double*, int*, cudaStream_t, bool);                       \
     template cudaError_t op_arnoldi<T>(const T*, const double*, double, double*, double*,         \
                                        const double*, int64_t, int, GridP, double*, int*,          \
                                        cudaStream_t);                                             \
     template cudaError_t op_arnoldi_dyn<T>(const T*, const GmDyn*, const double*, int64_t, GridP, \
-                                           double*, int*, cudaStream_t);                          \
+                                           double*, int*, cudaStream_t, bool);                    \
     template cudaError_t field_update<T>(const double*, const T*, const T*, T*, T*, const T*, T*, \
                                          GridP, double*, int, cudaStream_t);                      \
     template cudaError_t field_energy<T>(const T*, const T*, GridP, double*, int, cudaStream_t);  \

@@ -120,11 +120,12 @@ cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStre
 // on shared-memory tiles; err gets bit 2 if a staging wait gave up.
 // out = A v:
 template <typename T>
-cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, int* err, cudaStream_t st);
+cudaError_t apply_A(const T* M, const double* v, double* out, GridP g, int* err, cudaStream_t st,
+                    bool tr = false);   // tr: A^T (every mass-matrix block transposed)
 // r = b - A x and per-tile partials of |r|^2 (op_blocks(g) of them):
 template <typename T>
 cudaError_t op_residual(const T* M, const double* x, const double* b, double* r, GridP g, double* partial,
-                        int* err, cudaStream_t st);
+                        int* err, cudaStream_t st, bool tr = false);
 // one Arnoldi step on B: v_j = sc u is written to vj (if not null), w = B v_j,
 // and per tile the j+2 partials <w, V_q> (q < j), <w, v_j>, <w, w> (row
 // stride j+2):
@@ -164,6 +165,15 @@ cudaError_t gm_combine_dev(double* x, const double* V, int64_t ldv, const int* k
 cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, double* out,
                             cudaStream_t st);
 int gm_blocks(int64_t n);
+
+// adjoint of the field part of a step (FP64): gEt = gE1/theta - dt curl_n gB1;
+// after A^T lambda = gEt: gE0, gB0, gJ (each may be null) and the gradient of
+// the stored mass-matrix blocks (ncell x 45)
+cudaError_t adjoint_pre(const double* gE1, const double* gB1, double* gEt, GridP g, cudaStream_t st);
+cudaError_t adjoint_post(const double* gE1, const double* gB1, const double* lam, double* gE0, double* gB0,
+                         double* gJ, GridP g, cudaStream_t st);
+template <typename T>
+cudaError_t adjoint_mass(const double* lam, const T* Et, double* gM, GridP g, cudaStream_t st);
 
 // ----- device-side GMRES control (gmres.cu) -----
 // Launch arguments of the next Arnoldi iteration, written by the device (the
@@ -225,7 +235,7 @@ cudaError_t gm_finish_cycle(GmState* st, double* x, const double* V, int64_t ldv
 // Arnoldi iteration kernels reading their arguments from dyn
 template <typename T>
 cudaError_t op_arnoldi_dyn(const T* M, const GmDyn* dyn, const double* V, int64_t ldv, GridP g,
-                           double* partial, int* err, cudaStream_t st);
+                           double* partial, int* err, cudaStream_t st, bool tr = false);
 cudaError_t reduce_partials_dyn(const double* partial, int nblocks, const GmDyn* dyn, int maxsums,
                                 cudaStream_t st);
 cudaError_t gm_update_scale_dyn(const GmDyn* dyn, const double* V, int64_t ldv, int64_t n, cudaStream_t st);

@@ -1,0 +1,119 @@
+"""The adjoint of the field part of a step on the GPU against the oracle's.
+
+Both sides use the GPU's mass matrix and E^{n+theta} (read back after the
+forward solve), so they differ only in the adjoint solve: the GPU's
+transposed operator applied in the form's precision with GMRES to the
+context's tolerance, the oracle's dense solve in FP64. Tolerances relative
+to the largest entry: FP64 form 1e-9 (GMRES tolerance 1e-12), FP32 form 2e-5
+(an FP32 operator application carries ~1e-7 relative error, GMRES stops at
+1e-7).
+"""
+import numpy as np
+import pytest
+
+from relsim_inputs import random_state
+
+pytestmark = pytest.mark.gpu
+
+HALF = ((0, 0), (1, 0), (-1, 1), (0, 1), (1, 1))
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_11100_gb300 as rs
+    return rs
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.load()
+    return oracle
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def full_from_half(Mh, nx, ny):
+    nn = nx * ny
+    full = np.zeros((nn, 9, 3, 3))
+    idx = np.arange(nn)
+    i, j = idx % nx, idx // nx
+    for k, (di, dj) in enumerate(HALF):
+        full[:, (dj + 1) * 3 + di + 1] = Mh[:, k]
+        if k:
+            nb = ((j + dj) % ny) * nx + (i + di) % nx
+            full[nb, (-dj + 1) * 3 - di + 1] = Mh[:, k]
+    return full
+
+
+def half_grad_from_full(G, nx, ny):
+    # a stored block serves the pairs (g, g+o) and (g+o, g)
+    nn = nx * ny
+    out = np.zeros((nn, 5, 3, 3))
+    idx = np.arange(nn)
+    i, j = idx % nx, idx // nx
+    for k, (di, dj) in enumerate(HALF):
+        out[:, k] = G[:, (dj + 1) * 3 + di + 1]
+        if k:
+            nb = ((j + dj) % ny) * nx + (i + di) % nx
+            out[:, k] += G[nb, (-dj + 1) * 3 - di + 1]
+    return out
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("nx,ny,theta", [(13, 7, 0.5), (24, 16, 0.6)])
+def test_field_adjoint_matches_oracle(rs, orc, prec, nx, ny, theta):
+    dt = 0.7
+    st = random_state(nx, ny, [20 * nx * ny, 20 * nx * ny], seed=41, u_scale=1.0, field_scale=0.6)
+    cfg = rs.make_config(nx, ny, dt=dt, theta_implicit=theta, precision=prec,
+                         gmres_tol=1e-12 if prec == 64 else 1e-7, gmres_restart=60)
+    sim = rs.Simulation(cfg)
+    sim.load_state(st)
+    sim.build()
+    Mh, _ = sim.mass_matrix()
+    sim.solve()
+    Et = sim.E_theta()
+    rng = np.random.default_rng(5)
+    gE1, gB1 = rng.normal(size=(3, nx * ny)), rng.normal(size=(3, nx * ny))
+    g = sim.field_adjoint(gE1, gB1)
+    assert g["status"] == 0 and g["iters"] > 0
+    c = orc.make_config(nx, ny, dt=dt, theta=theta)
+    o = orc.field_adjoint(c, full_from_half(np.asarray(Mh).reshape(nx * ny, 5, 3, 3), nx, ny), Et, gE1, gB1)
+    t = 1e-9 if prec == 64 else 2e-5
+    for k in ("E0", "B0", "J"):
+        assert rel(g[k], o[k]) < t, (k, rel(g[k], o[k]))
+    assert rel(g["M"], half_grad_from_full(o["M"], nx, ny)) < t
+    # the adjoint leaves the forward step intact: the push still runs
+    sim.push()
+    sim.close()
+
+
+def test_field_adjoint_device_arrays_and_call_order(rs):
+    import torch
+    nx, ny = 16, 8
+    st = random_state(nx, ny, [500, 500], seed=42)
+    sim = rs.Simulation(rs.make_config(nx, ny, precision=64, gmres_tol=1e-12))
+    sim.load_state(st)
+    g1 = torch.randn(3, nx * ny, dtype=torch.float64, device="cuda")
+    g2 = torch.randn(3, nx * ny, dtype=torch.float64, device="cuda")
+    with pytest.raises(rs.RelsimError) as e:
+        sim.field_adjoint(g1, g2)   # no solved step yet
+    assert e.value.code == rs.RELSIM_ERR_BAD_STATE
+    sim.build()
+    sim.solve()
+    gd = sim.field_adjoint(g1, g2, mass=False)
+    gh = sim.field_adjoint(g1.cpu().numpy(), g2.cpu().numpy(), mass=False)
+    assert gd["E0"].is_cuda and gd["M"] is None
+    for k in ("E0", "B0", "J"):
+        assert rel(gd[k].cpu().numpy(), gh[k]) < 1e-13
+    sim.push()
+    with pytest.raises(rs.RelsimError):
+        sim.field_adjoint(g1, g2)   # after the push
+    sim.close()

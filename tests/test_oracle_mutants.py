@@ -67,6 +67,9 @@ PY_MUTANTS = {
     "modes_wrong_axis": ("F = np.fft.rfft(Bc, axis=1)", "F = np.fft.rfft(Bc.T, axis=1)"),
     "growth_fit_no_log": ("np.polyfit(t, np.log(seg), 1)[0]", "np.polyfit(t, seg, 1)[0]"),
     "growth_fit_smallest": ("if best is None or slope > best[0]:", "if best is None or slope < best[0]:"),
+    "adjoint_untransposed": ("lam = np.linalg.solve(A.T, gEt)", "lam = np.linalg.solve(A, gEt)"),
+    "adjoint_drops_E_extrapolation": ("gE0 = lam - (1.0 - th) / th * gE1", "gE0 = lam"),
+    "adjoint_mass_pair_swapped": ("np.outer(L3[:, g], Et[:, h])", "np.outer(L3[:, h], Et[:, g])"),
 }
 CASES = {**{k: ("relsim_oracle.c",) + v for k, v in MUTANTS.items()},
          **{k: ("__init__.py",) + v for k, v in PY_MUTANTS.items()}}

@@ -735,3 +735,59 @@ def test_predicted_gamma_reduces_the_relativistic_energy_error(orc):
             mis.append(abs(led["mismatch"]) / (led["W_E1"] + led["W_B1"] + led["K1"]))
         mean.append(np.mean(mis[5:]))
     assert mean[1] < mean[0] / 10, mean
+
+
+# ---------------------------------------------------------------------------
+# adjoint of the field part of a step (particles held fixed)
+
+def _field_forward(orc, c, M, E0, B0, J):
+    b = orc.rhs(c, E0, B0, J)
+    Et, st, it, rr = orc.gmres(c, M, b, np.zeros_like(b))
+    E1, B1 = orc.field_update(c, Et, E0, B0)
+    return E1, B1, Et
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.7])
+def test_field_adjoint_matches_directional_derivatives(orc, theta):
+    # L = <cE, E1> + <cB, B1> through the oracle's forward field step: linear
+    # in (E0, B0, J), so L(x + d) - L(x) = <grad, d> up to the solve
+    # tolerance; in M, a central difference of a perturbation of every block
+    nx, ny = 6, 5
+    c = cfg_for(orc, nx, ny, dt=0.6, theta=theta, gmres_tol=1e-14, gmres_restart=200)
+    st = random_state(nx, ny, [60, 50], seed=31, u_scale=1.0, field_scale=0.8)
+    J, M = orc.deposit(c, orc.Particles(st["species"]), st["B"])
+    E0, B0 = st["E"], st["B"]
+    rng = np.random.default_rng(8)
+    cE, cB = rng.normal(size=E0.shape), rng.normal(size=B0.shape)
+    L = lambda E1, B1: float(np.sum(cE * E1) + np.sum(cB * B1))
+    E1, B1, Et = _field_forward(orc, c, M, E0, B0, J)
+    L0 = L(E1, B1)
+    g = orc.field_adjoint(c, M, Et, cE, cB)
+    for name, base in (("E0", E0), ("B0", B0), ("J", J)):
+        d = rng.normal(size=base.shape)
+        args = {"E0": E0, "B0": B0, "J": J}
+        args[name] = base + d
+        E1d, B1d, _ = _field_forward(orc, c, M, args["E0"], args["B0"], args["J"])
+        assert abs((L(E1d, B1d) - L0) - np.sum(g[name] * d)) < 1e-10 * max(1.0, abs(L0)), name
+    D = rng.normal(size=M.shape) * 1e-3
+    h = 1e-4
+    Ep, Bp, _ = _field_forward(orc, c, M + h * D, E0, B0, J)
+    Em, Bm, _ = _field_forward(orc, c, M - h * D, E0, B0, J)
+    fd = (L(Ep, Bp) - L(Em, Bm)) / (2 * h)
+    assert abs(fd - np.sum(g["M"] * D)) < 1e-7 * max(1e-3, abs(fd))
+
+
+def test_field_adjoint_lambda_solves_the_transposed_system(orc):
+    # <A x, y> = <x, A^T y>: lambda from the adjoint satisfies
+    # <lambda, A v> = <gEt, v> for any v
+    nx, ny = 5, 4
+    c = cfg_for(orc, nx, ny, dt=0.5, theta=0.5, gmres_tol=1e-14)
+    st = random_state(nx, ny, [40, 40], seed=32, u_scale=1.5, field_scale=1.0)
+    J, M = orc.deposit(c, orc.Particles(st["species"]), st["B"])
+    rng = np.random.default_rng(9)
+    gE1, gB1 = rng.normal(size=(3, nx * ny)), rng.normal(size=(3, nx * ny))
+    g = orc.field_adjoint(c, M, st["E"], gE1, gB1)
+    gEt = gE1 / c.theta - c.dt * orc.curl_n(c, gB1)   # curl_c^T = curl_n on the periodic grid
+    for _ in range(3):
+        v = rng.normal(size=(3, nx * ny))
+        assert abs(np.sum(g["lambda"] * orc.apply_A(c, M, v)) - np.sum(gEt * v)) < 1e-11 * np.abs(gEt).sum()
