@@ -552,7 +552,7 @@ template <typename T> struct PushCfg {
     static constexpr int warps = 4;                        // static shared memory < 48 KB
     static constexpr int threads = 32 * warps;
     static constexpr int min_blocks = sizeof(T) == 4 ? 5 : 2;
-    static constexpr int cap = sizeof(T) == 4 ? 192 : 128;   // particles of a cell group staged per warp
+    static constexpr int cap = sizeof(T) == 4 ? 256 : 128;   // particles of a cell group staged per warp
 };
 constexpr int kGroupMax = 8;    // cells staged together at most
 constexpr int kLedger = 4;      // dK, work, mismatch, K1 (K0 is the previous K1)
