@@ -210,6 +210,7 @@ def run_ours(args):
                          gmres_tol=WORKLOAD["gmres_tol"], gmres_restart=WORKLOAD["gmres_restart"])
     sim = rs.Simulation(cfg)
     sim.load_state(state)
+    tuning = sim.autotune() if not args.no_autotune else None
     for _ in range(args.warmup):
         sim.step(ledger=True)
     torch.cuda.synchronize()
@@ -300,6 +301,7 @@ def run_ours(args):
         "kernel_ms_per_step": step_kernel_ms,
         "step_graph": {"graph_steps": graph["graph_steps"], "disabled": graph["disabled"],
                        "why": graph["why"] or None},
+        "autotune": tuning,
         "gpu_launches": int(launches),
         "gmres_iters_per_step": statistics.mean(iters),
         "ledger": {"residual_rel": abs(last["residual"]) / last["total"],
@@ -513,6 +515,8 @@ def run_scan(args):
                             stream=stream.cuda_stream)
         sim.load_state(st)
         del st
+        if not args.no_autotune:
+            sim.autotune()
         streams.append(stream)
         sims.append(sim)
     torch.cuda.synchronize()
@@ -644,6 +648,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (no autotuner pass after the load)")
     ap.add_argument("--workload", choices=["c1", "small", "scan"], default="c1",
                     help="small: 512x256 cells for profiler captures; scan: the 48-instance batched "
                          "tearing scan (run with --steps 400 for its full length)")

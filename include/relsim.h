@@ -347,6 +347,27 @@ RELSIM_API int relsim_batch_run(relsim_batch* b, int nsteps, int component, int 
 /* Free the batch (not its contexts). NULL is a no-op. */
 RELSIM_API void relsim_batch_destroy(relsim_batch* b);
 
+/* ---- launch-shape autotuner ----
+   Times candidate launch shapes of the two heaviest particle kernels on the
+   loaded state and keeps the fastest for this context: the deposit's block
+   count (it strides over row units of 32 cells: 1, 2, 3, 4 blocks per SM)
+   and the push's grid (at most 4, 8, 16, 32 blocks of four unit warps per
+   SM). Each candidate runs once untimed and three times timed (CUDA events;
+   the least counts). Call it on a loaded state before a build (the trials
+   overwrite only what the next step recomputes); later steps use the
+   choice (captured step graphs are recaptured). out (may be NULL) receives
+   the candidates, their times and the choice. Synchronises the stream.
+   Errors: INVALID_ARG, BAD_STATE, OOM, CUDA. */
+typedef struct {
+    int ncand;
+    int deposit_blocks[8];
+    float deposit_ms[8];
+    int push_blocks[8];
+    float push_ms[8];
+    int deposit_choice, push_choice;   /* indices into the candidates */
+} relsim_tuning;
+RELSIM_API int relsim_autotune(relsim_ctx* ctx, relsim_tuning* out);
+
 /* Library version (major*10000 + minor*100 + patch). */
 RELSIM_API int relsim_version(void);
 

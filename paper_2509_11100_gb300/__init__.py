@@ -29,7 +29,8 @@ __all__ = [
     "relsim_kinetic_energy_noalloc", "relsim_energy_spectrum", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
     "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
-    "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint",
+    "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
+    "relsim_tuning",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -128,10 +129,25 @@ _SIGS = {
     "relsim_batch_destroy": (None, [_P]),
     "relsim_graph_info": (ctypes.c_int, [_CTX, _P, _P, _P]),
     "relsim_field_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
+    "relsim_autotune": (ctypes.c_int, [_CTX, _P]),
 }
 
 PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
                  "gmres_ortho", "field_update", "rhs", "load", "general_sort")
+
+
+class relsim_tuning(ctypes.Structure):
+    _fields_ = [("ncand", ctypes.c_int), ("deposit_blocks", ctypes.c_int * 8),
+                ("deposit_ms", ctypes.c_float * 8), ("push_blocks", ctypes.c_int * 8),
+                ("push_ms", ctypes.c_float * 8), ("deposit_choice", ctypes.c_int),
+                ("push_choice", ctypes.c_int)]
+
+    def asdict(self) -> dict:
+        n = self.ncand
+        return {"deposit": [(self.deposit_blocks[k], self.deposit_ms[k]) for k in range(n)],
+                "push": [(self.push_blocks[k], self.push_ms[k]) for k in range(n)],
+                "deposit_blocks": self.deposit_blocks[self.deposit_choice],
+                "push_blocks": self.push_blocks[self.push_choice]}
 
 
 class relsim_profile(ctypes.Structure):
@@ -411,6 +427,14 @@ def relsim_field_adjoint(ctx, ncell, gE1, gB1, mass=True, device=False):
     return outs
 
 
+def relsim_autotune(ctx) -> dict:
+    """Time candidate launch shapes of the deposit and the push on the loaded
+    state and keep the fastest; returns the candidates and the choice."""
+    t = relsim_tuning()
+    _check(ctx, lib().relsim_autotune(ctx, ctypes.byref(t)))
+    return t.asdict()
+
+
 def relsim_graph_info(ctx) -> dict:
     """{"graph_steps": steps run as a CUDA graph, "disabled": capture failed,
     "why": the failure}."""
@@ -571,6 +595,9 @@ class Simulation:
 
     def graph_info(self):
         return relsim_graph_info(self.ctx)
+
+    def autotune(self):
+        return relsim_autotune(self.ctx)
 
     def field_adjoint(self, gE1, gB1, mass=True, device=False):
         return relsim_field_adjoint(self.ctx, self.ncell, gE1, gB1, mass, device)

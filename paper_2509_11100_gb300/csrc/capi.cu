@@ -126,6 +126,8 @@ struct relsim_ctx {
     uint64_t gen = 1;          // bumped whenever a buffer or the loaded state changes
     bool graph_off = false;    // a capture failed: host-driven steps from then on
     std::string graph_why;     // why
+    int dep_blocks = 0;        // launch shapes chosen by relsim_autotune (0: defaults)
+    int push_cap = 0;
     int64_t graph_steps = 0;   // steps run as a graph
     bool capturing = false;
     cudaStream_t gst = nullptr;        // graph stream, joined to st by events
@@ -510,12 +512,26 @@ int get_particles_impl(relsim_ctx* c, int s, double* x, double* u, double* w, in
 }
 
 template <typename T>
+DepositSpecies<T> deposit_args(relsim_ctx* c);
+
+template <typename T>
 int build_impl(relsim_ctx* c)
 {
     const int nc = c->g.ncell;
     PROF_BEGIN(RELSIM_PROF_DEPOSIT);
     CK(cudaMemsetAsync(c->M, 0, c->esz * (size_t)nc * kMBlock, c->st));
     CK(cudaMemsetAsync(c->J, 0, c->esz * 3 * (size_t)nc, c->st));
+    const DepositSpecies<T> ds = deposit_args<T>(c);
+    CK(deposit<T>(ds, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J, c->g,
+                  c->dpush, c->st, c->dep_blocks));
+    PROF_END();
+    return RELSIM_OK;
+}
+
+// the deposit's view of the current particles
+template <typename T>
+DepositSpecies<T> deposit_args(relsim_ctx* c)
+{
     DepositSpecies<T> ds;
     memset(&ds, 0, sizeof(ds));
     ds.nsp = c->cfg.nspecies;
@@ -534,9 +550,91 @@ int build_impl(relsim_ctx* c)
         ds.cJ[s] = (T)(c->cfg.q[s] / c->g.dV);
         ds.cM[s] = (T)(c->cfg.q[s] * beta / c->g.dV);
     }
-    CK(deposit<T>(ds, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J, c->g,
-                  c->dpush, c->st));
-    PROF_END();
+    return ds;
+}
+
+// Launch shapes timed on the loaded state: the deposit's block count (it
+// strides over the row units) and the push's grid cap (warps per unit). Each
+// candidate runs once untimed and three times timed with CUDA events; the
+// fastest (least of the three) is kept. The trials overwrite only what the
+// next step recomputes (M, Jhat, the other particle buffer, the run tables,
+// the partial sums); the push trials take E^n as their field (any finite
+// field times the same work).
+template <typename T>
+int autotune_impl(relsim_ctx* c, relsim_tuning* out)
+{
+    int dev = 0, nsm = 152;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int ncand = 4;
+    const int dep_c[ncand] = {nsm, 2 * nsm, 3 * nsm, 4 * nsm};
+    const int push_c[ncand] = {4 * nsm, 8 * nsm, 16 * nsm, 32 * nsm};
+    TRY(ensure_partial(c, (int64_t)push_grid_blocks(c->g, c->prec, push_c[ncand - 1]) * (kLedgerSpecies - 1)));
+    relsim_tuning t;
+    memset(&t, 0, sizeof(t));
+    t.ncand = ncand;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int r = RELSIM_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(c, RELSIM_ERR_CUDA, "event creation failed");
+    }
+    const DepositSpecies<T> ds = deposit_args<T>(c);
+    int big = 0;   // the push is timed on the species with the most particles
+    for (int s = 1; s < c->cfg.nspecies; ++s)
+        if (c->sp[s].n > c->sp[big].n) big = s;
+    Species& sp = c->sp[big];
+    const SpeciesConst sc{c->cfg.q[big], c->cfg.m[big]};
+    auto timed = [&](auto launch, float* best) -> int {
+        *best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            CK(cudaEventRecord(e0, c->st));
+            TRY(launch());
+            CK(cudaEventRecord(e1, c->st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0 && ms < *best) *best = ms;
+        }
+        return RELSIM_OK;
+    };
+    for (int k = 0; k < ncand && r == RELSIM_OK; ++k) {
+        t.deposit_blocks[k] = dep_c[k];
+        r = timed(
+            [&]() -> int {
+                CK(deposit<T>(ds, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J,
+                              c->g, c->dpush, c->st, dep_c[k]));
+                return RELSIM_OK;
+            },
+            &t.deposit_ms[k]);
+    }
+    for (int k = 0; k < ncand && r == RELSIM_OK && sp.n > 0; ++k) {
+        const int nbp = push_grid_blocks(c->g, c->prec, push_c[k]);
+        t.push_blocks[k] = nbp;
+        r = timed(
+            [&]() -> int {
+                CK(push_sort<T>(arrays<T>(sp, sp.cur), arrays<T>(sp, 1 - sp.cur), sp.start, c->n9, c->off9,
+                                (const T*)c->E, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, c->g,
+                                sc, c->partial, nbp, c->st));
+                return RELSIM_OK;
+            },
+            &t.push_ms[k]);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != RELSIM_OK) return r;
+    int bd = 0, bp = 0;
+    for (int k = 1; k < ncand; ++k) {
+        if (t.deposit_ms[k] < t.deposit_ms[bd]) bd = k;
+        if (t.push_ms[k] < t.push_ms[bp]) bp = k;
+    }
+    t.deposit_choice = bd;
+    t.push_choice = bp;
+    c->dep_blocks = dep_c[bd];
+    c->push_cap = push_c[bp];
+    ++c->gen;   // step graphs hold the old launch shapes
+    TRY(check_push(c));
+    if (out) *out = t;
     return RELSIM_OK;
 }
 
@@ -749,7 +847,7 @@ void push_commit(relsim_ctx* c)
 template <typename T>
 int push_enqueue(relsim_ctx* c)
 {
-    const int nbp = push_grid_blocks(c->g, c->prec);
+    const int nbp = push_grid_blocks(c->g, c->prec, c->push_cap);
     TRY(ensure_partial(c, (int64_t)nbp * (kLedgerSpecies - 1)));
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         Species& sp = c->sp[s];
@@ -904,7 +1002,7 @@ int capture_step(relsim_ctx* c, StepGraph& G)
 {
     const GmSetup S = gm_setup(c);
     TRY(solve_reserve(c, S));
-    TRY(ensure_partial(c, (int64_t)push_grid_blocks(c->g, c->prec) * (kLedgerSpecies - 1)));
+    TRY(ensure_partial(c, (int64_t)push_grid_blocks(c->g, c->prec, c->push_cap) * (kLedgerSpecies - 1)));
     if (G.exec) {
         cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;
@@ -1591,6 +1689,13 @@ int relsim_field_solve(relsim_ctx* c, int* iters, double* rel_residual)
     int r = DISPATCH(solve_impl, c, iters, rel_residual);
     if (r == RELSIM_OK || r == RELSIM_ERR_NOT_CONVERGED) c->state = kSolved;
     return r;
+}
+
+int relsim_autotune(relsim_ctx* c, relsim_tuning* out)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (c->state != kReady) return fail(c, RELSIM_ERR_BAD_STATE, "autotune needs a loaded state before a build");
+    return DISPATCH(autotune_impl, c, out);
 }
 
 int relsim_field_adjoint(relsim_ctx* c, const double* gE1, const double* gB1, double* gE0, double* gB0,

@@ -78,7 +78,8 @@ cudaError_t export_particles(PArrays<T> p, const int32_t* start, GridP g, double
                              double* w, int32_t* id, cudaStream_t st);
 template <typename T>
 cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, const T* En, T* M, T* J, GridP g, int* err,
-                    cudaStream_t st);   // En = E^n for the predicted-gamma variant, else null
+                    cudaStream_t st, int max_blocks = 0);   // En = E^n for the predicted-gamma variant, else
+                                                            // null; max_blocks 0: two per SM
 // push with the cell-local sort: each old cell's pushed particles are written
 // back over the cell's own index range in dst grouped by move direction d;
 // n9[c][d] and off9[c][d] receive the count and the start of each run; the
@@ -98,7 +99,7 @@ cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, i
 template <typename T>
 cudaError_t permute(PArrays<T> src, PArrays<T> dst, const int32_t* start_new, const int32_t* n9,
                     const int32_t* off9, GridP g, int* err, cudaStream_t st);
-int push_grid_blocks(GridP g, int precision);
+int push_grid_blocks(GridP g, int precision, int cap = 0);   // cap: most blocks (0: 152 x 16)
 // weighted and counted histogram of gamma - 1 (variable 0) or |u| (1) over
 // nbins bins between ascending edges (nbins + 1, rounded up to T), plus the
 // bins below and above them: wsum/cnt[nbins + 2], accumulated (zero them)

@@ -1156,10 +1156,10 @@ int blocks_for(int64_t n, int threads, int cap)
 
 }  // namespace
 
-int push_grid_blocks(GridP g, int precision)
+int push_grid_blocks(GridP g, int precision, int cap)
 {
     return blocks_for(units_of(g.nx, g.ny), precision == 32 ? PushCfg<float>::warps : PushCfg<double>::warps,
-                      152 * 16);
+                      cap > 0 ? cap : 152 * 16);
 }
 
 template <typename T>
@@ -1201,13 +1201,14 @@ cudaError_t export_particles(PArrays<T> p, const int32_t* start, GridP g, double
 
 template <typename T>
 cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, const T* En, T* M, T* J, GridP g, int* err,
-                    cudaStream_t st)
+                    cudaStream_t st, int max_blocks)
 {
     const int nunits = units_of(g.nx, g.ny);
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     nsm *= 2;   // two CTAs per SM
+    if (max_blocks > 0) nsm = max_blocks;
     const size_t smem = (size_t)kDepBuf * 6 * kDepCap * sizeof(T);
     auto kern = En ? k_deposit<T, true> : k_deposit<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1286,7 +1287,7 @@ cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int 
     template cudaError_t export_particles<T>(PArrays<T>, const int32_t*, GridP, double*, double*,  \
                                              double*, int32_t*, cudaStream_t);                     \
     template cudaError_t deposit<T>(const DepositSpecies<T>&, const T*, const T*, T*, T*, GridP, int*,  \
-                                    cudaStream_t);                                                  \
+                                    cudaStream_t, int);                                             \
     template cudaError_t push_sort<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, int32_t*,   \
                                       const T*, const T*, const T*, GridP, SpeciesConst, double*,   \
                                       int, cudaStream_t);                                           \

@@ -571,3 +571,38 @@ def test_graph_step_after_reload_and_not_converged(rs):
         assert code == rs.RELSIM_ERR_NOT_CONVERGED and led["gmres_iters"] == 1
     assert sim.graph_info()["graph_steps"] == 2
     sim.close()
+
+
+def test_autotuned_launch_shapes_give_the_same_steps(rs):
+    """The autotuner only changes launch shapes: after it, steps agree with
+    an untuned context's to rounding (the deposit's float atomics), with the
+    same GMRES iteration counts, and the choice is one of the candidates."""
+    nx, ny = 48, 24
+    st = harris_small(nx, ny, 8)
+    sims = [make_sim(rs, nx, ny, 32) for _ in range(2)]
+    for s in sims:
+        s.load_state(st)
+    t = sims[0].autotune()
+    assert t["deposit_blocks"] in [b for b, _ in t["deposit"]]
+    assert t["push_blocks"] in [b for b, _ in t["push"]]
+    assert all(ms > 0 for _, ms in t["deposit"] + t["push"])
+    its = [[], []]
+    for _ in range(4):
+        for k, s in enumerate(sims):
+            led, code = s.step()
+            assert code == 0
+            its[k].append(led["gmres_iters"])
+    assert all(abs(a - b) <= 1 for a, b in zip(*its))
+    for a, b in zip(sims[0].fields(), sims[1].fields()):
+        assert np.max(np.abs(a - b)) <= 2e-5 * np.abs(b).max()
+    x0, u0, w0 = sims[0].particles(0)[:3]
+    x1, u1, w1 = sims[1].particles(0)[:3]
+    assert np.max(np.abs(u0 - u1)) <= 2e-5 * np.abs(u1).max()
+    built = make_sim(rs, nx, ny, 32)
+    built.load_state(st)
+    built.build()
+    with pytest.raises(rs.RelsimError) as e:
+        built.autotune()
+    assert e.value.code == rs.RELSIM_ERR_BAD_STATE
+    for s in sims + [built]:
+        s.close()
