@@ -160,10 +160,18 @@ def traffic_record(kernel):
     if not rec:
         return None
     src = os.path.join(ROOT, "paper_2509_11100_gb300", "csrc", rec["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if h != rec.get("source_sha256_16"):
+    if kernel_source_hash(src) != rec.get("kernels_sha256_16"):
         return None
     return rec["dram_bytes_per_launch"]
+
+
+def kernel_source_hash(path):
+    """sha256[:16] of a source file's device code: the text before the end of
+    its first anonymous namespace, where the kernels and their device helpers
+    live (the host launchers that follow do not change what a kernel moves)."""
+    text = open(path, "rb").read()
+    end = text.find(b"}  // namespace\n")
+    return hashlib.sha256(text[:end if end >= 0 else len(text)]).hexdigest()[:16]
 
 
 def algorithmic_bytes(slot, n_particles, n_per_species, ncell, esz):
