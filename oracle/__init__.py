@@ -17,7 +17,8 @@ from .build import build, lib_path
 __all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "curl_c",
            "curl_n", "rhs", "gmres", "field_update", "push", "energies", "cell_keys",
            "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
-           "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit", "field_adjoint"]
+           "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit", "field_adjoint",
+           "push_adjoint"]
 
 
 class OracleConfig(ctypes.Structure):
@@ -399,3 +400,92 @@ def field_adjoint(c, M, Etheta, gE1, gB1):
             gM[g, slot] = -th * dt * np.outer(L3[:, g], Et[:, h])
     return {"E0": gE0.reshape(3, nn), "B0": gB0.reshape(3, nn), "J": gJ.reshape(3, nn), "M": gM,
             "lambda": lam.reshape(3, nn)}
+
+
+def _cic(c, x, y, shift):
+    """Linear weights of the 4 lattice points around (x, y) on a lattice
+    shifted by `shift` cells (0: nodes, 0.5: cell centres), with their x and
+    y derivatives: indices (4, n), W, dW/dx, dW/dy (4, n)."""
+    tx, ty = x / c.dx - shift, y / c.dy - shift
+    fi, fj = np.floor(tx), np.floor(ty)
+    fx, fy = tx - fi, ty - fj
+    i, j = fi.astype(np.int64) % c.nx, fj.astype(np.int64) % c.ny
+    i1, j1 = (i + 1) % c.nx, (j + 1) % c.ny
+    g = np.stack([j * c.nx + i, j * c.nx + i1, j1 * c.nx + i, j1 * c.nx + i1])
+    W = np.stack([(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy])
+    Wx = np.stack([-(1 - fy), 1 - fy, -fy, fy]) / c.dx
+    Wy = np.stack([-(1 - fx), -fx, 1 - fx, fx]) / c.dy
+    return g, W, Wx, Wy
+
+
+def push_adjoint(c, P: Particles, Etheta, B, gu1, gx1, gy1):
+    """Adjoint of the push (Sec. 2: the pusher is explicit) with the fields
+    held fixed, base scheme (gbar = gamma(u^n)). Forward, per particle:
+      Ep = sum_g W_g(x) E_g (nodes),  Bp = sum_c W_c(x) B_c (centres),
+      gbar = sqrt(1 + |u|^2),  a = beta Bp/gbar,  alpha = (I + [a]x)^{-1},
+      ubar = alpha (u + beta Ep),  u1 = 2 ubar - u,  x1 = x + dt u1/gamma(u1).
+    Given dL/du1 (gu1, (3, N)) and dL/dx1, dL/dy1 (N each), returns dL/du,
+    dL/dx, dL/dy per particle and dL/dE (nodes), dL/dB (centres), (3, nn),
+    by the chain rule in reverse: the transposes of the gathers are the
+    scatters with the same weights, alpha's transpose is applied to the
+    gradient of ubar, and d alpha = -alpha d[a]x alpha.
+    """
+    nn = c.nx * c.ny
+    E = np.asarray(Etheta, dtype=np.float64).reshape(3, nn)
+    Bf = np.asarray(B, dtype=np.float64).reshape(3, nn)
+    gu1 = np.asarray(gu1, dtype=np.float64).reshape(3, -1)
+    gx1 = np.asarray(gx1, dtype=np.float64).ravel()
+    gy1 = np.asarray(gy1, dtype=np.float64).ravel()
+    N = P.x.size
+    gu0 = np.zeros((3, N))
+    gx0 = gx1.copy()
+    gy0 = gy1.copy()
+    gE = np.zeros((3, nn))
+    gB = np.zeros((3, nn))
+    for s in range(int(c.nspecies)):
+        a0, a1 = int(P.off[s]), int(P.off[s + 1])
+        if a1 == a0:
+            continue
+        beta = c.q[s] * c.dt / (2.0 * c.m[s])
+        x, y = P.x[a0:a1], P.y[a0:a1]
+        u = np.stack([P.ux[a0:a1], P.uy[a0:a1], P.uz[a0:a1]])
+        gN, WN, WNx, WNy = _cic(c, x, y, 0.0)
+        gC, WC, WCx, WCy = _cic(c, x, y, 0.5)
+        Ep = sum(WN[k] * E[:, gN[k]] for k in range(4))
+        Bp = sum(WC[k] * Bf[:, gC[k]] for k in range(4))
+        gb = np.sqrt(1.0 + (u * u).sum(axis=0))
+        a = beta * Bp / gb
+        n = a1 - a0
+        ax = np.zeros((n, 3, 3))   # [a]x v = a x v
+        ax[:, 0, 1], ax[:, 0, 2] = -a[2], a[1]
+        ax[:, 1, 0], ax[:, 1, 2] = a[2], -a[0]
+        ax[:, 2, 0], ax[:, 2, 1] = -a[1], a[0]
+        alpha = np.linalg.inv(np.eye(3)[None] + ax)
+        w = u + beta * Ep
+        ub = np.einsum("nij,jn->in", alpha, w)
+        u1 = 2.0 * ub - u
+        g1 = np.sqrt(1.0 + (u1 * u1).sum(axis=0))
+        # x1 = x + dt u1/g1 (x and y components)
+        gpos = np.stack([gx1[a0:a1], gy1[a0:a1], np.zeros(n)])
+        gu1t = gu1[:, a0:a1] + c.dt * (gpos / g1 - u1 * (u1 * gpos).sum(axis=0) / g1 ** 3)
+        gub = 2.0 * gu1t
+        gu = -gu1t
+        gw = np.einsum("nji,jn->in", alpha, gub)          # alpha^T gubar
+        galpha = np.einsum("in,jn->nij", gub, w)           # gubar w^T
+        gu += gw
+        gEp = beta * gw
+        G = -np.einsum("nji,njk,nlk->nil", alpha, galpha, alpha)   # -alpha^T galpha alpha^T
+        ga = np.stack([G[:, 2, 1] - G[:, 1, 2], G[:, 0, 2] - G[:, 2, 0], G[:, 1, 0] - G[:, 0, 1]])
+        gBp = beta * ga / gb
+        ggb = -beta * (ga * Bp).sum(axis=0) / gb ** 2
+        gu += ggb * u / gb
+        for k in range(4):
+            for comp in range(3):
+                np.add.at(gE[comp], gN[k], WN[k] * gEp[comp])
+                np.add.at(gB[comp], gC[k], WC[k] * gBp[comp])
+            eg = (E[:, gN[k]] * gEp).sum(axis=0)
+            bg = (Bf[:, gC[k]] * gBp).sum(axis=0)
+            gx0[a0:a1] += WNx[k] * eg + WCx[k] * bg
+            gy0[a0:a1] += WNy[k] * eg + WCy[k] * bg
+        gu0[:, a0:a1] = gu
+    return {"u": gu0, "x": gx0, "y": gy0, "E": gE, "B": gB}

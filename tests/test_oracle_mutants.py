@@ -70,6 +70,10 @@ PY_MUTANTS = {
     "adjoint_untransposed": ("lam = np.linalg.solve(A.T, gEt)", "lam = np.linalg.solve(A, gEt)"),
     "adjoint_drops_E_extrapolation": ("gE0 = lam - (1.0 - th) / th * gE1", "gE0 = lam"),
     "adjoint_mass_pair_swapped": ("np.outer(L3[:, g], Et[:, h])", "np.outer(L3[:, h], Et[:, g])"),
+    "push_adjoint_alpha_untransposed": ('gw = np.einsum("nji,jn->in", alpha, gub)',
+                                        'gw = np.einsum("nij,jn->in", alpha, gub)'),
+    "push_adjoint_drops_gbar": ("        gu += ggb * u / gb\n", "\n"),
+    "push_adjoint_B_on_nodes": ("gC, WC, WCx, WCy = _cic(c, x, y, 0.5)", "gC, WC, WCx, WCy = _cic(c, x, y, 0.0)"),
 }
 CASES = {**{k: ("relsim_oracle.c",) + v for k, v in MUTANTS.items()},
          **{k: ("__init__.py",) + v for k, v in PY_MUTANTS.items()}}

@@ -791,3 +791,56 @@ def test_field_adjoint_lambda_solves_the_transposed_system(orc):
     for _ in range(3):
         v = rng.normal(size=(3, nx * ny))
         assert abs(np.sum(g["lambda"] * orc.apply_A(c, M, v)) - np.sum(gEt * v)) < 1e-11 * np.abs(gEt).sum()
+
+
+# ---------------------------------------------------------------------------
+# adjoint of the push (fields held fixed)
+
+def _push_loss(orc, c, P0, E, B, cu, cx, cy):
+    P = P0.copy()
+    orc.push(c, P, E, B)
+    Lx, Ly = c.nx * c.dx, c.ny * c.dy
+    # periodic in the positions, so a wrap inside the push changes nothing
+    return float(np.sum(cu[0] * P.ux + cu[1] * P.uy + cu[2] * P.uz)
+                 + np.sum(cx * np.sin(2 * np.pi * P.x / Lx)) + np.sum(cy * np.cos(2 * np.pi * P.y / Ly))), P
+
+
+def test_push_adjoint_matches_directional_derivatives(orc):
+    nx, ny = 7, 5
+    c = cfg_for(orc, nx, ny, dt=0.7, dx=0.9, dy=1.2)
+    st = random_state(nx, ny, [30, 25], seed=51, dx=0.9, dy=1.2, u_scale=1.3, field_scale=1.1)
+    P0 = orc.Particles(st["species"])
+    E, B = st["E"], st["B"]
+    rng = np.random.default_rng(13)
+    N = P0.x.size
+    cu, cx, cy = rng.normal(size=(3, N)), rng.normal(size=N), rng.normal(size=N)
+    L0, P1 = _push_loss(orc, c, P0, E, B, cu, cx, cy)
+    Lx, Ly = nx * c.dx, ny * c.dy
+    gx1 = cx * np.cos(2 * np.pi * P1.x / Lx) * 2 * np.pi / Lx
+    gy1 = -cy * np.sin(2 * np.pi * P1.y / Ly) * 2 * np.pi / Ly
+    g = orc.push_adjoint(c, P0, E, B, cu, gx1, gy1)
+    h = 1e-6
+
+    def fd(mod):
+        Pp, Pm = P0.copy(), P0.copy()
+        Ep, Bp_, Em, Bm = E.copy(), B.copy(), E.copy(), B.copy()
+        mod(Pp, Ep, Bp_, h)
+        mod(Pm, Em, Bm, -h)
+        return (_push_loss(orc, c, Pp, Ep, Bp_, cu, cx, cy)[0] - _push_loss(orc, c, Pm, Em, Bm, cu, cx, cy)[0]) / (2 * h)
+
+    du = rng.normal(size=(3, N))
+    def mu(P, Ee, Bb, s):
+        P.ux += s * du[0]; P.uy += s * du[1]; P.uz += s * du[2]
+    assert abs(fd(mu) - np.sum(g["u"] * du)) < 1e-6 * np.abs(g["u"] * du).sum()
+    dx = rng.normal(size=N) * 0.1
+    dy = rng.normal(size=N) * 0.1
+    def mx(P, Ee, Bb, s):
+        P.x += s * dx; P.y += s * dy
+    assert abs(fd(mx) - np.sum(g["x"] * dx + g["y"] * dy)) < 1e-6 * np.abs(g["x"] * dx).sum()
+    dE, dB = rng.normal(size=E.shape), rng.normal(size=B.shape)
+    def mE(P, Ee, Bb, s):
+        Ee += s * dE
+    def mB(P, Ee, Bb, s):
+        Bb += s * dB
+    assert abs(fd(mE) - np.sum(g["E"] * dE)) < 1e-6 * np.abs(g["E"] * dE).sum()
+    assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-6 * np.abs(g["B"] * dB).sum()
