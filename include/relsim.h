@@ -234,6 +234,24 @@ RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const do
                                     double* gB0, double* gJ, double* gM, int* iters, double* rel_residual,
                                     int where);
 
+/* Adjoint of the push of one species with the fields held fixed (the
+   explicit pusher of Sec. 2; base scheme, gbar = gamma(u^n)). For the
+   solved step's push u^{n+1} = 2 alpha (u^n + beta E^{n+theta}(x)) - u^n,
+   x^{n+3/2} = x + dt u^{n+1}/gamma^{n+1}, with alpha from B^n(x): given
+   gu1 = dL/du^{n+1} (3n, interleaved (ux, uy, uz)) and gx1 =
+   dL/dx^{n+3/2} (2n, interleaved (x, y)) for the species' n particles in
+   their current order (the order relsim_get_particles returns before the
+   push), it returns gu0 = dL/du^n (3n), gx0 = dL/dx^{n+1/2} (2n), and
+   overwrites gE = dL/dE^{n+theta} (node field, 3*ncell) and gB = dL/dB^n
+   (centre field, 3*ncell) with this species' contribution (sum the species
+   yourself). The push is replayed per particle in FP64 from the stored
+   values; the gathers' transposes are scatters with the same weights.
+   Call it between relsim_field_solve and relsim_push. Synchronises the
+   stream. Errors: INVALID_ARG (including a gamma_pred context), BAD_STATE,
+   OOM, CUDA. */
+RELSIM_API int relsim_push_adjoint(relsim_ctx* ctx, int species, const double* gu1, const double* gx1,
+                                   double* gu0, double* gx0, double* gE, double* gB, int where);
+
 /* E^{n+theta} of the last solve (3*ncell FP64). Errors: BAD_STATE, CUDA. */
 RELSIM_API int relsim_get_E_theta(relsim_ctx* ctx, double* E, int where);
 

@@ -30,7 +30,7 @@ __all__ = [
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
     "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
     "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
-    "relsim_tuning",
+    "relsim_tuning", "relsim_push_adjoint",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -130,6 +130,7 @@ _SIGS = {
     "relsim_graph_info": (ctypes.c_int, [_CTX, _P, _P, _P]),
     "relsim_field_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
     "relsim_autotune": (ctypes.c_int, [_CTX, _P]),
+    "relsim_push_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
 }
 
 PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
@@ -427,6 +428,21 @@ def relsim_field_adjoint(ctx, ncell, gE1, gB1, mass=True, device=False):
     return outs
 
 
+def relsim_push_adjoint(ctx, species, ncell, gu1, gx1, device=False):
+    """Adjoint of one species' push with the fields fixed: from dL/du^{n+1}
+    (n, 3) and dL/dx^{n+3/2} (n, 2) in the particles' current order, returns
+    {"u": (n, 3), "x": (n, 2), "E": (3, ncell), "B": (3, ncell)}."""
+    p1, p2 = _ptr(gu1), _ptr(gx1)
+    dev = _where(p1, p2) == RELSIM_DEVICE
+    n = relsim_num_particles(ctx, species)
+    outs = {"u": _out((n, 3), np.float64, dev), "x": _out((n, 2), np.float64, dev),
+            "E": _out((3, ncell), np.float64, dev), "B": _out((3, ncell), np.float64, dev)}
+    pp = {k: _ptr(v, writable=True) for k, v in outs.items()}
+    _check(ctx, lib().relsim_push_adjoint(ctx, species, p1[0], p2[0], pp["u"][0], pp["x"][0], pp["E"][0],
+                                          pp["B"][0], RELSIM_DEVICE if dev else RELSIM_HOST))
+    return outs
+
+
 def relsim_autotune(ctx) -> dict:
     """Time candidate launch shapes of the deposit and the push on the loaded
     state and keep the fastest; returns the candidates and the choice."""
@@ -598,6 +614,9 @@ class Simulation:
 
     def autotune(self):
         return relsim_autotune(self.ctx)
+
+    def push_adjoint(self, s, gu1, gx1, device=False):
+        return relsim_push_adjoint(self.ctx, s, self.ncell, gu1, gx1, device)
 
     def field_adjoint(self, gE1, gB1, mass=True, device=False):
         return relsim_field_adjoint(self.ctx, self.ncell, gE1, gB1, mass, device)

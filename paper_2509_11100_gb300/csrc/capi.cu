@@ -1145,6 +1145,39 @@ int adjoint_impl(relsim_ctx* c, const double* gE1, const double* gB1, double* gE
     return RELSIM_OK;
 }
 
+// The adjoint of the push of one species with the fields held fixed
+// (particles kernels: k_push_adjoint). Outputs gE, gB are overwritten with
+// this species' contribution.
+template <typename T>
+int push_adjoint_impl(relsim_ctx* c, int s, const double* gu1, const double* gx1, double* gu0, double* gx0,
+                      double* gE, double* gB, int where)
+{
+    Species& sp = c->sp[s];
+    const int64_t n = sp.n, nf = 3 * (int64_t)c->g.ncell;
+    const bool host = where == RELSIM_HOST;
+    if (host) TRY(ensure_stage(c, 10 * n + 2 * nf));
+    const double *d1, *d2;
+    TRY(stage_in(c, gu1, 3 * n, where, &d1, 0));
+    TRY(stage_in(c, gx1, 2 * n, where, &d2, 3 * n));
+    double* ou = host ? c->stage + 5 * n : gu0;
+    double* ox = host ? c->stage + 8 * n : gx0;
+    double* oE = host ? c->stage + 10 * n : gE;
+    double* oB = host ? c->stage + 10 * n + nf : gB;
+    CK(cudaMemsetAsync(oE, 0, sizeof(double) * (size_t)nf, c->st));
+    CK(cudaMemsetAsync(oB, 0, sizeof(double) * (size_t)nf, c->st));
+    if (n > 0)
+        CK(push_adjoint<T>(arrays<T>(sp, sp.cur), sp.start, d1, d2, ou, ox, oE, oB, (const T*)c->Eth,
+                           (const T*)c->B[c->bcur], c->g, SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st));
+    if (host) {
+        CK(cudaMemcpyAsync(gu0, ou, sizeof(double) * (size_t)(3 * n), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(gx0, ox, sizeof(double) * (size_t)(2 * n), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(gE, oE, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(gB, oB, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToHost, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    return RELSIM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // graph steps enqueued back to back (the batch runner): both layouts are
 // captured up front, each step is one graph launch on the context's stream
@@ -1696,6 +1729,19 @@ int relsim_autotune(relsim_ctx* c, relsim_tuning* out)
     if (!c) return RELSIM_ERR_INVALID_ARG;
     if (c->state != kReady) return fail(c, RELSIM_ERR_BAD_STATE, "autotune needs a loaded state before a build");
     return DISPATCH(autotune_impl, c, out);
+}
+
+int relsim_push_adjoint(relsim_ctx* c, int species, const double* gu1, const double* gx1, double* gu0,
+                        double* gx0, double* gE, double* gB, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (species < 0 || species >= c->cfg.nspecies) return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    if (c->sp[species].n > 0 && (!gu1 || !gx1 || !gu0 || !gx0)) return fail(c, RELSIM_ERR_INVALID_ARG, "null array");
+    if (!gE || !gB) return fail(c, RELSIM_ERR_INVALID_ARG, "null field gradient");
+    if (c->En) return fail(c, RELSIM_ERR_INVALID_ARG, "the push adjoint covers the base scheme (gamma_pred = 0)");
+    if (c->state != kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "the push adjoint needs a solved step (before the push)");
+    return DISPATCH(push_adjoint_impl, c, species, gu1, gx1, gu0, gx0, gE, gB, where);
 }
 
 int relsim_field_adjoint(relsim_ctx* c, const double* gE1, const double* gB1, double* gE0, double* gB0,

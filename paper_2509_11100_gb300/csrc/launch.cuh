@@ -94,6 +94,13 @@ template <typename T>
 cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, const T* Eth,
                          const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
                          cudaStream_t st);
+// adjoint of the push with the fields fixed (base scheme): per particle
+// dL/du^n, dL/dx^{n+1/2} from dL/du^{n+1}, dL/dx^{n+3/2} (FP64, interleaved,
+// current order); dL/dE^{n+theta}, dL/dB^n added into gE, gB (FP64 atomics)
+template <typename T>
+cudaError_t push_adjoint(PArrays<T> src, const int32_t* start, const double* gu1, const double* gx1, double* gu0,
+                         double* gx0, double* gE, double* gB, const T* Eth, const T* B, GridP g, SpeciesConst sc,
+                         cudaStream_t st);
 // the stable new-cell order from the runs of push_sort (err bit 1 if the
 // runs and the new cell starts disagree)
 template <typename T>

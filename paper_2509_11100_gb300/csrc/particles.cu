@@ -1146,6 +1146,146 @@ k_spectrum(PArrays<T> pa, int64_t n, int variable, const T* __restrict__ edges, 
         }
 }
 
+// Adjoint of the push with the fields held fixed (base scheme, gbar =
+// gamma(u^n)): per particle, the push is replayed in FP64 from the stored
+// values and the chain rule run in reverse. The gathers' transposes are
+// scatters with the same weights (FP64 atomics into gE on the nodes and gB
+// on the centres); alpha's transpose is applied to the gradient of ubar, and
+// d alpha = -alpha d[a]x alpha gives the gradient of a = beta B/gbar. gu1,
+// gx1 are dL/du^{n+1}, dL/dx^{n+3/2} (interleaved, in the particles' current
+// order); gu0, gx0 receive dL/du^n, dL/dx^{n+1/2}.
+template <typename T>
+__global__ void __launch_bounds__(PushCfg<T>::threads)
+k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gu1,
+               const double* __restrict__ gx1, double* __restrict__ gu0, double* __restrict__ gx0,
+               double* __restrict__ gE, double* __restrict__ gB, const T* __restrict__ Eth,
+               const T* __restrict__ B, GridP g, double beta)
+{
+    constexpr int W = PushCfg<T>::warps;
+    __shared__ int sstart[W][kUnitW + 1];
+    __shared__ PushTile<T> stile[W];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int nunits = units_of(nx, ny);
+    int* ss = sstart[wib];
+    PushTile<T>& tl = stile[wib];
+    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy, dt = g.dt;
+    for (int u = warp; u < nunits; u += nwarps) {
+        const Unit un = unit_of(u, nx);
+        unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
+        const int P0 = ss[0], P1 = ss[un.cn];
+        int cl = 0;
+        for (int p = P0 + lane; p < P1; p += 32) {
+            while (ss[cl + 1] <= p) ++cl;
+            const double fx = (double)ld(src.fx + p), fy = (double)ld(src.fy + p);
+            const double u0[3] = {(double)ld(src.ux + p), (double)ld(src.uy + p), (double)ld(src.uz + p)};
+            // node weights and their derivatives in x, y
+            const double X0 = 1.0 - fx, Y0 = 1.0 - fy;
+            const double Wn[4] = {X0 * Y0, fx * Y0, X0 * fy, fx * fy};
+            const double Wnx[4] = {-Y0 * rdx, Y0 * rdx, -fy * rdx, fy * rdx};
+            const double Wny[4] = {-X0 * rdy, -fx * rdy, X0 * rdy, fx * rdy};
+            double En[4][3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                En[0][k] = (double)tl.E[k][0][cl];
+                En[1][k] = (double)tl.E[k][0][cl + 1];
+                En[2][k] = (double)tl.E[k][1][cl];
+                En[3][k] = (double)tl.E[k][1][cl + 1];
+            }
+            // centre weights (the two centres below or above the offset)
+            const bool lx = fx < 0.5, ly = fy < 0.5;
+            const double tx = lx ? fx + 0.5 : fx - 0.5, ty = ly ? fy + 0.5 : fy - 0.5;
+            const int c0 = lx ? cl : cl + 1, r0 = ly ? 0 : 1;
+            const double Wc[4] = {(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
+            const double Wcx[4] = {-(1.0 - ty) * rdx, (1.0 - ty) * rdx, -ty * rdx, ty * rdx};
+            const double Wcy[4] = {-(1.0 - tx) * rdy, -tx * rdy, (1.0 - tx) * rdy, tx * rdy};
+            double Bc[4][3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Bc[0][k] = (double)tl.B[k][r0][c0];
+                Bc[1][k] = (double)tl.B[k][r0][c0 + 1];
+                Bc[2][k] = (double)tl.B[k][r0 + 1][c0];
+                Bc[3][k] = (double)tl.B[k][r0 + 1][c0 + 1];
+            }
+            double Ep[3], Bp[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Ep[k] = Wn[0] * En[0][k] + Wn[1] * En[1][k] + Wn[2] * En[2][k] + Wn[3] * En[3][k];
+                Bp[k] = Wc[0] * Bc[0][k] + Wc[1] * Bc[1][k] + Wc[2] * Bc[2][k] + Wc[3] * Bc[3][k];
+            }
+            // forward replay
+            const double gb = sqrt(1.0 + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+            const double a[3] = {beta * Bp[0] / gb, beta * Bp[1] / gb, beta * Bp[2] / gb};
+            const double ia = 1.0 / (1.0 + a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+            // alpha = (I - [a]x + a a^T)/(1 + |a|^2) = (I + [a]x)^{-1}
+            double al[3][3];
+            al[0][0] = (1.0 + a[0] * a[0]) * ia; al[0][1] = (a[0] * a[1] + a[2]) * ia; al[0][2] = (a[0] * a[2] - a[1]) * ia;
+            al[1][0] = (a[0] * a[1] - a[2]) * ia; al[1][1] = (1.0 + a[1] * a[1]) * ia; al[1][2] = (a[1] * a[2] + a[0]) * ia;
+            al[2][0] = (a[0] * a[2] + a[1]) * ia; al[2][1] = (a[1] * a[2] - a[0]) * ia; al[2][2] = (1.0 + a[2] * a[2]) * ia;
+            double w[3], ub[3], u1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) w[k] = u0[k] + beta * Ep[k];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) ub[r] = al[r][0] * w[0] + al[r][1] * w[1] + al[r][2] * w[2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) u1[k] = 2.0 * ub[k] - u0[k];
+            const double g1 = sqrt(1.0 + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+            // backward: x1 = x + dt u1/g1
+            const double gp[3] = {gx1[2 * (int64_t)p], gx1[2 * (int64_t)p + 1], 0.0};
+            const double up = u1[0] * gp[0] + u1[1] * gp[1];
+            double gt[3], gub[3], gu[3], gw[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gt[k] = gu1[3 * (int64_t)p + k] + dt * (gp[k] / g1 - u1[k] * up / (g1 * g1 * g1));
+                gub[k] = 2.0 * gt[k];
+                gu[k] = -gt[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gw[k] = al[0][k] * gub[0] + al[1][k] * gub[1] + al[2][k] * gub[2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gu[k] += gw[k];
+            // G = -alpha^T (gub w^T) alpha^T = -(alpha^T gub)(alpha w)^T = -gw ub^T
+            // (the outer product factorises); ga from <G, [da]x>
+            const double ga[3] = {-(gw[2] * ub[1] - gw[1] * ub[2]), -(gw[0] * ub[2] - gw[2] * ub[0]),
+                                  -(gw[1] * ub[0] - gw[0] * ub[1])};
+            const double gBp[3] = {beta * ga[0] / gb, beta * ga[1] / gb, beta * ga[2] / gb};
+            const double ggb = -beta * (ga[0] * Bp[0] + ga[1] * Bp[1] + ga[2] * Bp[2]) / (gb * gb);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gu[k] += ggb * u0[k] / gb;
+            const double gEp[3] = {beta * gw[0], beta * gw[1], beta * gw[2]};
+            double gxp = gp[0], gyp = gp[1];
+            const int i = un.i0 + cl, j = un.j;
+            const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+            const int64_t nodes[4] = {(int64_t)j * nx + i, (int64_t)j * nx + i1, (int64_t)j1 * nx + i,
+                                      (int64_t)j1 * nx + i1};
+            const int ic = wrap1(lx ? i - 1 : i, nx), jc = wrap1(ly ? j - 1 : j, ny);
+            const int ic1 = wrap1(ic + 1, nx), jc1 = wrap1(jc + 1, ny);
+            const int64_t cents[4] = {(int64_t)jc * nx + ic, (int64_t)jc * nx + ic1, (int64_t)jc1 * nx + ic,
+                                      (int64_t)jc1 * nx + ic1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double eg = 0.0, bg = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    atomicAdd(gE + (int64_t)k * nc + nodes[q], Wn[q] * gEp[k]);
+                    atomicAdd(gB + (int64_t)k * nc + cents[q], Wc[q] * gBp[k]);
+                    eg += En[q][k] * gEp[k];
+                    bg += Bc[q][k] * gBp[k];
+                }
+                gxp += Wnx[q] * eg + Wcx[q] * bg;
+                gyp += Wny[q] * eg + Wcy[q] * bg;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gu0[3 * (int64_t)p + k] = gu[k];
+            gx0[2 * (int64_t)p] = gxp;
+            gx0[2 * (int64_t)p + 1] = gyp;
+        }
+        __syncwarp();
+    }
+}
+
 int blocks_for(int64_t n, int threads, int cap)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -1234,6 +1374,18 @@ cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int3
 }
 
 template <typename T>
+cudaError_t push_adjoint(PArrays<T> src, const int32_t* start, const double* gu1, const double* gx1, double* gu0,
+                         double* gx0, double* gE, double* gB, const T* Eth, const T* B, GridP g, SpeciesConst sc,
+                         cudaStream_t st)
+{
+    const double beta = sc.q * g.dt / (2.0 * sc.m);
+    count_launches(1);
+    k_push_adjoint<T><<<push_grid_blocks(g, sizeof(T) == 4 ? 32 : 64), PushCfg<T>::threads, 0, st>>>(
+        src, start, gu1, gx1, gu0, gx0, gE, gB, Eth, B, g, beta);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, const T* Eth,
                          const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
                          cudaStream_t st)
@@ -1294,6 +1446,9 @@ cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int 
     template cudaError_t push_general<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, const T*, \
                                          const T*, const T*, GridP, SpeciesConst, double*, int,      \
                                          cudaStream_t);                                              \
+    template cudaError_t push_adjoint<T>(PArrays<T>, const int32_t*, const double*, const double*,   \
+                                         double*, double*, double*, double*, const T*, const T*,     \
+                                         GridP, SpeciesConst, cudaStream_t);                         \
     template cudaError_t permute<T>(PArrays<T>, PArrays<T>, const int32_t*, const int32_t*,         \
                                     const int32_t*, GridP, int*, cudaStream_t);                     \
     template cudaError_t kinetic_energy<T>(PArrays<T>, int64_t, double, double*, int, cudaStream_t); \
