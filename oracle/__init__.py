@@ -18,7 +18,7 @@ __all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "c
            "curl_n", "rhs", "gmres", "field_update", "push", "energies", "cell_keys",
            "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
            "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit", "field_adjoint",
-           "push_adjoint"]
+           "push_adjoint", "deposit_adjoint"]
 
 
 class OracleConfig(ctypes.Structure):
@@ -489,3 +489,85 @@ def push_adjoint(c, P: Particles, Etheta, B, gu1, gx1, gy1):
             gy0[a0:a1] += WNy[k] * eg + WCy[k] * bg
         gu0[:, a0:a1] = gu
     return {"u": gu0, "x": gx0, "y": gy0, "E": gE, "B": gB}
+
+
+def deposit_adjoint(c, P: Particles, B, gJ, gM):
+    """Adjoint of the deposit (base scheme, gbar = gamma(u^n)). Forward, per
+    particle: Bp = sum_c W_c(x) B_c, a = beta Bp/gbar, alpha = (I + [a]x)^-1,
+      Jhat_g += (w q/dV) W_g(x) alpha u/gbar,
+      M_{g g'} += (w q beta/dV) W_g(x) W_g'(x) alpha/gbar  (ordered pairs, full layout).
+    Given dL/dJhat (gJ, (3, nn)) and dL/dM (gM, (nn, 9, 3, 3) full layout),
+    returns dL/du (3, N), dL/dx, dL/dy (N) and dL/dB (3, nn): the gradient of
+    alpha collects the current and every node pair's block gradient, then
+    flows through a (d alpha = -alpha d[a]x alpha) to Bp and gbar."""
+    nn = c.nx * c.ny
+    dV = c.dx * c.dy
+    Bf = np.asarray(B, dtype=np.float64).reshape(3, nn)
+    gJ = np.asarray(gJ, dtype=np.float64).reshape(3, nn)
+    gM = np.asarray(gM, dtype=np.float64).reshape(nn, 9, 3, 3)
+    N = P.x.size
+    gu0 = np.zeros((3, N))
+    gx0 = np.zeros(N)
+    gy0 = np.zeros(N)
+    gB = np.zeros((3, nn))
+    for s in range(int(c.nspecies)):
+        a0, a1 = int(P.off[s]), int(P.off[s + 1])
+        if a1 == a0:
+            continue
+        q, m = c.q[s], c.m[s]
+        beta = q * c.dt / (2.0 * m)
+        x, y = P.x[a0:a1], P.y[a0:a1]
+        u = np.stack([P.ux[a0:a1], P.uy[a0:a1], P.uz[a0:a1]])
+        w = P.w[a0:a1]
+        n = a1 - a0
+        gN, WN, WNx, WNy = _cic(c, x, y, 0.0)
+        gC, WC, WCx, WCy = _cic(c, x, y, 0.5)
+        Bp = sum(WC[k] * Bf[:, gC[k]] for k in range(4))
+        gb = np.sqrt(1.0 + (u * u).sum(axis=0))
+        a = beta * Bp / gb
+        ax = np.zeros((n, 3, 3))
+        ax[:, 0, 1], ax[:, 0, 2] = -a[2], a[1]
+        ax[:, 1, 0], ax[:, 1, 2] = a[2], -a[0]
+        ax[:, 2, 0], ax[:, 2, 1] = -a[1], a[0]
+        alpha = np.linalg.inv(np.eye(3)[None] + ax)
+        cJ = w * q / dV
+        cM = w * q * beta / dV
+        au = np.einsum("nij,jn->in", alpha, u)
+        galpha = np.zeros((n, 3, 3))
+        gWn = np.zeros((4, n))
+        ggb = np.zeros(n)
+        gu = np.zeros((3, n))
+        for k in range(4):
+            gj = gJ[:, gN[k]]                                   # (3, n)
+            # Jhat: cJ W alpha u / gbar
+            galpha += (cJ * WN[k] / gb)[:, None, None] * np.einsum("in,jn->nij", gj, u)
+            gu += cJ * WN[k] / gb * np.einsum("nji,jn->in", alpha, gj)
+            sJ = (gj * au).sum(axis=0)
+            gWn[k] += cJ * sJ / gb
+            ggb -= cJ * WN[k] * sJ / gb ** 2
+            # M: every ordered node pair (k, l) of the cell
+            for l in range(4):
+                # the slot of node l seen from node k (offsets of the cell's nodes)
+                dk = (k % 2, k // 2)
+                dl = (l % 2, l // 2)
+                slot = (dl[1] - dk[1] + 1) * 3 + (dl[0] - dk[0] + 1)
+                G = gM[gN[k], slot]                              # (n, 3, 3)
+                s2 = np.einsum("nij,nij->n", G, alpha)
+                coef = cM * WN[k] * WN[l] / gb
+                galpha += coef[:, None, None] * G
+                gWn[k] += cM * WN[l] * s2 / gb
+                gWn[l] += cM * WN[k] * s2 / gb
+                ggb -= cM * WN[k] * WN[l] * s2 / gb ** 2
+        Gm = -np.einsum("nji,njk,nlk->nil", alpha, galpha, alpha)   # -alpha^T galpha alpha^T
+        ga = np.stack([Gm[:, 2, 1] - Gm[:, 1, 2], Gm[:, 0, 2] - Gm[:, 2, 0], Gm[:, 1, 0] - Gm[:, 0, 1]])
+        gBp = beta * ga / gb
+        ggb -= beta * (ga * Bp).sum(axis=0) / gb ** 2
+        gu += ggb * u / gb
+        for k in range(4):
+            for comp in range(3):
+                np.add.at(gB[comp], gC[k], WC[k] * gBp[comp])
+            bg = (Bf[:, gC[k]] * gBp).sum(axis=0)
+            gx0[a0:a1] += WNx[k] * gWn[k] + WCx[k] * bg
+            gy0[a0:a1] += WNy[k] * gWn[k] + WCy[k] * bg
+        gu0[:, a0:a1] = gu
+    return {"u": gu0, "x": gx0, "y": gy0, "B": gB}

@@ -72,8 +72,14 @@ PY_MUTANTS = {
     "adjoint_mass_pair_swapped": ("np.outer(L3[:, g], Et[:, h])", "np.outer(L3[:, h], Et[:, g])"),
     "push_adjoint_alpha_untransposed": ('gw = np.einsum("nji,jn->in", alpha, gub)',
                                         'gw = np.einsum("nij,jn->in", alpha, gub)'),
-    "push_adjoint_drops_gbar": ("        gu += ggb * u / gb\n", "\n"),
-    "push_adjoint_B_on_nodes": ("gC, WC, WCx, WCy = _cic(c, x, y, 0.5)", "gC, WC, WCx, WCy = _cic(c, x, y, 0.0)"),
+    "push_adjoint_drops_gbar": ("ggb = -beta * (ga * Bp).sum(axis=0) / gb ** 2\n        gu += ggb * u / gb\n",
+                                "ggb = -beta * (ga * Bp).sum(axis=0) / gb ** 2\n"),
+    "push_adjoint_B_on_nodes": ("gC, WC, WCx, WCy = _cic(c, x, y, 0.5)\n        Ep = sum(",
+                                "gC, WC, WCx, WCy = _cic(c, x, y, 0.0)\n        Ep = sum("),
+    "deposit_adjoint_drops_pair_gbar": ("                ggb -= cM * WN[k] * WN[l] * s2 / gb ** 2\n", "\n"),
+    "deposit_adjoint_current_untransposed": ('gu += cJ * WN[k] / gb * np.einsum("nji,jn->in", alpha, gj)',
+                                             'gu += cJ * WN[k] / gb * np.einsum("nij,jn->in", alpha, gj)'),
+    "deposit_adjoint_one_sided_pairs": ("                gWn[l] += cM * WN[k] * s2 / gb\n", "\n"),
 }
 CASES = {**{k: ("relsim_oracle.c",) + v for k, v in MUTANTS.items()},
          **{k: ("__init__.py",) + v for k, v in PY_MUTANTS.items()}}

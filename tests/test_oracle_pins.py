@@ -844,3 +844,42 @@ def test_push_adjoint_matches_directional_derivatives(orc):
         Bb += s * dB
     assert abs(fd(mE) - np.sum(g["E"] * dE)) < 1e-6 * np.abs(g["E"] * dE).sum()
     assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-6 * np.abs(g["B"] * dB).sum()
+
+
+def test_deposit_adjoint_matches_directional_derivatives(orc):
+    nx, ny = 6, 5
+    c = cfg_for(orc, nx, ny, dt=0.8, dx=0.9, dy=1.1, q=(1.0, -2.0), m=(1.0, 3.0))
+    st = random_state(nx, ny, [25, 20], seed=52, dx=0.9, dy=1.1, u_scale=1.4, field_scale=1.2,
+                      q=(1.0, -2.0), m=(1.0, 3.0))
+    P0 = orc.Particles(st["species"])
+    B = st["B"]
+    rng = np.random.default_rng(14)
+    nn = nx * ny
+    cJ, cM = rng.normal(size=(3, nn)), rng.normal(size=(nn, 9, 3, 3))
+
+    def L(P, Bb):
+        J, M = orc.deposit(c, P, Bb)
+        return float(np.sum(cJ * J) + np.sum(cM * M))
+
+    g = orc.deposit_adjoint(c, P0, B, cJ, cM)
+    h = 1e-6
+    N = P0.x.size
+
+    def fd(mod):
+        Pp, Pm, Bp_, Bm = P0.copy(), P0.copy(), B.copy(), B.copy()
+        mod(Pp, Bp_, h)
+        mod(Pm, Bm, -h)
+        return (L(Pp, Bp_) - L(Pm, Bm)) / (2 * h)
+
+    du = rng.normal(size=(3, N))
+    def mu(P, Bb, s):
+        P.ux += s * du[0]; P.uy += s * du[1]; P.uz += s * du[2]
+    assert abs(fd(mu) - np.sum(g["u"] * du)) < 1e-6 * np.abs(g["u"] * du).sum()
+    dx, dy = rng.normal(size=N) * 0.1, rng.normal(size=N) * 0.1
+    def mx(P, Bb, s):
+        P.x += s * dx; P.y += s * dy
+    assert abs(fd(mx) - np.sum(g["x"] * dx + g["y"] * dy)) < 1e-6 * (np.abs(g["x"] * dx).sum() + np.abs(g["y"] * dy).sum())
+    dB = rng.normal(size=B.shape)
+    def mB(P, Bb, s):
+        Bb += s * dB
+    assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-6 * np.abs(g["B"] * dB).sum()
