@@ -225,14 +225,35 @@ RELSIM_API int relsim_field_solve(relsim_ctx* ctx, int* iters, double* rel_resid
    (3*ncell each) and dL/dM for the stored mass-matrix blocks (ncell x 45 in
    relsim_get_mass_matrix's layout; a block serves both node pairs (g, g+o)
    and (g+o, g)): -theta dt (lambda_g E_{g+o}^T + [o != 0] lambda_{g+o}
-   E_g^T), E = E^{n+theta}. Any output may be NULL. Call it between
+   E_g^T), E = E^{n+theta}. gEt (may be NULL) is a further dL/dE^{n+theta}
+   added to the right-hand side, e.g. the pushes' (relsim_push_adjoint), to
+   chain the adjoints of one step. Any output may be NULL. Call it between
    relsim_field_solve and relsim_push (BAD_STATE otherwise). *iters and
    *rel_residual (may be NULL) report the adjoint solve. Synchronises the
    stream. Errors: INVALID_ARG, BAD_STATE, NOT_CONVERGED (outputs still
    written), NONFINITE, OOM, CUDA. */
-RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const double* gB1, double* gE0,
-                                    double* gB0, double* gJ, double* gM, int* iters, double* rel_residual,
-                                    int where);
+RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const double* gB1, const double* gEt,
+                                    double* gE0, double* gB0, double* gJ, double* gM, int* iters,
+                                    double* rel_residual, int where);
+
+/* Adjoint of the deposit of one species (base scheme, gbar = gamma(u^n)):
+   the deposit Jhat_g += (w q/dV) W_g(x) alpha u/gbar and M_{gg'} += (w q
+   beta/dV) W_g W_g' alpha/gbar, alpha from B^n(x). Given gJ = dL/dJhat
+   (3*ncell) and gM = dL/dM for the stored blocks (ncell x 45, the layout of
+   relsim_get_mass_matrix and relsim_field_adjoint's output), it returns per
+   particle gu0 = dL/du^n (3n, interleaved) and gx0 = dL/dx^{n+1/2} (2n,
+   interleaved), in the current order, and overwrites gB = dL/dB^n (centre
+   field, 3*ncell) with this species' contribution. Per particle in FP64
+   from the stored values. Call it after relsim_build_mass_matrix and before
+   relsim_push. Synchronises the stream. Errors: INVALID_ARG (including a
+   gamma_pred context), BAD_STATE, OOM, CUDA.
+   One step's adjoint chains the three: relsim_push_adjoint per species
+   (giving dL/dE^{n+theta} and part of dL/dB^n), relsim_field_adjoint with
+   gEt = their sum (giving dL/dE^n, the field part of dL/dB^n, dL/dJhat,
+   dL/dM), relsim_deposit_adjoint per species; dL/du^n and dL/dx^{n+1/2} are
+   the sums of the push's and the deposit's, dL/dB^n of all three. */
+RELSIM_API int relsim_deposit_adjoint(relsim_ctx* ctx, int species, const double* gJ, const double* gM,
+                                      double* gu0, double* gx0, double* gB, int where);
 
 /* Adjoint of the push of one species with the fields held fixed (the
    explicit pusher of Sec. 2; base scheme, gbar = gamma(u^n)). For the

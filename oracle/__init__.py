@@ -18,7 +18,7 @@ __all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "c
            "curl_n", "rhs", "gmres", "field_update", "push", "energies", "cell_keys",
            "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
            "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit", "field_adjoint",
-           "push_adjoint", "deposit_adjoint"]
+           "push_adjoint", "deposit_adjoint", "step_adjoint"]
 
 
 class OracleConfig(ctypes.Structure):
@@ -351,14 +351,15 @@ def growth_fit(s, dt, window):
     return best
 
 
-def field_adjoint(c, M, Etheta, gE1, gB1):
+def field_adjoint(c, M, Etheta, gE1, gB1, gEt=None):
     """Adjoint of the field part of one step with the particles (hence M and
     Jhat) held fixed. The forward map (Sec. 2: the implicit field solve) is
       b = E0 + theta dt curl_n B0 - theta dt J,   A Et = b,
       E1 = (Et - (1 - theta) E0)/theta,           B1 = B0 - dt curl_c Et,
     with A = I + (theta dt)^2 curl_n curl_c + theta dt M (M in the oracle's
     full layout, (nn, 9, 3, 3)). For L with dL/dE1 = gE1, dL/dB1 = gB1 this
-    returns dL/dE0, dL/dB0, dL/dJ and dL/dM (full layout), by the chain rule
+    returns dL/dE0, dL/dB0, dL/dJ and dL/dM (full layout) (gEt, if given, is
+    a further dL/dEt, e.g. from the push), by the chain rule
     written out with dense matrices: A, curl_c and curl_n are assembled
     column by column from the oracle's own operators and transposed with
     numpy, and A^T lambda = dL/dEt is solved densely. For small grids only.
@@ -382,7 +383,7 @@ def field_adjoint(c, M, Etheta, gE1, gB1):
     th, dt = c.theta, c.dt
     gE1 = np.asarray(gE1, dtype=np.float64).ravel()
     gB1 = np.asarray(gB1, dtype=np.float64).ravel()
-    gEt = gE1 / th - dt * (Cc.T @ gB1)
+    gEt = gE1 / th - dt * (Cc.T @ gB1) + (0.0 if gEt is None else np.asarray(gEt, dtype=np.float64).ravel())
     lam = np.linalg.solve(A.T, gEt)
     gE0 = lam - (1.0 - th) / th * gE1
     gB0 = gB1 + th * dt * (Cn.T @ lam)
@@ -571,3 +572,21 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
             gy0[a0:a1] += WNy[k] * gWn[k] + WCy[k] * bg
         gu0[:, a0:a1] = gu
     return {"u": gu0, "x": gx0, "y": gy0, "B": gB}
+
+
+def step_adjoint(c, P: Particles, E, B, gu1, gx1, gy1, gE1, gB1):
+    """Gradient of a loss of one full step's outputs (u^{n+1}, x^{n+3/2},
+    E^{n+1}, B^{n+1}) with respect to its inputs (u^n, x^{n+1/2}, E^n, B^n):
+    the push's adjoint (fields fixed) gives dL/dEt and part of dL/dB^n; the
+    field adjoint with that dL/dEt gives dL/dE^n, dL/dJhat, dL/dM and the
+    field part of dL/dB^n; the deposit's adjoint carries dL/dJhat and dL/dM
+    back to the particles and B^n. P is the state before the step."""
+    nn = c.nx * c.ny
+    J, M = deposit(c, P, B)
+    b = rhs(c, E, B, J)
+    Et, _, _, _ = gmres(c, M, b, np.zeros_like(b))
+    gp = push_adjoint(c, P, Et, B, gu1, gx1, gy1)
+    gf = field_adjoint(c, M, Et, gE1, gB1, gEt=gp["E"])
+    gd = deposit_adjoint(c, P, B, gf["J"], gf["M"])
+    return {"u": gp["u"] + gd["u"], "x": gp["x"] + gd["x"], "y": gp["y"] + gd["y"],
+            "E": gf["E0"], "B": gf["B0"] + gp["B"] + gd["B"], "push": gp, "field": gf, "deposit": gd}

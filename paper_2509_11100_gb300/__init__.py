@@ -30,7 +30,7 @@ __all__ = [
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
     "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
     "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
-    "relsim_tuning", "relsim_push_adjoint",
+    "relsim_tuning", "relsim_push_adjoint", "relsim_deposit_adjoint",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -128,7 +128,8 @@ _SIGS = {
     "relsim_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "relsim_batch_destroy": (None, [_P]),
     "relsim_graph_info": (ctypes.c_int, [_CTX, _P, _P, _P]),
-    "relsim_field_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
+    "relsim_field_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
+    "relsim_deposit_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int]),
     "relsim_autotune": (ctypes.c_int, [_CTX, _P]),
     "relsim_push_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
 }
@@ -409,22 +410,37 @@ def relsim_growth_fit(s, dt, window):
     return rate.value, first.value
 
 
-def relsim_field_adjoint(ctx, ncell, gE1, gB1, mass=True, device=False):
+def relsim_field_adjoint(ctx, ncell, gE1, gB1, mass=True, device=False, gEt=None):
     """Adjoint of the solved step's field part (particles fixed): returns
     {"E0", "B0", "J": (3, ncell), "M": (ncell, 5, 3, 3) or None, "iters",
-    "relres", "status"} for upstream gradients gE1, gB1 of E^{n+1}, B^{n+1}."""
-    p1, p2 = _ptr(gE1), _ptr(gB1)
-    dev = _where(p1, p2) == RELSIM_DEVICE
+    "relres", "status"} for upstream gradients gE1, gB1 of E^{n+1}, B^{n+1}
+    and an optional further gradient gEt of E^{n+theta}."""
+    p1, p2, p3 = _ptr(gE1), _ptr(gB1), _ptr(gEt)
+    dev = _where(p1, p2, p3) == RELSIM_DEVICE
     outs = {k: _out((3, ncell), np.float64, dev) for k in ("E0", "B0", "J")}
     outs["M"] = _out((ncell, 5, 3, 3), np.float64, dev) if mass else None
     ptrs = {k: _ptr(v, writable=True) for k, v in outs.items() if v is not None}
     it = ctypes.c_int()
     rr = ctypes.c_double()
     code = _check(ctx, lib().relsim_field_adjoint(
-        ctx, p1[0], p2[0], ptrs["E0"][0], ptrs["B0"][0], ptrs["J"][0], ptrs["M"][0] if mass else None,
+        ctx, p1[0], p2[0], p3[0], ptrs["E0"][0], ptrs["B0"][0], ptrs["J"][0], ptrs["M"][0] if mass else None,
         ctypes.byref(it), ctypes.byref(rr), RELSIM_DEVICE if dev else RELSIM_HOST),
         allow=(RELSIM_ERR_NOT_CONVERGED,))
     outs.update(iters=it.value, relres=rr.value, status=code)
+    return outs
+
+
+def relsim_deposit_adjoint(ctx, species, ncell, gJ, gM):
+    """Adjoint of one species' deposit: from dL/dJhat (3, ncell) and dL/dM
+    (ncell, 5, 3, 3), returns {"u": (n, 3), "x": (n, 2), "B": (3, ncell)}."""
+    p1, p2 = _ptr(gJ), _ptr(gM)
+    dev = _where(p1, p2) == RELSIM_DEVICE
+    n = relsim_num_particles(ctx, species)
+    outs = {"u": _out((n, 3), np.float64, dev), "x": _out((n, 2), np.float64, dev),
+            "B": _out((3, ncell), np.float64, dev)}
+    pp = {k: _ptr(v, writable=True) for k, v in outs.items()}
+    _check(ctx, lib().relsim_deposit_adjoint(ctx, species, p1[0], p2[0], pp["u"][0], pp["x"][0], pp["B"][0],
+                                             RELSIM_DEVICE if dev else RELSIM_HOST))
     return outs
 
 
@@ -618,8 +634,11 @@ class Simulation:
     def push_adjoint(self, s, gu1, gx1, device=False):
         return relsim_push_adjoint(self.ctx, s, self.ncell, gu1, gx1, device)
 
-    def field_adjoint(self, gE1, gB1, mass=True, device=False):
-        return relsim_field_adjoint(self.ctx, self.ncell, gE1, gB1, mass, device)
+    def field_adjoint(self, gE1, gB1, mass=True, device=False, gEt=None):
+        return relsim_field_adjoint(self.ctx, self.ncell, gE1, gB1, mass, device, gEt)
+
+    def deposit_adjoint(self, s, gJ, gM):
+        return relsim_deposit_adjoint(self.ctx, s, self.ncell, gJ, gM)
 
     def field_modes(self, component=1, nmodes=8, device=False):
         return relsim_field_modes(self.ctx, component, nmodes, device)

@@ -1102,17 +1102,18 @@ int step_graph(relsim_ctx* c, relsim_energy* ledger, int* status)
 // GMRES on the transposed operator, then the gradients of E^n, B^n, Jhat and
 // the stored mass-matrix blocks (see fields.cu).
 template <typename T>
-int adjoint_impl(relsim_ctx* c, const double* gE1, const double* gB1, double* gE0, double* gB0, double* gJ,
-                 double* gM, int* iters, double* relres, int where)
+int adjoint_impl(relsim_ctx* c, const double* gE1, const double* gB1, const double* gEt, double* gE0,
+                 double* gB0, double* gJ, double* gM, int* iters, double* relres, int where)
 {
     const int64_t n = c->nvec, nm = (int64_t)c->g.ncell * kMBlock;
-    if (where == RELSIM_HOST) TRY(ensure_stage(c, 5 * n + nm));
-    const double *d1, *d2;
+    if (where == RELSIM_HOST) TRY(ensure_stage(c, 6 * n + nm));
+    const double *d1, *d2, *d3 = nullptr;
     TRY(stage_in(c, gE1, n, where, &d1, 0));
     TRY(stage_in(c, gB1, n, where, &d2, n));
+    if (gEt) TRY(stage_in(c, gEt, n, where, &d3, 5 * n + nm));
     const GmSetup S = gm_setup(c);
     TRY(solve_reserve(c, S));
-    CK(adjoint_pre(d1, d2, c->gb, c->g, c->st));
+    CK(adjoint_pre(d1, d2, d3, c->gb, c->g, c->st));
     CK(gm_dots(c->V, S.ldv, 0, c->gb, S.n, c->partial, S.nb, c->st));
     CK(reduce_partials(c->partial, S.nb, 1, c->dsum, c->st));
     CK(gm_begin(c->gms, c->dsum, c->st));
@@ -1142,6 +1143,35 @@ int adjoint_impl(relsim_ctx* c, const double* gE1, const double* gB1, double* gE
     if (h.status == kGmNotConverged)
         return fail(c, RELSIM_ERR_NOT_CONVERGED, "adjoint GMRES reached %d iterations at relative residual %.3e",
                     h.total, h.relres);
+    return RELSIM_OK;
+}
+
+// The adjoint of one species' deposit (k_deposit_adjoint); gB is
+// overwritten with this species' contribution.
+template <typename T>
+int deposit_adjoint_impl(relsim_ctx* c, int s, const double* gJ, const double* gM, double* gu0, double* gx0,
+                         double* gB, int where)
+{
+    Species& sp = c->sp[s];
+    const int64_t n = sp.n, nf = 3 * (int64_t)c->g.ncell, nm = (int64_t)c->g.ncell * kMBlock;
+    const bool host = where == RELSIM_HOST;
+    if (host) TRY(ensure_stage(c, nf + nm + 5 * n + nf));
+    const double *dJ, *dM;
+    TRY(stage_in(c, gJ, nf, where, &dJ, 0));
+    TRY(stage_in(c, gM, nm, where, &dM, nf));
+    double* ou = host ? c->stage + nf + nm : gu0;
+    double* ox = host ? c->stage + nf + nm + 3 * n : gx0;
+    double* oB = host ? c->stage + nf + nm + 5 * n : gB;
+    CK(cudaMemsetAsync(oB, 0, sizeof(double) * (size_t)nf, c->st));
+    if (n > 0)
+        CK(deposit_adjoint<T>(arrays<T>(sp, sp.cur), sp.start, dJ, dM, ou, ox, oB, (const T*)c->B[c->bcur], c->g,
+                              SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st));
+    if (host) {
+        CK(cudaMemcpyAsync(gu0, ou, sizeof(double) * (size_t)(3 * n), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(gx0, ox, sizeof(double) * (size_t)(2 * n), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(gB, oB, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToHost, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
     return RELSIM_OK;
 }
 
@@ -1731,6 +1761,20 @@ int relsim_autotune(relsim_ctx* c, relsim_tuning* out)
     return DISPATCH(autotune_impl, c, out);
 }
 
+int relsim_deposit_adjoint(relsim_ctx* c, int species, const double* gJ, const double* gM, double* gu0,
+                           double* gx0, double* gB, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (species < 0 || species >= c->cfg.nspecies) return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    if (!gJ || !gM || !gB || (c->sp[species].n > 0 && (!gu0 || !gx0)))
+        return fail(c, RELSIM_ERR_INVALID_ARG, "null array");
+    if (c->En) return fail(c, RELSIM_ERR_INVALID_ARG, "the deposit adjoint covers the base scheme (gamma_pred = 0)");
+    if (c->state != kBuilt && c->state != kSolved)
+        return fail(c, RELSIM_ERR_BAD_STATE, "the deposit adjoint needs a built step (before the push)");
+    return DISPATCH(deposit_adjoint_impl, c, species, gJ, gM, gu0, gx0, gB, where);
+}
+
 int relsim_push_adjoint(relsim_ctx* c, int species, const double* gu1, const double* gx1, double* gu0,
                         double* gx0, double* gE, double* gB, int where)
 {
@@ -1744,14 +1788,14 @@ int relsim_push_adjoint(relsim_ctx* c, int species, const double* gu1, const dou
     return DISPATCH(push_adjoint_impl, c, species, gu1, gx1, gu0, gx0, gE, gB, where);
 }
 
-int relsim_field_adjoint(relsim_ctx* c, const double* gE1, const double* gB1, double* gE0, double* gB0,
-                         double* gJ, double* gM, int* iters, double* rel_residual, int where)
+int relsim_field_adjoint(relsim_ctx* c, const double* gE1, const double* gB1, const double* gEt, double* gE0,
+                         double* gB0, double* gJ, double* gM, int* iters, double* rel_residual, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
     if (!gE1 || !gB1) return fail(c, RELSIM_ERR_INVALID_ARG, "null upstream gradient");
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     if (c->state != kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "the adjoint needs a solved step (before the push)");
-    return DISPATCH(adjoint_impl, c, gE1, gB1, gE0, gB0, gJ, gM, iters, rel_residual, where);
+    return DISPATCH(adjoint_impl, c, gE1, gB1, gEt, gE0, gB0, gJ, gM, iters, rel_residual, where);
 }
 
 int relsim_get_E_theta(relsim_ctx* c, double* E, int where)

@@ -919,15 +919,16 @@ __device__ __forceinline__ void curl_n_at(const double* __restrict__ v, int i, i
     out[2] = dx[1] - dy[0];
 }
 
-__global__ void k_adj_pre(const double* __restrict__ gE1, const double* __restrict__ gB1, double* __restrict__ gEt,
-                          GridP g)
+__global__ void k_adj_pre(const double* __restrict__ gE1, const double* __restrict__ gB1,
+                          const double* __restrict__ gEx, double* __restrict__ gEt, GridP g)
 {
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.ncell; n += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(n % g.nx), j = (int)(n / g.nx);
         double cn[3];
         curl_n_at(gB1, i, j, g, cn);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) gEt[k * g.ncell + n] = gE1[k * g.ncell + n] / g.theta - g.dt * cn[k];
+        for (int k = 0; k < 3; ++k)
+            gEt[k * g.ncell + n] = gE1[k * g.ncell + n] / g.theta - g.dt * cn[k] + (gEx ? gEx[k * g.ncell + n] : 0.0);
     }
 }
 
@@ -986,10 +987,11 @@ __global__ void k_adj_mass(const double* __restrict__ lam, const T* __restrict__
     }
 }
 
-cudaError_t adjoint_pre(const double* gE1, const double* gB1, double* gEt, GridP g, cudaStream_t st)
+cudaError_t adjoint_pre(const double* gE1, const double* gB1, const double* gEx, double* gEt, GridP g,
+                        cudaStream_t st)
 {
     count_launches(1);
-    k_adj_pre<<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, gEt, g);
+    k_adj_pre<<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, gEx, gEt, g);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,12 @@ template <typename T>
 cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, const T* Eth,
                          const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
                          cudaStream_t st);
+// adjoint of the deposit (base scheme): per particle dL/du^n, dL/dx^{n+1/2}
+// from dL/dJhat (3 ncell) and dL/dM (ncell x 45, stored blocks); dL/dB^n
+// added into gB (FP64 atomics)
+template <typename T>
+cudaError_t deposit_adjoint(PArrays<T> src, const int32_t* start, const double* gJ, const double* gM, double* gu0,
+                            double* gx0, double* gB, const T* B, GridP g, SpeciesConst sc, cudaStream_t st);
 // adjoint of the push with the fields fixed (base scheme): per particle
 // dL/du^n, dL/dx^{n+1/2} from dL/du^{n+1}, dL/dx^{n+3/2} (FP64, interleaved,
 // current order); dL/dE^{n+theta}, dL/dB^n added into gE, gB (FP64 atomics)
@@ -174,10 +180,11 @@ cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, doubl
                             cudaStream_t st);
 int gm_blocks(int64_t n);
 
-// adjoint of the field part of a step (FP64): gEt = gE1/theta - dt curl_n gB1;
+// adjoint of the field part of a step (FP64): gEt = gE1/theta - dt curl_n gB1 (+ gEx);
 // after A^T lambda = gEt: gE0, gB0, gJ (each may be null) and the gradient of
 // the stored mass-matrix blocks (ncell x 45)
-cudaError_t adjoint_pre(const double* gE1, const double* gB1, double* gEt, GridP g, cudaStream_t st);
+cudaError_t adjoint_pre(const double* gE1, const double* gB1, const double* gEx, double* gEt, GridP g,
+                        cudaStream_t st);   // gEx (may be null): a further dL/dE^{n+theta} term
 cudaError_t adjoint_post(const double* gE1, const double* gB1, const double* lam, double* gE0, double* gB0,
                          double* gJ, GridP g, cudaStream_t st);
 template <typename T>

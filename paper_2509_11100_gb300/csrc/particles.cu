@@ -1286,6 +1286,158 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
     }
 }
 
+// Adjoint of the deposit (base scheme): per particle, alpha, gbar and the
+// shape weights are rebuilt in FP64 from the stored values; the gradient of
+// alpha collects the predicted current's (gJ at the cell's 4 nodes) and the
+// 10 node pairs' stored mass-matrix block gradients (gM, ncell x 45), then
+// flows through a = beta B/gbar to B (FP64 atomic scatter on the centres) and
+// gbar; the weights' derivatives give dL/dx. Outputs per particle dL/du^n
+// (gu0, interleaved) and dL/dx^{n+1/2} (gx0).
+template <typename T>
+__global__ void __launch_bounds__(PushCfg<T>::threads)
+k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gJ,
+                  const double* __restrict__ gM, double* __restrict__ gu0, double* __restrict__ gx0,
+                  double* __restrict__ gB, const T* __restrict__ B, GridP g, double beta, double cq)
+{
+    constexpr int W = PushCfg<T>::warps;
+    __shared__ int sstart[W][kUnitW + 1];
+    __shared__ PushTile<T> stile[W];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int nunits = units_of(nx, ny);
+    int* ss = sstart[wib];
+    PushTile<T>& tl = stile[wib];
+    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+    // the cell's node pairs: (node a, node b, storing node, half offset)
+    constexpr int pa[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
+    constexpr int pb[10] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
+    constexpr int ps[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
+    constexpr int po[10] = {0, 1, 3, 4, 0, 2, 3, 0, 1, 0};
+    for (int u = warp; u < nunits; u += nwarps) {
+        const Unit un = unit_of(u, nx);
+        unit_setup<T>(un, start, ss, tl, B, B, nx, ny, nc, lane);
+        const int P0 = ss[0], P1 = ss[un.cn];
+        int cl = 0;
+        for (int p = P0 + lane; p < P1; p += 32) {
+            while (ss[cl + 1] <= p) ++cl;
+            const double fx = (double)ld(src.fx + p), fy = (double)ld(src.fy + p);
+            const double u0[3] = {(double)ld(src.ux + p), (double)ld(src.uy + p), (double)ld(src.uz + p)};
+            const double wt = (double)ld(src.w + p);
+            const double X0 = 1.0 - fx, Y0 = 1.0 - fy;
+            const double Wn[4] = {X0 * Y0, fx * Y0, X0 * fy, fx * fy};
+            const double Wnx[4] = {-Y0 * rdx, Y0 * rdx, -fy * rdx, fy * rdx};
+            const double Wny[4] = {-X0 * rdy, -fx * rdy, X0 * rdy, fx * rdy};
+            const bool lx = fx < 0.5, ly = fy < 0.5;
+            const double tx = lx ? fx + 0.5 : fx - 0.5, ty = ly ? fy + 0.5 : fy - 0.5;
+            const int c0 = lx ? cl : cl + 1, r0 = ly ? 0 : 1;
+            const double Wc[4] = {(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
+            const double Wcx[4] = {-(1.0 - ty) * rdx, (1.0 - ty) * rdx, -ty * rdx, ty * rdx};
+            const double Wcy[4] = {-(1.0 - tx) * rdy, -tx * rdy, (1.0 - tx) * rdy, tx * rdy};
+            double Bc[4][3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Bc[0][k] = (double)tl.B[k][r0][c0];
+                Bc[1][k] = (double)tl.B[k][r0][c0 + 1];
+                Bc[2][k] = (double)tl.B[k][r0 + 1][c0];
+                Bc[3][k] = (double)tl.B[k][r0 + 1][c0 + 1];
+            }
+            double Bp[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Bp[k] = Wc[0] * Bc[0][k] + Wc[1] * Bc[1][k] + Wc[2] * Bc[2][k] + Wc[3] * Bc[3][k];
+            const double gb = sqrt(1.0 + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+            const double a[3] = {beta * Bp[0] / gb, beta * Bp[1] / gb, beta * Bp[2] / gb};
+            const double ia = 1.0 / (1.0 + a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+            double al[3][3];
+            al[0][0] = (1.0 + a[0] * a[0]) * ia; al[0][1] = (a[0] * a[1] + a[2]) * ia; al[0][2] = (a[0] * a[2] - a[1]) * ia;
+            al[1][0] = (a[0] * a[1] - a[2]) * ia; al[1][1] = (1.0 + a[1] * a[1]) * ia; al[1][2] = (a[1] * a[2] + a[0]) * ia;
+            al[2][0] = (a[0] * a[2] + a[1]) * ia; al[2][1] = (a[1] * a[2] - a[0]) * ia; al[2][2] = (1.0 + a[2] * a[2]) * ia;
+            double au[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) au[r] = al[r][0] * u0[0] + al[r][1] * u0[1] + al[r][2] * u0[2];
+            const double cJ = wt * cq / g.dV, cM = wt * cq * beta / g.dV;
+            const int i = un.i0 + cl, j = un.j;
+            const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+            const int64_t nodes[4] = {(int64_t)j * nx + i, (int64_t)j * nx + i1, (int64_t)j1 * nx + i,
+                                      (int64_t)j1 * nx + i1};
+            double ga_[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // dL/dalpha
+            double gW[4] = {0, 0, 0, 0}, ggb = 0.0, gu[3] = {0, 0, 0};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double gj[3] = {gJ[nodes[k]], gJ[nc + nodes[k]], gJ[2 * (int64_t)nc + nodes[k]]};
+                const double f = cJ * Wn[k] / gb;
+                double sJ = 0.0;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    sJ += gj[r] * au[r];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        ga_[r][q] += f * gj[r] * u0[q];
+                        gu[q] += f * al[r][q] * gj[r];
+                    }
+                }
+                gW[k] += cJ * sJ / gb;
+                ggb -= cJ * Wn[k] * sJ / (gb * gb);
+            }
+#pragma unroll
+            for (int pr = 0; pr < 10; ++pr) {
+                const double* G = gM + nodes[ps[pr]] * kMBlock + po[pr] * 9;
+                double s2 = 0.0;
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) s2 += G[r * 3 + q] * al[r][q];
+                const double wa = Wn[pa[pr]], wb = Wn[pb[pr]];
+                const double coef = cM * wa * wb / gb;
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) ga_[r][q] += coef * G[r * 3 + q];
+                gW[pa[pr]] += cM * wb * s2 / gb;
+                gW[pb[pr]] += cM * wa * s2 / gb;
+                ggb -= cM * wa * wb * s2 / (gb * gb);
+            }
+            // Gm = -alpha^T ga_ alpha^T; gradient of a from <Gm, [da]x>
+            double t1[3][3], Gm[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) t1[r][q] = al[0][r] * ga_[0][q] + al[1][r] * ga_[1][q] + al[2][r] * ga_[2][q];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Gm[r][q] = -(t1[r][0] * al[q][0] + t1[r][1] * al[q][1] + t1[r][2] * al[q][2]);
+            const double gav[3] = {Gm[2][1] - Gm[1][2], Gm[0][2] - Gm[2][0], Gm[1][0] - Gm[0][1]};
+            const double gBp[3] = {beta * gav[0] / gb, beta * gav[1] / gb, beta * gav[2] / gb};
+            ggb -= beta * (gav[0] * Bp[0] + gav[1] * Bp[1] + gav[2] * Bp[2]) / (gb * gb);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gu[k] += ggb * u0[k] / gb;
+            const int ic = wrap1(lx ? i - 1 : i, nx), jc = wrap1(ly ? j - 1 : j, ny);
+            const int ic1 = wrap1(ic + 1, nx), jc1 = wrap1(jc + 1, ny);
+            const int64_t cents[4] = {(int64_t)jc * nx + ic, (int64_t)jc * nx + ic1, (int64_t)jc1 * nx + ic,
+                                      (int64_t)jc1 * nx + ic1};
+            double gxp = 0.0, gyp = 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double bg = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    atomicAdd(gB + (int64_t)k * nc + cents[q], Wc[q] * gBp[k]);
+                    bg += Bc[q][k] * gBp[k];
+                }
+                gxp += Wnx[q] * gW[q] + Wcx[q] * bg;
+                gyp += Wny[q] * gW[q] + Wcy[q] * bg;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gu0[3 * (int64_t)p + k] = gu[k];
+            gx0[2 * (int64_t)p] = gxp;
+            gx0[2 * (int64_t)p + 1] = gyp;
+        }
+        __syncwarp();
+    }
+}
+
 int blocks_for(int64_t n, int threads, int cap)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -1374,6 +1526,17 @@ cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int3
 }
 
 template <typename T>
+cudaError_t deposit_adjoint(PArrays<T> src, const int32_t* start, const double* gJ, const double* gM, double* gu0,
+                            double* gx0, double* gB, const T* B, GridP g, SpeciesConst sc, cudaStream_t st)
+{
+    const double beta = sc.q * g.dt / (2.0 * sc.m);
+    count_launches(1);
+    k_deposit_adjoint<T><<<push_grid_blocks(g, sizeof(T) == 4 ? 32 : 64), PushCfg<T>::threads, 0, st>>>(
+        src, start, gJ, gM, gu0, gx0, gB, B, g, beta, sc.q);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t push_adjoint(PArrays<T> src, const int32_t* start, const double* gu1, const double* gx1, double* gu0,
                          double* gx0, double* gE, double* gB, const T* Eth, const T* B, GridP g, SpeciesConst sc,
                          cudaStream_t st)
@@ -1446,6 +1609,9 @@ cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int 
     template cudaError_t push_general<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, const T*, \
                                          const T*, const T*, GridP, SpeciesConst, double*, int,      \
                                          cudaStream_t);                                              \
+    template cudaError_t deposit_adjoint<T>(PArrays<T>, const int32_t*, const double*, const double*, \
+                                            double*, double*, double*, const T*, GridP, SpeciesConst, \
+                                            cudaStream_t);                                            \
     template cudaError_t push_adjoint<T>(PArrays<T>, const int32_t*, const double*, const double*,   \
                                          double*, double*, double*, double*, const T*, const T*,     \
                                          GridP, SpeciesConst, cudaStream_t);                         \

@@ -132,5 +132,5 @@ def test_batch_rejects_bad_arguments(librelsim):
     L.relsim_batch_destroy(None)
     assert L.relsim_field_modes(None, 1, 1, None, 0) == librelsim.RELSIM_ERR_INVALID_ARG
     assert L.relsim_autotune(None, None) == librelsim.RELSIM_ERR_INVALID_ARG
-    assert L.relsim_field_adjoint(None, None, None, None, None, None, None, None, None, 0) == \
+    assert L.relsim_field_adjoint(None, None, None, None, None, None, None, None, None, None, 0) == \
         librelsim.RELSIM_ERR_INVALID_ARG

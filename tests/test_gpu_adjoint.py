@@ -177,3 +177,80 @@ def test_push_adjoint_device_arrays(rs):
     ge = sim.push_adjoint(1, np.zeros((0, 3)), np.zeros((0, 2)))
     assert not np.any(ge["E"]) and not np.any(ge["B"])
     sim.close()
+
+
+def _gpu_state(rs, nx, ny, prec, dt, q, m, seed, tol=None):
+    st = random_state(nx, ny, [8 * nx * ny, 6 * nx * ny], seed=seed, u_scale=1.0, field_scale=0.5, q=q, m=m)
+    cfg = rs.make_config(nx, ny, dt=dt, precision=prec, q=q, m=m, track_ids=True,
+                         gmres_tol=tol or (1e-13 if prec == 64 else 1e-7), gmres_restart=100)
+    sim = rs.Simulation(cfg)
+    sim.load_state(st)
+    sim.build()
+    E0, B0 = sim.fields()
+    parts = [sim.particles(s, ids=True) for s in range(2)]
+    return sim, E0, B0, parts
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_deposit_adjoint_matches_oracle(rs, orc, prec):
+    nx, ny, dt = 17, 9, 0.6
+    q, m = (1.0, -2.0), (1.0, 3.0)
+    sim, E0, B0, parts = _gpu_state(rs, nx, ny, prec, dt, q, m, seed=63)
+    rng = np.random.default_rng(19)
+    gJ = rng.normal(size=(3, nx * ny))
+    gMh = rng.normal(size=(nx * ny, 5, 3, 3))
+    # the oracle's full layout: each stored block's gradient on its (g, g+o) slot
+    gMf = np.zeros((nx * ny, 9, 3, 3))
+    for k, (di, dj) in enumerate(HALF):
+        gMf[:, (dj + 1) * 3 + di + 1] = gMh[:, k]
+    for s in range(2):
+        x, u, w, ids = parts[s]
+        g = sim.deposit_adjoint(s, gJ, gMh)
+        c = orc.make_config(nx, ny, dt=dt, q=(q[s],), m=(m[s],))
+        P = orc.Particles([{"x": x[:, 0], "y": x[:, 1], "ux": u[:, 0], "uy": u[:, 1], "uz": u[:, 2], "w": w}])
+        o = orc.deposit_adjoint(c, P, B0, gJ, gMf)
+        assert rel(g["u"], o["u"].T) < 1e-10
+        assert rel(g["x"], np.stack([o["x"], o["y"]], axis=1)) < 1e-10
+        assert rel(g["B"], o["B"]) < 1e-10
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_one_step_adjoint_chain_matches_oracle(rs, orc, prec):
+    """One full step's gradient on the GPU, chained as the header describes
+    (push adjoints, field adjoint with their dL/dE^{n+theta}, deposit
+    adjoints), against the oracle's step adjoint on the GPU's own state and
+    fields (the oracle's chain is pinned by central differences of its full
+    step). The GPU solves with its FP64 or FP32 operator: FP64 1e-8, FP32
+    2e-4 of the largest entry (the FP32 form's adjoint solve)."""
+    nx, ny, dt = 12, 8, 0.6
+    q, m = (1.0, -1.0), (1.0, 1.0)
+    sim, E0, B0, parts = _gpu_state(rs, nx, ny, prec, dt, q, m, seed=64)
+    Mh, Jh = sim.mass_matrix()
+    sim.solve()
+    rng = np.random.default_rng(21)
+    nn = nx * ny
+    gE1, gB1 = rng.normal(size=(3, nn)), rng.normal(size=(3, nn))
+    gu1 = [rng.normal(size=(len(p[2]), 3)) for p in parts]
+    gx1 = [rng.normal(size=(len(p[2]), 2)) for p in parts]
+    gp = [sim.push_adjoint(s, gu1[s], gx1[s]) for s in range(2)]
+    gEt = gp[0]["E"] + gp[1]["E"]
+    gf = sim.field_adjoint(gE1, gB1, gEt=gEt)
+    gd = [sim.deposit_adjoint(s, gf["J"], gf["M"]) for s in range(2)]
+    gB = gf["B0"] + sum(g["B"] for g in gp) + sum(g["B"] for g in gd)
+    # the oracle on the same particles (both species, GPU order) and fields
+    allp = [{"x": p[0][:, 0], "y": p[0][:, 1], "ux": p[1][:, 0], "uy": p[1][:, 1], "uz": p[1][:, 2], "w": p[2]}
+            for p in parts]
+    c = orc.make_config(nx, ny, dt=dt, q=q, m=m, gmres_tol=1e-14, gmres_restart=200)
+    P = orc.Particles(allp)
+    o = orc.step_adjoint(c, P, E0, B0, np.concatenate(gu1).T, np.concatenate(gx1)[:, 0],
+                         np.concatenate(gx1)[:, 1], gE1, gB1)
+    t = 1e-8 if prec == 64 else 2e-4
+    gu = np.concatenate([gp[s]["u"] + gd[s]["u"] for s in range(2)])
+    gx = np.concatenate([gp[s]["x"] + gd[s]["x"] for s in range(2)])
+    assert rel(gu, o["u"].T) < t
+    assert rel(gx, np.stack([o["x"], o["y"]], axis=1)) < t
+    assert rel(gf["E0"], o["E"]) < t
+    assert rel(gB, o["B"]) < t
+    sim.push()
+    sim.close()

@@ -883,3 +883,54 @@ def test_deposit_adjoint_matches_directional_derivatives(orc):
     def mB(P, Bb, s):
         Bb += s * dB
     assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-6 * np.abs(g["B"] * dB).sum()
+
+
+def test_step_adjoint_matches_directional_derivatives(orc):
+    # one full step (deposit, implicit solve, field update, push) against
+    # central differences of the oracle's own step, in u, x, E and B
+    nx, ny = 6, 5
+    c = cfg_for(orc, nx, ny, dt=0.6, theta=0.5, gmres_tol=1e-14, gmres_restart=200)
+    st = random_state(nx, ny, [40, 30], seed=53, u_scale=1.0, field_scale=0.5)
+    P0 = orc.Particles(st["species"])
+    E0, B0 = st["E"], st["B"]
+    rng = np.random.default_rng(15)
+    N, nn = P0.x.size, nx * ny
+    cu, cx, cy = rng.normal(size=(3, N)), rng.normal(size=N), rng.normal(size=N)
+    cE, cB = rng.normal(size=(3, nn)), rng.normal(size=(3, nn))
+    Lx, Ly = nx * c.dx, ny * c.dy
+
+    def L(P, E, B):
+        P = P.copy()
+        E1, B1, _, _ = orc.step(c, P, E, B)
+        return float(np.sum(cu[0] * P.ux + cu[1] * P.uy + cu[2] * P.uz)
+                     + np.sum(cx * np.sin(2 * np.pi * P.x / Lx)) + np.sum(cy * np.cos(2 * np.pi * P.y / Ly))
+                     + np.sum(cE * E1) + np.sum(cB * B1)), P
+
+    _, P1 = L(P0, E0, B0)
+    gx1 = cx * np.cos(2 * np.pi * P1.x / Lx) * 2 * np.pi / Lx
+    gy1 = -cy * np.sin(2 * np.pi * P1.y / Ly) * 2 * np.pi / Ly
+    g = orc.step_adjoint(c, P0, E0, B0, cu, gx1, gy1, cE, cB)
+    h = 1e-6
+
+    def fd(mod):
+        Pp, Pm = P0.copy(), P0.copy()
+        Ep, Em, Bp_, Bm = E0.copy(), E0.copy(), B0.copy(), B0.copy()
+        mod(Pp, Ep, Bp_, h)
+        mod(Pm, Em, Bm, -h)
+        return (L(Pp, Ep, Bp_)[0] - L(Pm, Em, Bm)[0]) / (2 * h)
+
+    du = rng.normal(size=(3, N))
+    def mu(P, E, B, s):
+        P.ux += s * du[0]; P.uy += s * du[1]; P.uz += s * du[2]
+    assert abs(fd(mu) - np.sum(g["u"] * du)) < 1e-5 * np.abs(g["u"] * du).sum()
+    dx, dy = rng.normal(size=N) * 0.1, rng.normal(size=N) * 0.1
+    def mx(P, E, B, s):
+        P.x += s * dx; P.y += s * dy
+    assert abs(fd(mx) - np.sum(g["x"] * dx + g["y"] * dy)) < 1e-5 * (np.abs(g["x"] * dx).sum() + np.abs(g["y"] * dy).sum())
+    dE, dB = rng.normal(size=E0.shape), rng.normal(size=B0.shape)
+    def mE(P, E, B, s):
+        E += s * dE
+    def mB(P, E, B, s):
+        B += s * dB
+    assert abs(fd(mE) - np.sum(g["E"] * dE)) < 1e-5 * np.abs(g["E"] * dE).sum()
+    assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-5 * np.abs(g["B"] * dB).sum()
