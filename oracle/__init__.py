@@ -18,7 +18,8 @@ __all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "c
            "curl_n", "rhs", "gmres", "field_update", "push", "energies", "cell_keys",
            "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
            "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit", "field_adjoint",
-           "push_adjoint", "deposit_adjoint", "step_adjoint"]
+           "push_adjoint", "deposit_adjoint", "step_adjoint",
+           "mode_energy", "window_gradient"]
 
 
 class OracleConfig(ctypes.Structure):
@@ -590,3 +591,42 @@ def step_adjoint(c, P: Particles, E, B, gu1, gx1, gy1, gE1, gB1):
     gd = deposit_adjoint(c, P, B, gf["J"], gf["M"])
     return {"u": gp["u"] + gd["u"], "x": gp["x"] + gd["x"], "y": gp["y"] + gd["y"],
             "E": gf["E0"], "B": gf["B0"] + gp["B"] + gd["B"], "push": gp, "field": gf, "deposit": gd}
+
+
+def mode_energy(c, B, mode=1, component=1):
+    """Energy of Fourier mode m along x of one B component, and its gradient
+    with respect to B (3, nn): with F_j the DFT of row j (numpy's FFT), the
+    energy (1/2) dV (2/nx) sum_j |F_j|^2 has derivative
+    (2 dV/nx) Re(conj(F_j) exp(-2 pi sqrt(-1) m i/nx)) at cell (i, j)."""
+    nx, ny = c.nx, c.ny
+    dV = c.dx * c.dy
+    Bc = np.asarray(B, dtype=np.float64).reshape(3, ny, nx)[component]
+    F = np.fft.fft(Bc, axis=1)[:, mode]
+    W = 0.5 * dV * (2.0 / nx) * float(np.sum(np.abs(F) ** 2))
+    ph = np.exp(-2j * np.pi * mode * np.arange(nx) / nx)
+    g = np.zeros((3, ny, nx))
+    g[component] = (2.0 * dV / nx) * np.real(np.conj(F)[:, None] * ph[None, :])
+    return W, g.reshape(3, nx * ny)
+
+
+def window_gradient(c, species, E, B, nsteps, mode=1):
+    """Loss = mode_energy of B_y after nsteps oracle steps from the given
+    state, and its gradient with respect to the initial E, B and particles
+    (the oracle keeps the particles' order): the step adjoints chained
+    backwards over the stored start states."""
+    P = Particles(species)
+    E = np.asarray(E, dtype=np.float64).reshape(3, -1).copy()
+    B = np.asarray(B, dtype=np.float64).reshape(3, -1).copy()
+    pres = []
+    for n in range(nsteps):
+        pres.append((P.copy(), E.copy(), B.copy()))
+        E, B, _, _ = step(c, P, E, B)
+    W, gB = mode_energy(c, B, mode)
+    gE = np.zeros_like(E)
+    N = P.x.size
+    gu, gx, gy = np.zeros((3, N)), np.zeros(N), np.zeros(N)
+    for n in range(nsteps - 1, -1, -1):
+        Pn, En, Bn = pres[n]
+        g = step_adjoint(c, Pn, En, Bn, gu, gx, gy, gE, gB)
+        gu, gx, gy, gE, gB = g["u"], g["x"], g["y"], g["E"], g["B"]
+    return W, {"E": gE, "B": gB, "u": gu, "x": gx, "y": gy}

@@ -934,3 +934,29 @@ def test_step_adjoint_matches_directional_derivatives(orc):
         B += s * dB
     assert abs(fd(mE) - np.sum(g["E"] * dE)) < 1e-5 * np.abs(g["E"] * dE).sum()
     assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-5 * np.abs(g["B"] * dB).sum()
+
+
+def test_mode_energy_gradient_and_window_gradient(orc):
+    # the mode energy's gradient by central differences, and a 3-step
+    # window's gradient in E and B by central differences of the oracle's
+    # own steps
+    nx, ny = 6, 4
+    c = cfg_for(orc, nx, ny, dt=0.5, gmres_tol=1e-14, gmres_restart=200)
+    rng = np.random.default_rng(16)
+    B = rng.normal(size=(3, nx * ny))
+    W, g = orc.mode_energy(c, B, 1)
+    assert abs(W - orc.field_modes(c, B, 1, 2)[1]) < 1e-12 * W
+    d = rng.normal(size=B.shape)
+    h = 1e-6
+    fd = (orc.mode_energy(c, B + h * d, 1)[0] - orc.mode_energy(c, B - h * d, 1)[0]) / (2 * h)
+    assert abs(fd - np.sum(g * d)) < 1e-8 * np.abs(g * d).sum()
+    st = random_state(nx, ny, [24, 24], seed=54, u_scale=0.8, field_scale=0.5)
+    W0, gw = orc.window_gradient(c, st["species"], st["E"], st["B"], 3)
+    for name in ("E", "B"):
+        dd = rng.normal(size=st[name].shape)
+        plus, minus = dict(st), dict(st)
+        plus[name] = st[name] + h * dd
+        minus[name] = st[name] - h * dd
+        fd = (orc.window_gradient(c, st["species"], plus["E"], plus["B"], 3)[0]
+              - orc.window_gradient(c, st["species"], minus["E"], minus["B"], 3)[0]) / (2 * h)
+        assert abs(fd - np.sum(gw[name] * dd)) < 1e-5 * np.abs(gw[name] * dd).sum(), name
