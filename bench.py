@@ -619,6 +619,48 @@ def run_scan(args):
         dist.destroy_process_group()
 
 
+def run_window(args):
+    """The differentiable window on a 256x128 double Harris sheet (32 ppc per
+    species, sigma 10, theta_T 0.3): 20 steps with a checkpoint every 5, the
+    loss the k_x = 2 pi/L_x B_y mode energy after the window, its gradient
+    with respect to the initial fields and particles by the chained step
+    adjoints. Times the forward and the backward pass (host orchestration
+    and state transfers included)."""
+    import numpy as np
+    import torch
+    import paper_2509_11100_gb300 as rs
+    from paper_2509_11100_gb300.window import ModeEnergyWindow
+    from relsim_inputs import HarrisConfig, make_harris
+
+    torch.cuda.set_device(rank_info()[2])
+    hc = HarrisConfig(nx=256, ny=128, ppc=32, theta_T=0.3, delta=1.0, sigma=10.0, pert=0.01, dt=0.5)
+    st = make_harris(hc)
+    N = sum(len(s["w"]) for s in st["species"])
+    steps = 20
+    cfg = rs.make_config(hc.nx, hc.ny, dt=hc.dt, precision=32, gmres_tol=1e-7, gmres_restart=60)
+    win = ModeEnergyWindow(cfg, steps, checkpoint_every=5)
+    win.forward(st)   # warm-up (allocations, graph captures)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = win.forward(st)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g = win.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    win.close()
+    out = {"metric": "differentiable window: forward and backward time", "workload":
+           "2D double Harris sheet 256x128, 32 ppc per species (2,097,152 particles), 20 RelSIM steps, "
+           "checkpoint every 5, loss = B_y k_x=1 mode energy after the window, FP32 form",
+           "particles": N, "steps": steps, "loss": L, "forward_s": t1 - t0, "backward_s": t2 - t1,
+           "backward_over_forward": (t2 - t1) / (t1 - t0),
+           "grad_norms": {"E": float(np.linalg.norm(g["E"])), "B": float(np.linalg.norm(g["B"])),
+                          "u": float(sum(np.linalg.norm(p[0]) for p in g["particles"])),
+                          "x": float(sum(np.linalg.norm(p[1]) for p in g["particles"]))},
+           "n_gpus": 1, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def scan_single_reference(rs, torch, sizes=((1024, 512), (768, 384), (128, 64)), steps=20):
     """Single instances with the scan's parameters (32 ppc per species,
     dt = 0.5, delta 1, sigma 10, 0.1% perturbation), graph steps, for scale."""
@@ -658,9 +700,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (no autotuner pass after the load)")
-    ap.add_argument("--workload", choices=["c1", "small", "scan"], default="c1",
+    ap.add_argument("--workload", choices=["c1", "small", "scan", "window"], default="c1",
                     help="small: 512x256 cells for profiler captures; scan: the 48-instance batched "
-                         "tearing scan (run with --steps 400 for its full length)")
+                         "tearing scan (run with --steps 400 for its full length); window: the "
+                         "differentiable 20-step window on 256x128")
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the scan's batch runner")
     ap.add_argument("--scan-reference", action="store_true",
                     help="scan: also time single 1024x512, 768x384 and 128x64 instances with its parameters")
@@ -671,6 +714,8 @@ def main():
         run_reference(args)
     elif args.workload == "scan":
         run_scan(args)
+    elif args.workload == "window":
+        run_window(args)
     else:
         run_ours(args)
 
