@@ -273,6 +273,47 @@ RELSIM_API int relsim_deposit_adjoint(relsim_ctx* ctx, int species, const double
 RELSIM_API int relsim_push_adjoint(relsim_ctx* ctx, int species, const double* gu1, const double* gx1,
                                    double* gu0, double* gx0, double* gE, double* gB, int where);
 
+/* One whole step's adjoint on device memory, in place (base scheme, gbar =
+   gamma(u^n)): the chain rule through the step of Sec. 2 (deposit of the
+   mass matrices and the predicted current, implicit field solve, push).
+   From the state the context holds (loaded or pushed, not yet built) it
+   builds the mass matrix and solves the step forward, then runs the pushes'
+   adjoints (relsim_push_adjoint), the field adjoint with the pushes'
+   dL/dE^{n+theta} (relsim_field_adjoint) and the deposits' adjoints
+   (relsim_deposit_adjoint), and adds up every path. Arguments, all DEVICE
+   memory (FP64):
+     gE, gB   3*ncell each, field layout: on entry dL/dE^{n+1} (nodes) and
+              dL/dB^{n+1} (cell centres), on return dL/dE^n and dL/dB^n;
+     gu[s]    3 n_s, interleaved (ux, uy, uz), and
+     gx[s]    2 n_s, interleaved (x, y), one pair per species s (arrays of
+              nspecies host pointers to device arrays): indexed by the
+              particle's id (track_ids), on entry dL/du^{n+1} and
+              dL/dx^{n+3/2}, on return dL/du^n and dL/dx^{n+1/2}.
+   Ids must be a permutation of 0 .. n_s - 1 (as a load assigns them, or
+   after relsim_relabel_particles with a permutation); with repeated ids the
+   gradients of the colliding particles are undefined (every access stays in
+   bounds). Indexing by id makes the call independent of the order the
+   push's re-sort leaves, so a window of steps chains calls without
+   reordering anything. The context is left solved (relsim_push advances
+   it). *iters, *rel_residual (may be NULL): the adjoint solve. Device
+   scratch of 10 max_s(n_s) + 6*3*ncell + 45*ncell doubles is kept by the
+   context. Synchronises the stream. Errors: INVALID_ARG (a null array,
+   track_ids off, a gamma_pred context), BAD_STATE (not a loaded or pushed
+   state), NOT_CONVERGED (the forward or the adjoint solve; outputs still
+   written), NONFINITE, OOM, CUDA. */
+RELSIM_API int relsim_step_adjoint(relsim_ctx* ctx, double* gE, double* gB, double* const* gu, double* const* gx,
+                                   int* iters, double* rel_residual);
+
+/* Relabel a species' particles (track_ids): each particle carrying id j
+   gets ids[j] (n_s int32, host or device per where). Right after a load
+   the ids are the input indices, so this gives the particle loaded from
+   index i the label ids[i] (e.g. to keep the labels of a state saved with
+   relsim_get_particles). Every carried id and every ids[j] must lie in
+   [0, n_s): checked before anything changes. Synchronises the stream.
+   Errors: INVALID_ARG (species, where, ids not tracked, null ids, a value
+   out of range), CUDA. */
+RELSIM_API int relsim_relabel_particles(relsim_ctx* ctx, int species, const int32_t* ids, int where);
+
 /* E^{n+theta} of the last solve (3*ncell FP64). Errors: BAD_STATE, CUDA. */
 RELSIM_API int relsim_get_E_theta(relsim_ctx* ctx, double* E, int where);
 

@@ -30,7 +30,8 @@ __all__ = [
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
     "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
     "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
-    "relsim_tuning", "relsim_push_adjoint", "relsim_deposit_adjoint",
+    "relsim_tuning", "relsim_push_adjoint", "relsim_deposit_adjoint", "relsim_step_adjoint",
+    "relsim_relabel_particles",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -132,6 +133,9 @@ _SIGS = {
     "relsim_deposit_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int]),
     "relsim_autotune": (ctypes.c_int, [_CTX, _P]),
     "relsim_push_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
+    "relsim_step_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "relsim_relabel_particles": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
 }
 
 PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
@@ -459,6 +463,32 @@ def relsim_push_adjoint(ctx, species, ncell, gu1, gx1, device=False):
     return outs
 
 
+def relsim_step_adjoint(ctx, gE, gB, gu, gx):
+    """One whole step's adjoint in place on CUDA float64 tensors: gE, gB
+    (3, ncell) and per species gu[s] (n_s, 3), gx[s] (n_s, 2) indexed by
+    particle id; dL/d(state after the step) in, dL/d(state before) out.
+    Returns (adjoint iters, relative residual, status)."""
+    items = [_ptr(gE, writable=True), _ptr(gB, writable=True)]
+    pu = [_ptr(a, writable=True) for a in gu]
+    px = [_ptr(a, writable=True) for a in gx]
+    if _where(*(items + pu + px)) != RELSIM_DEVICE:
+        raise ValueError("relsim_step_adjoint takes device arrays only")
+    au = (ctypes.c_void_p * len(pu))(*[p[0] for p in pu])
+    ax = (ctypes.c_void_p * len(px))(*[p[0] for p in px])
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    code = _check(ctx, lib().relsim_step_adjoint(ctx, items[0][0], items[1][0], au, ax, ctypes.byref(it),
+                                                 ctypes.byref(rr)), allow=(RELSIM_ERR_NOT_CONVERGED,))
+    return it.value, rr.value, code
+
+
+def relsim_relabel_particles(ctx, species, ids):
+    """Each particle of the species carrying id j gets ids[j] (int32, host
+    array or CUDA tensor)."""
+    p = _ptr(ids, np.int32)
+    return _check(ctx, lib().relsim_relabel_particles(ctx, species, p[0], p[1]))
+
+
 def relsim_autotune(ctx) -> dict:
     """Time candidate launch shapes of the deposit and the push on the loaded
     state and keep the fastest; returns the candidates and the choice."""
@@ -636,6 +666,12 @@ class Simulation:
 
     def field_adjoint(self, gE1, gB1, mass=True, device=False, gEt=None):
         return relsim_field_adjoint(self.ctx, self.ncell, gE1, gB1, mass, device, gEt)
+
+    def step_adjoint(self, gE, gB, gu, gx):
+        return relsim_step_adjoint(self.ctx, gE, gB, gu, gx)
+
+    def relabel(self, s, ids):
+        return relsim_relabel_particles(self.ctx, s, ids)
 
     def deposit_adjoint(self, s, gJ, gM):
         return relsim_deposit_adjoint(self.ctx, s, self.ncell, gJ, gM)

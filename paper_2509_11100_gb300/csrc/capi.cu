@@ -148,6 +148,8 @@ struct relsim_ctx {
     // staging for host <-> device copies
     double* stage = nullptr;
     int64_t stage_cap = 0;   // doubles
+    double* adj = nullptr;   // scratch of the whole-step adjoint
+    int64_t adj_cap = 0;     // doubles
     int state = kEmpty;
     bool have_step = false;
     int64_t step = 0;
@@ -279,6 +281,16 @@ int ensure_stage(relsim_ctx* c, int64_t ndoubles)
     c->stage_cap = 0;
     TRY(dalloc(c, &c->stage, sizeof(double) * (size_t)ndoubles));
     c->stage_cap = ndoubles;
+    return RELSIM_OK;
+}
+
+int ensure_adj(relsim_ctx* c, int64_t ndoubles)
+{
+    if (ndoubles <= c->adj_cap) return RELSIM_OK;
+    dfree(c->adj);
+    c->adj_cap = 0;
+    TRY(dalloc(c, &c->adj, sizeof(double) * (size_t)ndoubles));
+    c->adj_cap = ndoubles;
     return RELSIM_OK;
 }
 
@@ -1208,6 +1220,80 @@ int push_adjoint_impl(relsim_ctx* c, int s, const double* gu1, const double* gx1
     return RELSIM_OK;
 }
 
+// One whole step's adjoint on the solved step, in place on gradients
+// indexed by particle id: per species the gradients are gathered into the
+// current order, the push adjoint runs (its dL/dE^{n+theta} and dL/dB^n
+// summed over species) and its dL/du^n, dL/dx^{n+1/2} are scattered back;
+// the field adjoint takes the pushes' dL/dE^{n+theta}; the deposit adjoints
+// add their particle terms and dL/dB^n.
+template <typename T>
+int step_adjoint_impl(relsim_ctx* c, double* gE, double* gB, double* const* gu, double* const* gx, int* iters,
+                      double* relres)
+{
+    const int64_t nf = 3 * (int64_t)c->g.ncell, nm = (int64_t)c->g.ncell * kMBlock;
+    int64_t nmax = 0;
+    for (int s = 0; s < c->cfg.nspecies; ++s) nmax = c->sp[s].n > nmax ? c->sp[s].n : nmax;
+    TRY(ensure_adj(c, 10 * nmax + 6 * nf + nm));
+    double* L = c->adj;           // 5 nmax: a species' gradients in its current order
+    double* P = L + 5 * nmax;     // 5 nmax: its push adjoint's dL/du^n, dL/dx^{n+1/2}
+    double* sE = P + 5 * nmax;    // dL/dE^{n+theta} of the pushes
+    double* sB = sE + nf;         // dL/dB^n of the pushes and the deposits
+    double* fE = sB + nf;         // the field adjoint's dL/dE^n, dL/dB^n, dL/dJhat, dL/dM
+    double* fB = fE + nf;
+    double* fJ = fB + nf;
+    double* fM = fJ + nf;
+    const T* Bn = (const T*)c->B[c->bcur];
+    CK(cudaMemsetAsync(sE, 0, sizeof(double) * (size_t)(2 * nf), c->st));
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        Species& sp = c->sp[s];
+        const int64_t n = sp.n;
+        if (n == 0) continue;
+        const PArrays<T> a = arrays<T>(sp, sp.cur);
+        CK(gather_grad(a.id, gu[s], gx[s], L, L + 3 * n, n, c->st));
+        CK(push_adjoint<T>(a, sp.start, L, L + 3 * n, P, P + 3 * n, sE, sB, (const T*)c->Eth, Bn, c->g,
+                           SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st));
+        CK(scatter_grad(a.id, P, P + 3 * n, gu[s], gx[s], n, false, c->st));
+    }
+    const int fr = adjoint_impl<T>(c, gE, gB, sE, fE, fB, fJ, fM, iters, relres, RELSIM_DEVICE);
+    if (fr != RELSIM_OK && fr != RELSIM_ERR_NOT_CONVERGED) return fr;
+    for (int s = 0; s < c->cfg.nspecies; ++s) {
+        Species& sp = c->sp[s];
+        const int64_t n = sp.n;
+        if (n == 0) continue;
+        const PArrays<T> a = arrays<T>(sp, sp.cur);
+        CK(deposit_adjoint<T>(a, sp.start, fJ, fM, L, L + 3 * n, sB, Bn, c->g, SpeciesConst{c->cfg.q[s], c->cfg.m[s]},
+                              c->st));
+        CK(scatter_grad(a.id, L, L + 3 * n, gu[s], gx[s], n, true, c->st));
+    }
+    CK(cudaMemcpyAsync(gE, fE, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToDevice, c->st));
+    CK(add_fields(fB, sB, gB, nf, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return fr;
+}
+
+// each carried id j of a species becomes ids[j] (range-checked first)
+int relabel_impl(relsim_ctx* c, int s, const int32_t* ids, int where)
+{
+    Species& sp = c->sp[s];
+    const int64_t n = sp.n;
+    if (n == 0) return RELSIM_OK;
+    const int32_t* d = ids;
+    if (where == RELSIM_HOST) {
+        TRY(ensure_adj(c, (n + 1) / 2));
+        CK(cudaMemcpyAsync(c->adj, ids, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->st));
+        d = (const int32_t*)c->adj;
+    }
+    int32_t* id = sp.id[sp.cur];
+    CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
+    CK(check_ids(id, d, n, c->dflag, c->st));
+    CK(cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (*c->hflag & 1) return fail(c, RELSIM_ERR_INVALID_ARG, "an id or a new label is outside [0, %lld)", (long long)n);
+    CK(relabel_ids(id, d, n, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return RELSIM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // graph steps enqueued back to back (the batch runner): both layouts are
 // captured up front, each step is one graph launch on the context's stream
@@ -1585,7 +1671,7 @@ void relsim_destroy(relsim_ctx* c)
     }
     dfree(c->rtmp);
     dfree(c->V); dfree(c->gw); dfree(c->gw2); dfree(c->gx); dfree(c->gb); dfree(c->partial);
-    dfree(c->dsum); dfree(c->dled); dfree(c->dflag); dfree(c->dpush); dfree(c->stage);
+    dfree(c->dsum); dfree(c->dled); dfree(c->dflag); dfree(c->dpush); dfree(c->stage); dfree(c->adj);
     dfree(c->spec_w); dfree(c->spec_c); dfree(c->spec_e);
     dfree(c->mode_tw); dfree(c->mode_rows);
     dfree(c->gms);
@@ -1786,6 +1872,36 @@ int relsim_push_adjoint(relsim_ctx* c, int species, const double* gu1, const dou
     if (c->En) return fail(c, RELSIM_ERR_INVALID_ARG, "the push adjoint covers the base scheme (gamma_pred = 0)");
     if (c->state != kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "the push adjoint needs a solved step (before the push)");
     return DISPATCH(push_adjoint_impl, c, species, gu1, gx1, gu0, gx0, gE, gB, where);
+}
+
+int relsim_step_adjoint(relsim_ctx* c, double* gE, double* gB, double* const* gu, double* const* gx, int* iters,
+                        double* rel_residual)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (!gE || !gB || !gu || !gx) return fail(c, RELSIM_ERR_INVALID_ARG, "null array");
+    for (int s = 0; s < c->cfg.nspecies; ++s)
+        if (c->sp[s].n > 0 && (!gu[s] || !gx[s])) return fail(c, RELSIM_ERR_INVALID_ARG, "null particle gradient");
+    if (!c->cfg.track_ids) return fail(c, RELSIM_ERR_INVALID_ARG, "the step adjoint needs track_ids");
+    if (c->En) return fail(c, RELSIM_ERR_INVALID_ARG, "the step adjoint covers the base scheme (gamma_pred = 0)");
+    if (c->state != kReady) return fail(c, RELSIM_ERR_BAD_STATE, "the step adjoint needs a loaded or pushed state");
+    int r = relsim_build_mass_matrix(c);
+    if (r != RELSIM_OK) return r;
+    const int fs = relsim_field_solve(c, nullptr, nullptr);
+    if (fs != RELSIM_OK && fs != RELSIM_ERR_NOT_CONVERGED) return fs;
+    r = DISPATCH(step_adjoint_impl, c, gE, gB, gu, gx, iters, rel_residual);
+    if (r == RELSIM_OK && fs == RELSIM_ERR_NOT_CONVERGED)
+        r = fail(c, RELSIM_ERR_NOT_CONVERGED, "the step's forward solve did not converge");
+    return r;
+}
+
+int relsim_relabel_particles(relsim_ctx* c, int species, const int32_t* ids, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (species < 0 || species >= c->cfg.nspecies) return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    if (!c->cfg.track_ids) return fail(c, RELSIM_ERR_INVALID_ARG, "ids are not tracked");
+    if (c->sp[species].n > 0 && !ids) return fail(c, RELSIM_ERR_INVALID_ARG, "null ids");
+    return relabel_impl(c, species, ids, where);
 }
 
 int relsim_field_adjoint(relsim_ctx* c, const double* gE1, const double* gB1, const double* gEt, double* gE0,

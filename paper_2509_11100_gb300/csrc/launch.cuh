@@ -64,6 +64,20 @@ cudaError_t histogram_keys(const int32_t* keys, int64_t n, int32_t* counts, int 
 cudaError_t move_counts(const int32_t* n9, int32_t* count_new, GridP g, cudaStream_t st);
 cudaError_t iota_i32(int32_t* a, int64_t n, cudaStream_t st);
 
+// ----- adjoint.cu -----
+// lu[i] = gu[id[i]], lx[i] = gx[id[i]] (FP64, 3 and 2 interleaved components)
+cudaError_t gather_grad(const int32_t* id, const double* gu, const double* gx, double* lu, double* lx, int64_t n,
+                        cudaStream_t st);
+// gu[id[i]] = lu[i], gx[id[i]] = lx[i] (or += with add)
+cudaError_t scatter_grad(const int32_t* id, const double* lu, const double* lx, double* gu, double* gx, int64_t n,
+                         bool add, cudaStream_t st);
+// bit 0 of *bad if id[i] or ids[i] is outside [0, n) (flag accumulates)
+cudaError_t check_ids(const int32_t* id, const int32_t* ids, int64_t n, int* bad, cudaStream_t st);
+// id[i] = ids[id[i]]
+cudaError_t relabel_ids(int32_t* id, const int32_t* ids, int64_t n, cudaStream_t st);
+// out = a + b (FP64)
+cudaError_t add_fields(const double* a, const double* b, double* out, int64_t n, cudaStream_t st);
+
 // ----- particles.cu -----
 // bit 2 of *flag if keys[0..n) is not non-decreasing (flag accumulates)
 cudaError_t keys_unsorted(const int32_t* keys, int64_t n, int* flag, cudaStream_t st);

@@ -1146,21 +1146,96 @@ k_spectrum(PArrays<T> pa, int64_t n, int variable, const T* __restrict__ edges, 
         }
 }
 
+// Segmented sums across a warp for the adjoints' scatters. In one pass of a
+// unit the lanes hold consecutive particles, so their cells ascend and the
+// lanes of one cell are consecutive: a suffix sum over those runs (five
+// shuffle steps) leaves each run's total in its first lane, which alone
+// issues the FP64 atomics. This replaces one global atomic per lane and
+// target by one per cell and target.
+struct Runs {
+    unsigned same;   // bit s: lane + 2^s < 32 holds the same key
+    bool head;       // first lane of its run
+};
+
+__device__ __forceinline__ Runs runs_of(int key, int lane)
+{
+    Runs r;
+    r.same = 0u;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 1 << s;
+        const int ko = __shfl_down_sync(0xffffffffu, key, d);
+        if (lane + d < 32 && ko == key) r.same |= 1u << s;
+    }
+    const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+    r.head = lane == 0 || kp != key;
+    return r;
+}
+
+template <typename A>
+__device__ __forceinline__ A run_sum(A v, const Runs& r)
+{
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const A o = __shfl_down_sync(0xffffffffu, v, 1 << s);
+        if ((r.same >> s) & 1u) v += o;
+    }
+    return v;
+}
+
+// The 3x3 cell centres around cell (i, j) (tile rows j-1..j+1, columns
+// i-1..i+1): a particle's four centre weights Wc as separable factors
+// Ry[r] Cx[c], zero outside its 2x2 (rows 0-1 when fy < 1/2, else 1-2;
+// likewise the columns).
+template <typename A>
+__device__ __forceinline__ void centre_factors(bool lx, bool ly, A tx, A ty, A (&Cx)[3], A (&Ry)[3])
+{
+    Cx[0] = lx ? A(1) - tx : A(0);
+    Cx[1] = lx ? tx : A(1) - tx;
+    Cx[2] = lx ? A(0) : tx;
+    Ry[0] = ly ? A(1) - ty : A(0);
+    Ry[1] = ly ? ty : A(1) - ty;
+    Ry[2] = ly ? A(0) : ty;
+}
+
+// the run totals of a 3x3 centre scatter (3 components) added to gB
+template <typename A>
+__device__ __forceinline__ void flush_centres(const A (&gc)[3][3][3], const Runs& rn, bool act, double* gB, int i,
+                                              int j, int nx, int ny, int nc)
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int gj = wrap1(j - 1 + r, ny);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int64_t cell = (int64_t)gj * nx + wrap1(i - 1 + c, nx);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const A s = run_sum(gc[k][r][c], rn);
+                if (rn.head && act) atomicAdd(gB + (int64_t)k * nc + cell, (double)s);
+            }
+        }
+    }
+}
+
 // Adjoint of the push with the fields held fixed (base scheme, gbar =
-// gamma(u^n)): per particle, the push is replayed in FP64 from the stored
-// values and the chain rule run in reverse. The gathers' transposes are
-// scatters with the same weights (FP64 atomics into gE on the nodes and gB
-// on the centres); alpha's transpose is applied to the gradient of ubar, and
-// d alpha = -alpha d[a]x alpha gives the gradient of a = beta B/gbar. gu1,
-// gx1 are dL/du^{n+1}, dL/dx^{n+3/2} (interleaved, in the particles' current
-// order); gu0, gx0 receive dL/du^n, dL/dx^{n+1/2}.
+// gamma(u^n)): per particle, the push is replayed from the stored values in
+// the form's precision (FP32 for the FP32 form: GB300's FP64 rate is a
+// small fraction of its FP32 rate) and the chain rule run in reverse. The
+// gathers' transposes are scatters with the same weights into gE on the
+// nodes and gB on the centres, summed per cell across the warp and added
+// with FP64 atomics; alpha's transpose is applied to the gradient of ubar,
+// and d alpha = -alpha d[a]x alpha gives the gradient of a = beta B/gbar.
+// gu1, gx1 are dL/du^{n+1}, dL/dx^{n+3/2} (FP64, interleaved, in the
+// particles' current order); gu0, gx0 receive dL/du^n, dL/dx^{n+1/2}.
 template <typename T>
 __global__ void __launch_bounds__(PushCfg<T>::threads)
 k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gu1,
                const double* __restrict__ gx1, double* __restrict__ gu0, double* __restrict__ gx0,
                double* __restrict__ gE, double* __restrict__ gB, const T* __restrict__ Eth,
-               const T* __restrict__ B, GridP g, double beta)
+               const T* __restrict__ B, GridP g, double beta_d)
 {
+    using A = T;
     constexpr int W = PushCfg<T>::warps;
     __shared__ int sstart[W][kUnitW + 1];
     __shared__ PushTile<T> stile[W];
@@ -1171,134 +1246,165 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
     const int nunits = units_of(nx, ny);
     int* ss = sstart[wib];
     PushTile<T>& tl = stile[wib];
-    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy, dt = g.dt;
+    const A rdx = A(1.0 / g.dx), rdy = A(1.0 / g.dy), dt = A(g.dt), beta = A(beta_d);
     for (int u = warp; u < nunits; u += nwarps) {
         const Unit un = unit_of(u, nx);
         unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
         const int P0 = ss[0], P1 = ss[un.cn];
         int cl = 0;
-        for (int p = P0 + lane; p < P1; p += 32) {
-            while (ss[cl + 1] <= p) ++cl;
-            const double fx = (double)ld(src.fx + p), fy = (double)ld(src.fy + p);
-            const double u0[3] = {(double)ld(src.ux + p), (double)ld(src.uy + p), (double)ld(src.uz + p)};
-            // node weights and their derivatives in x, y
-            const double X0 = 1.0 - fx, Y0 = 1.0 - fy;
-            const double Wn[4] = {X0 * Y0, fx * Y0, X0 * fy, fx * fy};
-            const double Wnx[4] = {-Y0 * rdx, Y0 * rdx, -fy * rdx, fy * rdx};
-            const double Wny[4] = {-X0 * rdy, -fx * rdy, X0 * rdy, fx * rdy};
-            double En[4][3];
+        for (int p0 = P0; p0 < P1; p0 += 32) {
+            const int p = p0 + lane;
+            const bool act = p < P1;
+            if (act)
+                while (ss[cl + 1] <= p) ++cl;
+            A gn[4][3], gc[3][3][3];   // this lane's node and centre scatters
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                En[0][k] = (double)tl.E[k][0][cl];
-                En[1][k] = (double)tl.E[k][0][cl + 1];
-                En[2][k] = (double)tl.E[k][1][cl];
-                En[3][k] = (double)tl.E[k][1][cl + 1];
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gn[q][k] = A(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) gc[k][r][c] = A(0);
+            if (act) {
+                const A fx = ld(src.fx + p), fy = ld(src.fy + p);
+                const A u0[3] = {ld(src.ux + p), ld(src.uy + p), ld(src.uz + p)};
+                // node weights and their derivatives in x, y
+                const A X0 = A(1) - fx, Y0 = A(1) - fy;
+                const A Wn[4] = {X0 * Y0, fx * Y0, X0 * fy, fx * fy};
+                const A Wnx[4] = {-Y0 * rdx, Y0 * rdx, -fy * rdx, fy * rdx};
+                const A Wny[4] = {-X0 * rdy, -fx * rdy, X0 * rdy, fx * rdy};
+                A En[4][3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    En[0][k] = tl.E[k][0][cl];
+                    En[1][k] = tl.E[k][0][cl + 1];
+                    En[2][k] = tl.E[k][1][cl];
+                    En[3][k] = tl.E[k][1][cl + 1];
+                }
+                // centre weights (the two centres below or above the offset)
+                const bool lx = fx < A(0.5), ly = fy < A(0.5);
+                const A tx = lx ? fx + A(0.5) : fx - A(0.5), ty = ly ? fy + A(0.5) : fy - A(0.5);
+                const int c0 = lx ? cl : cl + 1, r0 = ly ? 0 : 1;
+                const A Wc[4] = {(A(1) - tx) * (A(1) - ty), tx * (A(1) - ty), (A(1) - tx) * ty, tx * ty};
+                const A Wcx[4] = {-(A(1) - ty) * rdx, (A(1) - ty) * rdx, -ty * rdx, ty * rdx};
+                const A Wcy[4] = {-(A(1) - tx) * rdy, -tx * rdy, (A(1) - tx) * rdy, tx * rdy};
+                A Bc[4][3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    Bc[0][k] = tl.B[k][r0][c0];
+                    Bc[1][k] = tl.B[k][r0][c0 + 1];
+                    Bc[2][k] = tl.B[k][r0 + 1][c0];
+                    Bc[3][k] = tl.B[k][r0 + 1][c0 + 1];
+                }
+                A Ep[3], Bp[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    Ep[k] = Wn[0] * En[0][k] + Wn[1] * En[1][k] + Wn[2] * En[2][k] + Wn[3] * En[3][k];
+                    Bp[k] = Wc[0] * Bc[0][k] + Wc[1] * Bc[1][k] + Wc[2] * Bc[2][k] + Wc[3] * Bc[3][k];
+                }
+                // forward replay
+                const A gb = sqrt(A(1) + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+                const A a[3] = {beta * Bp[0] / gb, beta * Bp[1] / gb, beta * Bp[2] / gb};
+                const A ia = A(1) / (A(1) + a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+                // alpha = (I - [a]x + a a^T)/(1 + |a|^2) = (I + [a]x)^{-1}
+                A al[3][3];
+                al[0][0] = (A(1) + a[0] * a[0]) * ia; al[0][1] = (a[0] * a[1] + a[2]) * ia; al[0][2] = (a[0] * a[2] - a[1]) * ia;
+                al[1][0] = (a[0] * a[1] - a[2]) * ia; al[1][1] = (A(1) + a[1] * a[1]) * ia; al[1][2] = (a[1] * a[2] + a[0]) * ia;
+                al[2][0] = (a[0] * a[2] + a[1]) * ia; al[2][1] = (a[1] * a[2] - a[0]) * ia; al[2][2] = (A(1) + a[2] * a[2]) * ia;
+                A w[3], ub[3], u1[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) w[k] = u0[k] + beta * Ep[k];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) ub[r] = al[r][0] * w[0] + al[r][1] * w[1] + al[r][2] * w[2];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) u1[k] = A(2) * ub[k] - u0[k];
+                const A g1 = sqrt(A(1) + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+                // backward: x1 = x + dt u1/g1
+                const A gp[3] = {(A)gx1[2 * (int64_t)p], (A)gx1[2 * (int64_t)p + 1], A(0)};
+                const A up = u1[0] * gp[0] + u1[1] * gp[1];
+                A gt[3], gub[3], gu[3], gw[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    gt[k] = (A)gu1[3 * (int64_t)p + k] + dt * (gp[k] / g1 - u1[k] * up / (g1 * g1 * g1));
+                    gub[k] = A(2) * gt[k];
+                    gu[k] = -gt[k];
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gw[k] = al[0][k] * gub[0] + al[1][k] * gub[1] + al[2][k] * gub[2];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gu[k] += gw[k];
+                // G = -alpha^T (gub w^T) alpha^T = -(alpha^T gub)(alpha w)^T = -gw ub^T
+                // (the outer product factorises); ga from <G, [da]x>
+                const A ga[3] = {-(gw[2] * ub[1] - gw[1] * ub[2]), -(gw[0] * ub[2] - gw[2] * ub[0]),
+                                 -(gw[1] * ub[0] - gw[0] * ub[1])};
+                const A gBp[3] = {beta * ga[0] / gb, beta * ga[1] / gb, beta * ga[2] / gb};
+                const A ggb = -beta * (ga[0] * Bp[0] + ga[1] * Bp[1] + ga[2] * Bp[2]) / (gb * gb);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gu[k] += ggb * u0[k] / gb;
+                const A gEp[3] = {beta * gw[0], beta * gw[1], beta * gw[2]};
+                A gxp = gp[0], gyp = gp[1];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    A eg = A(0), bg = A(0);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        gn[q][k] = Wn[q] * gEp[k];
+                        eg += En[q][k] * gEp[k];
+                        bg += Bc[q][k] * gBp[k];
+                    }
+                    gxp += Wnx[q] * eg + Wcx[q] * bg;
+                    gyp += Wny[q] * eg + Wcy[q] * bg;
+                }
+                A Cx[3], Ry[3];
+                centre_factors(lx, ly, tx, ty, Cx, Ry);
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) gc[k][r][c] = Ry[r] * Cx[c] * gBp[k];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gu0[3 * (int64_t)p + k] = (double)gu[k];
+                gx0[2 * (int64_t)p] = (double)gxp;
+                gx0[2 * (int64_t)p + 1] = (double)gyp;
             }
-            // centre weights (the two centres below or above the offset)
-            const bool lx = fx < 0.5, ly = fy < 0.5;
-            const double tx = lx ? fx + 0.5 : fx - 0.5, ty = ly ? fy + 0.5 : fy - 0.5;
-            const int c0 = lx ? cl : cl + 1, r0 = ly ? 0 : 1;
-            const double Wc[4] = {(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
-            const double Wcx[4] = {-(1.0 - ty) * rdx, (1.0 - ty) * rdx, -ty * rdx, ty * rdx};
-            const double Wcy[4] = {-(1.0 - tx) * rdy, -tx * rdy, (1.0 - tx) * rdy, tx * rdy};
-            double Bc[4][3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                Bc[0][k] = (double)tl.B[k][r0][c0];
-                Bc[1][k] = (double)tl.B[k][r0][c0 + 1];
-                Bc[2][k] = (double)tl.B[k][r0 + 1][c0];
-                Bc[3][k] = (double)tl.B[k][r0 + 1][c0 + 1];
-            }
-            double Ep[3], Bp[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                Ep[k] = Wn[0] * En[0][k] + Wn[1] * En[1][k] + Wn[2] * En[2][k] + Wn[3] * En[3][k];
-                Bp[k] = Wc[0] * Bc[0][k] + Wc[1] * Bc[1][k] + Wc[2] * Bc[2][k] + Wc[3] * Bc[3][k];
-            }
-            // forward replay
-            const double gb = sqrt(1.0 + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
-            const double a[3] = {beta * Bp[0] / gb, beta * Bp[1] / gb, beta * Bp[2] / gb};
-            const double ia = 1.0 / (1.0 + a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-            // alpha = (I - [a]x + a a^T)/(1 + |a|^2) = (I + [a]x)^{-1}
-            double al[3][3];
-            al[0][0] = (1.0 + a[0] * a[0]) * ia; al[0][1] = (a[0] * a[1] + a[2]) * ia; al[0][2] = (a[0] * a[2] - a[1]) * ia;
-            al[1][0] = (a[0] * a[1] - a[2]) * ia; al[1][1] = (1.0 + a[1] * a[1]) * ia; al[1][2] = (a[1] * a[2] + a[0]) * ia;
-            al[2][0] = (a[0] * a[2] + a[1]) * ia; al[2][1] = (a[1] * a[2] - a[0]) * ia; al[2][2] = (1.0 + a[2] * a[2]) * ia;
-            double w[3], ub[3], u1[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) w[k] = u0[k] + beta * Ep[k];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) ub[r] = al[r][0] * w[0] + al[r][1] * w[1] + al[r][2] * w[2];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) u1[k] = 2.0 * ub[k] - u0[k];
-            const double g1 = sqrt(1.0 + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
-            // backward: x1 = x + dt u1/g1
-            const double gp[3] = {gx1[2 * (int64_t)p], gx1[2 * (int64_t)p + 1], 0.0};
-            const double up = u1[0] * gp[0] + u1[1] * gp[1];
-            double gt[3], gub[3], gu[3], gw[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                gt[k] = gu1[3 * (int64_t)p + k] + dt * (gp[k] / g1 - u1[k] * up / (g1 * g1 * g1));
-                gub[k] = 2.0 * gt[k];
-                gu[k] = -gt[k];
-            }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gw[k] = al[0][k] * gub[0] + al[1][k] * gub[1] + al[2][k] * gub[2];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gu[k] += gw[k];
-            // G = -alpha^T (gub w^T) alpha^T = -(alpha^T gub)(alpha w)^T = -gw ub^T
-            // (the outer product factorises); ga from <G, [da]x>
-            const double ga[3] = {-(gw[2] * ub[1] - gw[1] * ub[2]), -(gw[0] * ub[2] - gw[2] * ub[0]),
-                                  -(gw[1] * ub[0] - gw[0] * ub[1])};
-            const double gBp[3] = {beta * ga[0] / gb, beta * ga[1] / gb, beta * ga[2] / gb};
-            const double ggb = -beta * (ga[0] * Bp[0] + ga[1] * Bp[1] + ga[2] * Bp[2]) / (gb * gb);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gu[k] += ggb * u0[k] / gb;
-            const double gEp[3] = {beta * gw[0], beta * gw[1], beta * gw[2]};
-            double gxp = gp[0], gyp = gp[1];
+            // the cell runs' totals: nodes (i, j), (i+1, j), (i, j+1), (i+1, j+1)
+            const Runs rn = runs_of(act ? cl : -1, lane);
             const int i = un.i0 + cl, j = un.j;
             const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
             const int64_t nodes[4] = {(int64_t)j * nx + i, (int64_t)j * nx + i1, (int64_t)j1 * nx + i,
                                       (int64_t)j1 * nx + i1};
-            const int ic = wrap1(lx ? i - 1 : i, nx), jc = wrap1(ly ? j - 1 : j, ny);
-            const int ic1 = wrap1(ic + 1, nx), jc1 = wrap1(jc + 1, ny);
-            const int64_t cents[4] = {(int64_t)jc * nx + ic, (int64_t)jc * nx + ic1, (int64_t)jc1 * nx + ic,
-                                      (int64_t)jc1 * nx + ic1};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                double eg = 0.0, bg = 0.0;
+            for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    atomicAdd(gE + (int64_t)k * nc + nodes[q], Wn[q] * gEp[k]);
-                    atomicAdd(gB + (int64_t)k * nc + cents[q], Wc[q] * gBp[k]);
-                    eg += En[q][k] * gEp[k];
-                    bg += Bc[q][k] * gBp[k];
+                    const A s = run_sum(gn[q][k], rn);
+                    if (rn.head && act) atomicAdd(gE + (int64_t)k * nc + nodes[q], (double)s);
                 }
-                gxp += Wnx[q] * eg + Wcx[q] * bg;
-                gyp += Wny[q] * eg + Wcy[q] * bg;
-            }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gu0[3 * (int64_t)p + k] = gu[k];
-            gx0[2 * (int64_t)p] = gxp;
-            gx0[2 * (int64_t)p + 1] = gyp;
+            flush_centres(gc, rn, act, gB, i, j, nx, ny, nc);
         }
         __syncwarp();
     }
 }
 
 // Adjoint of the deposit (base scheme): per particle, alpha, gbar and the
-// shape weights are rebuilt in FP64 from the stored values; the gradient of
-// alpha collects the predicted current's (gJ at the cell's 4 nodes) and the
-// 10 node pairs' stored mass-matrix block gradients (gM, ncell x 45), then
-// flows through a = beta B/gbar to B (FP64 atomic scatter on the centres) and
-// gbar; the weights' derivatives give dL/dx. Outputs per particle dL/du^n
-// (gu0, interleaved) and dL/dx^{n+1/2} (gx0).
+// shape weights are rebuilt from the stored values in the form's precision;
+// the gradient of alpha collects the predicted current's (gJ at the cell's
+// 4 nodes) and the 10 node pairs' stored mass-matrix block gradients (gM,
+// ncell x 45), then flows through a = beta B/gbar to B (summed per cell
+// across the warp, FP64 atomics on the centres) and gbar; the weights'
+// derivatives give dL/dx. Outputs per particle dL/du^n (gu0, interleaved)
+// and dL/dx^{n+1/2} (gx0), FP64.
 template <typename T>
 __global__ void __launch_bounds__(PushCfg<T>::threads)
 k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gJ,
                   const double* __restrict__ gM, double* __restrict__ gu0, double* __restrict__ gx0,
-                  double* __restrict__ gB, const T* __restrict__ B, GridP g, double beta, double cq)
+                  double* __restrict__ gB, const T* __restrict__ B, GridP g, double beta_d, double cq)
 {
+    using A = T;
     constexpr int W = PushCfg<T>::warps;
     __shared__ int sstart[W][kUnitW + 1];
     __shared__ PushTile<T> stile[W];
@@ -1309,7 +1415,8 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
     const int nunits = units_of(nx, ny);
     int* ss = sstart[wib];
     PushTile<T>& tl = stile[wib];
-    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+    const A rdx = A(1.0 / g.dx), rdy = A(1.0 / g.dy), beta = A(beta_d);
+    const A cJ0 = A(cq / g.dV), cM0 = A(cq * beta_d / g.dV);
     // the cell's node pairs: (node a, node b, storing node, half offset)
     constexpr int pa[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
     constexpr int pb[10] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
@@ -1320,119 +1427,143 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
         unit_setup<T>(un, start, ss, tl, B, B, nx, ny, nc, lane);
         const int P0 = ss[0], P1 = ss[un.cn];
         int cl = 0;
-        for (int p = P0 + lane; p < P1; p += 32) {
-            while (ss[cl + 1] <= p) ++cl;
-            const double fx = (double)ld(src.fx + p), fy = (double)ld(src.fy + p);
-            const double u0[3] = {(double)ld(src.ux + p), (double)ld(src.uy + p), (double)ld(src.uz + p)};
-            const double wt = (double)ld(src.w + p);
-            const double X0 = 1.0 - fx, Y0 = 1.0 - fy;
-            const double Wn[4] = {X0 * Y0, fx * Y0, X0 * fy, fx * fy};
-            const double Wnx[4] = {-Y0 * rdx, Y0 * rdx, -fy * rdx, fy * rdx};
-            const double Wny[4] = {-X0 * rdy, -fx * rdy, X0 * rdy, fx * rdy};
-            const bool lx = fx < 0.5, ly = fy < 0.5;
-            const double tx = lx ? fx + 0.5 : fx - 0.5, ty = ly ? fy + 0.5 : fy - 0.5;
-            const int c0 = lx ? cl : cl + 1, r0 = ly ? 0 : 1;
-            const double Wc[4] = {(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
-            const double Wcx[4] = {-(1.0 - ty) * rdx, (1.0 - ty) * rdx, -ty * rdx, ty * rdx};
-            const double Wcy[4] = {-(1.0 - tx) * rdy, -tx * rdy, (1.0 - tx) * rdy, tx * rdy};
-            double Bc[4][3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                Bc[0][k] = (double)tl.B[k][r0][c0];
-                Bc[1][k] = (double)tl.B[k][r0][c0 + 1];
-                Bc[2][k] = (double)tl.B[k][r0 + 1][c0];
-                Bc[3][k] = (double)tl.B[k][r0 + 1][c0 + 1];
-            }
-            double Bp[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) Bp[k] = Wc[0] * Bc[0][k] + Wc[1] * Bc[1][k] + Wc[2] * Bc[2][k] + Wc[3] * Bc[3][k];
-            const double gb = sqrt(1.0 + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
-            const double a[3] = {beta * Bp[0] / gb, beta * Bp[1] / gb, beta * Bp[2] / gb};
-            const double ia = 1.0 / (1.0 + a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-            double al[3][3];
-            al[0][0] = (1.0 + a[0] * a[0]) * ia; al[0][1] = (a[0] * a[1] + a[2]) * ia; al[0][2] = (a[0] * a[2] - a[1]) * ia;
-            al[1][0] = (a[0] * a[1] - a[2]) * ia; al[1][1] = (1.0 + a[1] * a[1]) * ia; al[1][2] = (a[1] * a[2] + a[0]) * ia;
-            al[2][0] = (a[0] * a[2] + a[1]) * ia; al[2][1] = (a[1] * a[2] - a[0]) * ia; al[2][2] = (1.0 + a[2] * a[2]) * ia;
-            double au[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) au[r] = al[r][0] * u0[0] + al[r][1] * u0[1] + al[r][2] * u0[2];
-            const double cJ = wt * cq / g.dV, cM = wt * cq * beta / g.dV;
+        for (int p0 = P0; p0 < P1; p0 += 32) {
+            const int p = p0 + lane;
+            const bool act = p < P1;
+            if (act)
+                while (ss[cl + 1] <= p) ++cl;
             const int i = un.i0 + cl, j = un.j;
-            const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
-            const int64_t nodes[4] = {(int64_t)j * nx + i, (int64_t)j * nx + i1, (int64_t)j1 * nx + i,
-                                      (int64_t)j1 * nx + i1};
-            double ga_[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // dL/dalpha
-            double gW[4] = {0, 0, 0, 0}, ggb = 0.0, gu[3] = {0, 0, 0};
+            A gc[3][3][3];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const double gj[3] = {gJ[nodes[k]], gJ[nc + nodes[k]], gJ[2 * (int64_t)nc + nodes[k]]};
-                const double f = cJ * Wn[k] / gb;
-                double sJ = 0.0;
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    sJ += gj[r] * au[r];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        ga_[r][q] += f * gj[r] * u0[q];
-                        gu[q] += f * al[r][q] * gj[r];
-                    }
-                }
-                gW[k] += cJ * sJ / gb;
-                ggb -= cJ * Wn[k] * sJ / (gb * gb);
-            }
-#pragma unroll
-            for (int pr = 0; pr < 10; ++pr) {
-                const double* G = gM + nodes[ps[pr]] * kMBlock + po[pr] * 9;
-                double s2 = 0.0;
+            for (int k = 0; k < 3; ++k)
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) s2 += G[r * 3 + q] * al[r][q];
-                const double wa = Wn[pa[pr]], wb = Wn[pb[pr]];
-                const double coef = cM * wa * wb / gb;
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) ga_[r][q] += coef * G[r * 3 + q];
-                gW[pa[pr]] += cM * wb * s2 / gb;
-                gW[pb[pr]] += cM * wa * s2 / gb;
-                ggb -= cM * wa * wb * s2 / (gb * gb);
-            }
-            // Gm = -alpha^T ga_ alpha^T; gradient of a from <Gm, [da]x>
-            double t1[3][3], Gm[3][3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) t1[r][q] = al[0][r] * ga_[0][q] + al[1][r] * ga_[1][q] + al[2][r] * ga_[2][q];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) Gm[r][q] = -(t1[r][0] * al[q][0] + t1[r][1] * al[q][1] + t1[r][2] * al[q][2]);
-            const double gav[3] = {Gm[2][1] - Gm[1][2], Gm[0][2] - Gm[2][0], Gm[1][0] - Gm[0][1]};
-            const double gBp[3] = {beta * gav[0] / gb, beta * gav[1] / gb, beta * gav[2] / gb};
-            ggb -= beta * (gav[0] * Bp[0] + gav[1] * Bp[1] + gav[2] * Bp[2]) / (gb * gb);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gu[k] += ggb * u0[k] / gb;
-            const int ic = wrap1(lx ? i - 1 : i, nx), jc = wrap1(ly ? j - 1 : j, ny);
-            const int ic1 = wrap1(ic + 1, nx), jc1 = wrap1(jc + 1, ny);
-            const int64_t cents[4] = {(int64_t)jc * nx + ic, (int64_t)jc * nx + ic1, (int64_t)jc1 * nx + ic,
-                                      (int64_t)jc1 * nx + ic1};
-            double gxp = 0.0, gyp = 0.0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                double bg = 0.0;
+                    for (int c = 0; c < 3; ++c) gc[k][r][c] = A(0);
+            if (act) {
+                const A fx = ld(src.fx + p), fy = ld(src.fy + p);
+                const A u0[3] = {ld(src.ux + p), ld(src.uy + p), ld(src.uz + p)};
+                const A wt = ld(src.w + p);
+                const A X0 = A(1) - fx, Y0 = A(1) - fy;
+                const A Wn[4] = {X0 * Y0, fx * Y0, X0 * fy, fx * fy};
+                const A Wnx[4] = {-Y0 * rdx, Y0 * rdx, -fy * rdx, fy * rdx};
+                const A Wny[4] = {-X0 * rdy, -fx * rdy, X0 * rdy, fx * rdy};
+                const bool lx = fx < A(0.5), ly = fy < A(0.5);
+                const A tx = lx ? fx + A(0.5) : fx - A(0.5), ty = ly ? fy + A(0.5) : fy - A(0.5);
+                const int c0 = lx ? cl : cl + 1, r0 = ly ? 0 : 1;
+                const A Wc[4] = {(A(1) - tx) * (A(1) - ty), tx * (A(1) - ty), (A(1) - tx) * ty, tx * ty};
+                const A Wcx[4] = {-(A(1) - ty) * rdx, (A(1) - ty) * rdx, -ty * rdx, ty * rdx};
+                const A Wcy[4] = {-(A(1) - tx) * rdy, -tx * rdy, (A(1) - tx) * rdy, tx * rdy};
+                A Bc[4][3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    atomicAdd(gB + (int64_t)k * nc + cents[q], Wc[q] * gBp[k]);
-                    bg += Bc[q][k] * gBp[k];
+                    Bc[0][k] = tl.B[k][r0][c0];
+                    Bc[1][k] = tl.B[k][r0][c0 + 1];
+                    Bc[2][k] = tl.B[k][r0 + 1][c0];
+                    Bc[3][k] = tl.B[k][r0 + 1][c0 + 1];
                 }
-                gxp += Wnx[q] * gW[q] + Wcx[q] * bg;
-                gyp += Wny[q] * gW[q] + Wcy[q] * bg;
-            }
+                A Bp[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) gu0[3 * (int64_t)p + k] = gu[k];
-            gx0[2 * (int64_t)p] = gxp;
-            gx0[2 * (int64_t)p + 1] = gyp;
+                for (int k = 0; k < 3; ++k)
+                    Bp[k] = Wc[0] * Bc[0][k] + Wc[1] * Bc[1][k] + Wc[2] * Bc[2][k] + Wc[3] * Bc[3][k];
+                const A gb = sqrt(A(1) + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+                const A a[3] = {beta * Bp[0] / gb, beta * Bp[1] / gb, beta * Bp[2] / gb};
+                const A ia = A(1) / (A(1) + a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+                A al[3][3];
+                al[0][0] = (A(1) + a[0] * a[0]) * ia; al[0][1] = (a[0] * a[1] + a[2]) * ia; al[0][2] = (a[0] * a[2] - a[1]) * ia;
+                al[1][0] = (a[0] * a[1] - a[2]) * ia; al[1][1] = (A(1) + a[1] * a[1]) * ia; al[1][2] = (a[1] * a[2] + a[0]) * ia;
+                al[2][0] = (a[0] * a[2] + a[1]) * ia; al[2][1] = (a[1] * a[2] - a[0]) * ia; al[2][2] = (A(1) + a[2] * a[2]) * ia;
+                A au[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) au[r] = al[r][0] * u0[0] + al[r][1] * u0[1] + al[r][2] * u0[2];
+                const A rgb = A(1) / gb;
+                const A cJ = wt * cJ0 * rgb, cM = wt * cM0 * rgb;   // with the 1/gbar of both terms
+                const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+                const int64_t nodes[4] = {(int64_t)j * nx + i, (int64_t)j * nx + i1, (int64_t)j1 * nx + i,
+                                          (int64_t)j1 * nx + i1};
+                A ga_[3][3] = {{A(0), A(0), A(0)}, {A(0), A(0), A(0)}, {A(0), A(0), A(0)}};   // dL/dalpha
+                A gW[4] = {A(0), A(0), A(0), A(0)}, gu[3] = {A(0), A(0), A(0)};
+                A sg = A(0);   // sum of the terms' values: d/dgbar of each is -value/gbar
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const A gj[3] = {(A)gJ[nodes[k]], (A)gJ[nc + nodes[k]], (A)gJ[2 * (int64_t)nc + nodes[k]]};
+                    const A f = cJ * Wn[k];
+                    A sJ = A(0);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        sJ += gj[r] * au[r];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            ga_[r][q] += f * gj[r] * u0[q];
+                            gu[q] += f * al[r][q] * gj[r];
+                        }
+                    }
+                    gW[k] += cJ * sJ;
+                    sg += cJ * Wn[k] * sJ;
+                }
+#pragma unroll
+                for (int pr = 0; pr < 10; ++pr) {
+                    const double* G = gM + nodes[ps[pr]] * kMBlock + po[pr] * 9;
+                    A Gv[9];
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) Gv[e] = (A)G[e];
+                    A s2 = A(0);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) s2 += Gv[r * 3 + q] * al[r][q];
+                    const A wa = Wn[pa[pr]], wb = Wn[pb[pr]];
+                    const A coef = cM * wa * wb;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) ga_[r][q] += coef * Gv[r * 3 + q];
+                    gW[pa[pr]] += cM * wb * s2;
+                    gW[pb[pr]] += cM * wa * s2;
+                    sg += coef * s2;
+                }
+                A ggb = -sg * rgb;
+                // Gm = -alpha^T ga_ alpha^T; gradient of a from <Gm, [da]x>
+                A t1[3][3], Gm[3][3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        t1[r][q] = al[0][r] * ga_[0][q] + al[1][r] * ga_[1][q] + al[2][r] * ga_[2][q];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        Gm[r][q] = -(t1[r][0] * al[q][0] + t1[r][1] * al[q][1] + t1[r][2] * al[q][2]);
+                const A gav[3] = {Gm[2][1] - Gm[1][2], Gm[0][2] - Gm[2][0], Gm[1][0] - Gm[0][1]};
+                const A gBp[3] = {beta * gav[0] * rgb, beta * gav[1] * rgb, beta * gav[2] * rgb};
+                ggb -= (gav[0] * a[0] + gav[1] * a[1] + gav[2] * a[2]) * rgb;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gu[k] += ggb * u0[k] * rgb;
+                A gxp = A(0), gyp = A(0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    A bg = A(0);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) bg += Bc[q][k] * gBp[k];
+                    gxp += Wnx[q] * gW[q] + Wcx[q] * bg;
+                    gyp += Wny[q] * gW[q] + Wcy[q] * bg;
+                }
+                A Cx[3], Ry[3];
+                centre_factors(lx, ly, tx, ty, Cx, Ry);
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) gc[k][r][c] = Ry[r] * Cx[c] * gBp[k];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gu0[3 * (int64_t)p + k] = (double)gu[k];
+                gx0[2 * (int64_t)p] = (double)gxp;
+                gx0[2 * (int64_t)p + 1] = (double)gyp;
+            }
+            const Runs rn = runs_of(act ? cl : -1, lane);
+            flush_centres(gc, rn, act, gB, i, j, nx, ny, nc);
         }
         __syncwarp();
     }

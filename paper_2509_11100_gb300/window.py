@@ -3,19 +3,20 @@
 The loss is the energy of Fourier mode m of B_y along x after the last step
 of the window (the linear-tearing diagnostic of Sec. 3.1). Gradients with
 respect to the initial E field (per node) and B field (per cell centre), and
-through B, the amplitude of an initial B_y perturbation, come from one step's
-adjoint chained backwards over the window: per step, the pushes' adjoints
-(fields fixed), the field adjoint with their dL/dE^{n+theta}, then the
-deposits' adjoints (relsim_push_adjoint, relsim_field_adjoint,
-relsim_deposit_adjoint). The forward pass keeps a checkpoint of the state
-every `checkpoint_every` steps; the backward pass reloads each checkpoint,
-recomputes that segment's steps to recover their start states, and runs the
-adjoints backwards through it. Particles are matched across the re-sort of
-every push by the ids the library carries (`track_ids`).
+through B, the amplitude of an initial B_y perturbation, come from one
+step's adjoint chained backwards over the window (relsim_step_adjoint: the
+pushes' adjoints with the fields fixed, the field adjoint with their
+dL/dE^{n+theta}, the deposits' adjoints). The forward pass keeps a
+checkpoint of the state every `checkpoint_every` steps in device memory;
+the backward pass reloads each checkpoint, recomputes that segment's steps
+to recover their start states (kept on the device) and runs the step
+adjoints backwards through it. Every particle carries its index in the
+initial state as its id (relsim_relabel_particles after each reload), and
+the per-particle gradients live in that id order on the device, so no step
+needs a reordering or a host transfer.
 
 Everything runs in the library's kernels; this module only orders the
-calls and moves the per-step gradients between particle orders. It covers
-the base scheme (gbar = gamma(u^n)).
+calls. It covers the base scheme (gbar = gamma(u^n)).
 """
 from __future__ import annotations
 
@@ -58,42 +59,44 @@ class ModeEnergyWindow:
         self.dV = cfg.dx * cfg.dy
         self.checkpoints = {}
         self.iters = []
+        self.adjoint_iters = []
 
     def close(self):
+        self.checkpoints = {}
         self.sim.close()
 
-    # -- state transfer ---------------------------------------------------
+    # -- state transfer (device to device) ----------------------------------
     def _state(self):
-        """The current state as host arrays in the library's current order."""
+        """The current state as CUDA tensors in the library's current order;
+        the ids are the particles' indices in the initial state."""
         sp = []
         for s in range(self.nsp):
-            x, u, w, ids = self.sim.particles(s, ids=True)
+            x, u, w, ids = self.sim.particles(s, ids=True, device=True)
             sp.append({"x": x, "u": u, "w": w, "ids": ids})
-        E, B = self.sim.fields()
+        E, B = self.sim.fields(device=True)
         return {"species": sp, "E": E, "B": B}
 
     def _load(self, st):
-        """Load a state; the ids restart at the load order (which it keeps:
-        the particles are already in cell order)."""
+        """Load a saved state and give each particle its saved id."""
         for s, sp in enumerate(st["species"]):
             self.sim.load_species(s, sp["x"], sp["u"], sp["w"])
+            self.sim.relabel(s, sp["ids"])
         self.sim.set_fields(st["E"], st["B"])
 
     def _step(self):
-        led, code = self.sim.step(ledger=True)
+        led, code = self.sim.step(ledger=False)
         if code not in (0, RELSIM_ERR_NOT_CONVERGED):
             raise RuntimeError(f"step failed: {code}")
-        self.iters.append(led["gmres_iters"])
 
     # -- forward ------------------------------------------------------------
     def forward(self, state):
         """Run the window from `state` (a relsim_inputs-style dict); keep a
         checkpoint every `checkpoint_every` steps; return the loss."""
-        init = {"species": [{"x": np.stack([np.asarray(sp["x"], np.float64), np.asarray(sp["y"], np.float64)], 1),
-                             "u": np.stack([np.asarray(sp[k], np.float64) for k in ("ux", "uy", "uz")], 1),
-                             "w": np.asarray(sp["w"], np.float64)} for sp in state["species"]],
-                "E": np.asarray(state["E"], np.float64), "B": np.asarray(state["B"], np.float64)}
-        self._load(init)
+        for s, sp in enumerate(state["species"]):
+            x = np.stack([np.asarray(sp["x"], np.float64), np.asarray(sp["y"], np.float64)], 1)
+            u = np.stack([np.asarray(sp[k], np.float64) for k in ("ux", "uy", "uz")], 1)
+            self.sim.load_species(s, x, u, np.asarray(sp["w"], np.float64))   # ids = initial indices
+        self.sim.set_fields(np.asarray(state["E"], np.float64), np.asarray(state["B"], np.float64))
         self.checkpoints = {}
         for n in range(self.nsteps):
             if n % self.every == 0:
@@ -104,60 +107,39 @@ class ModeEnergyWindow:
         return self.loss
 
     # -- backward -----------------------------------------------------------
-    def _step_adjoint(self, pre, gpart, gE1, gB1):
-        """Reload the step's start state, rebuild and solve, run the three
-        adjoints. gpart[s] = (gu1 (n, 3), gx1 (n, 2)) in the start state's
-        order; returns the gradients with respect to the start state (per
-        species, in its order), dL/dE^n and dL/dB^n."""
-        self._load(pre)
-        self.sim.build()
-        self.sim.solve()
-        gp = [self.sim.push_adjoint(s, gpart[s][0], gpart[s][1]) for s in range(self.nsp)]
-        gEt = sum(g["E"] for g in gp)
-        gf = self.sim.field_adjoint(gE1, gB1, gEt=gEt)
-        gd = [self.sim.deposit_adjoint(s, gf["J"], gf["M"]) for s in range(self.nsp)]
-        gB = gf["B0"] + sum(g["B"] for g in gp) + sum(g["B"] for g in gd)
-        gsp = [(gp[s]["u"] + gd[s]["u"], gp[s]["x"] + gd[s]["x"]) for s in range(self.nsp)]
-        return gsp, gf["E0"], gB
-
     def backward(self):
         """dL/dE and dL/dB of the window's initial fields (3, ncell) each, and
         per species the gradients (du (N, 3), dx (N, 2)) of the initial
-        particles, indexed by their order in the initial state."""
-        nx, ny = self.nx, self.ny
-        gE = np.zeros((3, nx * ny))
-        gB = self.gB_final.copy()
-        # per species, gradients indexed by the particles' initial ids
-        gid = [(np.zeros((len(sp["w"]), 3)), np.zeros((len(sp["w"]), 2)))
-               for sp in self.checkpoints[0]["species"]]
+        particles, indexed by their order in the initial state (host arrays)."""
+        import torch
+        dev = self.checkpoints[0]["E"].device
+        gE = torch.zeros((3, self.nx * self.ny), dtype=torch.float64, device=dev)
+        gB = torch.as_tensor(self.gB_final, dtype=torch.float64).to(dev).contiguous()
+        gu = [torch.zeros((sp["w"].shape[0], 3), dtype=torch.float64, device=dev)
+              for sp in self.checkpoints[0]["species"]]
+        gx = [torch.zeros((sp["w"].shape[0], 2), dtype=torch.float64, device=dev)
+              for sp in self.checkpoints[0]["species"]]
+        self.adjoint_iters = []
         starts = sorted(self.checkpoints)
         for k in range(len(starts) - 1, -1, -1):
             s0 = starts[k]
             s1 = starts[k + 1] if k + 1 < len(starts) else self.nsteps
-            ck = self.checkpoints[s0]
-            # recompute the segment's start states; their ids count from the
-            # checkpoint's load, mapped back to initial ids through it
-            pres = [ck]
-            self._load(ck)
+            # recompute the segment's start states; the last one stays loaded
+            pres = [self.checkpoints[s0]]
+            self._load(pres[0])
             for n in range(s0, s1 - 1):
                 self._step()
-                st = self._state()
-                for s in range(self.nsp):
-                    st["species"][s]["ids"] = ck["species"][s]["ids"][st["species"][s]["ids"]]
-                pres.append(st)
+                if n < s1 - 2:
+                    pres.append(self._state())
             for n in range(s1 - 1, s0 - 1, -1):
-                pre = pres[n - s0]
-                gpart = []
-                for s in range(self.nsp):
-                    ids = pre["species"][s]["ids"]
-                    gpart.append((gid[s][0][ids], gid[s][1][ids]))
-                gsp, gE, gB = self._step_adjoint(pre, gpart, gE, gB)
-                for s in range(self.nsp):
-                    ids = pre["species"][s]["ids"]
-                    gid[s][0][ids] = gsp[s][0]
-                    gid[s][1][ids] = gsp[s][1]
+                if n < s1 - 1:
+                    self._load(pres[n - s0])
+                it, _, _ = self.sim.step_adjoint(gE, gB, gu, gx)
+                self.adjoint_iters.append(it)
+        torch.cuda.synchronize(dev)
+        gid = [(gu[s].cpu().numpy(), gx[s].cpu().numpy()) for s in range(self.nsp)]
         self.grad_particles = gid
-        return {"E": gE, "B": gB, "particles": gid}
+        return {"E": gE.cpu().numpy(), "B": gB.cpu().numpy(), "particles": gid}
 
 
 def _torch():
