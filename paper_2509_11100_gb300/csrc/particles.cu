@@ -1146,6 +1146,20 @@ k_spectrum(PArrays<T> pa, int64_t n, int variable, const T* __restrict__ edges, 
         }
 }
 
+int blocks_for(int64_t n, int threads, int cap)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the adjoints of the push and the deposit (they reuse the unit tiles above)
+namespace {
+
 // Segmented sums across a warp for the adjoints' scatters. In one pass of a
 // unit the lanes hold consecutive particles, so their cells ascend and the
 // lanes of one cell are consecutive: a suffix sum over those runs (five
@@ -1569,15 +1583,7 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
     }
 }
 
-int blocks_for(int64_t n, int threads, int cap)
-{
-    int64_t b = (n + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > cap) b = cap;
-    return (int)b;
-}
-
-}  // namespace
+}  // namespace (the adjoints)
 
 int push_grid_blocks(GridP g, int precision, int cap)
 {
