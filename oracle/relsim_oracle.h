@@ -104,6 +104,42 @@ int    orc_step(const orc_config* c, const int64_t* off,
                 double* E, double* B, orc_ledger* led,
                 double* J_out, double* M_out, double* Etheta_out);
 
+/* ---- 3D (relsim_oracle3.c): periodic nx x ny x nz, trilinear shapes, the
+   base scheme. Node and cell (i,j,k) have linear index (k*ny + j)*nx + i;
+   M[((g*27 + o)*3 + r)*3 + s] with o = (dk+1)*9 + (dj+1)*3 + (di+1). */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz, dt, theta;
+    int nspecies;
+    double q[4], m[4];
+    double gmres_tol;
+    int gmres_restart, gmres_maxit;
+} orc3_config;
+
+void   orc3_node_weights(const orc3_config* c, double x, double y, double z, int64_t g[8], double W[8]);
+void   orc3_gather_E(const orc3_config* c, const double* E, double x, double y, double z, double out[3]);
+void   orc3_gather_B(const orc3_config* c, const double* B, double x, double y, double z, double out[3]);
+void   orc3_deposit(const orc3_config* c, const int64_t* off, const double* x, const double* y, const double* z,
+                    const double* ux, const double* uy, const double* uz, const double* w, const double* B,
+                    double* J, double* M);
+void   orc3_curl_c(const orc3_config* c, const double* E, double* out);
+void   orc3_curl_n(const orc3_config* c, const double* B, double* out);
+void   orc3_apply_M(const orc3_config* c, const double* M, const double* v, double* out);
+void   orc3_apply_A(const orc3_config* c, const double* M, const double* v, double* out);
+void   orc3_rhs(const orc3_config* c, const double* E, const double* B, const double* J, double* b);
+int    orc3_gmres(const orc3_config* c, const double* M, const double* b, double* x, int* iters,
+                  double* relres);
+void   orc3_field_update(const orc3_config* c, const double* Etheta, double* E, double* B);
+void   orc3_push(const orc3_config* c, const int64_t* off, double* x, double* y, double* z, double* ux,
+                 double* uy, double* uz, const double* w, const double* Etheta, const double* B, double sums[4]);
+void   orc3_energies(const orc3_config* c, const int64_t* off, const double* ux, const double* uy,
+                     const double* uz, const double* w, const double* E, const double* B, double out[3]);
+void   orc3_cell_keys(const orc3_config* c, int64_t n, const double* x, const double* y, const double* z,
+                      int32_t* keys);
+int    orc3_step(const orc3_config* c, const int64_t* off, double* x, double* y, double* z, double* ux,
+                 double* uy, double* uz, const double* w, double* E, double* B, orc_ledger* led,
+                 double* J_out, double* M_out, double* Etheta_out);
+
 #ifdef __cplusplus
 }
 #endif

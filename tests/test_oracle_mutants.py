@@ -81,13 +81,37 @@ PY_MUTANTS = {
                                              'gu += cJ * WN[k] / gb * np.einsum("nij,jn->in", alpha, gj)'),
     "deposit_adjoint_one_sided_pairs": ("                gWn[l] += cM * WN[k] * s2 / gb\n", "\n"),
 }
-CASES = {**{k: ("relsim_oracle.c",) + v for k, v in MUTANTS.items()},
-         **{k: ("__init__.py",) + v for k, v in PY_MUTANTS.items()}}
+# mistakes planted in the 3D oracle, caught by its own pins
+MUTANTS3 = {
+    "curl3_c_z_edge_wrong_row": ("sz += f[idx3(c, i + e1, j + e2, k + 1)] - f[idx3(c, i + e1, j + e2, k)];",
+                                 "sz += f[idx3(c, i + e1, j + e2, k + 1)] - f[idx3(c, i + e1, j, k)];"),
+    "deposit3_dk_sign": ("int dk = ((b >> 2) & 1) - ((a >> 2) & 1);", "int dk = ((a >> 2) & 1) - ((b >> 2) & 1);"),
+    "weights3_z_from_y": ("(az ? f[2] : 1.0 - f[2])", "(az ? f[1] : 1.0 - f[1])"),
+    "gather3_B_on_nodes": ("weights3(c, x, y, z, 0.5, cell, g, W);", "weights3(c, x, y, z, 0.0, cell, g, W);"),
+    "apply_M3_z_neighbour_flipped": ("int64_t h = idx3(c, i + di, j + dj, k + dk);",
+                                     "int64_t h = idx3(c, i + di, j + dj, k - dk);"),
+    "push3_z_moves_with_uy": ("z[p] = wrap_pos3(z[p] + c->dt * u1[2] / g1, L[2]);",
+                              "z[p] = wrap_pos3(z[p] + c->dt * u1[1] / g1, L[2]);"),
+    "curl3_n_dz_uses_dy": ("sz += f[idx3(c, i + e1, j + e2, k)] - f[idx3(c, i + e1, j + e2, k - 1)];\n"
+                           "                        }\n"
+                           "                    d[0][comp] = sx / (4.0 * c->dx);\n"
+                           "                    d[1][comp] = sy / (4.0 * c->dy);\n"
+                           "                    d[2][comp] = sz / (4.0 * c->dz);",
+                           "sz += f[idx3(c, i + e1, j + e2, k)] - f[idx3(c, i + e1, j + e2, k - 1)];\n"
+                           "                        }\n"
+                           "                    d[0][comp] = sx / (4.0 * c->dx);\n"
+                           "                    d[1][comp] = sy / (4.0 * c->dy);\n"
+                           "                    d[2][comp] = sz / (4.0 * c->dy);"),
+}
+PINS = "test_oracle_pins.py"
+CASES = {**{k: ("relsim_oracle.c",) + v + (PINS,) for k, v in MUTANTS.items()},
+         **{k: ("__init__.py",) + v + (PINS,) for k, v in PY_MUTANTS.items()},
+         **{k: ("relsim_oracle3.c",) + v + ("test_oracle3_pins.py",) for k, v in MUTANTS3.items()}}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    fname, orig, repl = CASES[name]
+    fname, orig, repl, pins = CASES[name]
     src_dir = os.path.join(ROOT, "oracle")
     src = open(os.path.join(src_dir, fname)).read()
     assert src.count(orig) == 1, f"mutation site for {name} is not unique"
@@ -96,7 +120,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     (dst / fname).write_text(src.replace(orig, repl))
     env = dict(os.environ, RELSIM_ORACLE_MUTANT_DIR=str(tmp_path))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
     # the copy really was the one under test
     assert (dst / "liboracle.so").exists()
