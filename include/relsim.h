@@ -90,7 +90,7 @@ extern "C" {
 typedef struct relsim_ctx relsim_ctx;  /* opaque, owned by the library */
 
 typedef struct {
-    int dim;               /* must be 2                                        */
+    int dim;               /* 2, or 3 for the 3D form (see below)              */
     int nx, ny, nz;        /* cells per direction (nz ignored in 2D)           */
     double dx, dy, dz;     /* cell sizes                                       */
     double dt;             /* time step                                        */
@@ -146,7 +146,20 @@ RELSIM_API void relsim_destroy(relsim_ctx* ctx);
 /* Message of the last error on this context ("" if none). Owned by ctx. */
 RELSIM_API const char* relsim_last_error(const relsim_ctx* ctx);
 
-/* Load (replace) the particles of one species: n particles, positions x[2n],
+/* The 3D form (dim = 3, nx, ny, nz >= 3): the same step on a periodic
+   nx x ny x nz grid with trilinear shape functions (27-node stencil). Node
+   and cell (i,j,k) have linear index (k*ny + j)*nx + i, ncell = nx*ny*nz;
+   positions carry three coordinates (x[3n], (x, y, z) interleaved); the
+   stored mass matrix keeps 14 of the 27 offsets per node, in this order:
+   (0,0,0), (1,0,0), (-1,1,0), (0,1,0), (1,1,0), then (di,dj,1) for
+   dj = -1..1 (outer) and di = -1..1 (inner), i.e. ncell x 126 values (the
+   2D form: (0,0), (1,0), (-1,1), (0,1), (1,1), ncell x 45). The 3D form
+   covers the base scheme; its steps run host-driven with the general push
+   (any move length, radix sort). The adjoints and the autotuner cover the
+   2D form (INVALID_ARG in 3D).
+
+   Load (replace) the particles of one species: n particles, positions x[2n]
+   (x[3n] in 3D),
    momenta u[3n], weights w[n], all FP64 (layout above). Positions outside
    the box are wrapped periodically. The library converts to its internal
    form and sorts the particles by cell (stable: equal cells keep the input
@@ -170,7 +183,7 @@ RELSIM_API int relsim_get_fields(relsim_ctx* ctx, double* E, double* B, int wher
 RELSIM_API int relsim_num_particles(relsim_ctx* ctx, int species, int64_t* n);
 
 /* Copy the particles of a species out, in the library's current order
-   (sorted by cell, stable), as FP64 x[2n], u[3n], w[n] and, if ids are
+   (sorted by cell, stable), as FP64 x[2n] (x[3n] in 3D), u[3n], w[n] and, if ids are
    tracked, id[n] (each pointer may be NULL to skip it). Positions are
    absolute. Errors: INVALID_ARG (species out of range, id requested but not
    tracked), CUDA. */
@@ -188,8 +201,10 @@ RELSIM_API int relsim_build_mass_matrix(relsim_ctx* ctx);
 /* The deposited Jhat (3*ncell, component-major) and M, stored for the five
    neighbour offsets o in {(0,0), (1,0), (-1,1), (0,1), (1,1)} as
    M[(g*5 + k)*9 + r*3 + s] = block (r,s) of M_{g, g+o_k}; the other four
-   offsets follow from M_{g+o,g} = M_{g,g+o}. FP64 out. Either pointer may
-   be NULL. Errors: BAD_STATE (nothing built), INVALID_ARG, CUDA. */
+   offsets follow from M_{g+o,g} = M_{g,g+o}. In 3D the 14 stored offsets
+   listed with the 3D form: M[(g*14 + k)*9 + r*3 + s]. FP64 out. Either
+   pointer may be NULL. Errors: BAD_STATE (nothing built), INVALID_ARG,
+   CUDA. */
 RELSIM_API int relsim_get_mass_matrix(relsim_ctx* ctx, double* M, double* J, int where);
 
 /* Replace the built Jhat and M by caller values (same layouts as

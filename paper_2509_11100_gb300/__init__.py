@@ -242,12 +242,13 @@ def _stream(stream=None) -> int:
 
 def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta_implicit=0.5, precision=32,
                 q=(1.0, -1.0), m=(1.0, 1.0), gmres_tol=0.0, gmres_restart=0, gmres_maxit=0,
-                track_ids=False, gamma_pred=False) -> relsim_config:
+                track_ids=False, gamma_pred=False, nz=None, dz=1.0) -> relsim_config:
     """gamma_pred: the Lorentz factor in alpha and M is that of the
-    predicted half-step momentum u^n + beta E^n(x) instead of u^n."""
+    predicted half-step momentum u^n + beta E^n(x) instead of u^n. nz: the
+    3D form on an nx x ny x nz grid (cell size dz along z)."""
     c = relsim_config()
-    c.dim, c.nx, c.ny, c.nz = 2, nx, ny, 1
-    c.dx, c.dy, c.dz, c.dt, c.theta_implicit = dx, dy, 1.0, dt, theta_implicit
+    c.dim, c.nx, c.ny, c.nz = (2, nx, ny, 1) if nz is None else (3, nx, ny, nz)
+    c.dx, c.dy, c.dz, c.dt, c.theta_implicit = dx, dy, (1.0 if nz is None else dz), dt, theta_implicit
     c.precision, c.nspecies = precision, len(q)
     for s in range(len(q)):
         c.q[s] = q[s]
@@ -317,9 +318,9 @@ def relsim_num_particles(ctx, species) -> int:
     return n.value
 
 
-def relsim_get_particles(ctx, species, ids=False, device=False):
+def relsim_get_particles(ctx, species, ids=False, device=False, dim=2):
     n = relsim_num_particles(ctx, species)
-    x = _out((n, 2), np.float64, device)
+    x = _out((n, dim), np.float64, device)
     u = _out((n, 3), np.float64, device)
     w = _out((n,), np.float64, device)
     i = _out((n,), np.int32, device) if ids else None
@@ -340,8 +341,9 @@ def relsim_build_mass_matrix(ctx):
     return _check(ctx, lib().relsim_build_mass_matrix(ctx))
 
 
-def relsim_get_mass_matrix(ctx, ncell, device=False):
-    M = _out((ncell, 5, 3, 3), np.float64, device)
+def relsim_get_mass_matrix(ctx, ncell, device=False, nhalf=5):
+    """The stored blocks (ncell, nhalf, 3, 3): 5 offsets in 2D, 14 in 3D."""
+    M = _out((ncell, nhalf, 3, 3), np.float64, device)
     J = _out((3, ncell), np.float64, device)
     pM, pJ = _ptr(M, writable=True), _ptr(J, writable=True)
     _check(ctx, lib().relsim_get_mass_matrix(ctx, pM[0], pJ[0], _where(pM, pJ)))
@@ -582,7 +584,7 @@ class Simulation:
 
     def __init__(self, cfg: relsim_config, stream=None):
         self.cfg = cfg
-        self.ncell = cfg.nx * cfg.ny
+        self.ncell = cfg.nx * cfg.ny * (cfg.nz if cfg.dim == 3 else 1)
         self.ctx = relsim_init(cfg, stream)
 
     def close(self):
@@ -600,9 +602,11 @@ class Simulation:
         return relsim_load_particles(self.ctx, s, x, u, w)
 
     def load_state(self, state: dict):
-        """Load a state dict as produced by relsim_inputs (species + E + B)."""
+        """Load a state dict as produced by relsim_inputs (species + E + B);
+        3D states carry z as well."""
+        keys = ("x", "y", "z") if self.cfg.dim == 3 else ("x", "y")
         for s, sp in enumerate(state["species"]):
-            x = np.stack([np.asarray(sp["x"], np.float64), np.asarray(sp["y"], np.float64)], axis=1)
+            x = np.stack([np.asarray(sp[k], np.float64) for k in keys], axis=1)
             u = np.stack([np.asarray(sp[k], np.float64) for k in ("ux", "uy", "uz")], axis=1)
             self.load_species(s, x, u, np.asarray(sp["w"], np.float64))
         relsim_set_fields(self.ctx, np.asarray(state["E"], np.float64), np.asarray(state["B"], np.float64))
@@ -614,7 +618,7 @@ class Simulation:
         return relsim_get_fields(self.ctx, self.ncell, device)
 
     def particles(self, s, ids=False, device=False):
-        return relsim_get_particles(self.ctx, s, ids, device)
+        return relsim_get_particles(self.ctx, s, ids, device, self.cfg.dim)
 
     def cell_start(self, s, device=False):
         return relsim_get_cell_start(self.ctx, s, self.ncell, device)
@@ -623,7 +627,7 @@ class Simulation:
         return relsim_build_mass_matrix(self.ctx)
 
     def mass_matrix(self, device=False):
-        return relsim_get_mass_matrix(self.ctx, self.ncell, device)
+        return relsim_get_mass_matrix(self.ctx, self.ncell, device, 14 if self.cfg.dim == 3 else 5)
 
     def set_mass_matrix(self, M, J):
         return relsim_set_mass_matrix(self.ctx, M, J)

@@ -38,7 +38,7 @@ constexpr int kLedgerLen = kLedgerField + kLedgerSpecies * kMaxSpecies + 2;   //
 
 struct Species {
     int64_t n = 0, cap = 0;
-    void* a[2][6] = {};   // fx, fy, ux, uy, uz, w of buffer 0 and 1
+    void* a[2][7] = {};   // fx, fy, ux, uy, uz, w (and fz in 3D) of buffer 0 and 1
     int32_t* id[2] = {nullptr, nullptr};
     int cur = 0;
     int32_t* start = nullptr;
@@ -333,12 +333,13 @@ int ensure_species(relsim_ctx* c, int s, int64_t n)
     }
     if (n <= sp.cap) return RELSIM_OK;
     for (int b = 0; b < 2; ++b) {
-        for (int k = 0; k < 6; ++k) dfree(sp.a[b][k]);
+        for (int k = 0; k < 7; ++k) dfree(sp.a[b][k]);
         dfree(sp.id[b]);
     }
     sp.cap = 0;
+    const int narr = c->g.dim == 3 ? 7 : 6;
     for (int b = 0; b < 2; ++b) {
-        for (int k = 0; k < 6; ++k) TRY(dalloc(c, &sp.a[b][k], c->esz * (size_t)(n + 8)));
+        for (int k = 0; k < narr; ++k) TRY(dalloc(c, &sp.a[b][k], c->esz * (size_t)(n + 8)));
         if (c->cfg.track_ids) TRY(dalloc(c, &sp.id[b], sizeof(int32_t) * (size_t)n));
     }
     sp.cap = n;
@@ -388,15 +389,19 @@ int load_impl(relsim_ctx* c, int s, int64_t n, const double* x, const double* u,
         CK(cudaMemsetAsync(sp.start, 0, sizeof(int32_t) * (size_t)(c->g.ncell + 1), c->st));
     } else {
         const double *dx, *du, *dw;
-        if (where == RELSIM_HOST) TRY(ensure_stage(c, 6 * n));
-        TRY(stage_in(c, x, 2 * n, where, &dx, 0));
-        TRY(stage_in(c, u, 3 * n, where, &du, 2 * n));
-        TRY(stage_in(c, w, n, where, &dw, 5 * n));
+        const int D = c->g.dim;   // x holds D coordinates per particle
+        if (where == RELSIM_HOST) TRY(ensure_stage(c, (D + 4) * n));
+        TRY(stage_in(c, x, D * n, where, &dx, 0));
+        TRY(stage_in(c, u, 3 * n, where, &du, D * n));
+        TRY(stage_in(c, w, n, where, &dw, (D + 3) * n));
         TRY(ensure_radix(c, n));
         CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
         PROF_BEGIN(RELSIM_PROF_LOAD);
         PArrays<T> tmp = arrays<T>(sp, 1), dst = arrays<T>(sp, 0);
-        CK(load_convert<T>(dx, du, dw, n, c->g, tmp, c->rk[0], c->rv[0], c->dflag, c->st));
+        if (D == 3)
+            CK(load_convert3<T>(dx, du, dw, n, c->g, tmp, (T*)sp.a[1][6], c->rk[0], c->rv[0], c->dflag, c->st));
+        else
+            CK(load_convert<T>(dx, du, dw, n, c->g, tmp, c->rk[0], c->rv[0], c->dflag, c->st));
         CK(keys_unsorted(c->rk[0], n, c->dflag, c->st));
         PROF_END();
         CK(cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -411,7 +416,10 @@ int load_impl(relsim_ctx* c, int s, int64_t n, const double* x, const double* u,
                                 c->st));
             keys = c->rk[in1 ? 1 : 0];
             const int32_t* perm = c->rv[in1 ? 1 : 0];
-            CK(gather_particles<T>(perm, tmp, dst, n, true, c->st));
+            if (D == 3)
+                CK(gather_particles3<T>(perm, tmp, (const T*)sp.a[1][6], dst, (T*)sp.a[0][6], n, true, c->st));
+            else
+                CK(gather_particles<T>(perm, tmp, dst, n, true, c->st));
         } else {
             // already in cell order (e.g. state read back from this library):
             // the identity is the stable sort, and the converted buffer stays
@@ -505,17 +513,21 @@ int get_particles_impl(relsim_ctx* c, int s, double* x, double* u, double* w, in
     const int64_t n = sp.n;
     if (n == 0) return RELSIM_OK;
     PArrays<T> pa = arrays<T>(sp, sp.cur);
+    const int D = c->g.dim;
+    const T* fz = (const T*)sp.a[sp.cur][6];
     if (where == RELSIM_DEVICE) {
-        CK(export_particles<T>(pa, sp.start, c->g, x, u, w, id, c->st));
+        if (D == 3) CK(export_particles3<T>(pa, fz, sp.start, c->g, x, u, w, id, c->st));
+        else CK(export_particles<T>(pa, sp.start, c->g, x, u, w, id, c->st));
         return RELSIM_OK;
     }
-    TRY(ensure_stage(c, 6 * n + (n + 1) / 2));
+    TRY(ensure_stage(c, (D + 4) * n + (n + 1) / 2));
     double* dx = x ? c->stage : nullptr;
-    double* du = u ? c->stage + 2 * n : nullptr;
-    double* dw = w ? c->stage + 5 * n : nullptr;
-    int32_t* did = id ? (int32_t*)(c->stage + 6 * n) : nullptr;
-    CK(export_particles<T>(pa, sp.start, c->g, dx, du, dw, did, c->st));
-    if (x) CK(cudaMemcpyAsync(x, dx, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, c->st));
+    double* du = u ? c->stage + D * n : nullptr;
+    double* dw = w ? c->stage + (D + 3) * n : nullptr;
+    int32_t* did = id ? (int32_t*)(c->stage + (D + 4) * n) : nullptr;
+    if (D == 3) CK(export_particles3<T>(pa, fz, sp.start, c->g, dx, du, dw, did, c->st));
+    else CK(export_particles<T>(pa, sp.start, c->g, dx, du, dw, did, c->st));
+    if (x) CK(cudaMemcpyAsync(x, dx, sizeof(double) * D * n, cudaMemcpyDeviceToHost, c->st));
     if (u) CK(cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->st));
     if (w) CK(cudaMemcpyAsync(w, dw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
     if (id) CK(cudaMemcpyAsync(id, did, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
@@ -531,11 +543,18 @@ int build_impl(relsim_ctx* c)
 {
     const int nc = c->g.ncell;
     PROF_BEGIN(RELSIM_PROF_DEPOSIT);
-    CK(cudaMemsetAsync(c->M, 0, c->esz * (size_t)nc * kMBlock, c->st));
+    CK(cudaMemsetAsync(c->M, 0, c->esz * (size_t)nc * mblock_of(c->g), c->st));
     CK(cudaMemsetAsync(c->J, 0, c->esz * 3 * (size_t)nc, c->st));
     const DepositSpecies<T> ds = deposit_args<T>(c);
-    CK(deposit<T>(ds, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J, c->g,
-                  c->dpush, c->st, c->dep_blocks));
+    if (c->g.dim == 3) {
+        FzArrays<T> fz;
+        memset(&fz, 0, sizeof(fz));
+        for (int s = 0; s < c->cfg.nspecies; ++s) fz.fz[s] = (const T*)c->sp[s].a[c->sp[s].cur][6];
+        CK(deposit3<T>(ds, fz, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->st));
+    } else {
+        CK(deposit<T>(ds, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J, c->g,
+                      c->dpush, c->st, c->dep_blocks));
+    }
     PROF_END();
     return RELSIM_OK;
 }
@@ -859,7 +878,7 @@ void push_commit(relsim_ctx* c)
 template <typename T>
 int push_enqueue(relsim_ctx* c)
 {
-    const int nbp = push_grid_blocks(c->g, c->prec, c->push_cap);
+    const int nbp = c->g.dim == 3 ? push_blocks3(c->g) : push_grid_blocks(c->g, c->prec, c->push_cap);
     TRY(ensure_partial(c, (int64_t)nbp * (kLedgerSpecies - 1)));
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         Species& sp = c->sp[s];
@@ -872,7 +891,25 @@ int push_enqueue(relsim_ctx* c)
         PArrays<T> src = arrays<T>(sp, sp.cur), dst = arrays<T>(sp, 1 - sp.cur);
         const T* Eth = (const T*)c->Eth;
         const T* B = (const T*)c->B[c->bcur];
-        if (c->fast_sort) {
+        if (c->g.dim == 3) {
+            // 3D: push with the new cell per particle, radix sort, gather
+            TRY(ensure_radix(c, sp.n));
+            T* sfz = (T*)sp.a[sp.cur][6];
+            T* dfz = (T*)sp.a[1 - sp.cur][6];
+            PROF_BEGIN(RELSIM_PROF_GENERAL_SORT);
+            CK(cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+            CK(push3<T>(src, sfz, dst, dfz, sp.start, c->rk[0], Eth, B, c->g, sc, c->partial, nbp, c->st));
+            CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
+            CK(iota_i32(c->rv[0], sp.n, c->st));
+            bool in1 = false;
+            CK(radix_sort_pairs(c->rk[0], c->rv[0], c->rk[1], c->rv[1], sp.n, c->key_bits, c->rtmp, &in1, c->st));
+            const int32_t* keys = c->rk[in1 ? 1 : 0];
+            const int32_t* perm = c->rv[in1 ? 1 : 0];
+            CK(gather_particles3<T>(perm, dst, dfz, src, sfz, sp.n, false, c->st));
+            CK(histogram_keys(keys, sp.n, c->count_new, c->g.ncell, c->st));
+            CK(scan_exclusive_i32(c->count_new, sp.start, c->g.ncell, sp.start + c->g.ncell, c->scan_tmp, c->st));
+            PROF_END();
+        } else if (c->fast_sort) {
             // push, each old cell written back grouped by move direction
             // into the other buffer; then the stable new-cell order back into
             // the current buffer
@@ -1405,7 +1442,8 @@ int spectrum_impl(relsim_ctx* c, int s, int variable, int nbins, const double* e
 template <typename T>
 int modes_impl(relsim_ctx* c, int comp, int nmodes, double* energy, int where)
 {
-    const int nx = c->g.nx, ny = c->g.ny;
+    // rows of nx values along x: ny of them in 2D, ny nz in 3D (contiguous)
+    const int nx = c->g.nx, ny = c->g.ny * c->g.nz;
     if (nmodes > c->mode_tw_m) {
         dfree(c->mode_tw);
         c->mode_tw_m = 0;
@@ -1494,9 +1532,15 @@ int ledger_fill(relsim_ctx* c, const double* h, relsim_energy* out)
 int validate(const relsim_config* cfg, std::string* why)
 {
     char b[256];
-    if (cfg->dim != 2) { *why = "only dim = 2 is supported"; return 0; }
+    if (cfg->dim != 2 && cfg->dim != 3) { *why = "dim must be 2 or 3"; return 0; }
     if (cfg->nx < 3 || cfg->ny < 3) { *why = "nx and ny must be >= 3"; return 0; }
-    if ((int64_t)cfg->nx * cfg->ny > (int64_t)1 << 28) { *why = "grid too large (nx*ny > 2^28)"; return 0; }
+    if (cfg->dim == 3 && cfg->nz < 3) { *why = "nz must be >= 3 in 3D"; return 0; }
+    if (cfg->dim == 3 && !(cfg->dz > 0)) { *why = "dz must be > 0 in 3D"; return 0; }
+    if (cfg->dim == 3 && cfg->gamma_pred) { *why = "the 3D form covers the base scheme (gamma_pred = 0)"; return 0; }
+    if ((int64_t)cfg->nx * cfg->ny * (cfg->dim == 3 ? cfg->nz : 1) > (int64_t)1 << 28) {
+        *why = "grid too large (more than 2^28 cells)";
+        return 0;
+    }
     if (!(cfg->dx > 0) || !(cfg->dy > 0) || !(cfg->dt > 0)) { *why = "dx, dy, dt must be > 0"; return 0; }
     if (!(cfg->theta_implicit > 0) || cfg->theta_implicit > 1) { *why = "theta_implicit must be in (0, 1]"; return 0; }
     if (cfg->precision != 32 && cfg->precision != 64) { *why = "precision must be 32 or 64"; return 0; }
@@ -1551,14 +1595,18 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     c->mrest = c->cfg.gmres_restart;
     c->g.nx = cfg->nx;
     c->g.ny = cfg->ny;
-    c->g.ncell = cfg->nx * cfg->ny;
+    c->g.dim = cfg->dim;
+    c->g.nz = cfg->dim == 3 ? cfg->nz : 1;
+    c->g.dz = cfg->dim == 3 ? cfg->dz : 1.0;
+    c->g.ncell = cfg->nx * cfg->ny * c->g.nz;
     c->g.dx = cfg->dx;
     c->g.dy = cfg->dy;
     c->g.dt = cfg->dt;
     c->g.theta = cfg->theta_implicit;
-    c->g.dV = cfg->dx * cfg->dy;
-    // one-cell moves per step: c dt <= min(dx, dy)
-    c->fast_sort = cfg->dt <= cfg->dx && cfg->dt <= cfg->dy;
+    c->g.dV = cfg->dx * cfg->dy * c->g.dz;
+    // one-cell moves per step: c dt <= min(dx, dy); the 3D form always
+    // takes the general push (any move length, radix sort) and host-driven steps
+    c->fast_sort = cfg->dim == 2 && cfg->dt <= cfg->dx && cfg->dt <= cfg->dy;
     c->key_bits = 1;
     while (((int64_t)1 << c->key_bits) < (int64_t)c->g.ncell) ++c->key_bits;
     const int64_t nc = c->g.ncell;
@@ -1575,9 +1623,9 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     A(dalloc(c, &c->B[0], c->esz * 3 * nc));
     A(dalloc(c, &c->B[1], c->esz * 3 * nc));
     A(dalloc(c, &c->J, c->esz * 3 * nc));
-    A(dalloc(c, &c->M, c->esz * kMBlock * nc));
-    A(dalloc(c, &c->n9, sizeof(int32_t) * kNDir * nc));
-    A(dalloc(c, &c->off9, sizeof(int32_t) * kNDir * nc));
+    A(dalloc(c, &c->M, c->esz * mblock_of(c->g) * nc));
+    A(dalloc(c, &c->n9, c->g.dim == 3 ? 16 : sizeof(int32_t) * kNDir * nc));
+    A(dalloc(c, &c->off9, c->g.dim == 3 ? 16 : sizeof(int32_t) * kNDir * nc));
     A(dalloc(c, &c->count_new, sizeof(int32_t) * (nc + 1)));
     c->scan_tmp_n = scan_tmp_ints(nc);
     A(dalloc(c, &c->scan_tmp, sizeof(int32_t) * c->scan_tmp_n));
@@ -1626,7 +1674,7 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
         if (e == cudaSuccess) e = cudaMemsetAsync(c->dled, 0, sizeof(double) * kLedgerLen, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->dpush, 0, sizeof(int), c->st);
         *c->hpush = 0;
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->M, 0, c->esz * kMBlock * nc, c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->M, 0, c->esz * mblock_of(c->g) * nc, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->J, 0, c->esz * 3 * nc, c->st);
         if (e != cudaSuccess) {
             r = fail(c, RELSIM_ERR_CUDA, "init memset: %s", cudaGetErrorString(e));
@@ -1657,7 +1705,7 @@ void relsim_destroy(relsim_ctx* c)
     for (int s = 0; s < kMaxSpecies; ++s) {
         Species& sp = c->sp[s];
         for (int b = 0; b < 2; ++b) {
-            for (int k = 0; k < 6; ++k) dfree(sp.a[b][k]);
+            for (int k = 0; k < 7; ++k) dfree(sp.a[b][k]);
             dfree(sp.id[b]);
         }
         dfree(sp.start);
@@ -1795,7 +1843,7 @@ int relsim_get_mass_matrix(relsim_ctx* c, double* M, double* J, int where)
     if (!c) return RELSIM_ERR_INVALID_ARG;
     if (c->state != kBuilt && c->state != kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "no mass matrix built");
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
-    const int64_t nm = (int64_t)c->g.ncell * kMBlock, nj = 3 * (int64_t)c->g.ncell;
+    const int64_t nm = (int64_t)c->g.ncell * mblock_of(c->g), nj = 3 * (int64_t)c->g.ncell;
     double *dM = M, *dJ = J;
     if (where == RELSIM_HOST) {
         TRY(ensure_stage(c, nm + nj));
@@ -1818,7 +1866,7 @@ int relsim_set_mass_matrix(relsim_ctx* c, const double* M, const double* J, int 
     ++c->gen;
     if (c->state == kEmpty) return fail(c, RELSIM_ERR_BAD_STATE, "context not initialised");
     if (c->state == kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "push the solved step first");
-    const int64_t nm = (int64_t)c->g.ncell * kMBlock, nj = 3 * (int64_t)c->g.ncell;
+    const int64_t nm = (int64_t)c->g.ncell * mblock_of(c->g), nj = 3 * (int64_t)c->g.ncell;
     const double *dM, *dJ;
     if (where == RELSIM_HOST) TRY(ensure_stage(c, nm + nj));
     TRY(stage_in(c, M, nm, where, &dM, 0));
@@ -1843,6 +1891,7 @@ int relsim_field_solve(relsim_ctx* c, int* iters, double* rel_residual)
 int relsim_autotune(relsim_ctx* c, relsim_tuning* out)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the autotuner covers the 2D kernels");
     if (c->state != kReady) return fail(c, RELSIM_ERR_BAD_STATE, "autotune needs a loaded state before a build");
     return DISPATCH(autotune_impl, c, out);
 }
@@ -1851,6 +1900,7 @@ int relsim_deposit_adjoint(relsim_ctx* c, int species, const double* gJ, const d
                            double* gx0, double* gB, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form");
     if (species < 0 || species >= c->cfg.nspecies) return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     if (!gJ || !gM || !gB || (c->sp[species].n > 0 && (!gu0 || !gx0)))
@@ -1865,6 +1915,7 @@ int relsim_push_adjoint(relsim_ctx* c, int species, const double* gu1, const dou
                         double* gx0, double* gE, double* gB, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form");
     if (species < 0 || species >= c->cfg.nspecies) return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     if (c->sp[species].n > 0 && (!gu1 || !gx1 || !gu0 || !gx0)) return fail(c, RELSIM_ERR_INVALID_ARG, "null array");
@@ -1878,6 +1929,7 @@ int relsim_step_adjoint(relsim_ctx* c, double* gE, double* gB, double* const* gu
                         double* rel_residual)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form");
     if (!gE || !gB || !gu || !gx) return fail(c, RELSIM_ERR_INVALID_ARG, "null array");
     for (int s = 0; s < c->cfg.nspecies; ++s)
         if (c->sp[s].n > 0 && (!gu[s] || !gx[s])) return fail(c, RELSIM_ERR_INVALID_ARG, "null particle gradient");
@@ -1908,6 +1960,7 @@ int relsim_field_adjoint(relsim_ctx* c, const double* gE1, const double* gB1, co
                          double* gB0, double* gJ, double* gM, int* iters, double* rel_residual, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form");
     if (!gE1 || !gB1) return fail(c, RELSIM_ERR_INVALID_ARG, "null upstream gradient");
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     if (c->state != kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "the adjoint needs a solved step (before the push)");

@@ -22,10 +22,22 @@ constexpr int kNDir = 9;             // cell-to-cell moves of one step
 constexpr int kMaxSpecies = 4;
 constexpr int kMaxRestart = 100;
 
+// 3D: the half-stored mass matrix keeps 14 of the 27 offsets (0,0,0),
+// (1,0,0), (di,1,0) for di = -1..1 and (di,dj,1) for di, dj = -1..1; the
+// other 13 follow from M_{g+o,g} = M_{g,g+o}.
+constexpr int kHalf3 = 14;
+constexpr int kMBlock3 = kHalf3 * 9;
+
+// ncell counts all cells (nx ny nz in 3D); dV is the cell volume (dx dy in
+// 2D). nz = 1, dz = 1 and dim = 2 for the 2D form.
 struct GridP {
     int nx, ny, ncell;
     double dx, dy, dt, theta, dV;
+    int nz = 1, dim = 2;
+    double dz = 1.0;
 };
+
+__host__ __device__ __forceinline__ int mblock_of(const GridP& g) { return g.dim == 3 ? kMBlock3 : kMBlock; }
 
 __host__ __device__ __forceinline__ int wrap1(int i, int n)
 {

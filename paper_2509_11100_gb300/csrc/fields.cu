@@ -446,7 +446,7 @@ template <typename T>
 __global__ void k_mass_to_double(const T* __restrict__ M, const T* __restrict__ J, double* Md,
                                  double* Jd, GridP g)
 {
-    const int64_t nm = (int64_t)g.ncell * kMBlock, nj = 3 * (int64_t)g.ncell;
+    const int64_t nm = (int64_t)g.ncell * mblock_of(g), nj = 3 * (int64_t)g.ncell;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nm;
          k += (int64_t)gridDim.x * blockDim.x) {
         if (Md) Md[k] = (double)M[k];
@@ -458,7 +458,7 @@ template <typename T>
 __global__ void k_mass_from_double(const double* __restrict__ Md, const double* __restrict__ Jd, T* M,
                                    T* J, GridP g, int* bad)
 {
-    const int64_t nm = (int64_t)g.ncell * kMBlock, nj = 3 * (int64_t)g.ncell;
+    const int64_t nm = (int64_t)g.ncell * mblock_of(g), nj = 3 * (int64_t)g.ncell;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nm;
          k += (int64_t)gridDim.x * blockDim.x) {
         double a = Md[k];
@@ -661,6 +661,7 @@ int grid_for(int64_t n, int threads, int cap)
 int field_grid_blocks(GridP g) { return grid_for(g.ncell, kFieldThreads, 1 << 30); }
 int op_blocks(GridP g, int precision)
 {
+    if (g.dim == 3) return op_blocks3(g);
     const int X = 32, Y = precision == 32 ? OpTile<float>::Y : OpTile<double>::Y;
     return ((g.nx + X - 1) / X) * ((g.ny + Y - 1) / Y);
 }
@@ -685,6 +686,7 @@ cudaError_t fields_to_double(const T* in, double* out, int64_t n, cudaStream_t s
 template <typename T>
 cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStream_t st)
 {
+    if (g.dim == 3) return rhs3<T>(E, B, J, b, g, st);
     count_launches(1);
     k_rhs<T><<<grid_for(g.ncell, 256, 1 << 30), 256, 0, st>>>(E, B, J, b, g);
     return cudaGetLastError();
@@ -695,6 +697,7 @@ cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, 
                       const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st,
                       const GmDyn* dyn = nullptr)
 {
+    if (g.dim == 3) return launch_op3<T, MODE, TR>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, st, dyn);
     // the dynamic shared-memory limit, set once per kernel and device
     static std::atomic<unsigned> attr_set{0};
     const int smem = (int)sizeof(OpShared<T>);
@@ -751,6 +754,7 @@ template <typename T>
 cudaError_t field_update(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0,
                          T* B1, GridP g, double* partial, int nblocks, cudaStream_t st)
 {
+    if (g.dim == 3) return field_update3<T>(x, M, J, Eth, E, B0, B1, g, partial, nblocks, st);
     count_launches(1);
     k_field_update<T><<<nblocks, kFieldThreads, 0, st>>>(x, M, J, Eth, E, B0, B1, g, partial);
     return cudaGetLastError();

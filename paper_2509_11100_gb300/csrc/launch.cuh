@@ -64,6 +64,39 @@ cudaError_t histogram_keys(const int32_t* keys, int64_t n, int32_t* counts, int 
 cudaError_t move_counts(const int32_t* n9, int32_t* count_new, GridP g, cudaStream_t st);
 cudaError_t iota_i32(int32_t* a, int64_t n, cudaStream_t st);
 
+// ----- d3.cu (the 3D form) -----
+struct GmDyn;
+template <typename T>
+struct FzArrays {
+    const T* fz[kMaxSpecies];
+};
+template <typename T>
+cudaError_t load_convert3(const double* x, const double* u, const double* w, int64_t n, GridP g, PArrays<T> out,
+                          T* ofz, int32_t* key, int32_t* val, int* bad, cudaStream_t st);
+template <typename T>
+cudaError_t gather_particles3(const int32_t* perm, PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, int64_t n,
+                              bool ids_from_perm, cudaStream_t st);
+template <typename T>
+cudaError_t export_particles3(PArrays<T> p, const T* fz, const int32_t* start, GridP g, double* x, double* u,
+                              double* w, int32_t* id, cudaStream_t st);
+template <typename T>
+cudaError_t deposit3(const DepositSpecies<T>& ds, const FzArrays<T>& fz, const T* B, T* M, T* J, GridP g,
+                     cudaStream_t st);
+int op_blocks3(GridP g);
+template <typename T, int MODE, bool TR>
+cudaError_t launch_op3(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
+                       const double* V, int64_t ldv, int nv, GridP g, double* partial, cudaStream_t st,
+                       const GmDyn* dyn);
+template <typename T>
+cudaError_t rhs3(const T* E, const T* B, const T* J, double* b, GridP g, cudaStream_t st);
+template <typename T>
+cudaError_t field_update3(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0, T* B1, GridP g,
+                          double* partial, int nblocks, cudaStream_t st);
+int push_blocks3(GridP g);
+template <typename T>
+cudaError_t push3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const int32_t* start, int32_t* key,
+                  const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum, int nblocks, cudaStream_t st);
+
 // ----- adjoint.cu -----
 // lu[i] = gu[id[i]], lx[i] = gx[id[i]] (FP64, 3 and 2 interleaved components)
 cudaError_t gather_grad(const int32_t* id, const double* gu, const double* gx, double* lu, double* lx, int64_t n,
