@@ -661,6 +661,106 @@ def run_window(args):
     print(json.dumps(out), flush=True)
 
 
+def run_3d(args):
+    """The 3D double Harris sheet (256 x 128 x 128 cells, 16 particles per
+    cell per species, 134,217,728 particles; trilinear shapes, 27-node
+    stencil), FP32 form timed over the steps, the FP64 form over a few, the
+    per-kernel times from an event-profiled pass. Its own JSON line."""
+    import numpy as np
+    import torch
+    import paper_2509_11100_gb300 as rs
+    from relsim_inputs import HarrisConfig3, make_harris3
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    small = args.workload == "c2small"
+    hc = HarrisConfig3(nx=64 if small else 256, ny=32 if small else 128, nz=32 if small else 128, ppc=16,
+                       dt=0.5, seed=rank)
+    t0 = time.time()
+    st = make_harris3(hc)
+    t_gen = time.time() - t0
+    N = sum(len(sp["w"]) for sp in st["species"])
+    nn = hc.nx * hc.ny * hc.nz
+
+    def sim_for(prec):
+        cfg = rs.make_config(hc.nx, hc.ny, nz=hc.nz, dt=hc.dt, theta_implicit=hc.theta, precision=prec,
+                             gmres_tol=1e-6 if prec == 32 else 1e-10, gmres_restart=30)
+        sim = rs.Simulation(cfg)
+        sim.load_state(st)
+        return sim
+
+    sim = sim_for(32)
+    for _ in range(args.warmup):
+        sim.step(ledger=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = rs.relsim_kernel_launches()
+    ev0.record(stream)
+    leds = []
+    for _ in range(args.steps):
+        led, status = sim.step(ledger=True)
+        leds.append(led)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = rs.relsim_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    kp = max(1, min(args.steps, 5))
+    sim.profile(True)
+    sim.profile_read(reset=True)
+    for _ in range(kp):
+        sim.step(ledger=True)
+    prof = sim.profile_read(reset=True)
+    sim.profile(False)
+    per_kernel = {k: {"ms_per_step": v[0] / kp, "launches_per_step": v[2] / kp} for k, v in prof.items() if v[1] > 0}
+    peak, peak_kind = measured_peaks()
+    # algorithmic bytes (FP32 form): the deposit reads the 28-byte particle
+    # record and writes M (126 values) and Jhat (3) per node; the push and
+    # re-sort read and write the record, the keys and the permutation
+    # (28 + 28 + 4 + 4 (+ 8 for the radix passes' pairs) bytes per particle)
+    algo = {"deposit": N * 28 + nn * (126 + 3) * 4, "general_sort": N * (28 + 28 + 4 + 4 + 8)}
+    for k, ab in algo.items():
+        if k in per_kernel:
+            gbs = ab / (per_kernel[k]["ms_per_step"] / 1e3) / 1e9
+            per_kernel[k].update({"algorithmic_bytes_per_step": ab, "achieved_gbs": gbs, "frac": gbs / peak})
+    sim.close()
+    fp64 = None
+    if not args.no_fp64:
+        s64 = sim_for(64)
+        s64.step(ledger=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = 2
+        e0.record(stream)
+        for _ in range(k64):
+            l64, _ = s64.step(ledger=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        fp64 = {"value": N / (ms64 / 1e3), "unit": "particle-pushes/s", "ms_per_step": ms64, "steps": k64,
+                "ledger_residual_rel": abs(l64["residual"]) / l64["total"], "speedup_fp32_over_fp64": ms64 / ms}
+        s64.close()
+    last = leds[-1]
+    out = {"metric": METRIC, "value": N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"3D relativistic double Harris sheet, pair plasma, {hc.nx}x{hc.ny}x{hc.nz} cells "
+                                  f"(dx=dy=dz=1 d_e), 16 ppc per species ({N:,} particles), sigma=10, theta_T=0.3, "
+                                  "delta=1 d_e, dt=0.5/omega_pe, theta=0.5, 1% B_y perturbation in x-z modes 1-4, "
+                                  "trilinear shapes (27-node stencil), seed 0",
+                      "form": "FP32 particles/fields/mass matrix, FP64 GMRES basis and ledger",
+                      "l2": "inputs larger than L2 (3.8 GB of particle data per step), no flush"},
+           "per_kernel": per_kernel, "per_kernel_pass": f"{kp} further steps with event profiling",
+           "gpu_launches": launches, "gmres_iters_per_step": float(np.mean([l["gmres_iters"] for l in leds])),
+           "ledger": {"residual_rel": abs(last["residual"]) / last["total"],
+                      "mismatch_rel": abs(last["mismatch"]) / last["total"]},
+           "fp64_form": fp64, "clocks": clk, "input_generation_s": t_gen}
+    print(json.dumps(out), flush=True)
+
+
 def scan_single_reference(rs, torch, sizes=((1024, 512), (768, 384), (128, 64)), steps=20):
     """Single instances with the scan's parameters (32 ppc per species,
     dt = 0.5, delta 1, sigma 10, 0.1% perturbation), graph steps, for scale."""
@@ -700,10 +800,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (no autotuner pass after the load)")
-    ap.add_argument("--workload", choices=["c1", "small", "scan", "window"], default="c1",
+    ap.add_argument("--workload", choices=["c1", "small", "scan", "window", "c2", "c2small"], default="c1",
                     help="small: 512x256 cells for profiler captures; scan: the 48-instance batched "
                          "tearing scan (run with --steps 400 for its full length); window: the "
-                         "differentiable 20-step window on 256x128")
+                         "differentiable 20-step window on 256x128; c2: the 3D sheet on 256x128x128 "
+                         "(c2small: 64x32x32)")
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the scan's batch runner")
     ap.add_argument("--scan-reference", action="store_true",
                     help="scan: also time single 1024x512, 768x384 and 128x64 instances with its parameters")
@@ -716,6 +817,8 @@ def main():
         run_scan(args)
     elif args.workload == "window":
         run_window(args)
+    elif args.workload in ("c2", "c2small"):
+        run_3d(args)
     else:
         run_ours(args)
 
