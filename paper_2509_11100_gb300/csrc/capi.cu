@@ -892,22 +892,22 @@ int push_enqueue(relsim_ctx* c)
         const T* Eth = (const T*)c->Eth;
         const T* B = (const T*)c->B[c->bcur];
         if (c->g.dim == 3) {
-            // 3D: push with the new cell per particle, radix sort, gather
+            // 3D: push with each particle's new cell and its slot there
+            // (warp-aggregated counts), then an unstable counting sort: the
+            // cells' starts by a scan, each particle placed at start + slot.
+            // The order within a cell is not kept (nothing in the 3D form
+            // depends on it beyond rounding; ids follow the particles)
             TRY(ensure_radix(c, sp.n));
             T* sfz = (T*)sp.a[sp.cur][6];
             T* dfz = (T*)sp.a[1 - sp.cur][6];
             PROF_BEGIN(RELSIM_PROF_GENERAL_SORT);
             CK(cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-            CK(push3<T>(src, sfz, dst, dfz, sp.start, c->rk[0], Eth, B, c->g, sc, c->partial, nbp, c->st));
+            CK(cudaMemsetAsync(c->count_new, 0, sizeof(int32_t) * (size_t)(c->g.ncell + 1), c->st));
+            CK(push3<T>(src, sfz, dst, dfz, sp.start, c->rk[0], c->rv[0], c->count_new, Eth, B, c->g, sc, c->partial,
+                        nbp, c->st));
             CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
-            CK(iota_i32(c->rv[0], sp.n, c->st));
-            bool in1 = false;
-            CK(radix_sort_pairs(c->rk[0], c->rv[0], c->rk[1], c->rv[1], sp.n, c->key_bits, c->rtmp, &in1, c->st));
-            const int32_t* keys = c->rk[in1 ? 1 : 0];
-            const int32_t* perm = c->rv[in1 ? 1 : 0];
-            CK(gather_particles3<T>(perm, dst, dfz, src, sfz, sp.n, false, c->st));
-            CK(histogram_keys(keys, sp.n, c->count_new, c->g.ncell, c->st));
             CK(scan_exclusive_i32(c->count_new, sp.start, c->g.ncell, sp.start + c->g.ncell, c->scan_tmp, c->st));
+            CK(place3<T>(dst, dfz, src, sfz, c->rk[0], c->rv[0], sp.start, sp.n, c->st));
             PROF_END();
         } else if (c->fast_sort) {
             // push, each old cell written back grouped by move direction

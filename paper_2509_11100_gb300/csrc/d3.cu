@@ -188,7 +188,48 @@ __device__ __forceinline__ void alpha3(const T (&Bp)[3], T beta, T gbar, T (&al)
 constexpr int kDepWarps3 = 4;
 constexpr int kStage3 = 21;   // staged values per particle (20, padded to an odd stride)
 
-// the 36 unordered corner pairs (a <= b) of a cell, pair q: a = pa3(q), b = pb3(q)
+// a 3x3 block added to the stored block at dst (offset index hs): in FP32
+// as paired atomics (8-byte aligned pairs: the block starts on an even float
+// when hs is even, as 126 per node is even), halving the atomic operations
+__device__ __forceinline__ void add_block9(float* dst, const float (&v)[9], int hs)
+{
+    // constant indices in both branches keep v in registers
+    if (hs & 1) {
+        atomicAdd(dst, v[0]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            atomicAdd(reinterpret_cast<float2*>(dst + 1 + 2 * e), make_float2(v[1 + 2 * e], v[2 + 2 * e]));
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            atomicAdd(reinterpret_cast<float2*>(dst + 2 * e), make_float2(v[2 * e], v[2 * e + 1]));
+        atomicAdd(dst + 8, v[8]);
+    }
+}
+__device__ __forceinline__ void add_block9(double* dst, const double (&v)[9], int)
+{
+#pragma unroll
+    for (int e = 0; e < 9; ++e) atomicAdd(dst + e, v[e]);
+}
+
+// flush a cell's pair block: the block of pair (a, b) is stored at corner a
+// with the offset b - a when that offset is in the stored half, else at
+// corner b with a - b
+template <typename T>
+__device__ __forceinline__ void flush_pair3(T* M, int a, int b, const T (&acc)[9], int i, int j, int k, GridP g)
+{
+    const int di = (b & 1) - (a & 1), dj = ((b >> 1) & 1) - ((a >> 1) & 1), dk = ((b >> 2) & 1) - ((a >> 2) & 1);
+    int hs = half3(di, dj, dk), at = a;
+    if (hs < 0) {
+        hs = half3(-di, -dj, -dk);
+        at = b;
+    }
+    const int64_t gn =
+        node3(wrap1(i + (at & 1), g.nx), wrap1(j + ((at >> 1) & 1), g.ny), wrap1(k + ((at >> 2) & 1), g.nz), g);
+    add_block9(M + gn * kMBlock3 + hs * 9, acc, hs);
+}
+
+// the 36 unordered corner pairs (a <= b) of a cell, pair q
 __device__ __forceinline__ void pair_of(int q, int& a, int& b)
 {
     int r = q;
@@ -231,65 +272,68 @@ k_deposit3(DepositSpecies<T> ds, FzArrays<T> fz, const T* __restrict__ B, T* __r
             T acc0[9], acc1[9], accj = T(0);
 #pragma unroll
             for (int e = 0; e < 9; ++e) acc0[e] = acc1[e] = T(0);
-            bool any = false;
-            for (int s = 0; s < ds.nsp; ++s) {
-                const int p0 = ds.start[s][c], p1 = ds.start[s][c + 1];
-                any = any || p1 > p0;
-                for (int q0 = p0; q0 < p1; q0 += 32) {
-                    const int p = q0 + lane;
-                    if (p < p1) {
-                        const T fx = ld(ds.fx[s] + p), fy = ld(ds.fy[s] + p), fzz = ld(fz.fz[s] + p);
-                        const T ux = ld(ds.ux[s] + p), uy = ld(ds.uy[s] + p), uz = ld(ds.uz[s] + p);
-                        const T wt = ld(ds.w[s] + p);
-                        T W[8], Bp[3], al[9];
-                        corner_weights(fx, fy, fzz, W);
-                        gather_B3(B, i, j, k, fx, fy, fzz, g, Bp);
-                        const T gbar = sqrt(T(1) + ux * ux + uy * uy + uz * uz);
-                        alpha3(Bp, ds.beta[s], gbar, al);
-                        const T cM = wt * ds.cM[s] / gbar, cJ = wt * ds.cJ[s] / gbar;
+            // the cell's particles of all species as one list (cum[s] = the
+            // first list index of species s), staged 32 at a time
+            // (fully unrolled over the species so the tables stay in registers)
+            int cum[kMaxSpecies + 1], pst[kMaxSpecies];
+            cum[0] = 0;
 #pragma unroll
-                        for (int a = 0; a < 8; ++a) st[lane][a] = W[a];
-#pragma unroll
-                        for (int e = 0; e < 9; ++e) st[lane][8 + e] = cM * al[e];
-#pragma unroll
-                        for (int r = 0; r < 3; ++r)
-                            st[lane][17 + r] = cJ * (al[3 * r] * ux + al[3 * r + 1] * uy + al[3 * r + 2] * uz);
-                    }
-                    __syncwarp();
-                    const int m = min(32, p1 - q0);
-                    for (int t = 0; t < m; ++t) {
-                        const T wab = st[t][a0] * st[t][b0];
-#pragma unroll
-                        for (int e = 0; e < 9; ++e) acc0[e] += wab * st[t][8 + e];
-                        if (two) {
-                            const T w1 = st[t][a1] * st[t][b1];
-#pragma unroll
-                            for (int e = 0; e < 9; ++e) acc1[e] += w1 * st[t][8 + e];
-                        }
-                        if (ownj) accj += st[t][ja] * st[t][17 + jc];
-                    }
-                    __syncwarp();
-                }
+            for (int s = 0; s < kMaxSpecies; ++s) {
+                pst[s] = s < ds.nsp ? ds.start[s][c] : 0;
+                cum[s + 1] = cum[s] + (s < ds.nsp ? ds.start[s][c + 1] - pst[s] : 0);
             }
-            if (!any) continue;
+            const int total = cum[kMaxSpecies];
+            if (total == 0) continue;
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int t = q0 + lane;
+                if (t < total) {
+                    int s = 0, p = pst[0] + t;
+#pragma unroll
+                    for (int q = 1; q < kMaxSpecies; ++q)
+                        if (t >= cum[q] && cum[q + 1] > cum[q]) {
+                            s = q;
+                            p = pst[q] + (t - cum[q]);
+                        }
+                    const T fx = ld(ds.fx[s] + p), fy = ld(ds.fy[s] + p), fzz = ld(fz.fz[s] + p);
+                    const T ux = ld(ds.ux[s] + p), uy = ld(ds.uy[s] + p), uz = ld(ds.uz[s] + p);
+                    const T wt = ld(ds.w[s] + p);
+                    T W[8], Bp[3], al[9];
+                    corner_weights(fx, fy, fzz, W);
+                    gather_B3(B, i, j, k, fx, fy, fzz, g, Bp);
+                    const T gbar = sqrt(T(1) + ux * ux + uy * uy + uz * uz);
+                    alpha3(Bp, ds.beta[s], gbar, al);
+                    const T cM = wt * ds.cM[s] / gbar, cJ = wt * ds.cJ[s] / gbar;
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) st[lane][a] = W[a];
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) st[lane][8 + e] = cM * al[e];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+                        st[lane][17 + r] = cJ * (al[3 * r] * ux + al[3 * r + 1] * uy + al[3 * r + 2] * uz);
+                }
+                __syncwarp();
+                const int m = min(32, total - q0);
+                for (int t2 = 0; t2 < m; ++t2) {
+                    T al[9];
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) al[e] = st[t2][8 + e];
+                    const T wab = st[t2][a0] * st[t2][b0];
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) acc0[e] += wab * al[e];
+                    if (two) {
+                        const T w1 = st[t2][a1] * st[t2][b1];
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) acc1[e] += w1 * al[e];
+                    }
+                    if (ownj) accj += st[t2][ja] * st[t2][17 + jc];
+                }
+                __syncwarp();
+            }
             // flush: the block of pair (a, b) is stored at corner a with the
             // offset b - a when that offset is in the stored half, else at
             // corner b with a - b
-            for (int h = 0; h < (two ? 2 : 1); ++h) {
-                const int a = h ? a1 : a0, b = h ? b1 : b0;
-                const int di = (b & 1) - (a & 1), dj = ((b >> 1) & 1) - ((a >> 1) & 1),
-                          dk = ((b >> 2) & 1) - ((a >> 2) & 1);
-                int hs = half3(di, dj, dk), at = a;
-                if (hs < 0) {
-                    hs = half3(-di, -dj, -dk);
-                    at = b;
-                }
-                const int64_t gn = node3(wrap1(i + (at & 1), g.nx), wrap1(j + ((at >> 1) & 1), g.ny),
-                                         wrap1(k + ((at >> 2) & 1), g.nz), g);
-                T* dst = M + gn * kMBlock3 + hs * 9;
-#pragma unroll
-                for (int e = 0; e < 9; ++e) atomicAdd(dst + e, h ? acc1[e] : acc0[e]);
-            }
+            flush_pair3(M, a0, b0, acc0, i, j, k, g);
+            if (two) flush_pair3(M, a1, b1, acc1, i, j, k, g);
             if (ownj) {
                 const int64_t gn = node3(wrap1(i + (ja & 1), g.nx), wrap1(j + ((ja >> 1) & 1), g.ny),
                                          wrap1(k + ((ja >> 2) & 1), g.nz), g);
@@ -639,12 +683,16 @@ constexpr int kPushWarps3 = 4;
 // as a cell shift plus offsets; the pushed particle goes to the same index
 // of dst with its new cell in key. Ledger sums per block: dK, work,
 // mismatch, K1 (as the 2D push). Warp per row segment of up to 32 cells, the
-// lanes over the segment's particles.
+// lanes over the segment's particles. With rank non-null each particle also
+// takes a slot among its new cell's particles, rank[p] = count[key]++ (one
+// atomic per new cell and warp: the lanes with equal keys found by
+// match-any), for the unstable counting sort that follows.
 template <typename T>
 __global__ void __launch_bounds__(32 * kPushWarps3)
 k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict__ dfz,
-        const int32_t* __restrict__ start, int32_t* __restrict__ key, const T* __restrict__ Eth,
-        const T* __restrict__ B, GridP g, T beta, T qdt, T m, double* __restrict__ lsum)
+        const int32_t* __restrict__ start, int32_t* __restrict__ key, int32_t* __restrict__ rank,
+        int32_t* __restrict__ count, const T* __restrict__ Eth, const T* __restrict__ B, GridP g, T beta, T qdt,
+        T m, double* __restrict__ lsum)
 {
     __shared__ int sst[kPushWarps3][33];
     __shared__ double red[32 * 4];
@@ -668,7 +716,11 @@ k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict
         __syncwarp();
         const int P0 = ss[0], P1 = ss[cn];
         int cl = 0;
-        for (int p = P0 + lane; p < P1; p += 32) {
+        for (int p0 = P0; p0 < P1; p0 += 32) {
+            const int p = p0 + lane;
+            const bool act = p < P1;
+            int newkey = -1 - lane;   // distinct for idle lanes
+            if (act) {
             while (ss[cl + 1] <= p) ++cl;
             const int i = i0 + cl;
             const T fx = ld(src.fx + p), fy = ld(src.fy + p), fz = ld(sfz + p);
@@ -720,7 +772,8 @@ k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict
             dst.uz[p] = u1z;
             dst.w[p] = w;
             if (dst.id) dst.id[p] = src.id[p];
-            key[p] = (int32_t)node3(cnew[0], cnew[1], cnew[2], g);
+            newkey = (int32_t)node3(cnew[0], cnew[1], cnew[2], g);
+            key[p] = newkey;
             // ledger: g0 - g1 = (u0 - u1).(u0 + u1)/(g0 + g1)
             const T ue = ubx * E[0] + uby * E[1] + ubz * E[2];
             const T du = (ux - u1x) * (ux + u1x) + (uy - u1y) * (uy + u1y) + (uz - u1z) * (uz + u1z);
@@ -729,6 +782,15 @@ k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict
             acc[1] += qdt * w * ue / g0;
             acc[2] += qdt * w * ue * du * igs * igs / g0;
             acc[3] += w * m * u12 / (g1 + T(1));
+            }
+            if (rank) {
+                const unsigned peers = __match_any_sync(0xffffffffu, newkey);
+                const int leader = __ffs(peers) - 1;
+                int base = 0;
+                if (act && lane == leader) base = atomicAdd(count + newkey, __popc(peers));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (act) rank[p] = base + __popc(peers & ((1u << lane) - 1u));
+            }
         }
         __syncwarp();
     }
@@ -739,6 +801,25 @@ k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict
     if (threadIdx.x == 0)
 #pragma unroll
         for (int q = 0; q < 4; ++q) lsum[(int64_t)blockIdx.x * 4 + q] = o[q];
+}
+
+// the counting sort's placement: particle p to start[key[p]] + rank[p]
+template <typename T>
+__global__ void k_place3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict__ dfz,
+                         const int32_t* __restrict__ key, const int32_t* __restrict__ rank,
+                         const int32_t* __restrict__ start, int64_t n)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = (int64_t)start[key[p]] + rank[p];
+        dst.fx[q] = src.fx[p];
+        dst.fy[q] = src.fy[p];
+        dfz[q] = sfz[p];
+        dst.ux[q] = src.ux[p];
+        dst.uy[q] = src.uy[p];
+        dst.uz[q] = src.uz[p];
+        dst.w[q] = src.w[p];
+        if (dst.id) dst.id[q] = src.id[p];
+    }
 }
 
 }  // namespace
@@ -823,12 +904,23 @@ int push_blocks3(GridP g)
 
 template <typename T>
 cudaError_t push3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const int32_t* start, int32_t* key,
-                  const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum, int nblocks, cudaStream_t st)
+                  int32_t* rank, int32_t* count, const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum,
+                  int nblocks, cudaStream_t st)
 {
     count_launches(1);
-    k_push3<T><<<nblocks, 32 * kPushWarps3, 0, st>>>(src, sfz, dst, dfz, start, key, Eth, B, g,
+    k_push3<T><<<nblocks, 32 * kPushWarps3, 0, st>>>(src, sfz, dst, dfz, start, key, rank, count, Eth, B, g,
                                                        (T)(sc.q * g.dt / (2.0 * sc.m)), (T)(sc.q * g.dt), (T)sc.m,
                                                        lsum);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t place3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const int32_t* key, const int32_t* rank,
+                   const int32_t* start, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launches(1);
+    k_place3<T><<<grid3(n, 256, 152 * 32), 256, 0, st>>>(src, sfz, dst, dfz, key, rank, start, n);
     return cudaGetLastError();
 }
 
@@ -844,8 +936,10 @@ cudaError_t push3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const in
     template cudaError_t rhs3<T>(const T*, const T*, const T*, double*, GridP, cudaStream_t);                      \
     template cudaError_t field_update3<T>(const double*, const T*, const T*, T*, T*, const T*, T*, GridP, double*, \
                                           int, cudaStream_t);                                                      \
-    template cudaError_t push3<T>(PArrays<T>, const T*, PArrays<T>, T*, const int32_t*, int32_t*, const T*,        \
-                                  const T*, GridP, SpeciesConst, double*, int, cudaStream_t);                      \
+    template cudaError_t push3<T>(PArrays<T>, const T*, PArrays<T>, T*, const int32_t*, int32_t*, int32_t*,        \
+                                  int32_t*, const T*, const T*, GridP, SpeciesConst, double*, int, cudaStream_t);  \
+    template cudaError_t place3<T>(PArrays<T>, const T*, PArrays<T>, T*, const int32_t*, const int32_t*,           \
+                                   const int32_t*, int64_t, cudaStream_t);                                         \
     template cudaError_t launch_op3<T, 0, false>(const T*, const double*, double, const double*, double*, double*, \
                                                  const double*, int64_t, int, GridP, double*, cudaStream_t,        \
                                                  const GmDyn*);                                                    \

@@ -93,9 +93,14 @@ template <typename T>
 cudaError_t field_update3(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0, T* B1, GridP g,
                           double* partial, int nblocks, cudaStream_t st);
 int push_blocks3(GridP g);
+// rank/count null: keys only; else rank[p] = slot among the new cell's particles (count zeroed first)
 template <typename T>
 cudaError_t push3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const int32_t* start, int32_t* key,
-                  const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum, int nblocks, cudaStream_t st);
+                  int32_t* rank, int32_t* count, const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum,
+                  int nblocks, cudaStream_t st);
+template <typename T>
+cudaError_t place3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const int32_t* key, const int32_t* rank,
+                   const int32_t* start, int64_t n, cudaStream_t st);
 
 // ----- adjoint.cu -----
 // lu[i] = gu[id[i]], lx[i] = gx[id[i]] (FP64, 3 and 2 interleaved components)
