@@ -183,10 +183,114 @@ __device__ __forceinline__ void alpha3(const T (&Bp)[3], T beta, T gbar, T (&al)
 }
 
 // ---------------------------------------------------------------------------
+// field tiles of a row segment (cells i0 .. i0+cn-1 of row (j, k)), staged in
+// shared memory once per segment instead of 24 gathers per particle per field
+
+template <typename T>
+struct Tile3 {
+    T E[3][2][2][33];   // [comp][dy][dz][c]: node (i0 + c, j + dy, k + dz)
+    T B[3][3][3][34];   // [comp][dy][dz][c]: centre (i0 - 1 + c, j - 1 + dy, k - 1 + dz)
+};
+
+template <typename T>
+__device__ __forceinline__ void load_tile3(Tile3<T>& tl, const T* __restrict__ E, const T* __restrict__ B, int i0,
+                                           int cn, int j, int k, const GridP& g, int lane)
+{
+    const int64_t nc = g.ncell;
+    if (E)
+        for (int q = lane; q < 3 * 2 * 2 * 33; q += 32) {
+            const int c = q % 33, dz = (q / 33) % 2, dy = (q / 66) % 2, comp = q / 132;
+            if (c <= cn)
+                tl.E[comp][dy][dz][c] =
+                    ld(E + comp * nc + node3(wrap1(i0 + c, g.nx), wrap1(j + dy, g.ny), wrap1(k + dz, g.nz), g));
+        }
+    for (int q = lane; q < 3 * 3 * 3 * 34; q += 32) {
+        const int c = q % 34, dz = (q / 34) % 3, dy = (q / 102) % 3, comp = q / 306;
+        if (c <= cn + 1)
+            tl.B[comp][dy][dz][c] =
+                ld(B + comp * nc + node3(wrap1(i0 - 1 + c, g.nx), wrap1(j - 1 + dy, g.ny), wrap1(k - 1 + dz, g.nz), g));
+    }
+    __syncwarp();
+}
+
+// B^n at a particle of local cell cl with offsets f, from the tile
+template <typename T>
+__device__ __forceinline__ void tile_B3(const Tile3<T>& tl, int cl, T fx, T fy, T fz, T (&Bp)[3])
+{
+    const bool lx = fx < T(0.5), ly = fy < T(0.5), lz = fz < T(0.5);
+    const T tx = lx ? fx + T(0.5) : fx - T(0.5);
+    const T ty = ly ? fy + T(0.5) : fy - T(0.5);
+    const T tz = lz ? fz + T(0.5) : fz - T(0.5);
+    const int c0 = lx ? cl : cl + 1, y0 = ly ? 0 : 1, z0 = lz ? 0 : 1;
+    T W[8];
+    corner_weights(tx, ty, tz, W);
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+        T b = T(0);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) b += W[a] * tl.B[comp][y0 + ((a >> 1) & 1)][z0 + ((a >> 2) & 1)][c0 + (a & 1)];
+        Bp[comp] = b;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // deposit
 
-constexpr int kDepWarps3 = 4;
-constexpr int kStage3 = 21;   // staged values per particle (20, padded to an odd stride)
+template <typename T>
+struct DepCfg3 {
+    static constexpr int warps = sizeof(T) == 4 ? 4 : 2;   // static shared memory < 48 KB
+};
+constexpr int kStage3 = 22;   // staged values per particle (20, padded to an even stride for paired loads)
+
+// a pair block's 9 sums; in FP32 as four pairs and one, accumulated with
+// the paired FMA (one instruction for two sums)
+template <typename T>
+struct PairAcc {
+    T v[9];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) v[e] = T(0);
+    }
+    __device__ __forceinline__ void add(T w, const T* al)
+    {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) v[e] += w * al[e];
+    }
+    __device__ __forceinline__ void get(T (&o)[9]) const
+    {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) o[e] = v[e];
+    }
+};
+template <>
+struct PairAcc<float> {
+    float2 v2[4];
+    float v8;
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v2[k] = make_float2(0.f, 0.f);
+        v8 = 0.f;
+    }
+    // al: 8-byte aligned row of the 9 staged values
+    __device__ __forceinline__ void add(float w, const float2 (&al2)[4], float al8)
+    {
+        const float2 ww = make_float2(w, w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v2[k] = __ffma2_rn(ww, al2[k], v2[k]);
+        v8 = fmaf(w, al8, v8);
+    }
+    __device__ __forceinline__ void get(float (&o)[9]) const
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            o[2 * k] = v2[k].x;
+            o[2 * k + 1] = v2[k].y;
+        }
+        o[8] = v8;
+    }
+};
 
 // a 3x3 block added to the stored block at dst (offset index hs): in FP32
 // as paired atomics (8-byte aligned pairs: the block starts on an even float
@@ -242,11 +346,13 @@ __device__ __forceinline__ void pair_of(int q, int& a, int& b)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kDepWarps3)
+__global__ void __launch_bounds__(32 * DepCfg3<T>::warps)
 k_deposit3(DepositSpecies<T> ds, FzArrays<T> fz, const T* __restrict__ B, T* __restrict__ M, T* __restrict__ J,
            GridP g)
 {
-    __shared__ T sh[kDepWarps3][32][kStage3];
+    constexpr int kW = DepCfg3<T>::warps;
+    __shared__ __align__(16) T sh[kW][32][kStage3];
+    __shared__ Tile3<T> stl[kW];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -266,12 +372,15 @@ k_deposit3(DepositSpecies<T> ds, FzArrays<T> fz, const T* __restrict__ B, T* __r
         const int jk = (int)(u / nseg);
         const int j = jk % g.ny, k = jk / g.ny;
         const int cn = min(32, g.nx - i0);
+        __syncwarp();
+        load_tile3<T>(stl[wib], nullptr, B, i0, cn, j, k, g, lane);
         for (int cl = 0; cl < cn; ++cl) {
             const int i = i0 + cl;
             const int64_t c = node3(i, j, k, g);
-            T acc0[9], acc1[9], accj = T(0);
-#pragma unroll
-            for (int e = 0; e < 9; ++e) acc0[e] = acc1[e] = T(0);
+            PairAcc<T> acc0, acc1;
+            acc0.zero();
+            acc1.zero();
+            T accj = T(0);
             // the cell's particles of all species as one list (cum[s] = the
             // first list index of species s), staged 32 at a time
             // (fully unrolled over the species so the tables stay in registers)
@@ -299,7 +408,7 @@ k_deposit3(DepositSpecies<T> ds, FzArrays<T> fz, const T* __restrict__ B, T* __r
                     const T wt = ld(ds.w[s] + p);
                     T W[8], Bp[3], al[9];
                     corner_weights(fx, fy, fzz, W);
-                    gather_B3(B, i, j, k, fx, fy, fzz, g, Bp);
+                    tile_B3(stl[wib], cl, fx, fy, fzz, Bp);
                     const T gbar = sqrt(T(1) + ux * ux + uy * uy + uz * uz);
                     alpha3(Bp, ds.beta[s], gbar, al);
                     const T cM = wt * ds.cM[s] / gbar, cJ = wt * ds.cJ[s] / gbar;
@@ -314,16 +423,22 @@ k_deposit3(DepositSpecies<T> ds, FzArrays<T> fz, const T* __restrict__ B, T* __r
                 __syncwarp();
                 const int m = min(32, total - q0);
                 for (int t2 = 0; t2 < m; ++t2) {
-                    T al[9];
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) al[e] = st[t2][8 + e];
                     const T wab = st[t2][a0] * st[t2][b0];
+                    const T w1 = two ? st[t2][a1] * st[t2][b1] : T(0);
+                    if constexpr (sizeof(T) == 4) {
+                        float2 al2[4];
+                        const float2* r2 = reinterpret_cast<const float2*>(&st[t2][8]);
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) acc0[e] += wab * al[e];
-                    if (two) {
-                        const T w1 = st[t2][a1] * st[t2][b1];
+                        for (int q = 0; q < 4; ++q) al2[q] = r2[q];
+                        const float al8 = st[t2][16];
+                        acc0.add(wab, al2, al8);
+                        if (two) acc1.add(w1, al2, al8);
+                    } else {
+                        T al[9];
 #pragma unroll
-                        for (int e = 0; e < 9; ++e) acc1[e] += w1 * al[e];
+                        for (int e = 0; e < 9; ++e) al[e] = st[t2][8 + e];
+                        acc0.add(wab, al);
+                        if (two) acc1.add(w1, al);
                     }
                     if (ownj) accj += st[t2][ja] * st[t2][17 + jc];
                 }
@@ -332,8 +447,15 @@ k_deposit3(DepositSpecies<T> ds, FzArrays<T> fz, const T* __restrict__ B, T* __r
             // flush: the block of pair (a, b) is stored at corner a with the
             // offset b - a when that offset is in the stored half, else at
             // corner b with a - b
-            flush_pair3(M, a0, b0, acc0, i, j, k, g);
-            if (two) flush_pair3(M, a1, b1, acc1, i, j, k, g);
+            {
+                T v[9];
+                acc0.get(v);
+                flush_pair3(M, a0, b0, v, i, j, k, g);
+                if (two) {
+                    acc1.get(v);
+                    flush_pair3(M, a1, b1, v, i, j, k, g);
+                }
+            }
             if (ownj) {
                 const int64_t gn = node3(wrap1(i + (ja & 1), g.nx), wrap1(j + ((ja >> 1) & 1), g.ny),
                                          wrap1(k + ((ja >> 2) & 1), g.nz), g);
@@ -695,6 +817,7 @@ k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict
         T m, double* __restrict__ lsum)
 {
     __shared__ int sst[kPushWarps3][33];
+    __shared__ Tile3<T> stl[kPushWarps3];
     __shared__ double red[32 * 4];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -711,9 +834,11 @@ k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict
         const int j = jk % g.ny, k = jk / g.ny;
         const int cn = min(32, g.nx - i0);
         const int64_t c0 = node3(i0, j, k, g);
+        __syncwarp();
         if (lane <= cn) ss[lane] = start[c0 + lane];
         if (lane == 0 && cn == 32) ss[32] = start[c0 + 32];
-        __syncwarp();
+        load_tile3<T>(stl[wib], Eth, B, i0, cn, j, k, g, lane);
+        const Tile3<T>& tl = stl[wib];
         const int P0 = ss[0], P1 = ss[cn];
         int cl = 0;
         for (int p0 = P0; p0 < P1; p0 += 32) {
@@ -727,16 +852,16 @@ k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict
             const T ux = ld(src.ux + p), uy = ld(src.uy + p), uz = ld(src.uz + p), w = ld(src.w + p);
             T W[8];
             corner_weights(fx, fy, fz, W);
-            const int ii[2] = {i, wrap1(i + 1, g.nx)}, jj[2] = {j, wrap1(j + 1, g.ny)}, kk[2] = {k, wrap1(k + 1, g.nz)};
-            T E[3] = {T(0), T(0), T(0)};
+            T E[3];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) {
-                const int64_t gn = node3(ii[a & 1], jj[(a >> 1) & 1], kk[(a >> 2) & 1], g);
+            for (int c = 0; c < 3; ++c) {
+                T e = T(0);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) E[c] += W[a] * ld(Eth + c * nc + gn);
+                for (int a = 0; a < 8; ++a) e += W[a] * tl.E[c][(a >> 1) & 1][(a >> 2) & 1][cl + (a & 1)];
+                E[c] = e;
             }
             T Bp[3];
-            gather_B3(B, i, j, k, fx, fy, fz, g, Bp);
+            tile_B3(tl, cl, fx, fy, fz, Bp);
             const T u02 = ux * ux + uy * uy + uz * uz;
             const T g0 = sqrt(T(1) + u02);
             const T ax = beta * Bp[0] / g0, ay = beta * Bp[1] / g0, az = beta * Bp[2] / g0;
@@ -859,7 +984,7 @@ cudaError_t deposit3(const DepositSpecies<T>& ds, const FzArrays<T>& fz, const T
 {
     const int64_t units = (int64_t)((g.nx + 31) / 32) * g.ny * g.nz;
     count_launches(1);
-    k_deposit3<T><<<grid3(units, kDepWarps3, 152 * 8), 32 * kDepWarps3, 0, st>>>(ds, fz, B, M, J, g);
+    k_deposit3<T><<<grid3(units, DepCfg3<T>::warps, 152 * 8), 32 * DepCfg3<T>::warps, 0, st>>>(ds, fz, B, M, J, g);
     return cudaGetLastError();
 }
 
