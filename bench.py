@@ -744,6 +744,22 @@ def run_3d(args):
         fp64 = {"value": N / (ms64 / 1e3), "unit": "particle-pushes/s", "ms_per_step": ms64, "steps": k64,
                 "ledger_residual_rel": abs(l64["residual"]) / l64["total"], "speedup_fp32_over_fp64": ms64 / ms}
         s64.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the 3D oracle as it stands on one core, on the same sheet at 64x32x32
+        # (16 ppc per species, 2,097,152 particles): one full step
+        from oracle.three import Particles3, make_config3, step3
+        sc = HarrisConfig3(nx=64, ny=32, nz=32, ppc=16, dt=0.5, seed=rank)
+        ss = make_harris3(sc)
+        c3 = make_config3(sc.nx, sc.ny, sc.nz, dt=sc.dt, theta=sc.theta, gmres_tol=1e-12, gmres_restart=50)
+        P3 = Particles3(ss["species"])
+        t0 = time.perf_counter()
+        step3(c3, P3, ss["E"], ss["B"])
+        dtc = time.perf_counter() - t0
+        n3 = int(P3.off[-1])
+        cpu = {"value": n3 / dtc, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the same 3D sheet on 64x32x32 cells ({n3} particles), one full oracle step "
+                         "(deposit, GMRES tol 1e-12, push), single thread, FP64", "seconds": dtc}
     last = leds[-1]
     out = {"metric": METRIC, "value": N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -757,7 +773,7 @@ def run_3d(args):
            "gpu_launches": launches, "gmres_iters_per_step": float(np.mean([l["gmres_iters"] for l in leds])),
            "ledger": {"residual_rel": abs(last["residual"]) / last["total"],
                       "mismatch_rel": abs(last["mismatch"]) / last["total"]},
-           "fp64_form": fp64, "clocks": clk, "input_generation_s": t_gen}
+           "fp64_form": fp64, "cpu_baseline": cpu, "clocks": clk, "input_generation_s": t_gen}
     print(json.dumps(out), flush=True)
 
 
