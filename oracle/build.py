@@ -13,6 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "relsim_oracle.c")
 SRC3 = os.path.join(HERE, "relsim_oracle3.c")
+SRCQ = os.path.join(HERE, "relsim_oracle_q.c")
 
 
 def lib_path() -> str:
@@ -24,11 +25,12 @@ def build(force: bool = False) -> str:
     if (not force and os.path.exists(out)
             and os.path.getmtime(out) >= os.path.getmtime(SRC)
             and os.path.getmtime(out) >= os.path.getmtime(SRC3)
+            and os.path.getmtime(out) >= os.path.getmtime(SRCQ)
             and os.path.getmtime(out) >= os.path.getmtime(os.path.join(HERE, "relsim_oracle.h"))):
         return out
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-o", tmp, SRC, SRC3, "-lm"]
+           "-fno-fast-math", "-Wall", "-o", tmp, SRC, SRC3, SRCQ, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

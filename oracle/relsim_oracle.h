@@ -104,6 +104,26 @@ int    orc_step(const orc_config* c, const int64_t* off,
                 double* E, double* B, orc_ledger* led,
                 double* J_out, double* M_out, double* Etheta_out);
 
+/* ---- 2D with quadratic (TSC) shapes (relsim_oracle_q.c): a particle
+   touches 3 x 3 nodes; M for all 25 offsets, M[((g*25 + o)*3 + r)*3 + s]
+   with o = (dj+2)*5 + (di+2). Curls, rhs, field update, energies: the 2D
+   functions above. Base scheme. */
+void   orcq_node_weights(const orc_config* c, double x, double y, int64_t g[9], double W[9]);
+void   orcq_gather_E(const orc_config* c, const double* E, double x, double y, double out[3]);
+void   orcq_gather_B(const orc_config* c, const double* B, double x, double y, double out[3]);
+void   orcq_deposit(const orc_config* c, const int64_t* off, const double* x, const double* y,
+                    const double* ux, const double* uy, const double* uz, const double* w, const double* B,
+                    double* J, double* M);
+void   orcq_apply_M(const orc_config* c, const double* M, const double* v, double* out);
+void   orcq_apply_A(const orc_config* c, const double* M, const double* v, double* out);
+int    orcq_gmres(const orc_config* c, const double* M, const double* b, double* x, int* iters,
+                  double* relres);
+void   orcq_push(const orc_config* c, const int64_t* off, double* x, double* y, double* ux, double* uy,
+                 double* uz, const double* w, const double* Etheta, const double* B, double sums[4]);
+int    orcq_step(const orc_config* c, const int64_t* off, double* x, double* y, double* ux, double* uy,
+                 double* uz, const double* w, double* E, double* B, orc_ledger* led, double* J_out,
+                 double* M_out, double* Etheta_out);
+
 /* ---- 3D (relsim_oracle3.c): periodic nx x ny x nz, trilinear shapes, the
    base scheme. Node and cell (i,j,k) have linear index (k*ny + j)*nx + i;
    M[((g*27 + o)*3 + r)*3 + s] with o = (dk+1)*9 + (dj+1)*3 + (di+1). */

@@ -103,10 +103,22 @@ MUTANTS3 = {
                            "                    d[1][comp] = sy / (4.0 * c->dy);\n"
                            "                    d[2][comp] = sz / (4.0 * c->dy);"),
 }
+# mistakes planted in the quadratic-shape oracle, caught by its own pins
+MUTANTSQ = {
+    "quad_outer_weights_swapped": ("    w[0] = 0.5 * (0.5 - d) * (0.5 - d);\n", "    w[0] = 0.5 * (0.5 + d) * (0.5 + d);\n"),
+    "quad_centre_weight": ("    w[1] = 0.75 - d * d;\n", "    w[1] = 0.75 - 0.5 * d * d;\n"),
+    "quadB_on_nodes": ("    weightsq(c, x, y, 0.5, g, W);\n", "    weightsq(c, x, y, 0.0, g, W);\n"),
+    "quad_pair_offset_transposed": ("int o = (dj + 2) * 5 + (di + 2);\n                    double* blk",
+                                    "int o = (di + 2) * 5 + (dj + 2);\n                    double* blk"),
+    "quad_apply_M_wrong_neighbour": ("int64_t h = wrapq(j + dj, ny) * nx + wrapq(i + di, nx);",
+                                     "int64_t h = wrapq(j - dj, ny) * nx + wrapq(i + di, nx);"),
+    "quad_mass_matrix_drops_gamma": ("double cM = w[p] * q * beta / (gbar * dV);", "double cM = w[p] * q * beta / dV;"),
+}
 PINS = "test_oracle_pins.py"
 CASES = {**{k: ("relsim_oracle.c",) + v + (PINS,) for k, v in MUTANTS.items()},
          **{k: ("__init__.py",) + v + (PINS,) for k, v in PY_MUTANTS.items()},
-         **{k: ("relsim_oracle3.c",) + v + ("test_oracle3_pins.py",) for k, v in MUTANTS3.items()}}
+         **{k: ("relsim_oracle3.c",) + v + ("test_oracle3_pins.py",) for k, v in MUTANTS3.items()},
+         **{k: ("relsim_oracle_q.c",) + v + ("test_oracle_q_pins.py",) for k, v in MUTANTSQ.items()}}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
