@@ -110,6 +110,13 @@ typedef struct {
                               the predicted half-step momentum (E^n standing
                               in for E^{n+theta}), which shrinks the
                               relativistic energy error of a step          */
+    int shape;             /* particle shape: 0 or 1 linear (CIC); 2 quadratic
+                              (TSC, 2D base scheme only): 3 x 3 nodes per
+                              particle, node pairs up to two cells apart, the
+                              mass matrix stored for 13 offsets per node
+                              ((0,0), (1,0), (2,0), (di,1) and (di,2) for
+                              di = -2..2: ncell x 117); steps run host-driven
+                              with the counting-sort re-sort              */
 } relsim_config;
 
 typedef struct {

@@ -73,7 +73,7 @@ class relsim_config(ctypes.Structure):
                 ("q", ctypes.c_double * 4), ("m", ctypes.c_double * 4),
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_maxit", ctypes.c_int), ("track_ids", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("gamma_pred", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("gamma_pred", ctypes.c_int), ("shape", ctypes.c_int)]
 
 
 class relsim_energy(ctypes.Structure):
@@ -242,7 +242,7 @@ def _stream(stream=None) -> int:
 
 def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta_implicit=0.5, precision=32,
                 q=(1.0, -1.0), m=(1.0, 1.0), gmres_tol=0.0, gmres_restart=0, gmres_maxit=0,
-                track_ids=False, gamma_pred=False, nz=None, dz=1.0) -> relsim_config:
+                track_ids=False, gamma_pred=False, nz=None, dz=1.0, shape=1) -> relsim_config:
     """gamma_pred: the Lorentz factor in alpha and M is that of the
     predicted half-step momentum u^n + beta E^n(x) instead of u^n. nz: the
     3D form on an nx x ny x nz grid (cell size dz along z)."""
@@ -256,6 +256,7 @@ def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta_implicit=0.5, precision=32
     c.gmres_tol, c.gmres_restart, c.gmres_maxit = gmres_tol, gmres_restart, gmres_maxit
     c.track_ids = 1 if track_ids else 0
     c.gamma_pred = 1 if gamma_pred else 0
+    c.shape = int(shape)
     return c
 
 
@@ -627,7 +628,8 @@ class Simulation:
         return relsim_build_mass_matrix(self.ctx)
 
     def mass_matrix(self, device=False):
-        return relsim_get_mass_matrix(self.ctx, self.ncell, device, 14 if self.cfg.dim == 3 else 5)
+        nhalf = 14 if self.cfg.dim == 3 else (13 if self.cfg.shape == 2 else 5)
+        return relsim_get_mass_matrix(self.ctx, self.ncell, device, nhalf)
 
     def set_mass_matrix(self, M, J):
         return relsim_set_mass_matrix(self.ctx, M, J)

@@ -546,7 +546,9 @@ int build_impl(relsim_ctx* c)
     CK(cudaMemsetAsync(c->M, 0, c->esz * (size_t)nc * mblock_of(c->g), c->st));
     CK(cudaMemsetAsync(c->J, 0, c->esz * 3 * (size_t)nc, c->st));
     const DepositSpecies<T> ds = deposit_args<T>(c);
-    if (c->g.dim == 3) {
+    if (c->g.shape == 2) {
+        CK(deposit_q<T>(ds, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->st));
+    } else if (c->g.dim == 3) {
         FzArrays<T> fz;
         memset(&fz, 0, sizeof(fz));
         for (int s = 0; s < c->cfg.nspecies; ++s) fz.fz[s] = (const T*)c->sp[s].a[c->sp[s].cur][6];
@@ -878,7 +880,8 @@ void push_commit(relsim_ctx* c)
 template <typename T>
 int push_enqueue(relsim_ctx* c)
 {
-    const int nbp = c->g.dim == 3 ? push_blocks3(c->g) : push_grid_blocks(c->g, c->prec, c->push_cap);
+    const int nbp = c->g.dim == 3 ? push_blocks3(c->g)
+                    : (c->g.shape == 2 ? push_blocks_q(c->g) : push_grid_blocks(c->g, c->prec, c->push_cap));
     TRY(ensure_partial(c, (int64_t)nbp * (kLedgerSpecies - 1)));
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         Species& sp = c->sp[s];
@@ -908,6 +911,19 @@ int push_enqueue(relsim_ctx* c)
             CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
             CK(scan_exclusive_i32(c->count_new, sp.start, c->g.ncell, sp.start + c->g.ncell, c->scan_tmp, c->st));
             CK(place3<T>(dst, dfz, src, sfz, c->rk[0], c->rv[0], sp.start, sp.n, c->st));
+            PROF_END();
+        } else if (c->g.shape == 2) {
+            // quadratic shapes: the push with each particle's new cell and
+            // slot, the unstable counting sort as in 3D
+            TRY(ensure_radix(c, sp.n));
+            PROF_BEGIN(RELSIM_PROF_GENERAL_SORT);
+            CK(cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaMemsetAsync(c->count_new, 0, sizeof(int32_t) * (size_t)(c->g.ncell + 1), c->st));
+            CK(push_q<T>(src, dst, sp.start, c->rk[0], c->rv[0], c->count_new, Eth, B, c->g, sc, c->partial, nbp,
+                         c->st));
+            CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
+            CK(scan_exclusive_i32(c->count_new, sp.start, c->g.ncell, sp.start + c->g.ncell, c->scan_tmp, c->st));
+            CK(place3<T>(dst, nullptr, src, nullptr, c->rk[0], c->rv[0], sp.start, sp.n, c->st));
             PROF_END();
         } else if (c->fast_sort) {
             // push, each old cell written back grouped by move direction
@@ -1537,6 +1553,11 @@ int validate(const relsim_config* cfg, std::string* why)
     if (cfg->dim == 3 && cfg->nz < 3) { *why = "nz must be >= 3 in 3D"; return 0; }
     if (cfg->dim == 3 && !(cfg->dz > 0)) { *why = "dz must be > 0 in 3D"; return 0; }
     if (cfg->dim == 3 && cfg->gamma_pred) { *why = "the 3D form covers the base scheme (gamma_pred = 0)"; return 0; }
+    if (cfg->shape < 0 || cfg->shape > 2) { *why = "shape must be 0 or 1 (linear) or 2 (quadratic)"; return 0; }
+    if (cfg->shape == 2 && (cfg->dim != 2 || cfg->gamma_pred)) {
+        *why = "quadratic shapes cover the 2D base scheme";
+        return 0;
+    }
     if ((int64_t)cfg->nx * cfg->ny * (cfg->dim == 3 ? cfg->nz : 1) > (int64_t)1 << 28) {
         *why = "grid too large (more than 2^28 cells)";
         return 0;
@@ -1596,6 +1617,7 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     c->g.nx = cfg->nx;
     c->g.ny = cfg->ny;
     c->g.dim = cfg->dim;
+    c->g.shape = cfg->shape == 2 ? 2 : 1;
     c->g.nz = cfg->dim == 3 ? cfg->nz : 1;
     c->g.dz = cfg->dim == 3 ? cfg->dz : 1.0;
     c->g.ncell = cfg->nx * cfg->ny * c->g.nz;
@@ -1606,7 +1628,7 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     c->g.dV = cfg->dx * cfg->dy * c->g.dz;
     // one-cell moves per step: c dt <= min(dx, dy); the 3D form always
     // takes the general push (any move length, radix sort) and host-driven steps
-    c->fast_sort = cfg->dim == 2 && cfg->dt <= cfg->dx && cfg->dt <= cfg->dy;
+    c->fast_sort = cfg->dim == 2 && c->g.shape == 1 && cfg->dt <= cfg->dx && cfg->dt <= cfg->dy;
     c->key_bits = 1;
     while (((int64_t)1 << c->key_bits) < (int64_t)c->g.ncell) ++c->key_bits;
     const int64_t nc = c->g.ncell;
@@ -1891,7 +1913,8 @@ int relsim_field_solve(relsim_ctx* c, int* iters, double* rel_residual)
 int relsim_autotune(relsim_ctx* c, relsim_tuning* out)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
-    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the autotuner covers the 2D kernels");
+    if (c->g.dim == 3 || c->g.shape == 2)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "the autotuner covers the 2D kernels with linear shapes");
     if (c->state != kReady) return fail(c, RELSIM_ERR_BAD_STATE, "autotune needs a loaded state before a build");
     return DISPATCH(autotune_impl, c, out);
 }
@@ -1900,7 +1923,8 @@ int relsim_deposit_adjoint(relsim_ctx* c, int species, const double* gJ, const d
                            double* gx0, double* gB, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
-    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form");
+    if (c->g.dim == 3 || c->g.shape == 2)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form with linear shapes");
     if (species < 0 || species >= c->cfg.nspecies) return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     if (!gJ || !gM || !gB || (c->sp[species].n > 0 && (!gu0 || !gx0)))
@@ -1915,7 +1939,8 @@ int relsim_push_adjoint(relsim_ctx* c, int species, const double* gu1, const dou
                         double* gx0, double* gE, double* gB, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
-    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form");
+    if (c->g.dim == 3 || c->g.shape == 2)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form with linear shapes");
     if (species < 0 || species >= c->cfg.nspecies) return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     if (c->sp[species].n > 0 && (!gu1 || !gx1 || !gu0 || !gx0)) return fail(c, RELSIM_ERR_INVALID_ARG, "null array");
@@ -1929,7 +1954,8 @@ int relsim_step_adjoint(relsim_ctx* c, double* gE, double* gB, double* const* gu
                         double* rel_residual)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
-    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form");
+    if (c->g.dim == 3 || c->g.shape == 2)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form with linear shapes");
     if (!gE || !gB || !gu || !gx) return fail(c, RELSIM_ERR_INVALID_ARG, "null array");
     for (int s = 0; s < c->cfg.nspecies; ++s)
         if (c->sp[s].n > 0 && (!gu[s] || !gx[s])) return fail(c, RELSIM_ERR_INVALID_ARG, "null particle gradient");
@@ -1960,7 +1986,8 @@ int relsim_field_adjoint(relsim_ctx* c, const double* gE1, const double* gB1, co
                          double* gB0, double* gJ, double* gM, int* iters, double* rel_residual, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
-    if (c->g.dim == 3) return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form");
+    if (c->g.dim == 3 || c->g.shape == 2)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "the adjoints cover the 2D form with linear shapes");
     if (!gE1 || !gB1) return fail(c, RELSIM_ERR_INVALID_ARG, "null upstream gradient");
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     if (c->state != kSolved) return fail(c, RELSIM_ERR_BAD_STATE, "the adjoint needs a solved step (before the push)");

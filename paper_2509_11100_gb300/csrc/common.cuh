@@ -28,6 +28,11 @@ constexpr int kMaxRestart = 100;
 constexpr int kHalf3 = 14;
 constexpr int kMBlock3 = kHalf3 * 9;
 
+// quadratic (TSC) shapes in 2D: 13 of the 25 offsets stored, (0,0), (1,0),
+// (2,0), (di,1) and (di,2) for di = -2..2
+constexpr int kHalfQ = 13;
+constexpr int kMBlockQ = kHalfQ * 9;
+
 // ncell counts all cells (nx ny nz in 3D); dV is the cell volume (dx dy in
 // 2D). nz = 1, dz = 1 and dim = 2 for the 2D form.
 struct GridP {
@@ -35,9 +40,13 @@ struct GridP {
     double dx, dy, dt, theta, dV;
     int nz = 1, dim = 2;
     double dz = 1.0;
+    int shape = 1;   // 1: linear (CIC); 2: quadratic (TSC, 2D)
 };
 
-__host__ __device__ __forceinline__ int mblock_of(const GridP& g) { return g.dim == 3 ? kMBlock3 : kMBlock; }
+__host__ __device__ __forceinline__ int mblock_of(const GridP& g)
+{
+    return g.dim == 3 ? kMBlock3 : (g.shape == 2 ? kMBlockQ : kMBlock);
+}
 
 __host__ __device__ __forceinline__ int wrap1(int i, int n)
 {

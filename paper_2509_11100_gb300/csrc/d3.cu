@@ -938,7 +938,7 @@ __global__ void k_place3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> d
         const int64_t q = (int64_t)start[key[p]] + rank[p];
         dst.fx[q] = src.fx[p];
         dst.fy[q] = src.fy[p];
-        dfz[q] = sfz[p];
+        if (dfz) dfz[q] = sfz[p];   // null for 2D particles
         dst.ux[q] = src.ux[p];
         dst.uy[q] = src.uy[p];
         dst.uz[q] = src.uz[p];

@@ -662,6 +662,7 @@ int field_grid_blocks(GridP g) { return grid_for(g.ncell, kFieldThreads, 1 << 30
 int op_blocks(GridP g, int precision)
 {
     if (g.dim == 3) return op_blocks3(g);
+    if (g.shape == 2) return op_blocks_q(g);
     const int X = 32, Y = precision == 32 ? OpTile<float>::Y : OpTile<double>::Y;
     return ((g.nx + X - 1) / X) * ((g.ny + Y - 1) / Y);
 }
@@ -698,6 +699,7 @@ cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, 
                       const GmDyn* dyn = nullptr)
 {
     if (g.dim == 3) return launch_op3<T, MODE, TR>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, st, dyn);
+    if (g.shape == 2) return launch_op_q<T, MODE, TR>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, st, dyn);
     // the dynamic shared-memory limit, set once per kernel and device
     static std::atomic<unsigned> attr_set{0};
     const int smem = (int)sizeof(OpShared<T>);
@@ -755,6 +757,7 @@ cudaError_t field_update(const double* x, const T* M, const T* J, T* Eth, T* E, 
                          T* B1, GridP g, double* partial, int nblocks, cudaStream_t st)
 {
     if (g.dim == 3) return field_update3<T>(x, M, J, Eth, E, B0, B1, g, partial, nblocks, st);
+    if (g.shape == 2) return field_update_q<T>(x, M, J, Eth, E, B0, B1, g, partial, nblocks, st);
     count_launches(1);
     k_field_update<T><<<nblocks, kFieldThreads, 0, st>>>(x, M, J, Eth, E, B0, B1, g, partial);
     return cudaGetLastError();

@@ -102,6 +102,23 @@ template <typename T>
 cudaError_t place3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const int32_t* key, const int32_t* rank,
                    const int32_t* start, int64_t n, cudaStream_t st);
 
+// ----- quad.cu (2D, quadratic shapes) -----
+template <typename T>
+cudaError_t deposit_q(const DepositSpecies<T>& ds, const T* B, T* M, T* J, GridP g, cudaStream_t st);
+int op_blocks_q(GridP g);
+template <typename T, int MODE, bool TR>
+cudaError_t launch_op_q(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
+                        const double* V, int64_t ldv, int nv, GridP g, double* partial, cudaStream_t st,
+                        const GmDyn* dyn);
+template <typename T>
+cudaError_t field_update_q(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0, T* B1, GridP g,
+                           double* partial, int nblocks, cudaStream_t st);
+int push_blocks_q(GridP g);
+template <typename T>
+cudaError_t push_q(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, int32_t* rank,
+                   int32_t* count, const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum, int nblocks,
+                   cudaStream_t st);
+
 // ----- adjoint.cu -----
 // lu[i] = gu[id[i]], lx[i] = gx[id[i]] (FP64, 3 and 2 interleaved components)
 cudaError_t gather_grad(const int32_t* id, const double* gu, const double* gx, double* lu, double* lx, int64_t n,
