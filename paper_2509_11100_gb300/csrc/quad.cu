@@ -141,6 +141,7 @@ constexpr int kPairsQ = 106;  // node pairs of the 4 x 4 union at most two apart
 template <typename T>
 struct DepCfgQ {
     static constexpr int warps = sizeof(T) == 4 ? 4 : 2;
+    static constexpr int min_blocks = sizeof(T) == 4 ? 4 : 1;   // FP32: at most 128 registers
 };
 
 template <typename T>
@@ -191,6 +192,29 @@ struct AccQ<float> {
     }
 };
 
+// a 3x3 block added to the stored block at dst; in FP32 as paired atomics on
+// 8-byte aligned pairs (odd: dst starts on an odd float, as 117 values per
+// node and 9 per block are odd), constant indices in both branches
+__device__ __forceinline__ void add_block9q(float* dst, const float (&v)[9], int odd)
+{
+    if (odd) {
+        atomicAdd(dst, v[0]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            atomicAdd(reinterpret_cast<float2*>(dst + 1 + 2 * e), make_float2(v[1 + 2 * e], v[2 + 2 * e]));
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            atomicAdd(reinterpret_cast<float2*>(dst + 2 * e), make_float2(v[2 * e], v[2 * e + 1]));
+        atomicAdd(dst + 8, v[8]);
+    }
+}
+__device__ __forceinline__ void add_block9q(double* dst, const double (&v)[9], int)
+{
+#pragma unroll
+    for (int e = 0; e < 9; ++e) atomicAdd(dst + e, v[e]);
+}
+
 // the q-th pair (a <= b, node index 4 y + x in the 4 x 4 union, at most two
 // apart per axis)
 __device__ __forceinline__ void pair_q(int q, int& a, int& b)
@@ -221,13 +245,11 @@ __device__ __forceinline__ void flush_q(T* M, int a, int b, const AccQ<T>& acc, 
     const int64_t gn = (int64_t)wrap1(j - 1 + (at >> 2), g.ny) * g.nx + wrap1(i - 1 + (at & 3), g.nx);
     T v[9];
     acc.get(v);
-    T* dst = M + gn * kMBlockQ + hs * 9;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) atomicAdd(dst + e, v[e]);
+    add_block9q(M + gn * kMBlockQ + hs * 9, v, (int)((gn + hs) & 1));
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * DepCfgQ<T>::warps)
+__global__ void __launch_bounds__(32 * DepCfgQ<T>::warps, DepCfgQ<T>::min_blocks)
 k_deposit_q(DepositSpecies<T> ds, const T* __restrict__ B, T* __restrict__ M, T* __restrict__ J, GridP g)
 {
     constexpr int kW = DepCfgQ<T>::warps;
