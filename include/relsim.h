@@ -454,7 +454,10 @@ RELSIM_API void relsim_batch_destroy(relsim_batch* b);
    loaded state and keeps the fastest for this context: the deposit's block
    count (it strides over row units of 32 cells: 1, 2, 3, 4 blocks per SM)
    and the push's grid (at most 4, 8, 16, 32 blocks of four unit warps per
-   SM). Each candidate runs once untimed and three times timed (CUDA events;
+   SM), and a compile-time shape of the implicit operator: its tile height
+   (32-node-wide tiles of 8 or 4 rows in the FP32 form, 4 or 2 in FP64; an
+   Arnoldi-mode application with 8 dot products on the deposited mass
+   matrix). Each candidate runs once untimed and three times timed (CUDA events;
    the least counts). Call it on a loaded state before a build (the trials
    overwrite only what the next step recomputes); later steps use the
    choice (captured step graphs are recaptured). out (may be NULL) receives
@@ -467,8 +470,20 @@ typedef struct {
     int push_blocks[8];
     float push_ms[8];
     int deposit_choice, push_choice;   /* indices into the candidates */
+    int op_nrows;                      /* tile heights tried for the 2D operator */
+    int op_rows[4];                    /* rows per operator tile (32 nodes wide)  */
+    float op_ms[4];                    /* an Arnoldi-mode application, 8 dots    */
+    int op_choice;
 } relsim_tuning;
 RELSIM_API int relsim_autotune(relsim_ctx* ctx, relsim_tuning* out);
+
+/* Set the launch shapes the autotuner chooses (e.g. one instance's tuning
+   applied to others of the same size): the deposit's block count and the
+   push's grid cap (0: the defaults, two and 16 blocks per SM) and the 2D
+   operator's tile rows (0 or the form's default: 8 in FP32, 4 in FP64; or
+   the alternative: 4 in FP32, 2 in FP64). Results do not depend on the
+   shapes beyond rounding. Errors: INVALID_ARG. */
+RELSIM_API int relsim_set_launch_shapes(relsim_ctx* ctx, int deposit_blocks, int push_blocks, int op_rows);
 
 /* Library version (major*10000 + minor*100 + patch). */
 RELSIM_API int relsim_version(void);

@@ -31,7 +31,7 @@ __all__ = [
     "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
     "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
     "relsim_tuning", "relsim_push_adjoint", "relsim_deposit_adjoint", "relsim_step_adjoint",
-    "relsim_relabel_particles",
+    "relsim_relabel_particles", "relsim_set_launch_shapes",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -133,6 +133,7 @@ _SIGS = {
     "relsim_deposit_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int]),
     "relsim_autotune": (ctypes.c_int, [_CTX, _P]),
     "relsim_push_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
+    "relsim_set_launch_shapes": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "relsim_step_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_double)]),
     "relsim_relabel_particles": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
@@ -146,14 +147,17 @@ class relsim_tuning(ctypes.Structure):
     _fields_ = [("ncand", ctypes.c_int), ("deposit_blocks", ctypes.c_int * 8),
                 ("deposit_ms", ctypes.c_float * 8), ("push_blocks", ctypes.c_int * 8),
                 ("push_ms", ctypes.c_float * 8), ("deposit_choice", ctypes.c_int),
-                ("push_choice", ctypes.c_int)]
+                ("push_choice", ctypes.c_int), ("op_nrows", ctypes.c_int), ("op_rows", ctypes.c_int * 4),
+                ("op_ms", ctypes.c_float * 4), ("op_choice", ctypes.c_int)]
 
     def asdict(self) -> dict:
         n = self.ncand
         return {"deposit": [(self.deposit_blocks[k], self.deposit_ms[k]) for k in range(n)],
                 "push": [(self.push_blocks[k], self.push_ms[k]) for k in range(n)],
                 "deposit_blocks": self.deposit_blocks[self.deposit_choice],
-                "push_blocks": self.push_blocks[self.push_choice]}
+                "push_blocks": self.push_blocks[self.push_choice],
+                "op_tile_rows": [(self.op_rows[k], self.op_ms[k]) for k in range(self.op_nrows)],
+                "op_rows": self.op_rows[self.op_choice]}
 
 
 class relsim_profile(ctypes.Structure):
@@ -666,6 +670,10 @@ class Simulation:
 
     def autotune(self):
         return relsim_autotune(self.ctx)
+
+    def set_launch_shapes(self, deposit_blocks=0, push_blocks=0, op_rows=0):
+        return _check(self.ctx, lib().relsim_set_launch_shapes(self.ctx, int(deposit_blocks), int(push_blocks),
+                                                               int(op_rows)))
 
     def push_adjoint(self, s, gu1, gx1, device=False):
         return relsim_push_adjoint(self.ctx, s, self.ncell, gu1, gx1, device)

@@ -653,9 +653,43 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
             },
             &t.push_ms[k]);
     }
+    // the operator's tile height (a compile-time shape with two instances):
+    // an Arnoldi-mode application with 8 dot products on the deposited M
+    const int alt = c->prec == 32 ? 4 : 2;
+    const int rows_c[2] = {0, alt};
+    t.op_nrows = 2;
+    if (r == RELSIM_OK) {
+        const int jdots = 8;
+        int64_t most = 0;
+        for (int k = 0; k < 2; ++k) {
+            GridP gk = c->g;
+            gk.op_y = rows_c[k];
+            const int64_t nb = op_blocks(gk, c->prec);
+            most = nb > most ? nb : most;
+        }
+        r = ensure_partial(c, most * (jdots + 2));
+        if (r == RELSIM_OK && cudaMemsetAsync(c->V, 0, sizeof(double) * (size_t)(jdots + 1) * c->nvec, c->st) != cudaSuccess)
+            r = fail(c, RELSIM_ERR_CUDA, "cudaMemsetAsync failed");
+        if (r == RELSIM_OK && cudaMemsetAsync(c->gw, 0, sizeof(double) * (size_t)c->nvec, c->st) != cudaSuccess)
+            r = fail(c, RELSIM_ERR_CUDA, "cudaMemsetAsync failed");
+        for (int k = 0; k < 2 && r == RELSIM_OK; ++k) {
+            GridP gk = c->g;
+            gk.op_y = rows_c[k];
+            t.op_rows[k] = rows_c[k] > 0 ? rows_c[k] : (c->prec == 32 ? 8 : 4);
+            r = timed(
+                [&]() -> int {
+                    CK(op_arnoldi<T>((const T*)c->M, c->gw, 1.0, nullptr, c->gw2, c->V, c->nvec, jdots, gk, c->partial,
+                                     c->dpush, c->st));
+                    return RELSIM_OK;
+                },
+                &t.op_ms[k]);
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r != RELSIM_OK) return r;
+    t.op_choice = t.op_ms[1] < t.op_ms[0] ? 1 : 0;
+    c->g.op_y = rows_c[t.op_choice];
     int bd = 0, bp = 0;
     for (int k = 1; k < ncand; ++k) {
         if (t.deposit_ms[k] < t.deposit_ms[bd]) bd = k;
@@ -1908,6 +1942,21 @@ int relsim_field_solve(relsim_ctx* c, int* iters, double* rel_residual)
     int r = DISPATCH(solve_impl, c, iters, rel_residual);
     if (r == RELSIM_OK || r == RELSIM_ERR_NOT_CONVERGED) c->state = kSolved;
     return r;
+}
+
+int relsim_set_launch_shapes(relsim_ctx* c, int deposit_blocks, int push_blocks, int op_rows)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (deposit_blocks < 0 || push_blocks < 0 || deposit_blocks > (1 << 20) || push_blocks > (1 << 20))
+        return fail(c, RELSIM_ERR_INVALID_ARG, "block counts must be 0 .. 2^20");
+    const int def = c->prec == 32 ? 8 : 4, alt = c->prec == 32 ? 4 : 2;
+    if (op_rows != 0 && op_rows != def && op_rows != alt)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "operator tile rows must be 0, %d or %d", def, alt);
+    c->dep_blocks = deposit_blocks;
+    c->push_cap = push_blocks;
+    c->g.op_y = op_rows == alt ? alt : 0;
+    ++c->gen;   // step graphs hold the old launch shapes
+    return RELSIM_OK;
 }
 
 int relsim_autotune(relsim_ctx* c, relsim_tuning* out)

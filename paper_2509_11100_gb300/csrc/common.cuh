@@ -41,6 +41,7 @@ struct GridP {
     int nz = 1, dim = 2;
     double dz = 1.0;
     int shape = 1;   // 1: linear (CIC); 2: quadratic (TSC, 2D)
+    int op_y = 0;    // rows of the 2D operator's tiles (0: the form's default)
 };
 
 __host__ __device__ __forceinline__ int mblock_of(const GridP& g)

@@ -179,36 +179,42 @@ enum { kOpA = 0, kOpResidual = 1, kOpArnoldi = 2 };
 constexpr long long kOpMaxPolls = 1ll << 26;   // bounded mbarrier wait
 constexpr int kOpChunk = 8;                    // dot products reduced per shared-memory pass
 
-template <typename T>
+// The tile height is a compile-time shape with two instances per form (FP32:
+// 8 rows, or 4; FP64: 4, or 2); the autotuner picks one per context (YY = 0:
+// the default).
+template <typename T, int YY = 0>
 struct OpTile {
     static constexpr int X = 32;
-    static constexpr int Y = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int Y = YY > 0 ? YY : (sizeof(T) == 4 ? 8 : 4);
     static constexpr int threads = X * Y;
 };
 
-template <typename T>
+template <typename T, int YY = 0>
 struct OpShared {
     // rows j0-1 .., columns i0 .. i0+X-1; reused for the dot-product
     // reduction once the operator is applied
-    T Mm[OpTile<T>::Y + 1][OpTile<T>::X * kMBlock];
-    T Mh[OpTile<T>::Y + 1][2][kMBlock];          // columns i0-1 and i0+tw
-    T v[3][OpTile<T>::Y + 2][OpTile<T>::X + 2];  // rows j0-1 .. j0+Y, columns i0-1 .. i0+tw
+    T Mm[OpTile<T, YY>::Y + 1][OpTile<T, YY>::X * kMBlock];
+    T Mh[OpTile<T, YY>::Y + 1][2][kMBlock];              // columns i0-1 and i0+tw
+    T v[3][OpTile<T, YY>::Y + 2][OpTile<T, YY>::X + 2];  // rows j0-1 .. j0+Y, columns i0-1 .. i0+tw
     uint64_t mbar;
 };
-static_assert(sizeof(float) * (OpTile<float>::Y + 1) * OpTile<float>::X * kMBlock >=
-                  sizeof(double) * kOpChunk * OpTile<float>::threads,
-              "the reduction buffer fits in the mass-matrix tile");
-static_assert(sizeof(double) * (OpTile<double>::Y + 1) * OpTile<double>::X * kMBlock >=
-                  sizeof(double) * kOpChunk * OpTile<double>::threads,
+template <typename T, int YY>
+constexpr bool op_buffer_fits()
+{
+    return sizeof(T) * (OpTile<T, YY>::Y + 1) * OpTile<T, YY>::X * kMBlock >=
+           sizeof(double) * kOpChunk * OpTile<T, YY>::threads;
+}
+static_assert(op_buffer_fits<float, 0>() && op_buffer_fits<float, 4>() && op_buffer_fits<double, 0>() &&
+                  op_buffer_fits<double, 2>(),
               "the reduction buffer fits in the mass-matrix tile");
 
-template <typename T, int MODE, bool TR>
-__global__ void __launch_bounds__(OpTile<T>::threads, sizeof(T) == 4 ? 3 : 2)
+template <typename T, int MODE, bool TR, int YY = 0>
+__global__ void __launch_bounds__(OpTile<T, YY>::threads, sizeof(T) == 4 ? 3 : 2)
 k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const double* __restrict__ b,
      double* __restrict__ out, double* __restrict__ vj, const double* __restrict__ V, int64_t ldv, int nv,
      GridP g, int tma, double* __restrict__ partial, int* __restrict__ err, const GmDyn* __restrict__ dyn)
 {
-    constexpr int X = OpTile<T>::X, Y = OpTile<T>::Y, NT = OpTile<T>::threads;
+    constexpr int X = OpTile<T, YY>::X, Y = OpTile<T, YY>::Y, NT = OpTile<T, YY>::threads;
     if (MODE == kOpArnoldi && dyn) {
         // arguments of a device-decided Arnoldi iteration
         if (!dyn->live) return;
@@ -219,7 +225,7 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
         nv = dyn->nv;
     }
     extern __shared__ __align__(128) unsigned char op_smem[];
-    OpShared<T>& S = *reinterpret_cast<OpShared<T>*>(op_smem);
+    OpShared<T, YY>& S = *reinterpret_cast<OpShared<T, YY>*>(op_smem);
     const int nx = g.nx, ny = g.ny, nc = g.ncell;
     const int tilesx = (nx + X - 1) / X;
     const int i0 = (blockIdx.x % tilesx) * X, j0 = (blockIdx.x / tilesx) * Y;
@@ -663,7 +669,7 @@ int op_blocks(GridP g, int precision)
 {
     if (g.dim == 3) return op_blocks3(g);
     if (g.shape == 2) return op_blocks_q(g);
-    const int X = 32, Y = precision == 32 ? OpTile<float>::Y : OpTile<double>::Y;
+    const int X = 32, Y = g.op_y > 0 ? g.op_y : (precision == 32 ? OpTile<float>::Y : OpTile<double>::Y);
     return ((g.nx + X - 1) / X) * ((g.ny + Y - 1) / Y);
 }
 int gm_blocks(int64_t n) { return grid_for(n, kGmThreads, 152 * 4); }
@@ -693,6 +699,31 @@ cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStre
     return cudaGetLastError();
 }
 
+template <typename T, int MODE, bool TR, int YY>
+cudaError_t launch_op_y(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
+                        const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st,
+                        const GmDyn* dyn)
+{
+    // the dynamic shared-memory limit, set once per kernel and device
+    static std::atomic<unsigned> attr_set{0};
+    const int smem = (int)sizeof(OpShared<T, YY>);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned bit = 1u << (dev & 31);
+    if (!(attr_set.load() & bit)) {
+        e = cudaFuncSetAttribute(k_op<T, MODE, TR, YY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set.fetch_or(bit);
+    }
+    // bulk copies need every staged mass-matrix row to start on 16 bytes
+    const int tma = ((int64_t)g.nx * kMBlock * sizeof(T)) % 16 == 0 ? 1 : 0;
+    count_launches(1);
+    k_op<T, MODE, TR, YY><<<op_blocks(g, sizeof(T) == 4 ? 32 : 64), OpTile<T, YY>::threads, smem, st>>>(
+        M, in, sc, b, out, vj, V, ldv, nv, g, tma, partial, err, dyn);
+    return cudaGetLastError();
+}
+
 template <typename T, int MODE, bool TR = false>
 cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
                       const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st,
@@ -700,24 +731,10 @@ cudaError_t launch_op(const T* M, const double* in, double sc, const double* b, 
 {
     if (g.dim == 3) return launch_op3<T, MODE, TR>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, st, dyn);
     if (g.shape == 2) return launch_op_q<T, MODE, TR>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, st, dyn);
-    // the dynamic shared-memory limit, set once per kernel and device
-    static std::atomic<unsigned> attr_set{0};
-    const int smem = (int)sizeof(OpShared<T>);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned bit = 1u << (dev & 31);
-    if (!(attr_set.load() & bit)) {
-        e = cudaFuncSetAttribute(k_op<T, MODE, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set.fetch_or(bit);
-    }
-    // bulk copies need every staged mass-matrix row to start on 16 bytes
-    const int tma = ((int64_t)g.nx * kMBlock * sizeof(T)) % 16 == 0 ? 1 : 0;
-    count_launches(1);
-    k_op<T, MODE, TR><<<op_blocks(g, sizeof(T) == 4 ? 32 : 64), OpTile<T>::threads, smem, st>>>(
-        M, in, sc, b, out, vj, V, ldv, nv, g, tma, partial, err, dyn);
-    return cudaGetLastError();
+    // the autotuned tile height (g.op_y; 0: the default)
+    constexpr int kAlt = sizeof(T) == 4 ? 4 : 2;
+    if (g.op_y == kAlt) return launch_op_y<T, MODE, TR, kAlt>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, err, st, dyn);
+    return launch_op_y<T, MODE, TR, 0>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, err, st, dyn);
 }
 
 template <typename T>
