@@ -630,7 +630,7 @@ def run_quad(args):
 
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
-    hc = harris_config(seed=rank, small=False)
+    hc = harris_config(seed=rank, small=args.workload == "c1qsmall")
     st = make_harris(hc)
     N = sum(len(sp["w"]) for sp in st["species"])
     cfg = rs.make_config(hc.nx, hc.ny, dt=hc.dt, theta_implicit=hc.theta, precision=32, shape=2,
@@ -662,8 +662,8 @@ def run_quad(args):
     last = leds[-1]
     out = {"metric": METRIC, "value": N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "2D relativistic double Harris sheet as the headline line (1024x512, 64 ppc per "
-                                  "species, 67,108,864 particles) with quadratic (TSC) shape functions",
+           "config": {"workload": f"2D relativistic double Harris sheet as the headline line ({hc.nx}x{hc.ny}, 64 "
+                                  f"ppc per species, {N:,} particles) with quadratic (TSC) shape functions",
                       "l2": "inputs larger than L2, no flush"},
            "per_kernel": per_kernel, "gmres_iters_per_step": float(np.mean([l["gmres_iters"] for l in leds])),
            "ledger": {"residual_rel": abs(last["residual"]) / last["total"],
@@ -869,7 +869,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (no autotuner pass after the load)")
-    ap.add_argument("--workload", choices=["c1", "small", "scan", "window", "c2", "c2small", "c1q"], default="c1",
+    ap.add_argument("--workload", choices=["c1", "small", "scan", "window", "c2", "c2small", "c1q", "c1qsmall"], default="c1",
                     help="small: 512x256 cells for profiler captures; scan: the 48-instance batched "
                          "tearing scan (run with --steps 400 for its full length); window: the "
                          "differentiable 20-step window on 256x128; c2: the 3D sheet on 256x128x128 "
@@ -888,7 +888,7 @@ def main():
         run_window(args)
     elif args.workload in ("c2", "c2small"):
         run_3d(args)
-    elif args.workload == "c1q":
+    elif args.workload in ("c1q", "c1qsmall"):
         run_quad(args)
     else:
         run_ours(args)

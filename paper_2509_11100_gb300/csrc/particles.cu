@@ -1243,7 +1243,7 @@ __device__ __forceinline__ void flush_centres(const A (&gc)[3][3][3], const Runs
 // gu1, gx1 are dL/du^{n+1}, dL/dx^{n+3/2} (FP64, interleaved, in the
 // particles' current order); gu0, gx0 receive dL/du^n, dL/dx^{n+1/2}.
 template <typename T>
-__global__ void __launch_bounds__(PushCfg<T>::threads)
+__global__ void __launch_bounds__(PushCfg<T>::threads, sizeof(T) == 4 ? 4 : 1)
 k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gu1,
                const double* __restrict__ gx1, double* __restrict__ gu0, double* __restrict__ gx0,
                double* __restrict__ gE, double* __restrict__ gB, const T* __restrict__ Eth,
@@ -1413,7 +1413,7 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
 // derivatives give dL/dx. Outputs per particle dL/du^n (gu0, interleaved)
 // and dL/dx^{n+1/2} (gx0), FP64.
 template <typename T>
-__global__ void __launch_bounds__(PushCfg<T>::threads)
+__global__ void __launch_bounds__(PushCfg<T>::threads, sizeof(T) == 4 ? 4 : 1)
 k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gJ,
                   const double* __restrict__ gM, double* __restrict__ gu0, double* __restrict__ gx0,
                   double* __restrict__ gB, const T* __restrict__ B, GridP g, double beta_d, double cq)
