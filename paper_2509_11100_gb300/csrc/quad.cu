@@ -13,11 +13,11 @@
 // Kernels:
 //   k_deposit_q   warp per row segment of cells, the segment's B staged in
 //                 shared memory; per cell the particles of all species staged
-//                 with their weights on the 4 x 4 nodes that particles of the
-//                 cell can touch, c alpha and c alpha u / gbar; each lane owns
-//                 up to 4 of the 106 node pairs at most two cells apart and up
-//                 to 2 current components, accumulates with paired FP32 FMAs
-//                 and flushes once per cell
+//                 in four groups by the half of the cell they sit in (each
+//                 group touches a fixed 3 x 3 of the cell's 4 x 4 nodes); per
+//                 group each lane sums up to 2 of the 45 node pairs of 3 x 3
+//                 nodes with paired FP32 FMAs and adds them to the cell's 106
+//                 pair sums in shared memory, flushed once per cell
 //   k_op_q        the operator on 32 x 8-node tiles, the input staged on a
 //                 2-node halo, the 25 blocks per node from global memory, the
 //                 modes and partial dot products of the other operators
@@ -135,7 +135,6 @@ __device__ __forceinline__ void alphaq(const T (&Bp)[3], T beta, T gbar, T (&al)
 // ---------------------------------------------------------------------------
 // deposit
 
-constexpr int kStageQ = 30;   // 16 weights, 9 c alpha (at 16), 3 currents (at 25), padded
 constexpr int kPairsQ = 106;  // node pairs of the 4 x 4 union at most two apart per axis
 
 template <typename T>
@@ -234,7 +233,7 @@ __device__ __forceinline__ void pair_q(int q, int& a, int& b)
 }
 
 template <typename T>
-__device__ __forceinline__ void flush_q(T* M, int a, int b, const AccQ<T>& acc, int i, int j, const GridP& g)
+__device__ __forceinline__ void flush_q_vals(T* M, int a, int b, const T (&v)[9], int i, int j, const GridP& g)
 {
     const int di = (b & 3) - (a & 3), dj = (b >> 2) - (a >> 2);
     int hs = halfq(di, dj), at = a;
@@ -243,8 +242,6 @@ __device__ __forceinline__ void flush_q(T* M, int a, int b, const AccQ<T>& acc, 
         at = b;
     }
     const int64_t gn = (int64_t)wrap1(j - 1 + (at >> 2), g.ny) * g.nx + wrap1(i - 1 + (at & 3), g.nx);
-    T v[9];
-    acc.get(v);
     add_block9q(M + gn * kMBlockQ + hs * 9, v, (int)((gn + hs) & 1));
 }
 
@@ -252,15 +249,63 @@ template <typename T>
 __global__ void __launch_bounds__(32 * DepCfgQ<T>::warps, DepCfgQ<T>::min_blocks)
 k_deposit_q(DepositSpecies<T> ds, const T* __restrict__ B, T* __restrict__ M, T* __restrict__ J, GridP g)
 {
+    // The particles of a cell are taken in four groups by the half of the
+    // cell they sit in along x and y (hx, hy): a group's particles touch the
+    // same 3 x 3 nodes, the union nodes (x + hx, y + hy) of the frame nodes
+    // x, y = 0..2. Each lane owns frame pairs lane and lane + 32 of the 45
+    // pairs of a frame and frame current component lane (of 27), sums a
+    // group's particles in registers and adds the sums to the cell's union
+    // accumulators in shared memory (one owner per entry and group); the
+    // union sums are flushed to M and Jhat once per cell.
     constexpr int kW = DepCfgQ<T>::warps;
-    __shared__ __align__(16) T sh[kW][32][kStageQ];
+    constexpr int kSt = 22;   // 9 frame weights, pad, 9 c alpha at 10, 3 currents at 19
+    __shared__ __align__(16) T sh[kW][32][kSt];
+    __shared__ __align__(16) T um[kW][kPairsQ][9];
+    __shared__ T uj[kW][48];
     __shared__ TileQ<T> stl[kW];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int nseg = (g.nx + kQX - 1) / kQX;
     const int nunits = nseg * g.ny;
-    T (*st)[kStageQ] = sh[wib];
+    T (*st)[kSt] = sh[wib];
+    T (*U)[9] = um[wib];
+    T* UJ = uj[wib];
+    // this lane's frame pairs (a <= b in the frame order 3 y + x)
+    int fa[2] = {0, 0}, fb[2] = {0, 0};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int q = lane + 32 * t;
+        int n = 0;
+        for (int a = 0; a < 9; ++a)
+            for (int b = a; b < 9; ++b) {
+                if (n == q) {
+                    fa[t] = a;
+                    fb[t] = b;
+                }
+                ++n;
+            }
+    }
+    const bool two = lane + 32 < 45;
+    // their union pair index per group
+    int uq[2][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int gq = 0; gq < 4; ++gq) {
+            const int hx = gq & 1, hy = gq >> 1;
+            const int ua = 4 * (fa[t] / 3 + hy) + fa[t] % 3 + hx, ub = 4 * (fb[t] / 3 + hy) + fb[t] % 3 + hx;
+            int n = 0, found = 0;
+            for (int a = 0; a < 16; ++a)
+                for (int b = a; b < 16; ++b) {
+                    const int dx = (b & 3) - (a & 3), dy = (b >> 2) - (a >> 2);
+                    if (dx > 2 || dx < -2 || dy > 2) continue;
+                    if (a == ua && b == ub) found = n;
+                    ++n;
+                }
+            uq[t][gq] = found;
+        }
+    // the union pairs this lane flushes
     int pa[4], pb[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -268,10 +313,10 @@ k_deposit_q(DepositSpecies<T> ds, const T* __restrict__ B, T* __restrict__ M, T*
         if (q < kPairsQ) pair_q(q, pa[t], pb[t]);
         else pa[t] = pb[t] = 0;
     }
-    const bool four = lane + 96 < kPairsQ;
-    // the current components owned: index lane and lane + 32 of 48 (node, comp)
-    const int jn0 = lane / 3, jc0 = lane % 3, jn1 = (lane + 32) / 3, jc1 = (lane + 32) % 3;
-    const bool j2 = lane + 32 < 48;
+    const bool ownj = lane < 27;
+    const int jf = lane / 3, jc = lane % 3;   // frame node and component
+    for (int q = lane; q < kPairsQ * 9; q += 32) (&U[0][0])[q] = T(0);
+    for (int q = lane; q < 48; q += 32) UJ[q] = T(0);
     for (int u = warp; u < nunits; u += nwarps) {
         const int i0 = (u % nseg) * kQX, j = u / nseg;
         const int cn = min(kQX, g.nx - i0);
@@ -289,13 +334,12 @@ k_deposit_q(DepositSpecies<T> ds, const T* __restrict__ B, T* __restrict__ M, T*
             }
             const int total = cum[kMaxSpecies];
             if (total == 0) continue;
-            AccQ<T> acc[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) acc[t].zero();
-            T aj0 = T(0), aj1 = T(0);
             for (int q0 = 0; q0 < total; q0 += 32) {
                 const int t = q0 + lane;
-                if (t < total) {
+                const bool act = t < total;
+                int grp = -1;
+                T row[kSt];
+                if (act) {
                     int s = 0, p = pst[0] + t;
 #pragma unroll
                     for (int q = 1; q < kMaxSpecies; ++q)
@@ -306,46 +350,97 @@ k_deposit_q(DepositSpecies<T> ds, const T* __restrict__ B, T* __restrict__ M, T*
                     const T fx = ld(ds.fx[s] + p), fy = ld(ds.fy[s] + p);
                     const T ux = ld(ds.ux[s] + p), uy = ld(ds.uy[s] + p), uz = ld(ds.uz[s] + p);
                     const T wt = ld(ds.w[s] + p);
-                    T wx[4], wy[4], Bp[3], al[9];
-                    node4(fx, wx);
-                    node4(fy, wy);
+                    const int hx = fx >= T(0.5), hy = fy >= T(0.5);
+                    grp = 2 * hy + hx;
+                    T wx[3], wy[3], Bp[3], al[9];
+                    quad3(hx ? fx - T(1) : fx, wx);
+                    quad3(hy ? fy - T(1) : fy, wy);
                     tile_Bq(stl[wib], cl, fx, fy, Bp);
                     const T gbar = sqrt(T(1) + ux * ux + uy * uy + uz * uz);
                     alphaq(Bp, ds.beta[s], gbar, al);
                     const T cM = wt * ds.cM[s] / gbar, cJ = wt * ds.cJ[s] / gbar;
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < 3; ++r)
 #pragma unroll
-                        for (int c2 = 0; c2 < 4; ++c2) st[lane][4 * r + c2] = wy[r] * wx[c2];
+                        for (int c2 = 0; c2 < 3; ++c2) row[3 * r + c2] = wy[r] * wx[c2];
+                    row[9] = T(0);
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) st[lane][16 + e] = cM * al[e];
+                    for (int e = 0; e < 9; ++e) row[10 + e] = cM * al[e];
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
-                        st[lane][25 + r] = cJ * (al[3 * r] * ux + al[3 * r + 1] * uy + al[3 * r + 2] * uz);
+                        row[19 + r] = cJ * (al[3 * r] * ux + al[3 * r + 1] * uy + al[3 * r + 2] * uz);
+                }
+                // staging rows grouped by g (ballot prefix sums)
+                unsigned bal[4];
+                int gb[5];
+                gb[0] = 0;
+#pragma unroll
+                for (int gq = 0; gq < 4; ++gq) {
+                    bal[gq] = __ballot_sync(0xffffffffu, grp == gq);
+                    gb[gq + 1] = gb[gq] + __popc(bal[gq]);
+                }
+                if (act) {
+                    int r = 0;
+#pragma unroll
+                    for (int gq = 0; gq < 4; ++gq)
+                        if (grp == gq) r = gb[gq] + __popc(bal[gq] & ((1u << lane) - 1u));
+#pragma unroll
+                    for (int e = 0; e < kSt; ++e) st[r][e] = row[e];
                 }
                 __syncwarp();
-                const int m = min(32, total - q0);
-                for (int t2 = 0; t2 < m; ++t2) {
-                    const T* row = st[t2];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) acc[k].add(row[pa[k]] * row[pb[k]], row + 16);
-                    if (four) acc[3].add(row[pa[3]] * row[pb[3]], row + 16);
-                    aj0 += row[jn0] * row[25 + jc0];
-                    if (j2) aj1 += row[jn1] * row[25 + jc1];
+                for (int gq = 0; gq < 4; ++gq) {
+                    if (gb[gq + 1] == gb[gq]) continue;   // warp-uniform
+                    AccQ<T> a0, a1;
+                    a0.zero();
+                    a1.zero();
+                    T aj = T(0);
+                    for (int r = gb[gq]; r < gb[gq + 1]; ++r) {
+                        const T* rw = st[r];
+                        a0.add(rw[fa[0]] * rw[fb[0]], rw + 10);
+                        if (two) a1.add(rw[fa[1]] * rw[fb[1]], rw + 10);
+                        if (ownj) aj += rw[jf] * rw[19 + jc];
+                    }
+                    // into the union accumulators (distinct entries per lane)
+                    T v[9];
+                    a0.get(v);
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) U[uq[0][gq]][e] += v[e];
+                    if (two) {
+                        a1.get(v);
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) U[uq[1][gq]][e] += v[e];
+                    }
+                    if (ownj) {
+                        const int hx = gq & 1, hy = gq >> 1;
+                        UJ[3 * (4 * (jf / 3 + hy) + jf % 3 + hx) + jc] += aj;
+                    }
+                    __syncwarp();   // another lane may own these entries in the next group
                 }
                 __syncwarp();
             }
+            // flush the cell's union sums and clear them
 #pragma unroll
-            for (int k = 0; k < 3; ++k) flush_q(M, pa[k], pb[k], acc[k], i, j, g);
-            if (four) flush_q(M, pa[3], pb[3], acc[3], i, j, g);
-            {
-                const int64_t gn = (int64_t)wrap1(j - 1 + (jn0 >> 2), g.ny) * g.nx + wrap1(i - 1 + (jn0 & 3), g.nx);
-                atomicAdd(J + (int64_t)jc0 * g.ncell + gn, aj0);
+            for (int t2 = 0; t2 < 4; ++t2) {
+                const int q = lane + 32 * t2;
+                if (q < kPairsQ) {
+                    T v[9];
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) {
+                        v[e] = U[q][e];
+                        U[q][e] = T(0);
+                    }
+                    flush_q_vals(M, pa[t2], pb[t2], v, i, j, g);
+                }
             }
-            if (j2) {
-                const int64_t gn = (int64_t)wrap1(j - 1 + (jn1 >> 2), g.ny) * g.nx + wrap1(i - 1 + (jn1 & 3), g.nx);
-                atomicAdd(J + (int64_t)jc1 * g.ncell + gn, aj1);
+            for (int q = lane; q < 48; q += 32) {
+                const T val = UJ[q];
+                UJ[q] = T(0);
+                const int un = q / 3, comp = q % 3;
+                const int64_t gn = (int64_t)wrap1(j - 1 + (un >> 2), g.ny) * g.nx + wrap1(i - 1 + (un & 3), g.nx);
+                if (val != T(0)) atomicAdd(J + (int64_t)comp * g.ncell + gn, val);
             }
+            __syncwarp();
         }
     }
 }
