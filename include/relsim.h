@@ -115,8 +115,8 @@ typedef struct {
                               particle, node pairs up to two cells apart, the
                               mass matrix stored for 13 offsets per node
                               ((0,0), (1,0), (2,0), (di,1) and (di,2) for
-                              di = -2..2: ncell x 117); steps run host-driven
-                              with the counting-sort re-sort              */
+                              di = -2..2: ncell x 117); the re-sort is a
+                              counting sort, as in 3D                     */
 } relsim_config;
 
 typedef struct {
@@ -161,8 +161,8 @@ RELSIM_API const char* relsim_last_error(const relsim_ctx* ctx);
    (0,0,0), (1,0,0), (-1,1,0), (0,1,0), (1,1,0), then (di,dj,1) for
    dj = -1..1 (outer) and di = -1..1 (inner), i.e. ncell x 126 values (the
    2D form: (0,0), (1,0), (-1,1), (0,1), (1,1), ncell x 45). The 3D form
-   covers the base scheme; its steps run host-driven with the general push
-   (any move length, radix sort). The adjoints and the autotuner cover the
+   covers the base scheme; its push allows any move length and re-sorts by a
+   counting sort that does not keep the order within a cell. The adjoints and the autotuner cover the
    2D form (INVALID_ARG in 3D).
 
    Load (replace) the particles of one species: n particles, positions x[2n]
@@ -358,8 +358,9 @@ RELSIM_API int relsim_energy_ledger(relsim_ctx* ctx, relsim_energy* out);
 /* One full step: build, solve, push; fills *ledger if it is non-NULL.
    Returns the first error of its parts (NOT_CONVERGED still completes the
    step). The first step after a load runs its parts from the host; later
-   steps (when profiling is off and no particle can cross more than one cell
-   per step) run as one CUDA graph captured on first use for the current
+   steps (when profiling is off and, in the 2D form with linear shapes, no
+   particle can cross more than one cell per step; always in the 3D form and
+   with quadratic shapes) run as one CUDA graph captured on first use for the current
    buffer layout: the solve's restart and Arnoldi loops are conditional while
    nodes whose conditions the device sets, so the step needs one launch and
    one synchronisation. Both routes run the same kernels in the same order.

@@ -896,6 +896,19 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
     return solve_outcome(c, &h, iters_out, relres_out);
 }
 
+// the push's grid (its ledger partials are sized by it)
+int push_blocks_for(const relsim_ctx* c)
+{
+    return c->g.dim == 3 ? push_blocks3(c->g)
+                         : (c->g.shape == 2 ? push_blocks_q(c->g) : push_grid_blocks(c->g, c->prec, c->push_cap));
+}
+
+// steps that can run as a captured graph: the one-cell-move sort of the 2D
+// linear form, and the counting-sort paths of the 3D form and the quadratic
+// shapes (no host decision inside a step); the radix path of long moves is
+// left host-driven
+bool graph_path(const relsim_ctx* c) { return c->fast_sort || c->g.dim == 3 || c->g.shape == 2; }
+
 // the host side of a push: the new cell starts and the new B become current
 void push_commit(relsim_ctx* c)
 {
@@ -914,8 +927,7 @@ void push_commit(relsim_ctx* c)
 template <typename T>
 int push_enqueue(relsim_ctx* c)
 {
-    const int nbp = c->g.dim == 3 ? push_blocks3(c->g)
-                    : (c->g.shape == 2 ? push_blocks_q(c->g) : push_grid_blocks(c->g, c->prec, c->push_cap));
+    const int nbp = push_blocks_for(c);
     TRY(ensure_partial(c, (int64_t)nbp * (kLedgerSpecies - 1)));
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         Species& sp = c->sp[s];
@@ -1101,7 +1113,7 @@ int capture_step(relsim_ctx* c, StepGraph& G)
 {
     const GmSetup S = gm_setup(c);
     TRY(solve_reserve(c, S));
-    TRY(ensure_partial(c, (int64_t)push_grid_blocks(c->g, c->prec, c->push_cap) * (kLedgerSpecies - 1)));
+    TRY(ensure_partial(c, (int64_t)push_blocks_for(c) * (kLedgerSpecies - 1)));
     if (G.exec) {
         cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;
@@ -1389,7 +1401,7 @@ int relabel_impl(relsim_ctx* c, int s, const int32_t* ids, int where)
 
 bool graph_eligible(const relsim_ctx* c)
 {
-    return c->state == kReady && c->have_step && c->fast_sort && !c->prof.on && !c->graph_off;
+    return c->state == kReady && c->have_step && graph_path(c) && !c->prof.on && !c->graph_off;
 }
 
 StepGraph* graph_for_layout(relsim_ctx* c)
@@ -2168,7 +2180,7 @@ int relsim_step(relsim_ctx* c, relsim_energy* ledger)
     if (!c) return RELSIM_ERR_INVALID_ARG;
     // after one host-driven step has sized every buffer, steps run as a
     // captured graph (not while profiling: event timing needs host launches)
-    if (c->state == kReady && c->have_step && c->fast_sort && !c->prof.on && !c->graph_off) {
+    if (c->state == kReady && c->have_step && graph_path(c) && !c->prof.on && !c->graph_off) {
         int status = RELSIM_OK;
         const int r = DISPATCH(step_graph, c, ledger, &status);
         if (r == RELSIM_OK) return status;

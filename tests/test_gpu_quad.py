@@ -153,6 +153,9 @@ def test_three_fp64_steps_and_energy_identity(rs, oq):
         assert abs(led["residual"]) < 1e-10 * total
     Eg, Bg = sim.fields()
     assert rel(Eg, E) < 1e-9 and rel(Bg, B) < 1e-9
+    # the second and third steps ran as CUDA graphs
+    gi = sim.graph_info()
+    assert gi["graph_steps"] == 2 and not gi["disabled"], gi
     sim.close()
 
 
