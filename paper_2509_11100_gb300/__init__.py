@@ -496,6 +496,12 @@ def relsim_relabel_particles(ctx, species, ids):
     return _check(ctx, lib().relsim_relabel_particles(ctx, species, p[0], p[1]))
 
 
+def relsim_set_launch_shapes(ctx, deposit_blocks=0, push_blocks=0, op_rows=0):
+    """Apply launch shapes (as relsim_autotune chooses them): deposit blocks,
+    push grid cap (0: defaults) and the 2D operator's tile rows."""
+    return _check(ctx, lib().relsim_set_launch_shapes(ctx, int(deposit_blocks), int(push_blocks), int(op_rows)))
+
+
 def relsim_autotune(ctx) -> dict:
     """Time candidate launch shapes of the deposit and the push on the loaded
     state and keep the fastest; returns the candidates and the choice."""
@@ -672,8 +678,7 @@ class Simulation:
         return relsim_autotune(self.ctx)
 
     def set_launch_shapes(self, deposit_blocks=0, push_blocks=0, op_rows=0):
-        return _check(self.ctx, lib().relsim_set_launch_shapes(self.ctx, int(deposit_blocks), int(push_blocks),
-                                                               int(op_rows)))
+        return relsim_set_launch_shapes(self.ctx, deposit_blocks, push_blocks, op_rows)
 
     def push_adjoint(self, s, gu1, gx1, device=False):
         return relsim_push_adjoint(self.ctx, s, self.ncell, gu1, gx1, device)
