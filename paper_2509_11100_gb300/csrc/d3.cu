@@ -26,8 +26,6 @@
 namespace relsim {
 namespace {
 
-constexpr int kD3Threads = 256;
-
 unsigned grid3(int64_t n, int threads, int64_t cap)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -146,29 +144,6 @@ __device__ __forceinline__ void corner_weights(T fx, T fy, T fz, T (&W)[8])
     const T X[2] = {T(1) - fx, fx}, Y[2] = {T(1) - fy, fy}, Z[2] = {T(1) - fz, fz};
 #pragma unroll
     for (int a = 0; a < 8; ++a) W[a] = X[a & 1] * Y[(a >> 1) & 1] * Z[(a >> 2) & 1];
-}
-
-// B^n at the particle of cell (i,j,k) with offsets f: the centres around it
-// are (i-1, i) along x when fx < 1/2, else (i, i+1); likewise y and z
-template <typename T>
-__device__ __forceinline__ void gather_B3(const T* __restrict__ B, int i, int j, int k, T fx, T fy, T fz,
-                                          const GridP& g, T (&Bp)[3])
-{
-    const bool lx = fx < T(0.5), ly = fy < T(0.5), lz = fz < T(0.5);
-    const T tx = lx ? fx + T(0.5) : fx - T(0.5);
-    const T ty = ly ? fy + T(0.5) : fy - T(0.5);
-    const T tz = lz ? fz + T(0.5) : fz - T(0.5);
-    const int i0 = lx ? wrap1(i - 1, g.nx) : i, j0 = ly ? wrap1(j - 1, g.ny) : j, k0 = lz ? wrap1(k - 1, g.nz) : k;
-    const int ii[2] = {i0, wrap1(i0 + 1, g.nx)}, jj[2] = {j0, wrap1(j0 + 1, g.ny)}, kk[2] = {k0, wrap1(k0 + 1, g.nz)};
-    T W[8];
-    corner_weights(tx, ty, tz, W);
-    Bp[0] = Bp[1] = Bp[2] = T(0);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const int64_t c = node3(ii[a & 1], jj[(a >> 1) & 1], kk[(a >> 2) & 1], g);
-#pragma unroll
-        for (int comp = 0; comp < 3; ++comp) Bp[comp] += W[a] * ld(B + comp * (int64_t)g.ncell + c);
-    }
 }
 
 // alpha = (I - [a]x + a a^T)/(1 + |a|^2), a = beta B/gbar (row-major)
