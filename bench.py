@@ -363,12 +363,62 @@ def run_ours(args):
         for _ in range(ke):
             e2e_step()
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t1) / ke
+        te_serial = (time.perf_counter() - t1) / ke
+        # pipelined: two contexts on streams of their own, each step's inputs
+        # copied host -> device (copy engine, pinned memory) into one of two
+        # device buffers while the other context steps on the previous ones;
+        # every step still copies its full inputs and reads its ledger back
+        flat = [t for trio in pinned for t in trio] + [E, B]
+        dbuf = [[torch.empty(t.shape, dtype=t.dtype, device="cuda") for t in flat] for _ in range(2)]
+        cstream = [torch.cuda.Stream(), torch.cuda.Stream()]
+        sstream = [torch.cuda.Stream(), torch.cuda.Stream()]
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        sims = [rs.Simulation(cfg, stream=sstream[0].cuda_stream), rs.Simulation(cfg, stream=sstream[1].cuda_stream)]
+
+        def copy_in(k):
+            with torch.cuda.stream(cstream[k]):
+                for d, h in zip(dbuf[k], flat):
+                    d.copy_(h, non_blocking=True)
+                ready[k].record(cstream[k])
+
+        def run(k):
+            sstream[k].wait_event(ready[k])
+            d = dbuf[k]
+            with torch.cuda.stream(sstream[k]):
+                for s_ in range(len(pinned)):
+                    sims[k].load_species(s_, d[3 * s_], d[3 * s_ + 1], d[3 * s_ + 2])
+                sims[k].set_fields(d[-2], d[-1])
+                led, _ = sims[k].step(ledger=True)
+            # the buffer may be refilled once this step has read it
+            cstream[k].wait_stream(sstream[k])
+            return led
+
+        copy_in(0)
+        copy_in(1)
+        run(0)
+        run(1)   # warm-up: sizes both contexts
+        torch.cuda.synchronize()
+        barrier()
+        copy_in(0)
+        t1 = time.perf_counter()
+        for t in range(2 * ke):
+            if t + 1 < 2 * ke:
+                copy_in((t + 1) % 2)   # the next step's inputs while this one runs
+            run(t % 2)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t1) / (2 * ke)
+        for sm in sims:
+            sm.close()
+        del dbuf
         if dist is not None:
             te = max_over_ranks(te, dist)
+            te_serial = max_over_ranks(te_serial, dist)
         out["e2e"] = {"value": world * N / te, "unit": UNIT, "ms_per_step": te * 1e3,
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "steps": ke}
+                      "steps": 2 * ke,
+                      "mode": "pipelined: two contexts, each step's inputs copied from pinned host memory "
+                              "while the other context steps",
+                      "serial": {"value": world * N / te_serial, "ms_per_step": te_serial * 1e3, "steps": ke}}
         del pinned
     sim.close()
     del sim
