@@ -499,9 +499,11 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
       Jhat_g += (w q/dV) W_g(x) alpha u/gbar,
       M_{g g'} += (w q beta/dV) W_g(x) W_g'(x) alpha/gbar  (ordered pairs, full layout).
     Given dL/dJhat (gJ, (3, nn)) and dL/dM (gM, (nn, 9, 3, 3) full layout),
-    returns dL/du (3, N), dL/dx, dL/dy (N) and dL/dB (3, nn): the gradient of
-    alpha collects the current and every node pair's block gradient, then
-    flows through a (d alpha = -alpha d[a]x alpha) to Bp and gbar."""
+    returns dL/du (3, N), dL/dx, dL/dy (N), dL/dw (N) and dL/dB (3, nn): the
+    gradient of alpha collects the current and every node pair's block
+    gradient, then flows through a (d alpha = -alpha d[a]x alpha) to Bp and
+    gbar; J and M are linear in w, so dL/dw is the particle's contribution to
+    <gJ, Jhat> + <gM, M> per unit weight."""
     nn = c.nx * c.ny
     dV = c.dx * c.dy
     Bf = np.asarray(B, dtype=np.float64).reshape(3, nn)
@@ -511,6 +513,7 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
     gu0 = np.zeros((3, N))
     gx0 = np.zeros(N)
     gy0 = np.zeros(N)
+    gw0 = np.zeros(N)
     gB = np.zeros((3, nn))
     for s in range(int(c.nspecies)):
         a0, a1 = int(P.off[s]), int(P.off[s + 1])
@@ -547,6 +550,7 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
             sJ = (gj * au).sum(axis=0)
             gWn[k] += cJ * sJ / gb
             ggb -= cJ * WN[k] * sJ / gb ** 2
+            gw0[a0:a1] += (q / dV) * WN[k] * sJ / gb
             # M: every ordered node pair (k, l) of the cell
             for l in range(4):
                 # the slot of node l seen from node k (offsets of the cell's nodes)
@@ -560,6 +564,7 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
                 gWn[k] += cM * WN[l] * s2 / gb
                 gWn[l] += cM * WN[k] * s2 / gb
                 ggb -= cM * WN[k] * WN[l] * s2 / gb ** 2
+                gw0[a0:a1] += (q * beta / dV) * WN[k] * WN[l] * s2 / gb
         Gm = -np.einsum("nji,njk,nlk->nil", alpha, galpha, alpha)   # -alpha^T galpha alpha^T
         ga = np.stack([Gm[:, 2, 1] - Gm[:, 1, 2], Gm[:, 0, 2] - Gm[:, 2, 0], Gm[:, 1, 0] - Gm[:, 0, 1]])
         gBp = beta * ga / gb
@@ -572,7 +577,7 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
             gx0[a0:a1] += WNx[k] * gWn[k] + WCx[k] * bg
             gy0[a0:a1] += WNy[k] * gWn[k] + WCy[k] * bg
         gu0[:, a0:a1] = gu
-    return {"u": gu0, "x": gx0, "y": gy0, "B": gB}
+    return {"u": gu0, "x": gx0, "y": gy0, "w": gw0, "B": gB}
 
 
 def step_adjoint(c, P: Particles, E, B, gu1, gx1, gy1, gE1, gB1):
@@ -589,7 +594,7 @@ def step_adjoint(c, P: Particles, E, B, gu1, gx1, gy1, gE1, gB1):
     gp = push_adjoint(c, P, Et, B, gu1, gx1, gy1)
     gf = field_adjoint(c, M, Et, gE1, gB1, gEt=gp["E"])
     gd = deposit_adjoint(c, P, B, gf["J"], gf["M"])
-    return {"u": gp["u"] + gd["u"], "x": gp["x"] + gd["x"], "y": gp["y"] + gd["y"],
+    return {"u": gp["u"] + gd["u"], "x": gp["x"] + gd["x"], "y": gp["y"] + gd["y"], "w": gd["w"],
             "E": gf["E0"], "B": gf["B0"] + gp["B"] + gd["B"], "push": gp, "field": gf, "deposit": gd}
 
 
@@ -624,9 +629,10 @@ def window_gradient(c, species, E, B, nsteps, mode=1):
     W, gB = mode_energy(c, B, mode)
     gE = np.zeros_like(E)
     N = P.x.size
-    gu, gx, gy = np.zeros((3, N)), np.zeros(N), np.zeros(N)
+    gu, gx, gy, gw = np.zeros((3, N)), np.zeros(N), np.zeros(N), np.zeros(N)
     for n in range(nsteps - 1, -1, -1):
         Pn, En, Bn = pres[n]
         g = step_adjoint(c, Pn, En, Bn, gu, gx, gy, gE, gB)
         gu, gx, gy, gE, gB = g["u"], g["x"], g["y"], g["E"], g["B"]
-    return W, {"E": gE, "B": gB, "u": gu, "x": gx, "y": gy}
+        gw = gw + g["w"]   # the weights are the same at every step
+    return W, {"E": gE, "B": gB, "u": gu, "x": gx, "y": gy, "w": gw}

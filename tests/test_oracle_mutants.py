@@ -80,6 +80,9 @@ PY_MUTANTS = {
     "deposit_adjoint_current_untransposed": ('gu += cJ * WN[k] / gb * np.einsum("nji,jn->in", alpha, gj)',
                                              'gu += cJ * WN[k] / gb * np.einsum("nij,jn->in", alpha, gj)'),
     "deposit_adjoint_one_sided_pairs": ("                gWn[l] += cM * WN[k] * s2 / gb\n", "\n"),
+    "deposit_adjoint_w_drops_current": ("            gw0[a0:a1] += (q / dV) * WN[k] * sJ / gb\n", "\n"),
+    "deposit_adjoint_w_wrong_pair_weight": ("gw0[a0:a1] += (q * beta / dV) * WN[k] * WN[l] * s2 / gb",
+                                            "gw0[a0:a1] += (q * beta / dV) * WN[k] * WN[k] * s2 / gb"),
 }
 # mistakes planted in the 3D oracle, caught by its own pins
 MUTANTS3 = {

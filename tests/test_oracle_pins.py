@@ -883,6 +883,12 @@ def test_deposit_adjoint_matches_directional_derivatives(orc):
     def mB(P, Bb, s):
         Bb += s * dB
     assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-6 * np.abs(g["B"] * dB).sum()
+    # J and M are linear in the weights: a finite change equals <g_w, d>
+    # exactly (to rounding), whatever its size
+    dw = rng.normal(size=N) * 0.3
+    Pw = P0.copy()
+    Pw.w += dw
+    assert abs((L(Pw, B) - L(P0, B)) - np.sum(g["w"] * dw)) < 1e-10 * np.abs(g["w"] * dw).sum()
 
 
 def test_step_adjoint_matches_directional_derivatives(orc):
@@ -960,3 +966,18 @@ def test_mode_energy_gradient_and_window_gradient(orc):
         fd = (orc.window_gradient(c, st["species"], plus["E"], plus["B"], 3)[0]
               - orc.window_gradient(c, st["species"], minus["E"], minus["B"], 3)[0]) / (2 * h)
         assert abs(fd - np.sum(gw[name] * dd)) < 1e-5 * np.abs(gw[name] * dd).sum(), name
+    # the weights (the same at every step): central differences along a
+    # random direction of the particles' weights
+    N = sum(len(sp["w"]) for sp in st["species"])
+    dw = rng.normal(size=N) * 0.1
+    def with_w(sgn):
+        sps, k = [], 0
+        for sp in st["species"]:
+            n = len(sp["w"])
+            d = dict(sp)
+            d["w"] = sp["w"] + sgn * h * dw[k:k + n]
+            sps.append(d)
+            k += n
+        return orc.window_gradient(c, sps, st["E"], st["B"], 3)[0]
+    fd = (with_w(1) - with_w(-1)) / (2 * h)
+    assert abs(fd - np.sum(gw["w"] * dw)) < 1e-5 * np.abs(gw["w"] * dw).sum()
