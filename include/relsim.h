@@ -263,10 +263,13 @@ RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const do
    beta/dV) W_g W_g' alpha/gbar, alpha from B^n(x). Given gJ = dL/dJhat
    (3*ncell) and gM = dL/dM for the stored blocks (ncell x 45, the layout of
    relsim_get_mass_matrix and relsim_field_adjoint's output), it returns per
-   particle gu0 = dL/du^n (3n, interleaved) and gx0 = dL/dx^{n+1/2} (2n,
-   interleaved), in the current order, and overwrites gB = dL/dB^n (centre
-   field, 3*ncell) with this species' contribution. Per particle in FP64
-   from the stored values. Call it after relsim_build_mass_matrix and before
+   particle gu0 = dL/du^n (3n, interleaved), gx0 = dL/dx^{n+1/2} (2n,
+   interleaved) and, if gw0 is not NULL, gw0 = dL/dw (n; Jhat and M are
+   linear in the weight, so this is the particle's contribution to
+   <gJ, Jhat> + <gM, M> per unit weight), in the current order, and
+   overwrites gB = dL/dB^n (centre field, 3*ncell) with this species'
+   contribution. Per particle from the stored values, in the form's
+   precision. Call it after relsim_build_mass_matrix and before
    relsim_push. Synchronises the stream. Errors: INVALID_ARG (including a
    gamma_pred context), BAD_STATE, OOM, CUDA.
    One step's adjoint chains the three: relsim_push_adjoint per species
@@ -275,7 +278,7 @@ RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const do
    dL/dM), relsim_deposit_adjoint per species; dL/du^n and dL/dx^{n+1/2} are
    the sums of the push's and the deposit's, dL/dB^n of all three. */
 RELSIM_API int relsim_deposit_adjoint(relsim_ctx* ctx, int species, const double* gJ, const double* gM,
-                                      double* gu0, double* gx0, double* gB, int where);
+                                      double* gu0, double* gx0, double* gB, double* gw0, int where);
 
 /* Adjoint of the push of one species with the fields held fixed (the
    explicit pusher of Sec. 2; base scheme, gbar = gamma(u^n)). For the
@@ -310,7 +313,10 @@ RELSIM_API int relsim_push_adjoint(relsim_ctx* ctx, int species, const double* g
      gx[s]    2 n_s, interleaved (x, y), one pair per species s (arrays of
               nspecies host pointers to device arrays): indexed by the
               particle's id (track_ids), on entry dL/du^{n+1} and
-              dL/dx^{n+3/2}, on return dL/du^n and dL/dx^{n+1/2}.
+              dL/dx^{n+3/2}, on return dL/du^n and dL/dx^{n+1/2};
+     gw[s]    n_s per species (gw, or any gw[s], may be NULL), indexed by
+              id: the step's dL/dw is added (the weights do not change
+              from step to step, so a window sums the steps' terms).
    Ids must be a permutation of 0 .. n_s - 1 (as a load assigns them, or
    after relsim_relabel_particles with a permutation); with repeated ids the
    gradients of the colliding particles are undefined (every access stays in
@@ -324,7 +330,7 @@ RELSIM_API int relsim_push_adjoint(relsim_ctx* ctx, int species, const double* g
    state), NOT_CONVERGED (the forward or the adjoint solve; outputs still
    written), NONFINITE, OOM, CUDA. */
 RELSIM_API int relsim_step_adjoint(relsim_ctx* ctx, double* gE, double* gB, double* const* gu, double* const* gx,
-                                   int* iters, double* rel_residual);
+                                   double* const* gw, int* iters, double* rel_residual);
 
 /* Relabel a species' particles (track_ids): each particle carrying id j
    gets ids[j] (n_s int32, host or device per where). Right after a load

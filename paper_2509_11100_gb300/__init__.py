@@ -130,11 +130,11 @@ _SIGS = {
     "relsim_batch_destroy": (None, [_P]),
     "relsim_graph_info": (ctypes.c_int, [_CTX, _P, _P, _P]),
     "relsim_field_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
-    "relsim_deposit_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int]),
+    "relsim_deposit_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
     "relsim_autotune": (ctypes.c_int, [_CTX, _P]),
     "relsim_push_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
     "relsim_set_launch_shapes": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-    "relsim_step_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
+    "relsim_step_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_double)]),
     "relsim_relabel_particles": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
 }
@@ -443,15 +443,16 @@ def relsim_field_adjoint(ctx, ncell, gE1, gB1, mass=True, device=False, gEt=None
 
 def relsim_deposit_adjoint(ctx, species, ncell, gJ, gM):
     """Adjoint of one species' deposit: from dL/dJhat (3, ncell) and dL/dM
-    (ncell, 5, 3, 3), returns {"u": (n, 3), "x": (n, 2), "B": (3, ncell)}."""
+    (ncell, 5, 3, 3), returns {"u": (n, 3), "x": (n, 2), "w": (n,),
+    "B": (3, ncell)}."""
     p1, p2 = _ptr(gJ), _ptr(gM)
     dev = _where(p1, p2) == RELSIM_DEVICE
     n = relsim_num_particles(ctx, species)
     outs = {"u": _out((n, 3), np.float64, dev), "x": _out((n, 2), np.float64, dev),
-            "B": _out((3, ncell), np.float64, dev)}
+            "w": _out((n,), np.float64, dev), "B": _out((3, ncell), np.float64, dev)}
     pp = {k: _ptr(v, writable=True) for k, v in outs.items()}
     _check(ctx, lib().relsim_deposit_adjoint(ctx, species, p1[0], p2[0], pp["u"][0], pp["x"][0], pp["B"][0],
-                                             RELSIM_DEVICE if dev else RELSIM_HOST))
+                                             pp["w"][0], RELSIM_DEVICE if dev else RELSIM_HOST))
     return outs
 
 
@@ -470,21 +471,24 @@ def relsim_push_adjoint(ctx, species, ncell, gu1, gx1, device=False):
     return outs
 
 
-def relsim_step_adjoint(ctx, gE, gB, gu, gx):
+def relsim_step_adjoint(ctx, gE, gB, gu, gx, gw=None):
     """One whole step's adjoint in place on CUDA float64 tensors: gE, gB
     (3, ncell) and per species gu[s] (n_s, 3), gx[s] (n_s, 2) indexed by
     particle id; dL/d(state after the step) in, dL/d(state before) out.
+    gw (optional, per species (n_s,) by id): the step's dL/dw is added.
     Returns (adjoint iters, relative residual, status)."""
     items = [_ptr(gE, writable=True), _ptr(gB, writable=True)]
     pu = [_ptr(a, writable=True) for a in gu]
     px = [_ptr(a, writable=True) for a in gx]
-    if _where(*(items + pu + px)) != RELSIM_DEVICE:
+    pw = [_ptr(a, writable=True) for a in gw] if gw is not None else []
+    if _where(*(items + pu + px + pw)) != RELSIM_DEVICE:
         raise ValueError("relsim_step_adjoint takes device arrays only")
     au = (ctypes.c_void_p * len(pu))(*[p[0] for p in pu])
     ax = (ctypes.c_void_p * len(px))(*[p[0] for p in px])
+    aw = (ctypes.c_void_p * len(pw))(*[p[0] for p in pw]) if pw else None
     it = ctypes.c_int()
     rr = ctypes.c_double()
-    code = _check(ctx, lib().relsim_step_adjoint(ctx, items[0][0], items[1][0], au, ax, ctypes.byref(it),
+    code = _check(ctx, lib().relsim_step_adjoint(ctx, items[0][0], items[1][0], au, ax, aw, ctypes.byref(it),
                                                  ctypes.byref(rr)), allow=(RELSIM_ERR_NOT_CONVERGED,))
     return it.value, rr.value, code
 
@@ -686,8 +690,8 @@ class Simulation:
     def field_adjoint(self, gE1, gB1, mass=True, device=False, gEt=None):
         return relsim_field_adjoint(self.ctx, self.ncell, gE1, gB1, mass, device, gEt)
 
-    def step_adjoint(self, gE, gB, gu, gx):
-        return relsim_step_adjoint(self.ctx, gE, gB, gu, gx)
+    def step_adjoint(self, gE, gB, gu, gx, gw=None):
+        return relsim_step_adjoint(self.ctx, gE, gB, gu, gx, gw)
 
     def relabel(self, s, ids):
         return relsim_relabel_particles(self.ctx, s, ids)

@@ -64,6 +64,14 @@ __global__ void k_scatter_grad(const int32_t* __restrict__ id, const double* __r
     }
 }
 
+// gw[id[i]] += lw[i]
+__global__ void k_scatter_add_w(const int32_t* __restrict__ id, const double* __restrict__ lw, double* __restrict__ gw,
+                                int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        gw[id[i]] += lw[i];
+}
+
 // bit 0 of *bad if a carried id or a new label is outside [0, n)
 __global__ void k_check_ids(const int32_t* __restrict__ id, const int32_t* __restrict__ ids, int64_t n,
                             int* __restrict__ bad)
@@ -105,6 +113,14 @@ cudaError_t scatter_grad(const int32_t* id, const double* lu, const double* lx, 
         k_scatter_grad<true><<<grid_for(n), kThreads, 0, st>>>(id, lu, lx, gu, gx, n);
     else
         k_scatter_grad<false><<<grid_for(n), kThreads, 0, st>>>(id, lu, lx, gu, gx, n);
+    return cudaGetLastError();
+}
+
+cudaError_t scatter_add_w(const int32_t* id, const double* lw, double* gw, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launches(1);
+    k_scatter_add_w<<<grid_for(n), kThreads, 0, st>>>(id, lw, gw, n);
     return cudaGetLastError();
 }
 

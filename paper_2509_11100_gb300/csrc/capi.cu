@@ -1261,25 +1261,27 @@ int adjoint_impl(relsim_ctx* c, const double* gE1, const double* gB1, const doub
 // overwritten with this species' contribution.
 template <typename T>
 int deposit_adjoint_impl(relsim_ctx* c, int s, const double* gJ, const double* gM, double* gu0, double* gx0,
-                         double* gB, int where)
+                         double* gB, double* gw0, int where)
 {
     Species& sp = c->sp[s];
     const int64_t n = sp.n, nf = 3 * (int64_t)c->g.ncell, nm = (int64_t)c->g.ncell * kMBlock;
     const bool host = where == RELSIM_HOST;
-    if (host) TRY(ensure_stage(c, nf + nm + 5 * n + nf));
+    if (host) TRY(ensure_stage(c, nf + nm + 5 * n + nf + n));
     const double *dJ, *dM;
     TRY(stage_in(c, gJ, nf, where, &dJ, 0));
     TRY(stage_in(c, gM, nm, where, &dM, nf));
     double* ou = host ? c->stage + nf + nm : gu0;
     double* ox = host ? c->stage + nf + nm + 3 * n : gx0;
     double* oB = host ? c->stage + nf + nm + 5 * n : gB;
+    double* ow = gw0 ? (host ? c->stage + nf + nm + 5 * n + nf : gw0) : nullptr;
     CK(cudaMemsetAsync(oB, 0, sizeof(double) * (size_t)nf, c->st));
     if (n > 0)
-        CK(deposit_adjoint<T>(arrays<T>(sp, sp.cur), sp.start, dJ, dM, ou, ox, oB, (const T*)c->B[c->bcur], c->g,
+        CK(deposit_adjoint<T>(arrays<T>(sp, sp.cur), sp.start, dJ, dM, ou, ox, ow, oB, (const T*)c->B[c->bcur], c->g,
                               SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st));
     if (host) {
         CK(cudaMemcpyAsync(gu0, ou, sizeof(double) * (size_t)(3 * n), cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(gx0, ox, sizeof(double) * (size_t)(2 * n), cudaMemcpyDeviceToHost, c->st));
+        if (gw0) CK(cudaMemcpyAsync(gw0, ow, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(gB, oB, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToHost, c->st));
     }
     CK(cudaStreamSynchronize(c->st));
@@ -1326,8 +1328,8 @@ int push_adjoint_impl(relsim_ctx* c, int s, const double* gu1, const double* gx1
 // the field adjoint takes the pushes' dL/dE^{n+theta}; the deposit adjoints
 // add their particle terms and dL/dB^n.
 template <typename T>
-int step_adjoint_impl(relsim_ctx* c, double* gE, double* gB, double* const* gu, double* const* gx, int* iters,
-                      double* relres)
+int step_adjoint_impl(relsim_ctx* c, double* gE, double* gB, double* const* gu, double* const* gx,
+                      double* const* gw, int* iters, double* relres)
 {
     const int64_t nf = 3 * (int64_t)c->g.ncell, nm = (int64_t)c->g.ncell * kMBlock;
     int64_t nmax = 0;
@@ -1360,9 +1362,11 @@ int step_adjoint_impl(relsim_ctx* c, double* gE, double* gB, double* const* gu, 
         const int64_t n = sp.n;
         if (n == 0) continue;
         const PArrays<T> a = arrays<T>(sp, sp.cur);
-        CK(deposit_adjoint<T>(a, sp.start, fJ, fM, L, L + 3 * n, sB, Bn, c->g, SpeciesConst{c->cfg.q[s], c->cfg.m[s]},
-                              c->st));
+        double* lw = gw && gw[s] ? P : nullptr;   // the push adjoint's output was scattered already
+        CK(deposit_adjoint<T>(a, sp.start, fJ, fM, L, L + 3 * n, lw, sB, Bn, c->g,
+                              SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st));
         CK(scatter_grad(a.id, L, L + 3 * n, gu[s], gx[s], n, true, c->st));
+        if (lw) CK(scatter_add_w(a.id, lw, gw[s], n, c->st));
     }
     CK(cudaMemcpyAsync(gE, fE, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToDevice, c->st));
     CK(add_fields(fB, sB, gB, nf, c->st));
@@ -1981,7 +1985,7 @@ int relsim_autotune(relsim_ctx* c, relsim_tuning* out)
 }
 
 int relsim_deposit_adjoint(relsim_ctx* c, int species, const double* gJ, const double* gM, double* gu0,
-                           double* gx0, double* gB, int where)
+                           double* gx0, double* gB, double* gw0, int where)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
     if (c->g.dim == 3 || c->g.shape == 2)
@@ -1993,7 +1997,7 @@ int relsim_deposit_adjoint(relsim_ctx* c, int species, const double* gJ, const d
     if (c->En) return fail(c, RELSIM_ERR_INVALID_ARG, "the deposit adjoint covers the base scheme (gamma_pred = 0)");
     if (c->state != kBuilt && c->state != kSolved)
         return fail(c, RELSIM_ERR_BAD_STATE, "the deposit adjoint needs a built step (before the push)");
-    return DISPATCH(deposit_adjoint_impl, c, species, gJ, gM, gu0, gx0, gB, where);
+    return DISPATCH(deposit_adjoint_impl, c, species, gJ, gM, gu0, gx0, gB, gw0, where);
 }
 
 int relsim_push_adjoint(relsim_ctx* c, int species, const double* gu1, const double* gx1, double* gu0,
@@ -2011,8 +2015,8 @@ int relsim_push_adjoint(relsim_ctx* c, int species, const double* gu1, const dou
     return DISPATCH(push_adjoint_impl, c, species, gu1, gx1, gu0, gx0, gE, gB, where);
 }
 
-int relsim_step_adjoint(relsim_ctx* c, double* gE, double* gB, double* const* gu, double* const* gx, int* iters,
-                        double* rel_residual)
+int relsim_step_adjoint(relsim_ctx* c, double* gE, double* gB, double* const* gu, double* const* gx,
+                        double* const* gw, int* iters, double* rel_residual)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
     if (c->g.dim == 3 || c->g.shape == 2)
@@ -2027,7 +2031,7 @@ int relsim_step_adjoint(relsim_ctx* c, double* gE, double* gB, double* const* gu
     if (r != RELSIM_OK) return r;
     const int fs = relsim_field_solve(c, nullptr, nullptr);
     if (fs != RELSIM_OK && fs != RELSIM_ERR_NOT_CONVERGED) return fs;
-    r = DISPATCH(step_adjoint_impl, c, gE, gB, gu, gx, iters, rel_residual);
+    r = DISPATCH(step_adjoint_impl, c, gE, gB, gu, gx, gw, iters, rel_residual);
     if (r == RELSIM_OK && fs == RELSIM_ERR_NOT_CONVERGED)
         r = fail(c, RELSIM_ERR_NOT_CONVERGED, "the step's forward solve did not converge");
     return r;

@@ -126,6 +126,8 @@ cudaError_t gather_grad(const int32_t* id, const double* gu, const double* gx, d
 // gu[id[i]] = lu[i], gx[id[i]] = lx[i] (or += with add)
 cudaError_t scatter_grad(const int32_t* id, const double* lu, const double* lx, double* gu, double* gx, int64_t n,
                          bool add, cudaStream_t st);
+// gw[id[i]] += lw[i]
+cudaError_t scatter_add_w(const int32_t* id, const double* lw, double* gw, int64_t n, cudaStream_t st);
 // bit 0 of *bad if id[i] or ids[i] is outside [0, n) (flag accumulates)
 cudaError_t check_ids(const int32_t* id, const int32_t* ids, int64_t n, int* bad, cudaStream_t st);
 // id[i] = ids[id[i]]
@@ -164,11 +166,12 @@ cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, i
                          const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
                          cudaStream_t st);
 // adjoint of the deposit (base scheme): per particle dL/du^n, dL/dx^{n+1/2}
-// from dL/dJhat (3 ncell) and dL/dM (ncell x 45, stored blocks); dL/dB^n
-// added into gB (FP64 atomics)
+// and (gw0 not null) dL/dw from dL/dJhat (3 ncell) and dL/dM (ncell x 45,
+// stored blocks); dL/dB^n added into gB (FP64 atomics)
 template <typename T>
 cudaError_t deposit_adjoint(PArrays<T> src, const int32_t* start, const double* gJ, const double* gM, double* gu0,
-                            double* gx0, double* gB, const T* B, GridP g, SpeciesConst sc, cudaStream_t st);
+                            double* gx0, double* gw0, double* gB, const T* B, GridP g, SpeciesConst sc,
+                            cudaStream_t st);
 // adjoint of the push with the fields fixed (base scheme): per particle
 // dL/du^n, dL/dx^{n+1/2} from dL/du^{n+1}, dL/dx^{n+3/2} (FP64, interleaved,
 // current order); dL/dE^{n+theta}, dL/dB^n added into gE, gB (FP64 atomics)

@@ -1416,7 +1416,8 @@ template <typename T>
 __global__ void __launch_bounds__(PushCfg<T>::threads, sizeof(T) == 4 ? 4 : 1)
 k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gJ,
                   const double* __restrict__ gM, double* __restrict__ gu0, double* __restrict__ gx0,
-                  double* __restrict__ gB, const T* __restrict__ B, GridP g, double beta_d, double cq)
+                  double* __restrict__ gw0, double* __restrict__ gB, const T* __restrict__ B, GridP g, double beta_d,
+                  double cq)
 {
     using A = T;
     constexpr int W = PushCfg<T>::warps;
@@ -1498,6 +1499,7 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
                 A ga_[3][3] = {{A(0), A(0), A(0)}, {A(0), A(0), A(0)}, {A(0), A(0), A(0)}};   // dL/dalpha
                 A gW[4] = {A(0), A(0), A(0), A(0)}, gu[3] = {A(0), A(0), A(0)};
                 A sg = A(0);   // sum of the terms' values: d/dgbar of each is -value/gbar
+                A sJw = A(0), sMw = A(0);   // the same sums per unit weight (J and M are linear in w)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const A gj[3] = {(A)gJ[nodes[k]], (A)gJ[nc + nodes[k]], (A)gJ[2 * (int64_t)nc + nodes[k]]};
@@ -1514,6 +1516,7 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
                     }
                     gW[k] += cJ * sJ;
                     sg += cJ * Wn[k] * sJ;
+                    sJw += Wn[k] * sJ;
                 }
 #pragma unroll
                 for (int pr = 0; pr < 10; ++pr) {
@@ -1535,6 +1538,7 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
                     gW[pa[pr]] += cM * wb * s2;
                     gW[pb[pr]] += cM * wa * s2;
                     sg += coef * s2;
+                    sMw += wa * wb * s2;
                 }
                 A ggb = -sg * rgb;
                 // Gm = -alpha^T ga_ alpha^T; gradient of a from <Gm, [da]x>
@@ -1575,6 +1579,7 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
                 for (int k = 0; k < 3; ++k) gu0[3 * (int64_t)p + k] = (double)gu[k];
                 gx0[2 * (int64_t)p] = (double)gxp;
                 gx0[2 * (int64_t)p + 1] = (double)gyp;
+                if (gw0) gw0[p] = (double)((cJ0 * sJw + cM0 * sMw) * rgb);
             }
             const Runs rn = runs_of(act ? cl : -1, lane);
             flush_centres(gc, rn, act, gB, i, j, nx, ny, nc);
@@ -1664,12 +1669,12 @@ cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int3
 
 template <typename T>
 cudaError_t deposit_adjoint(PArrays<T> src, const int32_t* start, const double* gJ, const double* gM, double* gu0,
-                            double* gx0, double* gB, const T* B, GridP g, SpeciesConst sc, cudaStream_t st)
+                            double* gx0, double* gw0, double* gB, const T* B, GridP g, SpeciesConst sc, cudaStream_t st)
 {
     const double beta = sc.q * g.dt / (2.0 * sc.m);
     count_launches(1);
     k_deposit_adjoint<T><<<push_grid_blocks(g, sizeof(T) == 4 ? 32 : 64), PushCfg<T>::threads, 0, st>>>(
-        src, start, gJ, gM, gu0, gx0, gB, B, g, beta, sc.q);
+        src, start, gJ, gM, gu0, gx0, gw0, gB, B, g, beta, sc.q);
     return cudaGetLastError();
 }
 
@@ -1747,8 +1752,8 @@ cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int 
                                          const T*, const T*, GridP, SpeciesConst, double*, int,      \
                                          cudaStream_t);                                              \
     template cudaError_t deposit_adjoint<T>(PArrays<T>, const int32_t*, const double*, const double*, \
-                                            double*, double*, double*, const T*, GridP, SpeciesConst, \
-                                            cudaStream_t);                                            \
+                                            double*, double*, double*, double*, const T*, GridP,      \
+                                            SpeciesConst, cudaStream_t);                              \
     template cudaError_t push_adjoint<T>(PArrays<T>, const int32_t*, const double*, const double*,   \
                                          double*, double*, double*, double*, const T*, const T*,     \
                                          GridP, SpeciesConst, cudaStream_t);                         \

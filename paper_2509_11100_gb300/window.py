@@ -24,7 +24,7 @@ import numpy as np
 
 from . import RELSIM_ERR_NOT_CONVERGED, Simulation, relsim_config
 
-__all__ = ["ModeEnergyWindow", "mode_energy_and_gradient", "WindowLoss"]
+__all__ = ["ModeEnergyWindow", "mode_energy_and_gradient", "WindowLoss", "parameter_gradient"]
 
 
 def mode_energy_and_gradient(B, nx, ny, dV, mode=1, component=1):
@@ -119,6 +119,8 @@ class ModeEnergyWindow:
               for sp in self.checkpoints[0]["species"]]
         gx = [torch.zeros((sp["w"].shape[0], 2), dtype=torch.float64, device=dev)
               for sp in self.checkpoints[0]["species"]]
+        gw = [torch.zeros((sp["w"].shape[0],), dtype=torch.float64, device=dev)
+              for sp in self.checkpoints[0]["species"]]
         self.adjoint_iters = []
         starts = sorted(self.checkpoints)
         for k in range(len(starts) - 1, -1, -1):
@@ -134,12 +136,38 @@ class ModeEnergyWindow:
             for n in range(s1 - 1, s0 - 1, -1):
                 if n < s1 - 1:
                     self._load(pres[n - s0])
-                it, _, _ = self.sim.step_adjoint(gE, gB, gu, gx)
+                it, _, _ = self.sim.step_adjoint(gE, gB, gu, gx, gw)
                 self.adjoint_iters.append(it)
         torch.cuda.synchronize(dev)
         gid = [(gu[s].cpu().numpy(), gx[s].cpu().numpy()) for s in range(self.nsp)]
         self.grad_particles = gid
-        return {"E": gE.cpu().numpy(), "B": gB.cpu().numpy(), "particles": gid}
+        return {"E": gE.cpu().numpy(), "B": gB.cpu().numpy(), "particles": gid,
+                "w": [gw[s].cpu().numpy() for s in range(self.nsp)]}
+
+
+def parameter_gradient(grads, state_minus, state_plus, h, jump=1e-3):
+    """dL/dp for a parameter p of the initial state (e.g. the sheet
+    thickness of the loader), pathwise: the window's gradients (backward()'s
+    output, particles in the state's order) contracted with the central
+    difference (state_plus - state_minus)/(2h) of two states built at p - h
+    and p + h from the same random numbers, over E, B and every particle's
+    position, momentum and weight. A particle whose momentum changes by more
+    than `jump` between the two states took a different discrete choice in
+    the loader (a sheet membership or a flip) and is left out. Returns
+    (dL/dp, number of particles left out)."""
+    g = float(np.sum(grads["E"] * (np.asarray(state_plus["E"]) - np.asarray(state_minus["E"]))))
+    g += float(np.sum(grads["B"] * (np.asarray(state_plus["B"]) - np.asarray(state_minus["B"]))))
+    out = 0
+    for s, (sm, sp) in enumerate(zip(state_minus["species"], state_plus["species"])):
+        gu, gx = grads["particles"][s]
+        gw = grads["w"][s]
+        du = np.stack([np.asarray(sp[k]) - np.asarray(sm[k]) for k in ("ux", "uy", "uz")], axis=1)
+        dx = np.stack([np.asarray(sp[k]) - np.asarray(sm[k]) for k in ("x", "y")], axis=1)
+        dw = np.asarray(sp["w"]) - np.asarray(sm["w"])
+        keep = np.abs(du).max(axis=1) <= jump
+        out += int((~keep).sum())
+        g += float(np.sum(gu[keep] * du[keep]) + np.sum(gx[keep] * dx[keep]) + np.sum(gw[keep] * dw[keep]))
+    return g / (2.0 * h), out
 
 
 def _torch():

@@ -134,5 +134,5 @@ def test_batch_rejects_bad_arguments(librelsim):
     assert L.relsim_autotune(None, None) == librelsim.RELSIM_ERR_INVALID_ARG
     assert L.relsim_field_adjoint(None, None, None, None, None, None, None, None, None, None, 0) == \
         librelsim.RELSIM_ERR_INVALID_ARG
-    assert L.relsim_step_adjoint(None, None, None, None, None, None, None) == librelsim.RELSIM_ERR_INVALID_ARG
+    assert L.relsim_step_adjoint(None, None, None, None, None, None, None, None) == librelsim.RELSIM_ERR_INVALID_ARG
     assert L.relsim_relabel_particles(None, 0, None, 0) == librelsim.RELSIM_ERR_INVALID_ARG

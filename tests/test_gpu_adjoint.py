@@ -216,6 +216,7 @@ def test_deposit_adjoint_matches_oracle(rs, orc, prec):
         t = 1e-10 if prec == 64 else 2e-5   # FP32 form: FP32 replay, as for the push
         assert rel(g["u"], o["u"].T) < t
         assert rel(g["x"], np.stack([o["x"], o["y"]], axis=1)) < t
+        assert rel(g["w"], o["w"]) < t
         assert rel(g["B"], o["B"]) < t
     sim.close()
 
@@ -288,7 +289,8 @@ def test_step_adjoint_in_place_by_id_matches_oracle(rs, orc, prec):
     dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
     gE, gB = dev(gE1), dev(gB1)
     gu, gx = [dev(a) for a in gu_lab], [dev(a) for a in gx_lab]
-    it, rr, code = sim.step_adjoint(gE, gB, gu, gx)
+    gw = [torch.zeros(len(p[2]), dtype=torch.float64, device="cuda") for p in parts]
+    it, rr, code = sim.step_adjoint(gE, gB, gu, gx, gw)
     assert code == 0 and it > 0
     # the oracle in the GPU's order: particle k carries label ids[k]
     allp = [{"x": p[0][:, 0], "y": p[0][:, 1], "ux": p[1][:, 0], "uy": p[1][:, 1], "uz": p[1][:, 2], "w": p[2]}
@@ -304,10 +306,13 @@ def test_step_adjoint_in_place_by_id_matches_oracle(rs, orc, prec):
         ids = parts[s][3]
         want_u = np.empty_like(gu_lab[s])
         want_x = np.empty_like(gx_lab[s])
+        want_w = np.empty(len(ids))
         want_u[ids] = ou[sl]
         want_x[ids] = ox[sl]
+        want_w[ids] = o["w"][sl]
         assert rel(gu[s].cpu().numpy(), want_u) < t
         assert rel(gx[s].cpu().numpy(), want_x) < t
+        assert rel(gw[s].cpu().numpy(), want_w) < t
     assert rel(gE.cpu().numpy(), o["E"]) < t
     assert rel(gB.cpu().numpy(), o["B"]) < t
     sim.push()   # the context is left solved

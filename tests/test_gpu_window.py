@@ -81,6 +81,7 @@ def test_window_gradient_matches_oracle(rs, orc, prec):
     assert gu.shape[0] == 2 * n0
     assert rel(gu, go["u"].T) < t
     assert rel(gx, np.stack([go["x"], go["y"]], axis=1)) < t
+    assert rel(np.concatenate(g["w"]), go["w"]) < t
 
 
 def test_window_autograd_matches_central_differences(rs):
@@ -119,3 +120,29 @@ def test_window_autograd_matches_central_differences(rs):
     fd_e = (L(st["E"] + he * dE, 0.05) - L(st["E"] - he * dE, 0.05)) / (2 * he)
     assert abs(fd_e - float(np.sum(E0.grad.detach().numpy() * dE))) < 1e-6 * abs(fd_e)
     win.close()
+
+
+def test_window_gradient_in_sheet_thickness(rs):
+    """The gradient of the window loss in the sheet half-thickness delta (a
+    parameter of the loader: it sets the weights, the drift momenta of the
+    sheet members and the B_x profile), pathwise: the window's gradients in
+    the initial fields, momenta and weights (dL/dw summed over the steps)
+    contracted with the loader's central difference at delta -+ h (same
+    random numbers), against the central difference of the whole window
+    loss (FP64 form). h = 1e-6 changes no discrete choice of the loader on
+    this state (checked), so both sides see the same smooth map."""
+    from paper_2509_11100_gb300.window import parameter_gradient
+    h = 1e-6
+    def state(delta):
+        st = make_harris(HarrisConfig(nx=NX, ny=NY, ppc=4, dt=DT, pert=0.05, delta=delta))
+        return st
+    st0, stm, stp = state(1.0), state(1.0 - h), state(1.0 + h)
+    win = window(rs, 64)
+    win.forward(st0)
+    g = win.backward()
+    gd, out = parameter_gradient(g, stm, stp, h)
+    assert out == 0
+    fd = (win.forward(stp) - win.forward(stm)) / (2 * h)
+    win.close()
+    assert abs(gd - fd) < 1e-5 * abs(fd), (gd, fd)
+
