@@ -197,6 +197,35 @@ RELSIM_API int relsim_num_particles(relsim_ctx* ctx, int species, int64_t* n);
 RELSIM_API int relsim_get_particles(relsim_ctx* ctx, int species, double* x, double* u, double* w,
                          int32_t* id, int where);
 
+/* The particles of a species in the library's own form (the state it steps,
+   read out and loaded back bit for bit: a checkpoint, or a state that moves
+   between host and device every step at half the bytes of the FP64 record
+   in the FP32 form). The species is sorted by cell; cell c (index
+   (k*ny + j)*nx + i) holds particles start[c] .. start[c+1]-1. Per particle:
+   the offsets within its cell off[D*n] (component k of particle p at
+   off[k*n + p]: fx, fy and in 3D fz, each in [0, 1)), the momenta u[3n]
+   (component k at u[k*n + p]) and the weight w[n]. The element type of off,
+   u and w is the context's precision: float for precision 32, double for
+   64. start has ncell + 1 int32 entries; id[n] (optional) the carried ids.
+
+   relsim_get_particles_native copies the species out (each pointer may be
+   NULL to skip it). Errors: INVALID_ARG (species, id without tracking),
+   BAD_STATE (the species was never loaded), CUDA.
+
+   relsim_load_particles_native replaces the species by n particles in this
+   form (no conversion, no sort). It checks on the device: start[0] = 0,
+   start[ncell] = n and start never decreasing, every offset in [0, 1), u and
+   w finite, ids in [0, n); with ids tracked and id NULL the ids are
+   0..n-1. Errors: INVALID_ARG (species, n, NULL arrays with n > 0, a NULL
+   start table, id without tracking, a check above that fails), NONFINITE,
+   OOM, CUDA; after a failed check the species is empty. Resets the step
+   state like relsim_load_particles. */
+RELSIM_API int relsim_get_particles_native(relsim_ctx* ctx, int species, int32_t* start, void* off, void* u,
+                                           void* w, int32_t* id, int where);
+RELSIM_API int relsim_load_particles_native(relsim_ctx* ctx, int species, int64_t n, const int32_t* start,
+                                            const void* off, const void* u, const void* w, const int32_t* id,
+                                            int where);
+
 /* Start index of each cell's particles of a species in the current order:
    start[ncell+1], start[ncell] = n. Errors: INVALID_ARG, CUDA. */
 RELSIM_API int relsim_get_cell_start(relsim_ctx* ctx, int species, int64_t* start, int where);

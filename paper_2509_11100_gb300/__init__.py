@@ -31,7 +31,8 @@ __all__ = [
     "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
     "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
     "relsim_tuning", "relsim_push_adjoint", "relsim_deposit_adjoint", "relsim_step_adjoint",
-    "relsim_relabel_particles", "relsim_set_launch_shapes",
+    "relsim_relabel_particles", "relsim_set_launch_shapes", "relsim_get_particles_native",
+    "relsim_load_particles_native",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -137,6 +138,9 @@ _SIGS = {
     "relsim_step_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_double)]),
     "relsim_relabel_particles": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
+    "relsim_get_particles_native": (ctypes.c_int, [_CTX, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int]),
+    "relsim_load_particles_native": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P, _P,
+                                                    ctypes.c_int]),
 }
 
 PROFILE_SLOTS = ("deposit", "push", "sort_tables", "permute", "gmres_apply",
@@ -203,7 +207,8 @@ def _ptr(a, dtype=np.float64, writable=False):
         return None, RELSIM_HOST, None
     if _is_torch(a):
         import torch
-        want = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        want = {np.float64: torch.float64, np.float32: torch.float32, np.int64: torch.int64,
+                np.int32: torch.int32}[dtype]
         if a.dtype != want or not a.is_contiguous():
             raise TypeError(f"tensor must be contiguous {want}")
         return a.data_ptr(), (RELSIM_DEVICE if a.is_cuda else RELSIM_HOST), a
@@ -301,7 +306,8 @@ def relsim_set_fields(ctx, E=None, B=None):
 def _out(shape, dtype, device):
     if device:
         import torch
-        td = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        td = {np.float64: torch.float64, np.float32: torch.float32, np.int64: torch.int64,
+              np.int32: torch.int32}[dtype]
         return torch.empty(shape, dtype=td, device="cuda")
     return np.empty(shape, dtype=dtype)
 
@@ -333,6 +339,35 @@ def relsim_get_particles(ctx, species, ids=False, device=False, dim=2):
     pi = _ptr(i, np.int32, writable=True) if ids else (None, RELSIM_HOST, None)
     _check(ctx, lib().relsim_get_particles(ctx, species, px[0], pu[0], pw[0], pi[0], _where(px, pu, pw)))
     return (x, u, w, i) if ids else (x, u, w)
+
+
+def relsim_get_particles_native(ctx, species, ncell, precision=32, ids=False, device=False, dim=2):
+    """The species in the library's own form: (start[ncell + 1] int32,
+    off (dim, n), u (3, n), w (n,), [id (n,) int32]), the floating arrays in
+    the context's precision (float32 or float64)."""
+    n = relsim_num_particles(ctx, species)
+    ft = np.float32 if precision == 32 else np.float64
+    st = _out((ncell + 1,), np.int32, device)
+    off, u, w = _out((dim, n), ft, device), _out((3, n), ft, device), _out((n,), ft, device)
+    i = _out((n,), np.int32, device) if ids else None
+    ps = _ptr(st, np.int32, writable=True)
+    po, pu, pw = (_ptr(a, ft, writable=True) for a in (off, u, w))
+    pi = _ptr(i, np.int32, writable=True) if ids else (None, RELSIM_HOST, None)
+    _check(ctx, lib().relsim_get_particles_native(ctx, species, ps[0], po[0], pu[0], pw[0], pi[0],
+                                                  _where(ps, po, pu, pw)))
+    return (st, off, u, w, i) if ids else (st, off, u, w)
+
+
+def relsim_load_particles_native(ctx, species, start, off, u, w, ids=None, precision=32):
+    """Replace a species by particles in the library's own form (see
+    relsim_get_particles_native); no conversion and no sort."""
+    ft = np.float32 if precision == 32 else np.float64
+    n = int(w.shape[0])
+    ps = _ptr(start, np.int32)
+    po, pu, pw = _ptr(off, ft), _ptr(u, ft), _ptr(w, ft)
+    pi = _ptr(ids, np.int32) if ids is not None else (None, RELSIM_HOST, None)
+    return _check(ctx, lib().relsim_load_particles_native(ctx, species, n, ps[0], po[0], pu[0], pw[0], pi[0],
+                                                          _where(ps, po, pu, pw, pi)))
 
 
 def relsim_get_cell_start(ctx, species, ncell, device=False):
@@ -637,6 +672,14 @@ class Simulation:
 
     def cell_start(self, s, device=False):
         return relsim_get_cell_start(self.ctx, s, self.ncell, device)
+
+    def particles_native(self, s, ids=False, device=False):
+        """(start, off, u, w[, id]) in the library's own form."""
+        return relsim_get_particles_native(self.ctx, s, self.ncell, self.cfg.precision, ids, device,
+                                           self.cfg.dim)
+
+    def load_species_native(self, s, start, off, u, w, ids=None):
+        return relsim_load_particles_native(self.ctx, s, start, off, u, w, ids, self.cfg.precision)
 
     def build(self):
         return relsim_build_mass_matrix(self.ctx)

@@ -535,6 +535,88 @@ int get_particles_impl(relsim_ctx* c, int s, double* x, double* u, double* w, in
     return RELSIM_OK;
 }
 
+// the species in the library's own form (cell start table; per particle the
+// offsets within the cell, the momenta and the weight, one array per
+// component): plain copies, then one device check of the invariants the
+// kernels rely on. A failed check leaves the species empty.
+template <typename T>
+int load_native_impl(relsim_ctx* c, int s, int64_t n, const int32_t* start, const void* off, const void* u,
+                     const void* w, const int32_t* id, int where)
+{
+    Species& sp = c->sp[s];
+    TRY(ensure_species(c, s, n));
+    const int D = c->g.dim;
+    const int64_t nc1 = (int64_t)c->g.ncell + 1;
+    const cudaMemcpyKind kind = where == RELSIM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const size_t bytes = sizeof(T) * (size_t)n;
+    const int slot[3] = {0, 1, 6};   // fx, fy, fz
+    sp.n = n;
+    sp.cur = 0;
+    CK(cudaMemcpyAsync(sp.start, start, sizeof(int32_t) * (size_t)nc1, kind, c->st));
+    if (n > 0) {
+        const T* o = (const T*)off;
+        const T* uu = (const T*)u;
+        for (int k = 0; k < D; ++k) CK(cudaMemcpyAsync(sp.a[0][slot[k]], o + k * n, bytes, kind, c->st));
+        for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(sp.a[0][2 + k], uu + k * n, bytes, kind, c->st));
+        CK(cudaMemcpyAsync(sp.a[0][5], w, bytes, kind, c->st));
+        if (sp.id[0]) {
+            if (id) CK(cudaMemcpyAsync(sp.id[0], id, sizeof(int32_t) * (size_t)n, kind, c->st));
+            else CK(iota_ids(sp.id[0], n, c->st));
+        }
+    }
+    CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
+    PArrays<T> pa = arrays<T>(sp, 0);
+    if (!id) pa.id = nullptr;   // 0..n-1 need no check
+    PROF_BEGIN(RELSIM_PROF_LOAD);
+    CK(check_native<T>(sp.start, c->g.ncell, pa, D == 3 ? (const T*)sp.a[0][6] : nullptr, n, c->dflag, c->st));
+    PROF_END();
+    CK(cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const int f = *c->hflag;
+    if (f) {
+        sp.n = 0;
+        CK(cudaMemsetAsync(sp.start, 0, sizeof(int32_t) * (size_t)nc1, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (f & 1) return fail(c, RELSIM_ERR_NONFINITE, "non-finite momentum or weight");
+        if (f & 2) return fail(c, RELSIM_ERR_INVALID_ARG, "an offset outside [0, 1)");
+        if (f & 4) return fail(c, RELSIM_ERR_INVALID_ARG, "the cell start table does not run from 0 to n");
+        return fail(c, RELSIM_ERR_INVALID_ARG, "an id outside [0, n)");
+    }
+    // kinetic energy of the loaded species -> ledger slot K1
+    const int nb = 152 * 4;
+    TRY(ensure_partial(c, nb));
+    CK(cudaMemsetAsync(c->dled + kLedgerField + kLedgerSpecies * s, 0, sizeof(double) * kLedgerSpecies,
+                       c->st));
+    if (n > 0) {
+        CK(kinetic_energy<T>(arrays<T>(sp, 0), n, c->cfg.m[s], c->partial, nb, c->st));
+        CK(reduce_partials(c->partial, nb, 1, c->dled + kLedgerField + kLedgerSpecies * s + 4, c->st));
+    }
+    return RELSIM_OK;
+}
+
+template <typename T>
+int get_native_impl(relsim_ctx* c, int s, int32_t* start, void* off, void* u, void* w, int32_t* id, int where)
+{
+    Species& sp = c->sp[s];
+    const int64_t n = sp.n;
+    const int D = c->g.dim;
+    const cudaMemcpyKind kind = where == RELSIM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const size_t bytes = sizeof(T) * (size_t)n;
+    const int slot[3] = {0, 1, 6};
+    const int b = sp.cur;
+    if (start) CK(cudaMemcpyAsync(start, sp.start, sizeof(int32_t) * (size_t)(c->g.ncell + 1), kind, c->st));
+    if (n > 0) {
+        if (off)
+            for (int k = 0; k < D; ++k) CK(cudaMemcpyAsync((T*)off + k * n, sp.a[b][slot[k]], bytes, kind, c->st));
+        if (u)
+            for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync((T*)u + k * n, sp.a[b][2 + k], bytes, kind, c->st));
+        if (w) CK(cudaMemcpyAsync(w, sp.a[b][5], bytes, kind, c->st));
+        if (id) CK(cudaMemcpyAsync(id, sp.id[b], sizeof(int32_t) * (size_t)n, kind, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    return RELSIM_OK;
+}
+
 template <typename T>
 DepositSpecies<T> deposit_args(relsim_ctx* c);
 
@@ -1869,6 +1951,39 @@ int relsim_get_particles(relsim_ctx* c, int species, double* x, double* u, doubl
     if (id && !c->cfg.track_ids) return fail(c, RELSIM_ERR_INVALID_ARG, "ids are not tracked");
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     return DISPATCH(get_particles_impl, c, species, x, u, w, id, where);
+}
+
+int relsim_load_particles_native(relsim_ctx* c, int species, int64_t n, const int32_t* start, const void* off,
+                                 const void* u, const void* w, const int32_t* id, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    ++c->gen;
+    if (species < 0 || species >= c->cfg.nspecies)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
+    if (n < 0 || n > 2147483647LL) return fail(c, RELSIM_ERR_INVALID_ARG, "bad particle count %lld", (long long)n);
+    if (!start) return fail(c, RELSIM_ERR_INVALID_ARG, "null cell start table");
+    if (n > 0 && (!off || !u || !w)) return fail(c, RELSIM_ERR_INVALID_ARG, "null particle array");
+    if (id && !c->cfg.track_ids) return fail(c, RELSIM_ERR_INVALID_ARG, "ids are not tracked");
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    int r = DISPATCH(load_native_impl, c, species, n, start, off, u, w, id, where);
+    if (r == RELSIM_OK) {
+        c->state = kReady;
+        c->have_step = false;
+        c->step = 0;
+    }
+    return r;
+}
+
+int relsim_get_particles_native(relsim_ctx* c, int species, int32_t* start, void* off, void* u, void* w,
+                                int32_t* id, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (species < 0 || species >= c->cfg.nspecies)
+        return fail(c, RELSIM_ERR_INVALID_ARG, "species %d out of range", species);
+    if (id && !c->cfg.track_ids) return fail(c, RELSIM_ERR_INVALID_ARG, "ids are not tracked");
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    if (!c->sp[species].start) return fail(c, RELSIM_ERR_BAD_STATE, "species %d was never loaded", species);
+    return DISPATCH(get_native_impl, c, species, start, off, u, w, id, where);
 }
 
 namespace {

@@ -119,6 +119,16 @@ cudaError_t push_q(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t
                    int32_t* count, const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum, int nblocks,
                    cudaStream_t st);
 
+// ----- native.cu -----
+// bits of *bad (accumulated): 1 non-finite u or w, 2 an offset outside [0, 1),
+// 4 a start table that does not run from 0 to n without decreasing, 8 an id
+// outside [0, n) (p.id may be null; fz null in 2D)
+template <typename T>
+cudaError_t check_native(const int32_t* start, int ncell, PArrays<T> p, const T* fz, int64_t n, int* bad,
+                         cudaStream_t st);
+// id[i] = i
+cudaError_t iota_ids(int32_t* id, int64_t n, cudaStream_t st);
+
 // ----- adjoint.cu -----
 // lu[i] = gu[id[i]], lx[i] = gx[id[i]] (FP64, 3 and 2 interleaved components)
 cudaError_t gather_grad(const int32_t* id, const double* gu, const double* gx, double* lu, double* lx, int64_t n,
