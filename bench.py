@@ -719,6 +719,7 @@ def run_quad(args):
                          gmres_tol=WORKLOAD["gmres_tol"], gmres_restart=WORKLOAD["gmres_restart"])
     sim = rs.Simulation(cfg)
     sim.load_state(st)
+    tuning = sim.autotune() if not args.no_autotune else None
     for _ in range(args.warmup):
         sim.step(ledger=True)
     torch.cuda.synchronize()
@@ -750,7 +751,7 @@ def run_quad(args):
            "per_kernel": per_kernel, "gmres_iters_per_step": float(np.mean([l["gmres_iters"] for l in leds])),
            "ledger": {"residual_rel": abs(last["residual"]) / last["total"],
                       "mismatch_rel": abs(last["mismatch"]) / last["total"]},
-           "clocks": clk}
+           "autotune": tuning, "clocks": clk}
     print(json.dumps(out), flush=True)
 
 
@@ -825,6 +826,7 @@ def run_3d(args):
         return sim
 
     sim = sim_for(32)
+    tuning = sim.autotune() if not args.no_autotune else None
     for _ in range(args.warmup):
         sim.step(ledger=True)
     torch.cuda.synchronize()
@@ -908,7 +910,7 @@ def run_3d(args):
            "gpu_launches": launches, "gmres_iters_per_step": float(np.mean([l["gmres_iters"] for l in leds])),
            "ledger": {"residual_rel": abs(last["residual"]) / last["total"],
                       "mismatch_rel": abs(last["mismatch"]) / last["total"]},
-           "fp64_form": fp64, "cpu_baseline": cpu, "clocks": clk, "input_generation_s": t_gen}
+           "fp64_form": fp64, "cpu_baseline": cpu, "autotune": tuning, "clocks": clk, "input_generation_s": t_gen}
     print(json.dumps(out), flush=True)
 
 

@@ -162,8 +162,8 @@ RELSIM_API const char* relsim_last_error(const relsim_ctx* ctx);
    dj = -1..1 (outer) and di = -1..1 (inner), i.e. ncell x 126 values (the
    2D form: (0,0), (1,0), (-1,1), (0,1), (1,1), ncell x 45). The 3D form
    covers the base scheme; its push allows any move length and re-sorts by a
-   counting sort that does not keep the order within a cell. The adjoints and the autotuner cover the
-   2D form (INVALID_ARG in 3D).
+   counting sort that does not keep the order within a cell. The adjoints
+   cover the 2D form (INVALID_ARG in 3D).
 
    Load (replace) the particles of one species: n particles, positions x[2n]
    (x[3n] in 3D),
@@ -488,9 +488,11 @@ RELSIM_API void relsim_batch_destroy(relsim_batch* b);
 /* ---- launch-shape autotuner ----
    Times candidate launch shapes of the two heaviest particle kernels on the
    loaded state and keeps the fastest for this context: the deposit's block
-   count (it strides over row units of 32 cells: 1, 2, 3, 4 blocks per SM)
-   and the push's grid (at most 4, 8, 16, 32 blocks of four unit warps per
-   SM), and a compile-time shape of the implicit operator: its tile height
+   count (it strides over row units of 32 cells: 1, 2, 3, 4 blocks per SM in
+   the 2D form with linear shapes; 2, 4, 8, 16 in 3D and with quadratic
+   shapes) and the push's grid (at most 4, 8, 16, 32 blocks per SM), and, in
+   the 2D form with linear shapes, a compile-time shape of the implicit
+   operator (the 3D and quadratic operators have one): its tile height
    (32-node-wide tiles of 8 or 4 rows in the FP32 form, 4 or 2 in FP64; an
    Arnoldi-mode application with 8 dot products on the deposited mass
    matrix). Each candidate runs once untimed and three times timed (CUDA events;
@@ -515,7 +517,9 @@ RELSIM_API int relsim_autotune(relsim_ctx* ctx, relsim_tuning* out);
 
 /* Set the launch shapes the autotuner chooses (e.g. one instance's tuning
    applied to others of the same size): the deposit's block count and the
-   push's grid cap (0: the defaults, two and 16 blocks per SM) and the 2D
+   push's grid cap (0: the defaults; the deposit two blocks per SM in the 2D
+   form with linear shapes, at most 8 in 3D and with quadratic shapes; the
+   push at most 16) and the 2D
    operator's tile rows (0 or the form's default: 8 in FP32, 4 in FP64; or
    the alternative: 4 in FP32, 2 in FP64). Results do not depend on the
    shapes beyond rounding. Errors: INVALID_ARG. */

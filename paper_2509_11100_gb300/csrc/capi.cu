@@ -629,12 +629,12 @@ int build_impl(relsim_ctx* c)
     CK(cudaMemsetAsync(c->J, 0, c->esz * 3 * (size_t)nc, c->st));
     const DepositSpecies<T> ds = deposit_args<T>(c);
     if (c->g.shape == 2) {
-        CK(deposit_q<T>(ds, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->st));
+        CK(deposit_q<T>(ds, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->st, c->dep_blocks));
     } else if (c->g.dim == 3) {
         FzArrays<T> fz;
         memset(&fz, 0, sizeof(fz));
         for (int s = 0; s < c->cfg.nspecies; ++s) fz.fz[s] = (const T*)c->sp[s].a[c->sp[s].cur][6];
-        CK(deposit3<T>(ds, fz, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->st));
+        CK(deposit3<T>(ds, fz, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->st, c->dep_blocks));
     } else {
         CK(deposit<T>(ds, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J, c->g,
                       c->dpush, c->st, c->dep_blocks));
@@ -675,6 +675,13 @@ DepositSpecies<T> deposit_args(relsim_ctx* c)
 // next step recomputes (M, Jhat, the other particle buffer, the run tables,
 // the partial sums); the push trials take E^n as their field (any finite
 // field times the same work).
+// the push's grid for a cap on its block count (0: the form's default)
+int push_blocks_cap(const relsim_ctx* c, int cap)
+{
+    return c->g.dim == 3 ? push_blocks3(c->g, cap)
+                         : (c->g.shape == 2 ? push_blocks_q(c->g, cap) : push_grid_blocks(c->g, c->prec, cap));
+}
+
 template <typename T>
 int autotune_impl(relsim_ctx* c, relsim_tuning* out)
 {
@@ -682,9 +689,13 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int ncand = 4;
-    const int dep_c[ncand] = {nsm, 2 * nsm, 3 * nsm, 4 * nsm};
-    const int push_c[ncand] = {4 * nsm, 8 * nsm, 16 * nsm, 32 * nsm};
-    TRY(ensure_partial(c, (int64_t)push_grid_blocks(c->g, c->prec, push_c[ncand - 1]) * (kLedgerSpecies - 1)));
+    const bool lin2 = c->g.dim == 2 && c->g.shape != 2;   // the 2D kernels with linear shapes
+    int dep_c[ncand], push_c[ncand];
+    for (int k = 0; k < ncand; ++k) {
+        dep_c[k] = lin2 ? (k + 1) * nsm : (2 << k) * nsm;   // 1..4 blocks per SM; 3D, quadratic: 2, 4, 8, 16
+        push_c[k] = (4 << k) * nsm;                         // 4, 8, 16, 32 per SM
+    }
+    TRY(ensure_partial(c, (int64_t)push_blocks_cap(c, push_c[ncand - 1]) * (kLedgerSpecies - 1)));
     relsim_tuning t;
     memset(&t, 0, sizeof(t));
     t.ncand = ncand;
@@ -700,6 +711,7 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
         if (c->sp[s].n > c->sp[big].n) big = s;
     Species& sp = c->sp[big];
     const SpeciesConst sc{c->cfg.q[big], c->cfg.m[big]};
+    if (!lin2 && sp.n > 0) TRY(ensure_radix(c, sp.n));
     auto timed = [&](auto launch, float* best) -> int {
         *best = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
@@ -717,20 +729,43 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
         t.deposit_blocks[k] = dep_c[k];
         r = timed(
             [&]() -> int {
-                CK(deposit<T>(ds, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J,
-                              c->g, c->dpush, c->st, dep_c[k]));
+                const T* B = (const T*)c->B[c->bcur];
+                if (c->g.shape == 2) {
+                    CK(deposit_q<T>(ds, B, (T*)c->M, (T*)c->J, c->g, c->st, dep_c[k]));
+                } else if (c->g.dim == 3) {
+                    FzArrays<T> fz;
+                    memset(&fz, 0, sizeof(fz));
+                    for (int s = 0; s < c->cfg.nspecies; ++s) fz.fz[s] = (const T*)c->sp[s].a[c->sp[s].cur][6];
+                    CK(deposit3<T>(ds, fz, B, (T*)c->M, (T*)c->J, c->g, c->st, dep_c[k]));
+                } else {
+                    CK(deposit<T>(ds, B, c->En ? (const T*)c->E : nullptr, (T*)c->M, (T*)c->J, c->g, c->dpush,
+                                  c->st, dep_c[k]));
+                }
                 return RELSIM_OK;
             },
             &t.deposit_ms[k]);
     }
     for (int k = 0; k < ncand && r == RELSIM_OK && sp.n > 0; ++k) {
-        const int nbp = push_grid_blocks(c->g, c->prec, push_c[k]);
+        const int nbp = push_blocks_cap(c, push_c[k]);
         t.push_blocks[k] = nbp;
+        // the push reads the current buffer and writes the other one (and,
+        // in 3D and with quadratic shapes, each particle's new cell and slot)
         r = timed(
             [&]() -> int {
-                CK(push_sort<T>(arrays<T>(sp, sp.cur), arrays<T>(sp, 1 - sp.cur), sp.start, c->n9, c->off9,
-                                (const T*)c->E, (const T*)c->B[c->bcur], c->En ? (const T*)c->E : nullptr, c->g,
-                                sc, c->partial, nbp, c->st));
+                PArrays<T> src = arrays<T>(sp, sp.cur), dst = arrays<T>(sp, 1 - sp.cur);
+                const T* E = (const T*)c->E;
+                const T* B = (const T*)c->B[c->bcur];
+                if (!lin2)
+                    CK(cudaMemsetAsync(c->count_new, 0, sizeof(int32_t) * (size_t)(c->g.ncell + 1), c->st));
+                if (c->g.dim == 3)
+                    CK(push3<T>(src, (T*)sp.a[sp.cur][6], dst, (T*)sp.a[1 - sp.cur][6], sp.start, c->rk[0], c->rv[0],
+                                c->count_new, E, B, c->g, sc, c->partial, nbp, c->st));
+                else if (c->g.shape == 2)
+                    CK(push_q<T>(src, dst, sp.start, c->rk[0], c->rv[0], c->count_new, E, B, c->g, sc, c->partial,
+                                 nbp, c->st));
+                else
+                    CK(push_sort<T>(src, dst, sp.start, c->n9, c->off9, E, B, c->En ? E : nullptr, c->g, sc,
+                                    c->partial, nbp, c->st));
                 return RELSIM_OK;
             },
             &t.push_ms[k]);
@@ -739,8 +774,8 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
     // an Arnoldi-mode application with 8 dot products on the deposited M
     const int alt = c->prec == 32 ? 4 : 2;
     const int rows_c[2] = {0, alt};
-    t.op_nrows = 2;
-    if (r == RELSIM_OK) {
+    t.op_nrows = lin2 ? 2 : 0;   // the 3D and quadratic operators have one tile shape
+    if (r == RELSIM_OK && lin2) {
         const int jdots = 8;
         int64_t most = 0;
         for (int k = 0; k < 2; ++k) {
@@ -770,7 +805,7 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r != RELSIM_OK) return r;
-    t.op_choice = t.op_ms[1] < t.op_ms[0] ? 1 : 0;
+    t.op_choice = lin2 && t.op_ms[1] < t.op_ms[0] ? 1 : 0;
     c->g.op_y = rows_c[t.op_choice];
     int bd = 0, bp = 0;
     for (int k = 1; k < ncand; ++k) {
@@ -979,11 +1014,7 @@ int solve_impl(relsim_ctx* c, int* iters_out, double* relres_out)
 }
 
 // the push's grid (its ledger partials are sized by it)
-int push_blocks_for(const relsim_ctx* c)
-{
-    return c->g.dim == 3 ? push_blocks3(c->g)
-                         : (c->g.shape == 2 ? push_blocks_q(c->g) : push_grid_blocks(c->g, c->prec, c->push_cap));
-}
+int push_blocks_for(const relsim_ctx* c) { return push_blocks_cap(c, c->push_cap); }
 
 // steps that can run as a captured graph: the one-cell-move sort of the 2D
 // linear form, and the counting-sort paths of the 3D form and the quadratic
@@ -2093,8 +2124,6 @@ int relsim_set_launch_shapes(relsim_ctx* c, int deposit_blocks, int push_blocks,
 int relsim_autotune(relsim_ctx* c, relsim_tuning* out)
 {
     if (!c) return RELSIM_ERR_INVALID_ARG;
-    if (c->g.dim == 3 || c->g.shape == 2)
-        return fail(c, RELSIM_ERR_INVALID_ARG, "the autotuner covers the 2D kernels with linear shapes");
     if (c->state != kReady) return fail(c, RELSIM_ERR_BAD_STATE, "autotune needs a loaded state before a build");
     return DISPATCH(autotune_impl, c, out);
 }

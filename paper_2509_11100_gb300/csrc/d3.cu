@@ -955,11 +955,12 @@ cudaError_t export_particles3(PArrays<T> p, const T* fz, const int32_t* start, G
 
 template <typename T>
 cudaError_t deposit3(const DepositSpecies<T>& ds, const FzArrays<T>& fz, const T* B, T* M, T* J, GridP g,
-                     cudaStream_t st)
+                     cudaStream_t st, int blocks)
 {
     const int64_t units = (int64_t)((g.nx + 31) / 32) * g.ny * g.nz;
     count_launches(1);
-    k_deposit3<T><<<grid3(units, DepCfg3<T>::warps, 152 * 8), 32 * DepCfg3<T>::warps, 0, st>>>(ds, fz, B, M, J, g);
+    k_deposit3<T><<<grid3(units, DepCfg3<T>::warps, blocks > 0 ? blocks : 152 * 8), 32 * DepCfg3<T>::warps, 0, st>>>(
+        ds, fz, B, M, J, g);
     return cudaGetLastError();
 }
 
@@ -996,10 +997,10 @@ cudaError_t field_update3(const double* x, const T* M, const T* J, T* Eth, T* E,
     return cudaGetLastError();
 }
 
-int push_blocks3(GridP g)
+int push_blocks3(GridP g, int cap)
 {
     const int64_t units = (int64_t)((g.nx + 31) / 32) * g.ny * g.nz;
-    return (int)grid3(units, kPushWarps3, 152 * 16);
+    return (int)grid3(units, kPushWarps3, cap > 0 ? cap : 152 * 16);
 }
 
 template <typename T>
@@ -1032,7 +1033,7 @@ cudaError_t place3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const i
     template cudaError_t export_particles3<T>(PArrays<T>, const T*, const int32_t*, GridP, double*, double*,       \
                                               double*, int32_t*, cudaStream_t);                                    \
     template cudaError_t deposit3<T>(const DepositSpecies<T>&, const FzArrays<T>&, const T*, T*, T*, GridP,        \
-                                     cudaStream_t);                                                                \
+                                     cudaStream_t, int);                                                                \
     template cudaError_t rhs3<T>(const T*, const T*, const T*, double*, GridP, cudaStream_t);                      \
     template cudaError_t field_update3<T>(const double*, const T*, const T*, T*, T*, const T*, T*, GridP, double*, \
                                           int, cudaStream_t);                                                      \

@@ -81,7 +81,7 @@ cudaError_t export_particles3(PArrays<T> p, const T* fz, const int32_t* start, G
                               double* w, int32_t* id, cudaStream_t st);
 template <typename T>
 cudaError_t deposit3(const DepositSpecies<T>& ds, const FzArrays<T>& fz, const T* B, T* M, T* J, GridP g,
-                     cudaStream_t st);
+                     cudaStream_t st, int blocks = 0);   // blocks 0: at most 8 per SM
 int op_blocks3(GridP g);
 template <typename T, int MODE, bool TR>
 cudaError_t launch_op3(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
@@ -92,7 +92,7 @@ cudaError_t rhs3(const T* E, const T* B, const T* J, double* b, GridP g, cudaStr
 template <typename T>
 cudaError_t field_update3(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0, T* B1, GridP g,
                           double* partial, int nblocks, cudaStream_t st);
-int push_blocks3(GridP g);
+int push_blocks3(GridP g, int cap = 0);   // cap 0: 16 blocks per SM
 // rank/count null: keys only; else rank[p] = slot among the new cell's particles (count zeroed first)
 template <typename T>
 cudaError_t push3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const int32_t* start, int32_t* key,
@@ -104,7 +104,8 @@ cudaError_t place3(PArrays<T> src, const T* sfz, PArrays<T> dst, T* dfz, const i
 
 // ----- quad.cu (2D, quadratic shapes) -----
 template <typename T>
-cudaError_t deposit_q(const DepositSpecies<T>& ds, const T* B, T* M, T* J, GridP g, cudaStream_t st);
+cudaError_t deposit_q(const DepositSpecies<T>& ds, const T* B, T* M, T* J, GridP g, cudaStream_t st,
+                      int blocks = 0);   // blocks 0: at most 8 per SM
 int op_blocks_q(GridP g);
 template <typename T, int MODE, bool TR>
 cudaError_t launch_op_q(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
@@ -113,7 +114,7 @@ cudaError_t launch_op_q(const T* M, const double* in, double sc, const double* b
 template <typename T>
 cudaError_t field_update_q(const double* x, const T* M, const T* J, T* Eth, T* E, const T* B0, T* B1, GridP g,
                            double* partial, int nblocks, cudaStream_t st);
-int push_blocks_q(GridP g);
+int push_blocks_q(GridP g, int cap = 0);   // cap 0: 16 blocks per SM
 template <typename T>
 cudaError_t push_q(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, int32_t* rank,
                    int32_t* count, const T* Eth, const T* B, GridP g, SpeciesConst sc, double* lsum, int nblocks,

@@ -812,11 +812,12 @@ k_push_q(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int3
 }  // namespace
 
 template <typename T>
-cudaError_t deposit_q(const DepositSpecies<T>& ds, const T* B, T* M, T* J, GridP g, cudaStream_t st)
+cudaError_t deposit_q(const DepositSpecies<T>& ds, const T* B, T* M, T* J, GridP g, cudaStream_t st, int blocks)
 {
     const int units = ((g.nx + kQX - 1) / kQX) * g.ny;
     count_launches(1);
-    k_deposit_q<T><<<gridq(units, DepCfgQ<T>::warps, 152 * 8), 32 * DepCfgQ<T>::warps, 0, st>>>(ds, B, M, J, g);
+    k_deposit_q<T><<<gridq(units, DepCfgQ<T>::warps, blocks > 0 ? blocks : 152 * 8), 32 * DepCfgQ<T>::warps, 0, st>>>(
+        ds, B, M, J, g);
     return cudaGetLastError();
 }
 
@@ -842,10 +843,10 @@ cudaError_t field_update_q(const double* x, const T* M, const T* J, T* Eth, T* E
     return cudaGetLastError();
 }
 
-int push_blocks_q(GridP g)
+int push_blocks_q(GridP g, int cap)
 {
     const int64_t units = (int64_t)((g.nx + kQX - 1) / kQX) * g.ny;
-    return (int)gridq(units, kPushWarpsQ, 152 * 16);
+    return (int)gridq(units, kPushWarpsQ, cap > 0 ? cap : 152 * 16);
 }
 
 template <typename T>
@@ -865,7 +866,7 @@ cudaError_t push_q(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t
                                                   double*, const double*, int64_t, int, GridP, double*,           \
                                                   cudaStream_t, const GmDyn*);
 #define RELSIM_Q_INSTANTIATE(T)                                                                                   \
-    template cudaError_t deposit_q<T>(const DepositSpecies<T>&, const T*, T*, T*, GridP, cudaStream_t);           \
+    template cudaError_t deposit_q<T>(const DepositSpecies<T>&, const T*, T*, T*, GridP, cudaStream_t, int);           \
     template cudaError_t field_update_q<T>(const double*, const T*, const T*, T*, T*, const T*, T*, GridP,        \
                                            double*, int, cudaStream_t);                                           \
     template cudaError_t push_q<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, int32_t*, int32_t*,         \

@@ -189,9 +189,6 @@ def test_3d_config_checks_and_2d_only_calls(rs):
         rs.Simulation(rs.make_config(8, 8, nz=4, gamma_pred=True))
     st = random_state3(5, 4, 3, [60, 60], seed=34)
     sim = sim3(rs, 32, st, nx=5, ny=4, nz=3)
-    with pytest.raises(rs.RelsimError) as e:
-        sim.autotune()
-    assert e.value.code == rs.RELSIM_ERR_INVALID_ARG
     sim.build()
     sim.solve()
     with pytest.raises(rs.RelsimError):

@@ -166,8 +166,6 @@ def test_quadratic_config_checks(rs):
         rs.Simulation(rs.make_config(8, 8, shape=2, gamma_pred=True))
     st = random_state(8, 8, [100, 100], seed=54)
     sim = simq(rs, 32, st, 8, 8)
-    with pytest.raises(rs.RelsimError):
-        sim.autotune()
     sim.build()
     sim.solve()
     with pytest.raises(rs.RelsimError):
