@@ -136,3 +136,7 @@ def test_batch_rejects_bad_arguments(librelsim):
         librelsim.RELSIM_ERR_INVALID_ARG
     assert L.relsim_step_adjoint(None, None, None, None, None, None, None, None) == librelsim.RELSIM_ERR_INVALID_ARG
     assert L.relsim_relabel_particles(None, 0, None, 0) == librelsim.RELSIM_ERR_INVALID_ARG
+    assert L.relsim_get_particles_native(None, 0, None, None, None, None, None, 0) == \
+        librelsim.RELSIM_ERR_INVALID_ARG
+    assert L.relsim_load_particles_native(None, 0, 0, None, None, None, None, None, 0) == \
+        librelsim.RELSIM_ERR_INVALID_ARG
