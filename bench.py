@@ -215,7 +215,8 @@ def run_ours(args):
     ncell = hc.nx * hc.ny
 
     cfg = rs.make_config(hc.nx, hc.ny, dt=hc.dt, theta_implicit=hc.theta, precision=32,
-                         gmres_tol=WORKLOAD["gmres_tol"], gmres_restart=WORKLOAD["gmres_restart"])
+                         gmres_tol=WORKLOAD["gmres_tol"], gmres_restart=WORKLOAD["gmres_restart"],
+                         gamma_pred=args.gamma_pred)
     sim = rs.Simulation(cfg)
     sim.load_state(state)
     tuning = sim.autotune() if not args.no_autotune else None
@@ -284,7 +285,8 @@ def run_ours(args):
     achieved = ab / (launch_ms / 1e3) / 1e9 if ab else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                "traffic": traffic_record(dom), "algorithmic_bytes_per_launch": ab,
+                # the committed counters are of the gamma(u^n) kernels
+                "traffic": None if args.gamma_pred else traffic_record(dom), "algorithmic_bytes_per_launch": ab,
                 "launch_ms": launch_ms}
     # the mover + mass-matrix kernels together (deposit, push passes, sort tables)
     mover = ("deposit", "push", "sort_tables", "permute")
@@ -299,7 +301,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(args.workload == "small"),
-                       parallelism=f"replicas{world}" if world > 1 else "single"),
+                       parallelism=f"replicas{world}" if world > 1 else "single",
+                       gamma_bar="gamma(u^n + beta E^n(x)) (predicted)" if args.gamma_pred else "gamma(u^n)"),
         "roofline": roofline,
         "mover_mass_matrix": {"value": N / (mover_ms / 1e3), "unit": UNIT, "ms_per_step": mover_ms,
                               "achieved_gbs": mover_gbs, "frac": mover_gbs / peak,
@@ -458,7 +461,7 @@ def run_ours(args):
     # the FP64 form on the same GPU and workload
     if not args.no_fp64:
         cfg64 = rs.make_config(hc.nx, hc.ny, dt=hc.dt, theta_implicit=hc.theta, precision=64,
-                               gmres_tol=1e-10, gmres_restart=WORKLOAD["gmres_restart"])
+                               gmres_tol=1e-10, gmres_restart=WORKLOAD["gmres_restart"], gamma_pred=args.gamma_pred)
         s64 = rs.Simulation(cfg64)
         s64.load_state(state)
         s64.step()
@@ -942,6 +945,80 @@ def scan_single_reference(rs, torch, sizes=((1024, 512), (768, 384), (128, 64)),
     return res
 
 
+def run_long(args):
+    """The headline sheet (1024x512, 67.1M particles, FP32 form) run for
+    --long-steps steps (2000 by default) as one job: the throughput over the
+    whole run, the total energy's drift against the first step's (the
+    ledger's total every step), the m = 1 B_y mode energy every 10 steps
+    with its best growth rate over 40 samples (the tearing diagnostic), and
+    the spectrum of gamma - 1 (256 log bins over [1e-2, 1e4]) at the start
+    and at the end."""
+    import numpy as np
+    import torch
+    import paper_2509_11100_gb300 as rs
+    from relsim_inputs import make_harris
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    hc = harris_config(seed=rank)
+    state = make_harris(hc)
+    N = sum(len(sp["w"]) for sp in state["species"])
+    cfg = rs.make_config(hc.nx, hc.ny, dt=hc.dt, theta_implicit=hc.theta, precision=32,
+                         gmres_tol=WORKLOAD["gmres_tol"], gmres_restart=WORKLOAD["gmres_restart"],
+                         gamma_pred=args.gamma_pred)
+    sim = rs.Simulation(cfg)
+    sim.load_state(state)
+    del state
+    tuning = sim.autotune() if not args.no_autotune else None
+    edges = np.geomspace(1e-2, 1e4, 257)
+
+    def spectrum():
+        cnt = sum(sim.spectrum(s, edges, 0)[1] for s in range(2))
+        inner = np.asarray(cnt[1:-1], dtype=np.float64)
+        mid = np.sqrt(edges[:-1] * edges[1:])
+        return {"peak_bin_gamma_minus_1": float(mid[int(np.argmax(inner))]),
+                "above_10": float(inner[mid > 10].sum() / max(inner.sum(), 1)),
+                "above_100": float(inner[mid > 100].sum() / max(inner.sum(), 1)),
+                "max_bin_gamma_minus_1": float(mid[np.nonzero(inner)[0].max()]) if inner.any() else None}
+
+    spec0 = spectrum()
+    nsteps = args.long_steps
+    totals, modes, iters, fails = [], [], [], 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for n in range(nsteps):
+        led, code = sim.step(ledger=True)
+        fails += code != 0
+        totals.append(led["total"])
+        iters.append(led["gmres_iters"])
+        if n % 10 == 0:
+            modes.append(float(sim.field_modes(1, 2)[1]))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    rate, first = rs.relsim_growth_fit(np.asarray(modes), 10 * hc.dt, 40)
+    tot = np.asarray(totals)
+    out = {"metric": METRIC, "value": N * nsteps / wall, "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+           "warmup": 0, "ms_per_step": 1e3 * wall / nsteps, "higher_is_better": True, "dtype": "f32",
+           "data": "synthetic",
+           "config": dict(WORKLOAD, run="one long run, host wall clock over all steps including the per-step "
+                                        "ledger read back and the mode diagnostic every 10 steps",
+                          gamma_bar="gamma(u^n + beta E^n(x)) (predicted)" if args.gamma_pred
+                          else "gamma(u^n)"),
+           "energy": {"max_rel_drift": float(np.abs(tot - tot[0]).max() / abs(tot[0])),
+                      "final_rel_drift": float((tot[-1] - tot[0]) / abs(tot[0])),
+                      "drift_at": {str(k): float((tot[k - 1] - tot[0]) / abs(tot[0]))
+                                   for k in (200, 500, 1000, 2000) if k <= len(tot)}},
+           "gmres_iters_per_step": float(np.mean(iters)), "steps_not_converged": int(fails),
+           "tearing_m1": {"energy_first": modes[0], "energy_last": modes[-1], "growth_rate": rate,
+                          "fit_first_step": 10 * first, "samples": len(modes)},
+           "spectrum_start": spec0, "spectrum_end": spectrum(), "autotune": tuning, "clocks": clk}
+    sim.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -953,11 +1030,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (no autotuner pass after the load)")
-    ap.add_argument("--workload", choices=["c1", "small", "scan", "window", "c2", "c2small", "c1q", "c1qsmall"], default="c1",
+    ap.add_argument("--long-steps", type=int, default=2000, help="long: the number of steps of the run")
+    ap.add_argument("--gamma-pred", action="store_true",
+                    help="the predicted Lorentz factor gamma(u^n + beta E^n(x)) in alpha, Jhat, M and the push "
+                         "(headline and long workloads)")
+    ap.add_argument("--workload", choices=["c1", "small", "scan", "window", "c2", "c2small", "c1q", "c1qsmall",
+                                           "long"], default="c1",
                     help="small: 512x256 cells for profiler captures; scan: the 48-instance batched "
                          "tearing scan (run with --steps 400 for its full length); window: the "
                          "differentiable 20-step window on 256x128; c2: the 3D sheet on 256x128x128 "
-                         "(c2small: 64x32x32); c1q: the headline sheet with quadratic shapes")
+                         "(c2small: 64x32x32); c1q: the headline sheet with quadratic shapes; long: the "
+                         "headline sheet for --long-steps steps (energy drift, tearing mode, spectrum)")
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the scan's batch runner")
     ap.add_argument("--scan-reference", action="store_true",
                     help="scan: also time single 1024x512, 768x384 and 128x64 instances with its parameters")
@@ -974,6 +1057,8 @@ def main():
         run_3d(args)
     elif args.workload in ("c1q", "c1qsmall"):
         run_quad(args)
+    elif args.workload == "long":
+        run_long(args)
     else:
         run_ours(args)
 
