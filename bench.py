@@ -551,6 +551,9 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# Fourier modes of B_y recorded per instance and step in the scan (m = 0 ..
+# SCAN_MODES-1): the per-mode growth rates and the dispersion fit
+SCAN_MODES = 17
 SCAN = {
     "workload": "batched linear tearing scan: 48 independent 2D pair-plasma double Harris sheets, "
                 "L_x from {128,192,256,384,512,768} cells (L_y = L_x/2), delta from {0.5,1,2} d_e, "
@@ -633,7 +636,7 @@ def run_scan(args):
     for st in streams:
         st.wait_event(ev0)
     t1 = time.perf_counter()
-    modes, status, iters = batch.run(args.steps, component=1, nmodes=2)
+    modes, status, iters = batch.run(args.steps, component=1, nmodes=SCAN_MODES)
     wall = time.perf_counter() - t1
     for st in streams:
         e = torch.cuda.Event()
@@ -654,19 +657,36 @@ def run_scan(args):
         sim.close()
 
     # per instance: the m = 1 B_y mode's energy growth rate over its best
-    # 40-step window (the field amplitude grows at half of it)
+    # 40-step window (the field amplitude grows at half of it), and the
+    # per-mode amplitude rates of modes 1 .. SCAN_MODES-1 over one fixed
+    # window (steps steps/10 .. 6 steps/10) with their dispersion fit
+    # (Sec. 3.1, Fig. 1 b, d: rate = A x b (1 - x^2 b^2), x = k delta)
     rows = []
     win = min(40, args.steps)
+    dfirst, dwin = args.steps // 10, args.steps // 2
     for k, i in enumerate(mine):
         hc = insts[i]
         try:
             rate, first = rs.relsim_growth_fit(modes[k, :, 1], hc.dt, win) if win >= 2 else (None, None)
         except rs.RelsimError:
             rate, first = None, None
+        disp = None
+        if dwin >= 2:
+            try:
+                rates, A, b = rs.relsim_dispersion_fit(modes[k], hc.dt, dfirst, dwin, hc.nx * hc.dx, hc.delta)
+                x = 2 * np.pi * np.arange(SCAN_MODES) * hc.delta / (hc.nx * hc.dx)
+                fin = np.isfinite(rates)
+                disp = {"window_steps": [dfirst + 1, dfirst + dwin], "ka": [round(float(v), 5) for v in x[1:]],
+                        "amplitude_rates": [None if not np.isfinite(v) else float(v) for v in rates[1:]],
+                        "fastest_ka": float(x[fin][np.argmax(rates[fin])]) if fin.any() else None,
+                        "fit_A": A, "fit_b": b, "fit_peak_ka": 1.0 / (np.sqrt(3.0) * b),
+                        "fit_zero_ka": 1.0 / b}
+            except rs.RelsimError:
+                disp = None
         rows.append({"index": i, "nx": hc.nx, "ny": hc.ny, "delta": hc.delta, "sigma": hc.sigma,
                      "particles": sizes[i], "status": int(status[k]),
                      "gmres_iters_mean": float(np.mean(iters[k])) if args.steps else None,
-                     "m1_energy_growth_rate": rate, "fit_window_first_step": first})
+                     "m1_energy_growth_rate": rate, "fit_window_first_step": first, "dispersion": disp})
     # algorithmic bytes of the particle passes and mass-matrix flush per step
     esz = 4
     mover = 0

@@ -455,6 +455,28 @@ RELSIM_API int relsim_field_modes(relsim_ctx* ctx, int component, int nmodes, do
    INVALID_ARG (bad sizes, NULL, dt <= 0, or no admissible run). */
 RELSIM_API int relsim_growth_fit(const double* s, int n, double dt, int window, double* rate, int* first);
 
+/* Per-mode growth rates and the tearing dispersion fit (host code, no
+   context). Sec. 3.1 measures the growth of each Fourier mode of B_y as a
+   best fit over the linear phase and compares the rates with the
+   dispersion f(k) = ka (1 - k^2 a^2) of Sec. 2, whose peak lies at
+   ka = 1/sqrt(3) and whose unstable range ends at ka = 1 (Fig. 1 b, d).
+   modes: nsamples x nmodes energies, row-major by sample (the layout
+   relsim_batch_run writes for one instance), sampled every dt. For mode m
+   = 1 .. nmodes-1, rates[m] = half the least-squares slope of log
+   modes[k][m] against k dt over samples first .. first+window-1 (the
+   field amplitude's growth rate), or NaN when a sample there is not
+   positive and finite; rates[0] (the mean field) is NaN. Mode m has
+   x_m = k_m a = 2 pi m a / Lx. The fit: rate(x) = A x b (1 - x^2 b^2) by
+   least squares over the modes with finite rates, A closed-form for each
+   b, b minimising the residual over [0.2, 4] (a grid of step 1e-3, then a
+   golden-section search of the best grid cell to 1e-12); *A and *b receive
+   the fit, the fitted curve peaks at x = 1/(sqrt(3) b) and changes sign at
+   x = 1/b. Errors: INVALID_ARG (NULL pointers, nsamples < 2, nmodes < 3,
+   window < 2, first out of range, dt, Lx or a not positive and finite, or
+   fewer than two finite rates). */
+RELSIM_API int relsim_dispersion_fit(const double* modes, int nsamples, int nmodes, double dt, int first,
+                                     int window, double Lx, double a, double* rates, double* A, double* b);
+
 /* ---- batched independent instances (the paper has no counterpart: a
    parameter scan of independent tearing runs, e.g. over L_x, the sheet
    half-thickness and sigma, each instance a context of its own) ----

@@ -19,7 +19,8 @@ __all__ = ["OracleConfig", "Ledger", "load", "deposit", "apply_A", "apply_M", "c
            "stable_sort", "step", "gather_E", "gather_B", "alpha", "node_weights",
            "to_full_offsets", "make_config", "spectrum", "field_modes", "growth_fit", "field_adjoint",
            "push_adjoint", "deposit_adjoint", "step_adjoint",
-           "mode_energy", "window_gradient"]
+           "mode_energy", "window_gradient", "mode_growth_rates", "dispersion_fit",
+           "tearing_dispersion"]
 
 
 class OracleConfig(ctypes.Structure):
@@ -350,6 +351,56 @@ def growth_fit(s, dt, window):
     if best is None:
         raise ValueError("no admissible window")
     return best
+
+
+def mode_growth_rates(modes, dt, first, window):
+    """Amplitude growth rate of every Fourier mode over one fixed window
+    (Sec. 3.1: each mode's growth is a best fit over the linear phase).
+
+    modes is (nsamples, nmodes) mode energies sampled every dt; for mode m
+    the rate is half the least-squares slope (numpy polyfit) of log energy
+    against time over samples first .. first+window-1 (the amplitude grows
+    at half the energy's rate); NaN for mode 0 and for modes with a
+    non-positive or non-finite sample in the window."""
+    e = np.asarray(modes, dtype=np.float64)
+    t = np.arange(window) * dt
+    out = np.full(e.shape[1], np.nan)
+    for m in range(1, e.shape[1]):
+        seg = e[first:first + window, m]
+        if seg.size == window and np.all(np.isfinite(seg)) and np.all(seg > 0):
+            out[m] = 0.5 * np.polyfit(t, np.log(seg), 1)[0]
+    return out
+
+
+def dispersion_fit(x, rates):
+    """Least-squares fit of the tearing dispersion of Sec. 2, f(k) = ka
+    (1 - k^2 a^2), with a free scale and a free width: rate = A x b (1 -
+    x^2 b^2) in x = ka. For each b, A is the closed-form linear least
+    squares; b is the minimiser of the residual over a dense grid on
+    [0.2, 4] (step 1e-5). Non-finite rates are left out. Returns (A, b):
+    the fitted curve peaks at x = 1/(sqrt(3) b) and vanishes at x = 1/b."""
+    x = np.asarray(x, dtype=np.float64)
+    r = np.asarray(rates, dtype=np.float64)
+    keep = np.isfinite(r)
+    x, r = x[keep], r[keep]
+    if x.size < 2:
+        raise ValueError("fewer than two finite rates")
+    b = np.linspace(0.2, 4.0, 380001)
+    xb = np.outer(b, x)
+    g = xb * (1.0 - xb * xb)
+    A = (g @ r) / np.einsum("ij,ij->i", g, g)
+    res = ((A[:, None] * g - r[None, :]) ** 2).sum(axis=1)
+    i = int(np.argmin(res))
+    return float(A[i]), float(b[i])
+
+
+def tearing_dispersion(modes, dt, first, window, Lx, a):
+    """Per-mode rates over the window and their dispersion fit, with mode m
+    at x = 2 pi m a / Lx: returns (rates, A, b)."""
+    rates = mode_growth_rates(modes, dt, first, window)
+    x = 2.0 * np.pi * np.arange(rates.size) * a / Lx
+    A, b = dispersion_fit(x[1:], rates[1:])
+    return rates, A, b
 
 
 def field_adjoint(c, M, Etheta, gE1, gB1, gEt=None):

@@ -28,7 +28,7 @@ __all__ = [
     "relsim_profile_enable", "relsim_profile_read", "relsim_kernel_launches", "PROFILE_SLOTS",
     "relsim_kinetic_energy_noalloc", "relsim_energy_spectrum", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
-    "relsim_field_modes", "relsim_growth_fit", "relsim_batch_create", "relsim_batch_run",
+    "relsim_field_modes", "relsim_growth_fit", "relsim_dispersion_fit", "relsim_batch_create", "relsim_batch_run",
     "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
     "relsim_tuning", "relsim_push_adjoint", "relsim_deposit_adjoint", "relsim_step_adjoint",
     "relsim_relabel_particles", "relsim_set_launch_shapes", "relsim_get_particles_native",
@@ -126,6 +126,8 @@ _SIGS = {
                                               ctypes.c_int]),
     "relsim_field_modes": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int]),
     "relsim_growth_fit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P]),
+    "relsim_dispersion_fit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "relsim_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "relsim_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "relsim_batch_destroy": (None, [_P]),
@@ -441,6 +443,24 @@ def relsim_field_modes(ctx, component, nmodes, device=False):
     po = _ptr(out, writable=True)
     _check(ctx, lib().relsim_field_modes(ctx, component, nmodes, po[0], po[1]))
     return out
+
+
+def relsim_dispersion_fit(modes, dt, first, window, Lx, a):
+    """(rates, A, b): per-mode amplitude growth rates of an (nsamples, nmodes)
+    array of mode energies over samples first .. first+window-1 (rates[0] and
+    modes without a positive window are NaN), and the fit of
+    A x b (1 - x^2 b^2), x = 2 pi m a / Lx, to them."""
+    e = np.ascontiguousarray(modes, dtype=np.float64)
+    if e.ndim != 2:
+        raise ValueError("modes must be (nsamples, nmodes)")
+    rates = np.empty(e.shape[1])
+    A = ctypes.c_double()
+    b = ctypes.c_double()
+    code = lib().relsim_dispersion_fit(e.ctypes.data, e.shape[0], e.shape[1], float(dt), int(first), int(window),
+                                       float(Lx), float(a), rates.ctypes.data, ctypes.byref(A), ctypes.byref(b))
+    if code != RELSIM_OK:
+        raise RelsimError(code, "dispersion fit: bad arguments or fewer than two growing modes")
+    return rates, A.value, b.value
 
 
 def relsim_growth_fit(s, dt, window):

@@ -70,6 +70,98 @@ int relsim_growth_fit(const double* s, int n, double dt, int window, double* rat
     return RELSIM_OK;
 }
 
+// residual of the dispersion fit for a given b, with A in closed form
+static double dispersion_residual(const double* x, const double* r, int n, double b, double* Aout)
+{
+    double gg = 0.0, gr = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double xb = x[i] * b;
+        const double g = xb * (1.0 - xb * xb);
+        gg += g * g;
+        gr += g * r[i];
+    }
+    const double A = gg > 0.0 ? gr / gg : 0.0;
+    double res = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double xb = x[i] * b;
+        const double d = A * xb * (1.0 - xb * xb) - r[i];
+        res += d * d;
+    }
+    if (Aout) *Aout = A;
+    return res;
+}
+
+int relsim_dispersion_fit(const double* modes, int nsamples, int nmodes, double dt, int first, int window,
+                          double Lx, double a, double* rates, double* A, double* b)
+{
+    if (!modes || !rates || !A || !b || nsamples < 2 || nmodes < 3 || window < 2 || first < 0 ||
+        first > nsamples - window || !(dt > 0.0) || !std::isfinite(dt) || !(Lx > 0.0) || !std::isfinite(Lx) ||
+        !(a > 0.0) || !std::isfinite(a))
+        return RELSIM_ERR_INVALID_ARG;
+    // per mode: least-squares slope of log energy against time, centred
+    // abscissae k - (window-1)/2; half of it is the amplitude's rate
+    const double kc = 0.5 * (double)(window - 1);
+    double sxx = 0.0;
+    for (int k = 0; k < window; ++k) sxx += ((double)k - kc) * ((double)k - kc);
+    std::vector<double> xs, rs;
+    rates[0] = std::nan("");
+    for (int m = 1; m < nmodes; ++m) {
+        double sxy = 0.0;
+        bool ok = true;
+        for (int k = 0; k < window && ok; ++k) {
+            const double v = modes[(size_t)(first + k) * (size_t)nmodes + (size_t)m];
+            if (!(v > 0.0) || !std::isfinite(v)) ok = false;
+            else sxy += ((double)k - kc) * std::log(v);
+        }
+        rates[m] = ok ? 0.5 * sxy / sxx / dt : std::nan("");
+        if (ok) {
+            xs.push_back(2.0 * M_PI * (double)m * a / Lx);
+            rs.push_back(rates[m]);
+        }
+    }
+    const int n = (int)xs.size();
+    if (n < 2) return RELSIM_ERR_INVALID_ARG;
+    // b on a grid of step 1e-3 over [0.2, 4], then golden section in the
+    // cells either side of the best grid point
+    const double lo = 0.2, step = 1e-3;
+    const int ng = 3801;
+    int bi = 0;
+    double best = 0.0;
+    for (int i = 0; i < ng; ++i) {
+        const double r = dispersion_residual(xs.data(), rs.data(), n, lo + step * i, nullptr);
+        if (i == 0 || r < best) {
+            best = r;
+            bi = i;
+        }
+    }
+    double u = lo + step * (bi > 0 ? bi - 1 : 0), v = lo + step * (bi < ng - 1 ? bi + 1 : ng - 1);
+    const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+    double p = v - gr * (v - u), q = u + gr * (v - u);
+    double fp = dispersion_residual(xs.data(), rs.data(), n, p, nullptr);
+    double fq = dispersion_residual(xs.data(), rs.data(), n, q, nullptr);
+    for (int it = 0; it < 200 && v - u > 1e-12; ++it) {
+        if (fp <= fq) {
+            v = q; q = p; fq = fp;
+            p = v - gr * (v - u);
+            fp = dispersion_residual(xs.data(), rs.data(), n, p, nullptr);
+        } else {
+            u = p; p = q; fp = fq;
+            q = u + gr * (v - u);
+            fq = dispersion_residual(xs.data(), rs.data(), n, q, nullptr);
+        }
+    }
+    double bb = 0.5 * (u + v);
+    double Af = 0.0;
+    const double rb = dispersion_residual(xs.data(), rs.data(), n, bb, &Af);
+    if (best < rb) {   // the grid point itself was better (flat residual)
+        bb = lo + step * bi;
+        dispersion_residual(xs.data(), rs.data(), n, bb, &Af);
+    }
+    *A = Af;
+    *b = bb;
+    return RELSIM_OK;
+}
+
 int relsim_batch_create(relsim_ctx* const* ctxs, int count, int nworkers, relsim_batch** out)
 {
     if (!out) return RELSIM_ERR_INVALID_ARG;

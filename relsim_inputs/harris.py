@@ -32,8 +32,8 @@ design notes of this repository):
   Sobol's method when hot) and the boost uses Zenitani's flipping method
   (Zenitani 2015, "Loading relativistic Maxwell distributions in particle
   simulations"), all written here from the mathematics.
-* The initial perturbation is dB_y = pert * B0 * cos(2 pi x / L_x) at cell
-  centres (divergence free, uniform in y).
+* The initial perturbation is dB_y = pert * B0 * cos(2 pi m x / L_x) at cell
+  centres (divergence free, uniform in y), m = pert_mode (1 by default).
 """
 from __future__ import annotations
 
@@ -65,6 +65,7 @@ class HarrisConfig:
     delta: float = 1.0       # sheet half-thickness a, in d_0e
     sigma: float = 10.0      # B0^2 / (n_b m c^2): background magnetization
     pert: float = 0.01       # dB_y / B0, single cosine mode in x
+    pert_mode: int = 1       # its mode number m: k_x = 2 pi m / L_x
     dt: float = 0.5          # time step, in 1/omega_pe0
     theta: float = 0.5       # implicitness parameter of the field solve
     seed: int = 0
@@ -240,7 +241,7 @@ def make_harris(cfg: HarrisConfig, dtype=np.float64) -> dict:
     xc = (np.arange(nx) + 0.5) * cfg.dx
     yc = (np.arange(ny) + 0.5) * cfg.dy
     Bx = d["B0"] * (np.tanh((yc - 0.25 * Ly) / a) - np.tanh((yc - 0.75 * Ly) / a) - 1.0)
-    By = cfg.pert * d["B0"] * np.cos(2.0 * math.pi * xc / Lx)
+    By = cfg.pert * d["B0"] * np.cos(2.0 * math.pi * cfg.pert_mode * xc / Lx)
     B = np.zeros((3, ny, nx))
     B[0] = Bx[:, None]
     B[1] = By[None, :]

@@ -94,6 +94,41 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
         rs.lib()
 
 
+def test_dispersion_fit_host_code_matches_oracle(librelsim):
+    # relsim_dispersion_fit is host code: it runs without a GPU. Noisy mode
+    # energies of a tearing-like dispersion and one mode without a positive
+    # window, against the oracle's per-mode fit and its dense-grid fit of b
+    import oracle
+    rng = np.random.default_rng(11)
+    dt, n, nm, Lx, a = 0.5, 90, 9, 32.0, 1.0
+    t = np.arange(n) * dt
+    x = 2 * np.pi * np.arange(nm) * a / Lx
+    g = 0.16 * x * 0.93 * (1 - (x * 0.93) ** 2)
+    e = np.exp(2.0 * g[None, :] * t[:, None] + 0.05 * rng.normal(size=(n, nm))) * 1e-3
+    e[30, 5] = -1.0
+    for first, window in ((20, 60), (0, 90), (10, 2)):
+        rates, A, b = librelsim.relsim_dispersion_fit(e, dt, first, window, Lx, a)
+        orates, oA, ob = oracle.tearing_dispersion(e, dt, first, window, Lx, a)
+        assert np.array_equal(np.isnan(rates), np.isnan(orates))
+        ok = ~np.isnan(orates)
+        assert np.allclose(rates[ok], orates[ok], rtol=1e-10, atol=1e-13)
+        assert abs(b - ob) < 2e-5 * ob and abs(A - oA) < 1e-4 * abs(oA), (A, b, oA, ob)
+    L = librelsim.lib()
+    r = np.zeros(nm)
+    A, b = ctypes.c_double(), ctypes.c_double()
+    D = e.ctypes.data
+    for args in [(None, n, nm, dt, 0, 10, Lx, a), (D, 1, nm, dt, 0, 10, Lx, a), (D, n, 2, dt, 0, 10, Lx, a),
+                 (D, n, nm, 0.0, 0, 10, Lx, a), (D, n, nm, dt, -1, 10, Lx, a), (D, n, nm, dt, 85, 10, Lx, a),
+                 (D, n, nm, dt, 0, 1, Lx, a), (D, n, nm, dt, 0, 10, 0.0, a), (D, n, nm, dt, 0, 10, Lx, float("nan"))]:
+        assert L.relsim_dispersion_fit(*args, r.ctypes.data, ctypes.byref(A), ctypes.byref(b)) == \
+            librelsim.RELSIM_ERR_INVALID_ARG, args
+    # fewer than two modes with a positive window
+    neg = -np.ones((n, nm))
+    neg[:, 1] = 1.0
+    assert L.relsim_dispersion_fit(neg.ctypes.data, n, nm, dt, 0, 10, Lx, a, r.ctypes.data, ctypes.byref(A),
+                                   ctypes.byref(b)) == librelsim.RELSIM_ERR_INVALID_ARG
+
+
 def test_growth_fit_host_code_matches_oracle(librelsim):
     # relsim_growth_fit is host code: it runs without a GPU
     import oracle

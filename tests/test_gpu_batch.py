@@ -166,7 +166,7 @@ def test_batched_tearing_growth_rates_match_oracle(rs, orc):
         sim.load_state(st)
         sims.append(sim)
     batch = rs.Batch(sims, nworkers=3)
-    modes, status, _ = batch.run(STEPS, component=1, nmodes=2)
+    modes, status, _ = batch.run(STEPS, component=1, nmodes=6)
     batch.close()
     for s in sims:
         s.close()
@@ -175,11 +175,12 @@ def test_batched_tearing_growth_rates_match_oracle(rs, orc):
         c = orc.make_config(hc.nx, hc.ny, dt=hc.dt, gmres_tol=1e-10)
         P = orc.Particles(st["species"])
         E, B = st["E"], st["B"]
-        W = []
+        Wall = []
         for _ in range(STEPS):
             E, B, _, _ = orc.step(c, P, E, B)
-            W.append(orc.field_modes(c, B, 1, 2)[1])
-        W = np.array(W)
+            Wall.append(orc.field_modes(c, B, 1, 6))
+        Wall = np.array(Wall)
+        W = Wall[:, 1]
         g_orc, _ = orc.growth_fit(W, hc.dt, WINDOW)
         g_gpu, _ = rs.relsim_growth_fit(modes[k, :, 1], hc.dt, WINDOW)
         dev = np.abs(modes[k, :, 1] / W - 1.0)
@@ -191,3 +192,12 @@ def test_batched_tearing_growth_rates_match_oracle(rs, orc):
         # the mode energy is a grid-collective quantity: the FP32 run tracks
         # the FP64 one closely until the orbits' divergence reaches it
         assert np.all(dev[:80] < 1e-3), (k, dev[:80].max())
+        # the per-mode fit (modes 1 .. 5, steps 10 .. 80) and its dispersion
+        # fit (Sec. 3.1, Fig. 1 b, d) on the GPU's mode energies against the
+        # oracle's fit of the oracle's energies
+        Lx = hc.nx * hc.dx
+        rates, A, b = rs.relsim_dispersion_fit(modes[k], hc.dt, 9, 71, Lx, hc.delta)
+        orates, oA, ob = orc.tearing_dispersion(Wall, hc.dt, 9, 71, Lx, hc.delta)
+        print(f"   per-mode rates GPU {np.round(rates[1:], 4)}, oracle {np.round(orates[1:], 4)}; "
+              f"fit peak ka GPU {1 / (np.sqrt(3) * b):.3f}, oracle {1 / (np.sqrt(3) * ob):.3f}")
+        assert np.all(np.abs(rates[1:] - orates[1:]) < 2e-3 + 0.02 * np.abs(orates[1:])), (k, rates, orates)

@@ -81,6 +81,9 @@ PY_MUTANTS = {
                                              'gu += cJ * WN[k] / gb * np.einsum("nij,jn->in", alpha, gj)'),
     "deposit_adjoint_one_sided_pairs": ("                gWn[l] += cM * WN[k] * s2 / gb\n", "\n"),
     "deposit_adjoint_w_drops_current": ("            gw0[a0:a1] += (q / dV) * WN[k] * sJ / gb\n", "\n"),
+    "mode_rates_energy_slope": ("out[m] = 0.5 * np.polyfit(t, np.log(seg), 1)[0]",
+                                "out[m] = np.polyfit(t, np.log(seg), 1)[0]"),
+    "dispersion_fit_drops_cubic": ("g = xb * (1.0 - xb * xb)\n    A = (g @ r)", "g = xb * (1.0 - xb)\n    A = (g @ r)"),
     "deposit_adjoint_w_wrong_pair_weight": ("gw0[a0:a1] += (q * beta / dV) * WN[k] * WN[l] * s2 / gb",
                                             "gw0[a0:a1] += (q * beta / dV) * WN[k] * WN[k] * s2 / gb"),
 }
@@ -117,11 +120,25 @@ MUTANTSQ = {
                                      "int64_t h = wrapq(j - dj, ny) * nx + wrapq(i + di, nx);"),
     "quad_mass_matrix_drops_gamma": ("double cM = w[p] * q * beta / (gbar * dV);", "double cM = w[p] * q * beta / dV;"),
 }
+# sign mistakes in the curls that keep curl_n = curl_c^T, so the discrete
+# energy identity still closes: caught by the linear tearing pin (the Harris
+# sheet's force balance and its tearing dispersion), each run against that
+# pin alone
+MUTANTS_TEARING = {
+    "tearing_curl_z_pair_sign": [("out[2 * nn + n00] = DX(Ey) - DY(Ex);", "out[2 * nn + n00] = DY(Ex) - DX(Ey);"),
+                                 ("out[2 * nn + c11] = DX(By) - DY(Bx);", "out[2 * nn + c11] = DY(Bx) - DX(By);")],
+    "tearing_curl_inplane_pair_sign": [("out[n00] = DY(Ez);", "out[n00] = -DY(Ez);"),
+                                       ("out[nn + n00] = -DX(Ez);", "out[nn + n00] = DX(Ez);"),
+                                       ("out[c11] = DY(Bz);", "out[c11] = -DY(Bz);"),
+                                       ("out[nn + c11] = -DX(Bz);", "out[nn + c11] = DX(Bz);")],
+}
 PINS = "test_oracle_pins.py"
 CASES = {**{k: ("relsim_oracle.c",) + v + (PINS,) for k, v in MUTANTS.items()},
-         **{k: ("__init__.py",) + v + (PINS,) for k, v in PY_MUTANTS.items()},
+         **{k: ("__init__.py",) + v + (PINS if not k.startswith(("mode_rates", "dispersion")) else
+                                        "test_oracle_tearing.py",) for k, v in PY_MUTANTS.items()},
          **{k: ("relsim_oracle3.c",) + v + ("test_oracle3_pins.py",) for k, v in MUTANTS3.items()},
-         **{k: ("relsim_oracle_q.c",) + v + ("test_oracle_q_pins.py",) for k, v in MUTANTSQ.items()}}
+         **{k: ("relsim_oracle_q.c",) + v + ("test_oracle_q_pins.py",) for k, v in MUTANTSQ.items()},
+         **{k: ("relsim_oracle.c", v, None, "test_oracle_tearing.py") for k, v in MUTANTS_TEARING.items()}}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -129,10 +146,14 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     fname, orig, repl, pins = CASES[name]
     src_dir = os.path.join(ROOT, "oracle")
     src = open(os.path.join(src_dir, fname)).read()
-    assert src.count(orig) == 1, f"mutation site for {name} is not unique"
+    # one replacement, or a list of (site, replacement) pairs planted together
+    edits = orig if repl is None else [(orig, repl)]
+    for o, rp in edits:
+        assert src.count(o) == 1, f"mutation site {o!r} for {name} is not unique"
+        src = src.replace(o, rp)
     dst = tmp_path / "oracle"
     shutil.copytree(src_dir, dst, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
-    (dst / fname).write_text(src.replace(orig, repl))
+    (dst / fname).write_text(src)
     env = dict(os.environ, RELSIM_ORACLE_MUTANT_DIR=str(tmp_path))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", pins)],
