@@ -441,16 +441,22 @@ def run_ours(args):
             sm.close()
         if dist is not None:
             te_serial = max_over_ranks(te_serial, dist)
-        out["e2e"] = {"value": world * N / te, "unit": UNIT, "ms_per_step": te * 1e3,
-                      "h2d_bytes_per_step": int(h2d_n), "d2h_bytes_per_step": int(d2h),
+        # the headline end-to-end figure goes through the boundary's FP64
+        # record (relsim_load_particles: absolute FP64 positions, converted
+        # and sorted inside the library); the library's own form follows
+        out["e2e"] = {"value": world * N / te_rec, "unit": UNIT, "ms_per_step": te_rec * 1e3,
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                       "steps": 2 * ke,
-                      "mode": "pipelined: two contexts, each step's inputs (particles in the library's own "
-                              "form: cell start table, FP32 offsets, momenta, weights; FP64 E and B) copied "
-                              "from pinned host memory while the other context steps, loaded by "
-                              "relsim_load_particles_native and relsim_set_fields",
-                      "fp64_record": {"value": world * N / te_rec, "ms_per_step": te_rec * 1e3,
-                                      "h2d_bytes_per_step": int(h2d), "steps": 2 * ke,
-                                      "mode": "the same pipeline with the FP64 record (relsim_load_particles)"},
+                      "mode": "pipelined: two contexts, each step's inputs (the FP64 particle record of the "
+                              "C ABI: absolute positions, momenta, weights; FP64 E and B) copied from pinned "
+                              "host memory while the other context steps, loaded by relsim_load_particles "
+                              "(conversion and cell sort on the device) and relsim_set_fields, then "
+                              "relsim_step and the ledger read back",
+                      "native_form": {"value": world * N / te, "ms_per_step": te * 1e3,
+                                      "h2d_bytes_per_step": int(h2d_n), "steps": 2 * ke,
+                                      "mode": "the same pipeline with the particles in the library's own form "
+                                              "(cell start table, FP32 offsets, momenta, weights: 24 bytes a "
+                                              "particle), loaded by relsim_load_particles_native"},
                       "serial": {"value": world * N / te_serial, "ms_per_step": te_serial * 1e3, "steps": ke,
                                  "h2d_bytes_per_step": int(h2d),
                                  "mode": "one context, FP64 record, copy and step in turn"}}
@@ -482,7 +488,7 @@ def run_ours(args):
 
     # the FP64 CPU oracle, as it stands, on a bounded sample of the workload
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = oracle_baseline(state, hc, steps=2)
+        out["cpu_baseline"] = oracle_baseline(state, hc, steps=2, gamma_pred=args.gamma_pred)
 
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -490,12 +496,13 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def oracle_baseline(state, hc, steps=2, every=8):
+def oracle_baseline(state, hc, steps=2, every=8, gamma_pred=0):
     """Time the FP64 CPU oracle on the workload's grid with every 8th particle
     of each cell (8 ppc per species, 8.4M particles, weights x8)."""
     import oracle
     sample = subsample(state, every)
-    c = oracle.make_config(hc.nx, hc.ny, dt=hc.dt, theta=hc.theta, gmres_tol=1e-12, gmres_restart=50)
+    c = oracle.make_config(hc.nx, hc.ny, dt=hc.dt, theta=hc.theta, gmres_tol=1e-12, gmres_restart=50,
+                           gamma_pred=gamma_pred)
     P = oracle.Particles(sample["species"])
     n = int(P.off[-1])
     E, B = sample["E"], sample["B"]
@@ -503,7 +510,7 @@ def oracle_baseline(state, hc, steps=2, every=8):
     for _ in range(steps):
         E, B, led, _ = oracle.step(c, P, E, B)
     dt = time.perf_counter() - t0
-    return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"same 1024x512 grid and fields, every {every}th particle of each cell "
                       f"({n} particles, weights x{every}), {steps} full oracle steps "
                       f"(deposit, GMRES tol 1e-12, push), single thread, FP64",
@@ -516,15 +523,16 @@ def run_reference(args):
         return
     from relsim_inputs import make_harris
     import oracle
-    # a bounded sample per step: the oracle's FP64 field solve alone takes
-    # seconds on the 1024x512 grid, so long runs time the same double Harris
-    # sheet on 512x256 cells
-    small = args.steps + args.warmup > 20
-    hc = harris_config(seed=0, small=small)
+    # the same 1024x512 grid and fields as the GPU arm, a bounded particle
+    # sample per step: every 8th particle of each cell (the cpu_baseline
+    # sample, ~3 s per oracle step on one core) while steps + warmup <= 40,
+    # a sparser sample beyond so the whole run stays within a few minutes
+    hc = harris_config(seed=0, small=args.workload == "small")
     state = make_harris(hc)
-    every = 8
+    every = 8 if args.steps + args.warmup <= 40 else 8 * ((args.steps + args.warmup + 39) // 40)
     sample = subsample(state, every)
-    c = oracle.make_config(hc.nx, hc.ny, dt=hc.dt, theta=hc.theta, gmres_tol=1e-12, gmres_restart=50)
+    c = oracle.make_config(hc.nx, hc.ny, dt=hc.dt, theta=hc.theta, gmres_tol=1e-12, gmres_restart=50,
+                           gamma_pred=args.gamma_pred)
     P = oracle.Particles(sample["species"])
     n = int(P.off[-1])
     E, B = sample["E"], sample["B"]
@@ -536,16 +544,21 @@ def run_reference(args):
     dt = (time.perf_counter() - t0) / args.steps
     value = n / dt
     grid = f"{hc.nx}x{hc.ny}"
-    sample_desc = (f"the double Harris sheet of the workload on a {grid} grid, every {every}th particle of "
+    sample_desc = (f"the double Harris sheet of the workload on its {grid} grid, every {every}th particle of "
                    f"each cell ({n} particles, weights x{every}); one full FP64 oracle step (deposit, GMRES "
                    f"tol 1e-12, push) per timed step, single thread")
+    cfg = dict(workload_config(args.workload == "small"), parallelism="host cores (oracle)",
+               form="FP64 CPU oracle (plain C, single thread): particles, fields, mass matrix and GMRES in FP64",
+               gamma_bar="gamma(u^n + beta E^n(x)) (predicted)" if args.gamma_pred else "gamma(u^n)")
+    cfg.pop("gmres_tol", None)
+    cfg["gmres"] = "tol 1e-12, restart 50"
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(workload_config(small), parallelism="host cores (oracle)"),
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample_desc, "value": value,
-                         "unit": UNIT},
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "host_cores": os.cpu_count(), "sample": sample_desc,
+                         "value": value, "unit": UNIT},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -1018,6 +1031,15 @@ def run_long(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    # the same steps without the ledger read and the mode diagnostic: the
+    # solver's cost alone at the end of the run
+    nq = min(100, nsteps)
+    torch.cuda.synchronize()
+    tq = time.perf_counter()
+    for _ in range(nq):
+        sim.step(ledger=False)
+    torch.cuda.synchronize()
+    wall_q = (time.perf_counter() - tq) / max(1, nq)
     rate, first = rs.relsim_growth_fit(np.asarray(modes), 10 * hc.dt, 40)
     tot = np.asarray(totals)
     out = {"metric": METRIC, "value": N * nsteps / wall, "unit": UNIT, "n_gpus": 1, "steps": nsteps,
@@ -1032,8 +1054,12 @@ def run_long(args):
                       "drift_at": {str(k): float((tot[k - 1] - tot[0]) / abs(tot[0]))
                                    for k in (200, 500, 1000, 2000) if k <= len(tot)}},
            "gmres_iters_per_step": float(np.mean(iters)), "steps_not_converged": int(fails),
+           "ms_per_step_no_ledger_at_end": {"ms_per_step": 1e3 * wall_q, "steps": nq,
+                                            "note": "steps after the run, without the per-step ledger read "
+                                                    "and the mode diagnostic"},
            "tearing_m1": {"energy_first": modes[0], "energy_last": modes[-1], "growth_rate": rate,
-                          "fit_first_step": 10 * first, "samples": len(modes)},
+                          "fit_first_step": 10 * first + 1,
+                          "sampled_after_steps": "1, 11, 21, ... (every 10 steps)", "samples": len(modes)},
            "spectrum_start": spec0, "spectrum_end": spectrum(), "autotune": tuning, "clocks": clk}
     sim.close()
     print(json.dumps(out), flush=True)

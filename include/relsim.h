@@ -117,6 +117,13 @@ typedef struct {
                               ((0,0), (1,0), (2,0), (di,1) and (di,2) for
                               di = -2..2: ncell x 117); the re-sort is a
                               counting sort, as in 3D                     */
+    int gmres_fp64;        /* the GMRES vectors (Krylov basis, iterate, right-
+                              hand side) of the FP32 form of the 2D scheme
+                              with linear shapes: 0 double-float pairs (two
+                              FP32 numbers per value, about 48 significant
+                              bits, arithmetic on the FP32 pipe: GB300's FP64
+                              pipe issues at about 1/64 of the FP32 rate);
+                              1 FP64. Other forms always use FP64 vectors  */
 } relsim_config;
 
 typedef struct {
@@ -141,13 +148,16 @@ typedef struct {
 } relsim_energy;
 
 /* Create a context for one simulation on the current CUDA device.
+   Paper: no counterpart (the context holds the state of the step of Sec. 2,
+   "Methods and Simulation Setup"; the configuration's fields are that
+   step's parameters).
    cfg: see relsim_config. cuda_stream: a cudaStream_t (or 0). On success
    *out receives the context. Errors: INVALID_ARG (bad config), CUDA, OOM.
    Allocates the grid arrays (fields, Jhat, M, GMRES basis) up front. */
 RELSIM_API int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out);
 
-/* Free every device buffer of the context and the context itself. Safe on
-   NULL. Synchronises the context's stream first. */
+/* Free every device buffer of the context and the context itself (no
+   counterpart in the paper). Safe on NULL. Synchronises the context's stream first. */
 RELSIM_API void relsim_destroy(relsim_ctx* ctx);
 
 /* Message of the last error on this context ("" if none). Owned by ctx. */
@@ -165,7 +175,10 @@ RELSIM_API const char* relsim_last_error(const relsim_ctx* ctx);
    counting sort that does not keep the order within a cell. The adjoints
    cover the 2D form (INVALID_ARG in 3D).
 
-   Load (replace) the particles of one species: n particles, positions x[2n]
+   Load (replace) the particles of one species (paper: Sec. 2, the
+   particles of the explicit pusher, each with a position, a momentum
+   u = gamma v and a weight; the loaded state is the initial Harris
+   equilibrium of Sec. 2, Eqs. 3-6, or any state): n particles, positions x[2n]
    (x[3n] in 3D),
    momenta u[3n], weights w[n], all FP64 (layout above). Positions outside
    the box are wrapped periodically. The library converts to its internal
@@ -177,19 +190,23 @@ RELSIM_API const char* relsim_last_error(const relsim_ctx* ctx);
 RELSIM_API int relsim_load_particles(relsim_ctx* ctx, int species, int64_t n, const double* x,
                           const double* u, const double* w, int where);
 
-/* Set E^n on nodes and B^n on cell centres (each 3*ncell FP64, layout above).
+/* Set E^n on nodes and B^n on cell centres (each 3*ncell FP64, layout above;
+   paper: the fields of Sec. 2, e.g. the Harris B_x profile of Eq. 4).
    Either pointer may be NULL to keep that field. Resets the step state.
    Errors: INVALID_ARG, NONFINITE, CUDA. */
 RELSIM_API int relsim_set_fields(relsim_ctx* ctx, const double* E, const double* B, int where);
 
-/* Copy the current E and B (after a solve: E^{n+1}, B^{n+1}) out as FP64.
+/* Copy the current E and B (after a solve: E^{n+1}, B^{n+1}) out as FP64
+   (state access; no counterpart in the paper).
    Either pointer may be NULL. Errors: INVALID_ARG, CUDA. */
 RELSIM_API int relsim_get_fields(relsim_ctx* ctx, double* E, double* B, int where);
 
-/* Number of particles of a species. */
+/* Number of particles of a species (state access; no counterpart in the
+   paper). */
 RELSIM_API int relsim_num_particles(relsim_ctx* ctx, int species, int64_t* n);
 
-/* Copy the particles of a species out, in the library's current order
+/* (State access; no counterpart in the paper.) Copy the particles of a
+   species out, in the library's current order
    (sorted by cell, stable), as FP64 x[2n] (x[3n] in 3D), u[3n], w[n] and, if ids are
    tracked, id[n] (each pointer may be NULL to skip it). Positions are
    absolute. Errors: INVALID_ARG (species out of range, id requested but not
@@ -197,7 +214,8 @@ RELSIM_API int relsim_num_particles(relsim_ctx* ctx, int species, int64_t* n);
 RELSIM_API int relsim_get_particles(relsim_ctx* ctx, int species, double* x, double* u, double* w,
                          int32_t* id, int where);
 
-/* The particles of a species in the library's own form (the state it steps,
+/* (State access; no counterpart in the paper.) The particles of a species
+   in the library's own form (the state it steps,
    read out and loaded back bit for bit: a checkpoint, or a state that moves
    between host and device every step at half the bytes of the FP64 record
    in the FP32 form). The species is sorted by cell; cell c (index
@@ -226,15 +244,21 @@ RELSIM_API int relsim_load_particles_native(relsim_ctx* ctx, int species, int64_
                                             const void* off, const void* u, const void* w, const int32_t* id,
                                             int where);
 
-/* Start index of each cell's particles of a species in the current order:
+/* (State access; no counterpart in the paper.) Start index of each cell's
+   particles of a species in the current order:
    start[ncell+1], start[ncell] = n. Errors: INVALID_ARG, CUDA. */
 RELSIM_API int relsim_get_cell_start(relsim_ctx* ctx, int species, int64_t* start, int where);
 
-/* Step part 1: gather B^n, form alpha per particle, deposit Jhat and M.
+/* Step part 1 (paper: Sec. 2, "Methods and Simulation Setup": the field
+   solver's mass-matrix formulation, with each particle's relativistic
+   rotation through its Lorentz factor; the equations are the header's
+   gbar, a, alpha, Jhat and M lines): gather B^n, form alpha per particle,
+   deposit Jhat and M.
    Allowed after load/set_fields or a push. Errors: BAD_STATE, CUDA. */
 RELSIM_API int relsim_build_mass_matrix(relsim_ctx* ctx);
 
-/* The deposited Jhat (3*ncell, component-major) and M, stored for the five
+/* (State access; no counterpart in the paper.) The deposited Jhat (3*ncell,
+   component-major) and M (Sec. 2's mass matrices), stored for the five
    neighbour offsets o in {(0,0), (1,0), (-1,1), (0,1), (1,1)} as
    M[(g*5 + k)*9 + r*3 + s] = block (r,s) of M_{g, g+o_k}; the other four
    offsets follow from M_{g+o,g} = M_{g,g+o}. In 3D the 14 stored offsets
@@ -243,12 +267,16 @@ RELSIM_API int relsim_build_mass_matrix(relsim_ctx* ctx);
    CUDA. */
 RELSIM_API int relsim_get_mass_matrix(relsim_ctx* ctx, double* M, double* J, int where);
 
-/* Replace the built Jhat and M by caller values (same layouts as
+/* (Test access; no counterpart in the paper.) Replace the built Jhat and M
+   by caller values (same layouts as
    relsim_get_mass_matrix), e.g. to drive the field solve on its own.
    Leaves the context in the built state. Errors: INVALID_ARG, CUDA. */
 RELSIM_API int relsim_set_mass_matrix(relsim_ctx* ctx, const double* M, const double* J, int where);
 
-/* Step part 2: GMRES solve for E^{n+theta}, then E^{n+1}, B^{n+1}.
+/* Step part 2 (paper: Sec. 2, "the method is implicit only in the field
+   solver"; the equations are the header's implicit-system, E^{n+1} and
+   B^{n+1} lines; the paper names no linear solver, GMRES is this library's
+   choice): GMRES solve for E^{n+theta}, then E^{n+1}, B^{n+1}.
    *iters (may be NULL) receives the Arnoldi steps, *rel_residual (may be
    NULL) the true relative residual. Synchronises the stream. The restart
    and Arnoldi decisions (Givens rotations, stop tests, the triangular
@@ -260,8 +288,9 @@ RELSIM_API int relsim_set_mass_matrix(relsim_ctx* ctx, const double* M, const do
    the best iterate), NONFINITE, CUDA. */
 RELSIM_API int relsim_field_solve(relsim_ctx* ctx, int* iters, double* rel_residual);
 
-/* Adjoint of the field part of the solved step, with the particles held
-   fixed (the implicit field solve of Sec. 2 is the step's only global
+/* Adjoint of the field part of the solved step (the paper computes no
+   gradients: this is the chain rule through its Sec. 2 step), with the
+   particles held fixed (the implicit field solve of Sec. 2 is the step's only global
    coupling; this is the piece a differentiable window chains with the
    adjoints of the push and the deposit). The forward map is linear in
    (E^n, B^n, Jhat):
@@ -287,7 +316,9 @@ RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const do
                                     double* gE0, double* gB0, double* gJ, double* gM, int* iters,
                                     double* rel_residual, int where);
 
-/* Adjoint of the deposit of one species (base scheme, gbar = gamma(u^n)):
+/* Adjoint of the deposit of one species (no counterpart in the paper: the
+   chain rule through Sec. 2's mass-matrix deposit; base scheme, gbar =
+   gamma(u^n)):
    the deposit Jhat_g += (w q/dV) W_g(x) alpha u/gbar and M_{gg'} += (w q
    beta/dV) W_g W_g' alpha/gbar, alpha from B^n(x). Given gJ = dL/dJhat
    (3*ncell) and gM = dL/dM for the stored blocks (ncell x 45, the layout of
@@ -309,8 +340,9 @@ RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const do
 RELSIM_API int relsim_deposit_adjoint(relsim_ctx* ctx, int species, const double* gJ, const double* gM,
                                       double* gu0, double* gx0, double* gB, double* gw0, int where);
 
-/* Adjoint of the push of one species with the fields held fixed (the
-   explicit pusher of Sec. 2; base scheme, gbar = gamma(u^n)). For the
+/* Adjoint of the push of one species with the fields held fixed (no
+   counterpart in the paper: the chain rule through the explicit pusher of
+   Sec. 2; base scheme, gbar = gamma(u^n)). For the
    solved step's push u^{n+1} = 2 alpha (u^n + beta E^{n+theta}(x)) - u^n,
    x^{n+3/2} = x + dt u^{n+1}/gamma^{n+1}, with alpha from B^n(x): given
    gu1 = dL/du^{n+1} (3n, interleaved (ux, uy, uz)) and gx1 =
@@ -327,7 +359,8 @@ RELSIM_API int relsim_deposit_adjoint(relsim_ctx* ctx, int species, const double
 RELSIM_API int relsim_push_adjoint(relsim_ctx* ctx, int species, const double* gu1, const double* gx1,
                                    double* gu0, double* gx0, double* gE, double* gB, int where);
 
-/* One whole step's adjoint on device memory, in place (base scheme, gbar =
+/* One whole step's adjoint on device memory, in place (no counterpart in
+   the paper, which computes no gradients; base scheme, gbar =
    gamma(u^n)): the chain rule through the step of Sec. 2 (deposit of the
    mass matrices and the predicted current, implicit field solve, push).
    From the state the context holds (loaded or pushed, not yet built) it
@@ -361,7 +394,8 @@ RELSIM_API int relsim_push_adjoint(relsim_ctx* ctx, int species, const double* g
 RELSIM_API int relsim_step_adjoint(relsim_ctx* ctx, double* gE, double* gB, double* const* gu, double* const* gx,
                                    double* const* gw, int* iters, double* rel_residual);
 
-/* Relabel a species' particles (track_ids): each particle carrying id j
+/* (State access; no counterpart in the paper.) Relabel a species'
+   particles (track_ids): each particle carrying id j
    gets ids[j] (n_s int32, host or device per where). Right after a load
    the ids are the input indices, so this gives the particle loaded from
    index i the label ids[i] (e.g. to keep the labels of a state saved with
@@ -371,26 +405,37 @@ RELSIM_API int relsim_step_adjoint(relsim_ctx* ctx, double* gE, double* gB, doub
    out of range), CUDA. */
 RELSIM_API int relsim_relabel_particles(relsim_ctx* ctx, int species, const int32_t* ids, int where);
 
-/* E^{n+theta} of the last solve (3*ncell FP64). Errors: BAD_STATE, CUDA. */
+/* E^{n+theta} of the last solve (Sec. 2's implicit field; 3*ncell FP64;
+   state access). Errors: BAD_STATE, CUDA. */
 RELSIM_API int relsim_get_E_theta(relsim_ctx* ctx, double* E, int where);
 
-/* Apply the implicit operator A = I + (theta dt)^2 curl_n curl_c + theta dt M
+/* (Test access.) Apply the implicit operator of Sec. 2's field solve,
+   A = I + (theta dt)^2 curl_n curl_c + theta dt M
    of the built mass matrix to v (3*ncell FP64, device or host per where),
    writing out (same layout). Errors: BAD_STATE, INVALID_ARG, CUDA. */
 RELSIM_API int relsim_apply_operator(relsim_ctx* ctx, const double* v, double* out, int where);
 
-/* Step part 3: push velocities and positions of every species with
+/* Step part 3 (paper: Sec. 2, "the particle pusher is explicit"; the
+   equations are the header's ubar, u^{n+1} and x^{n+3/2} lines; the re-sort
+   by cell is this library's layout, the paper is silent on it): push
+   velocities and positions of every species with
    E^{n+theta} and B^n, then sort each species by its new cells. Also
    accumulates the particle terms of the energy ledger. Allowed after a
    solve. Errors: BAD_STATE, CUDA. */
 RELSIM_API int relsim_push(relsim_ctx* ctx);
 
 /* Energy ledger of the current state and of the last step (FP64 struct,
-   caller-owned). Synchronises the stream. Errors: INVALID_ARG, NONFINITE
+   caller-owned). Paper: Sec. 2's energy claim (the mass-matrix field solve
+   conserves energy exactly, to machine precision, in the non-relativistic
+   limit, and reduces the relativistic energy error) and Table 1's column of
+   the energy error |E - E0|/E0: W_E + W_B + K is the total energy, and
+   `residual` closes the step's discrete identity while `mismatch` is the
+   scheme's own relativistic energy error. Synchronises the stream. Errors: INVALID_ARG, NONFINITE
    (NaN/Inf in an energy), CUDA. */
 RELSIM_API int relsim_energy_ledger(relsim_ctx* ctx, relsim_energy* out);
 
-/* One full step: build, solve, push; fills *ledger if it is non-NULL.
+/* One full step of Sec. 2's method (build, solve, push; the three calls
+   above); fills *ledger if it is non-NULL.
    Returns the first error of its parts (NOT_CONVERGED still completes the
    step). The first step after a load runs its parts from the host; later
    steps (when profiling is off and, in the 2D form with linear shapes, no
@@ -404,7 +449,8 @@ RELSIM_API int relsim_energy_ledger(relsim_ctx* ctx, relsim_energy* out);
    the whole step ran (the state is then invalid, as on the host route). */
 RELSIM_API int relsim_step(relsim_ctx* ctx, relsim_energy* ledger);
 
-/* Whether steps run as graphs: *graph_steps (may be NULL) = steps run as a
+/* (Runtime state; no counterpart in the paper.) Whether steps run as
+   graphs: *graph_steps (may be NULL) = steps run as a
    graph so far; *disabled = 1 if a capture failed and *why (owned by the
    context) says why. Errors: INVALID_ARG. */
 RELSIM_API int relsim_graph_info(const relsim_ctx* ctx, int64_t* graph_steps, int* disabled, const char** why);
@@ -445,6 +491,18 @@ RELSIM_API int relsim_energy_spectrum(relsim_ctx* ctx, int species, int variable
    order: repeated calls give identical results. Errors: INVALID_ARG, OOM,
    CUDA. */
 RELSIM_API int relsim_field_modes(relsim_ctx* ctx, int component, int nmodes, double* energy, int where);
+
+/* The energy of one Fourier mode m of a B component (as relsim_field_modes:
+   Sec. 3.1's tearing diagnostic, the loss of a differentiable window) and
+   its gradient in the field: *energy = W_m, and gB (3*ncell FP64, field
+   layout) = dW_m/dB: zero outside `component`, and there
+     dW_m/dB_c(i, j) = dV (c_m/nx) (Re F_{m,j} cos(2 pi m i/nx)
+                                     - Im F_{m,j} sin(2 pi m i/nx)),
+   F_{m,j} = sum_i B_c(i, j) exp(-2 pi sqrt(-1) m i/nx). 0 <= mode <= nx/2.
+   Both outputs host or device per where (device: enqueued, nothing waits;
+   host: synchronises). Errors: INVALID_ARG, OOM, CUDA. */
+RELSIM_API int relsim_field_mode_gradient(relsim_ctx* ctx, int component, int mode, double* energy, double* gB,
+                                          int where);
 
 /* Exponential growth rate of a positive series s[k] sampled at equal
    steps dt (host code, no context): the least-squares slope of log s[k]
@@ -601,7 +659,10 @@ RELSIM_API int64_t relsim_kernel_launches(void);
 
    The first call on a device looks up that array's device address
    (cudaGetSymbolAddress) with the device current; make that first call
-   before any stream capture. All calls share the array and each overwrites
+   before any stream capture. The address is kept for the life of the
+   process: after cudaDeviceReset on that device it no longer points at the
+   array, so do not call this entry point on a device that was reset. All
+   calls share the array and each overwrites
    the partials it uses, so nothing needs clearing, but calls that overlap
    on the GPU (on different streams, or from several threads) race on it and
    must be serialised by the caller. The result is written by the second of

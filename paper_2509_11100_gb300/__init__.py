@@ -28,7 +28,7 @@ __all__ = [
     "relsim_profile_enable", "relsim_profile_read", "relsim_kernel_launches", "PROFILE_SLOTS",
     "relsim_kinetic_energy_noalloc", "relsim_energy_spectrum", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
-    "relsim_field_modes", "relsim_growth_fit", "relsim_dispersion_fit", "relsim_batch_create", "relsim_batch_run",
+    "relsim_field_modes", "relsim_field_mode_gradient", "relsim_growth_fit", "relsim_dispersion_fit", "relsim_batch_create", "relsim_batch_run",
     "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
     "relsim_tuning", "relsim_push_adjoint", "relsim_deposit_adjoint", "relsim_step_adjoint",
     "relsim_relabel_particles", "relsim_set_launch_shapes", "relsim_get_particles_native",
@@ -74,7 +74,8 @@ class relsim_config(ctypes.Structure):
                 ("q", ctypes.c_double * 4), ("m", ctypes.c_double * 4),
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_maxit", ctypes.c_int), ("track_ids", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("gamma_pred", ctypes.c_int), ("shape", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("gamma_pred", ctypes.c_int), ("shape", ctypes.c_int),
+                ("gmres_fp64", ctypes.c_int)]
 
 
 class relsim_energy(ctypes.Structure):
@@ -125,6 +126,7 @@ _SIGS = {
     "relsim_energy_spectrum": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                               ctypes.c_int]),
     "relsim_field_modes": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int]),
+    "relsim_field_mode_gradient": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int]),
     "relsim_growth_fit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P]),
     "relsim_dispersion_fit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
@@ -253,10 +255,12 @@ def _stream(stream=None) -> int:
 
 def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta_implicit=0.5, precision=32,
                 q=(1.0, -1.0), m=(1.0, 1.0), gmres_tol=0.0, gmres_restart=0, gmres_maxit=0,
-                track_ids=False, gamma_pred=False, nz=None, dz=1.0, shape=1) -> relsim_config:
+                track_ids=False, gamma_pred=False, nz=None, dz=1.0, shape=1, gmres_fp64=False) -> relsim_config:
     """gamma_pred: the Lorentz factor in alpha and M is that of the
     predicted half-step momentum u^n + beta E^n(x) instead of u^n. nz: the
-    3D form on an nx x ny x nz grid (cell size dz along z)."""
+    3D form on an nx x ny x nz grid (cell size dz along z). gmres_fp64: FP64
+    GMRES vectors in the FP32 form too (default: double-float pairs in the
+    2D FP32 form with linear shapes)."""
     c = relsim_config()
     c.dim, c.nx, c.ny, c.nz = (2, nx, ny, 1) if nz is None else (3, nx, ny, nz)
     c.dx, c.dy, c.dz, c.dt, c.theta_implicit = dx, dy, (1.0 if nz is None else dz), dt, theta_implicit
@@ -268,6 +272,7 @@ def make_config(nx, ny, dx=1.0, dy=1.0, dt=0.5, theta_implicit=0.5, precision=32
     c.track_ids = 1 if track_ids else 0
     c.gamma_pred = 1 if gamma_pred else 0
     c.shape = int(shape)
+    c.gmres_fp64 = 1 if gmres_fp64 else 0
     return c
 
 
@@ -443,6 +448,16 @@ def relsim_field_modes(ctx, component, nmodes, device=False):
     po = _ptr(out, writable=True)
     _check(ctx, lib().relsim_field_modes(ctx, component, nmodes, po[0], po[1]))
     return out
+
+
+def relsim_field_mode_gradient(ctx, component, mode, ncell, device=False):
+    """(energy (1,), gB (3, ncell)): the energy of mode m of a B component
+    and its gradient in B, computed on the device."""
+    e = _out((1,), np.float64, device)
+    g = _out((3, ncell), np.float64, device)
+    pe, pg = _ptr(e, writable=True), _ptr(g, writable=True)
+    _check(ctx, lib().relsim_field_mode_gradient(ctx, component, mode, pe[0], pg[0], pe[1]))
+    return e, g
 
 
 def relsim_dispersion_fit(modes, dt, first, window, Lx, a):
@@ -764,6 +779,9 @@ class Simulation:
 
     def field_modes(self, component=1, nmodes=8, device=False):
         return relsim_field_modes(self.ctx, component, nmodes, device)
+
+    def field_mode_gradient(self, component=1, mode=1, device=False):
+        return relsim_field_mode_gradient(self.ctx, component, mode, self.ncell, device)
 
 
 class Batch:

@@ -870,10 +870,10 @@ int solve_prologue(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond outer
 {
     PROF_BEGIN(RELSIM_PROF_RHS);
     CK(rhs<T>((const T*)c->E, (const T*)c->B[c->bcur], (const T*)c->J, c->gb, c->g, s));
-    CK(fields_to_double<T>((const T*)c->E, c->gx, S.n, s));
+    CK(fields_to_vec<T>((const T*)c->E, c->gx, S.n, c->g.df, s));
     PROF_END();
     PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-    CK(gm_dots(c->V, S.ldv, 0, c->gb, S.n, c->partial, S.nb, s));
+    CK(gm_dots(c->V, S.ldv, 0, c->gb, S.n, c->partial, S.nb, s, c->g.df));
     CK(reduce_partials(c->partial, S.nb, 1, c->dsum, s));
     CK(gm_begin(c->gms, c->dsum, s));
     CK(gm_zero_x(c->gms, c->gx, S.n, s));
@@ -895,7 +895,7 @@ int arnoldi_body(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond inner, 
     PROF_END();
     PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
     CK(reduce_partials_dyn(c->partial, S.nbo, &c->gms->dyn, S.m + 2, s));
-    CK(gm_update_scale_dyn(&c->gms->dyn, c->V, S.ldv, S.n, s));
+    CK(gm_update_scale_dyn(&c->gms->dyn, c->V, S.ldv, S.n, s, c->g.df));
     CK(gm_tail(c->gms, S.p, S.q, inner, s));
     PROF_END();
     return RELSIM_OK;
@@ -906,7 +906,7 @@ template <typename T>
 int cycle_end(relsim_ctx* c, const GmSetup& S, cudaStream_t s, GmCond outer, bool tr = false)
 {
     PROF_BEGIN(RELSIM_PROF_GMRES_ORTHO);
-    CK(gm_finish_cycle(c->gms, c->gx, c->V, S.ldv, S.n, S.m, s));
+    CK(gm_finish_cycle(c->gms, c->gx, c->V, S.ldv, S.n, S.m, s, c->g.df));
     PROF_END();
     PROF_BEGIN(RELSIM_PROF_GMRES_APPLY);
     CK(op_residual<T>((const T*)c->M, c->gx, c->gb, S.p.r, c->g, c->partial, c->dpush, s, tr));
@@ -1338,7 +1338,7 @@ int adjoint_impl(relsim_ctx* c, const double* gE1, const double* gB1, const doub
     const GmSetup S = gm_setup(c);
     TRY(solve_reserve(c, S));
     CK(adjoint_pre(d1, d2, d3, c->gb, c->g, c->st));
-    CK(gm_dots(c->V, S.ldv, 0, c->gb, S.n, c->partial, S.nb, c->st));
+    CK(gm_dots(c->V, S.ldv, 0, c->gb, S.n, c->partial, S.nb, c->st, c->g.df));
     CK(reduce_partials(c->partial, S.nb, 1, c->dsum, c->st));
     CK(gm_begin(c->gms, c->dsum, c->st));
     CK(cudaMemsetAsync(c->gx, 0, sizeof(double) * (size_t)n, c->st));
@@ -1648,6 +1648,43 @@ int modes_impl(relsim_ctx* c, int comp, int nmodes, double* energy, int where)
     return RELSIM_OK;
 }
 
+// the energy of one mode and its gradient in B (component comp)
+template <typename T>
+int mode_grad_impl(relsim_ctx* c, int comp, int mode, double* energy, double* gB, int where)
+{
+    const int nx = c->g.nx, ny = c->g.ny * c->g.nz;
+    const int64_t nc = c->g.ncell;
+    if (mode + 1 > c->mode_tw_m) {
+        dfree(c->mode_tw);
+        c->mode_tw_m = 0;
+        TRY(dalloc(c, &c->mode_tw, sizeof(T) * 2 * (size_t)nx * (size_t)(mode + 1)));
+        CK(mode_twiddles<T>((T*)c->mode_tw, nx, mode + 1, c->st));
+        c->mode_tw_m = mode + 1;
+    }
+    // device scratch: ny row values, the energy, and a 3 ncell gradient
+    // staged for host outputs
+    const int64_t need = (int64_t)ny + 1 + (where == RELSIM_HOST ? 3 * nc : 0);
+    if (need > c->mode_rows_cap) {
+        dfree(c->mode_rows);
+        c->mode_rows_cap = 0;
+        TRY(dalloc(c, &c->mode_rows, sizeof(double) * (size_t)need));
+        c->mode_rows_cap = need;
+    }
+    const int bnow = c->state == kSolved ? 1 - c->bcur : c->bcur;
+    const T* Bc = (const T*)c->B[bnow] + (int64_t)comp * nc;
+    double* e_dev = where == RELSIM_DEVICE ? energy : c->mode_rows + ny;
+    double* g_dev = where == RELSIM_DEVICE ? gB : c->mode_rows + ny + 1;
+    CK(cudaMemsetAsync(g_dev, 0, sizeof(double) * 3 * (size_t)nc, c->st));
+    CK(mode_gradient<T>(Bc, (const T*)c->mode_tw, nx, ny, mode, c->g.dV, c->mode_rows, e_dev,
+                        g_dev + (int64_t)comp * nc, c->st));
+    if (where == RELSIM_HOST) {
+        CK(cudaMemcpyAsync(energy, e_dev, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(gB, g_dev, sizeof(double) * 3 * (size_t)nc, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    return RELSIM_OK;
+}
+
 int check_push(relsim_ctx* c)
 {
     if (*c->hpush & 2)
@@ -1789,6 +1826,10 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     c->g.dt = cfg->dt;
     c->g.theta = cfg->theta_implicit;
     c->g.dV = cfg->dx * cfg->dy * c->g.dz;
+    // the FP32 form of the 2D scheme with linear shapes keeps its GMRES
+    // vectors as double-float pairs (FP32-pipe arithmetic at close to FP64
+    // precision) unless FP64 vectors are asked for
+    c->g.df = cfg->precision == 32 && cfg->dim == 2 && c->g.shape == 1 && !cfg->gmres_fp64 ? 1 : 0;
     // one-cell moves per step: c dt <= min(dx, dy); the 3D form always
     // takes the general push (any move length, radix sort) and host-driven steps
     c->fast_sort = cfg->dim == 2 && c->g.shape == 1 && cfg->dt <= cfg->dx && cfg->dt <= cfg->dy;
@@ -2227,12 +2268,23 @@ int relsim_apply_operator(relsim_ctx* c, const double* v, double* out, int where
     const double* dv;
     if (where == RELSIM_HOST) TRY(ensure_stage(c, n));
     TRY(stage_in(c, v, n, where, &dv, 0));
-    // the GMRES work vector is free outside a solve
-    if (c->prec == 32) CK(apply_A<float>((const float*)c->M, dv, c->gw, c->g, c->dpush, c->st));
-    else CK(apply_A<double>((const double*)c->M, dv, c->gw, c->g, c->dpush, c->st));
-    if (where == RELSIM_DEVICE) return copy_out(c, out, c->gw, n, where);
+    // the GMRES work vectors are free outside a solve; with double-float
+    // vectors the FP64 input and output are converted on either side
+    const double* vin = dv;
+    if (c->g.df) {
+        CK(vec_from_double(dv, c->gw2, n, 1, c->st));
+        vin = c->gw2;
+    }
+    if (c->prec == 32) CK(apply_A<float>((const float*)c->M, vin, c->gw, c->g, c->dpush, c->st));
+    else CK(apply_A<double>((const double*)c->M, vin, c->gw, c->g, c->dpush, c->st));
+    const double* res = c->gw;
+    if (c->g.df) {
+        CK(vec_to_double(c->gw, c->gw2, n, 1, c->st));
+        res = c->gw2;
+    }
+    if (where == RELSIM_DEVICE) return copy_out(c, out, res, n, where);
     CK(cudaMemcpyAsync(c->hpush, c->dpush, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    TRY(copy_out(c, out, c->gw, n, where));
+    TRY(copy_out(c, out, res, n, where));
     return check_push(c);
 }
 
@@ -2312,6 +2364,16 @@ int relsim_field_modes(relsim_ctx* c, int component, int nmodes, double* energy,
     if (!energy) return fail(c, RELSIM_ERR_INVALID_ARG, "null output");
     if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
     return DISPATCH(modes_impl, c, component, nmodes, energy, where);
+}
+
+int relsim_field_mode_gradient(relsim_ctx* c, int component, int mode, double* energy, double* gB, int where)
+{
+    if (!c) return RELSIM_ERR_INVALID_ARG;
+    if (component < 0 || component > 2) return fail(c, RELSIM_ERR_INVALID_ARG, "component %d out of range", component);
+    if (mode < 0 || mode > c->g.nx / 2) return fail(c, RELSIM_ERR_INVALID_ARG, "mode %d outside [0, nx/2]", mode);
+    if (!energy || !gB) return fail(c, RELSIM_ERR_INVALID_ARG, "null output");
+    if (where != RELSIM_HOST && where != RELSIM_DEVICE) return fail(c, RELSIM_ERR_INVALID_ARG, "bad where");
+    return DISPATCH(mode_grad_impl, c, component, mode, energy, gB, where);
 }
 
 int relsim_graph_info(const relsim_ctx* c, int64_t* graph_steps, int* disabled, const char** why)

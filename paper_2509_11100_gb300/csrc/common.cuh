@@ -42,6 +42,8 @@ struct GridP {
     double dz = 1.0;
     int shape = 1;   // 1: linear (CIC); 2: quadratic (TSC, 2D)
     int op_y = 0;    // rows of the 2D operator's tiles (0: the form's default)
+    int df = 0;      // 1: the GMRES vectors hold double-float pairs (dfloat.cuh)
+                     // in their 8-byte slots (FP32 form, 2D, linear shapes)
 };
 
 __host__ __device__ __forceinline__ int mblock_of(const GridP& g)

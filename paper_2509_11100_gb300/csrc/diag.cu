@@ -59,6 +59,18 @@ __global__ void k_mode_rows(const T* __restrict__ Bc, const T* __restrict__ tw, 
     }
 }
 
+// the energy of mode m from its ny row values |F_{m,j}|^2 (fixed order)
+__global__ void k_mode_sum_one(const double* __restrict__ rows, int nx, int ny, int m, double dV,
+                               double* __restrict__ out)
+{
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int j = 0; j < ny; ++j) s += rows[j];
+        const double cm = (m == 0 || 2 * m == nx) ? 1.0 : 2.0;
+        *out = 0.5 * dV * cm * s / (double)nx;
+    }
+}
+
 __global__ void k_mode_sum(const double* __restrict__ rows, int nx, int ny, int nmodes, double dV,
                            double* __restrict__ out)
 {
@@ -70,7 +82,54 @@ __global__ void k_mode_sum(const double* __restrict__ rows, int nx, int ny, int 
     }
 }
 
+// The gradient of one mode's energy with respect to the component: warp per
+// row j forms F_{m,j} as k_mode_rows does, then writes
+//   dW_m/dB(i, j) = dV (c_m / nx) (Re F cos(2 pi m i/nx) - Im F sin(2 pi m i/nx))
+// (FP64) and |F|^2 for the energy (summed by k_mode_sum).
+template <typename T>
+__global__ void k_mode_grad(const T* __restrict__ Bc, const T* __restrict__ tw, int nx, int ny, int m,
+                            double dV, double* __restrict__ rows, double* __restrict__ g)
+{
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const double cm = (m == 0 || 2 * m == nx) ? 1.0 : 2.0;
+    const double sc = dV * cm / (double)nx;
+    const T* t = tw + 2 * (int64_t)m * nx;
+    for (int j = blockIdx.x * warps + (threadIdx.x >> 5); j < ny; j += gridDim.x * warps) {
+        const T* row = Bc + (int64_t)j * nx;
+        T re = 0, im = 0;
+        for (int i = lane; i < nx; i += 32) {
+            const T b = row[i];
+            re += b * t[2 * i];
+            im -= b * t[2 * i + 1];
+        }
+        double dr = (double)re, di = (double)im;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dr += __shfl_xor_sync(0xffffffffu, dr, o);
+            di += __shfl_xor_sync(0xffffffffu, di, o);
+        }
+        if (lane == 0) rows[j] = dr * dr + di * di;
+        double* gr = g + (int64_t)j * nx;
+        for (int i = lane; i < nx; i += 32) gr[i] = sc * (dr * (double)t[2 * i] - di * (double)t[2 * i + 1]);
+    }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t mode_gradient(const T* Bc, const T* tw, int nx, int ny, int m, double dV, double* rows,
+                          double* energy, double* g, cudaStream_t st)
+{
+    count_launches(2);
+    const int warps = 8;
+    const int blocks = (ny + warps - 1) / warps;
+    k_mode_grad<T><<<blocks, 32 * warps, 0, st>>>(Bc, tw, nx, ny, m, dV, rows, g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // one mode: k_mode_sum over a one-mode row table scaled as mode m
+    k_mode_sum_one<<<1, 32, 0, st>>>(rows, nx, ny, m, dV, energy);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t mode_twiddles(T* tw, int nx, int nmodes, cudaStream_t st)
@@ -98,6 +157,10 @@ cudaError_t field_modes(const T* Bc, const T* tw, int nx, int ny, int nmodes, do
 
 template cudaError_t mode_twiddles<float>(float*, int, int, cudaStream_t);
 template cudaError_t mode_twiddles<double>(double*, int, int, cudaStream_t);
+template cudaError_t mode_gradient<float>(const float*, const float*, int, int, int, double, double*, double*,
+                                          double*, cudaStream_t);
+template cudaError_t mode_gradient<double>(const double*, const double*, int, int, int, double, double*, double*,
+                                           double*, cudaStream_t);
 template cudaError_t field_modes<float>(const float*, const float*, int, int, int, double, double*, double*,
                                         cudaStream_t);
 template cudaError_t field_modes<double>(const double*, const double*, int, int, int, double, double*,

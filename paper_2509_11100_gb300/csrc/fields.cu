@@ -1,6 +1,12 @@
 // fields.cu -- grid kernels: right-hand side and matrix-free operator of
 // the implicit field equation, the field update with the field terms of the
-// energy ledger, FP64 GMRES vector kernels, and format conversions.
+// energy ledger, the GMRES vector kernels, and format conversions.
+//
+// GMRES vectors (Krylov basis, iterate, right-hand side, work vectors) have
+// 8-byte elements: FP64, or, in the FP32 form of the 2D scheme with linear
+// shapes (GridP::df), double-float pairs hi + lo (dfloat.cuh) whose
+// arithmetic runs on the FP32 pipe. Kernels take them as double pointers and
+// read them through the DF template parameter.
 //
 // Discrete curls (2D, all three components kept, z ignorable):
 //   curl_c (node -> centre (i+1/2, j+1/2)): differences across the cell,
@@ -11,6 +17,7 @@
 //     makes the discrete Poynting balance exact.
 #include <atomic>
 
+#include "dfloat.cuh"
 #include "launch.cuh"
 
 namespace relsim {
@@ -39,8 +46,16 @@ __global__ void k_to_double(const T* __restrict__ in, double* out, int64_t n)
         out[k] = (double)in[k];
 }
 
+// store v (formed in T) in a GMRES vector slot
+template <bool DF, typename T>
+__device__ __forceinline__ void vst(double* v, int64_t k, T val)
+{
+    if constexpr (DF) reinterpret_cast<dfl*>(v)[k] = df_from_f((float)val);
+    else v[k] = (double)val;
+}
+
 // b = E^n + theta dt curl_n B^n - theta dt Jhat
-template <typename T>
+template <typename T, bool DF>
 __global__ void k_rhs(const T* __restrict__ E, const T* __restrict__ B, const T* __restrict__ J,
                       double* __restrict__ b, GridP g)
 {
@@ -59,14 +74,50 @@ __global__ void k_rhs(const T* __restrict__ E, const T* __restrict__ B, const T*
     const T dxBz = (Bz[c11] - Bz[c01] + Bz[c10] - Bz[c00]) * idx2;
     const T dyBz = (Bz[c11] - Bz[c10] + Bz[c01] - Bz[c00]) * idy2;
     const T td = T(g.theta * g.dt);
-    b[gidx] = (double)(E[gidx] + td * dyBz - td * J[gidx]);
-    b[nc + gidx] = (double)(E[nc + gidx] - td * dxBz - td * J[nc + gidx]);
-    b[2 * nc + gidx] = (double)(E[2 * nc + gidx] + td * (dxBy - dyBx) - td * J[2 * nc + gidx]);
+    vst<DF>(b, gidx, E[gidx] + td * dyBz - td * J[gidx]);
+    vst<DF>(b, nc + gidx, E[nc + gidx] - td * dxBz - td * J[nc + gidx]);
+    vst<DF>(b, 2 * nc + gidx, E[2 * nc + gidx] + td * (dxBy - dyBx) - td * J[2 * nc + gidx]);
 }
 
-// Node-local loads of a vector given in FP64 as T
-template <typename T>
-__device__ __forceinline__ T vld(const double* v, int64_t k) { return (T)__ldg(v + k); }
+// a field (T) into a GMRES vector (the initial iterate x = E^n)
+template <typename T, bool DF>
+__global__ void k_to_vec(const T* __restrict__ in, double* out, int64_t n)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        vst<DF>(out, k, in[k]);
+}
+
+// FP64 <-> double-float vectors (the caller-facing operator application)
+__global__ void k_df_from_double(const double* __restrict__ in, double* out, int64_t n)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        reinterpret_cast<dfl*>(out)[k] = df_from_double(in[k]);
+}
+__global__ void k_df_to_double(const double* __restrict__ in, double* out, int64_t n)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = df_to_double(reinterpret_cast<const dfl*>(in)[k]);
+}
+
+// Node-local loads of a GMRES vector as T
+template <typename T, bool DF = false>
+__device__ __forceinline__ T vld(const double* v, int64_t k)
+{
+    if constexpr (DF) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(v) + k);
+        return (T)df_to_f(dfl{a.x, a.y});
+    } else {
+        return (T)__ldg(v + k);
+    }
+}
+__device__ __forceinline__ dfl dld(const double* v, int64_t k)
+{
+    const float2 a = __ldg(reinterpret_cast<const float2*>(v) + k);
+    return dfl{a.x, a.y};
+}
 
 // (curl_n curl_c v) and (M v) at a node from its 3x3 stencil of v,
 // f[k][a][b] = component k at node (i-1+a, j-1+b), and its mass-matrix
@@ -135,8 +186,9 @@ __device__ __forceinline__ void op_stencil(const T (&f)[3][3][3], P Mg, const P 
     op_stencil_t<T, P, false>(f, Mg, Mn, idx2, idy2, cc, mv);
 }
 
-// the same at node (i,j) straight from global memory (v FP64, component-major)
-template <typename T>
+// the same at node (i,j) straight from global memory (v a GMRES vector,
+// component-major)
+template <typename T, bool DF = false>
 __device__ __forceinline__ void op_parts(const T* __restrict__ M, const double* __restrict__ v, int i,
                                          int j, const GridP& g, T cc[3], T mv[3])
 {
@@ -149,7 +201,7 @@ __device__ __forceinline__ void op_parts(const T* __restrict__ M, const double* 
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) f[k][a][b] = vld<T>(v, (int64_t)k * nc + ys[b] + xs[a]);
+            for (int b = 0; b < 3; ++b) f[k][a][b] = vld<T, DF>(v, (int64_t)k * nc + ys[b] + xs[a]);
     const T* Mg = M + ((int64_t)ys[1] + xs[1]) * kMBlock;
     const T* Mn[4] = {M + ((int64_t)ys[1] + xs[0]) * kMBlock + 9, M + ((int64_t)ys[0] + xs[2]) * kMBlock + 18,
                       M + ((int64_t)ys[0] + xs[1]) * kMBlock + 27, M + ((int64_t)ys[0] + xs[0]) * kMBlock + 36};
@@ -208,12 +260,47 @@ static_assert(op_buffer_fits<float, 0>() && op_buffer_fits<float, 4>() && op_buf
                   op_buffer_fits<double, 2>(),
               "the reduction buffer fits in the mass-matrix tile");
 
-template <typename T, int MODE, bool TR, int YY = 0>
+// Dot2 (Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26, 2005) on the FP32 pipe: a running sum s with its error e,
+// each term's product split exactly by TwoProduct and added by TwoSum.
+struct Dot2 {
+    float s = 0.0f, e = 0.0f;
+    // += a b, a double-float, b FP32
+    __device__ __forceinline__ void add(dfl a, float b)
+    {
+        const dfl p = df_two_prod(a.hi, b);
+        const dfl t = df_two_sum(s, p.hi);
+        s = t.hi;
+        e = __fadd_rn(e, __fadd_rn(t.lo, __fmaf_rn(a.lo, b, p.lo)));
+    }
+    // += a b, both double-float
+    __device__ __forceinline__ void add(dfl a, dfl b)
+    {
+        const dfl p = df_two_prod(a.hi, b.hi);
+        const float pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+        const dfl t = df_two_sum(s, p.hi);
+        s = t.hi;
+        e = __fadd_rn(e, __fadd_rn(t.lo, pe));
+    }
+    // -= a b, both double-float
+    __device__ __forceinline__ void sub(dfl a, dfl b)
+    {
+        const dfl p = df_two_prod(a.hi, b.hi);
+        const float pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+        const dfl t = df_two_sum(s, -p.hi);
+        s = t.hi;
+        e = __fadd_rn(e, __fsub_rn(t.lo, pe));
+    }
+    __device__ __forceinline__ dfl value() const { return df_fast_two_sum(s, e); }
+};
+
+template <typename T, int MODE, bool TR, int YY = 0, bool DF = false>
 __global__ void __launch_bounds__(OpTile<T, YY>::threads, sizeof(T) == 4 ? 3 : 2)
 k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const double* __restrict__ b,
      double* __restrict__ out, double* __restrict__ vj, const double* __restrict__ V, int64_t ldv, int nv,
      GridP g, int tma, double* __restrict__ partial, int* __restrict__ err, const GmDyn* __restrict__ dyn)
 {
+    static_assert(!DF || sizeof(T) == 4, "double-float vectors belong to the FP32 form");
     constexpr int X = OpTile<T, YY>::X, Y = OpTile<T, YY>::Y, NT = OpTile<T, YY>::threads;
     if (MODE == kOpArnoldi && dyn) {
         // arguments of a device-decided Arnoldi iteration
@@ -254,13 +341,21 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
             for (int q = tid; q < tw * kMBlock; q += NT) S.Mm[r][q] = ld(src + q);
         }
     }
-    // the node's own input value in FP64
+    // the node's own input value in the vectors' precision (FP64 or
+    // double-float; the scale s differs from 1 only for a cycle's first
+    // vector)
     double own[3] = {0.0, 0.0, 0.0};
+    dfl ownd[3] = {dfl{0.f, 0.f}, dfl{0.f, 0.f}, dfl{0.f, 0.f}};
     if (active)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            own[k] = __ldg(in + (int64_t)k * nc + gidx);
-            if (MODE == kOpArnoldi && s != 1.0) own[k] *= s;
+            if constexpr (DF) {
+                ownd[k] = dld(in, (int64_t)k * nc + gidx);
+                if (MODE == kOpArnoldi && s != 1.0) ownd[k] = df_mul(ownd[k], df_from_double(s));
+            } else {
+                own[k] = __ldg(in + (int64_t)k * nc + gidx);
+                if (MODE == kOpArnoldi && s != 1.0) own[k] *= s;
+            }
         }
     for (int q = tid; q < (th + 1) * 2 * kMBlock; q += NT) {
         const int r = q / (2 * kMBlock), side = (q / kMBlock) % 2, e = q % kMBlock;
@@ -271,7 +366,10 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
     const T sT = (T)s;
     for (int q = tid; q < 3 * vh * vw; q += NT) {
         const int k = q / (vh * vw), rem = q % (vh * vw), r = rem / vw, cc = rem % vw;
-        T val = (T)__ldg(in + (int64_t)k * nc + (int64_t)wrap1(j0 - 1 + r, ny) * nx + wrap1(i0 - 1 + cc, nx));
+        const int64_t at = (int64_t)k * nc + (int64_t)wrap1(j0 - 1 + r, ny) * nx + wrap1(i0 - 1 + cc, nx);
+        T val;
+        if constexpr (DF) val = (T)dld(in, at).hi;   // the FP32 operator reads the leading part
+        else val = (T)__ldg(in + at);
         if (MODE == kOpArnoldi) val *= sT;
         S.v[k][r][cc] = val;
     }
@@ -286,6 +384,8 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
     }
 
     double wv[3] = {0.0, 0.0, 0.0};
+    dfl wd[3] = {dfl{0.f, 0.f}, dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+    float bvf[3] = {0.f, 0.f, 0.f};
     if (active) {
         T f[3][3][3];
 #pragma unroll
@@ -305,12 +405,23 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
         const T td = T(g.theta * g.dt);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double bv = (double)(td * td * cc[k] + td * mv[k]);
-            if (MODE == kOpA) wv[k] = own[k] + bv;
-            else if (MODE == kOpResidual) wv[k] = b[(int64_t)k * nc + gidx] - (own[k] + bv);
-            else wv[k] = bv;
-            out[(int64_t)k * nc + gidx] = wv[k];
-            if (MODE == kOpArnoldi && vj) vj[(int64_t)k * nc + gidx] = own[k];
+            const T bvT = td * td * cc[k] + td * mv[k];
+            const int64_t at = (int64_t)k * nc + gidx;
+            if constexpr (DF) {
+                bvf[k] = (float)bvT;
+                if (MODE == kOpA) wd[k] = df_add_f(ownd[k], bvf[k]);
+                else if (MODE == kOpResidual) wd[k] = df_sub(dld(b, at), df_add_f(ownd[k], bvf[k]));
+                else wd[k] = df_from_f(bvf[k]);
+                reinterpret_cast<dfl*>(out)[at] = wd[k];
+                if (MODE == kOpArnoldi && vj) reinterpret_cast<dfl*>(vj)[at] = ownd[k];
+            } else {
+                const double bv = (double)bvT;
+                if (MODE == kOpA) wv[k] = own[k] + bv;
+                else if (MODE == kOpResidual) wv[k] = b[at] - (own[k] + bv);
+                else wv[k] = bv;
+                out[at] = wv[k];
+                if (MODE == kOpArnoldi && vj) vj[at] = own[k];
+            }
         }
     }
     if (MODE == kOpA) return;
@@ -319,47 +430,91 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
     // products to shared memory, then each warp sums some of them
     const int nq = MODE == kOpResidual ? 1 : nv + 2;
     const int lane = tid & 31, wid = tid >> 5;
-    double* buf = reinterpret_cast<double*>(&S.Mm[0][0]);   // [kOpChunk][NT]
+    double* buf = reinterpret_cast<double*>(&S.Mm[0][0]);   // [kOpChunk][NT] (8-byte slots)
     __syncthreads();   // the mass-matrix tile is no longer read
     for (int q0 = 0; q0 < nq; q0 += kOpChunk) {
         const int kc = min(kOpChunk, nq - q0);   // live sums in this pass (warp-uniform)
-        double vq[kOpChunk][3];
+        if constexpr (DF) {
+            dfl* bufd = reinterpret_cast<dfl*>(buf);
+            dfl vq[kOpChunk][3];
 #pragma unroll
-        for (int c = 0; c < kOpChunk; ++c) {
-            const int q = q0 + c;
-            const bool gl = MODE == kOpArnoldi && active && q < nv;
-            const double* Vq = V + (int64_t)(gl ? q : 0) * ldv + gidx;
+            for (int c = 0; c < kOpChunk; ++c) {
+                const int q = q0 + c;
+                const bool gl = MODE == kOpArnoldi && active && q < nv;
+                const double* Vq = V + (int64_t)(gl ? q : 0) * ldv + gidx;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) vq[c][k] = gl ? __ldg(Vq + (int64_t)k * nc) : 0.0;
-        }
-        // FP64 work only for the live sums: a branch, not predication (a
-        // predicated-off FP64 instruction still takes its slot on the pipe)
-#pragma unroll
-        for (int c = 0; c < kOpChunk; ++c) {
-            if (c >= kc) break;
-            const int q = q0 + c;
-            double d = 0.0;
-            if (active) {
-                if (MODE == kOpResidual || q == nv + 1) d = wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2];
-                else if (q == nv) d = wv[0] * own[0] + wv[1] * own[1] + wv[2] * own[2];
-                else d = wv[0] * vq[c][0] + wv[1] * vq[c][1] + wv[2] * vq[c][2];
+                for (int k = 0; k < 3; ++k) vq[c][k] = gl ? dld(Vq, (int64_t)k * nc) : dfl{0.f, 0.f};
             }
-            buf[c * NT + tid] = d;
-        }
-        __syncthreads();
-        for (int c = wid; c < kc; c += NT / 32) {
-            double t = 0.0;
 #pragma unroll
-            for (int m = 0; m < NT / 32; ++m) t += buf[c * NT + m * 32 + lane];
-            t = warp_sum(t);
-            if (lane == 0) partial[(int64_t)blockIdx.x * nq + q0 + c] = t;
+            for (int c = 0; c < kOpChunk; ++c) {
+                if (c >= kc) break;
+                const int q = q0 + c;
+                Dot2 d;
+                if (active) {
+                    if (MODE == kOpResidual) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) d.add(wd[k], wd[k]);
+                    } else if (q == nv + 1) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) d.add(df_from_f(bvf[k]), bvf[k]);
+                    } else if (q == nv) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) d.add(ownd[k], bvf[k]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) d.add(vq[c][k], bvf[k]);
+                    }
+                }
+                bufd[c * NT + tid] = d.value();
+            }
+            __syncthreads();
+            for (int c = wid; c < kc; c += NT / 32) {
+                dfl t = dfl{0.f, 0.f};
+#pragma unroll
+                for (int m = 0; m < NT / 32; ++m) t = df_add(t, bufd[c * NT + m * 32 + lane]);
+                t = df_warp_sum(t);
+                if (lane == 0) partial[(int64_t)blockIdx.x * nq + q0 + c] = df_to_double(t);
+            }
+            __syncthreads();
+        } else {
+            double vq[kOpChunk][3];
+#pragma unroll
+            for (int c = 0; c < kOpChunk; ++c) {
+                const int q = q0 + c;
+                const bool gl = MODE == kOpArnoldi && active && q < nv;
+                const double* Vq = V + (int64_t)(gl ? q : 0) * ldv + gidx;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) vq[c][k] = gl ? __ldg(Vq + (int64_t)k * nc) : 0.0;
+            }
+            // FP64 work only for the live sums: a branch, not predication (a
+            // predicated-off FP64 instruction still takes its slot on the pipe)
+#pragma unroll
+            for (int c = 0; c < kOpChunk; ++c) {
+                if (c >= kc) break;
+                const int q = q0 + c;
+                double d = 0.0;
+                if (active) {
+                    if (MODE == kOpResidual || q == nv + 1) d = wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2];
+                    else if (q == nv) d = wv[0] * own[0] + wv[1] * own[1] + wv[2] * own[2];
+                    else d = wv[0] * vq[c][0] + wv[1] * vq[c][1] + wv[2] * vq[c][2];
+                }
+                buf[c * NT + tid] = d;
+            }
+            __syncthreads();
+            for (int c = wid; c < kc; c += NT / 32) {
+                double t = 0.0;
+#pragma unroll
+                for (int m = 0; m < NT / 32; ++m) t += buf[c * NT + m * 32 + lane];
+                t = warp_sum(t);
+                if (lane == 0) partial[(int64_t)blockIdx.x * nq + q0 + c] = t;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
 // E^{n+theta} from the solve, E^{n+1}, B^{n+1}, and the field ledger terms.
-template <typename T>
+template <typename T, bool DF>
 __global__ void __launch_bounds__(kFieldThreads)
 k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* __restrict__ J,
                T* __restrict__ Eth, T* __restrict__ E, const T* __restrict__ B0, T* __restrict__ B1,
@@ -374,7 +529,7 @@ k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* _
         const T th = T(g.theta), hdV = T(0.5 * g.dV);
         T et[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) et[k] = vld<T>(x, (int64_t)k * nc + gidx);
+        for (int k = 0; k < 3; ++k) et[k] = vld<T, DF>(x, (int64_t)k * nc + gidx);
         // E update
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -394,8 +549,8 @@ k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* _
         T dxE[3], dyE[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const T a = vld<T>(x, k * nc + n00), b = vld<T>(x, k * nc + n10);
-            const T c = vld<T>(x, k * nc + n01), d = vld<T>(x, k * nc + n11);
+            const T a = vld<T, DF>(x, k * nc + n00), b = vld<T, DF>(x, k * nc + n10);
+            const T c = vld<T, DF>(x, k * nc + n01), d = vld<T, DF>(x, k * nc + n11);
             dxE[k] = (b - a + d - c) * idx2;
             dyE[k] = (c - a + d - b) * idy2;
         }
@@ -413,7 +568,7 @@ k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* _
         acc[2] *= T((g.theta - 0.5) * g.dV);
         // work: dt dV (Jhat + M E^{n+theta}) . E^{n+theta}
         T cc[3], mv[3];
-        op_parts<T>(M, x, i, j, g, cc, mv);
+        op_parts<T, DF>(M, x, i, j, g, cc, mv);
         T wk = T(0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) wk += (J[(int64_t)k * nc + gidx] + mv[k]) * et[k];
@@ -479,31 +634,73 @@ __global__ void k_mass_from_double(const double* __restrict__ Md, const double* 
 }
 
 // ---------------------------------------------------------------------------
-// GMRES vectors (FP64)
+// GMRES vectors: FP64, or double-float (DF) with every sum of products formed
+// by Dot2 / Sum2-style compensation on the FP32 pipe
 
 constexpr int kGmThreads = 256;
 constexpr int kDotChunk = 8;
 
+// a block's double-float sums of N values, converted to FP64 once per block
+template <int N>
+__device__ __forceinline__ void df_block_sum(dfl (&v)[N], dfl* red, double (&out)[N])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = df_warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) red[wid * N + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            dfl t = lane < nw ? red[lane * N + k] : dfl{0.f, 0.f};
+            t = df_warp_sum(t);
+            out[k] = df_to_double(t);
+        }
+    }
+    __syncthreads();
+}
+
+template <bool DF>
 __global__ void __launch_bounds__(kGmThreads)
 k_gm_dots(const double* __restrict__ V, int64_t ldv, int k0, int kc, const double* __restrict__ w,
           int64_t n, double* __restrict__ partial, int stride, bool with_ww)
 {
     __shared__ double red[32 * (kDotChunk + 1)];
-    double acc[kDotChunk + 1];
-#pragma unroll
-    for (int c = 0; c <= kDotChunk; ++c) acc[c] = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const double we = w[e];
-#pragma unroll
-        for (int c = 0; c < kDotChunk; ++c) {
-            if (c >= kc) break;   // a branch: no predicated-off FP64 work
-            acc[c] += V[(int64_t)(k0 + c) * ldv + e] * we;
-        }
-        if (with_ww) acc[kDotChunk] += we * we;
-    }
     double out[kDotChunk + 1];
-    block_sum<kDotChunk + 1>(acc, red, out);
+    if constexpr (DF) {
+        Dot2 acc[kDotChunk + 1];
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const dfl we = dld(w, e);
+#pragma unroll
+            for (int c = 0; c < kDotChunk; ++c) {
+                if (c >= kc) break;
+                acc[c].add(dld(V + (int64_t)(k0 + c) * ldv, e), we);
+            }
+            if (with_ww) acc[kDotChunk].add(we, we);
+        }
+        dfl v[kDotChunk + 1];
+#pragma unroll
+        for (int c = 0; c <= kDotChunk; ++c) v[c] = acc[c].value();
+        df_block_sum<kDotChunk + 1>(v, reinterpret_cast<dfl*>(red), out);
+    } else {
+        double acc[kDotChunk + 1];
+#pragma unroll
+        for (int c = 0; c <= kDotChunk; ++c) acc[c] = 0.0;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const double we = w[e];
+#pragma unroll
+            for (int c = 0; c < kDotChunk; ++c) {
+                if (c >= kc) break;   // a branch: no predicated-off FP64 work
+                acc[c] += V[(int64_t)(k0 + c) * ldv + e] * we;
+            }
+            if (with_ww) acc[kDotChunk] += we * we;
+        }
+        block_sum<kDotChunk + 1>(acc, red, out);
+    }
     if (threadIdx.x == 0) {
         for (int c = 0; c < kc; ++c) partial[(int64_t)blockIdx.x * stride + k0 + c] = out[c];
         if (with_ww) partial[(int64_t)blockIdx.x * stride + stride - 1] = out[kDotChunk];
@@ -512,40 +709,82 @@ k_gm_dots(const double* __restrict__ V, int64_t ldv, int k0, int kc, const doubl
 
 constexpr int kGmChunk = 8;   // basis vectors per group of independent loads
 
+// s - sum_c h_c V_c(e) over c < k, double-float (Sum2-style: the running sum
+// and its error apart, each product split exactly)
+__device__ __forceinline__ dfl df_sub_combination(dfl w, const dfl* hs, const double* __restrict__ V,
+                                                  int64_t ldv, int k, int64_t e, float sign)
+{
+    Dot2 d;
+    d.s = w.hi;
+    d.e = w.lo;
+    for (int c0 = 0; c0 < k; c0 += kGmChunk) {
+        const int kc = min(kGmChunk, k - c0);
+        dfl vv[kGmChunk];
+#pragma unroll
+        for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? dld(V + (int64_t)(c0 + c) * ldv, e) : dfl{0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < kGmChunk; ++c) {
+            if (c >= kc) break;
+            const dfl h = hs[c0 + c];
+            if (sign < 0.f) d.sub(h, vv[c]);
+            else d.add(h, vv[c]);
+        }
+    }
+    return d.value();
+}
+
+template <bool DF>
 __global__ void __launch_bounds__(kGmThreads)
 k_gm_update(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int k,
             const double* __restrict__ h, int64_t n, double* __restrict__ partial)
 {
     __shared__ double hs[kMaxRestart + 1];
     __shared__ double red[32];
-    for (int c = threadIdx.x; c < k; c += blockDim.x) hs[c] = h[c];
-    __syncthreads();
-    double acc = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double s = w[e];
-        for (int c0 = 0; c0 < k; c0 += kGmChunk) {
-            const int kc = min(kGmChunk, k - c0);
-            double vv[kGmChunk];
-#pragma unroll
-            for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
-#pragma unroll
-            for (int c = 0; c < kGmChunk; ++c) {
-                if (c >= kc) break;   // a branch: no predicated-off FP64 work
-                s -= hs[c0 + c] * vv[c];
-            }
-        }
-        w[e] = s;
-        acc += s * s;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if constexpr (DF) reinterpret_cast<dfl*>(hs)[c] = df_from_double(h[c]);
+        else hs[c] = h[c];
     }
-    double v[1] = {acc}, out[1];
-    block_sum<1>(v, red, out);
+    __syncthreads();
+    double out[1];
+    if constexpr (DF) {
+        Dot2 acc;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const dfl s = df_sub_combination(dld(w, e), reinterpret_cast<const dfl*>(hs), V, ldv, k, e, -1.f);
+            reinterpret_cast<dfl*>(w)[e] = s;
+            acc.add(s, s);
+        }
+        dfl v[1] = {acc.value()};
+        df_block_sum<1>(v, reinterpret_cast<dfl*>(red), out);
+    } else {
+        double acc = 0.0;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            double s = w[e];
+            for (int c0 = 0; c0 < k; c0 += kGmChunk) {
+                const int kc = min(kGmChunk, k - c0);
+                double vv[kGmChunk];
+#pragma unroll
+                for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
+#pragma unroll
+                for (int c = 0; c < kGmChunk; ++c) {
+                    if (c >= kc) break;   // a branch: no predicated-off FP64 work
+                    s -= hs[c0 + c] * vv[c];
+                }
+            }
+            w[e] = s;
+            acc += s * s;
+        }
+        double v[1] = {acc};
+        block_sum<1>(v, red, out);
+    }
     if (threadIdx.x == 0) partial[blockIdx.x] = out[0];
 }
 
 // Arnoldi update with the normalisation fused: v_{k} = (w - sum_{c<k} h_c V_c)/hn
 // with hn^2 = <w,w> - sum h_c^2 (h and <w,w> from the dot-product sums hw =
 // [h_0 .. h_{k-1}, <w,w>]; every block forms hn itself).
+template <bool DF>
 __global__ void __launch_bounds__(kGmThreads)
 k_gm_update_scale(const double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int k,
                   const double* __restrict__ hw, double* __restrict__ vout, int64_t n,
@@ -560,78 +799,123 @@ k_gm_update_scale(const double* __restrict__ w, const double* __restrict__ V, in
         hw = dyn->ds;
         vout = const_cast<double*>(V) + (int64_t)k * ldv;
     }
-    for (int c = threadIdx.x; c < k; c += blockDim.x) hs[c] = hw[c];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if constexpr (DF) reinterpret_cast<dfl*>(hs)[c] = df_from_double(hw[c]);
+        else hs[c] = hw[c];
+    }
     if (threadIdx.x == 0) {
         double h2 = hw[k];
         for (int c = 0; c < k; ++c) h2 -= hw[c] * hw[c];
-        inv = h2 > 0.0 ? 1.0 / sqrt(h2) : 0.0;
+        const double iv = h2 > 0.0 ? 1.0 / sqrt(h2) : 0.0;
+        if constexpr (DF) *reinterpret_cast<dfl*>(&inv) = df_from_double(iv);
+        else inv = iv;
     }
     __syncthreads();
-    const double sc = inv;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double s = w[e];
-        for (int c0 = 0; c0 < k; c0 += kGmChunk) {
-            const int kc = min(kGmChunk, k - c0);
-            double vv[kGmChunk];
-#pragma unroll
-            for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
-#pragma unroll
-            for (int c = 0; c < kGmChunk; ++c) {
-                if (c >= kc) break;   // a branch: no predicated-off FP64 work
-                s -= hs[c0 + c] * vv[c];
-            }
+    if constexpr (DF) {
+        const dfl sc = *reinterpret_cast<const dfl*>(&inv);
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const dfl s = df_sub_combination(dld(w, e), reinterpret_cast<const dfl*>(hs), V, ldv, k, e, -1.f);
+            reinterpret_cast<dfl*>(vout)[e] = df_mul(s, sc);
         }
-        vout[e] = s * sc;
+    } else {
+        const double sc = inv;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            double s = w[e];
+            for (int c0 = 0; c0 < k; c0 += kGmChunk) {
+                const int kc = min(kGmChunk, k - c0);
+                double vv[kGmChunk];
+#pragma unroll
+                for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
+#pragma unroll
+                for (int c = 0; c < kGmChunk; ++c) {
+                    if (c >= kc) break;   // a branch: no predicated-off FP64 work
+                    s -= hs[c0 + c] * vv[c];
+                }
+            }
+            vout[e] = s * sc;
+        }
     }
 }
 
+template <bool DF>
 __global__ void k_gm_scale(double* dst, const double* __restrict__ src, double s, int64_t n)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x)
-        dst[e] = src[e] * s;
+    if constexpr (DF) {
+        const dfl sd = df_from_double(s);
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x)
+            reinterpret_cast<dfl*>(dst)[e] = df_mul(dld(src, e), sd);
+    } else {
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x)
+            dst[e] = src[e] * s;
+    }
 }
 
+template <bool DF>
 __global__ void __launch_bounds__(kGmThreads)
 k_gm_sub(double* r, const double* __restrict__ b, const double* __restrict__ Ax, int64_t n,
          double* partial)
 {
     __shared__ double red[32];
-    double acc = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double s = b[e] - Ax[e];
-        r[e] = s;
-        acc += s * s;
+    double out[1];
+    if constexpr (DF) {
+        Dot2 acc;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const dfl s = df_sub(dld(b, e), dld(Ax, e));
+            reinterpret_cast<dfl*>(r)[e] = s;
+            acc.add(s, s);
+        }
+        dfl v[1] = {acc.value()};
+        df_block_sum<1>(v, reinterpret_cast<dfl*>(red), out);
+    } else {
+        double acc = 0.0;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            double s = b[e] - Ax[e];
+            r[e] = s;
+            acc += s * s;
+        }
+        double v[1] = {acc};
+        block_sum<1>(v, red, out);
     }
-    double v[1] = {acc}, out[1];
-    block_sum<1>(v, red, out);
     if (threadIdx.x == 0) partial[blockIdx.x] = out[0];
 }
 
+template <bool DF>
 __global__ void k_gm_combine(double* x, const double* __restrict__ V, int64_t ldv, int k,
                              const double* __restrict__ y, int64_t n, const int* __restrict__ kdev)
 {
     __shared__ double ys[kMaxRestart + 1];
     if (kdev) k = *kdev;   // the dimension decided on the device
-    for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = y[c];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if constexpr (DF) reinterpret_cast<dfl*>(ys)[c] = df_from_double(y[c]);
+        else ys[c] = y[c];
+    }
     __syncthreads();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        double s = x[e];
-        for (int c0 = 0; c0 < k; c0 += kGmChunk) {
-            const int kc = min(kGmChunk, k - c0);
-            double vv[kGmChunk];
+        if constexpr (DF) {
+            reinterpret_cast<dfl*>(x)[e] =
+                df_sub_combination(dld(x, e), reinterpret_cast<const dfl*>(ys), V, ldv, k, e, 1.f);
+        } else {
+            double s = x[e];
+            for (int c0 = 0; c0 < k; c0 += kGmChunk) {
+                const int kc = min(kGmChunk, k - c0);
+                double vv[kGmChunk];
 #pragma unroll
-            for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
+                for (int c = 0; c < kGmChunk; ++c) vv[c] = c < kc ? __ldg(V + (int64_t)(c0 + c) * ldv + e) : 0.0;
 #pragma unroll
-            for (int c = 0; c < kGmChunk; ++c) {
-                if (c >= kc) break;   // a branch: no predicated-off FP64 work
-                s += ys[c0 + c] * vv[c];
+                for (int c = 0; c < kGmChunk; ++c) {
+                    if (c >= kc) break;   // a branch: no predicated-off FP64 work
+                    s += ys[c0 + c] * vv[c];
+                }
             }
+            x[e] = s;
         }
-        x[e] = s;
     }
 }
 
@@ -695,14 +979,50 @@ cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStre
 {
     if (g.dim == 3) return rhs3<T>(E, B, J, b, g, st);
     count_launches(1);
-    k_rhs<T><<<grid_for(g.ncell, 256, 1 << 30), 256, 0, st>>>(E, B, J, b, g);
+    if constexpr (sizeof(T) == 4) {
+        if (g.df) {
+            k_rhs<T, true><<<grid_for(g.ncell, 256, 1 << 30), 256, 0, st>>>(E, B, J, b, g);
+            return cudaGetLastError();
+        }
+    }
+    k_rhs<T, false><<<grid_for(g.ncell, 256, 1 << 30), 256, 0, st>>>(E, B, J, b, g);
     return cudaGetLastError();
 }
 
-template <typename T, int MODE, bool TR, int YY>
-cudaError_t launch_op_y(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
-                        const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st,
-                        const GmDyn* dyn)
+template <typename T>
+cudaError_t fields_to_vec(const T* in, double* out, int64_t n, int df, cudaStream_t st)
+{
+    count_launches(1);
+    if constexpr (sizeof(T) == 4) {
+        if (df) {
+            k_to_vec<T, true><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(in, out, n);
+            return cudaGetLastError();
+        }
+    }
+    k_to_vec<T, false><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t vec_from_double(const double* in, double* out, int64_t n, int df, cudaStream_t st)
+{
+    if (!df) return in == out ? cudaSuccess : cudaMemcpyAsync(out, in, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    count_launches(1);
+    k_df_from_double<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t vec_to_double(const double* in, double* out, int64_t n, int df, cudaStream_t st)
+{
+    if (!df) return in == out ? cudaSuccess : cudaMemcpyAsync(out, in, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    count_launches(1);
+    k_df_to_double<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE, bool TR, int YY, bool DF>
+cudaError_t launch_op_yd(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
+                         const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st,
+                         const GmDyn* dyn)
 {
     // the dynamic shared-memory limit, set once per kernel and device
     static std::atomic<unsigned> attr_set{0};
@@ -712,16 +1032,28 @@ cudaError_t launch_op_y(const T* M, const double* in, double sc, const double* b
     if (e != cudaSuccess) return e;
     const unsigned bit = 1u << (dev & 31);
     if (!(attr_set.load() & bit)) {
-        e = cudaFuncSetAttribute(k_op<T, MODE, TR, YY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(k_op<T, MODE, TR, YY, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(bit);
     }
     // bulk copies need every staged mass-matrix row to start on 16 bytes
     const int tma = ((int64_t)g.nx * kMBlock * sizeof(T)) % 16 == 0 ? 1 : 0;
     count_launches(1);
-    k_op<T, MODE, TR, YY><<<op_blocks(g, sizeof(T) == 4 ? 32 : 64), OpTile<T, YY>::threads, smem, st>>>(
+    k_op<T, MODE, TR, YY, DF><<<op_blocks(g, sizeof(T) == 4 ? 32 : 64), OpTile<T, YY>::threads, smem, st>>>(
         M, in, sc, b, out, vj, V, ldv, nv, g, tma, partial, err, dyn);
     return cudaGetLastError();
+}
+
+template <typename T, int MODE, bool TR, int YY>
+cudaError_t launch_op_y(const T* M, const double* in, double sc, const double* b, double* out, double* vj,
+                        const double* V, int64_t ldv, int nv, GridP g, double* partial, int* err, cudaStream_t st,
+                        const GmDyn* dyn)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (g.df)
+            return launch_op_yd<T, MODE, TR, YY, true>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, err, st, dyn);
+    }
+    return launch_op_yd<T, MODE, TR, YY, false>(M, in, sc, b, out, vj, V, ldv, nv, g, partial, err, st, dyn);
 }
 
 template <typename T, int MODE, bool TR = false>
@@ -776,7 +1108,13 @@ cudaError_t field_update(const double* x, const T* M, const T* J, T* Eth, T* E, 
     if (g.dim == 3) return field_update3<T>(x, M, J, Eth, E, B0, B1, g, partial, nblocks, st);
     if (g.shape == 2) return field_update_q<T>(x, M, J, Eth, E, B0, B1, g, partial, nblocks, st);
     count_launches(1);
-    k_field_update<T><<<nblocks, kFieldThreads, 0, st>>>(x, M, J, Eth, E, B0, B1, g, partial);
+    if constexpr (sizeof(T) == 4) {
+        if (g.df) {
+            k_field_update<T, true><<<nblocks, kFieldThreads, 0, st>>>(x, M, J, Eth, E, B0, B1, g, partial);
+            return cudaGetLastError();
+        }
+    }
+    k_field_update<T, false><<<nblocks, kFieldThreads, 0, st>>>(x, M, J, Eth, E, B0, B1, g, partial);
     return cudaGetLastError();
 }
 
@@ -808,72 +1146,86 @@ cudaError_t mass_from_double(const double* Md, const double* Jd, T* M, T* J, Gri
 }
 
 cudaError_t gm_dots(const double* V, int64_t ldv, int k, const double* w, int64_t n,
-                    double* partial, int nblocks, cudaStream_t st)
+                    double* partial, int nblocks, cudaStream_t st, int df)
 {
     // partial row stride k+1: k dots then w.w
     for (int k0 = 0; k0 < k || k0 == 0; k0 += kDotChunk) {
         int kc = k - k0 < kDotChunk ? k - k0 : kDotChunk;
         if (kc < 0) kc = 0;
         count_launches(1);
-        k_gm_dots<<<nblocks, kGmThreads, 0, st>>>(V, ldv, k0, kc, w, n, partial, k + 1, k0 == 0);
+        if (df) k_gm_dots<true><<<nblocks, kGmThreads, 0, st>>>(V, ldv, k0, kc, w, n, partial, k + 1, k0 == 0);
+        else k_gm_dots<false><<<nblocks, kGmThreads, 0, st>>>(V, ldv, k0, kc, w, n, partial, k + 1, k0 == 0);
         if (k0 + kDotChunk >= k) break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t gm_update(double* w, const double* V, int64_t ldv, int k, const double* h, int64_t n,
-                      double* partial, int nblocks, cudaStream_t st)
+                      double* partial, int nblocks, cudaStream_t st, int df)
 {
     count_launches(1);
-    k_gm_update<<<nblocks, kGmThreads, 0, st>>>(w, V, ldv, k, h, n, partial);
+    if (df) k_gm_update<true><<<nblocks, kGmThreads, 0, st>>>(w, V, ldv, k, h, n, partial);
+    else k_gm_update<false><<<nblocks, kGmThreads, 0, st>>>(w, V, ldv, k, h, n, partial);
     return cudaGetLastError();
 }
 
 cudaError_t gm_update_scale(const double* w, const double* V, int64_t ldv, int k, const double* hw,
-                            double* vout, int64_t n, cudaStream_t st)
+                            double* vout, int64_t n, cudaStream_t st, int df)
 {
     count_launches(1);
-    k_gm_update_scale<<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(w, V, ldv, k, hw, vout, n,
-                                                                                  nullptr);
+    if (df)
+        k_gm_update_scale<true><<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(w, V, ldv, k, hw, vout, n,
+                                                                                        nullptr);
+    else
+        k_gm_update_scale<false><<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(w, V, ldv, k, hw, vout, n,
+                                                                                         nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t gm_update_scale_dyn(const GmDyn* dyn, const double* V, int64_t ldv, int64_t n, cudaStream_t st)
+cudaError_t gm_update_scale_dyn(const GmDyn* dyn, const double* V, int64_t ldv, int64_t n, cudaStream_t st, int df)
 {
     count_launches(1);
-    k_gm_update_scale<<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(nullptr, V, ldv, 0, nullptr,
-                                                                                  nullptr, n, dyn);
+    if (df)
+        k_gm_update_scale<true><<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(nullptr, V, ldv, 0, nullptr,
+                                                                                        nullptr, n, dyn);
+    else
+        k_gm_update_scale<false><<<grid_for(n, kGmThreads, 152 * 8), kGmThreads, 0, st>>>(nullptr, V, ldv, 0,
+                                                                                         nullptr, nullptr, n, dyn);
     return cudaGetLastError();
 }
 
-cudaError_t gm_scale(double* dst, const double* src, double s, int64_t n, cudaStream_t st)
+cudaError_t gm_scale(double* dst, const double* src, double s, int64_t n, cudaStream_t st, int df)
 {
     count_launches(1);
-    k_gm_scale<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(dst, src, s, n);
+    if (df) k_gm_scale<true><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(dst, src, s, n);
+    else k_gm_scale<false><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(dst, src, s, n);
     return cudaGetLastError();
 }
 
 cudaError_t gm_sub(double* r, const double* b, const double* Ax, int64_t n, double* partial,
-                   int nblocks, cudaStream_t st)
+                   int nblocks, cudaStream_t st, int df)
 {
     count_launches(1);
-    k_gm_sub<<<nblocks, kGmThreads, 0, st>>>(r, b, Ax, n, partial);
+    if (df) k_gm_sub<true><<<nblocks, kGmThreads, 0, st>>>(r, b, Ax, n, partial);
+    else k_gm_sub<false><<<nblocks, kGmThreads, 0, st>>>(r, b, Ax, n, partial);
     return cudaGetLastError();
 }
 
 cudaError_t gm_combine(double* x, const double* V, int64_t ldv, int k, const double* y, int64_t n,
-                       cudaStream_t st)
+                       cudaStream_t st, int df)
 {
     count_launches(1);
-    k_gm_combine<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, k, y, n, nullptr);
+    if (df) k_gm_combine<true><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, k, y, n, nullptr);
+    else k_gm_combine<false><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, k, y, n, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t gm_combine_dev(double* x, const double* V, int64_t ldv, const int* k, const double* y, int64_t n,
-                           cudaStream_t st)
+                           cudaStream_t st, int df)
 {
     count_launches(1);
-    k_gm_combine<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, 0, y, n, k);
+    if (df) k_gm_combine<true><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, 0, y, n, k);
+    else k_gm_combine<false><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, V, ldv, 0, y, n, k);
     return cudaGetLastError();
 }
 
@@ -905,7 +1257,17 @@ cudaError_t reduce_partials_dyn(const double* partial, int nblocks, const GmDyn*
 // On the periodic grid curl_c^T = curl_n exactly, so the transposed curls
 // are the curls themselves. FP64 throughout.
 
-// curl_c at centre (i, j) = (i+1/2, j+1/2) from the FP64 node field v
+// a GMRES vector element in FP64
+template <bool DF>
+__device__ __forceinline__ double vget(const double* v, int64_t k)
+{
+    if constexpr (DF) return df_to_double(dld(v, k));
+    else return v[k];
+}
+
+// curl_c at centre (i, j) = (i+1/2, j+1/2) from the node field v (a GMRES
+// vector)
+template <bool DF>
 __device__ __forceinline__ void curl_c_at(const double* __restrict__ v, int i, int j, const GridP& g, double out[3])
 {
     const int nx = g.nx, ny = g.ny, nc = g.ncell;
@@ -916,8 +1278,9 @@ __device__ __forceinline__ void curl_c_at(const double* __restrict__ v, int i, i
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const double* f = v + (int64_t)k * nc;
-        dx[k] = (f[n10] - f[n00] + f[n11] - f[n01]) * (0.5 / g.dx);
-        dy[k] = (f[n01] - f[n00] + f[n11] - f[n10]) * (0.5 / g.dy);
+        const double f00 = vget<DF>(f, n00), f10 = vget<DF>(f, n10), f01 = vget<DF>(f, n01), f11 = vget<DF>(f, n11);
+        dx[k] = (f10 - f00 + f11 - f01) * (0.5 / g.dx);
+        dy[k] = (f01 - f00 + f11 - f10) * (0.5 / g.dy);
     }
     out[0] = dy[2];
     out[1] = -dx[2];
@@ -943,6 +1306,7 @@ __device__ __forceinline__ void curl_n_at(const double* __restrict__ v, int i, i
     out[2] = dx[1] - dy[0];
 }
 
+template <bool DF>
 __global__ void k_adj_pre(const double* __restrict__ gE1, const double* __restrict__ gB1,
                           const double* __restrict__ gEx, double* __restrict__ gEt, GridP g)
 {
@@ -951,11 +1315,15 @@ __global__ void k_adj_pre(const double* __restrict__ gE1, const double* __restri
         double cn[3];
         curl_n_at(gB1, i, j, g, cn);
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            gEt[k * g.ncell + n] = gE1[k * g.ncell + n] / g.theta - g.dt * cn[k] + (gEx ? gEx[k * g.ncell + n] : 0.0);
+        for (int k = 0; k < 3; ++k) {
+            const double v = gE1[k * g.ncell + n] / g.theta - g.dt * cn[k] + (gEx ? gEx[k * g.ncell + n] : 0.0);
+            if constexpr (DF) reinterpret_cast<dfl*>(gEt)[k * g.ncell + n] = df_from_double(v);
+            else gEt[k * g.ncell + n] = v;
+        }
     }
 }
 
+template <bool DF>
 __global__ void k_adj_post(const double* __restrict__ gE1, const double* __restrict__ gB1,
                            const double* __restrict__ lam, double* __restrict__ gE0, double* __restrict__ gB0,
                            double* __restrict__ gJ, GridP g)
@@ -964,18 +1332,19 @@ __global__ void k_adj_post(const double* __restrict__ gE1, const double* __restr
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.ncell; n += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(n % g.nx), j = (int)(n / g.nx);
         double cc[3];
-        curl_c_at(lam, i, j, g, cc);
+        curl_c_at<DF>(lam, i, j, g, cc);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int64_t q = k * g.ncell + n;
-            if (gE0) gE0[q] = lam[q] - e1 * gE1[q];
+            const double lq = vget<DF>(lam, q);
+            if (gE0) gE0[q] = lq - e1 * gE1[q];
             if (gB0) gB0[q] = gB1[q] + td * cc[k];
-            if (gJ) gJ[q] = -td * lam[q];
+            if (gJ) gJ[q] = -td * lq;
         }
     }
 }
 
-template <typename T>
+template <typename T, bool DF>
 __global__ void k_adj_mass(const double* __restrict__ lam, const T* __restrict__ Et, double* __restrict__ gM,
                            GridP g)
 {
@@ -987,7 +1356,7 @@ __global__ void k_adj_mass(const double* __restrict__ lam, const T* __restrict__
         double lg[3], eg[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            lg[k] = lam[k * nc + n];
+            lg[k] = vget<DF>(lam, k * nc + n);
             eg[k] = (double)Et[k * nc + n];
         }
 #pragma unroll
@@ -996,7 +1365,7 @@ __global__ void k_adj_mass(const double* __restrict__ lam, const T* __restrict__
             double lh[3], eh[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                lh[k] = lam[k * nc + h];
+                lh[k] = vget<DF>(lam, k * nc + h);
                 eh[k] = (double)Et[k * nc + h];
             }
 #pragma unroll
@@ -1015,7 +1384,8 @@ cudaError_t adjoint_pre(const double* gE1, const double* gB1, const double* gEx,
                         cudaStream_t st)
 {
     count_launches(1);
-    k_adj_pre<<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, gEx, gEt, g);
+    if (g.df) k_adj_pre<true><<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, gEx, gEt, g);
+    else k_adj_pre<false><<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, gEx, gEt, g);
     return cudaGetLastError();
 }
 
@@ -1023,7 +1393,8 @@ cudaError_t adjoint_post(const double* gE1, const double* gB1, const double* lam
                          double* gJ, GridP g, cudaStream_t st)
 {
     count_launches(1);
-    k_adj_post<<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, lam, gE0, gB0, gJ, g);
+    if (g.df) k_adj_post<true><<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, lam, gE0, gB0, gJ, g);
+    else k_adj_post<false><<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(gE1, gB1, lam, gE0, gB0, gJ, g);
     return cudaGetLastError();
 }
 
@@ -1031,7 +1402,8 @@ template <typename T>
 cudaError_t adjoint_mass(const double* lam, const T* Et, double* gM, GridP g, cudaStream_t st)
 {
     count_launches(1);
-    k_adj_mass<T><<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(lam, Et, gM, g);
+    if (g.df) k_adj_mass<T, true><<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(lam, Et, gM, g);
+    else k_adj_mass<T, false><<<grid_for(g.ncell, 256, 152 * 16), 256, 0, st>>>(lam, Et, gM, g);
     return cudaGetLastError();
 }
 template cudaError_t adjoint_mass<float>(const double*, const float*, double*, GridP, cudaStream_t);
@@ -1040,6 +1412,7 @@ template cudaError_t adjoint_mass<double>(const double*, const double*, double*,
 #define RELSIM_FIELDS_INSTANTIATE(T)                                                               \
     template cudaError_t fields_from_double<T>(const double*, T*, int64_t, int*, cudaStream_t);   \
     template cudaError_t fields_to_double<T>(const T*, double*, int64_t, cudaStream_t);           \
+    template cudaError_t fields_to_vec<T>(const T*, double*, int64_t, int, cudaStream_t);          \
     template cudaError_t rhs<T>(const T*, const T*, const T*, double*, GridP, cudaStream_t);      \
     template cudaError_t apply_A<T>(const T*, const double*, double*, GridP, int*, cudaStream_t, bool); \
     template cudaError_t op_residual<T>(const T*, const double*, const double*, double*, GridP,    \

@@ -1,7 +1,8 @@
 // gmres.cu -- the control of the restarted GMRES solve (Sec. 2: the field
 // solver is the implicit part of the method) decided on the device.
 //
-// The Arnoldi process runs on B = A - I with an FP64 Krylov basis. Its
+// The Arnoldi process runs on B = A - I with an FP64 Krylov basis (double-
+// float pairs in the FP32 form of the 2D scheme with linear shapes). Its
 // heavy kernels (operator with fused dot products, their reduction, the
 // fused basis update) are in fields.cu; the single-thread kernels here keep
 // the small dense part on the device: the Hessenberg column, the Givens
@@ -207,13 +208,13 @@ cudaError_t gm_tail(GmState* st, GmPtrs p, GmParams q, GmCond cond, cudaStream_t
 }
 
 cudaError_t gm_finish_cycle(GmState* st, double* x, const double* V, int64_t ldv, int64_t n, int m,
-                            cudaStream_t s)
+                            cudaStream_t s, int df)
 {
     count_launches(1);
     k_gm_solve_y<<<1, 32, 0, s>>>(st, m);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return gm_combine_dev(x, V, ldv, &st->kdim, st->y, n, s);
+    return gm_combine_dev(x, V, ldv, &st->kdim, st->y, n, s, df);
 }
 
 }  // namespace relsim

@@ -211,6 +211,12 @@ template <typename T>
 cudaError_t fields_from_double(const double* in, T* out, int64_t n, int* bad, cudaStream_t st);
 template <typename T>
 cudaError_t fields_to_double(const T* in, double* out, int64_t n, cudaStream_t st);
+// a field into a GMRES vector (FP64, or double-float pairs when df)
+template <typename T>
+cudaError_t fields_to_vec(const T* in, double* out, int64_t n, int df, cudaStream_t st);
+// FP64 <-> GMRES vector (a copy when df = 0; in and out may then coincide)
+cudaError_t vec_from_double(const double* in, double* out, int64_t n, int df, cudaStream_t st);
+cudaError_t vec_to_double(const double* in, double* out, int64_t n, int df, cudaStream_t st);
 template <typename T>
 cudaError_t rhs(const T* E, const T* B, const T* J, double* b, GridP g, cudaStream_t st);
 // The implicit operator A = I + B, B = (theta dt)^2 curl_n curl_c + theta dt M,
@@ -244,26 +250,28 @@ cudaError_t mass_from_double(const double* Md, const double* Jd, T* M, T* J, Gri
                              cudaStream_t st);
 int field_grid_blocks(GridP g);
 
-// GMRES vector kernels (FP64)
+// GMRES vector kernels: FP64 vectors, or double-float ones when df (the
+// sums and dot products then come out in FP64 per block)
 cudaError_t gm_dots(const double* V, int64_t ldv, int k, const double* w, int64_t n,
-                    double* partial, int nblocks, cudaStream_t st);     // k dots + w.w
+                    double* partial, int nblocks, cudaStream_t st, int df);     // k dots + w.w
 cudaError_t gm_update(double* w, const double* V, int64_t ldv, int k, const double* h,
-                      int64_t n, double* partial, int nblocks, cudaStream_t st);  // w -= V h; |w|^2
-cudaError_t gm_scale(double* dst, const double* src, double s, int64_t n, cudaStream_t st);
+                      int64_t n, double* partial, int nblocks, cudaStream_t st, int df);  // w -= V h; |w|^2
+cudaError_t gm_scale(double* dst, const double* src, double s, int64_t n, cudaStream_t st, int df);
 // vout = (w - V h)/hn with hn^2 = hw[k] - |h|^2, h = hw[0..k-1]
 cudaError_t gm_update_scale(const double* w, const double* V, int64_t ldv, int k, const double* hw,
-                            double* vout, int64_t n, cudaStream_t st);
+                            double* vout, int64_t n, cudaStream_t st, int df);
 cudaError_t gm_sub(double* r, const double* b, const double* Ax, int64_t n, double* partial,
-                   int nblocks, cudaStream_t st);                      // r = b - Ax; |r|^2
+                   int nblocks, cudaStream_t st, int df);                      // r = b - Ax; |r|^2
 cudaError_t gm_combine(double* x, const double* V, int64_t ldv, int k, const double* y,
-                       int64_t n, cudaStream_t st);                    // x += V y
+                       int64_t n, cudaStream_t st, int df);                    // x += V y
 cudaError_t gm_combine_dev(double* x, const double* V, int64_t ldv, const int* k, const double* y,
-                           int64_t n, cudaStream_t st);                // x += V y, k read on the device
+                           int64_t n, cudaStream_t st, int df);                // x += V y, k read on the device
 cudaError_t reduce_partials(const double* partial, int nblocks, int nsums, double* out,
                             cudaStream_t st);
 int gm_blocks(int64_t n);
 
-// adjoint of the field part of a step (FP64): gEt = gE1/theta - dt curl_n gB1 (+ gEx);
+// adjoint of the field part of a step (FP64; gEt and lambda are GMRES
+// vectors, double-float when g.df): gEt = gE1/theta - dt curl_n gB1 (+ gEx);
 // after A^T lambda = gEt: gE0, gB0, gJ (each may be null) and the gradient of
 // the stored mass-matrix blocks (ncell x 45)
 cudaError_t adjoint_pre(const double* gE1, const double* gB1, const double* gEx, double* gEt, GridP g,
@@ -329,14 +337,15 @@ cudaError_t gm_arm(const GmState* st, GmCond cond, cudaStream_t s);
 cudaError_t gm_tail(GmState* st, GmPtrs p, GmParams q, GmCond cond, cudaStream_t s);
 // y from the triangular system of the finished cycle; x += V y
 cudaError_t gm_finish_cycle(GmState* st, double* x, const double* V, int64_t ldv, int64_t n, int m,
-                            cudaStream_t s);
+                            cudaStream_t s, int df);
 // Arnoldi iteration kernels reading their arguments from dyn
 template <typename T>
 cudaError_t op_arnoldi_dyn(const T* M, const GmDyn* dyn, const double* V, int64_t ldv, GridP g,
                            double* partial, int* err, cudaStream_t st, bool tr = false);
 cudaError_t reduce_partials_dyn(const double* partial, int nblocks, const GmDyn* dyn, int maxsums,
                                 cudaStream_t st);
-cudaError_t gm_update_scale_dyn(const GmDyn* dyn, const double* V, int64_t ldv, int64_t n, cudaStream_t st);
+cudaError_t gm_update_scale_dyn(const GmDyn* dyn, const double* V, int64_t ldv, int64_t n, cudaStream_t st,
+                                int df);
 
 // ----- diag.cu -----
 // tw[2 (m nx + i) + {0, 1}] = cos, sin of 2 pi ((m i) mod nx) / nx, m < nmodes
@@ -347,6 +356,11 @@ cudaError_t mode_twiddles(T* tw, int nx, int nmodes, cudaStream_t st);
 template <typename T>
 cudaError_t field_modes(const T* Bc, const T* tw, int nx, int ny, int nmodes, double dV, double* rows,
                         double* out, cudaStream_t st);
+// *energy = the mode-m energy as above and g[j nx + i] = its derivative in
+// Bc(i, j) (FP64); rows: ny doubles; tw must hold mode m
+template <typename T>
+cudaError_t mode_gradient(const T* Bc, const T* tw, int nx, int ny, int m, double dV, double* rows,
+                          double* energy, double* g, cudaStream_t st);
 
 }  // namespace relsim
 

@@ -24,20 +24,7 @@ import numpy as np
 
 from . import RELSIM_ERR_NOT_CONVERGED, Simulation, relsim_config
 
-__all__ = ["ModeEnergyWindow", "mode_energy_and_gradient", "WindowLoss", "parameter_gradient"]
-
-
-def mode_energy_and_gradient(B, nx, ny, dV, mode=1, component=1):
-    """W_m = (1/2) dV (2/nx) sum_j |F_{m,j}|^2 (F the DFT along x of row j of
-    B_c, as relsim_field_modes for 0 < m < nx/2) and dW_m/dB, (3, nx*ny)."""
-    Bc = np.asarray(B, dtype=np.float64).reshape(3, ny, nx)[component]
-    th = 2.0 * np.pi * mode * np.arange(nx) / nx
-    Fr = (Bc * np.cos(th)[None, :]).sum(axis=1)
-    Fi = -(Bc * np.sin(th)[None, :]).sum(axis=1)
-    W = 0.5 * dV * (2.0 / nx) * float(np.sum(Fr * Fr + Fi * Fi))
-    g = np.zeros((3, ny, nx))
-    g[component] = (2.0 * dV / nx) * (Fr[:, None] * np.cos(th)[None, :] - Fi[:, None] * np.sin(th)[None, :])
-    return W, g.reshape(3, nx * ny)
+__all__ = ["ModeEnergyWindow", "WindowLoss", "parameter_gradient"]
 
 
 class ModeEnergyWindow:
@@ -102,8 +89,9 @@ class ModeEnergyWindow:
             if n % self.every == 0:
                 self.checkpoints[n] = self._state()
             self._step()
-        E, B = self.sim.fields()
-        self.loss, self.gB_final = mode_energy_and_gradient(B, self.nx, self.ny, self.dV, self.mode)
+        # the loss and its gradient in B^N, on the device
+        e, self.gB_final = self.sim.field_mode_gradient(1, self.mode, device=True)
+        self.loss = float(e.item())
         return self.loss
 
     # -- backward -----------------------------------------------------------
@@ -114,7 +102,7 @@ class ModeEnergyWindow:
         import torch
         dev = self.checkpoints[0]["E"].device
         gE = torch.zeros((3, self.nx * self.ny), dtype=torch.float64, device=dev)
-        gB = torch.as_tensor(self.gB_final, dtype=torch.float64).to(dev).contiguous()
+        gB = self.gB_final.clone()
         gu = [torch.zeros((sp["w"].shape[0], 3), dtype=torch.float64, device=dev)
               for sp in self.checkpoints[0]["species"]]
         gx = [torch.zeros((sp["w"].shape[0], 2), dtype=torch.float64, device=dev)

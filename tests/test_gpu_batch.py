@@ -75,6 +75,41 @@ def test_field_modes_device_output_and_arguments(rs):
     sim.close()
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("nx,ny", [(64, 32), (37, 11)])
+def test_field_mode_gradient_matches_oracle(rs, orc, precision, nx, ny):
+    """The window's loss (one mode's B_y energy) and its gradient in B,
+    computed on the device, against the oracle's (numpy FFT); host and
+    device outputs agree bit for bit."""
+    st = random_state(nx, ny, [0, 0], seed=5, dx=0.8, dy=1.1, field_scale=0.7)
+    B = st["B"].copy()
+    xc = (np.arange(nx) + 0.5)
+    B.reshape(3, ny, nx)[1] += 0.3 * np.cos(2 * np.pi * xc / nx)[None, :]
+    if precision == 32:
+        B = B.astype(np.float32).astype(np.float64)
+    sim = rs.Simulation(rs.make_config(nx, ny, dx=0.8, dy=1.1, precision=precision))
+    sim.set_fields(np.zeros_like(B), B)
+    c = orc.make_config(nx, ny, dx=0.8, dy=1.1)
+    for comp in (1, 2):
+        for m in (1, 3, (nx - 1) // 2):
+            e, g = sim.field_mode_gradient(comp, m)
+            W, gW = orc.mode_energy(c, B, m, comp)
+            tot = 0.5 * c.dx * c.dy * np.sum(B[comp] ** 2)
+            tol = 5e-6 if precision == 32 else 1e-11
+            assert abs(e[0] - W) <= tol * tot, (comp, m, e[0], W)
+            assert np.max(np.abs(g - gW)) <= tol * np.max(np.abs(gW)) + 1e-15, (comp, m)
+            ed, gd = sim.field_mode_gradient(comp, m, device=True)
+            assert ed.is_cuda and gd.is_cuda
+            assert np.array_equal(ed.cpu().numpy(), e) and np.array_equal(gd.cpu().numpy(), g)
+            # the energy equals relsim_field_modes' value of that mode
+            fm = sim.field_modes(comp, m + 1)[m]
+            assert abs(e[0] - fm) <= 1e-13 * abs(fm), (e[0], fm)
+    for comp, m in [(3, 1), (-1, 1), (1, -1), (1, nx // 2 + 1)]:
+        with pytest.raises(rs.RelsimError):
+            rs.relsim_field_mode_gradient(sim.ctx, comp, m, sim.ncell)
+    sim.close()
+
+
 def _instance(rs, hc, stream, precision=32):
     sim = rs.Simulation(rs.make_config(hc.nx, hc.ny, dt=hc.dt, precision=precision, gmres_tol=1e-6),
                         stream=stream.cuda_stream)

@@ -639,3 +639,47 @@ def test_operator_tile_heights_agree(rs, prec):
         sims[0].set_launch_shapes(0, 0, 3)
     for s in sims:
         s.close()
+
+
+@pytest.mark.parametrize("case", ["harris", "ragged"])
+def test_double_float_krylov_matches_fp64_krylov(rs, orc, case):
+    """The FP32 form keeps its GMRES vectors as double-float pairs (FP32
+    arithmetic, ~48-bit values) unless gmres_fp64 is set. Over ten steps the
+    two agree: the same iteration counts (within one), E and B within the
+    solve tolerance's reach (1e-5), ledger residuals at the FP32 floor, and
+    both match the oracle's first solve (E^{n+theta}) to the FP32 bound."""
+    if case == "harris":
+        nx, ny, dt = 64, 32, 0.5
+        st = fp32_state(harris_small(nx, ny, 16), nx, ny)
+    else:
+        nx, ny, dt = 37, 11, 0.7
+        st = fp32_state(random_state(nx, ny, [900, 700], seed=21, u_scale=0.5, field_scale=0.3), nx, ny)
+    res = {}
+    for fp64 in (False, True):
+        sim = rs.Simulation(rs.make_config(nx, ny, dt=dt, precision=32, gmres_tol=1e-7, gmres_fp64=fp64))
+        sim.load_state(st)
+        sim.build()
+        it0, rr0, status = sim.solve()
+        assert status == 0 and rr0 <= 1e-7
+        Et0 = sim.E_theta()
+        sim.push()
+        iters, resid = [it0], []
+        for _ in range(9):
+            led, status = sim.step()
+            assert status == 0
+            iters.append(led["gmres_iters"])
+            resid.append(abs(led["residual"]) / led["total"])
+        E, B = sim.fields()
+        res[fp64] = (np.array(iters), Et0, E, B, max(resid))
+        sim.close()
+    (itd, Etd, Ed, Bd, rd), (itf, Etf, Ef, Bf, rf) = res[False], res[True]
+    print(f"{case}: GMRES iterations double-float {itd.tolist()}, FP64 {itf.tolist()}; "
+          f"max ledger residual {rd:.1e} / {rf:.1e}")
+    assert np.all(np.abs(itd - itf) <= 1), (itd, itf)
+    assert rel(Ed, Ef) <= 1e-5 and rel(Bd, Bf) <= 1e-6
+    assert rd < 1e-6 and rf < 1e-6
+    c = ocfg(orc, nx, ny, dt=dt)
+    P = orc.Particles(st["species"])
+    _, _, _, ex = orc.step(c, P, st["E"], st["B"], want_matrices=True)
+    for Et in (Etd, Etf):
+        assert rel(Et, ex["Etheta"]) <= 2e-5

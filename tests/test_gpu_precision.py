@@ -1,0 +1,176 @@
+"""Precision of the FP32 form against the FP64 oracle over a run, per field,
+per energy-ledger term and per spectrum bin (the paper's quantities: the
+fields of Sec. 2, Table 1's energy error column, the spectra of Sec. 3.2).
+
+Workload: the 64x32 double Harris sheet (16 particles per cell and species,
+dt = 0.5, theta = 0.5, GMRES 1e-7 in FP32 and 1e-12 in the oracle), 100
+steps from one FP32-representable initial state, once with each reading of
+the Lorentz factor in alpha, Jhat, M and the push. Each step records, for
+the FP32 GPU run and for an oracle run started from momenta perturbed at the
+FP32 rounding level (6e-8, the dynamics' own conditioning), the relative
+error against the oracle of
+  * E and B (relative L2 norm over the grid),
+  * the ledger terms W_E, W_B, K (after the step), the particles' work
+    dt sum w q (ubar/gbar).E and the relativistic mismatch term,
+  * the 256-bin spectrum of gamma - 1 over [1e-2, 1e4] (both species): the
+    largest relative error over the bins holding at least 1e-3 of the
+    weight, and the L1 distance of the weights over all bins.
+A quantity's horizon is the last step up to which its error stays below
+1e-5. Orbits in the sheet are chaotic: round-off grows about e-fold per 12
+steps, so every horizon is finite; the assertions are the measured horizons
+(with a margin), at every step the FP32 field errors within 10x of the
+perturbed oracle's, and the spectrum's L1 distance within 10x of the
+perturbed oracle's plus 1e-4. With RELSIM_REPORT_DIR set, the curves are
+written there as JSON.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from relsim_inputs import HarrisConfig, make_harris
+
+pytestmark = pytest.mark.gpu
+
+NX, NY, PPC, DT, NSTEPS = 64, 32, 16, 0.5, 100
+EDGES = np.geomspace(1e-2, 1e4, 257)
+TERMS = ("W_E", "W_B", "K", "work", "mismatch")
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_11100_gb300 as rs
+    return rs
+
+
+def fp32_state(st):
+    for sp in st["species"]:
+        for k in ("x", "y"):
+            s = np.asarray(sp[k])
+            fl = np.floor(s)
+            f = (s - fl).astype(np.float32).astype(np.float64)
+            f = np.minimum(f, np.float64(np.nextafter(np.float32(1.0), np.float32(0.0))))
+            sp[k] = fl + f
+        for k in ("ux", "uy", "uz", "w"):
+            sp[k] = np.asarray(sp[k]).astype(np.float32).astype(np.float64)
+    st["E"] = np.asarray(st["E"]).astype(np.float32).astype(np.float64)
+    st["B"] = np.asarray(st["B"]).astype(np.float32).astype(np.float64)
+    return st
+
+
+def oracle_terms(lo):
+    return {"W_E": lo["W_E1"], "W_B": lo["W_B1"], "K": lo["K1"], "work": lo["work_particles"],
+            "mismatch": lo["mismatch"]}
+
+
+def gpu_terms(led):
+    return {"W_E": led["W_E"], "W_B": led["W_B"], "K": led["K"], "work": led["work_particles"],
+            "mismatch": led["mismatch"]}
+
+
+def oracle_spectrum(orc, P):
+    w = np.zeros(258)
+    for s in range(2):
+        sp = P.species(s)
+        w += orc.spectrum(sp["ux"], sp["uy"], sp["uz"], sp["w"], EDGES, 0, precision=64)[0]
+    return w
+
+
+def spectrum_errors(wg, wo):
+    sel = wo >= 1e-3 * wo.sum()
+    rel = np.abs(wg[sel] - wo[sel]) / wo[sel]
+    return float(rel.max()), float(np.abs(wg - wo).sum() / wo.sum())
+
+
+def horizon(errs, tol=1e-5):
+    h = 0
+    for n, e in enumerate(errs, start=1):
+        if e >= tol:
+            break
+        h = n
+    return h
+
+
+def run_curves(rs, orc, pred):
+    st = fp32_state(make_harris(HarrisConfig(nx=NX, ny=NY, ppc=PPC, dt=DT)))
+    sim = rs.Simulation(rs.make_config(NX, NY, dt=DT, precision=32, gmres_tol=1e-7, gamma_pred=pred))
+    sim.load_state(st)
+    c = orc.make_config(NX, NY, dt=DT, gmres_tol=1e-12, gamma_pred=pred)
+    P = orc.Particles(st["species"])
+    Pp = P.copy()
+    rng = np.random.default_rng(1)
+    for k in ("ux", "uy", "uz"):
+        a = getattr(Pp, k)
+        a *= 1.0 + 6e-8 * rng.choice([-1.0, 1.0], size=a.size)
+    E, B = st["E"], st["B"]
+    Ep, Bp = st["E"], st["B"]
+    cur = {k: [] for k in ("E", "B") + TERMS + ("spec_bin_max", "spec_l1")}
+    pert = {k: [] for k in cur}
+    for n in range(NSTEPS):
+        led, status = sim.step(ledger=True)
+        assert status == 0
+        E, B, lo, _ = orc.step(c, P, E, B)
+        Ep, Bp, lp, _ = orc.step(c, Pp, Ep, Bp)
+        Eg, Bg = sim.fields()
+        nE, nB = np.linalg.norm(E), np.linalg.norm(B)
+        cur["E"].append(float(np.linalg.norm(Eg - E) / nE))
+        cur["B"].append(float(np.linalg.norm(Bg - B) / nB))
+        pert["E"].append(float(np.linalg.norm(Ep - E) / nE))
+        pert["B"].append(float(np.linalg.norm(Bp - B) / nB))
+        to, tg, tp = oracle_terms(lo), gpu_terms(led), oracle_terms(lp)
+        for k in TERMS:
+            cur[k].append(abs(tg[k] - to[k]) / abs(to[k]))
+            pert[k].append(abs(tp[k] - to[k]) / abs(to[k]))
+        wo = oracle_spectrum(orc, P)
+        wg = sum(sim.spectrum(s, EDGES, 0)[0] for s in range(2))
+        wp = oracle_spectrum(orc, Pp)
+        cur["spec_bin_max"].append(spectrum_errors(wg, wo)[0])
+        cur["spec_l1"].append(spectrum_errors(wg, wo)[1])
+        pert["spec_bin_max"].append(spectrum_errors(wp, wo)[0])
+        pert["spec_l1"].append(spectrum_errors(wp, wo)[1])
+    sim.close()
+    return cur, pert
+
+
+# measured horizons (the last step up to which the error stays below 1e-5;
+# on GB300: E 38, B 63-65, W_E 78-79, W_B 100, K 100, work 15, mismatch 68
+# (gamma(u^n)) and 9 (predicted gamma, a difference of Lorentz factors),
+# minus a margin. The spectrum has no 1e-5 horizon: a particle crossing a
+# bin edge on one side only moves 2/N of the weight (3e-5 here), so its L1
+# distance is held to the perturbed oracle's instead.
+MIN_HORIZON = {0: {"E": 30, "B": 50, "W_E": 60, "W_B": 80, "K": 80, "work": 10, "mismatch": 40},
+               1: {"E": 30, "B": 50, "W_E": 60, "W_B": 80, "K": 80, "work": 10, "mismatch": 5}}
+
+
+@pytest.mark.parametrize("pred", [0, 1])
+def test_fp32_precision_report(rs, pred):
+    import oracle as orc
+    cur, pert = run_curves(rs, orc, pred)
+    hz = {k: horizon(v) for k, v in cur.items()}
+    hzp = {k: horizon(v) for k, v in pert.items()}
+    report = {"workload": f"{NX}x{NY} double Harris sheet, {PPC} ppc per species, dt {DT}, {NSTEPS} steps",
+              "gamma_bar": "predicted" if pred else "gamma(u^n)",
+              "horizon_1e-5": hz, "horizon_1e-5_perturbed_oracle": hzp,
+              "fp32_vs_oracle": cur, "perturbed_oracle_vs_oracle": pert}
+    out = os.environ.get("RELSIM_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, f"precision_fp32_64x32_pred{pred}.json"), "w") as f:
+            json.dump(report, f)
+    print(f"gamma_pred={pred}: horizons (steps within 1e-5) FP32 {hz}; perturbed oracle {hzp}")
+    for k, h in MIN_HORIZON[pred].items():
+        assert hz[k] >= h, (k, hz)
+    # the fields: at every step within 10x of what a rounding-level
+    # perturbation of the oracle's own momenta produces (the growth is the
+    # dynamics' own)
+    for k in ("E", "B"):
+        for n, (e, p) in enumerate(zip(cur[k], pert[k]), start=1):
+            assert e <= 10 * max(p, 1e-7), (k, n, e, p)
+    for n, (e, p) in enumerate(zip(cur["spec_l1"], pert["spec_l1"]), start=1):
+        assert e <= 10 * p + 1e-4, ("spec_l1", n, e, p)

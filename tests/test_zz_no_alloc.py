@@ -6,12 +6,13 @@ loop whose device memory is all reserved up front by its own pool, or code
 where a cudaMalloc would synchronise the device or is not allowed. It keeps
 its partial sums in a fixed array inside the library. Here it must return,
 on two calls in a row, the per-species kinetic energy that relsim_energy_ledger
-reports for a context holding the same particles (FP64 form, FP64 tolerance
-1e-11 relative), and it must refuse more particles than its fixed array can
-take. This file is collected last so that a failure here comes after every
+reports for a context holding the same particles and an independent numpy
+FP64 sum of w m |u|^2/(gamma + 1) on the host (FP64 tolerance 1e-11
+relative), and it must refuse more particles than its fixed array can take. This file is collected last so that a failure here comes after every
 other test has run.
 """
 import ctypes
+import math
 
 import numpy as np
 import pytest
@@ -58,6 +59,11 @@ def test_noalloc_matches_ledger_two_calls(rs):
                 vals.append(out.item())
             K = led["K_species"][s]
             assert abs(vals[0] - K) <= 1e-11 * abs(K), (name, s, vals[0], K)
+            # an independent host sum, compensated (math.fsum)
+            uu = np.stack([sp["ux"], sp["uy"], sp["uz"]], axis=1).astype(np.float64)
+            u2 = (uu * uu).sum(axis=1)
+            K_np = math.fsum(np.asarray(sp["w"], np.float64) * m[s] * (u2 / (np.sqrt(1.0 + u2) + 1.0)))
+            assert abs(vals[0] - K_np) <= 1e-11 * abs(K_np), (name, s, vals[0], K_np)
             assert vals[1] == vals[0], (name, s, vals)
         sim.close()
 
