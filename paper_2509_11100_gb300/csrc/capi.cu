@@ -340,7 +340,8 @@ int ensure_species(relsim_ctx* c, int s, int64_t n)
     const int narr = c->g.dim == 3 ? 7 : 6;
     for (int b = 0; b < 2; ++b) {
         for (int k = 0; k < narr; ++k) TRY(dalloc(c, &sp.a[b][k], c->esz * (size_t)(n + 8)));
-        if (c->cfg.track_ids) TRY(dalloc(c, &sp.id[b], sizeof(int32_t) * (size_t)n));
+        // 8 elements of slack: bulk copies round a range out to 16 bytes
+        if (c->cfg.track_ids) TRY(dalloc(c, &sp.id[b], sizeof(int32_t) * (size_t)(n + 8)));
     }
     sp.cap = n;
     return RELSIM_OK;
@@ -693,7 +694,9 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
     int dep_c[ncand], push_c[ncand];
     for (int k = 0; k < ncand; ++k) {
         dep_c[k] = lin2 ? (k + 1) * nsm : (2 << k) * nsm;   // 1..4 blocks per SM; 3D, quadratic: 2, 4, 8, 16
-        push_c[k] = (4 << k) * nsm;                         // 4, 8, 16, 32 per SM
+        // 2D linear: the resident blocks per SM (3 in FP32, 2 in FP64: the
+        // staged push is bound by shared memory) times 1, 2, 4, 8; others 4 .. 32
+        push_c[k] = lin2 ? ((c->prec == 32 ? 3 : 2) << k) * nsm : (4 << k) * nsm;
     }
     TRY(ensure_partial(c, (int64_t)push_blocks_cap(c, push_c[ncand - 1]) * (kLedgerSpecies - 1)));
     relsim_tuning t;
@@ -765,7 +768,7 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
                                  nbp, c->st));
                 else
                     CK(push_sort<T>(src, dst, sp.start, c->n9, c->off9, E, B, c->En ? E : nullptr, c->g, sc,
-                                    c->partial, nbp, c->st));
+                                    c->partial, nbp, c->dpush, c->st));
                 return RELSIM_OK;
             },
             &t.push_ms[k]);
@@ -1092,7 +1095,7 @@ int push_enqueue(relsim_ctx* c)
             // K0 of this step is the kinetic energy the last push (or load) left
             CK(cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
             CK(push_sort<T>(src, dst, sp.start, c->n9, c->off9, Eth, B, (const T*)c->En, c->g, sc, c->partial,
-                            nbp, c->st));
+                            nbp, c->dpush, c->st));
             CK(reduce_partials(c->partial, nbp, kLedgerSpecies - 1, led + 1, c->st));
             PROF_END();
             PROF_BEGIN(RELSIM_PROF_SORT_TABLES);
@@ -1688,7 +1691,7 @@ int mode_grad_impl(relsim_ctx* c, int comp, int mode, double* energy, double* gB
 int check_push(relsim_ctx* c)
 {
     if (*c->hpush & 2)
-        return fail(c, RELSIM_ERR_TIMEOUT, "a shared-memory staging wait gave up (deposit or operator)");
+        return fail(c, RELSIM_ERR_TIMEOUT, "a shared-memory staging wait gave up (deposit, push or operator)");
     if (*c->hpush)
         return fail(c, RELSIM_ERR_INTERNAL, "particle sort: the moves counted and the new cell starts disagreed");
     return RELSIM_OK;
