@@ -656,9 +656,11 @@ struct PushTile {
 // One warp's shared memory in k_push_sort: the input of two cell groups in
 // flight (bulk copies of the six arrays, and the ids when tracked), the
 // pushed records written back in place, the per-particle sort keys, the
-// unit's field tiles and the cell starts of two units.
+// unit's field tiles and the cell starts of two units. Aligned to 16 bytes
+// (the size too), so that every warp's staged arrays start on the 16-byte
+// boundary the bulk copies need.
 template <typename T, bool PRED>
-struct PushWarp {
+struct __align__(16) PushWarp {
     static constexpr int C = PushCfg<T>::cap, S = PushCfg<T>::slot;
     T a[2][6][S];
     int32_t id[2][S];
@@ -678,6 +680,13 @@ struct PushSmem {
     PushWarp<T, PRED> w[PushCfg<T>::warps];
     double red[32 * kLedger];
 };
+static_assert(sizeof(PushWarp<float, false>) % 16 == 0 && sizeof(PushWarp<float, true>) % 16 == 0 &&
+                  sizeof(PushWarp<double, false>) % 16 == 0 && sizeof(PushWarp<double, true>) % 16 == 0 &&
+                  (2 * 6 * PushCfg<float>::slot * sizeof(float)) % 16 == 0 &&
+                  (2 * 6 * PushCfg<double>::slot * sizeof(double)) % 16 == 0 &&
+                  (PushCfg<float>::slot * sizeof(float)) % 16 == 0 && (PushCfg<double>::slot * sizeof(double)) % 16 == 0 &&
+                  (PushCfg<float>::slot * sizeof(int32_t)) % 16 == 0,
+              "bulk-copy destinations on 16-byte boundaries");
 // min_blocks blocks per SM within 228 KB of shared memory (1 KB reserved per block)
 static_assert(PushCfg<float>::min_blocks * (sizeof(PushSmem<float, true>) + 1024) <= 228 * 1024 &&
                   PushCfg<double>::min_blocks * (sizeof(PushSmem<double, true>) + 1024) <= 228 * 1024,
