@@ -694,9 +694,7 @@ int autotune_impl(relsim_ctx* c, relsim_tuning* out)
     int dep_c[ncand], push_c[ncand];
     for (int k = 0; k < ncand; ++k) {
         dep_c[k] = lin2 ? (k + 1) * nsm : (2 << k) * nsm;   // 1..4 blocks per SM; 3D, quadratic: 2, 4, 8, 16
-        // 2D linear: the resident blocks per SM (3 in FP32, 2 in FP64: the
-        // staged push is bound by shared memory) times 1, 2, 4, 8; others 4 .. 32
-        push_c[k] = lin2 ? ((c->prec == 32 ? 3 : 2) << k) * nsm : (4 << k) * nsm;
+        push_c[k] = (4 << k) * nsm;                         // 4, 8, 16, 32 per SM
     }
     TRY(ensure_partial(c, (int64_t)push_blocks_cap(c, push_c[ncand - 1]) * (kLedgerSpecies - 1)));
     relsim_tuning t;

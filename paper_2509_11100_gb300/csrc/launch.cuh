@@ -169,7 +169,7 @@ cudaError_t deposit(const DepositSpecies<T>& sp, const T* B, const T* En, T* M, 
 template <typename T>
 cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* n9, int32_t* off9,
                       const T* Eth, const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial,
-                      int lsum_blocks, int* err, cudaStream_t st);   // err bit 2: a staging wait gave up
+                      int lsum_blocks, int* err, cudaStream_t st);   // err: reserved for a bounded wait
 // general path (moves longer than one cell): pushed particles to the same
 // index of dst, their new cell to key; ledger sums as above
 template <typename T>
@@ -195,7 +195,7 @@ cudaError_t push_adjoint(PArrays<T> src, const int32_t* start, const double* gu1
 template <typename T>
 cudaError_t permute(PArrays<T> src, PArrays<T> dst, const int32_t* start_new, const int32_t* n9,
                     const int32_t* off9, GridP g, int* err, cudaStream_t st);
-int push_grid_blocks(GridP g, int precision, int cap = 0);   // cap: most blocks (0: the blocks resident at once)
+int push_grid_blocks(GridP g, int precision, int cap = 0);   // cap: most blocks (0: 152 x 16)
 // weighted and counted histogram of gamma - 1 (variable 0) or |u| (1) over
 // nbins bins between ascending edges (nbins + 1, rounded up to T), plus the
 // bins below and above them: wsum/cnt[nbins + 2], accumulated (zero them)

@@ -295,6 +295,25 @@ template <typename T>
 struct Moments {
     T S[81];
     T Jm[12];
+    T pad;
+    // flat order: S[k][q] at k*9 + q, then the 12 currents, then padding
+    // (index e a compile-time constant after unrolling: a register)
+    static constexpr int kFlat = 96;
+    __device__ __forceinline__ T& at(int e) { return e < 81 ? S[e] : (e < 93 ? Jm[e - 81] : pad); }
+    // flat entry e: a moment (k, q; it = -1) or a current (it >= 0); false
+    // for padding
+    __device__ __forceinline__ static bool locate(int e, int& k, int& q, int& it)
+    {
+        if (e < 81) {
+            k = e / 9;
+            q = e - 9 * k;
+            it = -1;
+            return true;
+        }
+        it = e - 81;
+        k = q = 0;
+        return it < 12;
+    }
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
@@ -327,6 +346,27 @@ template <>
 struct Moments<float> {
     float2 S2[45];   // S2[k*5 + h] = (S[k][2h], S[k][2h+1]); S[k][9] is padding
     float Jm[12];
+    float pad;
+    // flat order: S[k][q] at k*10 + q (q = 9: the zero padding), then the 12
+    // currents, then padding (index e a compile-time constant after
+    // unrolling: a register)
+    static constexpr int kFlat = 104;
+    __device__ __forceinline__ float& at(int e)
+    {
+        return e < 90 ? ((e & 1) ? S2[e >> 1].y : S2[e >> 1].x) : (e < 102 ? Jm[e - 90] : pad);
+    }
+    __device__ __forceinline__ static bool locate(int e, int& k, int& q, int& it)
+    {
+        if (e < 90) {
+            k = e / 10;
+            q = e - 10 * k;
+            it = -1;
+            return q < 9;
+        }
+        it = e - 90;
+        k = q = 0;
+        return it < 12;
+    }
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
@@ -364,6 +404,36 @@ struct Moments<float> {
         }
     }
 };
+
+// Sum over the 8 lanes of a group (lane bits 0-2) of the NV flat entries of
+// the accumulators, each lane keeping a different eighth: three halving
+// exchanges (xor 1, 2, 4), each lane sending the half it gives up. Afterwards
+// lane gl holds in entries 0 .. NV/8-1 the totals of entries base + t, base =
+// (gl&1) NV/2 + (gl>>1&1) NV/4 + (gl>>2&1) NV/8. The padding entries are set
+// to zero first.
+template <typename T>
+__device__ __forceinline__ void reduce_scatter8(Moments<T>& m, int gl)
+{
+    constexpr int NV = Moments<T>::kFlat;
+    static_assert(NV % 8 == 0, "eight equal shares");
+    m.pad = T(0);
+    const bool b0 = gl & 1, b1 = (gl >> 1) & 1, b2 = (gl >> 2) & 1;
+#pragma unroll
+    for (int t = 0; t < NV / 2; ++t) {
+        const T lo = m.at(t), hi = m.at(NV / 2 + t);
+        m.at(t) = (b0 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b0 ? lo : hi, 1);
+    }
+#pragma unroll
+    for (int t = 0; t < NV / 4; ++t) {
+        const T lo = m.at(t), hi = m.at(NV / 4 + t);
+        m.at(t) = (b1 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b1 ? lo : hi, 2);
+    }
+#pragma unroll
+    for (int t = 0; t < NV / 8; ++t) {
+        const T lo = m.at(t), hi = m.at(NV / 8 + t);
+        m.at(t) = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
+    }
+}
 
 template <typename T, bool PRED>
 __device__ __forceinline__ void deposit_particle(const T fx, const T fy, const T ux, const T uy, const T uz,
@@ -500,26 +570,38 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
             }
         }
         if (s == nsp - 1) {
-            acc.template group_reduce<G>();
+            // the group's sums, spread over its lanes: each of the G = 8
+            // lanes ends with NV/8 totals, which it flushes with one atomic
+            // each (two for the moment that two node pairs share)
+            constexpr int NV = Moments<T>::kFlat, NL = NV / G;
+            reduce_scatter8<T>(acc, gl);
             if (valid) {
                 const int i = un.i0 + grp, j = un.j;
                 const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
                 const int n00 = j * nx + i, n10 = j * nx + i1, n01 = j1 * nx + i, n11 = j1 * nx + i1;
-                // (destination node, half offset, moment k) of the ten node pairs
-                const int pn[10] = {n00, n00, n00, n00, n10, n10, n10, n01, n01, n11};
-                constexpr int po[10] = {0, 1, 3, 4, 0, 2, 3, 0, 1, 0};
-                constexpr int pk[10] = {0, 3, 1, 4, 6, 4, 7, 2, 5, 8};
+                const int base = (gl & 1) * (NV / 2) + ((gl >> 1) & 1) * (NV / 4) + ((gl >> 2) & 1) * (NV / 8);
 #pragma unroll
-                for (int it = 0; it < 90; ++it) {
-                    if (it % G == gl) {
-                        const int pr = it / 9, q = it % 9;
-                        atomicAdd(M + (int64_t)pn[pr] * kMBlock + po[pr] * 9 + q, acc.get(pk[pr], q));
+                for (int t = 0; t < NL; ++t) {
+                    int k, q, it;
+                    if (!Moments<T>::locate(base + t, k, q, it)) continue;
+                    if (it < 0) {
+                        // moment S[k][q] -> the node pair(s) with that moment:
+                        // pair pr = (k-th entry of 0 2 7 1 3 8 4 6 9), and pair
+                        // 5 as well for k = 4; pairs 0-3 start at n00, 4-6 at
+                        // n10, 7-8 at n01, 9 at n11; half offsets 0 1 3 4 0 2 3 0 1 0
+                        constexpr unsigned long long kPr = 0x964831720ull, kPo = 0x0103204310ull;
+                        const int pr = (int)((kPr >> (4 * k)) & 0xF);
+                        const int po = (int)((kPo >> (4 * pr)) & 0xF);
+                        const int node = pr <= 3 ? n00 : (pr <= 6 ? n10 : (pr <= 8 ? n01 : n11));
+                        atomicAdd(M + (int64_t)node * kMBlock + po * 9 + q, acc.at(t));
+                        if (k == 4) atomicAdd(M + (int64_t)n10 * kMBlock + 2 * 9 + q, acc.at(t));
+                    } else {
+                        // current: entry it = node a (n00 n10 n01 n11) * 3 + component
+                        const int a = it / 3, comp = it - 3 * a;
+                        const int node = a == 0 ? n00 : (a == 1 ? n10 : (a == 2 ? n01 : n11));
+                        atomicAdd(J + (int64_t)comp * nc + node, acc.at(t));
                     }
                 }
-                const int jn[4] = {n00, n10, n01, n11};
-#pragma unroll
-                for (int it = 0; it < 12; ++it)
-                    if ((90 + it) % G == gl) atomicAdd(J + (int64_t)(it % 3) * nc + jn[it / 3], acc.Jm[it]);
             }
         }
         __syncthreads();   // buffer b and the B tile are free for the next stage
@@ -549,15 +631,13 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
 // takes the general path (k_push_general + radix sort).
 
 template <typename T> struct PushCfg {
-    static constexpr int warps = 4;
+    static constexpr int warps = 4;                        // static shared memory < 48 KB
     static constexpr int threads = 32 * warps;
-    static constexpr int min_blocks = sizeof(T) == 4 ? 3 : 2;   // bounded by the dynamic shared memory
-    static constexpr int cap = sizeof(T) == 4 ? 240 : 128;      // particles of a cell group staged per warp
-    static constexpr int slot = cap + 2 * (16 / sizeof(T));     // staged elements per array (bulk-copy slack)
+    static constexpr int min_blocks = sizeof(T) == 4 ? 5 : 2;
+    static constexpr int cap = sizeof(T) == 4 ? 256 : 128;   // particles of a cell group staged per warp
 };
 constexpr int kGroupMax = 8;    // cells staged together at most
 constexpr int kLedger = 4;      // dK, work, mismatch, K1 (K0 is the previous K1)
-constexpr long long kPushMaxPolls = 1ll << 26;   // bounded mbarrier wait
 
 template <typename T>
 struct Pushed {
@@ -653,52 +733,19 @@ struct PushTile {
     T E[3][2][kTE];
 };
 
-// One warp's shared memory in k_push_sort: the input of two cell groups in
-// flight (bulk copies of the six arrays, and the ids when tracked), the
-// pushed records written back in place, the per-particle sort keys, the
-// unit's field tiles and the cell starts of two units. Aligned to 16 bytes
-// (the size too), so that every warp's staged arrays start on the 16-byte
-// boundary the bulk copies need.
-template <typename T, bool PRED>
-struct __align__(16) PushWarp {
-    static constexpr int C = PushCfg<T>::cap, S = PushCfg<T>::slot;
-    T a[2][6][S];
-    int32_t id[2][S];
-    uint64_t mb[2];
-    int p0a[2];                  // the aligned first particle of each staged range
+// a cell's pushed particles, staged for the write back in direction order
+// a group of cells' pushed particles, staged for the write back in cell and
+// direction order
+template <typename T>
+struct PushStage {
+    static constexpr int C = PushCfg<T>::cap;
+    T fx[C], fy[C], ux[C], uy[C], uz[C], w[C];
+    int32_t id[C];
     uint8_t dir[C], rank[C], inv[C], cell[C];
     int doff[kGroupMax * (kNDir + 1)];
     int run[kGroupMax * kNDir];
-    int ss[2][kUnitW + 1];       // cell starts of the planner's and the pusher's unit
-    PushTile<T> tile;
-    PredTile<T, PRED> en;
 };
 static_assert(PushCfg<float>::cap <= 256 && PushCfg<double>::cap <= 256, "uint8 staging indices");
-
-template <typename T, bool PRED>
-struct PushSmem {
-    PushWarp<T, PRED> w[PushCfg<T>::warps];
-    double red[32 * kLedger];
-};
-static_assert(sizeof(PushWarp<float, false>) % 16 == 0 && sizeof(PushWarp<float, true>) % 16 == 0 &&
-                  sizeof(PushWarp<double, false>) % 16 == 0 && sizeof(PushWarp<double, true>) % 16 == 0 &&
-                  (2 * 6 * PushCfg<float>::slot * sizeof(float)) % 16 == 0 &&
-                  (2 * 6 * PushCfg<double>::slot * sizeof(double)) % 16 == 0 &&
-                  (PushCfg<float>::slot * sizeof(float)) % 16 == 0 && (PushCfg<double>::slot * sizeof(double)) % 16 == 0 &&
-                  (PushCfg<float>::slot * sizeof(int32_t)) % 16 == 0,
-              "bulk-copy destinations on 16-byte boundaries");
-// min_blocks blocks per SM within 228 KB of shared memory (1 KB reserved per block)
-static_assert(PushCfg<float>::min_blocks * (sizeof(PushSmem<float, true>) + 1024) <= 228 * 1024 &&
-                  PushCfg<double>::min_blocks * (sizeof(PushSmem<double, true>) + 1024) <= 228 * 1024,
-              "the push's blocks fit an SM");
-
-// a cell group of a unit: cells l .. l+gsz-1 (particles s0 .. s0+tot-1), or
-// a single cell holding more than the staging capacity (big)
-struct PushGroup {
-    int k;      // the unit's ordinal in this warp's sequence
-    int l, gsz, s0, tot;
-    bool big;
-};
 
 template <typename T>
 __device__ __forceinline__ void block_ledger(const T (&acc)[kLedger], double* red, double* __restrict__ lsum)
@@ -749,242 +796,166 @@ __device__ __forceinline__ unsigned dir_peers(bool act, int dir)
     return m;
 }
 
-// fence between generic-proxy accesses of shared memory and the bulk copies
-// that next write it
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 template <typename T, bool PRED>
 __global__ void __launch_bounds__(PushCfg<T>::threads, PushCfg<T>::min_blocks)
 k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int32_t* __restrict__ n9,
             int32_t* __restrict__ off9, const T* __restrict__ Eth, const T* __restrict__ B,
-            const T* __restrict__ En, GridP g, T beta, T dt_dx, T dt_dy, T qdt, T m, double* __restrict__ lsum,
-            int* __restrict__ err)
+            const T* __restrict__ En, GridP g, T beta, T dt_dx, T dt_dy, T qdt, T m, double* __restrict__ lsum)
 {
-    constexpr int CAP = PushCfg<T>::cap, A = 16 / (int)sizeof(T);
-    extern __shared__ __align__(128) unsigned char push_smem[];
-    PushSmem<T, PRED>& S = *reinterpret_cast<PushSmem<T, PRED>*>(push_smem);
+    constexpr int W = PushCfg<T>::warps;
+    __shared__ int sstart[W][kUnitW + 1];
+    __shared__ PushTile<T> stile[W];
+    __shared__ PredTile<T, PRED> sen[W];
+    __shared__ PushStage<T> sstage[W];
+    __shared__ double red[32 * kLedger];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int nx = g.nx, ny = g.ny, nc = g.ncell;
     const int nunits = units_of(nx, ny);
     const unsigned lt = (1u << lane) - 1u;
-    PushWarp<T, PRED>& W = S.w[wib];
-    PushTile<T>& tl = W.tile;
+    int* ss = sstart[wib];
+    PushTile<T>& tl = stile[wib];
+    PushStage<T>& st = sstage[wib];
     const bool ids = dst.id != nullptr;
-    // ids (4 bytes) ride along in the bulk copies when the records are 4-byte
-    // values too (the same alignment); in the FP64 form they are read directly
-    const bool staged_ids = ids && sizeof(T) == 4;
-    const int narr = staged_ids ? 7 : 6;
     T acc[kLedger] = {T(0), T(0), T(0), T(0)};
 
-    if (lane == 0) {
-        mbar_init(&W.mb[0], 1);
-        mbar_init(&W.mb[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-
-    // The planner walks this warp's units (u = warp + k nwarps) cell group by
-    // cell group, one group ahead of the pusher, so the bulk copies of the
-    // next group's particles are in flight while this one is pushed.
-    int pk = 0, pl = 0;
-    auto load_ss = [&](int k) {
-        const Unit un = unit_of(warp + k * nwarps, nx);
-#pragma unroll
-        for (int k0 = 0; k0 <= kUnitW; k0 += 32)
-            if (k0 + lane <= un.cn) W.ss[k & 1][k0 + lane] = start[un.c0 + k0 + lane];
-        __syncwarp();
-    };
-    auto plan = [&](PushGroup& gr) -> bool {
-        for (;;) {
-            const int u = warp + pk * nwarps;
-            if (u >= nunits) return false;
-            const Unit un = unit_of(u, nx);
-            if (pl >= un.cn) {
-                ++pk;
-                pl = 0;
-                if (warp + pk * nwarps < nunits) load_ss(pk);
+    for (int u = warp; u < nunits; u += nwarps) {
+        const Unit un = unit_of(u, nx);
+        unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
+        if constexpr (PRED) {
+            load_tile_E<T, 32>(sen[wib].En, En, un, nx, ny, nc, lane);
+            __syncwarp();
+        }
+        const int P1 = ss[un.cn];
+        int pf_pos = -1;   // the first particle of the prefetched batch
+        T pfx = T(0), pfy = T(0), pux = T(0), puy = T(0), puz = T(0), pw = T(0);
+        for (int l = 0; l < un.cn;) {
+            const int s0 = ss[l];
+            if (ss[l + 1] - s0 > PushCfg<T>::cap) {
+                // a big cell alone: a counting pass (no ledger, nothing
+                // written), then every particle written to its slot directly
+                const int s1 = ss[l + 1];
+                int* run = st.run;
+                if (lane < kNDir) run[lane] = 0;
+                __syncwarp();
+                for (int b0 = s0; b0 < s1; b0 += 32) {
+                    const int p = b0 + lane;
+                    const bool act = p < s1;
+                    const int q = act ? p : s0;
+                    Pushed<T> o;
+                    push_particle<T, PRED>(ld(src.fx + q), ld(src.fy + q), ld(src.ux + q), ld(src.uy + q),
+                                           ld(src.uz + q), ld(src.w + q), l, tl.E, tl.B, sen[wib].en(), beta,
+                                           dt_dx, dt_dy, qdt, m, true, false, acc, o);
+                    const unsigned peers = __match_any_sync(0xffffffffu, act ? o.dir : 1024 + lane);
+                    if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
+                    __syncwarp();
+                }
+                store_doff(run, st.doff, lane);
+                __syncwarp();
+                if (lane < kNDir) run[lane] = 0;
+                __syncwarp();
+                for (int b0 = s0; b0 < s1; b0 += 32) {
+                    const int p = b0 + lane;
+                    const bool act = p < s1;
+                    const int q = act ? p : s0;
+                    T fx, fy, ux, uy, uz, w;
+                    if (pf_pos == b0) {
+                        fx = pfx; fy = pfy; ux = pux; uy = puy; uz = puz; w = pw;
+                    } else {
+                        fx = ld(src.fx + q); fy = ld(src.fy + q); ux = ld(src.ux + q);
+                        uy = ld(src.uy + q); uz = ld(src.uz + q); w = ld(src.w + q);
+                    }
+                    pf_pos = -1;
+                    Pushed<T> o;
+                    push_particle<T, PRED>(fx, fy, ux, uy, uz, act ? w : T(0), l, tl.E, tl.B, sen[wib].en(), beta,
+                                           dt_dx, dt_dy, qdt, m, true, true, acc, o);
+                    const unsigned peers = __match_any_sync(0xffffffffu, act ? o.dir : 1024 + lane);
+                    const int rank = (act ? run[o.dir] : 0) + __popc(peers & lt);
+                    __syncwarp();
+                    if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
+                    __syncwarp();
+                    if (act) {
+                        const int pos = s0 + st.doff[o.dir] + rank;
+                        dst.fx[pos] = o.fxn;
+                        dst.fy[pos] = o.fyn;
+                        dst.ux[pos] = o.u1x;
+                        dst.uy[pos] = o.u1y;
+                        dst.uz[pos] = o.u1z;
+                        dst.w[pos] = o.w;
+                        if (ids) dst.id[pos] = src.id[p];
+                    }
+                }
+                const int c = un.c0 + l;
+                if (lane < kNDir) {
+                    n9[(int64_t)c * kNDir + lane] = st.doff[lane + 1] - st.doff[lane];
+                    off9[(int64_t)c * kNDir + lane] = s0 + st.doff[lane];
+                }
+                __syncwarp();
+                ++l;
                 continue;
             }
-            const int* ss = W.ss[pk & 1];
-            gr.k = pk;
-            gr.l = pl;
-            gr.s0 = ss[pl];
-            int gsz = 1, tot = ss[pl + 1] - ss[pl];
-            if (tot > CAP) {
-                gr.big = true;
-            } else {
-                gr.big = false;
-                while (gsz < kGroupMax && pl + gsz < un.cn) {
-                    const int nn = ss[pl + gsz + 1] - ss[pl + gsz];
-                    if (tot + nn > CAP) break;
-                    tot += nn;
-                    ++gsz;
-                }
-            }
-            gr.gsz = gsz;
-            gr.tot = tot;
-            pl += gsz;
-            return true;
-        }
-    };
-    // lane 0: the bulk copies of a group into buffer b (an arrival with no
-    // bytes for an empty or big group)
-    auto issue = [&](const PushGroup& gr, int b) {
-        if (lane != 0) return;
-        const int p0a = gr.s0 & ~(A - 1);
-        W.p0a[b] = p0a;
-        if (gr.big || gr.tot == 0) {
-            mbar_expect_tx_arrive(&W.mb[b], 0);
-            return;
-        }
-        const int p1a = (gr.s0 + gr.tot + A - 1) & ~(A - 1);
-        const unsigned bytes = (unsigned)((p1a - p0a) * (int)sizeof(T));
-        fence_proxy_async_smem();   // this buffer's earlier generic reads and writes come first
-        mbar_expect_tx_arrive(&W.mb[b], (unsigned)narr * bytes);
-        const T* srcs[6] = {src.fx, src.fy, src.ux, src.uy, src.uz, src.w};
-#pragma unroll
-        for (int a = 0; a < 6; ++a) bulk_g2s(&W.a[b][a][0], srcs[a] + p0a, bytes, &W.mb[b]);
-        if (staged_ids) bulk_g2s(&W.id[b][0], src.id + p0a, bytes, &W.mb[b]);
-    };
-
-    if (warp < nunits) load_ss(0);
-    PushGroup cur, nxt;
-    bool have = plan(cur);
-    if (have) issue(cur, 0);
-    __syncwarp();
-    unsigned uses[2] = {0u, 0u};   // completed phases per buffer
-    bool pend[2] = {have, false};  // a phase in flight per buffer
-    int tile_k = -1;
-    bool failed = false;
-    for (int gi = 0; have; ++gi) {
-        const int b = gi & 1;
-        const bool more = plan(nxt);
-        if (more) {
-            issue(nxt, b ^ 1);
-            pend[b ^ 1] = true;
-        }
-        __syncwarp();
-        const Unit un = unit_of(warp + cur.k * nwarps, nx);
-        const int* ss = W.ss[cur.k & 1];
-        if (cur.k != tile_k) {
-            // the unit's field tiles
-            load_tile_B<T, 32>(tl.B, B, un, nx, ny, nc, lane);
-            load_tile_E<T, 32>(tl.E, Eth, un, nx, ny, nc, lane);
-            if constexpr (PRED) load_tile_E<T, 32>(W.en.En, En, un, nx, ny, nc, lane);
-            tile_k = cur.k;
-        }
-        const bool ok = mbar_wait(&W.mb[b], uses[b] & 1u, kPushMaxPolls);
-        if (!__all_sync(0xffffffffu, ok)) {
-            failed = true;
-            break;
-        }
-        uses[b] += 1;
-        pend[b] = false;
-        __syncwarp();   // the tiles and p0a
-        const int l = cur.l, s0 = cur.s0;
-        if (cur.big) {
-            // a big cell alone, from global memory: a counting pass (no
-            // ledger, nothing written), then every particle written to its
-            // slot directly
-            const int s1 = s0 + cur.tot;
-            int* run = W.run;
-            if (lane < kNDir) run[lane] = 0;
-            __syncwarp();
-            for (int b0 = s0; b0 < s1; b0 += 32) {
-                const int p = b0 + lane;
-                const bool act = p < s1;
-                const int q = act ? p : s0;
-                Pushed<T> o;
-                push_particle<T, PRED>(ld(src.fx + q), ld(src.fy + q), ld(src.ux + q), ld(src.uy + q),
-                                       ld(src.uz + q), ld(src.w + q), l, tl.E, tl.B, W.en.en(), beta,
-                                       dt_dx, dt_dy, qdt, m, true, false, acc, o);
-                const unsigned peers = __match_any_sync(0xffffffffu, act ? o.dir : 1024 + lane);
-                if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
-                __syncwarp();
-            }
-            store_doff(run, W.doff, lane);
-            __syncwarp();
-            if (lane < kNDir) run[lane] = 0;
-            __syncwarp();
-            for (int b0 = s0; b0 < s1; b0 += 32) {
-                const int p = b0 + lane;
-                const bool act = p < s1;
-                const int q = act ? p : s0;
-                Pushed<T> o;
-                push_particle<T, PRED>(ld(src.fx + q), ld(src.fy + q), ld(src.ux + q), ld(src.uy + q),
-                                       ld(src.uz + q), act ? ld(src.w + q) : T(0), l, tl.E, tl.B, W.en.en(), beta,
-                                       dt_dx, dt_dy, qdt, m, true, true, acc, o);
-                const unsigned peers = __match_any_sync(0xffffffffu, act ? o.dir : 1024 + lane);
-                const int rank = (act ? run[o.dir] : 0) + __popc(peers & lt);
-                __syncwarp();
-                if (act && (peers & lt) == 0) run[o.dir] += __popc(peers);
-                __syncwarp();
-                if (act) {
-                    const int pos = s0 + W.doff[o.dir] + rank;
-                    dst.fx[pos] = o.fxn;
-                    dst.fy[pos] = o.fyn;
-                    dst.ux[pos] = o.u1x;
-                    dst.uy[pos] = o.u1y;
-                    dst.uz[pos] = o.u1z;
-                    dst.w[pos] = o.w;
-                    if (ids) dst.id[pos] = src.id[p];
-                }
-            }
-            const int c = un.c0 + l;
-            if (lane < kNDir) {
-                n9[(int64_t)c * kNDir + lane] = W.doff[lane + 1] - W.doff[lane];
-                off9[(int64_t)c * kNDir + lane] = s0 + W.doff[lane];
-            }
-            __syncwarp();
-        } else {
             // a group of consecutive cells staged together: the warp's lanes
             // run over the group's particles in batches of 32 whatever cell
-            // they belong to, so short cells do not leave lanes idle; the
-            // pushed records replace the inputs in the staging buffer
-            const int gsz = cur.gsz, tot = cur.tot;
+            // they belong to, so short cells do not leave lanes idle
+            int gsz = 1, tot = ss[l + 1] - s0;
+            while (gsz < kGroupMax && l + gsz < un.cn) {
+                const int nn = ss[l + gsz + 1] - ss[l + gsz];
+                if (tot + nn > PushCfg<T>::cap) break;
+                tot += nn;
+                ++gsz;
+            }
             const int s1 = s0 + tot;
-            const int off = s0 - W.p0a[b];
-            T* const fxs = &W.a[b][0][off];
-            T* const fys = &W.a[b][1][off];
-            T* const uxs = &W.a[b][2][off];
-            T* const uys = &W.a[b][3][off];
-            T* const uzs = &W.a[b][4][off];
-            T* const ws = &W.a[b][5][off];
-            const int32_t* const idss = staged_ids ? &W.id[b][off] : src.id + s0;
-            for (int i = lane; i < gsz * kNDir; i += 32) W.run[i] = 0;
+            for (int i = lane; i < gsz * kNDir; i += 32) st.run[i] = 0;
             __syncwarp();
             int ci = 0;   // this lane's cell within the group
-            for (int b0 = 0; b0 < tot; b0 += 32) {
-                const int e = b0 + lane;
-                const bool act = e < tot;
-                const int q = act ? e : 0;
-                while (ci + 1 < gsz && ss[l + ci + 1] <= s0 + e) ++ci;
+            // the next batch of the unit (this group's or the next cell's) is
+            // loaded while this one is pushed
+            for (int b0 = s0; b0 < s1; b0 += 32) {
+                const int p = b0 + lane;
+                const bool act = p < s1;
+                const int q = act ? p : s0;
+                while (ci + 1 < gsz && ss[l + ci + 1] <= p) ++ci;
+                T fx, fy, ux, uy, uz, w;
+                if (pf_pos == b0) {
+                    fx = pfx; fy = pfy; ux = pux; uy = puy; uz = puz; w = pw;
+                } else {
+                    fx = ld(src.fx + q); fy = ld(src.fy + q); ux = ld(src.ux + q);
+                    uy = ld(src.uy + q); uz = ld(src.uz + q); w = ld(src.w + q);
+                }
+                pf_pos = b0 + 32 < s1 ? b0 + 32 : s1;
+                if (pf_pos < P1) {
+                    const int pq = pf_pos + lane < P1 ? pf_pos + lane : P1 - 1;
+                    pfx = ld(src.fx + pq);
+                    pfy = ld(src.fy + pq);
+                    pux = ld(src.ux + pq);
+                    puy = ld(src.uy + pq);
+                    puz = ld(src.uz + pq);
+                    pw = ld(src.w + pq);
+                }
                 Pushed<T> o;
                 // idle lanes carry weight 0: no ledger contribution (and nothing is stored)
-                push_particle<T, PRED>(fxs[q], fys[q], uxs[q], uys[q], uzs[q], act ? ws[q] : T(0), l + ci, tl.E, tl.B,
-                                       W.en.en(), beta, dt_dx, dt_dy, qdt, m, true, true, acc, o);
+                push_particle<T, PRED>(fx, fy, ux, uy, uz, act ? w : T(0), l + ci, tl.E, tl.B, sen[wib].en(),
+                                       beta, dt_dx, dt_dy, qdt, m, true, true, acc, o);
                 // rank among the group's particles of the same cell and direction, in order
                 const unsigned peers = __match_any_sync(0xffffffffu, act ? ci * 16 + o.dir : 1024 + lane);
                 const int ridx = ci * kNDir + o.dir;
-                const int rank = (act ? W.run[ridx] : 0) + __popc(peers & lt);
+                const int rank = (act ? st.run[ridx] : 0) + __popc(peers & lt);
                 __syncwarp();
-                if (act && (peers & lt) == 0) W.run[ridx] += __popc(peers);
+                if (act && (peers & lt) == 0) st.run[ridx] += __popc(peers);
                 __syncwarp();
                 if (act) {
-                    fxs[e] = o.fxn;
-                    fys[e] = o.fyn;
-                    uxs[e] = o.u1x;
-                    uys[e] = o.u1y;
-                    uzs[e] = o.u1z;
-                    ws[e] = o.w;
-                    W.dir[e] = (uint8_t)o.dir;
-                    W.rank[e] = (uint8_t)rank;
-                    W.cell[e] = (uint8_t)ci;
+                    const int e = p - s0;
+                    st.fx[e] = o.fxn;
+                    st.fy[e] = o.fyn;
+                    st.ux[e] = o.u1x;
+                    st.uy[e] = o.u1y;
+                    st.uz[e] = o.u1z;
+                    st.w[e] = o.w;
+                    if (ids) st.id[e] = src.id[p];
+                    st.dir[e] = (uint8_t)o.dir;
+                    st.rank[e] = (uint8_t)rank;
+                    st.cell[e] = (uint8_t)ci;
                 }
             }
             // offsets per (cell, direction) within the group, the inverse
@@ -994,48 +965,37 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
                 int v = ss[l + i] - s0;
 #pragma unroll
                 for (int d = 0; d < kNDir; ++d) {
-                    W.doff[i * (kNDir + 1) + d] = v;
-                    v += W.run[i * kNDir + d];
+                    st.doff[i * (kNDir + 1) + d] = v;
+                    v += st.run[i * kNDir + d];
                 }
-                W.doff[i * (kNDir + 1) + kNDir] = v;
+                st.doff[i * (kNDir + 1) + kNDir] = v;
             }
             __syncwarp();
             for (int e = lane; e < tot; e += 32)
-                W.inv[W.doff[W.cell[e] * (kNDir + 1) + W.dir[e]] + W.rank[e]] = (uint8_t)e;
+                st.inv[st.doff[st.cell[e] * (kNDir + 1) + st.dir[e]] + st.rank[e]] = (uint8_t)e;
             __syncwarp();
             for (int qq = lane; qq < tot; qq += 32) {
-                const int e = W.inv[qq];
-                dst.fx[s0 + qq] = fxs[e];
-                dst.fy[s0 + qq] = fys[e];
-                dst.ux[s0 + qq] = uxs[e];
-                dst.uy[s0 + qq] = uys[e];
-                dst.uz[s0 + qq] = uzs[e];
-                dst.w[s0 + qq] = ws[e];
-                if (ids) dst.id[s0 + qq] = idss[e];
+                const int e = st.inv[qq];
+                dst.fx[s0 + qq] = st.fx[e];
+                dst.fy[s0 + qq] = st.fy[e];
+                dst.ux[s0 + qq] = st.ux[e];
+                dst.uy[s0 + qq] = st.uy[e];
+                dst.uz[s0 + qq] = st.uz[e];
+                dst.w[s0 + qq] = st.w[e];
+                if (ids) dst.id[s0 + qq] = st.id[e];
             }
             // the runs of the group's cells: counts and starts per direction
             for (int i = lane; i < gsz * kNDir; i += 32) {
-                const int gi2 = i / kNDir, d = i - gi2 * kNDir;
-                const int64_t c = un.c0 + l + gi2;
-                n9[c * kNDir + d] = W.run[i];
-                off9[c * kNDir + d] = s0 + W.doff[gi2 * (kNDir + 1) + d];
+                const int gi = i / kNDir, d = i - gi * kNDir;
+                const int64_t c = un.c0 + l + gi;
+                n9[c * kNDir + d] = st.run[i];
+                off9[c * kNDir + d] = s0 + st.doff[gi * (kNDir + 1) + d];
             }
-            (void)s1;
+            __syncwarp();
+            l += gsz;
         }
-        __syncwarp();
-        cur = nxt;
-        have = more;
     }
-    if (failed) {
-        if (lane == 0) {
-            atomicOr(err, 2);
-            // let the copies already issued land before the warp leaves (bounded)
-            for (int bb = 0; bb < 2; ++bb)
-                if (pend[bb]) mbar_wait(&W.mb[bb], uses[bb] & 1u, kPushMaxPolls);
-        }
-        __syncwarp();
-    }
-    block_ledger<T>(acc, S.red, lsum);
+    block_ledger<T>(acc, red, lsum);
 }
 
 // General path (moves of more than one cell): push in place order, write the
@@ -1714,10 +1674,8 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
 
 int push_grid_blocks(GridP g, int precision, int cap)
 {
-    // default: the blocks resident at once (the staged push's warps walk
-    // their units with the next group's copies in flight)
     return blocks_for(units_of(g.nx, g.ny), precision == 32 ? PushCfg<float>::warps : PushCfg<double>::warps,
-                      cap > 0 ? cap : 152 * (precision == 32 ? PushCfg<float>::min_blocks : PushCfg<double>::min_blocks));
+                      cap > 0 ? cap : 152 * 16);
 }
 
 template <typename T>
@@ -1782,15 +1740,13 @@ cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int3
                       const T* Eth, const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial,
                       int lsum_blocks, int* err, cudaStream_t st)
 {
+    (void)err;   // the push has no bounded wait to report
     const T beta = (T)(sc.q * g.dt / (2.0 * sc.m));
     auto kern = En ? k_push_sort<T, true> : k_push_sort<T, false>;
-    const int smem = En ? (int)sizeof(PushSmem<T, true>) : (int)sizeof(PushSmem<T, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
     count_launches(1);
-    kern<<<lsum_blocks, PushCfg<T>::threads, smem, st>>>(src, dst, start, n9, off9, Eth, B, En, g, beta,
-                                                         (T)(g.dt / g.dx), (T)(g.dt / g.dy), (T)(sc.q * g.dt),
-                                                         (T)sc.m, lsum_partial, err);
+    kern<<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(src, dst, start, n9, off9, Eth, B, En, g, beta,
+                                                      (T)(g.dt / g.dx), (T)(g.dt / g.dy), (T)(sc.q * g.dt),
+                                                      (T)sc.m, lsum_partial);
     return cudaGetLastError();
 }
 

@@ -7,9 +7,15 @@ direction in the initial E).
 Loss: the energy of the k_x = 2 pi / L_x mode of B_y after the window, on a
 16x8 double Harris sheet (4 ppc per species) with a small random initial E.
 The GPU's FP64 form follows the oracle's trajectory to ~1e-11 per step, so
-its gradients agree to 1e-6 of the largest entry; the FP32 form's steps and
-adjoint solves carry FP32 rounding (1e-7 per operation, GMRES at 1e-7),
-amplified over the window: 1e-3.
+its gradients agree to 1e-6 of the largest entry (measured 7.5e-13); the
+FP32 form's steps and adjoint solves carry FP32 rounding (1e-7 per
+operation, GMRES at 1e-7), amplified over the window: measured on GB300 the
+largest difference over the largest entry is 5.7e-7 (E), 2.9e-7 (B), 7.9e-7
+(u), 5.1e-7 (x), 4.9e-7 (w); asserted 1e-5, ten times inside the 1e-4 the
+FP32 form is held to. A second window of the configured length (20 steps,
+a checkpoint every 5, 32 particles per cell per species) on the largest
+grid the oracle's dense field adjoint handles quickly (32x16) is held to
+1e-4 as well.
 """
 import numpy as np
 import pytest
@@ -71,17 +77,53 @@ def test_window_gradient_matches_oracle(rs, orc, prec):
     win.close()
     c = orc.make_config(NX, NY, dt=DT, gmres_tol=1e-14, gmres_restart=200)
     Lo, go = orc.window_gradient(c, st["species"], st["E"], st["B"], STEPS)
-    t = 1e-6 if prec == 64 else 1e-3
-    assert abs(L - Lo) < (1e-9 if prec == 64 else 1e-4) * Lo
-    assert rel(g["E"], go["E"]) < t
-    assert rel(g["B"], go["B"]) < t
+    t = 1e-6 if prec == 64 else 1e-5
     n0 = len(st["species"][0]["w"])
     gu = np.concatenate([g["particles"][s][0] for s in range(2)])
     gx = np.concatenate([g["particles"][s][1] for s in range(2)])
+    print(f"FP{prec} window: loss {abs(L - Lo) / Lo:.1e}, E {rel(g['E'], go['E']):.1e}, B {rel(g['B'], go['B']):.1e}, "
+          f"u {rel(gu, go['u'].T):.1e}, x {rel(gx, np.stack([go['x'], go['y']], axis=1)):.1e}, "
+          f"w {rel(np.concatenate(g['w']), go['w']):.1e} (largest difference over the largest entry)")
+    assert abs(L - Lo) < (1e-9 if prec == 64 else 1e-4) * Lo
+    assert rel(g["E"], go["E"]) < t
+    assert rel(g["B"], go["B"]) < t
     assert gu.shape[0] == 2 * n0
     assert rel(gu, go["u"].T) < t
     assert rel(gx, np.stack([go["x"], go["y"]], axis=1)) < t
     assert rel(np.concatenate(g["w"]), go["w"]) < t
+
+
+def test_window_20_steps_fp32_matches_oracle(rs, orc):
+    """FP32 form, 32x16 sheet, 32 ppc per species, 20 steps with a
+    checkpoint every 5: every gradient (initial E and B per cell, every
+    particle's u, x and w) within 1e-4 of the largest entry of the FP64
+    oracle's window gradient from the same FP32-representable state."""
+    from paper_2509_11100_gb300.window import ModeEnergyWindow
+    nx, ny, steps = 32, 16, 20
+    st = make_harris(HarrisConfig(nx=nx, ny=ny, ppc=32, dt=DT, pert=0.05))
+    rng = np.random.default_rng(5)
+    st["E"] = 0.02 * rng.normal(size=st["E"].shape)
+    for sp in st["species"]:
+        for k in ("x", "y", "ux", "uy", "uz", "w"):
+            sp[k] = np.asarray(sp[k]).astype(np.float32).astype(np.float64)
+    st["E"] = st["E"].astype(np.float32).astype(np.float64)
+    st["B"] = st["B"].astype(np.float32).astype(np.float64)
+    cfg = rs.make_config(nx, ny, dt=DT, precision=32, gmres_tol=1e-7, gmres_restart=100)
+    win = ModeEnergyWindow(cfg, steps, checkpoint_every=5)
+    L = win.forward(st)
+    g = win.backward()
+    win.close()
+    c = orc.make_config(nx, ny, dt=DT, gmres_tol=1e-14, gmres_restart=200)
+    Lo, go = orc.window_gradient(c, st["species"], st["E"], st["B"], steps)
+    gu = np.concatenate([g["particles"][s][0] for s in range(2)])
+    gx = np.concatenate([g["particles"][s][1] for s in range(2)])
+    errs = {"E": rel(g["E"], go["E"]), "B": rel(g["B"], go["B"]), "u": rel(gu, go["u"].T),
+            "x": rel(gx, np.stack([go["x"], go["y"]], axis=1)), "w": rel(np.concatenate(g["w"]), go["w"])}
+    print(f"FP32 window 32x16, 20 steps: loss {abs(L - Lo) / Lo:.1e}; gradients "
+          + ", ".join(f"{k} {v:.1e}" for k, v in errs.items()))
+    assert abs(L - Lo) < 1e-5 * Lo
+    for k, v in errs.items():
+        assert v < 1e-4, (k, v)
 
 
 def test_window_autograd_matches_central_differences(rs):
