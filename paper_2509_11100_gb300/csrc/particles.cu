@@ -295,25 +295,6 @@ template <typename T>
 struct Moments {
     T S[81];
     T Jm[12];
-    T pad;
-    // flat order: S[k][q] at k*9 + q, then the 12 currents, then padding
-    // (index e a compile-time constant after unrolling: a register)
-    static constexpr int kFlat = 96;
-    __device__ __forceinline__ T& at(int e) { return e < 81 ? S[e] : (e < 93 ? Jm[e - 81] : pad); }
-    // flat entry e: a moment (k, q; it = -1) or a current (it >= 0); false
-    // for padding
-    __device__ __forceinline__ static bool locate(int e, int& k, int& q, int& it)
-    {
-        if (e < 81) {
-            k = e / 9;
-            q = e - 9 * k;
-            it = -1;
-            return true;
-        }
-        it = e - 81;
-        k = q = 0;
-        return it < 12;
-    }
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
@@ -346,27 +327,6 @@ template <>
 struct Moments<float> {
     float2 S2[45];   // S2[k*5 + h] = (S[k][2h], S[k][2h+1]); S[k][9] is padding
     float Jm[12];
-    float pad;
-    // flat order: S[k][q] at k*10 + q (q = 9: the zero padding), then the 12
-    // currents, then padding (index e a compile-time constant after
-    // unrolling: a register)
-    static constexpr int kFlat = 104;
-    __device__ __forceinline__ float& at(int e)
-    {
-        return e < 90 ? ((e & 1) ? S2[e >> 1].y : S2[e >> 1].x) : (e < 102 ? Jm[e - 90] : pad);
-    }
-    __device__ __forceinline__ static bool locate(int e, int& k, int& q, int& it)
-    {
-        if (e < 90) {
-            k = e / 10;
-            q = e - 10 * k;
-            it = -1;
-            return q < 9;
-        }
-        it = e - 90;
-        k = q = 0;
-        return it < 12;
-    }
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
@@ -404,36 +364,6 @@ struct Moments<float> {
         }
     }
 };
-
-// Sum over the 8 lanes of a group (lane bits 0-2) of the NV flat entries of
-// the accumulators, each lane keeping a different eighth: three halving
-// exchanges (xor 1, 2, 4), each lane sending the half it gives up. Afterwards
-// lane gl holds in entries 0 .. NV/8-1 the totals of entries base + t, base =
-// (gl&1) NV/2 + (gl>>1&1) NV/4 + (gl>>2&1) NV/8. The padding entries are set
-// to zero first.
-template <typename T>
-__device__ __forceinline__ void reduce_scatter8(Moments<T>& m, int gl)
-{
-    constexpr int NV = Moments<T>::kFlat;
-    static_assert(NV % 8 == 0, "eight equal shares");
-    m.pad = T(0);
-    const bool b0 = gl & 1, b1 = (gl >> 1) & 1, b2 = (gl >> 2) & 1;
-#pragma unroll
-    for (int t = 0; t < NV / 2; ++t) {
-        const T lo = m.at(t), hi = m.at(NV / 2 + t);
-        m.at(t) = (b0 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b0 ? lo : hi, 1);
-    }
-#pragma unroll
-    for (int t = 0; t < NV / 4; ++t) {
-        const T lo = m.at(t), hi = m.at(NV / 4 + t);
-        m.at(t) = (b1 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b1 ? lo : hi, 2);
-    }
-#pragma unroll
-    for (int t = 0; t < NV / 8; ++t) {
-        const T lo = m.at(t), hi = m.at(NV / 8 + t);
-        m.at(t) = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
-    }
-}
 
 template <typename T, bool PRED>
 __device__ __forceinline__ void deposit_particle(const T fx, const T fy, const T ux, const T uy, const T uz,
@@ -570,38 +500,26 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
             }
         }
         if (s == nsp - 1) {
-            // the group's sums, spread over its lanes: each of the G = 8
-            // lanes ends with NV/8 totals, which it flushes with one atomic
-            // each (two for the moment that two node pairs share)
-            constexpr int NV = Moments<T>::kFlat, NL = NV / G;
-            reduce_scatter8<T>(acc, gl);
+            acc.template group_reduce<G>();
             if (valid) {
                 const int i = un.i0 + grp, j = un.j;
                 const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
                 const int n00 = j * nx + i, n10 = j * nx + i1, n01 = j1 * nx + i, n11 = j1 * nx + i1;
-                const int base = (gl & 1) * (NV / 2) + ((gl >> 1) & 1) * (NV / 4) + ((gl >> 2) & 1) * (NV / 8);
+                // (destination node, half offset, moment k) of the ten node pairs
+                const int pn[10] = {n00, n00, n00, n00, n10, n10, n10, n01, n01, n11};
+                constexpr int po[10] = {0, 1, 3, 4, 0, 2, 3, 0, 1, 0};
+                constexpr int pk[10] = {0, 3, 1, 4, 6, 4, 7, 2, 5, 8};
 #pragma unroll
-                for (int t = 0; t < NL; ++t) {
-                    int k, q, it;
-                    if (!Moments<T>::locate(base + t, k, q, it)) continue;
-                    if (it < 0) {
-                        // moment S[k][q] -> the node pair(s) with that moment:
-                        // pair pr = (k-th entry of 0 2 7 1 3 8 4 6 9), and pair
-                        // 5 as well for k = 4; pairs 0-3 start at n00, 4-6 at
-                        // n10, 7-8 at n01, 9 at n11; half offsets 0 1 3 4 0 2 3 0 1 0
-                        constexpr unsigned long long kPr = 0x964831720ull, kPo = 0x0103204310ull;
-                        const int pr = (int)((kPr >> (4 * k)) & 0xF);
-                        const int po = (int)((kPo >> (4 * pr)) & 0xF);
-                        const int node = pr <= 3 ? n00 : (pr <= 6 ? n10 : (pr <= 8 ? n01 : n11));
-                        atomicAdd(M + (int64_t)node * kMBlock + po * 9 + q, acc.at(t));
-                        if (k == 4) atomicAdd(M + (int64_t)n10 * kMBlock + 2 * 9 + q, acc.at(t));
-                    } else {
-                        // current: entry it = node a (n00 n10 n01 n11) * 3 + component
-                        const int a = it / 3, comp = it - 3 * a;
-                        const int node = a == 0 ? n00 : (a == 1 ? n10 : (a == 2 ? n01 : n11));
-                        atomicAdd(J + (int64_t)comp * nc + node, acc.at(t));
+                for (int it = 0; it < 90; ++it) {
+                    if (it % G == gl) {
+                        const int pr = it / 9, q = it % 9;
+                        atomicAdd(M + (int64_t)pn[pr] * kMBlock + po[pr] * 9 + q, acc.get(pk[pr], q));
                     }
                 }
+                const int jn[4] = {n00, n10, n01, n11};
+#pragma unroll
+                for (int it = 0; it < 12; ++it)
+                    if ((90 + it) % G == gl) atomicAdd(J + (int64_t)(it % 3) * nc + jn[it / 3], acc.Jm[it]);
             }
         }
         __syncthreads();   // buffer b and the B tile are free for the next stage
