@@ -242,6 +242,7 @@ def run_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = rs.relsim_kernel_launches() - launches0
+    path = batch.last_path
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -631,7 +632,7 @@ def run_scan(args):
     torch.cuda.synchronize()
     t_setup = time.time() - t0
     N = sum(sizes[i] for i in mine)
-    batch = rs.Batch(sims, nworkers=args.workers)
+    batch = rs.Batch(sims, nworkers=args.workers, shared=args.scan_launch == "shared")
     batch.run(args.warmup)
     torch.cuda.synchronize()
 
@@ -658,6 +659,7 @@ def run_scan(args):
     ev1.record(dflt)
     torch.cuda.synchronize()
     launches = rs.relsim_kernel_launches() - launches0
+    path = batch.last_path
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -717,6 +719,10 @@ def run_scan(args):
         "data": "synthetic",
         "config": dict(SCAN, instances=len(insts), instances_here=len(mine), particles_total=total,
                        particles_here=N, workers=args.workers,
+                       launch={"shared": "one deposit, push and re-sort launch per species over all instances "
+                                         "per step, the instances' solves as branches of one graph",
+                               "graphs": "one step graph per instance on its own stream",
+                               "host": "host-driven steps by worker threads"}.get(path, path),
                        parallelism=f"instances sharded over {world} ranks" if world > 1 else "single"),
         "step_effective": {"mover_bytes_per_step": mover, "gbs": mover / (ms / 1e3) / 1e9,
                            "frac_of_peak": mover / (ms / 1e3) / 1e9 / peak, "peak": peak,
@@ -1088,6 +1094,8 @@ def main():
                          "(c2small: 64x32x32); c1q: the headline sheet with quadratic shapes; long: the "
                          "headline sheet for --long-steps steps (energy drift, tearing mode, spectrum)")
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the scan's batch runner")
+    ap.add_argument("--scan-launch", choices=["shared", "instances"], default="shared",
+                    help="scan: shared launches over all instances (default) or one step graph per instance")
     ap.add_argument("--scan-reference", action="store_true",
                     help="scan: also time single 1024x512, 768x384 and 128x64 instances with its parameters")
     args = ap.parse_args()

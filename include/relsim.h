@@ -562,6 +562,30 @@ RELSIM_API int relsim_batch_create(relsim_ctx* const* ctxs, int count, int nwork
 RELSIM_API int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, double* modes,
                                 int* status, int* iters);
 
+/* Shared launches over the batch's instances (off by default). With on = 1,
+   relsim_batch_run steps every instance through ONE graph per step in which
+   one deposit launch, one push launch and one re-sort launch per species
+   cover the particles of all instances (each instance's row units numbered
+   after the previous instance's), while each instance's field solve, field
+   update and sort tables run as parallel branches of the same graph. This is
+   the batched form of the data-parallel step over independent instances
+   (Sec. 3.1's scan of tearing runs: many small grids that one instance
+   alone cannot fill the GPU with). It applies when every instance is of the
+   2D form with linear shapes and one-cell moves, shares the precision,
+   species count and reading of the Lorentz factor, has every species
+   loaded, and all instances have taken the same number of steps in the run
+   so far; otherwise relsim_batch_run falls back to per-instance graphs or
+   host-driven steps. deposit_blocks and push_blocks set the shared launches'
+   grids (<= 0: 2 and 16 blocks per SM). Results equal the per-instance
+   steps' up to the order of floating-point sums (the deposit's and the
+   ledger's atomics). Errors: INVALID_ARG. */
+RELSIM_API int relsim_batch_set_shared(relsim_batch* b, int on, int deposit_blocks, int push_blocks);
+
+/* How the last relsim_batch_run advanced the instances after their first
+   step: 0 host-driven workers, 1 per-instance step graphs, 2 shared launches
+   (relsim_batch_set_shared); -1 before any run. */
+RELSIM_API int relsim_batch_last_path(const relsim_batch* b);
+
 /* Free the batch (not its contexts). NULL is a no-op. */
 RELSIM_API void relsim_batch_destroy(relsim_batch* b);
 

@@ -29,7 +29,7 @@ __all__ = [
     "relsim_kinetic_energy_noalloc", "relsim_energy_spectrum", "RELSIM_ERR_TOO_LARGE", "RELSIM_NOALLOC_MAX_PARTICLES",
     "RELSIM_HOST", "RELSIM_DEVICE", "RELSIM_OK", "RELSIM_ERR_NOT_CONVERGED",
     "relsim_field_modes", "relsim_field_mode_gradient", "relsim_growth_fit", "relsim_dispersion_fit", "relsim_batch_create", "relsim_batch_run",
-    "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
+    "relsim_batch_set_shared", "relsim_batch_last_path", "relsim_batch_destroy", "Batch", "relsim_graph_info", "relsim_field_adjoint", "relsim_autotune",
     "relsim_tuning", "relsim_push_adjoint", "relsim_deposit_adjoint", "relsim_step_adjoint",
     "relsim_relabel_particles", "relsim_set_launch_shapes", "relsim_get_particles_native",
     "relsim_load_particles_native",
@@ -132,6 +132,8 @@ _SIGS = {
                                              ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "relsim_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "relsim_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "relsim_batch_set_shared": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "relsim_batch_last_path": (ctypes.c_int, [_P]),
     "relsim_batch_destroy": (None, [_P]),
     "relsim_graph_info": (ctypes.c_int, [_CTX, _P, _P, _P]),
     "relsim_field_adjoint": (ctypes.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
@@ -615,6 +617,19 @@ def relsim_batch_run(b, count, nsteps, component=1, nmodes=0):
     return modes, status, iters, code
 
 
+def relsim_batch_set_shared(b, on=True, deposit_blocks=0, push_blocks=0):
+    """Shared launches over the batch's instances (one deposit, push and
+    re-sort launch per species for all of them) on or off."""
+    code = lib().relsim_batch_set_shared(b, 1 if on else 0, int(deposit_blocks), int(push_blocks))
+    if code != RELSIM_OK:
+        raise RelsimError(code, "batch set_shared: bad arguments")
+
+
+def relsim_batch_last_path(b):
+    """0 host-driven, 1 per-instance step graphs, 2 shared launches, -1 no run yet."""
+    return int(lib().relsim_batch_last_path(b))
+
+
 def relsim_batch_destroy(b):
     lib().relsim_batch_destroy(b)
 
@@ -789,9 +804,19 @@ class Batch:
     threads (each Simulation should have a CUDA stream of its own). The
     batch does not own the simulations."""
 
-    def __init__(self, sims, nworkers=8):
+    def __init__(self, sims, nworkers=8, shared=False, deposit_blocks=0, push_blocks=0):
         self.sims = list(sims)
         self.b = relsim_batch_create([s.ctx for s in self.sims], nworkers)
+        if shared:
+            relsim_batch_set_shared(self.b, True, deposit_blocks, push_blocks)
+
+    def set_shared(self, on=True, deposit_blocks=0, push_blocks=0):
+        relsim_batch_set_shared(self.b, on, deposit_blocks, push_blocks)
+
+    @property
+    def last_path(self):
+        """How the last run stepped: "host", "graphs", "shared" or None."""
+        return {0: "host", 1: "graphs", 2: "shared"}.get(relsim_batch_last_path(self.b))
 
     def run(self, nsteps, component=1, nmodes=0):
         """Returns (modes[count, nsteps, nmodes] or None, status[count],

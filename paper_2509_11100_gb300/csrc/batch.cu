@@ -12,6 +12,10 @@
 // solve's outcome, and waits once at the end. No host decision sits between
 // two steps, so the GPU holds work of every instance at once.
 //
+// With shared launches on, one graph per step covers all instances: one
+// deposit, one push and one re-sort launch per species over the particles of
+// every instance, and each instance's solve as a branch of its own.
+//
 // Instances that cannot step as graphs (event profiling on, or moves of more
 // than one cell per step) are driven by host threads instead: workers take
 // instances largest first and run each one through all its steps, so one
@@ -31,6 +35,10 @@ struct relsim_batch {
     std::vector<relsim_ctx*> ctx;
     int nworkers = 1;
     int device = 0;
+    bool shared = false;
+    int dep_blocks = 0, push_blocks = 0;
+    int last_path = -1;
+    relsim_shared* sb = nullptr;   // the shared graphs, kept while they fit the instances
 };
 
 using namespace relsim;
@@ -189,6 +197,115 @@ int relsim_batch_create(relsim_ctx* const* ctxs, int count, int nworkers, relsim
     return RELSIM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// merge one step's solve outcome r into an instance's status: the first
+// error sticks; NOT_CONVERGED is kept unless an error follows
+void merge_status(int& st, int r)
+{
+    if (r != RELSIM_OK && (st == RELSIM_OK || st == RELSIM_ERR_NOT_CONVERGED) &&
+        !(r == RELSIM_ERR_NOT_CONVERGED && st == RELSIM_ERR_NOT_CONVERGED))
+        st = r;
+}
+
+// steps first .. nsteps-1 of every instance through shared launches; -1 when
+// the instances are not eligible (nothing enqueued)
+int run_shared(relsim_batch* b, int nsteps, int first, int component, int nmodes, double* dmodes, size_t per,
+               int* status, int* iters)
+{
+    const int count = (int)b->ctx.size();
+    if (b->sb && !shared_valid(b->sb, b->ctx.data(), count, b->dep_blocks, b->push_blocks)) {
+        shared_destroy(b->sb);
+        b->sb = nullptr;
+    }
+    if (!b->sb) {
+        const int made = shared_create(b->ctx.data(), count, b->dep_blocks, b->push_blocks, &b->sb);
+        if (made == 0) return -1;
+        if (made != 1) return made;
+    }
+    relsim_shared* sb = b->sb;
+    const size_t hb = ctx_graph_head_bytes();
+    const int ns = nsteps - first;
+    unsigned char* heads = nullptr;
+    std::vector<cudaEvent_t> ev(count + 1, nullptr);
+    int rc = RELSIM_OK;
+    if (cudaMallocHost((void**)&heads, hb * (size_t)count * (size_t)ns) != cudaSuccess) rc = RELSIM_ERR_OOM;
+    for (int i = 0; i <= count && rc == RELSIM_OK; ++i)
+        if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) rc = RELSIM_ERR_CUDA;
+    cudaStream_t st = shared_stream(sb);
+    // the shared stream follows each instance's earlier work; the mode
+    // energies of step s run on the instance's stream between shared steps
+    auto join_into = [&](cudaStream_t to) -> int {
+        for (int i = 0; i < count; ++i) {
+            if (cudaEventRecord(ev[i], ctx_stream(b->ctx[i])) != cudaSuccess ||
+                cudaStreamWaitEvent(to, ev[i], 0) != cudaSuccess)
+                return RELSIM_ERR_CUDA;
+        }
+        return RELSIM_OK;
+    };
+    if (rc == RELSIM_OK) rc = join_into(st);
+    for (int s = first; s < nsteps && rc == RELSIM_OK; ++s) {
+        rc = shared_enqueue(sb, heads + hb * (size_t)(s - first), hb * (size_t)ns);
+        if (rc != RELSIM_OK || nmodes == 0) continue;
+        if (cudaEventRecord(ev[count], st) != cudaSuccess) {
+            rc = RELSIM_ERR_CUDA;
+            break;
+        }
+        for (int i = 0; i < count && rc == RELSIM_OK; ++i) {
+            relsim_ctx* c = b->ctx[i];
+            if (cudaStreamWaitEvent(ctx_stream(c), ev[count], 0) != cudaSuccess) {
+                rc = RELSIM_ERR_CUDA;
+                break;
+            }
+            rc = relsim_field_modes(c, component, nmodes, dmodes + per * (size_t)i + (size_t)(s + 1) * nmodes,
+                                    RELSIM_DEVICE);
+        }
+        if (rc == RELSIM_OK) rc = join_into(st);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == RELSIM_OK) rc = RELSIM_ERR_CUDA;
+    for (int i = 0; i < count; ++i)
+        if (cudaStreamSynchronize(ctx_stream(b->ctx[i])) != cudaSuccess && rc == RELSIM_OK) rc = RELSIM_ERR_CUDA;
+    if (rc == RELSIM_OK)
+        for (int s = first; s < nsteps; ++s)
+            for (int i = 0; i < count; ++i) {
+                int it = 0;
+                const int r = shared_outcome(sb, i, heads + hb * ((size_t)i * ns + (s - first)), &it, i == 0);
+                if (iters) iters[(size_t)i * nsteps + s] = it;
+                merge_status(status[i], r);
+            }
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    if (heads) cudaFreeHost(heads);
+    if (rc != RELSIM_OK) {
+        shared_destroy(sb);
+        b->sb = nullptr;
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int relsim_batch_set_shared(relsim_batch* b, int on, int deposit_blocks, int push_blocks)
+{
+    if (!b || (on != 0 && on != 1) || deposit_blocks > (1 << 20) || push_blocks > (1 << 20))
+        return RELSIM_ERR_INVALID_ARG;
+    b->shared = on != 0;
+    b->dep_blocks = deposit_blocks > 0 ? deposit_blocks : 0;
+    b->push_blocks = push_blocks > 0 ? push_blocks : 0;
+    if (!b->shared && b->sb) {
+        cudaSetDevice(b->device);
+        shared_destroy(b->sb);
+        b->sb = nullptr;
+    }
+    return RELSIM_OK;
+}
+
+int relsim_batch_last_path(const relsim_batch* b) { return b ? b->last_path : -1; }
+
 int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, double* modes, int* status,
                      int* iters)
 {
@@ -242,7 +359,24 @@ int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, dou
             if (nsteps > 1 && !ctx_graph_prepare(c)) graphs = false;
         }
     }
+    b->last_path = 0;
+    bool same = true;
+    for (int i = 1; i < count; ++i) same = same && done[i] == done[0] && status[i] == RELSIM_OK;
+    if (graphs && b->shared && same && status[0] == RELSIM_OK && done[0] < nsteps) {
+        const int rc = run_shared(b, nsteps, done[0], component, nmodes, dmodes, per, status, iters);
+        if (rc < 0) {   // not eligible: per-instance graphs
+        } else if (rc != RELSIM_OK) {
+            cudaDeviceSynchronize();
+            cudaFree(dmodes);
+            return rc;
+        } else {
+            for (int i = 0; i < count; ++i) done[i] = nsteps;
+            graphs = false;
+            b->last_path = 2;
+        }
+    }
     if (graphs) {
+        b->last_path = 1;
         const size_t hb = ctx_graph_head_bytes();
         unsigned char* heads = nullptr;
         if (cudaMallocHost((void**)&heads, hb * (size_t)count * (size_t)nsteps) != cudaSuccess) {
@@ -267,9 +401,7 @@ int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, dou
                         int it = 0;
                         const int r = ctx_graph_outcome(b->ctx[i], heads + hb * ((size_t)i * nsteps + s), &it);
                         if (iters) iters[(size_t)i * nsteps + s] = it;
-                        if (r != RELSIM_OK && (status[i] == RELSIM_OK || status[i] == RELSIM_ERR_NOT_CONVERGED) &&
-                            !(r == RELSIM_ERR_NOT_CONVERGED && status[i] == RELSIM_ERR_NOT_CONVERGED))
-                            status[i] = r;
+                        merge_status(status[i], r);
                     }
             cudaFreeHost(heads);
             if (rc != RELSIM_OK) {
@@ -358,6 +490,14 @@ int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, dou
     return RELSIM_OK;
 }
 
-void relsim_batch_destroy(relsim_batch* b) { delete b; }
+void relsim_batch_destroy(relsim_batch* b)
+{
+    if (!b) return;
+    if (b->sb) {
+        cudaSetDevice(b->device);
+        shared_destroy(b->sb);
+    }
+    delete b;
+}
 
 }  // extern "C"

@@ -181,6 +181,13 @@ int ledger_fill(relsim_ctx* c, const double* h, relsim_energy* out);
         if (e_ != cudaSuccess)                                                               \
             return fail(c, RELSIM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));        \
     } while (0)
+// the same, reporting on context cx
+#define CK_CTX(cx, call)                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(cx, RELSIM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
 
 int prof_flush(relsim_ctx* c)
 {
@@ -1531,7 +1538,366 @@ StepGraph* graph_for_layout(relsim_ctx* c)
 
 }  // namespace
 
+namespace {
+// ---------------------------------------------------------------------------
+// Shared launches over the instances of a batch: one deposit launch, one push
+// launch and one re-sort launch per species cover the row units of every
+// instance (numbered across them); each instance's solve (prologue, the
+// restart and Arnoldi loops as conditional nodes, field update) and its
+// sort tables run as branches of the same graph, forked from and joined back
+// to the batch's stream. Both buffer layouts are captured up front, as for
+// single contexts.
+
+template <typename T>
+struct SharedDesc {
+    std::vector<DepDesc<T>> dep;
+    std::vector<PushDesc<T>> push;   // [species][instance]
+};
+
+template <typename T>
+void shared_descs(const std::vector<relsim_ctx*>& cs, SharedDesc<T>& d, int* total)
+{
+    const int n = (int)cs.size(), nsp = cs[0]->cfg.nspecies;
+    d.dep.assign(n, DepDesc<T>{});
+    d.push.assign((size_t)n * nsp, PushDesc<T>{});
+    int u0 = 0;
+    for (int i = 0; i < n; ++i) {
+        relsim_ctx* c = cs[i];
+        DepDesc<T>& dd = d.dep[i];
+        dd.ds = deposit_args<T>(c);
+        dd.B = (const T*)c->B[c->bcur];
+        dd.En = c->En ? (const T*)c->E : nullptr;
+        dd.M = (T*)c->M;
+        dd.J = (T*)c->J;
+        dd.g = c->g;
+        dd.unit0 = u0;
+        for (int s = 0; s < nsp; ++s) {
+            Species& sp = c->sp[s];
+            PushDesc<T>& p = d.push[(size_t)s * n + i];
+            p.src = arrays<T>(sp, sp.cur);
+            p.dst = arrays<T>(sp, 1 - sp.cur);
+            p.start = sp.start;
+            p.start_new = sp.start_alt;
+            p.n9 = c->n9;
+            p.off9 = c->off9;
+            p.Eth = (const T*)c->Eth;
+            p.B = (const T*)c->B[c->bcur];
+            p.En = (const T*)c->En;
+            p.g = c->g;
+            p.beta = (T)(c->cfg.q[s] * c->g.dt / (2.0 * c->cfg.m[s]));
+            p.dt_dx = (T)(c->g.dt / c->g.dx);
+            p.dt_dy = (T)(c->g.dt / c->g.dy);
+            p.qdt = (T)(c->cfg.q[s] * c->g.dt);
+            p.m = (T)c->cfg.m[s];
+            p.led = c->dled + kLedgerField + kLedgerSpecies * s + 1;
+            p.err = c->dpush;
+            p.unit0 = u0;
+        }
+        u0 += row_units(c->g);
+    }
+    *total = u0;
+}
+
+}  // namespace
+
+// what a shared graph slot was captured for, per instance
+struct SharedKey {
+    uint64_t gen = 0;
+    int bcur = -1;
+    int32_t* start[kMaxSpecies] = {};
+};
+
+struct relsim_shared {
+    std::vector<relsim_ctx*> c;
+    std::vector<SharedKey> key[2];
+    int prec = 32, nsp = 1;
+    bool pred = false;
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    void* desc[2] = {nullptr, nullptr};   // device descriptors of the two layouts
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    long long k_static[2] = {0, 0};
+    std::vector<long long> k_cycle, k_iter;   // per instance
+    int total_units = 0;
+    int dep_blocks = 0, push_blocks = 0;           // the launches' grids
+    int dep_blocks_req = 0, push_blocks_req = 0;   // as asked for (0: default)
+    int64_t steps = 0;
+};
+
+namespace {
+
+// every instance on the shared path: 2D, linear shapes, one-cell moves, ready
+// for graph steps, the same precision, species count and reading of gbar,
+// every species loaded
+bool shared_eligible(const std::vector<relsim_ctx*>& cs)
+{
+    if (cs.empty()) return false;
+    for (relsim_ctx* c : cs) {
+        if (!graph_eligible(c) || !c->fast_sort || c->g.dim != 2 || c->g.shape != 1) return false;
+        if (c->prec != cs[0]->prec || c->cfg.nspecies != cs[0]->cfg.nspecies ||
+            (c->En != nullptr) != (cs[0]->En != nullptr))
+            return false;
+        for (int s = 0; s < c->cfg.nspecies; ++s)
+            if (c->sp[s].n <= 0) return false;
+    }
+    return true;
+}
+
+// capture one step of every instance for the current buffer layout into
+// graph slot k (descriptors already uploaded to sb->desc[k])
+template <typename T>
+int shared_capture(relsim_shared* sb, int k)
+{
+    const int n = (int)sb->c.size(), nsp = sb->nsp;
+    relsim_ctx* c0 = sb->c[0];
+    const DepDesc<T>* ddep = (const DepDesc<T>*)sb->desc[k];
+    const PushDesc<T>* dpush = (const PushDesc<T>*)((const unsigned char*)sb->desc[k] + sizeof(DepDesc<T>) * n);
+    std::vector<StepGraph> tally(n);
+    sb->k_static[k] = 0;
+    t_capture_count = &sb->k_static[k];
+    int r = RELSIM_OK;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(sb->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        t_capture_count = nullptr;
+        return fail(c0, RELSIM_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    auto run = [&]() -> int {
+        for (relsim_ctx* c : sb->c) {
+            CK(cudaMemsetAsync(c->M, 0, c->esz * (size_t)c->g.ncell * mblock_of(c->g), sb->st));
+            CK(cudaMemsetAsync(c->J, 0, c->esz * 3 * (size_t)c->g.ncell, sb->st));
+        }
+        CK_CTX(c0, deposit_batch<T>(ddep, n, sb->total_units, sb->pred, c0->dpush, sb->st, sb->dep_blocks));
+        CK_CTX(c0, cudaEventRecord(sb->fork, sb->st));
+        for (int i = 0; i < n; ++i) {
+            relsim_ctx* c = sb->c[i];
+            CK(cudaStreamWaitEvent(c->gst, sb->fork, 0));
+            cudaStream_t user = c->st;
+            c->st = c->gst;
+            c->capturing = true;
+            t_capture_count = &tally[i].k_static;
+            const GmSetup S = gm_setup(c);
+            int rr = capture_solve<T>(c, S, tally[i]);
+            for (int s = 0; s < nsp && rr == RELSIM_OK; ++s) {
+                double* led = c->dled + kLedgerField + kLedgerSpecies * s;
+                // K0 of this step is the kinetic energy the last push left;
+                // the shared push adds its sums into the slots after it
+                if (cudaMemcpyAsync(led, led + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess ||
+                    cudaMemsetAsync(led + 1, 0, sizeof(double) * (kLedgerSpecies - 1), c->st) != cudaSuccess)
+                    rr = fail(c0, RELSIM_ERR_CUDA, "ledger slots: %s", cudaGetErrorString(cudaGetLastError()));
+            }
+            if (rr == RELSIM_OK && cudaEventRecord(sb->join[i], c->st) != cudaSuccess)
+                rr = fail(c0, RELSIM_ERR_CUDA, "join");
+            c->st = user;
+            c->capturing = false;
+            t_capture_count = &sb->k_static[k];
+            if (rr != RELSIM_OK) return rr;
+            sb->k_static[k] += tally[i].k_static;
+            sb->k_cycle[i] = tally[i].k_cycle;
+            sb->k_iter[i] = tally[i].k_iter;
+        }
+        for (int i = 0; i < n; ++i) CK_CTX(c0, cudaStreamWaitEvent(sb->st, sb->join[i], 0));
+        for (int s = 0; s < nsp; ++s) {
+            const PushDesc<T>* dp = dpush + (size_t)s * n;
+            CK_CTX(c0, push_sort_batch<T>(dp, n, sb->total_units, sb->pred, sb->push_blocks, sb->st));
+            CK_CTX(c0, cudaEventRecord(sb->fork, sb->st));
+            for (int i = 0; i < n; ++i) {
+                relsim_ctx* c = sb->c[i];
+                Species& sp = c->sp[s];
+                CK(cudaStreamWaitEvent(c->gst, sb->fork, 0));
+                CK(move_counts(c->n9, c->count_new, c->g, c->gst));
+                CK(scan_exclusive_i32(c->count_new, sp.start_alt, c->g.ncell, sp.start_alt + c->g.ncell, c->scan_tmp,
+                                      c->gst));
+                CK(cudaEventRecord(sb->join[i], c->gst));
+            }
+            for (int i = 0; i < n; ++i) CK_CTX(c0, cudaStreamWaitEvent(sb->st, sb->join[i], 0));
+            CK_CTX(c0, permute_batch<T>(dp, n, sb->total_units, sb->st));
+        }
+        for (relsim_ctx* c : sb->c) CK(cudaMemcpyAsync(c->hpush, c->dpush, sizeof(int), cudaMemcpyDeviceToHost, sb->st));
+        return RELSIM_OK;
+    };
+    r = run();
+    e = cudaStreamEndCapture(sb->st, &graph);
+    t_capture_count = nullptr;
+    if (r == RELSIM_OK && e != cudaSuccess) r = fail(c0, RELSIM_ERR_CUDA, "shared capture: %s", cudaGetErrorString(e));
+    if (r == RELSIM_OK) {
+        e = cudaGraphInstantiate(&sb->exec[k], graph, 0);
+        if (e != cudaSuccess) {
+            sb->exec[k] = nullptr;
+            r = fail(c0, RELSIM_ERR_CUDA, "shared cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();
+    if (r == RELSIM_OK) {
+        sb->key[k].assign(n, SharedKey{});
+        for (int i = 0; i < n; ++i) {
+            SharedKey& q = sb->key[k][i];
+            q.gen = sb->c[i]->gen;
+            q.bcur = sb->c[i]->bcur;
+            for (int s = 0; s < kMaxSpecies; ++s) q.start[s] = sb->c[i]->sp[s].start;
+        }
+    }
+    return r;
+}
+
+// the graph slot captured for every instance's current buffer layout, -1 if
+// none (an instance was reloaded, retuned or stepped on its own since)
+int shared_slot(const relsim_shared* sb)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (!sb->exec[k] || sb->key[k].size() != sb->c.size()) continue;
+        bool ok = true;
+        for (size_t i = 0; i < sb->c.size() && ok; ++i) {
+            const relsim_ctx* c = sb->c[i];
+            const SharedKey& q = sb->key[k][i];
+            ok = q.gen == c->gen && q.bcur == c->bcur && graph_eligible(c);
+            for (int s = 0; s < kMaxSpecies && ok; ++s) ok = q.start[s] == c->sp[s].start;
+        }
+        if (ok) return k;
+    }
+    return -1;
+}
+
+template <typename T>
+int shared_upload(relsim_shared* sb, int k)
+{
+    SharedDesc<T> d;
+    shared_descs<T>(sb->c, d, &sb->total_units);
+    const size_t bd = sizeof(DepDesc<T>) * d.dep.size(), bp = sizeof(PushDesc<T>) * d.push.size();
+    if (!sb->desc[k] && cudaMalloc(&sb->desc[k], bd + bp) != cudaSuccess) return RELSIM_ERR_OOM;
+    if (cudaMemcpy(sb->desc[k], d.dep.data(), bd, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy((unsigned char*)sb->desc[k] + bd, d.push.data(), bp, cudaMemcpyHostToDevice) != cudaSuccess)
+        return RELSIM_ERR_CUDA;
+    return RELSIM_OK;
+}
+
+template <typename T>
+int shared_prepare(relsim_shared* sb)
+{
+    const int n = (int)sb->c.size();
+    relsim_ctx* c = sb->c[0];
+    for (relsim_ctx* ci : sb->c) {
+        TRY(solve_reserve(ci, gm_setup(ci)));
+        CK_CTX(ci, cudaStreamSynchronize(ci->st));
+    }
+    int dev = 0, nsm = 152;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (sb->dep_blocks <= 0) sb->dep_blocks = 2 * nsm;
+    if (sb->push_blocks <= 0) sb->push_blocks = 16 * nsm;
+    sb->k_cycle.assign(n, 0);
+    sb->k_iter.assign(n, 0);
+    for (int k = 0; k < 2; ++k) {
+        int r = shared_upload<T>(sb, k);
+        if (r == RELSIM_OK) r = shared_capture<T>(sb, k);
+        if (r != RELSIM_OK) {
+            if (k == 1)
+                for (relsim_ctx* ci : sb->c) push_commit(ci);
+            return r;
+        }
+        for (relsim_ctx* ci : sb->c) push_commit(ci);   // the next layout; after both, the first again
+    }
+    return RELSIM_OK;
+}
+
+}  // namespace
+
 namespace relsim {
+
+int shared_create(relsim_ctx* const* ctxs, int count, int dep_blocks, int push_blocks, relsim_shared** out)
+{
+    *out = nullptr;
+    std::vector<relsim_ctx*> cs(ctxs, ctxs + count);
+    if (!shared_eligible(cs)) return 0;
+    relsim_shared* sb = new (std::nothrow) relsim_shared;
+    if (!sb) return RELSIM_ERR_OOM;
+    sb->c = cs;
+    sb->prec = cs[0]->prec;
+    sb->nsp = cs[0]->cfg.nspecies;
+    sb->pred = cs[0]->En != nullptr;
+    sb->dep_blocks = sb->dep_blocks_req = dep_blocks;
+    sb->push_blocks = sb->push_blocks_req = push_blocks;
+    sb->join.assign(count, nullptr);
+    int r = RELSIM_OK;
+    if (cudaStreamCreateWithFlags(&sb->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sb->fork, cudaEventDisableTiming) != cudaSuccess)
+        r = RELSIM_ERR_CUDA;
+    for (int i = 0; i < count && r == RELSIM_OK; ++i)
+        if (cudaEventCreateWithFlags(&sb->join[i], cudaEventDisableTiming) != cudaSuccess) r = RELSIM_ERR_CUDA;
+    if (r == RELSIM_OK) r = sb->prec == 32 ? shared_prepare<float>(sb) : shared_prepare<double>(sb);
+    if (r != RELSIM_OK) {
+        shared_destroy(sb);
+        return r;
+    }
+    *out = sb;
+    return 1;
+}
+
+void shared_destroy(relsim_shared* sb)
+{
+    if (!sb) return;
+    if (sb->st) cudaStreamSynchronize(sb->st);
+    for (int k = 0; k < 2; ++k) {
+        if (sb->exec[k]) cudaGraphExecDestroy(sb->exec[k]);
+        if (sb->desc[k]) cudaFree(sb->desc[k]);
+    }
+    for (cudaEvent_t e : sb->join)
+        if (e) cudaEventDestroy(e);
+    if (sb->fork) cudaEventDestroy(sb->fork);
+    if (sb->st) cudaStreamDestroy(sb->st);
+    (void)cudaGetLastError();
+    delete sb;
+}
+
+cudaStream_t shared_stream(const relsim_shared* sb) { return sb->st; }
+
+bool shared_valid(const relsim_shared* sb, relsim_ctx* const* ctxs, int count, int dep_blocks, int push_blocks)
+{
+    if (!sb || (int)sb->c.size() != count || sb->dep_blocks_req != dep_blocks || sb->push_blocks_req != push_blocks)
+        return false;
+    for (int i = 0; i < count; ++i)
+        if (sb->c[i] != ctxs[i]) return false;
+    return shared_slot(sb) >= 0;
+}
+
+// one step of every instance: the graph of the current layout, then each
+// instance's solve outcome copied to heads + i * head_stride (pinned)
+int shared_enqueue(relsim_shared* sb, unsigned char* heads, size_t head_stride)
+{
+    const int k = shared_slot(sb);
+    relsim_ctx* c0 = sb->c[0];
+    if (k < 0) return fail(c0, RELSIM_ERR_INTERNAL, "no shared graph for the instances' current layout");
+    CK_CTX(c0, cudaGraphLaunch(sb->exec[k], sb->st));
+    for (size_t i = 0; i < sb->c.size(); ++i) {
+        relsim_ctx* c = sb->c[i];
+        CK_CTX(c0, cudaMemcpyAsync(heads + i * head_stride, c->gms, kGmHead, cudaMemcpyDeviceToHost, sb->st));
+        push_commit(c);
+        c->state = kReady;
+        c->have_step = true;
+        ++c->step;
+        ++c->graph_steps;
+    }
+    ++sb->steps;
+    return RELSIM_OK;
+}
+
+// one instance's outcome of a shared step (after the batch's stream was
+// synchronised); counts the kernels its branches ran
+int shared_outcome(relsim_shared* sb, int i, const void* head, int* iters, bool first)
+{
+    relsim_ctx* c = sb->c[i];
+    GmState h;
+    memcpy(&h, head, kGmHead);
+    if (first) count_launches((int)sb->k_static[0]);
+    count_launches((int)(sb->k_cycle[i] * h.restarts + sb->k_iter[i] * h.total));
+    // the shared deposit reports its staging timeouts on the first instance
+    if (i != 0 && (*sb->c[0]->hpush & 2))
+        return fail(c, RELSIM_ERR_TIMEOUT, "a shared-memory staging wait of the shared deposit gave up");
+    TRY(check_push(c));
+    return solve_outcome(c, &h, iters, nullptr);
+}
 
 size_t ctx_graph_head_bytes() { return kGmHead; }
 

@@ -46,6 +46,54 @@ struct DepositSpecies {
     T cM[kMaxSpecies];     // q beta / dV
 };
 
+// One instance's species in a shared launch over several instances (the
+// push and the re-sort of the batched 2D form with linear shapes): its
+// arrays, fields, grid and constants, its ledger slots (dK, work, mismatch,
+// K1, added to atomically) and the first unit of the instance in the
+// launch's numbering (ascending across the descriptors).
+template <typename T>
+struct PushDesc {
+    PArrays<T> src, dst;
+    const int32_t* start;       // cell starts of src (the push's input)
+    const int32_t* start_new;   // the new cell starts (the re-sort's)
+    int32_t* n9;
+    int32_t* off9;
+    const T* Eth;
+    const T* B;
+    const T* En;
+    GridP g;
+    T beta, dt_dx, dt_dy, qdt, m;
+    double* led;
+    int* err;
+    int unit0;
+};
+
+// One instance in a shared deposit launch: its species' particles (as the
+// single-instance deposit takes them), B, E^n (the predicted-gamma form),
+// its mass matrix and current, grid, and first unit.
+template <typename T>
+struct DepDesc {
+    DepositSpecies<T> ds;
+    const T* B;
+    const T* En;
+    T* M;
+    T* J;
+    GridP g;
+    int unit0;
+};
+
+// shared launches over several instances (descs in device memory, unit0
+// ascending; all instances of the 2D form with linear shapes and one-cell
+// moves, the same precision, species count and reading of gbar)
+template <typename T>
+cudaError_t deposit_batch(const DepDesc<T>* descs, int ninst, int total_units, bool pred, int* err, cudaStream_t st,
+                          int blocks);
+template <typename T>
+cudaError_t push_sort_batch(const PushDesc<T>* descs, int ninst, int total_units, bool pred, int blocks,
+                            cudaStream_t st);   // ledger sums added to each descriptor's led
+template <typename T>
+cudaError_t permute_batch(const PushDesc<T>* descs, int ninst, int total_units, cudaStream_t st);
+
 // ----- sort.cu -----
 // exclusive scan of n int32 values (n <= 4096*16384); out may alias in;
 // *total (device) receives the sum if non-null. tmp: scan_tmp_size(n) ints.
@@ -195,7 +243,8 @@ cudaError_t push_adjoint(PArrays<T> src, const int32_t* start, const double* gu1
 template <typename T>
 cudaError_t permute(PArrays<T> src, PArrays<T> dst, const int32_t* start_new, const int32_t* n9,
                     const int32_t* off9, GridP g, int* err, cudaStream_t st);
-int push_grid_blocks(GridP g, int precision, int cap = 0);   // cap: most blocks (0: 152 x 16)
+int push_grid_blocks(GridP g, int precision, int cap = 0);
+int row_units(GridP g);   // the row units (up to 32 cells of one row) of the 2D particle passes   // cap: most blocks (0: 152 x 16)
 // weighted and counted histogram of gamma - 1 (variable 0) or |u| (1) over
 // nbins bins between ascending edges (nbins + 1, rounded up to T), plus the
 // bins below and above them: wsum/cnt[nbins + 2], accumulated (zero them)
@@ -378,4 +427,22 @@ size_t ctx_graph_head_bytes();
 int ctx_graph_prepare(relsim_ctx* c);
 int ctx_graph_enqueue(relsim_ctx* c, void* head);
 int ctx_graph_outcome(relsim_ctx* c, const void* head, int* iters);
+}  // namespace relsim
+
+// shared launches over the instances of a batch (capi.cu): create returns 1
+// and *out when every instance qualifies (then both layouts are captured),
+// 0 when one does not, or a negative error; enqueue launches one step of all
+// instances on the shared stream and copies each instance's solve outcome
+// to heads + i head_stride; outcome reads instance i's after the stream was
+// synchronised (first: count the shared kernels once per step)
+struct relsim_shared;
+namespace relsim {
+int shared_create(relsim_ctx* const* ctxs, int count, int dep_blocks, int push_blocks, relsim_shared** out);
+void shared_destroy(relsim_shared* sb);
+cudaStream_t shared_stream(const relsim_shared* sb);
+int shared_enqueue(relsim_shared* sb, unsigned char* heads, size_t head_stride);
+// the shared graphs still fit these instances (same contexts and grids, no
+// reload, retune or lone step since the capture)
+bool shared_valid(const relsim_shared* sb, relsim_ctx* const* ctxs, int count, int dep_blocks, int push_blocks);
+int shared_outcome(relsim_shared* sb, int i, const void* head, int* iters, bool first);
 }  // namespace relsim

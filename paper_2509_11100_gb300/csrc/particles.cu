@@ -405,10 +405,77 @@ __device__ __forceinline__ void deposit_particle(const T fx, const T fy, const T
     acc.add(t, e);
 }
 
-template <typename T, bool PRED>
-__global__ void __launch_bounds__(kDepThreads, sizeof(T) == 4 ? 2 : 1)
-k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ En, T* __restrict__ M,
-          T* __restrict__ J, GridP g, int* __restrict__ err)
+// the instance of a shared launch that owns global unit u: the last whose
+// first unit is <= u (the descriptors ascend in unit0)
+template <typename D>
+__device__ __forceinline__ int find_inst(const D* __restrict__ d, int n, int u)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].unit0 <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Where the deposit's units come from: one instance (the kernel's own
+// arguments) or the instances of a shared launch (units numbered across them;
+// the stage of a unit takes its instance's particles, fields and grid).
+template <typename T>
+struct DepSingle {
+    const DepositSpecies<T>* sp;   // the kernel's own (grid-constant) argument
+    const T* B;
+    const T* En;
+    T* M;
+    T* J;
+    GridP g;
+    __device__ __forceinline__ int nsp() const { return sp->nsp; }
+    __device__ __forceinline__ int nunits() const { return units_of(g.nx, g.ny); }
+    __device__ __forceinline__ int inst(int) const { return 0; }
+    __device__ __forceinline__ int unit(int, int gu) const { return gu; }
+    __device__ __forceinline__ GridP grid(int) const { return g; }
+    __device__ __forceinline__ const int32_t* start(int, int s) const { return sp->start[s]; }
+    __device__ __forceinline__ const T* arr(int, int a, int s) const
+    {
+        return a == 0 ? sp->fx[s] : a == 1 ? sp->fy[s] : a == 2 ? sp->ux[s] : a == 3 ? sp->uy[s]
+               : a == 4 ? sp->uz[s] : sp->w[s];
+    }
+    __device__ __forceinline__ T beta(int, int s) const { return sp->beta[s]; }
+    __device__ __forceinline__ T cJ(int, int s) const { return sp->cJ[s]; }
+    __device__ __forceinline__ T cM(int, int s) const { return sp->cM[s]; }
+    __device__ __forceinline__ const T* Bf(int) const { return B; }
+    __device__ __forceinline__ const T* Enf(int) const { return En; }
+    __device__ __forceinline__ T* Mf(int) const { return M; }
+    __device__ __forceinline__ T* Jf(int) const { return J; }
+};
+
+template <typename T>
+struct DepBatch {
+    const DepDesc<T>* __restrict__ d;
+    int n, total;
+    __device__ __forceinline__ int nsp() const { return d[0].ds.nsp; }
+    __device__ __forceinline__ int nunits() const { return total; }
+    __device__ __forceinline__ int inst(int gu) const { return find_inst(d, n, gu); }
+    __device__ __forceinline__ int unit(int i, int gu) const { return gu - d[i].unit0; }
+    __device__ __forceinline__ GridP grid(int i) const { return d[i].g; }
+    __device__ __forceinline__ const int32_t* start(int i, int s) const { return d[i].ds.start[s]; }
+    __device__ __forceinline__ const T* arr(int i, int a, int s) const
+    {
+        const DepositSpecies<T>& sp = d[i].ds;
+        return a == 0 ? sp.fx[s] : a == 1 ? sp.fy[s] : a == 2 ? sp.ux[s] : a == 3 ? sp.uy[s] : a == 4 ? sp.uz[s] : sp.w[s];
+    }
+    __device__ __forceinline__ T beta(int i, int s) const { return d[i].ds.beta[s]; }
+    __device__ __forceinline__ T cJ(int i, int s) const { return d[i].ds.cJ[s]; }
+    __device__ __forceinline__ T cM(int i, int s) const { return d[i].ds.cM[s]; }
+    __device__ __forceinline__ const T* Bf(int i) const { return d[i].B; }
+    __device__ __forceinline__ const T* Enf(int i) const { return d[i].En; }
+    __device__ __forceinline__ T* Mf(int i) const { return d[i].M; }
+    __device__ __forceinline__ T* Jf(int i) const { return d[i].J; }
+};
+
+template <typename T, bool PRED, class Src>
+__device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ err)
 {
     constexpr int G = kDepG;
     constexpr int NB = kDepBuf;
@@ -422,9 +489,8 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
     T* buf = reinterpret_cast<T*>(dsmem);
     const int tid = threadIdx.x;
     const int gl = tid % G, grp = tid / G;
-    const int nx = g.nx, ny = g.ny, nc = g.ncell;
-    const int nsp = sp.nsp;
-    const int nunits = units_of(nx, ny);
+    const int nsp = src.nsp();
+    const int nunits = src.nunits();
     const int myunits = blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int nstages = myunits * nsp;
 
@@ -438,9 +504,12 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
     auto issue = [&](int k) {
         if (k >= nstages) return;
         const int b = k % NB;
-        const Unit un = unit_of(blockIdx.x + (k / nsp) * gridDim.x, nx);
+        const int gu = blockIdx.x + (k / nsp) * gridDim.x;
+        const int ii = src.inst(gu);
+        const Unit un = unit_of(src.unit(ii, gu), src.grid(ii).nx);
         const int s = k % nsp;
-        const int p0 = sp.start[s][un.c0], p1 = sp.start[s][un.c0 + un.cn];
+        const int32_t* st0 = src.start(ii, s);
+        const int p0 = st0[un.c0], p1 = st0[un.c0 + un.cn];
         const int p0a = p0 & ~(A - 1);
         const int p1a = (p1 + A - 1) & ~(A - 1);
         const int cnt = p1a - p0a;
@@ -450,9 +519,8 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
             const unsigned bytes = (unsigned)(cnt * sizeof(T));
             mbar_expect_tx_arrive(&mbar[b], 6 * bytes);
             T* dst = buf + (size_t)b * 6 * kDepCap;
-            const T* srcs[6] = {sp.fx[s], sp.fy[s], sp.ux[s], sp.uy[s], sp.uz[s], sp.w[s]};
 #pragma unroll
-            for (int a = 0; a < 6; ++a) bulk_g2s(dst + a * kDepCap, srcs[a] + p0a, bytes, &mbar[b]);
+            for (int a = 0; a < 6; ++a) bulk_g2s(dst + a * kDepCap, src.arr(ii, a, s) + p0a, bytes, &mbar[b]);
         } else {
             sstaged[b] = 0;
             mbar_expect_tx_arrive(&mbar[b], 0);
@@ -467,12 +535,16 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
     for (int k = 0; k < nstages; ++k) {
         if (tid == 0) issue(k + NB - 1);
         const int b = k % NB;
-        const Unit un = unit_of(blockIdx.x + (k / nsp) * gridDim.x, nx);
+        const int gu = blockIdx.x + (k / nsp) * gridDim.x;
+        const int ii = src.inst(gu);
+        const GridP gg = src.grid(ii);
+        const int nx = gg.nx, ny = gg.ny, nc = gg.ncell;
+        const Unit un = unit_of(src.unit(ii, gu), nx);
         const int s = k % nsp;
         if (s == 0) {
             acc.zero();
-            load_tile_B<T, kDepThreads>(sB, B, un, nx, ny, nc, tid);
-            if constexpr (PRED) load_tile_E<T, kDepThreads>(sEn.En, En, un, nx, ny, nc, tid);
+            load_tile_B<T, kDepThreads>(sB, src.Bf(ii), un, nx, ny, nc, tid);
+            if constexpr (PRED) load_tile_E<T, kDepThreads>(sEn.En, src.Enf(ii), un, nx, ny, nc, tid);
         }
         const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1), kDepMaxPolls);
         // leave together if any thread gave up (never diverge at a barrier);
@@ -484,8 +556,9 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
         const bool valid = grp < un.cn;
         const int c = un.c0 + grp;
         if (valid) {
-            const int p0 = sp.start[s][c], p1 = sp.start[s][c + 1];
-            const T beta = sp.beta[s], cJ = sp.cJ[s], cM = sp.cM[s];
+            const int32_t* st0 = src.start(ii, s);
+            const int p0 = st0[c], p1 = st0[c + 1];
+            const T beta = src.beta(ii, s), cJ = src.cJ(ii, s), cM = src.cM(ii, s);
             if (sstaged[b]) {
                 const T* sb = buf + (size_t)b * 6 * kDepCap - sp0a[b];
                 for (int p = p0 + gl; p < p1; p += G)
@@ -493,14 +566,17 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
                                               sb[4 * kDepCap + p], sb[5 * kDepCap + p], sB, sEn.en(), grp, beta,
                                               cJ, cM, acc);
             } else {
+                const T *gfx = src.arr(ii, 0, s), *gfy = src.arr(ii, 1, s), *gux = src.arr(ii, 2, s),
+                        *guy = src.arr(ii, 3, s), *guz = src.arr(ii, 4, s), *gw = src.arr(ii, 5, s);
                 for (int p = p0 + gl; p < p1; p += G)
-                    deposit_particle<T, PRED>(ld(sp.fx[s] + p), ld(sp.fy[s] + p), ld(sp.ux[s] + p),
-                                              ld(sp.uy[s] + p), ld(sp.uz[s] + p), ld(sp.w[s] + p), sB, sEn.en(),
-                                              grp, beta, cJ, cM, acc);
+                    deposit_particle<T, PRED>(ld(gfx + p), ld(gfy + p), ld(gux + p), ld(guy + p), ld(guz + p),
+                                              ld(gw + p), sB, sEn.en(), grp, beta, cJ, cM, acc);
             }
         }
         if (s == nsp - 1) {
             acc.template group_reduce<G>();
+            T* const M = src.Mf(ii);
+            T* const J = src.Jf(ii);
             if (valid) {
                 const int i = un.i0 + grp, j = un.j;
                 const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
@@ -529,6 +605,24 @@ k_deposit(DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ E
         // let the copies already issued land before the CTA leaves (bounded)
         for (int kk = kfail; kk < nstages && kk < kfail + NB; ++kk) mbar_wait(&mbar[kk % NB], (kk / NB) & 1, kDepMaxPolls);
     }
+}
+
+template <typename T, bool PRED>
+__global__ void __launch_bounds__(kDepThreads, sizeof(T) == 4 ? 2 : 1)
+k_deposit(const __grid_constant__ DepositSpecies<T> sp, const T* __restrict__ B, const T* __restrict__ En,
+          T* __restrict__ M, T* __restrict__ J, GridP g, int* __restrict__ err)
+{
+    const DepSingle<T> src{&sp, B, En, M, J, g};
+    deposit_core<T, PRED>(src, err);
+}
+
+// the deposit over the units of several instances in one launch
+template <typename T, bool PRED>
+__global__ void __launch_bounds__(kDepThreads, sizeof(T) == 4 ? 2 : 1)
+k_deposit_batch(const DepDesc<T>* __restrict__ descs, int ninst, int total_units, int* __restrict__ err)
+{
+    const DepBatch<T> src{descs, ninst, total_units};
+    deposit_core<T, PRED>(src, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -714,11 +808,29 @@ __device__ __forceinline__ unsigned dir_peers(bool act, int dir)
     return m;
 }
 
-template <typename T, bool PRED>
-__global__ void __launch_bounds__(PushCfg<T>::threads, PushCfg<T>::min_blocks)
-k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int32_t* __restrict__ n9,
-            int32_t* __restrict__ off9, const T* __restrict__ Eth, const T* __restrict__ B,
-            const T* __restrict__ En, GridP g, T beta, T dt_dx, T dt_dy, T qdt, T m, double* __restrict__ lsum)
+// the warp's ledger sums of one unit added to an instance's slots (FP64)
+template <typename T>
+__device__ __forceinline__ void ledger_to_instance(T (&acc)[kLedger], double* led, int lane)
+{
+#pragma unroll
+    for (int s = 0; s < kLedger; ++s) {
+        double v = warp_sum((double)acc[s]);
+        if (lane == 0) atomicAdd(led + s, v);
+        acc[s] = T(0);
+    }
+}
+
+// The push body, shared by the single-instance kernel and the shared launch
+// over several instances (BATCH: units numbered across the instances of
+// descs; each unit takes its instance's arrays, fields, grid and constants,
+// and its ledger sums go to that instance's slots).
+template <typename T, bool PRED, bool BATCH>
+__device__ __forceinline__ void push_sort_core(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start,
+                                               int32_t* __restrict__ n9, int32_t* __restrict__ off9,
+                                               const T* __restrict__ Eth, const T* __restrict__ B,
+                                               const T* __restrict__ En, GridP g, T beta, T dt_dx, T dt_dy, T qdt,
+                                               T m, double* __restrict__ lsum, const PushDesc<T>* __restrict__ descs,
+                                               int ninst, int total_units)
 {
     constexpr int W = PushCfg<T>::warps;
     __shared__ int sstart[W][kUnitW + 1];
@@ -729,16 +841,40 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int nx = g.nx, ny = g.ny, nc = g.ncell;
-    const int nunits = units_of(nx, ny);
+    int nx = g.nx, ny = g.ny, nc = g.ncell;
+    const int nunits = BATCH ? total_units : units_of(nx, ny);
     const unsigned lt = (1u << lane) - 1u;
     int* ss = sstart[wib];
     PushTile<T>& tl = stile[wib];
     PushStage<T>& st = sstage[wib];
-    const bool ids = dst.id != nullptr;
+    bool ids = dst.id != nullptr;
     T acc[kLedger] = {T(0), T(0), T(0), T(0)};
 
-    for (int u = warp; u < nunits; u += nwarps) {
+    for (int ug = warp; ug < nunits; ug += nwarps) {
+        int u = ug;
+        double* led = nullptr;
+        if constexpr (BATCH) {
+            const PushDesc<T>& d = descs[find_inst(descs, ninst, ug)];
+            src = d.src;
+            dst = d.dst;
+            start = d.start;
+            n9 = d.n9;
+            off9 = d.off9;
+            Eth = d.Eth;
+            B = d.B;
+            En = d.En;
+            nx = d.g.nx;
+            ny = d.g.ny;
+            nc = d.g.ncell;
+            beta = d.beta;
+            dt_dx = d.dt_dx;
+            dt_dy = d.dt_dy;
+            qdt = d.qdt;
+            m = d.m;
+            led = d.led;
+            ids = dst.id != nullptr;
+            u = ug - d.unit0;
+        }
         const Unit un = unit_of(u, nx);
         unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
         if constexpr (PRED) {
@@ -912,8 +1048,30 @@ k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, i
             __syncwarp();
             l += gsz;
         }
+        if constexpr (BATCH) ledger_to_instance<T>(acc, led, lane);
     }
-    block_ledger<T>(acc, red, lsum);
+    if constexpr (!BATCH) block_ledger<T>(acc, red, lsum);
+}
+
+template <typename T, bool PRED>
+__global__ void __launch_bounds__(PushCfg<T>::threads, PushCfg<T>::min_blocks)
+k_push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int32_t* __restrict__ n9,
+            int32_t* __restrict__ off9, const T* __restrict__ Eth, const T* __restrict__ B,
+            const T* __restrict__ En, GridP g, T beta, T dt_dx, T dt_dy, T qdt, T m, double* __restrict__ lsum)
+{
+    push_sort_core<T, PRED, false>(src, dst, start, n9, off9, Eth, B, En, g, beta, dt_dx, dt_dy, qdt, m, lsum,
+                                   nullptr, 0, 0);
+}
+
+// the push of one species over the units of several instances in one launch
+template <typename T, bool PRED>
+__global__ void __launch_bounds__(PushCfg<T>::threads, PushCfg<T>::min_blocks)
+k_push_sort_batch(const PushDesc<T>* __restrict__ descs, int ninst, int total_units)
+{
+    PArrays<T> none;
+    memset(&none, 0, sizeof(none));
+    push_sort_core<T, PRED, true>(none, none, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, GridP{}, T(0),
+                                  T(0), T(0), T(0), T(0), nullptr, descs, ninst, total_units);
 }
 
 // General path (moves of more than one cell): push in place order, write the
@@ -976,10 +1134,11 @@ k_push_general(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start
 // then the lanes walk the unit's whole new range, 32 consecutive particles at
 // a time, each finding its cell and run. A cell whose runs do not add up to
 // its new count flags err.
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_permute(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start_new, const int32_t* __restrict__ n9,
-          const int32_t* __restrict__ off9, GridP g, int* __restrict__ err)
+template <typename T, bool BATCH>
+__device__ __forceinline__ void permute_core(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start_new,
+                                             const int32_t* __restrict__ n9, const int32_t* __restrict__ off9,
+                                             GridP g, int* __restrict__ err, const PushDesc<T>* __restrict__ descs,
+                                             int ninst, int total_units)
 {
     __shared__ int scs[8][kUnitW + 1];          // new cell starts of the unit
     __shared__ int srs[8][kUnitW][kNDir];       // run start in src, in run order
@@ -987,11 +1146,27 @@ k_permute(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start_new,
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int nx = g.nx, ny = g.ny;
-    const int nunits = units_of(nx, ny);
-    const bool ids = dst.id != nullptr;
+    int nx = g.nx, ny = g.ny;
+    const int nunits = BATCH ? total_units : units_of(nx, ny);
+    bool ids = dst.id != nullptr;
     int* cs = scs[wib];
-    for (int u = warp; u < nunits; u += nwarps) {
+    for (int ug = warp; ug < nunits; ug += nwarps) {
+        int u = ug;
+        if constexpr (BATCH) {
+            // the re-sort reads the push's output (dst of the push) and
+            // writes the new order back into the push's input
+            const PushDesc<T>& d = descs[find_inst(descs, ninst, ug)];
+            src = d.dst;
+            dst = d.src;
+            start_new = d.start_new;
+            n9 = d.n9;
+            off9 = d.off9;
+            err = d.err;
+            nx = d.g.nx;
+            ny = d.g.ny;
+            ids = dst.id != nullptr;
+            u = ug - d.unit0;
+        }
         const Unit un = unit_of(u, nx);
         const int cn = un.cn;
 #pragma unroll
@@ -1075,6 +1250,24 @@ k_permute(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start_new,
         }
         __syncwarp();
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_permute(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start_new, const int32_t* __restrict__ n9,
+          const int32_t* __restrict__ off9, GridP g, int* __restrict__ err)
+{
+    permute_core<T, false>(src, dst, start_new, n9, off9, g, err, nullptr, 0, 0);
+}
+
+// the re-sort of one species over the units of several instances
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_permute_batch(const PushDesc<T>* __restrict__ descs, int ninst, int total_units)
+{
+    PArrays<T> none;
+    memset(&none, 0, sizeof(none));
+    permute_core<T, true>(none, none, nullptr, nullptr, nullptr, GridP{}, nullptr, descs, ninst, total_units);
 }
 
 template <typename T>
@@ -1590,6 +1783,8 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
 
 }  // namespace (the adjoints)
 
+int row_units(GridP g) { return units_of(g.nx, g.ny); }
+
 int push_grid_blocks(GridP g, int precision, int cap)
 {
     return blocks_for(units_of(g.nx, g.ny), precision == 32 ? PushCfg<float>::warps : PushCfg<double>::warps,
@@ -1665,6 +1860,41 @@ cudaError_t push_sort(PArrays<T> src, PArrays<T> dst, const int32_t* start, int3
     kern<<<lsum_blocks, PushCfg<T>::threads, 0, st>>>(src, dst, start, n9, off9, Eth, B, En, g, beta,
                                                       (T)(g.dt / g.dx), (T)(g.dt / g.dy), (T)(sc.q * g.dt),
                                                       (T)sc.m, lsum_partial);
+    return cudaGetLastError();
+}
+
+// shared launches over the instances of a batch (units numbered across them)
+template <typename T>
+cudaError_t deposit_batch(const DepDesc<T>* descs, int ninst, int total_units, bool pred, int* err, cudaStream_t st,
+                          int blocks)
+{
+    const size_t smem = (size_t)kDepBuf * 6 * kDepCap * sizeof(T);
+    auto kern = pred ? k_deposit_batch<T, true> : k_deposit_batch<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (blocks > total_units) blocks = total_units;
+    if (blocks < 1) blocks = 1;
+    count_launches(1);
+    kern<<<blocks, kDepThreads, smem, st>>>(descs, ninst, total_units, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t push_sort_batch(const PushDesc<T>* descs, int ninst, int total_units, bool pred, int blocks,
+                            cudaStream_t st)
+{
+    auto kern = pred ? k_push_sort_batch<T, true> : k_push_sort_batch<T, false>;
+    const int need = blocks_for(total_units, PushCfg<T>::warps, blocks > 0 ? blocks : 152 * 16);
+    count_launches(1);
+    kern<<<need, PushCfg<T>::threads, 0, st>>>(descs, ninst, total_units);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t permute_batch(const PushDesc<T>* descs, int ninst, int total_units, cudaStream_t st)
+{
+    count_launches(1);
+    k_permute_batch<T><<<blocks_for(total_units, 8, 152 * 16), 256, 0, st>>>(descs, ninst, total_units);
     return cudaGetLastError();
 }
 
@@ -1746,6 +1976,9 @@ cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int 
                                              double*, int32_t*, cudaStream_t);                     \
     template cudaError_t deposit<T>(const DepositSpecies<T>&, const T*, const T*, T*, T*, GridP, int*,  \
                                     cudaStream_t, int);                                             \
+    template cudaError_t deposit_batch<T>(const DepDesc<T>*, int, int, bool, int*, cudaStream_t, int); \
+    template cudaError_t push_sort_batch<T>(const PushDesc<T>*, int, int, bool, int, cudaStream_t);  \
+    template cudaError_t permute_batch<T>(const PushDesc<T>*, int, int, cudaStream_t);              \
     template cudaError_t push_sort<T>(PArrays<T>, PArrays<T>, const int32_t*, int32_t*, int32_t*,   \
                                       const T*, const T*, const T*, GridP, SpeciesConst, double*,   \
                                       int, int*, cudaStream_t);                                           \

@@ -141,8 +141,10 @@ def parameter_gradient(grads, state_minus, state_plus, h, jump=1e-3):
     and p + h from the same random numbers, over E, B and every particle's
     position, momentum and weight. A particle whose momentum changes by more
     than `jump` between the two states took a different discrete choice in
-    the loader (a sheet membership or a flip) and is left out. Returns
-    (dL/dp, number of particles left out)."""
+    the loader (a sheet membership or a flip) and is left out; jump=None
+    keeps every particle (a loader with no discrete choice, e.g. the
+    weighted Harris loading). Returns (dL/dp, number of particles left
+    out)."""
     g = float(np.sum(grads["E"] * (np.asarray(state_plus["E"]) - np.asarray(state_minus["E"]))))
     g += float(np.sum(grads["B"] * (np.asarray(state_plus["B"]) - np.asarray(state_minus["B"]))))
     out = 0
@@ -152,7 +154,7 @@ def parameter_gradient(grads, state_minus, state_plus, h, jump=1e-3):
         du = np.stack([np.asarray(sp[k]) - np.asarray(sm[k]) for k in ("ux", "uy", "uz")], axis=1)
         dx = np.stack([np.asarray(sp[k]) - np.asarray(sm[k]) for k in ("x", "y")], axis=1)
         dw = np.asarray(sp["w"]) - np.asarray(sm["w"])
-        keep = np.abs(du).max(axis=1) <= jump
+        keep = np.ones(dw.shape, bool) if jump is None else np.abs(du).max(axis=1) <= jump
         out += int((~keep).sum())
         g += float(np.sum(gu[keep] * du[keep]) + np.sum(gx[keep] * dx[keep]) + np.sum(gw[keep] * dw[keep]))
     return g / (2.0 * h), out

@@ -34,6 +34,17 @@ design notes of this repository):
   simulations"), all written here from the mathematics.
 * The initial perturbation is dB_y = pert * B0 * cos(2 pi m x / L_x) at cell
   centres (divergence free, uniform in y), m = pert_mode (1 by default).
+* loader = "weighted" is a second loading of the same equilibrium whose
+  particles are smooth functions of the parameters for fixed random numbers
+  (for gradients in delta, theta_T, ... by central differences): each cell's
+  ppc particles take fixed roles by their index in the cell (k mod 3:
+  background, sheet 1, sheet 2), a role's weight is its density n_role(y) dx
+  dy over the role's count in the cell, and the drifting members are boosted
+  without the flip, their weight multiplied by 1 + beta v'_z instead (the
+  rest-frame draw has density f'(u'); the drifting Maxwell-Juettner law is
+  (gamma/gamma') f'(u') = Gamma (1 + beta v'_z) f'(u'), and the mean of
+  1 + beta v'_z over the isotropic rest frame is 1, so the lab density stays
+  n_role). No discrete choice depends on a parameter.
 """
 from __future__ import annotations
 
@@ -49,6 +60,7 @@ __all__ = [
     "random_state",
     "sample_maxwell_juettner",
     "boost_flip",
+    "boost_weighted",
 ]
 
 
@@ -66,6 +78,7 @@ class HarrisConfig:
     sigma: float = 10.0      # B0^2 / (n_b m c^2): background magnetization
     pert: float = 0.01       # dB_y / B0, single cosine mode in x
     pert_mode: int = 1       # its mode number m: k_x = 2 pi m / L_x
+    loader: str = "sampled"  # "sampled" (sheet membership drawn, flip boost) or "weighted"
     dt: float = 0.5          # time step, in 1/omega_pe0
     theta: float = 0.5       # implicitness parameter of the field solve
     seed: int = 0
@@ -186,6 +199,18 @@ def boost_flip(rng: np.random.Generator, u: np.ndarray, beta: np.ndarray) -> np.
     return u
 
 
+def boost_weighted(u: np.ndarray, beta: np.ndarray, w: np.ndarray):
+    """Boost rest-frame momenta along z by beta without flipping: u_z' =
+    Gamma (u_z + beta gamma), the weight multiplied by 1 + beta v_z (the
+    factor the flip method realises by mirroring). Returns (u', w')."""
+    u = u.copy()
+    g = np.sqrt(1.0 + (u * u).sum(axis=0))
+    vz = u[2] / g
+    G = 1.0 / np.sqrt(1.0 - beta * beta)
+    u[2] = G * (u[2] + beta * g)
+    return u, w * (1.0 + beta * vz)
+
+
 def make_harris(cfg: HarrisConfig, dtype=np.float64) -> dict:
     """Build the seeded initial state of the double Harris sheet.
 
@@ -218,9 +243,19 @@ def make_harris(cfg: HarrisConfig, dtype=np.float64) -> dict:
     n1 = (1.0 / np.cosh((y - 0.25 * Ly) / a)) ** 2   # sech^2, no overflow far out
     n2 = (1.0 / np.cosh((y - 0.75 * Ly) / a)) ** 2
     ntot = n1 + n2 + d["n_b"]
-    w = ntot * cfg.dx * cfg.dy / ppc
-    rmem = _rng(cfg.seed, 0xFF, 2).random(n)
-    sheet = np.where(rmem < n1 / ntot, 1, np.where(rmem < (n1 + n2) / ntot, 2, 0))
+    if cfg.loader == "sampled":
+        w = ntot * cfg.dx * cfg.dy / ppc
+        rmem = _rng(cfg.seed, 0xFF, 2).random(n)
+        sheet = np.where(rmem < n1 / ntot, 1, np.where(rmem < (n1 + n2) / ntot, 2, 0))
+    elif cfg.loader == "weighted":
+        if ppc < 3:
+            raise ValueError("the weighted loader needs ppc >= 3 (one particle per role)")
+        sheet = np.tile(np.arange(ppc) % 3, ncell)
+        count = np.array([(np.arange(ppc) % 3 == r).sum() for r in range(3)])
+        dens = np.where(sheet == 1, n1, np.where(sheet == 2, n2, d["n_b"]))
+        w = dens * cfg.dx * cfg.dy / count[sheet]
+    else:
+        raise ValueError(f"unknown loader {cfg.loader!r}")
 
     species = []
     for s, (q, m) in enumerate(zip(cfg.q, cfg.m)):
@@ -230,11 +265,15 @@ def make_harris(cfg: HarrisConfig, dtype=np.float64) -> dict:
         sgn_q = 1.0 if q > 0 else -1.0
         beta = np.where(sheet == 1, -sgn_q * d["beta_d"],
                         np.where(sheet == 2, sgn_q * d["beta_d"], 0.0))
-        u = boost_flip(r, u, beta)
+        if cfg.loader == "sampled":
+            u = boost_flip(r, u, beta)
+            ws = w
+        else:
+            u, ws = boost_weighted(u, beta, w)
         species.append({
             "x": x.astype(dtype), "y": y.astype(dtype),
             "ux": u[0].astype(dtype), "uy": u[1].astype(dtype), "uz": u[2].astype(dtype),
-            "w": w.astype(dtype), "q": float(q), "m": float(m),
+            "w": ws.astype(dtype), "q": float(q), "m": float(m),
         })
 
     # fields: E = 0 on nodes; B on cell centres

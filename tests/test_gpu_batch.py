@@ -8,6 +8,8 @@
   the same instances stepped one by one (the deposit's float atomics make
   both runs differ in the last bits, so 1e-4 of the mode energies after a
   few steps), and the batched run's tearing growth rates match the oracle's.
+* shared launches over the instances (relsim_batch_set_shared) equal the
+  per-instance step graphs on the same instances.
 """
 import numpy as np
 import pytest
@@ -154,6 +156,65 @@ def test_batch_equals_instances_stepped_one_by_one(rs):
         B1 = sim.fields()[1]
         assert np.max(np.abs(after[k] - B1)) <= 1e-4 * np.abs(B1).max(), k
         sim.close()
+
+
+@pytest.mark.parametrize("precision,pred", [(32, 0), (32, 1), (64, 0)])
+def test_shared_launches_equal_per_instance_graphs(rs, precision, pred):
+    """Shared launches (one deposit, push and re-sort launch per species over
+    every instance; each instance's solve a branch of the same graph) give
+    the per-instance graphs' results on the same uneven instances: fields,
+    mode energies, every particle by id, the energy ledger and the GMRES
+    iteration counts, up to the order of the deposit's and the ledger's
+    floating-point atomics (FP32: 1e-4 of each quantity's scale after 6
+    steps; FP64: 1e-9)."""
+    import torch
+    steps, nm = 6, 6
+    tol = 1e-4 if precision == 32 else 1e-9
+    out = {}
+    for shared in (True, False):
+        streams = [torch.cuda.Stream() for _ in SIZES]
+        sims = []
+        for hc, stream in zip(SIZES, streams):
+            sim = rs.Simulation(rs.make_config(hc.nx, hc.ny, dt=hc.dt, precision=precision, gmres_tol=1e-6,
+                                               gamma_pred=pred, track_ids=True), stream=stream.cuda_stream)
+            sim.load_state(make_harris(hc))
+            sims.append(sim)
+        batch = rs.Batch(sims, nworkers=3, shared=shared)
+        modes, status, iters = batch.run(steps, component=1, nmodes=nm)
+        assert list(status) == [0] * len(SIZES)
+        assert batch.last_path == ("shared" if shared else "graphs")
+        res = []
+        for sim in sims:
+            E, B = sim.fields()
+            parts = []
+            for s in range(2):
+                x, u, w, ids = sim.particles(s, ids=True)
+                o = np.argsort(ids)
+                parts.append((x[o], u[o], w[o]))
+            res.append((E, B, parts, sim.ledger()))
+        out[shared] = (modes, iters, res)
+        # a second run continues from where the first stopped
+        modes2, status2, _ = batch.run(2, component=1, nmodes=nm)
+        assert list(status2) == [0] * len(SIZES)
+        out[shared] += (modes2,)
+        batch.close()
+        for sim in sims:
+            sim.close()
+    (mA, iA, rA, m2A), (mB, iB, rB, m2B) = out[True], out[False]
+    assert np.max(np.abs(mA - mB)) <= tol * np.abs(mB).max()
+    assert np.max(np.abs(m2A - m2B)) <= tol * np.abs(m2B).max()
+    assert np.max(np.abs(iA - iB)) <= 1
+    for k in range(len(SIZES)):
+        EA, BA, pA, lA = rA[k]
+        EB, BB, pB, lB = rB[k]
+        assert np.max(np.abs(EA - EB)) <= tol * np.abs(EB).max(), k
+        assert np.max(np.abs(BA - BB)) <= tol * np.abs(BB).max(), k
+        for (xa, ua, wa), (xb, ub, wb) in zip(pA, pB):
+            assert np.array_equal(wa, wb)
+            assert np.max(np.abs(ua - ub)) <= tol * max(1.0, np.abs(ub).max()), k
+            assert np.max(np.abs(xa - xb)) <= tol, k
+        for key in ("W_E", "W_B", "K", "work_particles", "mismatch", "total"):
+            assert abs(lA[key] - lB[key]) <= tol * abs(lB["total"]), (k, key, lA[key], lB[key])
 
 
 def test_batch_more_workers_than_instances_and_zero_steps(rs):

@@ -65,7 +65,7 @@ PY_MUTANTS = {
     "modes_nyquist_counted_twice": ("        cm[-1] = 1.0", "        cm[-1] = 2.0"),
     "modes_drops_cell_volume": ("return (0.5 * dV * cm * e / nx)[:nmodes]", "return (0.5 * cm * e / nx)[:nmodes]"),
     "modes_wrong_axis": ("F = np.fft.rfft(Bc, axis=1)", "F = np.fft.rfft(Bc.T, axis=1)"),
-    "growth_fit_no_log": ("np.polyfit(t, np.log(seg), 1)[0]", "np.polyfit(t, seg, 1)[0]"),
+    "growth_fit_no_log": ("slope = np.polyfit(t, np.log(seg), 1)[0]", "slope = np.polyfit(t, seg, 1)[0]"),
     "growth_fit_smallest": ("if best is None or slope > best[0]:", "if best is None or slope < best[0]:"),
     "adjoint_untransposed": ("lam = np.linalg.solve(A.T, gEt)", "lam = np.linalg.solve(A, gEt)"),
     "adjoint_drops_E_extrapolation": ("gE0 = lam - (1.0 - th) / th * gE1", "gE0 = lam"),

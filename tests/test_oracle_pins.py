@@ -468,6 +468,54 @@ def test_harris_drift_and_current_profile():
     assert np.corrcoef(jz, jth)[0, 1] > 0.98
 
 
+def test_weighted_harris_loader_moments_and_smoothness():
+    # the weighted loading of the same sheet: the weighted lab-frame mean
+    # velocity of each drifting role is the boost, its mean Lorentz factor
+    # that of the flip-loaded members, the J_z profile follows -dB_x/dy, and
+    # every particle is a smooth function of delta for fixed random numbers
+    hc = HarrisConfig(nx=32, ny=32, ppc=64, seed=1, loader="weighted")
+    s = make_harris(hc)
+    ref = make_harris(HarrisConfig(nx=32, ny=32, ppc=64, seed=1))
+    d = s["derived"]
+    sheet, sheet_ref = s["sheet"], ref["sheet"]
+    for sp, sr in zip(s["species"], ref["species"]):
+        assert (sp["w"] > 0).all()
+        g = np.sqrt(1 + sp["ux"] ** 2 + sp["uy"] ** 2 + sp["uz"] ** 2)
+        gr = np.sqrt(1 + sr["ux"] ** 2 + sr["uy"] ** 2 + sr["uz"] ** 2)
+        sgn = 1.0 if sp["q"] > 0 else -1.0
+        for role, beta in ((1, -sgn * d["beta_d"]), (2, sgn * d["beta_d"])):
+            m = sheet == role
+            wv = np.sum(sp["w"][m] * sp["uz"][m] / g[m]) / np.sum(sp["w"][m])
+            assert abs(wv - beta) < 0.02, (role, wv, beta)
+            wg = np.sum(sp["w"][m] * g[m]) / np.sum(sp["w"][m])
+            mr = sheet_ref == role
+            assert abs(wg - gr[mr].mean()) < 0.02 * gr[mr].mean()
+    Ly = hc.ny * hc.dy
+    y = s["species"][0]["y"]
+    jz = np.zeros(hc.ny)
+    for sp in s["species"]:
+        g = np.sqrt(1 + sp["ux"] ** 2 + sp["uy"] ** 2 + sp["uz"] ** 2)
+        np.add.at(jz, (y // hc.dy).astype(int), sp["q"] * sp["w"] * sp["uz"] / g)
+    jz /= hc.nx * hc.dx * hc.dy
+    yc = (np.arange(hc.ny) + 0.5) * hc.dy
+    a, B0 = hc.delta, d["B0"]
+    jth = -(B0 / a) * (1 / np.cosh((yc - Ly / 4) / a) ** 2 - 1 / np.cosh((yc - 3 * Ly / 4) / a) ** 2)
+    assert np.abs(jz - jth).max() < 0.15 * np.abs(jth).max()
+    assert np.corrcoef(jz, jth)[0, 1] > 0.98
+    # smooth in delta: a step h moves every particle by O(h), none jumps
+    h = 1e-3
+    sm = make_harris(HarrisConfig(nx=32, ny=32, ppc=64, seed=1, loader="weighted", delta=1.0 - h))
+    sp_ = make_harris(HarrisConfig(nx=32, ny=32, ppc=64, seed=1, loader="weighted", delta=1.0 + h))
+    for a_, b_ in zip(sm["species"], sp_["species"]):
+        assert np.array_equal(a_["x"], b_["x"]) and np.array_equal(a_["y"], b_["y"])
+        for k in ("uz", "w"):
+            assert np.abs(b_[k] - a_[k]).max() < 50 * h * max(1.0, np.abs(a_[k]).max()), k
+        # the second difference is O(h^2): no kink inside the stencil
+        c = s["species"][0] if a_["q"] > 0 else s["species"][1]
+        dd = np.abs(b_["uz"] - 2 * c["uz"] + a_["uz"]).max()
+        assert dd < 1e-4, dd
+
+
 @pytest.mark.parametrize("T", [1e-3, 0.3, 3.0])
 def test_maxwell_juettner_mean_gamma(T):
     # <gamma> of Maxwell-Juettner is K1(1/T)/K2(1/T) + 3 T (scaled Bessel
