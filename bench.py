@@ -242,7 +242,6 @@ def run_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = rs.relsim_kernel_launches() - launches0
-    path = batch.last_path
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -286,8 +285,9 @@ def run_ours(args):
     achieved = ab / (launch_ms / 1e3) / 1e9 if ab else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                # the committed counters are of the gamma(u^n) kernels
-                "traffic": None if args.gamma_pred else traffic_record(dom), "algorithmic_bytes_per_launch": ab,
+                # counters of the kernel variant this run launched
+                "traffic": traffic_record(dom + ("_pred" if args.gamma_pred else "")),
+                "algorithmic_bytes_per_launch": ab,
                 "launch_ms": launch_ms}
     # the mover + mass-matrix kernels together (deposit, push passes, sort tables)
     mover = ("deposit", "push", "sort_tables", "permute")
@@ -621,7 +621,8 @@ def run_scan(args):
         st = make_harris(hc)
         stream = torch.cuda.Stream()
         sim = rs.Simulation(rs.make_config(hc.nx, hc.ny, dt=hc.dt, theta_implicit=hc.theta, precision=32,
-                                           gmres_tol=SCAN["gmres_tol"], gmres_restart=SCAN["gmres_restart"]),
+                                           gmres_tol=SCAN["gmres_tol"], gmres_restart=SCAN["gmres_restart"],
+                                           gamma_pred=args.gamma_pred),
                             stream=stream.cuda_stream)
         sim.load_state(st)
         del st
@@ -632,7 +633,7 @@ def run_scan(args):
     torch.cuda.synchronize()
     t_setup = time.time() - t0
     N = sum(sizes[i] for i in mine)
-    batch = rs.Batch(sims, nworkers=args.workers, shared=args.scan_launch == "shared")
+    batch = rs.Batch(sims, nworkers=args.workers, shared=args.scan_launch == "shared", groups=args.scan_groups)
     batch.run(args.warmup)
     torch.cuda.synchronize()
 
@@ -718,9 +719,11 @@ def run_scan(args):
         "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": dict(SCAN, instances=len(insts), instances_here=len(mine), particles_total=total,
+                       gamma_bar="gamma(u^n + beta E^n(x)) (predicted)" if args.gamma_pred else "gamma(u^n)",
                        particles_here=N, workers=args.workers,
-                       launch={"shared": "one deposit, push and re-sort launch per species over all instances "
-                                         "per step, the instances' solves as branches of one graph",
+                       launch={"shared": f"shared launches: {args.scan_groups} groups of instances, each group's "
+                                         "step one graph (one deposit, push and re-sort launch per species over "
+                                         "the group's instances, their solves as branches) on its own stream",
                                "graphs": "one step graph per instance on its own stream",
                                "host": "host-driven steps by worker threads"}.get(path, path),
                        parallelism=f"instances sharded over {world} ranks" if world > 1 else "single"),
@@ -1083,9 +1086,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (no autotuner pass after the load)")
     ap.add_argument("--long-steps", type=int, default=2000, help="long: the number of steps of the run")
-    ap.add_argument("--gamma-pred", action="store_true",
-                    help="the predicted Lorentz factor gamma(u^n + beta E^n(x)) in alpha, Jhat, M and the push "
-                         "(headline and long workloads)")
+    ap.add_argument("--gamma-bar", choices=["pred", "un"], default="pred",
+                    help="the Lorentz factor in alpha, Jhat, M and the push: pred (default) the predicted "
+                         "gamma(u^n + beta E^n(x)), whose runs keep the energy balance over long runs; un: "
+                         "gamma(u^n) (headline, scan and long workloads, and the reference arm)")
     ap.add_argument("--workload", choices=["c1", "small", "scan", "window", "c2", "c2small", "c1q", "c1qsmall",
                                            "long"], default="c1",
                     help="small: 512x256 cells for profiler captures; scan: the 48-instance batched "
@@ -1096,9 +1100,12 @@ def main():
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the scan's batch runner")
     ap.add_argument("--scan-launch", choices=["shared", "instances"], default="shared",
                     help="scan: shared launches over all instances (default) or one step graph per instance")
+    ap.add_argument("--scan-groups", type=int, default=4,
+                    help="scan: instance groups of the shared launches (each group on its own stream)")
     ap.add_argument("--scan-reference", action="store_true",
                     help="scan: also time single 1024x512, 768x384 and 128x64 instances with its parameters")
     args = ap.parse_args()
+    args.gamma_pred = 1 if args.gamma_bar == "pred" else 0
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

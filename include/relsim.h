@@ -563,11 +563,14 @@ RELSIM_API int relsim_batch_run(relsim_batch* b, int nsteps, int component, int 
                                 int* status, int* iters);
 
 /* Shared launches over the batch's instances (off by default). With on = 1,
-   relsim_batch_run steps every instance through ONE graph per step in which
-   one deposit launch, one push launch and one re-sort launch per species
-   cover the particles of all instances (each instance's row units numbered
-   after the previous instance's), while each instance's field solve, field
-   update and sort tables run as parallel branches of the same graph. This is
+   relsim_batch_run splits the instances into `groups` groups of about equal
+   particle count (groups <= 0: one group) and steps each group through ONE
+   graph per step in which one deposit launch, one push launch and one
+   re-sort launch per species cover the particles of all its instances (each
+   instance's row units numbered after the previous instance's), while each
+   instance's field solve, field update and sort tables run as parallel
+   branches of the same graph; the groups run on streams of their own, so one
+   group's solves overlap another's particle kernels. This is
    the batched form of the data-parallel step over independent instances
    (Sec. 3.1's scan of tearing runs: many small grids that one instance
    alone cannot fill the GPU with). It applies when every instance is of the
@@ -579,7 +582,7 @@ RELSIM_API int relsim_batch_run(relsim_batch* b, int nsteps, int component, int 
    grids (<= 0: 2 and 16 blocks per SM). Results equal the per-instance
    steps' up to the order of floating-point sums (the deposit's and the
    ledger's atomics). Errors: INVALID_ARG. */
-RELSIM_API int relsim_batch_set_shared(relsim_batch* b, int on, int deposit_blocks, int push_blocks);
+RELSIM_API int relsim_batch_set_shared(relsim_batch* b, int on, int groups, int deposit_blocks, int push_blocks);
 
 /* How the last relsim_batch_run advanced the instances after their first
    step: 0 host-driven workers, 1 per-instance step graphs, 2 shared launches

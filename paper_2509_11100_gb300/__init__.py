@@ -132,7 +132,7 @@ _SIGS = {
                                              ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "relsim_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "relsim_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
-    "relsim_batch_set_shared": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "relsim_batch_set_shared": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "relsim_batch_last_path": (ctypes.c_int, [_P]),
     "relsim_batch_destroy": (None, [_P]),
     "relsim_graph_info": (ctypes.c_int, [_CTX, _P, _P, _P]),
@@ -617,10 +617,10 @@ def relsim_batch_run(b, count, nsteps, component=1, nmodes=0):
     return modes, status, iters, code
 
 
-def relsim_batch_set_shared(b, on=True, deposit_blocks=0, push_blocks=0):
-    """Shared launches over the batch's instances (one deposit, push and
-    re-sort launch per species for all of them) on or off."""
-    code = lib().relsim_batch_set_shared(b, 1 if on else 0, int(deposit_blocks), int(push_blocks))
+def relsim_batch_set_shared(b, on=True, groups=1, deposit_blocks=0, push_blocks=0):
+    """Shared launches over the batch's instances (per group of instances,
+    one deposit, push and re-sort launch per species) on or off."""
+    code = lib().relsim_batch_set_shared(b, 1 if on else 0, int(groups), int(deposit_blocks), int(push_blocks))
     if code != RELSIM_OK:
         raise RelsimError(code, "batch set_shared: bad arguments")
 
@@ -804,14 +804,14 @@ class Batch:
     threads (each Simulation should have a CUDA stream of its own). The
     batch does not own the simulations."""
 
-    def __init__(self, sims, nworkers=8, shared=False, deposit_blocks=0, push_blocks=0):
+    def __init__(self, sims, nworkers=8, shared=False, groups=1, deposit_blocks=0, push_blocks=0):
         self.sims = list(sims)
         self.b = relsim_batch_create([s.ctx for s in self.sims], nworkers)
         if shared:
-            relsim_batch_set_shared(self.b, True, deposit_blocks, push_blocks)
+            relsim_batch_set_shared(self.b, True, groups, deposit_blocks, push_blocks)
 
-    def set_shared(self, on=True, deposit_blocks=0, push_blocks=0):
-        relsim_batch_set_shared(self.b, on, deposit_blocks, push_blocks)
+    def set_shared(self, on=True, groups=1, deposit_blocks=0, push_blocks=0):
+        relsim_batch_set_shared(self.b, on, groups, deposit_blocks, push_blocks)
 
     @property
     def last_path(self):

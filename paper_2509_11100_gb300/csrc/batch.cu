@@ -38,7 +38,9 @@ struct relsim_batch {
     bool shared = false;
     int dep_blocks = 0, push_blocks = 0;
     int last_path = -1;
-    relsim_shared* sb = nullptr;   // the shared graphs, kept while they fit the instances
+    int groups = 1;                          // instance groups of the shared launches
+    std::vector<relsim_shared*> sbs;         // their graphs, kept while they fit the instances
+    std::vector<std::vector<int>> gmem;      // the instances of each group
 };
 
 using namespace relsim;
@@ -210,78 +212,133 @@ void merge_status(int& st, int r)
         st = r;
 }
 
-// steps first .. nsteps-1 of every instance through shared launches; -1 when
-// the instances are not eligible (nothing enqueued)
+// the instances split into g groups of about equal particle count (largest
+// first onto the lightest group); a group keeps the instances' order
+std::vector<std::vector<int>> shared_groups(const relsim_batch* b, int g)
+{
+    const int count = (int)b->ctx.size();
+    if (g > count) g = count;
+    if (g < 1) g = 1;
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return ctx_particles(b->ctx[x]) > ctx_particles(b->ctx[y]); });
+    std::vector<int64_t> load(g, 0);
+    std::vector<int> owner(count, 0);
+    for (int i : order) {
+        int best = 0;
+        for (int q = 1; q < g; ++q)
+            if (load[q] < load[best]) best = q;
+        owner[i] = best;
+        load[best] += ctx_particles(b->ctx[i]);
+    }
+    std::vector<std::vector<int>> groups(g);
+    for (int i = 0; i < count; ++i) groups[owner[i]].push_back(i);
+    return groups;
+}
+
+void shared_drop(relsim_batch* b)
+{
+    for (relsim_shared* sb : b->sbs) shared_destroy(sb);
+    b->sbs.clear();
+    b->gmem.clear();
+}
+
+// steps first .. nsteps-1 of every instance through shared launches, one
+// graph per group of instances and step, each group on its own stream (the
+// groups' deposits, solves and pushes overlap as single instances' do); -1
+// when the instances are not eligible (nothing enqueued)
 int run_shared(relsim_batch* b, int nsteps, int first, int component, int nmodes, double* dmodes, size_t per,
                int* status, int* iters)
 {
     const int count = (int)b->ctx.size();
-    if (b->sb && !shared_valid(b->sb, b->ctx.data(), count, b->dep_blocks, b->push_blocks)) {
-        shared_destroy(b->sb);
-        b->sb = nullptr;
+    std::vector<std::vector<int>> groups = shared_groups(b, b->groups);
+    const int ng = (int)groups.size();
+    bool valid = (int)b->sbs.size() == ng && b->gmem == groups;
+    std::vector<relsim_ctx*> gc;
+    for (int g = 0; g < ng && valid; ++g) {
+        gc.clear();
+        for (int i : groups[g]) gc.push_back(b->ctx[i]);
+        valid = shared_valid(b->sbs[g], gc.data(), (int)gc.size(), b->dep_blocks, b->push_blocks);
     }
-    if (!b->sb) {
-        const int made = shared_create(b->ctx.data(), count, b->dep_blocks, b->push_blocks, &b->sb);
-        if (made == 0) return -1;
-        if (made != 1) return made;
+    if (!valid) {
+        shared_drop(b);
+        for (int g = 0; g < ng; ++g) {
+            gc.clear();
+            for (int i : groups[g]) gc.push_back(b->ctx[i]);
+            relsim_shared* sb = nullptr;
+            const int made = shared_create(gc.data(), (int)gc.size(), b->dep_blocks, b->push_blocks, &sb);
+            if (made != 1) {
+                shared_drop(b);
+                return made == 0 ? -1 : made;
+            }
+            b->sbs.push_back(sb);
+        }
+        b->gmem = groups;
     }
-    relsim_shared* sb = b->sb;
     const size_t hb = ctx_graph_head_bytes();
     const int ns = nsteps - first;
+    // heads: group by group, instance by instance, step by step
+    std::vector<size_t> off(ng + 1, 0);
+    for (int g = 0; g < ng; ++g) off[g + 1] = off[g] + groups[g].size();
     unsigned char* heads = nullptr;
-    std::vector<cudaEvent_t> ev(count + 1, nullptr);
+    std::vector<cudaEvent_t> ev(count + ng, nullptr);
     int rc = RELSIM_OK;
     if (cudaMallocHost((void**)&heads, hb * (size_t)count * (size_t)ns) != cudaSuccess) rc = RELSIM_ERR_OOM;
-    for (int i = 0; i <= count && rc == RELSIM_OK; ++i)
+    for (size_t i = 0; i < ev.size() && rc == RELSIM_OK; ++i)
         if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) rc = RELSIM_ERR_CUDA;
-    cudaStream_t st = shared_stream(sb);
-    // the shared stream follows each instance's earlier work; the mode
-    // energies of step s run on the instance's stream between shared steps
-    auto join_into = [&](cudaStream_t to) -> int {
-        for (int i = 0; i < count; ++i) {
+    // a group's stream follows its instances' earlier work; the mode
+    // energies of step s run on each instance's stream between the group's
+    // steps
+    auto join_group = [&](int g) -> int {
+        cudaStream_t to = shared_stream(b->sbs[g]);
+        for (int i : groups[g])
             if (cudaEventRecord(ev[i], ctx_stream(b->ctx[i])) != cudaSuccess ||
                 cudaStreamWaitEvent(to, ev[i], 0) != cudaSuccess)
                 return RELSIM_ERR_CUDA;
-        }
         return RELSIM_OK;
     };
-    if (rc == RELSIM_OK) rc = join_into(st);
-    for (int s = first; s < nsteps && rc == RELSIM_OK; ++s) {
-        rc = shared_enqueue(sb, heads + hb * (size_t)(s - first), hb * (size_t)ns);
-        if (rc != RELSIM_OK || nmodes == 0) continue;
-        if (cudaEventRecord(ev[count], st) != cudaSuccess) {
-            rc = RELSIM_ERR_CUDA;
-            break;
-        }
-        for (int i = 0; i < count && rc == RELSIM_OK; ++i) {
-            relsim_ctx* c = b->ctx[i];
-            if (cudaStreamWaitEvent(ctx_stream(c), ev[count], 0) != cudaSuccess) {
+    for (int g = 0; g < ng && rc == RELSIM_OK; ++g) rc = join_group(g);
+    for (int s = first; s < nsteps && rc == RELSIM_OK; ++s)
+        for (int g = 0; g < ng && rc == RELSIM_OK; ++g) {
+            relsim_shared* sb = b->sbs[g];
+            rc = shared_enqueue(sb, heads + hb * (size_t)ns * off[g] + hb * (size_t)(s - first), hb * (size_t)ns);
+            if (rc != RELSIM_OK || nmodes == 0) continue;
+            if (cudaEventRecord(ev[count + g], shared_stream(sb)) != cudaSuccess) {
                 rc = RELSIM_ERR_CUDA;
                 break;
             }
-            rc = relsim_field_modes(c, component, nmodes, dmodes + per * (size_t)i + (size_t)(s + 1) * nmodes,
-                                    RELSIM_DEVICE);
+            for (int i : groups[g]) {
+                relsim_ctx* c = b->ctx[i];
+                if (cudaStreamWaitEvent(ctx_stream(c), ev[count + g], 0) != cudaSuccess) {
+                    rc = RELSIM_ERR_CUDA;
+                    break;
+                }
+                rc = relsim_field_modes(c, component, nmodes, dmodes + per * (size_t)i + (size_t)(s + 1) * nmodes,
+                                        RELSIM_DEVICE);
+                if (rc != RELSIM_OK) break;
+            }
+            if (rc == RELSIM_OK) rc = join_group(g);
         }
-        if (rc == RELSIM_OK) rc = join_into(st);
-    }
-    if (cudaStreamSynchronize(st) != cudaSuccess && rc == RELSIM_OK) rc = RELSIM_ERR_CUDA;
+    for (relsim_shared* sb : b->sbs)
+        if (cudaStreamSynchronize(shared_stream(sb)) != cudaSuccess && rc == RELSIM_OK) rc = RELSIM_ERR_CUDA;
     for (int i = 0; i < count; ++i)
         if (cudaStreamSynchronize(ctx_stream(b->ctx[i])) != cudaSuccess && rc == RELSIM_OK) rc = RELSIM_ERR_CUDA;
     if (rc == RELSIM_OK)
         for (int s = first; s < nsteps; ++s)
-            for (int i = 0; i < count; ++i) {
-                int it = 0;
-                const int r = shared_outcome(sb, i, heads + hb * ((size_t)i * ns + (s - first)), &it, i == 0);
-                if (iters) iters[(size_t)i * nsteps + s] = it;
-                merge_status(status[i], r);
-            }
+            for (int g = 0; g < ng; ++g)
+                for (size_t il = 0; il < groups[g].size(); ++il) {
+                    const int i = groups[g][il];
+                    int it = 0;
+                    const unsigned char* h = heads + hb * (size_t)ns * (off[g] + il) + hb * (size_t)(s - first);
+                    const int r = shared_outcome(b->sbs[g], (int)il, h, &it, il == 0);
+                    if (iters) iters[(size_t)i * nsteps + s] = it;
+                    merge_status(status[i], r);
+                }
     for (cudaEvent_t e : ev)
         if (e) cudaEventDestroy(e);
     if (heads) cudaFreeHost(heads);
-    if (rc != RELSIM_OK) {
-        shared_destroy(sb);
-        b->sb = nullptr;
-    }
+    if (rc != RELSIM_OK) shared_drop(b);
     return rc;
 }
 
@@ -289,17 +346,17 @@ int run_shared(relsim_batch* b, int nsteps, int first, int component, int nmodes
 
 extern "C" {
 
-int relsim_batch_set_shared(relsim_batch* b, int on, int deposit_blocks, int push_blocks)
+int relsim_batch_set_shared(relsim_batch* b, int on, int groups, int deposit_blocks, int push_blocks)
 {
-    if (!b || (on != 0 && on != 1) || deposit_blocks > (1 << 20) || push_blocks > (1 << 20))
+    if (!b || (on != 0 && on != 1) || groups > 4096 || deposit_blocks > (1 << 20) || push_blocks > (1 << 20))
         return RELSIM_ERR_INVALID_ARG;
     b->shared = on != 0;
+    b->groups = groups > 0 ? groups : 1;
     b->dep_blocks = deposit_blocks > 0 ? deposit_blocks : 0;
     b->push_blocks = push_blocks > 0 ? push_blocks : 0;
-    if (!b->shared && b->sb) {
+    if (!b->sbs.empty()) {
         cudaSetDevice(b->device);
-        shared_destroy(b->sb);
-        b->sb = nullptr;
+        shared_drop(b);
     }
     return RELSIM_OK;
 }
@@ -493,9 +550,9 @@ int relsim_batch_run(relsim_batch* b, int nsteps, int component, int nmodes, dou
 void relsim_batch_destroy(relsim_batch* b)
 {
     if (!b) return;
-    if (b->sb) {
+    if (!b->sbs.empty()) {
         cudaSetDevice(b->device);
-        shared_destroy(b->sb);
+        shared_drop(b);
     }
     delete b;
 }

@@ -229,11 +229,15 @@ __device__ __forceinline__ T gbar_u2(T ux, T uy, T uz, T beta, const T (*sEn)[2]
         sz = uz;
         return ux * ux + uy * uy + uz * uz;
     }
-    T Ex, Ey, Ez;
-    tile_E(sEn, l, W0, W1, W2, W3, Ex, Ey, Ez);
-    sx = ux + beta * Ex;
-    sy = uy + beta * Ey;
-    sz = uz + beta * Ez;
+    // one component at a time (compiler barriers between them): the twelve
+    // tile loads in flight together would push the deposit past its 128
+    // registers
+    sx = ux + beta * (W0 * sEn[0][0][l] + W1 * sEn[0][0][l + 1] + W2 * sEn[0][1][l] + W3 * sEn[0][1][l + 1]);
+    asm volatile("" ::: "memory");
+    sy = uy + beta * (W0 * sEn[1][0][l] + W1 * sEn[1][0][l + 1] + W2 * sEn[1][1][l] + W3 * sEn[1][1][l + 1]);
+    asm volatile("" ::: "memory");
+    sz = uz + beta * (W0 * sEn[2][0][l] + W1 * sEn[2][0][l + 1] + W2 * sEn[2][1][l] + W3 * sEn[2][1][l + 1]);
+    asm volatile("" ::: "memory");
     return sx * sx + sy * sy + sz * sz;
 }
 
@@ -325,29 +329,43 @@ struct Moments {
 
 template <>
 struct Moments<float> {
-    float2 S2[45];   // S2[k*5 + h] = (S[k][2h], S[k][2h+1]); S[k][9] is padding
+    // the 81 moments S[k][q] in 81 registers: P[k*4 + h] = (S[k][2h],
+    // S[k][2h+1]) for q < 8, Q[m] = (S[2m][8], S[2m+1][8]), R = S[8][8]; all
+    // but R accumulate with paired FMAs (FFMA2)
+    float2 P[36];
+    float2 Q[4];
+    float R;
     float Jm[12];
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
-        for (int q = 0; q < 45; ++q) S2[q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < 36; ++q) P[q] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Q[m] = make_float2(0.f, 0.f);
+        R = 0.f;
 #pragma unroll
         for (int q = 0; q < 12; ++q) Jm[q] = 0.f;
     }
     __device__ __forceinline__ void add(const float (&t)[9], const float (&e)[9])
     {
-        const float2 e2[5] = {make_float2(e[0], e[1]), make_float2(e[2], e[3]), make_float2(e[4], e[5]),
-                              make_float2(e[6], e[7]), make_float2(e[8], 0.f)};
+        const float2 e2[4] = {make_float2(e[0], e[1]), make_float2(e[2], e[3]), make_float2(e[4], e[5]),
+                              make_float2(e[6], e[7])};
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const float2 tk = make_float2(t[k], t[k]);
 #pragma unroll
-            for (int h = 0; h < 5; ++h) S2[k * 5 + h] = __ffma2_rn(tk, e2[h], S2[k * 5 + h]);
+            for (int h = 0; h < 4; ++h) P[k * 4 + h] = __ffma2_rn(tk, e2[h], P[k * 4 + h]);
         }
+        const float2 e8 = make_float2(e[8], e[8]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Q[m] = __ffma2_rn(make_float2(t[2 * m], t[2 * m + 1]), e8, Q[m]);
+        R = fmaf(t[8], e[8], R);
     }
     __device__ __forceinline__ float get(int k, int q) const
     {
-        return (q & 1) ? S2[k * 5 + q / 2].y : S2[k * 5 + q / 2].x;
+        if (q < 8) return (q & 1) ? P[k * 4 + q / 2].y : P[k * 4 + q / 2].x;
+        if (k < 8) return (k & 1) ? Q[k / 2].y : Q[k / 2].x;
+        return R;
     }
     template <int G>
     __device__ __forceinline__ void group_reduce()
@@ -355,10 +373,16 @@ struct Moments<float> {
 #pragma unroll
         for (int o = G / 2; o >= 1; o >>= 1) {
 #pragma unroll
-            for (int q = 0; q < 45; ++q) {
-                S2[q].x += __shfl_xor_sync(0xffffffffu, S2[q].x, o);
-                if (q % 5 != 4) S2[q].y += __shfl_xor_sync(0xffffffffu, S2[q].y, o);
+            for (int q = 0; q < 36; ++q) {
+                P[q].x += __shfl_xor_sync(0xffffffffu, P[q].x, o);
+                P[q].y += __shfl_xor_sync(0xffffffffu, P[q].y, o);
             }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                Q[m].x += __shfl_xor_sync(0xffffffffu, Q[m].x, o);
+                Q[m].y += __shfl_xor_sync(0xffffffffu, Q[m].y, o);
+            }
+            R += __shfl_xor_sync(0xffffffffu, R, o);
 #pragma unroll
             for (int q = 0; q < 12; ++q) Jm[q] += __shfl_xor_sync(0xffffffffu, Jm[q], o);
         }
@@ -647,6 +671,9 @@ template <typename T> struct PushCfg {
     static constexpr int threads = 32 * warps;
     static constexpr int min_blocks = sizeof(T) == 4 ? 5 : 2;
     static constexpr int cap = sizeof(T) == 4 ? 256 : 128;   // particles of a cell group staged per warp
+    // with the E^n tile of the predicted gamma (3 KB more per block in
+    // FP32) a smaller group keeps five blocks on an SM
+    static constexpr int cap_pred = sizeof(T) == 4 ? 224 : 128;
 };
 constexpr int kGroupMax = 8;    // cells staged together at most
 constexpr int kLedger = 4;      // dK, work, mismatch, K1 (K0 is the previous K1)
@@ -748,16 +775,17 @@ struct PushTile {
 // a cell's pushed particles, staged for the write back in direction order
 // a group of cells' pushed particles, staged for the write back in cell and
 // direction order
-template <typename T>
+template <typename T, int C>
 struct PushStage {
-    static constexpr int C = PushCfg<T>::cap;
     T fx[C], fy[C], ux[C], uy[C], uz[C], w[C];
     int32_t id[C];
     uint8_t dir[C], rank[C], inv[C], cell[C];
     int doff[kGroupMax * (kNDir + 1)];
     int run[kGroupMax * kNDir];
 };
-static_assert(PushCfg<float>::cap <= 256 && PushCfg<double>::cap <= 256, "uint8 staging indices");
+static_assert(PushCfg<float>::cap <= 256 && PushCfg<double>::cap <= 256 && PushCfg<float>::cap_pred <= 256 &&
+                  PushCfg<double>::cap_pred <= 256,
+              "uint8 staging indices");
 
 template <typename T>
 __device__ __forceinline__ void block_ledger(const T (&acc)[kLedger], double* red, double* __restrict__ lsum)
@@ -836,7 +864,8 @@ __device__ __forceinline__ void push_sort_core(PArrays<T> src, PArrays<T> dst, c
     __shared__ int sstart[W][kUnitW + 1];
     __shared__ PushTile<T> stile[W];
     __shared__ PredTile<T, PRED> sen[W];
-    __shared__ PushStage<T> sstage[W];
+    constexpr int CAP = PRED ? PushCfg<T>::cap_pred : PushCfg<T>::cap;
+    __shared__ PushStage<T, CAP> sstage[W];
     __shared__ double red[32 * kLedger];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -846,7 +875,7 @@ __device__ __forceinline__ void push_sort_core(PArrays<T> src, PArrays<T> dst, c
     const unsigned lt = (1u << lane) - 1u;
     int* ss = sstart[wib];
     PushTile<T>& tl = stile[wib];
-    PushStage<T>& st = sstage[wib];
+    PushStage<T, CAP>& st = sstage[wib];
     bool ids = dst.id != nullptr;
     T acc[kLedger] = {T(0), T(0), T(0), T(0)};
 
@@ -886,7 +915,7 @@ __device__ __forceinline__ void push_sort_core(PArrays<T> src, PArrays<T> dst, c
         T pfx = T(0), pfy = T(0), pux = T(0), puy = T(0), puz = T(0), pw = T(0);
         for (int l = 0; l < un.cn;) {
             const int s0 = ss[l];
-            if (ss[l + 1] - s0 > PushCfg<T>::cap) {
+            if (ss[l + 1] - s0 > CAP) {
                 // a big cell alone: a counting pass (no ledger, nothing
                 // written), then every particle written to its slot directly
                 const int s1 = ss[l + 1];
@@ -955,7 +984,7 @@ __device__ __forceinline__ void push_sort_core(PArrays<T> src, PArrays<T> dst, c
             int gsz = 1, tot = ss[l + 1] - s0;
             while (gsz < kGroupMax && l + gsz < un.cn) {
                 const int nn = ss[l + gsz + 1] - ss[l + gsz];
-                if (tot + nn > PushCfg<T>::cap) break;
+                if (tot + nn > CAP) break;
                 tot += nn;
                 ++gsz;
             }

@@ -158,10 +158,11 @@ def test_batch_equals_instances_stepped_one_by_one(rs):
         sim.close()
 
 
-@pytest.mark.parametrize("precision,pred", [(32, 0), (32, 1), (64, 0)])
-def test_shared_launches_equal_per_instance_graphs(rs, precision, pred):
-    """Shared launches (one deposit, push and re-sort launch per species over
-    every instance; each instance's solve a branch of the same graph) give
+@pytest.mark.parametrize("precision,pred,groups", [(32, 0, 1), (32, 1, 2), (64, 0, 3)])
+def test_shared_launches_equal_per_instance_graphs(rs, precision, pred, groups):
+    """Shared launches (per group of instances one deposit, push and re-sort
+    launch per species; each instance's solve a branch of the group's graph;
+    1, 2 or 3 groups on streams of their own) give
     the per-instance graphs' results on the same uneven instances: fields,
     mode energies, every particle by id, the energy ledger and the GMRES
     iteration counts, up to the order of the deposit's and the ledger's
@@ -179,7 +180,7 @@ def test_shared_launches_equal_per_instance_graphs(rs, precision, pred):
                                                gamma_pred=pred, track_ids=True), stream=stream.cuda_stream)
             sim.load_state(make_harris(hc))
             sims.append(sim)
-        batch = rs.Batch(sims, nworkers=3, shared=shared)
+        batch = rs.Batch(sims, nworkers=3, shared=shared, groups=groups)
         modes, status, iters = batch.run(steps, component=1, nmodes=nm)
         assert list(status) == [0] * len(SIZES)
         assert batch.last_path == ("shared" if shared else "graphs")
