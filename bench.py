@@ -41,7 +41,7 @@ WORKLOAD = {
                 "64 ppc per species (67,108,864 particles), sigma=10, theta_T=0.3, delta=1 d_e, "
                 "dt=1/omega_pe, theta=0.5, 1% B_y perturbation, seed 0",
     "nx": 1024, "ny": 512, "ppc_per_species": 64, "particles": 67108864,
-    "form": "FP32 particles/fields/mass matrix, FP64 GMRES basis and ledger",
+    "form": "FP32 particles/fields/mass matrix, GMRES vectors as double-float pairs (FP32 arithmetic, ~48-bit values), FP64 ledger",
     "gmres_tol": 1e-6, "gmres_restart": 30,
     "l2": "inputs larger than L2 (1.6 GB of particle data per step), no flush",
 }
@@ -573,7 +573,7 @@ SCAN = {
                 "L_x from {128,192,256,384,512,768} cells (L_y = L_x/2), delta from {0.5,1,2} d_e, "
                 "sigma from {1,10,40} (SplitMix64 draws from seed 0), theta_T=0.3, 32 ppc per species, "
                 "0.1% B_y perturbation, dt=0.5/omega_pe, theta=0.5",
-    "form": "FP32 particles/fields/mass matrix, FP64 GMRES basis and ledger",
+    "form": "FP32 particles/fields/mass matrix, GMRES vectors as double-float pairs (FP32 arithmetic, ~48-bit values), FP64 ledger",
     "gmres_tol": 1e-6, "gmres_restart": 30,
     "l2": "inputs larger than L2 (about 8 GB of particle data per step), no flush",
 }
@@ -792,6 +792,8 @@ def run_quad(args):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"2D relativistic double Harris sheet as the headline line ({hc.nx}x{hc.ny}, 64 "
                                   f"ppc per species, {N:,} particles) with quadratic (TSC) shape functions",
+                      "form": "FP32 particles/fields/mass matrix, FP64 GMRES basis and ledger",
+                      "gamma_bar": "gamma(u^n) (the quadratic shapes cover the base scheme)",
                       "l2": "inputs larger than L2, no flush"},
            "per_kernel": per_kernel, "gmres_iters_per_step": float(np.mean([l["gmres_iters"] for l in leds])),
            "ledger": {"residual_rel": abs(last["residual"]) / last["total"],
@@ -950,6 +952,7 @@ def run_3d(args):
                                   "delta=1 d_e, dt=0.5/omega_pe, theta=0.5, 1% B_y perturbation in x-z modes 1-4, "
                                   "trilinear shapes (27-node stencil), seed 0",
                       "form": "FP32 particles/fields/mass matrix, FP64 GMRES basis and ledger",
+                      "gamma_bar": "gamma(u^n) (the 3D form covers the base scheme)",
                       "l2": "inputs larger than L2 (3.8 GB of particle data per step), no flush"},
            "per_kernel": per_kernel, "per_kernel_pass": f"{kp} further steps with event profiling",
            "gpu_launches": launches, "gmres_iters_per_step": float(np.mean([l["gmres_iters"] for l in leds])),

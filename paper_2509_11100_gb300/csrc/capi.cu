@@ -633,8 +633,8 @@ int build_impl(relsim_ctx* c)
 {
     const int nc = c->g.ncell;
     PROF_BEGIN(RELSIM_PROF_DEPOSIT);
-    CK(cudaMemsetAsync(c->M, 0, c->esz * (size_t)nc * mblock_of(c->g), c->st));
-    CK(cudaMemsetAsync(c->J, 0, c->esz * 3 * (size_t)nc, c->st));
+    CK(zero_fill(c->M, c->esz * (size_t)nc * mblock_of(c->g), c->st));
+    CK(zero_fill(c->J, c->esz * 3 * (size_t)nc, c->st));
     const DepositSpecies<T> ds = deposit_args<T>(c);
     if (c->g.shape == 2) {
         CK(deposit_q<T>(ds, (const T*)c->B[c->bcur], (T*)c->M, (T*)c->J, c->g, c->st, c->dep_blocks));
@@ -1665,8 +1665,8 @@ int shared_capture(relsim_shared* sb, int k)
     }
     auto run = [&]() -> int {
         for (relsim_ctx* c : sb->c) {
-            CK(cudaMemsetAsync(c->M, 0, c->esz * (size_t)c->g.ncell * mblock_of(c->g), sb->st));
-            CK(cudaMemsetAsync(c->J, 0, c->esz * 3 * (size_t)c->g.ncell, sb->st));
+            CK(zero_fill(c->M, c->esz * (size_t)c->g.ncell * mblock_of(c->g), sb->st));
+            CK(zero_fill(c->J, c->esz * 3 * (size_t)c->g.ncell, sb->st));
         }
         CK_CTX(c0, deposit_batch<T>(ddep, n, sb->total_units, sb->pred, c0->dpush, sb->st, sb->dep_blocks));
         CK_CTX(c0, cudaEventRecord(sb->fork, sb->st));

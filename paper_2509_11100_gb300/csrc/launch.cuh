@@ -110,6 +110,8 @@ cudaError_t histogram_keys(const int32_t* keys, int64_t n, int32_t* counts, int 
                            cudaStream_t st);
 // new-cell counts of the neighbour-move sort
 cudaError_t move_counts(const int32_t* n9, int32_t* count_new, GridP g, cudaStream_t st);
+// zero `bytes` (a multiple of 4) from p (16-byte aligned) with a kernel
+cudaError_t zero_fill(void* p, size_t bytes, cudaStream_t st);
 cudaError_t iota_i32(int32_t* a, int64_t n, cudaStream_t st);
 
 // ----- d3.cu (the 3D form) -----

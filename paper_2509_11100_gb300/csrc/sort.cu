@@ -216,7 +216,30 @@ __global__ void k_move_counts(const int32_t* __restrict__ n9, int32_t* count_new
     count_new[k] = c;
 }
 
+// zero n4 16-byte words, then ntail 4-byte words after them
+__global__ void k_zero(uint4* __restrict__ p4, int64_t n4, uint32_t* __restrict__ tail, int ntail)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride)
+        p4[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x == 0 && (int)threadIdx.x < ntail) tail[threadIdx.x] = 0u;
+}
+
 }  // namespace
+
+cudaError_t zero_fill(void* p, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) return cudaSuccess;
+    if (((uintptr_t)p & 15) != 0 || (bytes & 3) != 0) return cudaErrorInvalidValue;
+    const int64_t n4 = (int64_t)(bytes / 16);
+    const int ntail = (int)((bytes % 16) / 4);
+    int64_t blocks = (n4 + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    count_launches(1);
+    k_zero<<<(unsigned)blocks, 256, 0, st>>>((uint4*)p, n4, (uint32_t*)((char*)p + n4 * 16), ntail);
+    return cudaGetLastError();
+}
 
 size_t scan_tmp_ints(int64_t n)
 {
