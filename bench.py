@@ -1101,8 +1101,9 @@ def main():
                          "(c2small: 64x32x32); c1q: the headline sheet with quadratic shapes; long: the "
                          "headline sheet for --long-steps steps (energy drift, tearing mode, spectrum)")
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the scan's batch runner")
-    ap.add_argument("--scan-launch", choices=["shared", "instances"], default="shared",
-                    help="scan: shared launches over all instances (default) or one step graph per instance")
+    ap.add_argument("--scan-launch", choices=["shared", "instances"], default="instances",
+                    help="scan: one step graph per instance on its own stream (default, the faster as measured) "
+                         "or shared launches over groups of instances")
     ap.add_argument("--scan-groups", type=int, default=4,
                     help="scan: instance groups of the shared launches (each group on its own stream)")
     ap.add_argument("--scan-reference", action="store_true",
