@@ -360,8 +360,8 @@ RELSIM_API int relsim_push_adjoint(relsim_ctx* ctx, int species, const double* g
                                    double* gu0, double* gx0, double* gE, double* gB, int where);
 
 /* One whole step's adjoint on device memory, in place (no counterpart in
-   the paper, which computes no gradients; base scheme, gbar =
-   gamma(u^n)): the chain rule through the step of Sec. 2 (deposit of the
+   the paper, which computes no gradients; either reading of gbar): the
+   chain rule through the step of Sec. 2 (deposit of the
    mass matrices and the predicted current, implicit field solve, push).
    From the state the context holds (loaded or pushed, not yet built) it
    builds the mass matrix and solves the step forward, then runs the pushes'
@@ -386,9 +386,12 @@ RELSIM_API int relsim_push_adjoint(relsim_ctx* ctx, int species, const double* g
    push's re-sort leaves, so a window of steps chains calls without
    reordering anything. The context is left solved (relsim_push advances
    it). *iters, *rel_residual (may be NULL): the adjoint solve. Device
-   scratch of 10 max_s(n_s) + 6*3*ncell + 45*ncell doubles is kept by the
-   context. Synchronises the stream. Errors: INVALID_ARG (a null array,
-   track_ids off, a gamma_pred context), BAD_STATE (not a loaded or pushed
+   scratch of 10 max_s(n_s) + 7*3*ncell + 45*ncell doubles is kept by the
+   context. In a gamma_pred context the chain also runs through the
+   predicted Lorentz factor gamma(u^n + beta E^n(x)) of the deposit and the
+   push: its dL/dE^n joins the field adjoint's in gE, its dL/du^n and
+   dL/dx^{n+1/2} the particles'. Synchronises the stream. Errors:
+   INVALID_ARG (a null array, track_ids off), BAD_STATE (not a loaded or pushed
    state), NOT_CONVERGED (the forward or the adjoint solve; outputs still
    written), NONFINITE, OOM, CUDA. */
 RELSIM_API int relsim_step_adjoint(relsim_ctx* ctx, double* gE, double* gB, double* const* gu, double* const* gx,

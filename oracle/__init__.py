@@ -471,20 +471,45 @@ def _cic(c, x, y, shift):
     return g, W, Wx, Wy
 
 
-def push_adjoint(c, P: Particles, Etheta, B, gu1, gx1, gy1):
+def _gbar_back(c, ggb, u, s, gb, beta, gN, WN, WNx, WNy, En, gEn, gx0, gy0, a0, a1):
+    """dL/dgbar carried back through gbar: to u (base scheme, gbar =
+    gamma(u)), or, with the predicted gbar = gamma(s), s = u + beta E^n(x), to
+    u, to E^n on the nodes (the gather's transpose) and to x through the
+    gather's weights. Returns dL/du's share."""
+    gs = ggb * s / gb
+    if not c.gamma_pred:
+        return gs
+    gEp = beta * gs
+    for k in range(4):
+        for comp in range(3):
+            np.add.at(gEn[comp], gN[k], WN[k] * gEp[comp])
+        eg = (En[:, gN[k]] * gEp).sum(axis=0)
+        gx0[a0:a1] += WNx[k] * eg
+        gy0[a0:a1] += WNy[k] * eg
+    return gs
+
+
+def push_adjoint(c, P: Particles, Etheta, B, gu1, gx1, gy1, En=None):
     """Adjoint of the push (Sec. 2: the pusher is explicit) with the fields
-    held fixed, base scheme (gbar = gamma(u^n)). Forward, per particle:
+    held fixed. Forward, per particle:
       Ep = sum_g W_g(x) E_g (nodes),  Bp = sum_c W_c(x) B_c (centres),
-      gbar = sqrt(1 + |u|^2),  a = beta Bp/gbar,  alpha = (I + [a]x)^{-1},
+      gbar = sqrt(1 + |s|^2) with s = u (base scheme) or, with gamma_pred,
+      s = u + beta E^n(x) (E^n = En on the nodes),
+      a = beta Bp/gbar,  alpha = (I + [a]x)^{-1},
       ubar = alpha (u + beta Ep),  u1 = 2 ubar - u,  x1 = x + dt u1/gamma(u1).
     Given dL/du1 (gu1, (3, N)) and dL/dx1, dL/dy1 (N each), returns dL/du,
     dL/dx, dL/dy per particle and dL/dE (nodes), dL/dB (centres), (3, nn),
-    by the chain rule in reverse: the transposes of the gathers are the
-    scatters with the same weights, alpha's transpose is applied to the
-    gradient of ubar, and d alpha = -alpha d[a]x alpha.
+    and with gamma_pred dL/dEn (nodes), by the chain rule in reverse: the
+    transposes of the gathers are the scatters with the same weights,
+    alpha's transpose is applied to the gradient of ubar, and d alpha =
+    -alpha d[a]x alpha.
     """
     nn = c.nx * c.ny
     E = np.asarray(Etheta, dtype=np.float64).reshape(3, nn)
+    if c.gamma_pred and En is None:
+        raise ValueError("the predicted-gamma push adjoint needs E^n")
+    En = np.zeros((3, nn)) if En is None else np.asarray(En, dtype=np.float64).reshape(3, nn)
+    gEn = np.zeros((3, nn))
     Bf = np.asarray(B, dtype=np.float64).reshape(3, nn)
     gu1 = np.asarray(gu1, dtype=np.float64).reshape(3, -1)
     gx1 = np.asarray(gx1, dtype=np.float64).ravel()
@@ -506,7 +531,8 @@ def push_adjoint(c, P: Particles, Etheta, B, gu1, gx1, gy1):
         gC, WC, WCx, WCy = _cic(c, x, y, 0.5)
         Ep = sum(WN[k] * E[:, gN[k]] for k in range(4))
         Bp = sum(WC[k] * Bf[:, gC[k]] for k in range(4))
-        gb = np.sqrt(1.0 + (u * u).sum(axis=0))
+        sv = u + beta * sum(WN[k] * En[:, gN[k]] for k in range(4)) if c.gamma_pred else u
+        gb = np.sqrt(1.0 + (sv * sv).sum(axis=0))
         a = beta * Bp / gb
         n = a1 - a0
         ax = np.zeros((n, 3, 3))   # [a]x v = a x v
@@ -531,7 +557,7 @@ def push_adjoint(c, P: Particles, Etheta, B, gu1, gx1, gy1):
         ga = np.stack([G[:, 2, 1] - G[:, 1, 2], G[:, 0, 2] - G[:, 2, 0], G[:, 1, 0] - G[:, 0, 1]])
         gBp = beta * ga / gb
         ggb = -beta * (ga * Bp).sum(axis=0) / gb ** 2
-        gu += ggb * u / gb
+        gu += _gbar_back(c, ggb, u, sv, gb, beta, gN, WN, WNx, WNy, En, gEn, gx0, gy0, a0, a1)
         for k in range(4):
             for comp in range(3):
                 np.add.at(gE[comp], gN[k], WN[k] * gEp[comp])
@@ -541,23 +567,32 @@ def push_adjoint(c, P: Particles, Etheta, B, gu1, gx1, gy1):
             gx0[a0:a1] += WNx[k] * eg + WCx[k] * bg
             gy0[a0:a1] += WNy[k] * eg + WCy[k] * bg
         gu0[:, a0:a1] = gu
-    return {"u": gu0, "x": gx0, "y": gy0, "E": gE, "B": gB}
+    out = {"u": gu0, "x": gx0, "y": gy0, "E": gE, "B": gB}
+    if c.gamma_pred:
+        out["En"] = gEn
+    return out
 
 
-def deposit_adjoint(c, P: Particles, B, gJ, gM):
-    """Adjoint of the deposit (base scheme, gbar = gamma(u^n)). Forward, per
-    particle: Bp = sum_c W_c(x) B_c, a = beta Bp/gbar, alpha = (I + [a]x)^-1,
+def deposit_adjoint(c, P: Particles, B, gJ, gM, En=None):
+    """Adjoint of the deposit. Forward, per particle: Bp = sum_c W_c(x) B_c,
+    gbar = gamma(u^n) (base scheme) or, with gamma_pred, gamma(u^n + beta
+    E^n(x)) (E^n = En on the nodes), a = beta Bp/gbar, alpha = (I + [a]x)^-1,
       Jhat_g += (w q/dV) W_g(x) alpha u/gbar,
       M_{g g'} += (w q beta/dV) W_g(x) W_g'(x) alpha/gbar  (ordered pairs, full layout).
     Given dL/dJhat (gJ, (3, nn)) and dL/dM (gM, (nn, 9, 3, 3) full layout),
     returns dL/du (3, N), dL/dx, dL/dy (N), dL/dw (N) and dL/dB (3, nn): the
     gradient of alpha collects the current and every node pair's block
     gradient, then flows through a (d alpha = -alpha d[a]x alpha) to Bp and
-    gbar; J and M are linear in w, so dL/dw is the particle's contribution to
+    gbar (and, with gamma_pred, through gbar to E^n: dL/dEn in the result);
+    J and M are linear in w, so dL/dw is the particle's contribution to
     <gJ, Jhat> + <gM, M> per unit weight."""
     nn = c.nx * c.ny
     dV = c.dx * c.dy
     Bf = np.asarray(B, dtype=np.float64).reshape(3, nn)
+    if c.gamma_pred and En is None:
+        raise ValueError("the predicted-gamma deposit adjoint needs E^n")
+    En = np.zeros((3, nn)) if En is None else np.asarray(En, dtype=np.float64).reshape(3, nn)
+    gEn = np.zeros((3, nn))
     gJ = np.asarray(gJ, dtype=np.float64).reshape(3, nn)
     gM = np.asarray(gM, dtype=np.float64).reshape(nn, 9, 3, 3)
     N = P.x.size
@@ -579,7 +614,8 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
         gN, WN, WNx, WNy = _cic(c, x, y, 0.0)
         gC, WC, WCx, WCy = _cic(c, x, y, 0.5)
         Bp = sum(WC[k] * Bf[:, gC[k]] for k in range(4))
-        gb = np.sqrt(1.0 + (u * u).sum(axis=0))
+        sv = u + beta * sum(WN[k] * En[:, gN[k]] for k in range(4)) if c.gamma_pred else u
+        gb = np.sqrt(1.0 + (sv * sv).sum(axis=0))
         a = beta * Bp / gb
         ax = np.zeros((n, 3, 3))
         ax[:, 0, 1], ax[:, 0, 2] = -a[2], a[1]
@@ -620,7 +656,7 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
         ga = np.stack([Gm[:, 2, 1] - Gm[:, 1, 2], Gm[:, 0, 2] - Gm[:, 2, 0], Gm[:, 1, 0] - Gm[:, 0, 1]])
         gBp = beta * ga / gb
         ggb -= beta * (ga * Bp).sum(axis=0) / gb ** 2
-        gu += ggb * u / gb
+        gu += _gbar_back(c, ggb, u, sv, gb, beta, gN, WN, WNx, WNy, En, gEn, gx0, gy0, a0, a1)
         for k in range(4):
             for comp in range(3):
                 np.add.at(gB[comp], gC[k], WC[k] * gBp[comp])
@@ -628,7 +664,10 @@ def deposit_adjoint(c, P: Particles, B, gJ, gM):
             gx0[a0:a1] += WNx[k] * gWn[k] + WCx[k] * bg
             gy0[a0:a1] += WNy[k] * gWn[k] + WCy[k] * bg
         gu0[:, a0:a1] = gu
-    return {"u": gu0, "x": gx0, "y": gy0, "w": gw0, "B": gB}
+    out = {"u": gu0, "x": gx0, "y": gy0, "w": gw0, "B": gB}
+    if c.gamma_pred:
+        out["En"] = gEn
+    return out
 
 
 def step_adjoint(c, P: Particles, E, B, gu1, gx1, gy1, gE1, gB1):
@@ -639,14 +678,16 @@ def step_adjoint(c, P: Particles, E, B, gu1, gx1, gy1, gE1, gB1):
     field part of dL/dB^n; the deposit's adjoint carries dL/dJhat and dL/dM
     back to the particles and B^n. P is the state before the step."""
     nn = c.nx * c.ny
-    J, M = deposit(c, P, B)
+    En = E if c.gamma_pred else None
+    J, M = deposit(c, P, B, En)
     b = rhs(c, E, B, J)
     Et, _, _, _ = gmres(c, M, b, np.zeros_like(b))
-    gp = push_adjoint(c, P, Et, B, gu1, gx1, gy1)
+    gp = push_adjoint(c, P, Et, B, gu1, gx1, gy1, En)
     gf = field_adjoint(c, M, Et, gE1, gB1, gEt=gp["E"])
-    gd = deposit_adjoint(c, P, B, gf["J"], gf["M"])
+    gd = deposit_adjoint(c, P, B, gf["J"], gf["M"], En)
+    gE0 = gf["E0"] + (gp["En"] + gd["En"] if c.gamma_pred else 0.0)
     return {"u": gp["u"] + gd["u"], "x": gp["x"] + gd["x"], "y": gp["y"] + gd["y"], "w": gd["w"],
-            "E": gf["E0"], "B": gf["B0"] + gp["B"] + gd["B"], "push": gp, "field": gf, "deposit": gd}
+            "E": gE0, "B": gf["B0"] + gp["B"] + gd["B"], "push": gp, "field": gf, "deposit": gd}
 
 
 def mode_energy(c, B, mode=1, component=1):

@@ -1455,7 +1455,7 @@ int step_adjoint_impl(relsim_ctx* c, double* gE, double* gB, double* const* gu, 
     const int64_t nf = 3 * (int64_t)c->g.ncell, nm = (int64_t)c->g.ncell * kMBlock;
     int64_t nmax = 0;
     for (int s = 0; s < c->cfg.nspecies; ++s) nmax = c->sp[s].n > nmax ? c->sp[s].n : nmax;
-    TRY(ensure_adj(c, 10 * nmax + 6 * nf + nm));
+    TRY(ensure_adj(c, 10 * nmax + 7 * nf + nm));
     double* L = c->adj;           // 5 nmax: a species' gradients in its current order
     double* P = L + 5 * nmax;     // 5 nmax: its push adjoint's dL/du^n, dL/dx^{n+1/2}
     double* sE = P + 5 * nmax;    // dL/dE^{n+theta} of the pushes
@@ -1464,8 +1464,12 @@ int step_adjoint_impl(relsim_ctx* c, double* gE, double* gB, double* const* gu, 
     double* fB = fE + nf;
     double* fJ = fB + nf;
     double* fM = fJ + nf;
+    double* sEn = fM + nm;        // predicted gbar: dL/dE^n of the pushes and the deposits
     const T* Bn = (const T*)c->B[c->bcur];
+    // E^n of the predicted gbar (the solve kept it before E^{n+1} replaced it)
+    const T* En = c->En ? (const T*)c->En : nullptr;
     CK(cudaMemsetAsync(sE, 0, sizeof(double) * (size_t)(2 * nf), c->st));
+    if (En) CK(cudaMemsetAsync(sEn, 0, sizeof(double) * (size_t)nf, c->st));
     for (int s = 0; s < c->cfg.nspecies; ++s) {
         Species& sp = c->sp[s];
         const int64_t n = sp.n;
@@ -1473,7 +1477,7 @@ int step_adjoint_impl(relsim_ctx* c, double* gE, double* gB, double* const* gu, 
         const PArrays<T> a = arrays<T>(sp, sp.cur);
         CK(gather_grad(a.id, gu[s], gx[s], L, L + 3 * n, n, c->st));
         CK(push_adjoint<T>(a, sp.start, L, L + 3 * n, P, P + 3 * n, sE, sB, (const T*)c->Eth, Bn, c->g,
-                           SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st));
+                           SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st, En, sEn));
         CK(scatter_grad(a.id, P, P + 3 * n, gu[s], gx[s], n, false, c->st));
     }
     const int fr = adjoint_impl<T>(c, gE, gB, sE, fE, fB, fJ, fM, iters, relres, RELSIM_DEVICE);
@@ -1485,11 +1489,14 @@ int step_adjoint_impl(relsim_ctx* c, double* gE, double* gB, double* const* gu, 
         const PArrays<T> a = arrays<T>(sp, sp.cur);
         double* lw = gw && gw[s] ? P : nullptr;   // the push adjoint's output was scattered already
         CK(deposit_adjoint<T>(a, sp.start, fJ, fM, L, L + 3 * n, lw, sB, Bn, c->g,
-                              SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st));
+                              SpeciesConst{c->cfg.q[s], c->cfg.m[s]}, c->st, En, sEn));
         CK(scatter_grad(a.id, L, L + 3 * n, gu[s], gx[s], n, true, c->st));
         if (lw) CK(scatter_add_w(a.id, lw, gw[s], n, c->st));
     }
-    CK(cudaMemcpyAsync(gE, fE, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToDevice, c->st));
+    if (En)
+        CK(add_fields(fE, sEn, gE, nf, c->st));
+    else
+        CK(cudaMemcpyAsync(gE, fE, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToDevice, c->st));
     CK(add_fields(fB, sB, gB, nf, c->st));
     CK(cudaStreamSynchronize(c->st));
     return fr;
@@ -2577,7 +2584,6 @@ int relsim_step_adjoint(relsim_ctx* c, double* gE, double* gB, double* const* gu
     for (int s = 0; s < c->cfg.nspecies; ++s)
         if (c->sp[s].n > 0 && (!gu[s] || !gx[s])) return fail(c, RELSIM_ERR_INVALID_ARG, "null particle gradient");
     if (!c->cfg.track_ids) return fail(c, RELSIM_ERR_INVALID_ARG, "the step adjoint needs track_ids");
-    if (c->En) return fail(c, RELSIM_ERR_INVALID_ARG, "the step adjoint covers the base scheme (gamma_pred = 0)");
     if (c->state != kReady) return fail(c, RELSIM_ERR_BAD_STATE, "the step adjoint needs a loaded or pushed state");
     int r = relsim_build_mass_matrix(c);
     if (r != RELSIM_OK) return r;

@@ -226,20 +226,23 @@ template <typename T>
 cudaError_t push_general(PArrays<T> src, PArrays<T> dst, const int32_t* start, int32_t* key, const T* Eth,
                          const T* B, const T* En, GridP g, SpeciesConst sc, double* lsum_partial, int lsum_blocks,
                          cudaStream_t st);
-// adjoint of the deposit (base scheme): per particle dL/du^n, dL/dx^{n+1/2}
-// and (gw0 not null) dL/dw from dL/dJhat (3 ncell) and dL/dM (ncell x 45,
-// stored blocks); dL/dB^n added into gB (FP64 atomics)
+// adjoint of the deposit: per particle dL/du^n, dL/dx^{n+1/2} and (gw0 not
+// null) dL/dw from dL/dJhat (3 ncell) and dL/dM (ncell x 45, stored
+// blocks); dL/dB^n added into gB (FP64 atomics). En not null: the
+// predicted gbar = gamma(u^n + beta E^n(x)) with E^n = En, and dL/dE^n
+// added into gEn.
 template <typename T>
 cudaError_t deposit_adjoint(PArrays<T> src, const int32_t* start, const double* gJ, const double* gM, double* gu0,
                             double* gx0, double* gw0, double* gB, const T* B, GridP g, SpeciesConst sc,
-                            cudaStream_t st);
-// adjoint of the push with the fields fixed (base scheme): per particle
-// dL/du^n, dL/dx^{n+1/2} from dL/du^{n+1}, dL/dx^{n+3/2} (FP64, interleaved,
-// current order); dL/dE^{n+theta}, dL/dB^n added into gE, gB (FP64 atomics)
+                            cudaStream_t st, const T* En = nullptr, double* gEn = nullptr);
+// adjoint of the push with the fields fixed: per particle dL/du^n,
+// dL/dx^{n+1/2} from dL/du^{n+1}, dL/dx^{n+3/2} (FP64, interleaved, current
+// order); dL/dE^{n+theta}, dL/dB^n added into gE, gB (FP64 atomics); En not
+// null: the predicted gbar, dL/dE^n added into gEn
 template <typename T>
 cudaError_t push_adjoint(PArrays<T> src, const int32_t* start, const double* gu1, const double* gx1, double* gu0,
                          double* gx0, double* gE, double* gB, const T* Eth, const T* B, GridP g, SpeciesConst sc,
-                         cudaStream_t st);
+                         cudaStream_t st, const T* En = nullptr, double* gEn = nullptr);
 // the stable new-cell order from the runs of push_sort (err bit 1 if the
 // runs and the new cell starts disagree)
 template <typename T>

@@ -1464,17 +1464,19 @@ __device__ __forceinline__ void flush_centres(const A (&gc)[3][3][3], const Runs
 // and d alpha = -alpha d[a]x alpha gives the gradient of a = beta B/gbar.
 // gu1, gx1 are dL/du^{n+1}, dL/dx^{n+3/2} (FP64, interleaved, in the
 // particles' current order); gu0, gx0 receive dL/du^n, dL/dx^{n+1/2}.
-template <typename T>
+template <typename T, bool PRED>
 __global__ void __launch_bounds__(PushCfg<T>::threads, sizeof(T) == 4 ? 4 : 1)
 k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gu1,
                const double* __restrict__ gx1, double* __restrict__ gu0, double* __restrict__ gx0,
                double* __restrict__ gE, double* __restrict__ gB, const T* __restrict__ Eth,
-               const T* __restrict__ B, GridP g, double beta_d)
+               const T* __restrict__ B, GridP g, double beta_d, const T* __restrict__ Eold,
+               double* __restrict__ gEold)
 {
     using A = T;
     constexpr int W = PushCfg<T>::warps;
     __shared__ int sstart[W][kUnitW + 1];
     __shared__ PushTile<T> stile[W];
+    __shared__ PredTile<T, PRED> sen[W];   // E^n of the predicted gbar
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1486,6 +1488,10 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
     for (int u = warp; u < nunits; u += nwarps) {
         const Unit un = unit_of(u, nx);
         unit_setup<T>(un, start, ss, tl, Eth, B, nx, ny, nc, lane);
+        if constexpr (PRED) {
+            load_tile_E<T, 32>(sen[wib].En, Eold, un, nx, ny, nc, lane);
+            __syncwarp();
+        }
         const int P0 = ss[0], P1 = ss[un.cn];
         int cl = 0;
         for (int p0 = P0; p0 < P1; p0 += 32) {
@@ -1494,6 +1500,11 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
             if (act)
                 while (ss[cl + 1] <= p) ++cl;
             A gn[4][3], gc[3][3][3];   // this lane's node and centre scatters
+            A go[PRED ? 4 : 1][3];     // and, predicted gbar, its E^n node scatter
+#pragma unroll
+            for (int q = 0; q < (PRED ? 4 : 1); ++q)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) go[q][k] = A(0);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -1541,8 +1552,22 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
                     Ep[k] = Wn[0] * En[0][k] + Wn[1] * En[1][k] + Wn[2] * En[2][k] + Wn[3] * En[3][k];
                     Bp[k] = Wc[0] * Bc[0][k] + Wc[1] * Bc[1][k] + Wc[2] * Bc[2][k] + Wc[3] * Bc[3][k];
                 }
-                // forward replay
-                const A gb = sqrt(A(1) + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+                // forward replay; gbar = gamma(s), s = u^n or, predicted,
+                // u^n + beta E^n(x)
+                A sv[3] = {u0[0], u0[1], u0[2]};
+                A Eo[PRED ? 4 : 1][3];
+                if constexpr (PRED) {
+                    const T (*te)[2][kTE] = sen[wib].en();
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        Eo[0][k] = te[k][0][cl];
+                        Eo[1][k] = te[k][0][cl + 1];
+                        Eo[2][k] = te[k][1][cl];
+                        Eo[3][k] = te[k][1][cl + 1];
+                        sv[k] += beta * (Wn[0] * Eo[0][k] + Wn[1] * Eo[1][k] + Wn[2] * Eo[2][k] + Wn[3] * Eo[3][k]);
+                    }
+                }
+                const A gb = sqrt(A(1) + sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
                 const A a[3] = {beta * Bp[0] / gb, beta * Bp[1] / gb, beta * Bp[2] / gb};
                 const A ia = A(1) / (A(1) + a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
                 // alpha = (I - [a]x + a a^T)/(1 + |a|^2) = (I + [a]x)^{-1}
@@ -1578,8 +1603,14 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
                                  -(gw[1] * ub[0] - gw[0] * ub[1])};
                 const A gBp[3] = {beta * ga[0] / gb, beta * ga[1] / gb, beta * ga[2] / gb};
                 const A ggb = -beta * (ga[0] * Bp[0] + ga[1] * Bp[1] + ga[2] * Bp[2]) / (gb * gb);
+                // dL/dgbar through gbar = gamma(s): to u^n and, predicted,
+                // to E^n at the particle (beta dL/ds)
+                A gs[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) gu[k] += ggb * u0[k] / gb;
+                for (int k = 0; k < 3; ++k) {
+                    gs[k] = ggb * sv[k] / gb;
+                    gu[k] += gs[k];
+                }
                 const A gEp[3] = {beta * gw[0], beta * gw[1], beta * gw[2]};
                 A gxp = gp[0], gyp = gp[1];
 #pragma unroll
@@ -1590,6 +1621,13 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
                         gn[q][k] = Wn[q] * gEp[k];
                         eg += En[q][k] * gEp[k];
                         bg += Bc[q][k] * gBp[k];
+                    }
+                    if constexpr (PRED) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            go[q][k] = Wn[q] * beta * gs[k];
+                            eg += Eo[q][k] * beta * gs[k];
+                        }
                     }
                     gxp += Wnx[q] * eg + Wcx[q] * bg;
                     gyp += Wny[q] * eg + Wcy[q] * bg;
@@ -1620,6 +1658,15 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
                     const A s = run_sum(gn[q][k], rn);
                     if (rn.head && act) atomicAdd(gE + (int64_t)k * nc + nodes[q], (double)s);
                 }
+            if constexpr (PRED) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const A s = run_sum(go[q][k], rn);
+                        if (rn.head && act) atomicAdd(gEold + (int64_t)k * nc + nodes[q], (double)s);
+                    }
+            }
             flush_centres(gc, rn, act, gB, i, j, nx, ny, nc);
         }
         __syncwarp();
@@ -1634,17 +1681,18 @@ k_push_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* 
 // across the warp, FP64 atomics on the centres) and gbar; the weights'
 // derivatives give dL/dx. Outputs per particle dL/du^n (gu0, interleaved)
 // and dL/dx^{n+1/2} (gx0), FP64.
-template <typename T>
+template <typename T, bool PRED>
 __global__ void __launch_bounds__(PushCfg<T>::threads, sizeof(T) == 4 ? 4 : 1)
 k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const double* __restrict__ gJ,
                   const double* __restrict__ gM, double* __restrict__ gu0, double* __restrict__ gx0,
                   double* __restrict__ gw0, double* __restrict__ gB, const T* __restrict__ B, GridP g, double beta_d,
-                  double cq)
+                  double cq, const T* __restrict__ Eold, double* __restrict__ gEold)
 {
     using A = T;
     constexpr int W = PushCfg<T>::warps;
     __shared__ int sstart[W][kUnitW + 1];
     __shared__ PushTile<T> stile[W];
+    __shared__ PredTile<T, PRED> sen[W];   // E^n of the predicted gbar
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1662,6 +1710,10 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
     for (int u = warp; u < nunits; u += nwarps) {
         const Unit un = unit_of(u, nx);
         unit_setup<T>(un, start, ss, tl, B, B, nx, ny, nc, lane);
+        if constexpr (PRED) {
+            load_tile_E<T, 32>(sen[wib].En, Eold, un, nx, ny, nc, lane);
+            __syncwarp();
+        }
         const int P0 = ss[0], P1 = ss[un.cn];
         int cl = 0;
         for (int p0 = P0; p0 < P1; p0 += 32) {
@@ -1670,6 +1722,11 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
             if (act)
                 while (ss[cl + 1] <= p) ++cl;
             const int i = un.i0 + cl, j = un.j;
+            A go[PRED ? 4 : 1][3];   // predicted gbar: this lane's E^n node scatter
+#pragma unroll
+            for (int q = 0; q < (PRED ? 4 : 1); ++q)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) go[q][k] = A(0);
             A gc[3][3][3];
 #pragma unroll
             for (int k = 0; k < 3; ++k)
@@ -1703,7 +1760,21 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
                     Bp[k] = Wc[0] * Bc[0][k] + Wc[1] * Bc[1][k] + Wc[2] * Bc[2][k] + Wc[3] * Bc[3][k];
-                const A gb = sqrt(A(1) + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+                // gbar = gamma(s), s = u^n or, predicted, u^n + beta E^n(x)
+                A sv[3] = {u0[0], u0[1], u0[2]};
+                A Eo[PRED ? 4 : 1][3];
+                if constexpr (PRED) {
+                    const T (*te)[2][kTE] = sen[wib].en();
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        Eo[0][k] = te[k][0][cl];
+                        Eo[1][k] = te[k][0][cl + 1];
+                        Eo[2][k] = te[k][1][cl];
+                        Eo[3][k] = te[k][1][cl + 1];
+                        sv[k] += beta * (Wn[0] * Eo[0][k] + Wn[1] * Eo[1][k] + Wn[2] * Eo[2][k] + Wn[3] * Eo[3][k]);
+                    }
+                }
+                const A gb = sqrt(A(1) + sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
                 const A a[3] = {beta * Bp[0] / gb, beta * Bp[1] / gb, beta * Bp[2] / gb};
                 const A ia = A(1) / (A(1) + a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
                 A al[3][3];
@@ -1778,16 +1849,29 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
                 const A gav[3] = {Gm[2][1] - Gm[1][2], Gm[0][2] - Gm[2][0], Gm[1][0] - Gm[0][1]};
                 const A gBp[3] = {beta * gav[0] * rgb, beta * gav[1] * rgb, beta * gav[2] * rgb};
                 ggb -= (gav[0] * a[0] + gav[1] * a[1] + gav[2] * a[2]) * rgb;
+                // dL/dgbar through gbar = gamma(s): to u^n and, predicted,
+                // to E^n at the particle (beta dL/ds)
+                A gs[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) gu[k] += ggb * u0[k] * rgb;
+                for (int k = 0; k < 3; ++k) {
+                    gs[k] = ggb * sv[k] * rgb;
+                    gu[k] += gs[k];
+                }
                 A gxp = A(0), gyp = A(0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    A bg = A(0);
+                    A bg = A(0), eo = A(0);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) bg += Bc[q][k] * gBp[k];
-                    gxp += Wnx[q] * gW[q] + Wcx[q] * bg;
-                    gyp += Wny[q] * gW[q] + Wcy[q] * bg;
+                    if constexpr (PRED) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            go[q][k] = Wn[q] * beta * gs[k];
+                            eo += Eo[q][k] * beta * gs[k];
+                        }
+                    }
+                    gxp += Wnx[q] * (gW[q] + eo) + Wcx[q] * bg;
+                    gyp += Wny[q] * (gW[q] + eo) + Wcy[q] * bg;
                 }
                 A Cx[3], Ry[3];
                 centre_factors(lx, ly, tx, ty, Cx, Ry);
@@ -1805,6 +1889,18 @@ k_deposit_adjoint(PArrays<T> src, const int32_t* __restrict__ start, const doubl
             }
             const Runs rn = runs_of(act ? cl : -1, lane);
             flush_centres(gc, rn, act, gB, i, j, nx, ny, nc);
+            if constexpr (PRED) {
+                const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+                const int64_t nodes[4] = {(int64_t)j * nx + i, (int64_t)j * nx + i1, (int64_t)j1 * nx + i,
+                                          (int64_t)j1 * nx + i1};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const A sq = run_sum(go[q][k], rn);
+                        if (rn.head && act) atomicAdd(gEold + (int64_t)k * nc + nodes[q], (double)sq);
+                    }
+            }
         }
         __syncwarp();
     }
@@ -1929,24 +2025,35 @@ cudaError_t permute_batch(const PushDesc<T>* descs, int ninst, int total_units, 
 
 template <typename T>
 cudaError_t deposit_adjoint(PArrays<T> src, const int32_t* start, const double* gJ, const double* gM, double* gu0,
-                            double* gx0, double* gw0, double* gB, const T* B, GridP g, SpeciesConst sc, cudaStream_t st)
+                            double* gx0, double* gw0, double* gB, const T* B, GridP g, SpeciesConst sc, cudaStream_t st,
+                            const T* En, double* gEn)
 {
     const double beta = sc.q * g.dt / (2.0 * sc.m);
     count_launches(1);
-    k_deposit_adjoint<T><<<push_grid_blocks(g, sizeof(T) == 4 ? 32 : 64, 152 * 16), PushCfg<T>::threads, 0, st>>>(
-        src, start, gJ, gM, gu0, gx0, gw0, gB, B, g, beta, sc.q);
+    const int nb = push_grid_blocks(g, sizeof(T) == 4 ? 32 : 64, 152 * 16);
+    if (En)
+        k_deposit_adjoint<T, true><<<nb, PushCfg<T>::threads, 0, st>>>(src, start, gJ, gM, gu0, gx0, gw0, gB, B, g,
+                                                                       beta, sc.q, En, gEn);
+    else
+        k_deposit_adjoint<T, false><<<nb, PushCfg<T>::threads, 0, st>>>(src, start, gJ, gM, gu0, gx0, gw0, gB, B, g,
+                                                                        beta, sc.q, nullptr, nullptr);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t push_adjoint(PArrays<T> src, const int32_t* start, const double* gu1, const double* gx1, double* gu0,
                          double* gx0, double* gE, double* gB, const T* Eth, const T* B, GridP g, SpeciesConst sc,
-                         cudaStream_t st)
+                         cudaStream_t st, const T* En, double* gEn)
 {
     const double beta = sc.q * g.dt / (2.0 * sc.m);
     count_launches(1);
-    k_push_adjoint<T><<<push_grid_blocks(g, sizeof(T) == 4 ? 32 : 64, 152 * 16), PushCfg<T>::threads, 0, st>>>(
-        src, start, gu1, gx1, gu0, gx0, gE, gB, Eth, B, g, beta);
+    const int nb = push_grid_blocks(g, sizeof(T) == 4 ? 32 : 64, 152 * 16);
+    if (En)
+        k_push_adjoint<T, true><<<nb, PushCfg<T>::threads, 0, st>>>(src, start, gu1, gx1, gu0, gx0, gE, gB, Eth, B,
+                                                                    g, beta, En, gEn);
+    else
+        k_push_adjoint<T, false><<<nb, PushCfg<T>::threads, 0, st>>>(src, start, gu1, gx1, gu0, gx0, gE, gB, Eth, B,
+                                                                     g, beta, nullptr, nullptr);
     return cudaGetLastError();
 }
 
@@ -2016,10 +2123,10 @@ cudaError_t spectrum(PArrays<T> p, int64_t n, int variable, const T* edges, int 
                                          cudaStream_t);                                              \
     template cudaError_t deposit_adjoint<T>(PArrays<T>, const int32_t*, const double*, const double*, \
                                             double*, double*, double*, double*, const T*, GridP,      \
-                                            SpeciesConst, cudaStream_t);                              \
+                                            SpeciesConst, cudaStream_t, const T*, double*);           \
     template cudaError_t push_adjoint<T>(PArrays<T>, const int32_t*, const double*, const double*,   \
                                          double*, double*, double*, double*, const T*, const T*,     \
-                                         GridP, SpeciesConst, cudaStream_t);                         \
+                                         GridP, SpeciesConst, cudaStream_t, const T*, double*);      \
     template cudaError_t permute<T>(PArrays<T>, PArrays<T>, const int32_t*, const int32_t*,         \
                                     const int32_t*, GridP, int*, cudaStream_t);                     \
     template cudaError_t kinetic_energy<T>(PArrays<T>, int64_t, double, double*, int, cudaStream_t); \

@@ -33,8 +33,6 @@ class ModeEnergyWindow:
 
     def __init__(self, cfg: relsim_config, nsteps: int, checkpoint_every: int = 5, mode: int = 1,
                  stream=None):
-        if cfg.gamma_pred:
-            raise ValueError("the window's adjoint covers the base scheme (gamma_pred = 0)")
         cfg.track_ids = 1
         self.cfg = cfg
         self.nsteps = int(nsteps)

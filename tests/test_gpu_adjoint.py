@@ -262,18 +262,20 @@ def test_one_step_adjoint_chain_matches_oracle(rs, orc, prec):
     sim.close()
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-def test_step_adjoint_in_place_by_id_matches_oracle(rs, orc, prec):
+@pytest.mark.parametrize("prec,pred", [(64, 0), (32, 0), (64, 1), (32, 1)])
+def test_step_adjoint_in_place_by_id_matches_oracle(rs, orc, prec, pred):
     """relsim_step_adjoint (build, solve and the three adjoints in one call,
     gradients in place and indexed by particle id) on particles relabelled by
     a random permutation, against the oracle's step adjoint on the same
     state: the label-indexed gradients map to the GPU order through the ids
-    read back. FP64 1e-8, FP32 2e-4 of the largest entry."""
+    read back. Both readings of gbar (pred: gamma(u^n + beta E^n(x)), whose
+    chain also reaches E^n and u^n through gbar). FP64 1e-8, FP32 2e-4 of
+    the largest entry."""
     import torch
     nx, ny, dt = 12, 8, 0.6
     q, m = (1.0, -1.0), (1.0, 1.0)
     st = random_state(nx, ny, [8 * nx * ny, 6 * nx * ny], seed=71, u_scale=1.0, field_scale=0.5, q=q, m=m)
-    cfg = rs.make_config(nx, ny, dt=dt, precision=prec, q=q, m=m, track_ids=True,
+    cfg = rs.make_config(nx, ny, dt=dt, precision=prec, q=q, m=m, track_ids=True, gamma_pred=pred,
                          gmres_tol=1e-13 if prec == 64 else 1e-7, gmres_restart=100)
     sim = rs.Simulation(cfg)
     sim.load_state(st)
@@ -295,7 +297,7 @@ def test_step_adjoint_in_place_by_id_matches_oracle(rs, orc, prec):
     # the oracle in the GPU's order: particle k carries label ids[k]
     allp = [{"x": p[0][:, 0], "y": p[0][:, 1], "ux": p[1][:, 0], "uy": p[1][:, 1], "uz": p[1][:, 2], "w": p[2]}
             for p in parts]
-    c = orc.make_config(nx, ny, dt=dt, q=q, m=m, gmres_tol=1e-14, gmres_restart=200)
+    c = orc.make_config(nx, ny, dt=dt, q=q, m=m, gmres_tol=1e-14, gmres_restart=200, gamma_pred=pred)
     gu1 = np.concatenate([gu_lab[s][parts[s][3]] for s in range(2)])
     gx1 = np.concatenate([gx_lab[s][parts[s][3]] for s in range(2)])
     o = orc.step_adjoint(c, orc.Particles(allp), E0, B0, gu1.T, gx1[:, 0], gx1[:, 1], gE1, gB1)

@@ -61,27 +61,27 @@ def state32():
     return st
 
 
-def window(rs, prec):
+def window(rs, prec, pred=0):
     from paper_2509_11100_gb300.window import ModeEnergyWindow
     cfg = rs.make_config(NX, NY, dt=DT, precision=prec, gmres_tol=1e-13 if prec == 64 else 1e-7,
-                         gmres_restart=100)
+                         gmres_restart=100, gamma_pred=pred)
     return ModeEnergyWindow(cfg, STEPS, checkpoint_every=5)
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-def test_window_gradient_matches_oracle(rs, orc, prec):
+@pytest.mark.parametrize("prec,pred", [(64, 0), (32, 0), (64, 1), (32, 1)])
+def test_window_gradient_matches_oracle(rs, orc, prec, pred):
     st = state32()
-    win = window(rs, prec)
+    win = window(rs, prec, pred)
     L = win.forward(st)
     g = win.backward()
     win.close()
-    c = orc.make_config(NX, NY, dt=DT, gmres_tol=1e-14, gmres_restart=200)
+    c = orc.make_config(NX, NY, dt=DT, gmres_tol=1e-14, gmres_restart=200, gamma_pred=pred)
     Lo, go = orc.window_gradient(c, st["species"], st["E"], st["B"], STEPS)
     t = 1e-6 if prec == 64 else 1e-5
     n0 = len(st["species"][0]["w"])
     gu = np.concatenate([g["particles"][s][0] for s in range(2)])
     gx = np.concatenate([g["particles"][s][1] for s in range(2)])
-    print(f"FP{prec} window: loss {abs(L - Lo) / Lo:.1e}, E {rel(g['E'], go['E']):.1e}, B {rel(g['B'], go['B']):.1e}, "
+    print(f"FP{prec} window (gamma_pred={pred}): loss {abs(L - Lo) / Lo:.1e}, E {rel(g['E'], go['E']):.1e}, B {rel(g['B'], go['B']):.1e}, "
           f"u {rel(gu, go['u'].T):.1e}, x {rel(gx, np.stack([go['x'], go['y']], axis=1)):.1e}, "
           f"w {rel(np.concatenate(g['w']), go['w']):.1e} (largest difference over the largest entry)")
     assert abs(L - Lo) < (1e-9 if prec == 64 else 1e-4) * Lo

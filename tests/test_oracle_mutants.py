@@ -72,8 +72,13 @@ PY_MUTANTS = {
     "adjoint_mass_pair_swapped": ("np.outer(L3[:, g], Et[:, h])", "np.outer(L3[:, h], Et[:, g])"),
     "push_adjoint_alpha_untransposed": ('gw = np.einsum("nji,jn->in", alpha, gub)',
                                         'gw = np.einsum("nij,jn->in", alpha, gub)'),
-    "push_adjoint_drops_gbar": ("ggb = -beta * (ga * Bp).sum(axis=0) / gb ** 2\n        gu += ggb * u / gb\n",
+    "push_adjoint_drops_gbar": ("ggb = -beta * (ga * Bp).sum(axis=0) / gb ** 2\n        gu += _gbar_back(c, ggb, u, sv, gb, beta, gN, WN, WNx, WNy, En, gEn, gx0, gy0, a0, a1)\n",
                                 "ggb = -beta * (ga * Bp).sum(axis=0) / gb ** 2\n"),
+    "pred_adjoint_drops_En_path": ("    gEp = beta * gs\n", "    gEp = 0.0 * gs\n"),
+    "pred_push_adjoint_gbar_of_u": ("sv = u + beta * sum(WN[k] * En[:, gN[k]] for k in range(4)) if c.gamma_pred else u\n"
+                                    "        gb = np.sqrt(1.0 + (sv * sv).sum(axis=0))\n        a = beta * Bp / gb\n        n = a1 - a0",
+                                    "sv = u\n"
+                                    "        gb = np.sqrt(1.0 + (sv * sv).sum(axis=0))\n        a = beta * Bp / gb\n        n = a1 - a0"),
     "push_adjoint_B_on_nodes": ("gC, WC, WCx, WCy = _cic(c, x, y, 0.5)\n        Ep = sum(",
                                 "gC, WC, WCx, WCy = _cic(c, x, y, 0.0)\n        Ep = sum("),
     "deposit_adjoint_drops_pair_gbar": ("                ggb -= cM * WN[k] * WN[l] * s2 / gb ** 2\n", "\n"),

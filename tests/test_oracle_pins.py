@@ -1015,6 +1015,120 @@ def test_step_adjoint_matches_directional_derivatives(orc):
     assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-5 * np.abs(g["B"] * dB).sum()
 
 
+def test_predicted_gamma_adjoints_match_directional_derivatives(orc):
+    # the predicted-gamma variant (gbar = gamma(u^n + beta E^n(x))): the push
+    # and deposit adjoints carry dL/dgbar to u, x and E^n; against central
+    # differences of the oracle's own push and deposit, including a
+    # direction in E^n, which reaches the outputs only through gbar
+    nx, ny = 6, 5
+    c = cfg_for(orc, nx, ny, dt=0.7, dx=0.9, dy=1.1, gamma_pred=1)
+    st = random_state(nx, ny, [30, 25], seed=57, dx=0.9, dy=1.1, u_scale=1.3, field_scale=1.1)
+    P0 = orc.Particles(st["species"])
+    Et, B = st["E"], st["B"]
+    rng = np.random.default_rng(23)
+    En = rng.normal(size=Et.shape)
+    N, nn = P0.x.size, nx * ny
+    Lx, Ly = nx * c.dx, ny * c.dy
+    cu, cx, cy = rng.normal(size=(3, N)), rng.normal(size=N), rng.normal(size=N)
+    cJ, cM = rng.normal(size=(3, nn)), rng.normal(size=(nn, 9, 3, 3))
+
+    def L(P0_, Et_, B_, En_):
+        P = P0_.copy()
+        J, M = orc.deposit(c, P, B_, En_)
+        orc.push(c, P, Et_, B_, En_)
+        return (float(np.sum(cu[0] * P.ux + cu[1] * P.uy + cu[2] * P.uz)
+                      + np.sum(cx * np.sin(2 * np.pi * P.x / Lx)) + np.sum(cy * np.cos(2 * np.pi * P.y / Ly))
+                      + np.sum(cJ * J) + np.sum(cM * M)), P)
+
+    _, P1 = L(P0, Et, B, En)
+    gx1 = cx * np.cos(2 * np.pi * P1.x / Lx) * 2 * np.pi / Lx
+    gy1 = -cy * np.sin(2 * np.pi * P1.y / Ly) * 2 * np.pi / Ly
+    gp = orc.push_adjoint(c, P0, Et, B, cu, gx1, gy1, En)
+    gd = orc.deposit_adjoint(c, P0, B, cJ, cM, En)
+    g = {k: gp[k] + gd[k] for k in ("u", "x", "y", "B", "En")}
+    g["E"] = gp["E"]
+    with pytest.raises(ValueError):
+        orc.push_adjoint(c, P0, Et, B, cu, gx1, gy1)
+    h = 1e-6
+
+    def fd(mod):
+        args = []
+        for sgn in (1, -1):
+            P, Ee, Bb, Nn = P0.copy(), Et.copy(), B.copy(), En.copy()
+            mod(P, Ee, Bb, Nn, sgn * h)
+            args.append(L(P, Ee, Bb, Nn)[0])
+        return (args[0] - args[1]) / (2 * h)
+
+    du = rng.normal(size=(3, N))
+    def mu(P, Ee, Bb, Nn, t):
+        P.ux += t * du[0]; P.uy += t * du[1]; P.uz += t * du[2]
+    assert abs(fd(mu) - np.sum(g["u"] * du)) < 1e-6 * np.abs(g["u"] * du).sum()
+    dx, dy = rng.normal(size=N) * 0.1, rng.normal(size=N) * 0.1
+    def mx(P, Ee, Bb, Nn, t):
+        P.x += t * dx; P.y += t * dy
+    assert abs(fd(mx) - np.sum(g["x"] * dx + g["y"] * dy)) < 1e-6 * (np.abs(g["x"] * dx).sum() + np.abs(g["y"] * dy).sum())
+    for name, arr in (("E", Et), ("B", B), ("En", En)):
+        d = rng.normal(size=arr.shape)
+        def mf(P, Ee, Bb, Nn, t, name=name, d=d):
+            {"E": Ee, "B": Bb, "En": Nn}[name][...] += t * d
+        assert abs(fd(mf) - np.sum(g[name] * d)) < 1e-6 * np.abs(g[name] * d).sum(), name
+    # the E^n gradient is the variant's own: zero in the base scheme
+    assert np.abs(gp["En"]).sum() > 0 and np.abs(gd["En"]).sum() > 0
+
+
+def test_predicted_gamma_step_adjoint_matches_directional_derivatives(orc):
+    # one full step of the predicted-gamma variant against central
+    # differences of the oracle's step; E^n enters the solve, the field
+    # update and gbar
+    nx, ny = 6, 5
+    c = cfg_for(orc, nx, ny, dt=0.6, theta=0.5, gmres_tol=1e-14, gmres_restart=200, gamma_pred=1)
+    st = random_state(nx, ny, [40, 30], seed=58, u_scale=1.0, field_scale=0.5)
+    P0 = orc.Particles(st["species"])
+    E0, B0 = st["E"], st["B"]
+    rng = np.random.default_rng(24)
+    N, nn = P0.x.size, nx * ny
+    cu, cx, cy = rng.normal(size=(3, N)), rng.normal(size=N), rng.normal(size=N)
+    cE, cB = rng.normal(size=(3, nn)), rng.normal(size=(3, nn))
+    Lx, Ly = nx * c.dx, ny * c.dy
+
+    def L(P, E, B):
+        P = P.copy()
+        E1, B1, _, _ = orc.step(c, P, E, B)
+        return float(np.sum(cu[0] * P.ux + cu[1] * P.uy + cu[2] * P.uz)
+                     + np.sum(cx * np.sin(2 * np.pi * P.x / Lx)) + np.sum(cy * np.cos(2 * np.pi * P.y / Ly))
+                     + np.sum(cE * E1) + np.sum(cB * B1)), P
+
+    _, P1 = L(P0, E0, B0)
+    gx1 = cx * np.cos(2 * np.pi * P1.x / Lx) * 2 * np.pi / Lx
+    gy1 = -cy * np.sin(2 * np.pi * P1.y / Ly) * 2 * np.pi / Ly
+    g = orc.step_adjoint(c, P0, E0, B0, cu, gx1, gy1, cE, cB)
+    h = 1e-6
+
+    def fd(mod):
+        vals = []
+        for sgn in (1, -1):
+            P, E, B = P0.copy(), E0.copy(), B0.copy()
+            mod(P, E, B, sgn * h)
+            vals.append(L(P, E, B)[0])
+        return (vals[0] - vals[1]) / (2 * h)
+
+    du = rng.normal(size=(3, N))
+    def mu(P, E, B, t):
+        P.ux += t * du[0]; P.uy += t * du[1]; P.uz += t * du[2]
+    assert abs(fd(mu) - np.sum(g["u"] * du)) < 1e-5 * np.abs(g["u"] * du).sum()
+    dx, dy = rng.normal(size=N) * 0.1, rng.normal(size=N) * 0.1
+    def mx(P, E, B, t):
+        P.x += t * dx; P.y += t * dy
+    assert abs(fd(mx) - np.sum(g["x"] * dx + g["y"] * dy)) < 1e-5 * (np.abs(g["x"] * dx).sum() + np.abs(g["y"] * dy).sum())
+    dE, dB = rng.normal(size=E0.shape), rng.normal(size=B0.shape)
+    def mE(P, E, B, t):
+        E += t * dE
+    def mB(P, E, B, t):
+        B += t * dB
+    assert abs(fd(mE) - np.sum(g["E"] * dE)) < 1e-5 * np.abs(g["E"] * dE).sum()
+    assert abs(fd(mB) - np.sum(g["B"] * dB)) < 1e-5 * np.abs(g["B"] * dB).sum()
+
+
 def test_mode_energy_gradient_and_window_gradient(orc):
     # the mode energy's gradient by central differences, and a 3-step
     # window's gradient in E and B by central differences of the oracle's
