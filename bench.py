@@ -820,7 +820,8 @@ def run_window(args):
     st = make_harris(hc)
     N = sum(len(s["w"]) for s in st["species"])
     steps = 20
-    cfg = rs.make_config(hc.nx, hc.ny, dt=hc.dt, precision=32, gmres_tol=1e-7, gmres_restart=60)
+    cfg = rs.make_config(hc.nx, hc.ny, dt=hc.dt, precision=32, gmres_tol=1e-7, gmres_restart=60,
+                         gamma_pred=args.gamma_pred)
     win = ModeEnergyWindow(cfg, steps, checkpoint_every=5)
     win.forward(st)   # warm-up (allocations, graph captures)
     torch.cuda.synchronize()
@@ -835,6 +836,7 @@ def run_window(args):
     out = {"metric": "differentiable window: forward and backward time", "workload":
            "2D double Harris sheet 256x128, 32 ppc per species (2,097,152 particles), 20 RelSIM steps, "
            "checkpoint every 5, loss = B_y k_x=1 mode energy after the window, FP32 form",
+           "gamma_bar": "gamma(u^n + beta E^n(x)) (predicted)" if args.gamma_pred else "gamma(u^n)",
            "particles": N, "steps": steps, "loss": L, "forward_s": t1 - t0, "backward_s": t2 - t1,
            "backward_over_forward": (t2 - t1) / (t1 - t0),
            "grad_norms": {"E": float(np.linalg.norm(g["E"])), "B": float(np.linalg.norm(g["B"])),

@@ -160,7 +160,8 @@ RELSIM_API int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_c
    counterpart in the paper). Safe on NULL. Synchronises the context's stream first. */
 RELSIM_API void relsim_destroy(relsim_ctx* ctx);
 
-/* Message of the last error on this context ("" if none). Owned by ctx. */
+/* Message of the last error on this context ("" if none; no counterpart in
+   the paper). Owned by ctx. */
 RELSIM_API const char* relsim_last_error(const relsim_ctx* ctx);
 
 /* The 3D form (dim = 3, nx, ny, nz >= 3): the same step on a periodic
@@ -512,8 +513,10 @@ RELSIM_API int relsim_field_mode_gradient(relsim_ctx* ctx, int component, int mo
    against k dt over every run of `window` consecutive samples
    (2 <= window <= n), and the largest of them with the index of its first
    sample. Runs containing a non-positive or non-finite sample are skipped.
-   For a mode energy the field amplitude grows at half this rate. Errors:
-   INVALID_ARG (bad sizes, NULL, dt <= 0, or no admissible run). */
+   For a mode energy the field amplitude grows at half this rate (Sec. 3.1:
+   the tearing rate as the best-fit slope of a mode's energy over its linear
+   phase). Errors: INVALID_ARG (bad sizes, NULL, dt <= 0, or no admissible
+   run). */
 RELSIM_API int relsim_growth_fit(const double* s, int n, double dt, int window, double* rate, int* first);
 
 /* Per-mode growth rates and the tearing dispersion fit (host code, no
@@ -550,7 +553,7 @@ typedef struct relsim_batch relsim_batch;
 RELSIM_API int relsim_batch_create(relsim_ctx* const* ctxs, int count, int nworkers, relsim_batch** out);
 
 /* Advance every instance nsteps full steps (relsim_step without the
-   ledger). The workers take instances largest first (by particle count) and
+   ledger; the independent tearing runs of a scan such as Sec. 3.1's). The workers take instances largest first (by particle count) and
    each runs its instance through all steps before taking the next; no two
    threads touch one context. After every step of instance b the energies of
    modes 0 .. nmodes-1 of B's component `component` (as relsim_field_modes)
@@ -588,14 +591,16 @@ RELSIM_API int relsim_batch_run(relsim_batch* b, int nsteps, int component, int 
 RELSIM_API int relsim_batch_set_shared(relsim_batch* b, int on, int groups, int deposit_blocks, int push_blocks);
 
 /* How the last relsim_batch_run advanced the instances after their first
-   step: 0 host-driven workers, 1 per-instance step graphs, 2 shared launches
-   (relsim_batch_set_shared); -1 before any run. */
+   step (no counterpart in the paper): 0 host-driven workers, 1 per-instance
+   step graphs, 2 shared launches (relsim_batch_set_shared); -1 before any
+   run. */
 RELSIM_API int relsim_batch_last_path(const relsim_batch* b);
 
-/* Free the batch (not its contexts). NULL is a no-op. */
+/* Free the batch (not its contexts; no counterpart in the paper). NULL is
+   a no-op. */
 RELSIM_API void relsim_batch_destroy(relsim_batch* b);
 
-/* ---- launch-shape autotuner ----
+/* ---- launch-shape autotuner (no counterpart in the paper) ----
    Times candidate launch shapes of the two heaviest particle kernels on the
    loaded state and keeps the fastest for this context: the deposit's block
    count (it strides over row units of 32 cells: 1, 2, 3, 4 blocks per SM in
@@ -632,10 +637,12 @@ RELSIM_API int relsim_autotune(relsim_ctx* ctx, relsim_tuning* out);
    push at most 16) and the 2D
    operator's tile rows (0 or the form's default: 8 in FP32, 4 in FP64; or
    the alternative: 4 in FP32, 2 in FP64). Results do not depend on the
-   shapes beyond rounding. Errors: INVALID_ARG. */
+   shapes beyond rounding (launch shapes have no counterpart in the paper).
+   Errors: INVALID_ARG. */
 RELSIM_API int relsim_set_launch_shapes(relsim_ctx* ctx, int deposit_blocks, int push_blocks, int op_rows);
 
-/* Library version (major*10000 + minor*100 + patch). */
+/* Library version (major*10000 + minor*100 + patch; no counterpart in the
+   paper). */
 RELSIM_API int relsim_version(void);
 
 /* ---- profiling (the paper has no counterpart; a measurement aid) ----
@@ -661,15 +668,18 @@ typedef struct {
     int64_t kernels[16];     /* kernel launches per slot                    */
 } relsim_profile;
 
-/* Turn event timing on (nonzero) or off. Errors: INVALID_ARG, CUDA. */
+/* Turn event timing on (nonzero) or off (a measurement aid with no
+   counterpart in the paper). Errors: INVALID_ARG, CUDA. */
 RELSIM_API int relsim_profile_enable(relsim_ctx* ctx, int on);
 
-/* Read the accumulated times (synchronises the stream); reset != 0 clears
-   them afterwards. Errors: INVALID_ARG, CUDA. */
+/* Read the accumulated times (synchronises the stream; no counterpart in
+   the paper); reset != 0 clears them afterwards. Errors: INVALID_ARG,
+   CUDA. */
 RELSIM_API int relsim_profile_read(relsim_ctx* ctx, relsim_profile* out, int reset);
 
 /* Total kernel launches made by this library in this process (all
-   contexts), for counting the kernels of a timed region. */
+   contexts), for counting the kernels of a timed region (no counterpart in
+   the paper). */
 RELSIM_API int64_t relsim_kernel_launches(void);
 
 /* ---- allocation-free kinetic energy (the paper has no counterpart) ----

@@ -6,7 +6,8 @@ from one backward pass (the chained step adjoints) against central
 differences of the whole window with h = 1e-3:
 
 * the amplitude of the initial B_y perturbation (0.01), through
-  loss.backward() of the torch.autograd.Function;
+  loss.backward() of the torch.autograd.Function, with either reading of
+  gbar;
 * the sheet half-thickness delta of the loader, pathwise (the window's
   gradients in the initial fields, momenta, positions and weights contracted
   with the loader's central difference at delta -+ h, same random numbers),
@@ -51,10 +52,14 @@ def setup():
     win.close()
 
 
-def test_window_fullsize_gradient_in_amplitude_matches_central_difference(setup):
+@pytest.mark.parametrize("pred", [0, 1])
+def test_window_fullsize_gradient_in_amplitude_matches_central_difference(setup, pred):
     import torch
-    from paper_2509_11100_gb300.window import WindowLoss
+    from paper_2509_11100_gb300.window import ModeEnergyWindow, WindowLoss
     rs, hc, make_harris, HarrisConfig, win = setup
+    if pred:   # the predicted gbar, whose adjoint also runs through E^n and u^n in gbar
+        cfg = rs.make_config(hc.nx, hc.ny, dt=hc.dt, precision=32, gmres_tol=1e-7, gmres_restart=60, gamma_pred=1)
+        win = ModeEnergyWindow(cfg, 20, checkpoint_every=5)
     st = make_harris(hc)
     d = st["derived"]
     xc = np.arange(hc.nx) + 0.5
@@ -73,7 +78,10 @@ def test_window_fullsize_gradient_in_amplitude_matches_central_difference(setup)
 
     fd = (L(hc.pert + H) - L(hc.pert - H)) / (2 * H)
     g = float(pert.grad)
-    print(f"window 256x128: dL/dpert adjoint {g:.6e}, central difference {fd:.6e}, rel {abs(fd - g) / abs(fd):.2e}")
+    if pred:
+        win.close()
+    print(f"window 256x128 (gamma_pred={pred}): dL/dpert adjoint {g:.6e}, central difference {fd:.6e}, "
+          f"rel {abs(fd - g) / abs(fd):.2e}")
     assert np.isfinite(g) and g > 0
     assert abs(fd - g) < 1e-2 * abs(fd), (fd, g)
 
