@@ -332,7 +332,8 @@ RELSIM_API int relsim_field_adjoint(relsim_ctx* ctx, const double* gE1, const do
    contribution. Per particle from the stored values, in the form's
    precision. Call it after relsim_build_mass_matrix and before
    relsim_push. Synchronises the stream. Errors: INVALID_ARG (including a
-   gamma_pred context), BAD_STATE, OOM, CUDA.
+   gamma_pred context: relsim_step_adjoint covers that reading), BAD_STATE,
+   OOM, CUDA.
    One step's adjoint chains the three: relsim_push_adjoint per species
    (giving dL/dE^{n+theta} and part of dL/dB^n), relsim_field_adjoint with
    gEt = their sum (giving dL/dE^n, the field part of dL/dB^n, dL/dJhat,

@@ -16,7 +16,9 @@ the per-particle gradients live in that id order on the device, so no step
 needs a reordering or a host transfer.
 
 Everything runs in the library's kernels; this module only orders the
-calls. It covers the base scheme (gbar = gamma(u^n)).
+calls. It covers both readings of gbar (gamma(u^n), and with gamma_pred the
+predicted gamma(u^n + beta E^n(x)), whose step adjoint also carries dL/dgbar
+to E^n, u^n and x).
 """
 from __future__ import annotations
 

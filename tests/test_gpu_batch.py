@@ -181,6 +181,11 @@ def test_shared_launches_equal_per_instance_graphs(rs, precision, pred, groups):
             sim.load_state(make_harris(hc))
             sims.append(sim)
         batch = rs.Batch(sims, nworkers=3, shared=shared, groups=groups)
+        assert batch.last_path is None
+        for bad in (dict(groups=5000), dict(deposit_blocks=1 << 21)):
+            with pytest.raises(rs.RelsimError):
+                rs.relsim_batch_set_shared(batch.b, True, **bad)
+        batch.set_shared(shared, groups=groups)
         modes, status, iters = batch.run(steps, component=1, nmodes=nm)
         assert list(status) == [0] * len(SIZES)
         assert batch.last_path == ("shared" if shared else "graphs")
