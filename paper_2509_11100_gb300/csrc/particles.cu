@@ -126,6 +126,8 @@ __global__ void k_export(PArrays<T> pa, const int32_t* __restrict__ start, GridP
 constexpr int kUnitW = 32;
 constexpr int kTB = kUnitW + 2;   // centre columns i0-1 .. i0+cn
 constexpr int kTE = kUnitW + 1;   // node columns i0 .. i0+cn
+constexpr int kTBD = 43;          // the deposit's padded row strides (tile_B / tile_E)
+constexpr int kTED = 43;
 
 struct Unit {
     int j, i0, cn, c0;
@@ -147,8 +149,8 @@ __host__ __device__ __forceinline__ int units_of(int nx, int ny) { return ny * (
 // B^n on the centres around a unit: [comp][row j-1, j, j+1][col i0-1 .. i0+cn].
 // NTHR threads (tid < NTHR) share the loads; for a warp the loop unrolls so
 // its loads issue together.
-template <typename T, int NTHR>
-__device__ __forceinline__ void load_tile_B(T (*sB)[3][kTB], const T* __restrict__ B, const Unit& un, int nx,
+template <typename T, int NTHR, int RB = kTB>
+__device__ __forceinline__ void load_tile_B(T (*sB)[3][RB], const T* __restrict__ B, const Unit& un, int nx,
                                             int ny, int nc, int tid)
 {
 #pragma unroll(NTHR < 128 ? 16 : 1)
@@ -163,8 +165,8 @@ __device__ __forceinline__ void load_tile_B(T (*sB)[3][kTB], const T* __restrict
 }
 
 // E^{n+theta} on the nodes of a unit: [comp][row j, j+1][col i0 .. i0+cn]
-template <typename T, int NTHR>
-__device__ __forceinline__ void load_tile_E(T (*sE)[2][kTE], const T* __restrict__ E, const Unit& un, int nx,
+template <typename T, int NTHR, int RE = kTE>
+__device__ __forceinline__ void load_tile_E(T (*sE)[2][RE], const T* __restrict__ E, const Unit& un, int nx,
                                             int ny, int nc, int tid)
 {
 #pragma unroll(NTHR < 128 ? 16 : 1)
@@ -180,8 +182,8 @@ __device__ __forceinline__ void load_tile_E(T (*sE)[2][kTE], const T* __restrict
 
 // B at a particle of local cell l: the centre lattice coordinate is
 // i + fx - 1/2, so the two centres are (i-1, i) when fx < 1/2, else (i, i+1)
-template <typename T>
-__device__ __forceinline__ void tile_B(const T (*sB)[3][kTB], int l, T fx, T fy, T& Bx, T& By, T& Bz)
+template <typename T, int RB = kTB>
+__device__ __forceinline__ void tile_B(const T (*sB)[3][RB], int l, T fx, T fy, T& Bx, T& By, T& Bz)
 {
     const bool lx = fx < T(0.5), ly = fy < T(0.5);
     const T tx = lx ? fx + T(0.5) : fx - T(0.5);
@@ -207,20 +209,20 @@ __device__ __forceinline__ void tile_E(const T (*sE)[2][kTE], int l, T W0, T W1,
 
 // E^n on a unit's nodes, held only by the predicted-gamma variant (gbar =
 // gamma(u^n + beta E^n(x))); empty otherwise
-template <typename T, bool PRED>
+template <typename T, bool PRED, int RE = kTE>
 struct PredTile {
-    __device__ const T (*en() const)[2][kTE] { return nullptr; }
+    __device__ const T (*en() const)[2][RE] { return nullptr; }
 };
-template <typename T>
-struct PredTile<T, true> {
-    T En[3][2][kTE];
-    __device__ const T (*en() const)[2][kTE] { return En; }
+template <typename T, int RE>
+struct PredTile<T, true, RE> {
+    T En[3][2][RE];
+    __device__ const T (*en() const)[2][RE] { return En; }
 };
 
 // |u|^2 of the momentum whose Lorentz factor enters alpha: u^n, or with
 // PRED the predicted u^n + beta E^n(x) (node weights W0..W3 of cell l)
-template <typename T, bool PRED>
-__device__ __forceinline__ T gbar_u2(T ux, T uy, T uz, T beta, const T (*sEn)[2][kTE], int l, T W0, T W1, T W2,
+template <typename T, bool PRED, int RE = kTE>
+__device__ __forceinline__ T gbar_u2(T ux, T uy, T uz, T beta, const T (*sEn)[2][RE], int l, T W0, T W1, T W2,
                                      T W3, T& sx, T& sy, T& sz)
 {
     if (!PRED) {
@@ -389,16 +391,16 @@ struct Moments<float> {
     }
 };
 
-template <typename T, bool PRED>
+template <typename T, bool PRED, int RB = kTB, int RE = kTE>
 __device__ __forceinline__ void deposit_particle(const T fx, const T fy, const T ux, const T uy, const T uz,
-                                                 const T w, const T (*sB)[3][kTB], const T (*sEn)[2][kTE], int l,
+                                                 const T w, const T (*sB)[3][RB], const T (*sEn)[2][RE], int l,
                                                  T beta, T cJ, T cM, Moments<T>& acc)
 {
     T Bx, By, Bz;
-    tile_B(sB, l, fx, fy, Bx, By, Bz);
+    tile_B<T, RB>(sB, l, fx, fy, Bx, By, Bz);
     T sx, sy, sz;
-    const T u2 = gbar_u2<T, PRED>(ux, uy, uz, beta, sEn, l, (T(1) - fx) * (T(1) - fy), fx * (T(1) - fy),
-                                  (T(1) - fx) * fy, fx * fy, sx, sy, sz);
+    const T u2 = gbar_u2<T, PRED, RE>(ux, uy, uz, beta, sEn, l, (T(1) - fx) * (T(1) - fy), fx * (T(1) - fy),
+                                      (T(1) - fx) * fy, fx * fy, sx, sy, sz);
     const Rot<T> r = rotation<T>(u2, Bx, By, Bz, beta);
     const T ax = r.ax, ay = r.ay, az = r.az;
     T e[9];
@@ -508,8 +510,11 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
     __shared__ uint64_t mbar[NB];
     __shared__ int sp0a[NB];      // aligned first particle of the staged range
     __shared__ int sstaged[NB];   // 1 if staged in shared memory, 0 if read from global
-    __shared__ T sB[3][3][kTB];
-    __shared__ PredTile<T, PRED> sEn;
+    // the tiles' rows padded to 43 (11 mod 32 banks): the two rows a warp's
+    // gathers touch, over the six columns of its four cells, fall in
+    // distinct banks (34 would put row r + 1 column c on row r column c + 2)
+    __shared__ T sB[3][3][kTBD];
+    __shared__ PredTile<T, PRED, kTED> sEn;
     T* buf = reinterpret_cast<T*>(dsmem);
     const int tid = threadIdx.x;
     const int gl = tid % G, grp = tid / G;
@@ -567,8 +572,8 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
         const int s = k % nsp;
         if (s == 0) {
             acc.zero();
-            load_tile_B<T, kDepThreads>(sB, src.Bf(ii), un, nx, ny, nc, tid);
-            if constexpr (PRED) load_tile_E<T, kDepThreads>(sEn.En, src.Enf(ii), un, nx, ny, nc, tid);
+            load_tile_B<T, kDepThreads, kTBD>(sB, src.Bf(ii), un, nx, ny, nc, tid);
+            if constexpr (PRED) load_tile_E<T, kDepThreads, kTED>(sEn.En, src.Enf(ii), un, nx, ny, nc, tid);
         }
         const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1), kDepMaxPolls);
         // leave together if any thread gave up (never diverge at a barrier);
@@ -586,14 +591,14 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
             if (sstaged[b]) {
                 const T* sb = buf + (size_t)b * 6 * kDepCap - sp0a[b];
                 for (int p = p0 + gl; p < p1; p += G)
-                    deposit_particle<T, PRED>(sb[p], sb[kDepCap + p], sb[2 * kDepCap + p], sb[3 * kDepCap + p],
+                    deposit_particle<T, PRED, kTBD, kTED>(sb[p], sb[kDepCap + p], sb[2 * kDepCap + p], sb[3 * kDepCap + p],
                                               sb[4 * kDepCap + p], sb[5 * kDepCap + p], sB, sEn.en(), grp, beta,
                                               cJ, cM, acc);
             } else {
                 const T *gfx = src.arr(ii, 0, s), *gfy = src.arr(ii, 1, s), *gux = src.arr(ii, 2, s),
                         *guy = src.arr(ii, 3, s), *guz = src.arr(ii, 4, s), *gw = src.arr(ii, 5, s);
                 for (int p = p0 + gl; p < p1; p += G)
-                    deposit_particle<T, PRED>(ld(gfx + p), ld(gfy + p), ld(gux + p), ld(guy + p), ld(guz + p),
+                    deposit_particle<T, PRED, kTBD, kTED>(ld(gfx + p), ld(gfy + p), ld(gux + p), ld(guy + p), ld(guz + p),
                                               ld(gw + p), sB, sEn.en(), grp, beta, cJ, cM, acc);
             }
         }
