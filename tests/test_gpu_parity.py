@@ -645,9 +645,15 @@ def test_operator_tile_heights_agree(rs, prec):
 def test_double_float_krylov_matches_fp64_krylov(rs, orc, case):
     """The FP32 form keeps its GMRES vectors as double-float pairs (FP32
     arithmetic, ~48-bit values) unless gmres_fp64 is set. Over ten steps the
-    two agree: the same iteration counts (within one), E and B within the
-    solve tolerance's reach (1e-5), ledger residuals at the FP32 floor, and
-    both match the oracle's first solve (E^{n+theta}) to the FP32 bound."""
+    two agree: the same iteration counts (within one), E within the solve
+    tolerance's reach (1e-5) and B within 5e-6, ledger residuals at the FP32
+    floor, and both match the oracle's first solve (E^{n+theta}) to the FP32
+    bound. The FP32 form's deposit adds the cells' mass-matrix and current
+    sums into the nodes with atomics in no fixed order, so two runs of the
+    same configuration differ too: over these ten steps by up to 9.4e-7 in B
+    and 1.7e-6 in E on the ragged case (four runs each, both Krylov forms),
+    as much as the two Krylov forms differ from each other; the B bound
+    stands about five times above that spread."""
     if case == "harris":
         nx, ny, dt = 64, 32, 0.5
         st = fp32_state(harris_small(nx, ny, 16), nx, ny)
@@ -676,7 +682,7 @@ def test_double_float_krylov_matches_fp64_krylov(rs, orc, case):
     print(f"{case}: GMRES iterations double-float {itd.tolist()}, FP64 {itf.tolist()}; "
           f"max ledger residual {rd:.1e} / {rf:.1e}")
     assert np.all(np.abs(itd - itf) <= 1), (itd, itf)
-    assert rel(Ed, Ef) <= 1e-5 and rel(Bd, Bf) <= 1e-6
+    assert rel(Ed, Ef) <= 1e-5 and rel(Bd, Bf) <= 5e-6
     assert rd < 1e-6 and rf < 1e-6
     c = ocfg(orc, nx, ny, dt=dt)
     P = orc.Particles(st["species"])
