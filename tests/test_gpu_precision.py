@@ -11,7 +11,9 @@ FP32 rounding level (6e-8, the dynamics' own conditioning), the relative
 error against the oracle of
   * E and B (relative L2 norm over the grid),
   * the ledger terms W_E, W_B, K (after the step), the particles' work
-    dt sum w q (ubar/gbar).E and the relativistic mismatch term,
+    dt sum w q (ubar/gbar).E (against the larger of its value and its RMS
+    over the run: a signed flow that passes close to zero on some steps)
+    and the relativistic mismatch term,
   * the 256-bin spectrum of gamma - 1 over [1e-2, 1e4] (both species): the
     largest relative error over the bins holding at least 1e-3 of the
     weight, the L1 distance of the weights over all bins, and the particles'
@@ -133,6 +135,7 @@ def run_curves(rs, orc, pred):
     cur = {k: [] for k in ("E", "B") + TERMS + ("spec_bin_max", "spec_l1", "eta")}
     pert = {k: [] for k in cur}
     l1_bound = []
+    raw_work = []   # (oracle, GPU, perturbed oracle) per step
     for n in range(NSTEPS):
         led, status = sim.step(ledger=True)
         assert status == 0
@@ -146,6 +149,9 @@ def run_curves(rs, orc, pred):
         pert["B"].append(float(np.linalg.norm(Bp - B) / nB))
         to, tg, tp = oracle_terms(lo), gpu_terms(led), oracle_terms(lp)
         for k in TERMS:
+            if k == "work":
+                raw_work.append((to[k], tg[k], tp[k]))
+                continue
             cur[k].append(abs(tg[k] - to[k]) / abs(to[k]))
             pert[k].append(abs(tp[k] - to[k]) / abs(to[k]))
         wo = oracle_spectrum(orc, P)
@@ -182,17 +188,27 @@ def run_curves(rs, orc, pred):
         pert["spec_bin_max"].append(spectrum_errors(wp, wo)[0])
         pert["spec_l1"].append(spectrum_errors(wp, wo)[1])
     sim.close()
+    # the particles' work is a signed flow that passes close to zero on some
+    # steps (there the relative error of the GPU and of the perturbed oracle
+    # both jump tenfold); its errors are taken against the larger of its
+    # value and its RMS over the run
+    w = np.array(raw_work)
+    scale = np.maximum(np.abs(w[:, 0]), np.sqrt(np.mean(w[:, 0] ** 2)))
+    cur["work"] = [float(v) for v in np.abs(w[:, 1] - w[:, 0]) / scale]
+    pert["work"] = [float(v) for v in np.abs(w[:, 2] - w[:, 0]) / scale]
     return cur, pert, l1_bound
 
 
 # measured horizons (the last step up to which the error stays below 1e-5;
-# on GB300: E 38, B 63-65, W_E 78-79, W_B 100, K 100, work 15, mismatch 68
-# (gamma(u^n)) and 9 (predicted gamma, a difference of Lorentz factors),
-# minus a margin. The spectrum has no 1e-5 horizon: a particle crossing a
+# on GB300: E 37-38, B 63-66, W_E 78-89, W_B 100, K 100, work 54-60 (its
+# error against its RMS over the run; against its own value the horizon
+# was 4 or 15 from run to run, set by a near-zero work at step 5), mismatch
+# 68-69 (gamma(u^n)) and 9 (predicted gamma, a difference of Lorentz
+# factors), minus a margin. The spectrum has no 1e-5 horizon: a particle crossing a
 # bin edge on one side only moves 2/N of the weight (3e-5 here), so its L1
 # distance is held to the perturbed oracle's instead.
-MIN_HORIZON = {0: {"E": 30, "B": 50, "W_E": 60, "W_B": 80, "K": 80, "work": 10, "mismatch": 40},
-               1: {"E": 30, "B": 50, "W_E": 60, "W_B": 80, "K": 80, "work": 10, "mismatch": 5}}
+MIN_HORIZON = {0: {"E": 30, "B": 50, "W_E": 60, "W_B": 80, "K": 80, "work": 40, "mismatch": 40},
+               1: {"E": 30, "B": 50, "W_E": 60, "W_B": 80, "K": 80, "work": 40, "mismatch": 5}}
 
 
 @pytest.mark.parametrize("pred", [0, 1])
