@@ -2200,6 +2200,7 @@ int relsim_init(const relsim_config* cfg, void* cuda_stream, relsim_ctx** out)
     c->g.dt = cfg->dt;
     c->g.theta = cfg->theta_implicit;
     c->g.dV = cfg->dx * cfg->dy * c->g.dz;
+    grid_derive(c->g);
     // the FP32 form of the 2D scheme with linear shapes keeps its GMRES
     // vectors as double-float pairs (FP32-pipe arithmetic at close to FP64
     // precision) unless FP64 vectors are asked for

@@ -33,6 +33,19 @@ constexpr int kMBlock3 = kHalf3 * 9;
 constexpr int kHalfQ = 13;
 constexpr int kMBlockQ = kHalfQ * 9;
 
+// Constants of the grid and step in one precision, derived on the host
+// (grid_derive): formed in every thread they would each cost FP64 work (a
+// division, a conversion), and this GPU runs every FP64 operation on a pipe
+// about 64 times slower than FP32.
+template <typename T>
+struct GridC {
+    T hdx, hdy;          // 1/(2 dx), 1/(2 dy)
+    T qdx, qdy, qdz;     // 1/(4 dx), 1/(4 dy), 1/(4 dz)
+    T rdx, rdy, rdz;     // 1/dx, 1/dy, 1/dz
+    T dt, theta, td;     // dt, theta, theta dt
+    T hdV, thdV, dtdV;   // dV/2, (theta - 1/2) dV, dt dV
+};
+
 // ncell counts all cells (nx ny nz in 3D); dV is the cell volume (dx dy in
 // 2D). nz = 1, dz = 1 and dim = 2 for the 2D form.
 struct GridP {
@@ -44,7 +57,45 @@ struct GridP {
     int op_y = 0;    // rows of the 2D operator's tiles (0: the form's default)
     int df = 0;      // 1: the GMRES vectors hold double-float pairs (dfloat.cuh)
                      // in their 8-byte slots (FP32 form, 2D, linear shapes)
+    GridC<float> cf{};    // derived constants (grid_derive), FP32
+    GridC<double> cd{};   // and FP64
 };
+
+// x == 1.0 by its bits (an integer compare instead of an FP64 one)
+__device__ __forceinline__ bool is_one(double x) { return __double_as_longlong(x) == 0x3FF0000000000000LL; }
+
+template <typename T>
+__host__ __device__ __forceinline__ const GridC<T>& gc(const GridP& g);
+template <>
+__host__ __device__ __forceinline__ const GridC<float>& gc<float>(const GridP& g) { return g.cf; }
+template <>
+__host__ __device__ __forceinline__ const GridC<double>& gc<double>(const GridP& g) { return g.cd; }
+
+// fill cf and cd from dx, dy, dz, dt, theta and dV (each value formed in FP64
+// and rounded once, as a kernel forming it would)
+template <typename T>
+inline void grid_derive_one(const GridP& g, GridC<T>& c)
+{
+    c.hdx = (T)(0.5 / g.dx);
+    c.hdy = (T)(0.5 / g.dy);
+    c.qdx = (T)(0.25 / g.dx);
+    c.qdy = (T)(0.25 / g.dy);
+    c.qdz = (T)(0.25 / g.dz);
+    c.rdx = (T)(1.0 / g.dx);
+    c.rdy = (T)(1.0 / g.dy);
+    c.rdz = (T)(1.0 / g.dz);
+    c.dt = (T)g.dt;
+    c.theta = (T)g.theta;
+    c.td = (T)(g.theta * g.dt);
+    c.hdV = (T)(0.5 * g.dV);
+    c.thdV = (T)((g.theta - 0.5) * g.dV);
+    c.dtdV = (T)(g.dt * g.dV);
+}
+inline void grid_derive(GridP& g)
+{
+    grid_derive_one(g, g.cf);
+    grid_derive_one(g, g.cd);
+}
 
 __host__ __device__ __forceinline__ int mblock_of(const GridP& g)
 {

@@ -595,13 +595,13 @@ k_op3(const T* __restrict__ M, const double* __restrict__ in, double s, const do
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             own[c] = __ldg(in + c * nc + gidx);
-            if (MODE == k3Arnoldi && s != 1.0) own[c] *= s;
+            if (MODE == k3Arnoldi && !is_one(s)) own[c] *= s;
         }
         auto f = [&](int comp, int a, int bb, int cc) -> T { return sv[comp][tz + cc][ty + bb][tx + a]; };
         T cc3[3], mv[3];
-        curlcurl3<T>(f, T(0.25 / g.dx), T(0.25 / g.dy), T(0.25 / g.dz), cc3);
+        curlcurl3<T>(f, gc<T>(g).qdx, gc<T>(g).qdy, gc<T>(g).qdz, cc3);
         mv3<T, TR>(M, i, j, k, g, f, mv);
-        const T td = T(g.theta * g.dt);
+        const T td = gc<T>(g).td;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double bv = (double)(td * td * cc3[c] + td * mv[c]);
@@ -664,12 +664,12 @@ __global__ void k_rhs3(const T* __restrict__ E, const T* __restrict__ B, const T
                     sy += f[node3(ii[e1], jj[1], kk[e2], g)] - f[node3(ii[e1], jj[0], kk[e2], g)];
                     sz += f[node3(ii[e1], jj[e2], kk[1], g)] - f[node3(ii[e1], jj[e2], kk[0], g)];
                 }
-            d[0][comp] = sx * T(0.25 / g.dx);
-            d[1][comp] = sy * T(0.25 / g.dy);
-            d[2][comp] = sz * T(0.25 / g.dz);
+            d[0][comp] = sx * gc<T>(g).qdx;
+            d[1][comp] = sy * gc<T>(g).qdy;
+            d[2][comp] = sz * gc<T>(g).qdz;
         }
         const T cn[3] = {d[1][2] - d[2][1], d[2][0] - d[0][2], d[0][1] - d[1][0]};
-        const T td = T(g.theta * g.dt);
+        const T td = gc<T>(g).td;
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp)
             b[comp * nc + gi] = (double)(E[comp * nc + gi] + td * cn[comp] - td * J[comp * nc + gi]);
@@ -692,7 +692,7 @@ k_field_update3(const double* __restrict__ x, T* __restrict__ Eth, T* __restrict
     T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (gidx < nc) {
         const int i = (int)(gidx % g.nx), j = (int)((gidx / g.nx) % g.ny), k = (int)(gidx / ((int64_t)g.nx * g.ny));
-        const T th = T(g.theta), hdV = T(0.5 * g.dV);
+        const T th = gc<T>(g).theta, hdV = gc<T>(g).hdV;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T et = (T)x[c * nc + gidx];
@@ -717,12 +717,12 @@ k_field_update3(const double* __restrict__ x, T* __restrict__ Eth, T* __restrict
                     sy += (T)x[comp * nc + node3(ii[e1], jj[1], kk[e2], g)] - (T)x[comp * nc + node3(ii[e1], jj[0], kk[e2], g)];
                     sz += (T)x[comp * nc + node3(ii[e1], jj[e2], kk[1], g)] - (T)x[comp * nc + node3(ii[e1], jj[e2], kk[0], g)];
                 }
-            d[0][comp] = sx * T(0.25 / g.dx);
-            d[1][comp] = sy * T(0.25 / g.dy);
-            d[2][comp] = sz * T(0.25 / g.dz);
+            d[0][comp] = sx * gc<T>(g).qdx;
+            d[1][comp] = sy * gc<T>(g).qdy;
+            d[2][comp] = sz * gc<T>(g).qdz;
         }
         const T curl[3] = {d[1][2] - d[2][1], d[2][0] - d[0][2], d[0][1] - d[1][0]};
-        const T dt = T(g.dt);
+        const T dt = gc<T>(g).dt;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T b0 = B0[c * nc + gidx];
@@ -732,7 +732,7 @@ k_field_update3(const double* __restrict__ x, T* __restrict__ Eth, T* __restrict
             acc[2] += (b1 - b0) * (b1 - b0);
             acc[4] += hdV * b1 * b1;
         }
-        acc[2] *= T((g.theta - 0.5) * g.dV);
+        acc[2] *= gc<T>(g).thdV;
     }
     double v[5], o[5];
 #pragma unroll
@@ -763,7 +763,7 @@ k_work3(const T* __restrict__ M, const T* __restrict__ J, const T* __restrict__ 
         mv3<T, false>(M, i, j, k, g, f, mv);
 #pragma unroll
         for (int c = 0; c < 3; ++c) wk += (J[c * nc + gidx] + mv[c]) * Eth[c * nc + gidx];
-        wk *= T(g.dt * g.dV);
+        wk *= gc<T>(g).dtdV;
     }
     double v[1] = {(double)wk}, o[1];
     block_sum<1>(v, red, o);
@@ -799,9 +799,8 @@ k_push3(PArrays<T> src, const T* __restrict__ sfz, PArrays<T> dst, T* __restrict
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int nseg = (g.nx + 31) / 32;
     const int64_t nunits = (int64_t)nseg * g.ny * g.nz;
-    const int64_t nc = g.ncell;
     int* ss = sst[wib];
-    const T dt = T(g.dt), rdx = T(1.0 / g.dx), rdy = T(1.0 / g.dy), rdz = T(1.0 / g.dz);
+    const T dt = gc<T>(g).dt, rdx = gc<T>(g).rdx, rdy = gc<T>(g).rdy, rdz = gc<T>(g).rdz;
     T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int64_t u = warp; u < nunits; u += nwarps) {
         const int i0 = (int)(u % nseg) * 32;

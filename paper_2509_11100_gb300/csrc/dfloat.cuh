@@ -107,4 +107,27 @@ __device__ __forceinline__ dfl df_warp_sum(dfl a)
     return a;
 }
 
+// a block's double-float sums of N values, converted to FP64 once per block
+// (every thread of the block calls it; red holds 32 N pairs)
+template <int N>
+__device__ __forceinline__ void df_block_sum(dfl (&v)[N], dfl* red, double (&out)[N])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = df_warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) red[wid * N + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            dfl t = lane < nw ? red[lane * N + k] : dfl{0.f, 0.f};
+            t = df_warp_sum(t);
+            out[k] = df_to_double(t);
+        }
+    }
+    __syncthreads();
+}
+
 }  // namespace relsim

@@ -65,7 +65,7 @@ __global__ void k_rhs(const T* __restrict__ E, const T* __restrict__ B, const T*
     const int i = gidx % nx, j = gidx / nx;
     const int im = wrap1(i - 1, nx), jm = wrap1(j - 1, g.ny);
     const int c11 = j * nx + i, c01 = j * nx + im, c10 = jm * nx + i, c00 = jm * nx + im;
-    const T idx2 = T(0.5 / g.dx), idy2 = T(0.5 / g.dy);
+    const T idx2 = gc<T>(g).hdx, idy2 = gc<T>(g).hdy;
     const T* Bx = B;
     const T* By = B + nc;
     const T* Bz = B + 2 * nc;
@@ -73,7 +73,7 @@ __global__ void k_rhs(const T* __restrict__ E, const T* __restrict__ B, const T*
     const T dyBx = (Bx[c11] - Bx[c10] + Bx[c01] - Bx[c00]) * idy2;
     const T dxBz = (Bz[c11] - Bz[c01] + Bz[c10] - Bz[c00]) * idx2;
     const T dyBz = (Bz[c11] - Bz[c10] + Bz[c01] - Bz[c00]) * idy2;
-    const T td = T(g.theta * g.dt);
+    const T td = gc<T>(g).td;
     vst<DF>(b, gidx, E[gidx] + td * dyBz - td * J[gidx]);
     vst<DF>(b, nc + gidx, E[nc + gidx] - td * dxBz - td * J[nc + gidx]);
     vst<DF>(b, 2 * nc + gidx, E[2 * nc + gidx] + td * (dxBy - dyBx) - td * J[2 * nc + gidx]);
@@ -205,7 +205,7 @@ __device__ __forceinline__ void op_parts(const T* __restrict__ M, const double* 
     const T* Mg = M + ((int64_t)ys[1] + xs[1]) * kMBlock;
     const T* Mn[4] = {M + ((int64_t)ys[1] + xs[0]) * kMBlock + 9, M + ((int64_t)ys[0] + xs[2]) * kMBlock + 18,
                       M + ((int64_t)ys[0] + xs[1]) * kMBlock + 27, M + ((int64_t)ys[0] + xs[0]) * kMBlock + 36};
-    op_stencil<T, const T*>(f, Mg, Mn, T(0.5 / g.dx), T(0.5 / g.dy), cc, mv);
+    op_stencil<T, const T*>(f, Mg, Mn, gc<T>(g).hdx, gc<T>(g).hdy, cc, mv);
 }
 
 // ---------------------------------------------------------------------------
@@ -351,10 +351,10 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
         for (int k = 0; k < 3; ++k) {
             if constexpr (DF) {
                 ownd[k] = dld(in, (int64_t)k * nc + gidx);
-                if (MODE == kOpArnoldi && s != 1.0) ownd[k] = df_mul(ownd[k], df_from_double(s));
+                if (MODE == kOpArnoldi && !is_one(s)) ownd[k] = df_mul(ownd[k], df_from_double(s));
             } else {
                 own[k] = __ldg(in + (int64_t)k * nc + gidx);
-                if (MODE == kOpArnoldi && s != 1.0) own[k] *= s;
+                if (MODE == kOpArnoldi && !is_one(s)) own[k] *= s;
             }
         }
     for (int q = tid; q < (th + 1) * 2 * kMBlock; q += NT) {
@@ -401,8 +401,8 @@ k_op(const T* __restrict__ M, const double* __restrict__ in, double s, const dou
         const T* Mn[4] = {blk(tx - 1, ty) + 9, blk(tx + 1, ty - 1) + 18, blk(tx, ty - 1) + 27,
                           blk(tx - 1, ty - 1) + 36};
         T cc[3], mv[3];
-        op_stencil_t<T, const T*, TR>(f, blk(tx, ty), Mn, T(0.5 / g.dx), T(0.5 / g.dy), cc, mv);
-        const T td = T(g.theta * g.dt);
+        op_stencil_t<T, const T*, TR>(f, blk(tx, ty), Mn, gc<T>(g).hdx, gc<T>(g).hdy, cc, mv);
+        const T td = gc<T>(g).td;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const T bvT = td * td * cc[k] + td * mv[k];
@@ -526,7 +526,7 @@ k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* _
     if (gidx < g.ncell) {
         const int nc = g.ncell, nx = g.nx, ny = g.ny;
         const int i = gidx % nx, j = gidx / nx;
-        const T th = T(g.theta), hdV = T(0.5 * g.dV);
+        const T th = gc<T>(g).theta, hdV = gc<T>(g).hdV;
         T et[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) et[k] = vld<T, DF>(x, (int64_t)k * nc + gidx);
@@ -545,7 +545,7 @@ k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* _
         const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
         const int64_t n00 = (int64_t)j * nx + i, n10 = (int64_t)j * nx + i1;
         const int64_t n01 = (int64_t)j1 * nx + i, n11 = (int64_t)j1 * nx + i1;
-        const T idx2 = T(0.5 / g.dx), idy2 = T(0.5 / g.dy);
+        const T idx2 = gc<T>(g).hdx, idy2 = gc<T>(g).hdy;
         T dxE[3], dyE[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -555,7 +555,7 @@ k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* _
             dyE[k] = (c - a + d - b) * idy2;
         }
         const T curl[3] = {dyE[2], -dxE[2], dxE[1] - dyE[0]};
-        const T dt = T(g.dt);
+        const T dt = gc<T>(g).dt;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const T b0 = B0[(int64_t)k * nc + gidx];
@@ -565,19 +565,29 @@ k_field_update(const double* __restrict__ x, const T* __restrict__ M, const T* _
             acc[2] += (b1 - b0) * (b1 - b0);
             acc[4] += hdV * b1 * b1;
         }
-        acc[2] *= T((g.theta - 0.5) * g.dV);
+        acc[2] *= gc<T>(g).thdV;
         // work: dt dV (Jhat + M E^{n+theta}) . E^{n+theta}
         T cc[3], mv[3];
         op_parts<T, DF>(M, x, i, j, g, cc, mv);
         T wk = T(0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) wk += (J[(int64_t)k * nc + gidx] + mv[k]) * et[k];
-        acc[5] = T(g.dt * g.dV) * wk;
+        acc[5] = gc<T>(g).dtdV * wk;
     }
-    double v[kFieldLedger], out[kFieldLedger];
+    double out[kFieldLedger];
+    if constexpr (sizeof(T) == 4) {
+        // the FP32 form: the block's sums as double-float pairs on the FP32
+        // pipe (error-free additions), converted to FP64 once per block
+        dfl v[kFieldLedger];
 #pragma unroll
-    for (int s = 0; s < kFieldLedger; ++s) v[s] = (double)acc[s];
-    block_sum<kFieldLedger>(v, red, out);
+        for (int s = 0; s < kFieldLedger; ++s) v[s] = dfl{acc[s], 0.f};
+        df_block_sum<kFieldLedger>(v, reinterpret_cast<dfl*>(red), out);
+    } else {
+        double v[kFieldLedger];
+#pragma unroll
+        for (int s = 0; s < kFieldLedger; ++s) v[s] = (double)acc[s];
+        block_sum<kFieldLedger>(v, red, out);
+    }
     if (threadIdx.x == 0)
 #pragma unroll
         for (int s = 0; s < kFieldLedger; ++s) partial[(int64_t)blockIdx.x * kFieldLedger + s] = out[s];
@@ -639,28 +649,6 @@ __global__ void k_mass_from_double(const double* __restrict__ Md, const double* 
 
 constexpr int kGmThreads = 256;
 constexpr int kDotChunk = 8;
-
-// a block's double-float sums of N values, converted to FP64 once per block
-template <int N>
-__device__ __forceinline__ void df_block_sum(dfl (&v)[N], dfl* red, double (&out)[N])
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = df_warp_sum(v[k]);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < N; ++k) red[wid * N + k] = v[k];
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            dfl t = lane < nw ? red[lane * N + k] : dfl{0.f, 0.f};
-            t = df_warp_sum(t);
-            out[k] = df_to_double(t);
-        }
-    }
-    __syncthreads();
-}
 
 template <bool DF>
 __global__ void __launch_bounds__(kGmThreads)
@@ -931,8 +919,20 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nblock
         out = dyn->ds;
         if (s >= nsums) return;
     }
+    // the loads of a thread's strided partials issued together (U in
+    // flight), then added in the order of the plain loop
+    constexpr int U = 16;
+    const int nt = blockDim.x;
     double acc = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += partial[(int64_t)b * nsums + s];
+    int b = threadIdx.x;
+    for (; b + (U - 1) * nt < nblocks; b += U * nt) {
+        double t[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) t[u] = partial[(int64_t)(b + u * nt) * nsums + s];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += t[u];
+    }
+    for (; b < nblocks; b += nt) acc += partial[(int64_t)b * nsums + s];
     double v[1] = {acc}, o[1];
     block_sum<1>(v, red, o);
     if (threadIdx.x == 0) out[s] = o[0];
@@ -1279,8 +1279,8 @@ __device__ __forceinline__ void curl_c_at(const double* __restrict__ v, int i, i
     for (int k = 0; k < 3; ++k) {
         const double* f = v + (int64_t)k * nc;
         const double f00 = vget<DF>(f, n00), f10 = vget<DF>(f, n10), f01 = vget<DF>(f, n01), f11 = vget<DF>(f, n11);
-        dx[k] = (f10 - f00 + f11 - f01) * (0.5 / g.dx);
-        dy[k] = (f01 - f00 + f11 - f10) * (0.5 / g.dy);
+        dx[k] = (f10 - f00 + f11 - f01) * g.cd.hdx;
+        dy[k] = (f01 - f00 + f11 - f10) * g.cd.hdy;
     }
     out[0] = dy[2];
     out[1] = -dx[2];
@@ -1298,8 +1298,8 @@ __device__ __forceinline__ void curl_n_at(const double* __restrict__ v, int i, i
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const double* f = v + (int64_t)k * nc;
-        dx[k] = (f[c11] - f[c01] + f[c10] - f[c00]) * (0.5 / g.dx);
-        dy[k] = (f[c11] - f[c10] + f[c01] - f[c00]) * (0.5 / g.dy);
+        dx[k] = (f[c11] - f[c01] + f[c10] - f[c00]) * g.cd.hdx;
+        dy[k] = (f[c11] - f[c10] + f[c01] - f[c00]) * g.cd.hdy;
     }
     out[0] = dy[2];
     out[1] = -dx[2];
@@ -1328,7 +1328,7 @@ __global__ void k_adj_post(const double* __restrict__ gE1, const double* __restr
                            const double* __restrict__ lam, double* __restrict__ gE0, double* __restrict__ gB0,
                            double* __restrict__ gJ, GridP g)
 {
-    const double td = g.theta * g.dt, e1 = (1.0 - g.theta) / g.theta;
+    const double td = g.cd.td, e1 = (1.0 - g.theta) / g.theta;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.ncell; n += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(n % g.nx), j = (int)(n / g.nx);
         double cc[3];
@@ -1349,7 +1349,7 @@ __global__ void k_adj_mass(const double* __restrict__ lam, const T* __restrict__
                            GridP g)
 {
     constexpr int hdi[5] = {0, 1, -1, 0, 1}, hdj[5] = {0, 0, 1, 1, 1};
-    const double td = g.theta * g.dt;
+    const double td = g.cd.td;
     const int nc = g.ncell;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nc; n += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(n % g.nx), j = (int)(n / g.nx);

@@ -5,6 +5,7 @@
 // Particles of a species are stored sorted by cell (SoA, offsets fx, fy in
 // [0,1) within the cell, momenta u = gamma v, weight w). Cell c owns the
 // index range [start[c], start[c+1]).
+#include "dfloat.cuh"
 #include "launch.cuh"
 
 namespace relsim {
@@ -389,18 +390,165 @@ struct Moments<float> {
             for (int q = 0; q < 12; ++q) Jm[q] += __shfl_xor_sync(0xffffffffu, Jm[q], o);
         }
     }
+    // Reduce-scatter over the 8 lanes of a group (recursive halving, partner
+    // distances 4, 2, 1): afterwards lane gl holds the group sums of the 12
+    // flat values 12 gl .. 12 gl + 11, where lane L's block is S[L][0..8]
+    // followed by S[8][3L..3L+2] (L < 3), Jm[3(L-3)..3(L-3)+2] (3 <= L < 7)
+    // or zeros (L = 7). Each sum pairs the lanes' values in the order the
+    // butterfly of group_reduce does, so the results are the same.
+    __device__ __forceinline__ void reduce_scatter8(int gl, float (&r)[12]) const
+    {
+        float v[96];
+#pragma unroll
+        for (int L = 0; L < 8; ++L) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[12 * L + q] = get(L, q);
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                v[12 * L + 9 + e] = L < 3 ? get(8, 3 * L + e) : L < 7 ? Jm[3 * (L - 3) + e] : 0.f;
+        }
+        float h[48];
+        const bool b2 = (gl & 4) != 0, b1 = (gl & 2) != 0, b0 = (gl & 1) != 0;
+#pragma unroll
+        for (int i = 0; i < 48; ++i) {
+            const float keep = b2 ? v[48 + i] : v[i], send = b2 ? v[i] : v[48 + i];
+            h[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        float g[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            const float keep = b1 ? h[24 + i] : h[i], send = b1 ? h[i] : h[24 + i];
+            g[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        }
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const float keep = b0 ? g[12 + i] : g[i], send = b0 ? g[i] : g[12 + i];
+            r[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+        }
+    }
 };
 
-template <typename T, bool PRED, int RB = kTB, int RE = kTE>
+// The node and half offset where the moments S[k][*] of a cell go (k = xx*3
+// + yy): nodes 0..3 = n00, n10, n01, n11; S[4][*] goes to (n00, 4) and also
+// to (n10, 2). Packed 2 and 3 bits per k for a lane-indexed lookup.
+constexpr int kMomNode[9] = {0, 0, 2, 0, 0, 2, 1, 1, 3};
+constexpr int kMomOff[9] = {0, 3, 0, 1, 4, 1, 0, 3, 0};
+constexpr unsigned pack_bits(const int (&a)[9], int w)
+{
+    unsigned v = 0;
+    for (int k = 0; k < 9; ++k) v |= (unsigned)a[k] << (w * k);
+    return v;
+}
+constexpr unsigned kMomNodeBits = pack_bits(kMomNode, 2);
+constexpr unsigned kMomOffBits = pack_bits(kMomOff, 3);
+
+// The deposit's field tiles of a unit: B^n on the centres and, for the
+// predicted gamma, E^n on the nodes. The rows are padded to 43 (11 mod 32
+// banks): the two rows a warp's B gathers touch, over the six columns of its
+// four cells, fall in distinct banks (34 would put row r + 1 column c on
+// row r column c + 2).
+template <typename T, bool PRED>
+struct DepTiles {
+    T B[3][3][kTBD];
+    PredTile<T, PRED, kTED> En;
+    __device__ __forceinline__ void load(const T* __restrict__ Bg, const T* __restrict__ Eg, const Unit& un, int nx,
+                                         int ny, int nc, int tid)
+    {
+        load_tile_B<T, kDepThreads, kTBD>(B, Bg, un, nx, ny, nc, tid);
+        if constexpr (PRED) load_tile_E<T, kDepThreads, kTED>(En.En, Eg, un, nx, ny, nc, tid);
+    }
+    __device__ __forceinline__ void gather_B(int l, T fx, T fy, T& Bx, T& By, T& Bz) const
+    {
+        tile_B<T, kTBD>(B, l, fx, fy, Bx, By, Bz);
+    }
+    __device__ __forceinline__ T u2(T ux, T uy, T uz, T beta, int l, T W0, T W1, T W2, T W3, T& sx, T& sy,
+                                    T& sz) const
+    {
+        return gbar_u2<T, PRED, kTED>(ux, uy, uz, beta, En.en(), l, W0, W1, W2, W3, sx, sy, sz);
+    }
+};
+
+// FP32: every entry holds a value and its right neighbour, so the two
+// columns of a gather come in one 64-bit load (six loads for B, six for E^n
+// instead of twelve each). Rows of 38 pairs (6 mod 16 bank pairs) keep the
+// two rows of a warp's B gathers apart as above.
+constexpr int kTBP = 38;
+template <bool PRED>
+struct DepTiles<float, PRED> {
+    float2 B[3][3][kTBP];   // [comp][row j-1, j, j+1][col]: (B(i0-1+col), B(i0+col)), col = 0..cn
+    float2 En[PRED ? 3 : 1][2][PRED ? kUnitW : 1];   // [comp][row j, j+1][l]: (E(i0+l), E(i0+l+1))
+    __device__ __forceinline__ void load(const float* __restrict__ Bg, const float* __restrict__ Eg, const Unit& un,
+                                         int nx, int ny, int nc, int tid)
+    {
+        for (int idx = tid; idx < 9 * (kUnitW + 1); idx += kDepThreads) {
+            const int comp = idx / (3 * (kUnitW + 1)), r = (idx / (kUnitW + 1)) % 3, col = idx % (kUnitW + 1);
+            if (col <= un.cn) {
+                const int gj = wrap1(un.j - 1 + r, ny);
+                const float* row = Bg + comp * nc + gj * nx;
+                B[comp][r][col] = make_float2(ld(row + wrap1(un.i0 - 1 + col, nx)), ld(row + wrap1(un.i0 + col, nx)));
+            }
+        }
+        if constexpr (PRED) {
+            for (int idx = tid; idx < 6 * kUnitW; idx += kDepThreads) {
+                const int comp = idx / (2 * kUnitW), r = (idx / kUnitW) % 2, l = idx % kUnitW;
+                if (l < un.cn) {
+                    const int gj = wrap1(un.j + r, ny);
+                    const float* row = Eg + comp * nc + gj * nx;
+                    En[comp][r][l] = make_float2(ld(row + wrap1(un.i0 + l, nx)), ld(row + wrap1(un.i0 + l + 1, nx)));
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ void gather_B(int l, float fx, float fy, float& Bx, float& By, float& Bz) const
+    {
+        const bool lx = fx < 0.5f, ly = fy < 0.5f;
+        const float tx = lx ? fx + 0.5f : fx - 0.5f;
+        const float ty = ly ? fy + 0.5f : fy - 0.5f;
+        const int c0 = lx ? l : l + 1;
+        const int r0 = ly ? 0 : 1;
+        const float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty);
+        const float w01 = (1.f - tx) * ty, w11 = tx * ty;
+        const float2 x0 = B[0][r0][c0], x1 = B[0][r0 + 1][c0];
+        Bx = w00 * x0.x + w10 * x0.y + w01 * x1.x + w11 * x1.y;
+        const float2 y0 = B[1][r0][c0], y1 = B[1][r0 + 1][c0];
+        By = w00 * y0.x + w10 * y0.y + w01 * y1.x + w11 * y1.y;
+        const float2 z0 = B[2][r0][c0], z1 = B[2][r0 + 1][c0];
+        Bz = w00 * z0.x + w10 * z0.y + w01 * z1.x + w11 * z1.y;
+    }
+    __device__ __forceinline__ float u2(float ux, float uy, float uz, float beta, int l, float W0, float W1,
+                                        float W2, float W3, float& sx, float& sy, float& sz) const
+    {
+        if constexpr (!PRED) {
+            sx = ux;
+            sy = uy;
+            sz = uz;
+            return ux * ux + uy * uy + uz * uz;
+        } else {
+            // one component at a time, as in gbar_u2
+            const float2 a0 = En[0][0][l], a1 = En[0][1][l];
+            sx = ux + beta * (W0 * a0.x + W1 * a0.y + W2 * a1.x + W3 * a1.y);
+            asm volatile("" ::: "memory");
+            const float2 b0 = En[1][0][l], b1 = En[1][1][l];
+            sy = uy + beta * (W0 * b0.x + W1 * b0.y + W2 * b1.x + W3 * b1.y);
+            asm volatile("" ::: "memory");
+            const float2 c0 = En[2][0][l], c1 = En[2][1][l];
+            sz = uz + beta * (W0 * c0.x + W1 * c0.y + W2 * c1.x + W3 * c1.y);
+            asm volatile("" ::: "memory");
+            return sx * sx + sy * sy + sz * sz;
+        }
+    }
+};
+
+template <typename T, bool PRED>
 __device__ __forceinline__ void deposit_particle(const T fx, const T fy, const T ux, const T uy, const T uz,
-                                                 const T w, const T (*sB)[3][RB], const T (*sEn)[2][RE], int l,
-                                                 T beta, T cJ, T cM, Moments<T>& acc)
+                                                 const T w, const DepTiles<T, PRED>& tl, int l, T beta, T cJ,
+                                                 T cM, Moments<T>& acc)
 {
     T Bx, By, Bz;
-    tile_B<T, RB>(sB, l, fx, fy, Bx, By, Bz);
+    tl.gather_B(l, fx, fy, Bx, By, Bz);
     T sx, sy, sz;
-    const T u2 = gbar_u2<T, PRED, RE>(ux, uy, uz, beta, sEn, l, (T(1) - fx) * (T(1) - fy), fx * (T(1) - fy),
-                                      (T(1) - fx) * fy, fx * fy, sx, sy, sz);
+    const T u2 = tl.u2(ux, uy, uz, beta, l, (T(1) - fx) * (T(1) - fy), fx * (T(1) - fy), (T(1) - fx) * fy,
+                       fx * fy, sx, sy, sz);
     const Rot<T> r = rotation<T>(u2, Bx, By, Bz, beta);
     const T ax = r.ax, ay = r.ay, az = r.az;
     T e[9];
@@ -510,11 +658,7 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
     __shared__ uint64_t mbar[NB];
     __shared__ int sp0a[NB];      // aligned first particle of the staged range
     __shared__ int sstaged[NB];   // 1 if staged in shared memory, 0 if read from global
-    // the tiles' rows padded to 43 (11 mod 32 banks): the two rows a warp's
-    // gathers touch, over the six columns of its four cells, fall in
-    // distinct banks (34 would put row r + 1 column c on row r column c + 2)
-    __shared__ T sB[3][3][kTBD];
-    __shared__ PredTile<T, PRED, kTED> sEn;
+    __shared__ DepTiles<T, PRED> stl;
     T* buf = reinterpret_cast<T*>(dsmem);
     const int tid = threadIdx.x;
     const int gl = tid % G, grp = tid / G;
@@ -572,8 +716,7 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
         const int s = k % nsp;
         if (s == 0) {
             acc.zero();
-            load_tile_B<T, kDepThreads, kTBD>(sB, src.Bf(ii), un, nx, ny, nc, tid);
-            if constexpr (PRED) load_tile_E<T, kDepThreads, kTED>(sEn.En, src.Enf(ii), un, nx, ny, nc, tid);
+            stl.load(src.Bf(ii), src.Enf(ii), un, nx, ny, nc, tid);
         }
         const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1), kDepMaxPolls);
         // leave together if any thread gave up (never diverge at a barrier);
@@ -591,40 +734,74 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
             if (sstaged[b]) {
                 const T* sb = buf + (size_t)b * 6 * kDepCap - sp0a[b];
                 for (int p = p0 + gl; p < p1; p += G)
-                    deposit_particle<T, PRED, kTBD, kTED>(sb[p], sb[kDepCap + p], sb[2 * kDepCap + p], sb[3 * kDepCap + p],
-                                              sb[4 * kDepCap + p], sb[5 * kDepCap + p], sB, sEn.en(), grp, beta,
-                                              cJ, cM, acc);
+                    deposit_particle<T, PRED>(sb[p], sb[kDepCap + p], sb[2 * kDepCap + p], sb[3 * kDepCap + p],
+                                              sb[4 * kDepCap + p], sb[5 * kDepCap + p], stl, grp, beta, cJ, cM,
+                                              acc);
             } else {
                 const T *gfx = src.arr(ii, 0, s), *gfy = src.arr(ii, 1, s), *gux = src.arr(ii, 2, s),
                         *guy = src.arr(ii, 3, s), *guz = src.arr(ii, 4, s), *gw = src.arr(ii, 5, s);
                 for (int p = p0 + gl; p < p1; p += G)
-                    deposit_particle<T, PRED, kTBD, kTED>(ld(gfx + p), ld(gfy + p), ld(gux + p), ld(guy + p), ld(guz + p),
-                                              ld(gw + p), sB, sEn.en(), grp, beta, cJ, cM, acc);
+                    deposit_particle<T, PRED>(ld(gfx + p), ld(gfy + p), ld(gux + p), ld(guy + p), ld(guz + p),
+                                              ld(gw + p), stl, grp, beta, cJ, cM, acc);
             }
         }
         if (s == nsp - 1) {
-            acc.template group_reduce<G>();
             T* const M = src.Mf(ii);
             T* const J = src.Jf(ii);
-            if (valid) {
-                const int i = un.i0 + grp, j = un.j;
-                const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
-                const int n00 = j * nx + i, n10 = j * nx + i1, n01 = j1 * nx + i, n11 = j1 * nx + i1;
-                // (destination node, half offset, moment k) of the ten node pairs
-                const int pn[10] = {n00, n00, n00, n00, n10, n10, n10, n01, n01, n11};
-                constexpr int po[10] = {0, 1, 3, 4, 0, 2, 3, 0, 1, 0};
-                constexpr int pk[10] = {0, 3, 1, 4, 6, 4, 7, 2, 5, 8};
+            if constexpr (std::is_same<T, float>::value) {
+                static_assert(G == 8, "the FP32 flush scatters over 8 lanes");
+                float r[12];
+                acc.reduce_scatter8(gl, r);
+                if (valid) {
+                    const int i = un.i0 + grp, j = un.j;
+                    const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+                    const int n00 = j * nx + i, n10 = j * nx + i1, n01 = j1 * nx + i, n11 = j1 * nx + i1;
+                    // lane gl: S[gl][0..8] to its node and offset (S[4] twice)
+                    const int nd = (kMomNodeBits >> (2 * gl)) & 3, of = (kMomOffBits >> (3 * gl)) & 7;
+                    const int nn = nd == 0 ? n00 : nd == 1 ? n10 : nd == 2 ? n01 : n11;
+                    float* const mk = M + (int64_t)nn * kMBlock + of * 9;
 #pragma unroll
-                for (int it = 0; it < 90; ++it) {
-                    if (it % G == gl) {
-                        const int pr = it / 9, q = it % 9;
-                        atomicAdd(M + (int64_t)pn[pr] * kMBlock + po[pr] * 9 + q, acc.get(pk[pr], q));
+                    for (int q = 0; q < 9; ++q) atomicAdd(mk + q, r[q]);
+                    if (gl == 4) {
+                        float* const m4 = M + (int64_t)n10 * kMBlock + 2 * 9;
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) atomicAdd(m4 + q, r[q]);
+                    }
+                    // the extras: S[8][3gl..3gl+2] (node n11, offset 0) or the
+                    // currents of node gl - 3, components 0..2
+                    if (gl < 3) {
+                        float* const m8 = M + (int64_t)n11 * kMBlock + 3 * gl;
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) atomicAdd(m8 + e, r[9 + e]);
+                    } else if (gl < 7) {
+                        const int a = gl - 3;
+                        const int jn = a == 0 ? n00 : a == 1 ? n10 : a == 2 ? n01 : n11;
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) atomicAdd(J + (int64_t)e * nc + jn, r[9 + e]);
                     }
                 }
-                const int jn[4] = {n00, n10, n01, n11};
+            } else {
+                acc.template group_reduce<G>();
+                if (valid) {
+                    const int i = un.i0 + grp, j = un.j;
+                    const int i1 = wrap1(i + 1, nx), j1 = wrap1(j + 1, ny);
+                    const int n00 = j * nx + i, n10 = j * nx + i1, n01 = j1 * nx + i, n11 = j1 * nx + i1;
+                    // (destination node, half offset, moment k) of the ten node pairs
+                    const int pn[10] = {n00, n00, n00, n00, n10, n10, n10, n01, n01, n11};
+                    constexpr int po[10] = {0, 1, 3, 4, 0, 2, 3, 0, 1, 0};
+                    constexpr int pk[10] = {0, 3, 1, 4, 6, 4, 7, 2, 5, 8};
 #pragma unroll
-                for (int it = 0; it < 12; ++it)
-                    if ((90 + it) % G == gl) atomicAdd(J + (int64_t)(it % 3) * nc + jn[it / 3], acc.Jm[it]);
+                    for (int it = 0; it < 90; ++it) {
+                        if (it % G == gl) {
+                            const int pr = it / 9, q = it % 9;
+                            atomicAdd(M + (int64_t)pn[pr] * kMBlock + po[pr] * 9 + q, acc.get(pk[pr], q));
+                        }
+                    }
+                    const int jn[4] = {n00, n10, n01, n11};
+#pragma unroll
+                    for (int it = 0; it < 12; ++it)
+                        if ((90 + it) % G == gl) atomicAdd(J + (int64_t)(it % 3) * nc + jn[it / 3], acc.Jm[it]);
+                }
             }
         }
         __syncthreads();   // buffer b and the B tile are free for the next stage
@@ -795,10 +972,20 @@ static_assert(PushCfg<float>::cap <= 256 && PushCfg<double>::cap <= 256 && PushC
 template <typename T>
 __device__ __forceinline__ void block_ledger(const T (&acc)[kLedger], double* red, double* __restrict__ lsum)
 {
-    double v[kLedger], out[kLedger];
+    double out[kLedger];
+    if constexpr (sizeof(T) == 4) {
+        // FP32 sums as double-float pairs (error-free additions on the FP32
+        // pipe), one conversion to FP64 per block
+        dfl v[kLedger];
 #pragma unroll
-    for (int s = 0; s < kLedger; ++s) v[s] = (double)acc[s];
-    block_sum<kLedger>(v, red, out);
+        for (int s = 0; s < kLedger; ++s) v[s] = dfl{acc[s], 0.f};
+        df_block_sum<kLedger>(v, reinterpret_cast<dfl*>(red), out);
+    } else {
+        double v[kLedger];
+#pragma unroll
+        for (int s = 0; s < kLedger; ++s) v[s] = (double)acc[s];
+        block_sum<kLedger>(v, red, out);
+    }
     if (threadIdx.x == 0)
 #pragma unroll
         for (int s = 0; s < kLedger; ++s) lsum[(int64_t)blockIdx.x * kLedger + s] = out[s];
@@ -828,26 +1015,15 @@ __device__ __forceinline__ void store_doff(const int* run, int* doff, int lane)
     if (lane <= kNDir) doff[lane] = v;
 }
 
-// the lanes (of those active) whose move direction equals this lane's: one
-// ballot per bit of the direction code
-__device__ __forceinline__ unsigned dir_peers(bool act, int dir)
-{
-    unsigned m = __ballot_sync(0xffffffffu, act);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const unsigned bal = __ballot_sync(0xffffffffu, (dir >> b) & 1);
-        m &= ((dir >> b) & 1) ? bal : ~bal;
-    }
-    return m;
-}
-
 // the warp's ledger sums of one unit added to an instance's slots (FP64)
 template <typename T>
 __device__ __forceinline__ void ledger_to_instance(T (&acc)[kLedger], double* led, int lane)
 {
 #pragma unroll
     for (int s = 0; s < kLedger; ++s) {
-        double v = warp_sum((double)acc[s]);
+        double v;
+        if constexpr (sizeof(T) == 4) v = df_to_double(df_warp_sum(dfl{acc[s], 0.f}));   // FP32 pipe
+        else v = warp_sum((double)acc[s]);
         if (lane == 0) atomicAdd(led + s, v);
         acc[s] = T(0);
     }
@@ -896,7 +1072,7 @@ __device__ __forceinline__ void push_sort_core(PArrays<T> src, PArrays<T> dst, c
             off9 = d.off9;
             Eth = d.Eth;
             B = d.B;
-            En = d.En;
+            if constexpr (PRED) En = d.En;
             nx = d.g.nx;
             ny = d.g.ny;
             nc = d.g.ncell;

@@ -557,14 +557,14 @@ k_op_q(const T* __restrict__ M, const double* __restrict__ in, double s, const d
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             own[c] = __ldg(in + c * nc + gidx);
-            if (MODE == kqArnoldi && s != 1.0) own[c] *= s;
+            if (MODE == kqArnoldi && !is_one(s)) own[c] *= s;
         }
         auto f1 = [&](int comp, int a, int bb) -> T { return sv[comp][ty + 1 + bb][tx + 1 + a]; };
         auto f2 = [&](int comp, int a, int bb) -> T { return sv[comp][ty + bb][tx + a]; };
         T cc[3], mv[3];
-        curlcurl_q<T>(f1, T(0.5 / g.dx), T(0.5 / g.dy), cc);
+        curlcurl_q<T>(f1, gc<T>(g).hdx, gc<T>(g).hdy, cc);
         mv_q<T, TR>(M, i, j, g, f2, mv);
-        const T td = T(g.theta * g.dt);
+        const T td = gc<T>(g).td;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double bv = (double)(td * td * cc[c] + td * mv[c]);
@@ -620,7 +620,7 @@ k_field_update_q(const double* __restrict__ x, T* __restrict__ Eth, T* __restric
     T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (gidx < nc) {
         const int i = (int)(gidx % g.nx), j = (int)(gidx / g.nx);
-        const T th = T(g.theta), hdV = T(0.5 * g.dV);
+        const T th = gc<T>(g).theta, hdV = gc<T>(g).hdV;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T et = (T)x[c * nc + gidx];
@@ -635,7 +635,7 @@ k_field_update_q(const double* __restrict__ x, T* __restrict__ Eth, T* __restric
         const int i1 = wrap1(i + 1, g.nx), j1 = wrap1(j + 1, g.ny);
         const int64_t n00 = (int64_t)j * g.nx + i, n10 = (int64_t)j * g.nx + i1;
         const int64_t n01 = (int64_t)j1 * g.nx + i, n11 = (int64_t)j1 * g.nx + i1;
-        const T idx2 = T(0.5 / g.dx), idy2 = T(0.5 / g.dy);
+        const T idx2 = gc<T>(g).hdx, idy2 = gc<T>(g).hdy;
         T dxE[3], dyE[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -644,7 +644,7 @@ k_field_update_q(const double* __restrict__ x, T* __restrict__ Eth, T* __restric
             dyE[c] = (cq - a + d - bq) * idy2;
         }
         const T curl[3] = {dyE[2], -dxE[2], dxE[1] - dyE[0]};
-        const T dt = T(g.dt);
+        const T dt = gc<T>(g).dt;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T b0 = B0[c * nc + gidx];
@@ -654,7 +654,7 @@ k_field_update_q(const double* __restrict__ x, T* __restrict__ Eth, T* __restric
             acc[2] += (b1 - b0) * (b1 - b0);
             acc[4] += hdV * b1 * b1;
         }
-        acc[2] *= T((g.theta - 0.5) * g.dV);
+        acc[2] *= gc<T>(g).thdV;
     }
     double v[5], o[5];
 #pragma unroll
@@ -683,7 +683,7 @@ k_work_q(const T* __restrict__ M, const T* __restrict__ J, const T* __restrict__
         mv_q<T, false>(M, i, j, g, f, mv);
 #pragma unroll
         for (int c = 0; c < 3; ++c) wk += (J[c * nc + gidx] + mv[c]) * Eth[c * nc + gidx];
-        wk *= T(g.dt * g.dV);
+        wk *= gc<T>(g).dtdV;
     }
     double v[1] = {(double)wk}, o[1];
     block_sum<1>(v, red, o);
@@ -710,7 +710,7 @@ k_push_q(PArrays<T> src, PArrays<T> dst, const int32_t* __restrict__ start, int3
     const int nseg = (g.nx + kQX - 1) / kQX;
     const int nunits = nseg * g.ny;
     int* ss = sst[wib];
-    const T dt = T(g.dt), rdx = T(1.0 / g.dx), rdy = T(1.0 / g.dy);
+    const T dt = gc<T>(g).dt, rdx = gc<T>(g).rdx, rdy = gc<T>(g).rdy;
     T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int u = warp; u < nunits; u += nwarps) {
         const int i0 = (u % nseg) * kQX, j = u / nseg;
