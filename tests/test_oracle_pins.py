@@ -409,19 +409,39 @@ def test_nonrelativistic_limit_conserves_energy(orc):
     assert rel[2] < 1e-11
 
 
-def test_mismatch_shrinks_with_dt(orc):
-    # the relativistic energy error of one step falls off faster than dt
-    vals = []
-    for dt in (0.5, 0.25, 0.125):
+def test_mismatch_sign_and_order_in_dt(orc):
+    """With gbar = gamma(u^n) a particle's mismatch term is
+    w q dt (ubar.E) (2/(g0+g1) - 1/g0). Since u^{n+1} - u^n = 2(ubar - u^n)
+    and ubar - u^n = beta E + ubar x a (the rotation drops out of
+    ubar.(ubar - u^n)), g1 - g0 = 4 beta (E.ubar)/(g0+g1), so the term equals
+    -2 w q^2 dt^2 (ubar.E)^2 / (m g0 (g0+g1)^2): never positive, and second
+    order in dt at a fixed state and field. From the Harris equilibrium
+    (E^0 = 0) the field grows as O(dt), so the second step's mismatch is
+    fourth order. Halving dt must divide it by 4, resp. 16, in the limit."""
+    dts = (0.5, 0.25, 0.125, 0.0625, 0.03125)
+    rng = np.random.default_rng(3)
+    s0 = make_harris(small_harris())
+    assert np.abs(np.asarray(s0["E"])).max() == 0.0
+    Efix = 0.05 * rng.standard_normal(np.asarray(s0["E"]).shape)
+    fixed, equil = [], []
+    for dt in dts:
         hc = small_harris(dt=dt)
         s = make_harris(hc)
         c = cfg_for(orc, hc.nx, hc.ny, dt=dt, gmres_tol=1e-13)
         P = orc.Particles(s["species"])
-        E, B, led, _ = orc.step(c, P, s["E"], s["B"])
-        E, B, led, _ = orc.step(c, P, E, B)
-        vals.append(abs(led["mismatch"]))
-    assert vals[0] > vals[1] > vals[2]
-    assert vals[0] / vals[2] > 4.0
+        _, _, led, _ = orc.step(c, P.copy(), s["E"] + Efix, s["B"])
+        fixed.append(led["mismatch"])
+        E, B, led1, _ = orc.step(c, P, s["E"], s["B"])
+        _, _, led2, _ = orc.step(c, P, E, B)
+        assert led1["mismatch"] <= 0.0
+        equil.append(led2["mismatch"])
+    fixed, equil = np.array(fixed), np.array(equil)
+    assert np.all(fixed < 0.0) and np.all(equil < 0.0)
+    rf = fixed[:-1] / fixed[1:]
+    re = equil[:-1] / equil[1:]
+    # measured: 6.3, 5.1, 4.4, 4.1 (fixed field); 8.9, 13.8, 15.5, 15.9 (from rest)
+    assert np.all(rf > 3.6) and np.all(np.abs(rf[-2:] - 4.0) < 0.6), rf
+    assert np.all(re > 4.0) and np.all(np.abs(re[-2:] - 16.0) < 2.5), re
 
 
 # ---------------------------------------------------------------------------
