@@ -1339,7 +1339,7 @@ int adjoint_impl(relsim_ctx* c, const double* gE1, const double* gB1, const doub
 {
     const int64_t n = c->nvec, nm = (int64_t)c->g.ncell * kMBlock;
     if (where == RELSIM_HOST) TRY(ensure_stage(c, 6 * n + nm));
-    const double *d1, *d2, *d3 = nullptr;
+    const double *d1 = nullptr, *d2 = nullptr, *d3 = nullptr;
     TRY(stage_in(c, gE1, n, where, &d1, 0));
     TRY(stage_in(c, gB1, n, where, &d2, n));
     if (gEt) TRY(stage_in(c, gEt, n, where, &d3, 5 * n + nm));
@@ -1388,7 +1388,7 @@ int deposit_adjoint_impl(relsim_ctx* c, int s, const double* gJ, const double* g
     const int64_t n = sp.n, nf = 3 * (int64_t)c->g.ncell, nm = (int64_t)c->g.ncell * kMBlock;
     const bool host = where == RELSIM_HOST;
     if (host) TRY(ensure_stage(c, nf + nm + 5 * n + nf + n));
-    const double *dJ, *dM;
+    const double *dJ = nullptr, *dM = nullptr;
     TRY(stage_in(c, gJ, nf, where, &dJ, 0));
     TRY(stage_in(c, gM, nm, where, &dM, nf));
     double* ou = host ? c->stage + nf + nm : gu0;
@@ -1420,7 +1420,7 @@ int push_adjoint_impl(relsim_ctx* c, int s, const double* gu1, const double* gx1
     const int64_t n = sp.n, nf = 3 * (int64_t)c->g.ncell;
     const bool host = where == RELSIM_HOST;
     if (host) TRY(ensure_stage(c, 10 * n + 2 * nf));
-    const double *d1, *d2;
+    const double *d1 = nullptr, *d2 = nullptr;
     TRY(stage_in(c, gu1, 3 * n, where, &d1, 0));
     TRY(stage_in(c, gx1, 2 * n, where, &d2, 3 * n));
     double* ou = host ? c->stage + 5 * n : gu0;
