@@ -198,6 +198,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
+// an asynchronous 4-byte copy from global into shared memory (completes
+// at the issuing thread's cp.async.wait_all / wait_group)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// one arrival (release semantics at CTA scope: the thread's earlier shared
+// memory accesses are ordered before a waiter's later ones)
+__device__ __forceinline__ void mbar_arrive(uint64_t* mb)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mb)) : "memory");
+}
+
 // bounded wait on the mbarrier phase with the given parity: at most
 // max_polls polls; false if it gave up
 __device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity, long long max_polls)
@@ -212,6 +226,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity, long lo
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+    }
+    return false;
+}
+
+// the same, also giving up (false) once *abort is set by another warp
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* mb, unsigned parity, long long max_polls,
+                                                   const volatile int* abort)
+{
+    const unsigned a = smem_u32(mb);
+    for (long long it = 0; it < max_polls; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && *abort) return false;
     }
     return false;
 }

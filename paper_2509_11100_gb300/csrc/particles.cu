@@ -293,6 +293,7 @@ constexpr int kDepCells = kDepThreads / kDepG;         // = kUnitW cells per uni
 constexpr int kDepCap = 2176;                          // particles per staged array
 constexpr int kDepBuf = 2;                             // stages in flight
 constexpr long long kDepMaxPolls = 1ll << 26;          // bounded mbarrier wait
+constexpr long long kDepWarpPolls = 1ll << 22;         // bounded wait on the other warps (tiles, refills)
 static_assert(kDepCells == kUnitW, "one group of lanes per cell of a unit");
 
 // Register accumulators of one lane: 81 moments S[k][e] and 12 currents.
@@ -648,83 +649,150 @@ struct DepBatch {
     __device__ __forceinline__ T* Jf(int i) const { return d[i].J; }
 };
 
+// The deposit body. The block's warps share no barrier inside the stage
+// loop: each (unit, species) stage sits in one of two staging buffers,
+// filled by TMA bulk copies (an mbarrier per buffer counts the bytes), and
+// the warp that finishes a stage last refills its buffer with the stage two
+// ahead (the range prefetched in registers one stage earlier); a unit's
+// field tiles alternate between two copies, which every thread fills one
+// unit ahead, with an mbarrier that counts the threads' stores (full) and
+// one that counts the warps done with the unit (free). So the warps drift
+// apart by up to a unit instead of meeting at every stage, and a stage's
+// uneven cells no longer hold the block back. Every wait is bounded; a warp
+// that gives up raises the block's abort flag, the others leave at their
+// next wait, and the copies in flight land before the block exits.
 template <typename T, bool PRED, class Src>
 __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ err)
 {
     constexpr int G = kDepG;
     constexpr int NB = kDepBuf;
+    constexpr int NW = kDepThreads / 32;
     constexpr int A = 16 / sizeof(T);   // elements per 16 bytes (TMA granule)
     extern __shared__ __align__(128) unsigned char dsmem[];
-    __shared__ uint64_t mbar[NB];
-    __shared__ int sp0a[NB];      // aligned first particle of the staged range
-    __shared__ int sstaged[NB];   // 1 if staged in shared memory, 0 if read from global
-    __shared__ DepTiles<T, PRED> stl;
+    __shared__ uint64_t mbar[NB];    // staged particles landed
+    __shared__ uint64_t tfull[2];    // a tile copy stored (kDepThreads arrivals)
+    __shared__ uint64_t tfree[2];    // every warp done with that copy's unit (NW arrivals)
+    __shared__ int sp0a[NB];         // aligned first particle of the staged range
+    __shared__ int sstaged[NB];      // 1 if staged in shared memory, 0 if read from global
+    __shared__ int sdone[NB];        // warps done with the stage in the buffer
+    __shared__ int slast[NB];        // the last stage issued into the buffer
+    __shared__ volatile int sabort;
+    __shared__ int srng[NW][2];      // each warp's copy of the range two stages ahead
+    __shared__ DepTiles<T, PRED> stl[2];
     T* buf = reinterpret_cast<T*>(dsmem);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int gl = tid % G, grp = tid / G;
     const int nsp = src.nsp();
     const int nunits = src.nunits();
     const int myunits = blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int nstages = myunits * nsp;
+    if (nstages == 0) return;
 
-    if (tid == 0) {
-        for (int b = 0; b < NB; ++b) mbar_init(&mbar[b], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    // thread 0: start the copies of stage k into buffer k % NB
-    auto issue = [&](int k) {
-        if (k >= nstages) return;
-        const int b = k % NB;
+    // the range of stage k's particles (lane-local loads of the start table)
+    auto range_of = [&](int k, int& p0, int& p1) {
         const int gu = blockIdx.x + (k / nsp) * gridDim.x;
         const int ii = src.inst(gu);
         const Unit un = unit_of(src.unit(ii, gu), src.grid(ii).nx);
+        const int32_t* st0 = src.start(ii, k % nsp);
+        p0 = st0[un.c0];
+        p1 = st0[un.c0 + un.cn];
+    };
+    // one lane: start the copies of stage k (particles p0 .. p1) into buffer k % NB
+    auto issue = [&](int k, int p0, int p1) {
+        const int b = k % NB;
+        const int gu = blockIdx.x + (k / nsp) * gridDim.x;
+        const int ii = src.inst(gu);
         const int s = k % nsp;
-        const int32_t* st0 = src.start(ii, s);
-        const int p0 = st0[un.c0], p1 = st0[un.c0 + un.cn];
         const int p0a = p0 & ~(A - 1);
         const int p1a = (p1 + A - 1) & ~(A - 1);
         const int cnt = p1a - p0a;
         sp0a[b] = p0a;
+        slast[b] = k;
         if (p1 > p0 && cnt <= kDepCap) {
             sstaged[b] = 1;
             const unsigned bytes = (unsigned)(cnt * sizeof(T));
             mbar_expect_tx_arrive(&mbar[b], 6 * bytes);
             T* dst = buf + (size_t)b * 6 * kDepCap;
 #pragma unroll
-            for (int a = 0; a < 6; ++a) bulk_g2s(dst + a * kDepCap, src.arr(ii, a, s) + p0a, bytes, &mbar[b]);
+            for (int a2 = 0; a2 < 6; ++a2) bulk_g2s(dst + a2 * kDepCap, src.arr(ii, a2, s) + p0a, bytes, &mbar[b]);
         } else {
             sstaged[b] = 0;
             mbar_expect_tx_arrive(&mbar[b], 0);
         }
     };
+    // every thread: its share of unit u's tiles into copy u % 2, then one arrival
+    auto load_tiles = [&](int u) {
+        const int gu = blockIdx.x + u * gridDim.x;
+        const int ii = src.inst(gu);
+        const GridP gg = src.grid(ii);
+        const Unit un = unit_of(src.unit(ii, gu), gg.nx);
+        stl[u & 1].load(src.Bf(ii), src.Enf(ii), un, gg.nx, gg.ny, gg.ncell, tid);
+        mbar_arrive(&tfull[u & 1]);
+    };
 
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&mbar[b], 1);
+            sdone[b] = 0;
+            slast[b] = -1;
+        }
+        for (int x = 0; x < 2; ++x) {
+            mbar_init(&tfull[x], kDepThreads);
+            mbar_init(&tfree[x], NW);
+        }
+        sabort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     if (tid == 0)
-        for (int k = 0; k < NB - 1; ++k) issue(k);
+        for (int k = 0; k < NB && k < nstages; ++k) {
+            int p0, p1;
+            range_of(k, p0, p1);
+            issue(k, p0, p1);
+        }
+    load_tiles(0);
 
     Moments<T> acc;
-    int kfail = -1;
+    bool ok = true;
     for (int k = 0; k < nstages; ++k) {
-        if (tid == 0) issue(k + NB - 1);
         const int b = k % NB;
-        const int gu = blockIdx.x + (k / nsp) * gridDim.x;
+        const int u = k / nsp, s = k % nsp;
+        const int gu = blockIdx.x + u * gridDim.x;
         const int ii = src.inst(gu);
         const GridP gg = src.grid(ii);
         const int nx = gg.nx, ny = gg.ny, nc = gg.ncell;
         const Unit un = unit_of(src.unit(ii, gu), nx);
-        const int s = k % nsp;
         if (s == 0) {
             acc.zero();
-            stl.load(src.Bf(ii), src.Enf(ii), un, nx, ny, nc, tid);
+            if (u + 1 < myunits) {
+                // copy (u+1) % 2 last held unit u - 1: wait until every warp is done with it
+                if (u >= 1) ok = mbar_wait_or_abort(&tfree[(u + 1) & 1], (unsigned)(((u - 1) >> 1) & 1),
+                                                    kDepWarpPolls, &sabort);
+                ok = __all_sync(0xffffffffu, ok);   // the warp leaves as one
+                if (!ok) break;
+                load_tiles(u + 1);
+            }
+            ok = mbar_wait_or_abort(&tfull[u & 1], (unsigned)((u >> 1) & 1), kDepWarpPolls, &sabort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
         }
-        const bool ok = mbar_wait(&mbar[b], (unsigned)((k / NB) & 1), kDepMaxPolls);
-        // leave together if any thread gave up (never diverge at a barrier);
-        // the barrier also publishes the B tile
-        if (__syncthreads_or(!ok)) {
-            kfail = k;
-            break;
+        // the range of the stage this buffer takes next: copied into the
+        // warp's slot by an asynchronous copy while this stage runs (no
+        // registers held across the stage)
+        if (lane == 0 && k + NB < nstages) {
+            const int kn = k + NB;
+            const int gun = blockIdx.x + (kn / nsp) * gridDim.x;
+            const int iin = src.inst(gun);
+            const Unit unn = unit_of(src.unit(iin, gun), src.grid(iin).nx);
+            const int32_t* stn = src.start(iin, kn % nsp);
+            cp_async4(&srng[wid][0], stn + unn.c0);
+            cp_async4(&srng[wid][1], stn + unn.c0 + unn.cn);
+            asm volatile("cp.async.commit_group;" ::: "memory");
         }
+        ok = mbar_wait_or_abort(&mbar[b], (unsigned)((k / NB) & 1), kDepWarpPolls, &sabort);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        const DepTiles<T, PRED>& tl = stl[u & 1];
         const bool valid = grp < un.cn;
         const int c = un.c0 + grp;
         if (valid) {
@@ -735,14 +803,14 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
                 const T* sb = buf + (size_t)b * 6 * kDepCap - sp0a[b];
                 for (int p = p0 + gl; p < p1; p += G)
                     deposit_particle<T, PRED>(sb[p], sb[kDepCap + p], sb[2 * kDepCap + p], sb[3 * kDepCap + p],
-                                              sb[4 * kDepCap + p], sb[5 * kDepCap + p], stl, grp, beta, cJ, cM,
+                                              sb[4 * kDepCap + p], sb[5 * kDepCap + p], tl, grp, beta, cJ, cM,
                                               acc);
             } else {
                 const T *gfx = src.arr(ii, 0, s), *gfy = src.arr(ii, 1, s), *gux = src.arr(ii, 2, s),
                         *guy = src.arr(ii, 3, s), *guz = src.arr(ii, 4, s), *gw = src.arr(ii, 5, s);
                 for (int p = p0 + gl; p < p1; p += G)
                     deposit_particle<T, PRED>(ld(gfx + p), ld(gfy + p), ld(gux + p), ld(guy + p), ld(guz + p),
-                                              ld(gw + p), stl, grp, beta, cJ, cM, acc);
+                                              ld(gw + p), tl, grp, beta, cJ, cM, acc);
             }
         }
         if (s == nsp - 1) {
@@ -804,13 +872,29 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
                 }
             }
         }
-        __syncthreads();   // buffer b and the B tile are free for the next stage
+        // the warp is done with buffer b (and, after its unit's last stage,
+        // with the tile copy); the last warp out refills the buffer
+        __syncwarp();
+        if (lane == 0) {
+            if (atomicAdd(&sdone[b], 1) == NW - 1) {
+                sdone[b] = 0;
+                if (k + NB < nstages) {
+                    asm volatile("cp.async.wait_all;" ::: "memory");
+                    issue(k + NB, srng[wid][0], srng[wid][1]);
+                }
+            }
+            if (s == nsp - 1) mbar_arrive(&tfree[u & 1]);
+        }
     }
-    if (kfail >= 0 && tid == 0) {
-        atomicOr(err, 2);
-        // let the copies already issued land before the CTA leaves (bounded)
-        for (int kk = kfail; kk < nstages && kk < kfail + NB; ++kk) mbar_wait(&mbar[kk % NB], (kk / NB) & 1, kDepMaxPolls);
+    if (!ok) {
+        sabort = 1;
+        if (lane == 0) atomicOr(err, 2);
     }
+    // every warp out of the loop; then the copies still in flight land (bounded)
+    __syncthreads();
+    if (sabort && tid == 0)
+        for (int b = 0; b < NB; ++b)
+            if (slast[b] >= 0) mbar_wait(&mbar[b], (unsigned)((slast[b] / NB) & 1), kDepMaxPolls);
 }
 
 template <typename T, bool PRED>
