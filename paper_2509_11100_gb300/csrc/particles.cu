@@ -653,7 +653,8 @@ struct DepBatch {
 // loop: each (unit, species) stage sits in one of two staging buffers,
 // filled by TMA bulk copies (an mbarrier per buffer counts the bytes), and
 // the warp that finishes a stage last refills its buffer with the stage two
-// ahead (the range prefetched in registers one stage earlier); a unit's
+// ahead (its particle range brought into shared memory by an asynchronous
+// copy one stage earlier); a unit's
 // field tiles alternate between two copies, which every thread fills one
 // unit ahead, with an mbarrier that counts the threads' stores (full) and
 // one that counts the warps done with the unit (free). So the warps drift
