@@ -136,7 +136,6 @@ static double gamma_m1(double ux, double uy, double uz)
     return u2 / (sqrt(1.0 + u2) + 1.0);
 }
 
-/* Offset slot of node b relative to node a, both nodes of one cell. */
 /* the Lorentz factor in alpha and M (step 1) */
 static double gbar_of(const orc_config* c, double beta, const double* E, double x, double y,
                       const double u[3])
@@ -147,6 +146,7 @@ static double gbar_of(const orc_config* c, double beta, const double* E, double 
     return gamma_of(u[0] + beta * Ep[0], u[1] + beta * Ep[1], u[2] + beta * Ep[2]);
 }
 
+/* Offset slot of node b relative to node a, both nodes of one cell. */
 static int pair_slot(const orc_config* c, int64_t ga, int64_t gb)
 {
     int64_t ia = ga % c->nx, ja = ga / c->nx, ib = gb % c->nx, jb = gb / c->nx;
