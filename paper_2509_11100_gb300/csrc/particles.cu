@@ -786,6 +786,9 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
             const int iin = src.inst(gun);
             const Unit unn = unit_of(src.unit(iin, gun), src.grid(iin).nx);
             const int32_t* stn = src.start(iin, kn % nsp);
+            // the slot's previous copy (a stage old, long landed) completes
+            // first: two copies in flight to one address land in no fixed order
+            asm volatile("cp.async.wait_all;" ::: "memory");
             cp_async4(&srng[wid][0], stn + unn.c0);
             cp_async4(&srng[wid][1], stn + unn.c0 + unn.cn);
             asm volatile("cp.async.commit_group;" ::: "memory");
@@ -891,7 +894,9 @@ __device__ __forceinline__ void deposit_core(const Src& src, int* __restrict__ e
         sabort = 1;
         if (lane == 0) atomicOr(err, 2);
     }
-    // every warp out of the loop; then the copies still in flight land (bounded)
+    // every warp out of the loop, its range copies landed; then the bulk
+    // copies still in flight land (bounded)
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (sabort && tid == 0)
         for (int b = 0; b < NB; ++b)
